@@ -1,0 +1,178 @@
+"""ctypes front end of the plain C oracle (dgec_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by the smoke check and by the
+benchmark's CPU-baseline leg; never by the product package.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dgec_oracle.c")
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIB = os.path.join(_LIBDIR, "libdgec_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+I32P = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+I64P = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+U64P = np.ctypeslib.ndpointer(dtype=np.uint64, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with the host C compiler (plain C11, no arch flags)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC",
+                               "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            i64, i32 = ctypes.c_int64, ctypes.c_int32
+            L.orc_validate.argtypes = [i64, i32, I32P, I32P]
+            L.orc_csr.argtypes = [i64, i32, I32P, I32P, I64P, I64P, I32P, I64P, I32P]
+            L.orc_skeleton_raw.argtypes = [i64, i32, I32P, I32P, I64P, I32P, I32P, I64P, I32P]
+            L.orc_skeleton_raw.restype = i64
+            L.orc_skeleton.argtypes = [i64, i32, I32P, I32P, I64P, I32P, I32P, I64P]
+            L.orc_skeleton.restype = i64
+            L.orc_knn.argtypes = [i64, i32, I32P, I32P, I64P, i32, i64, I32P, I32P, I64P]
+            L.orc_mst.argtypes = [i64, i64, I32P, I32P, I64P, I32P, I32P, I64P]
+            L.orc_mst.restype = i64
+            L.orc_linkage.argtypes = [i64, i64, I32P, I32P, I32P, I32P, I64P]
+            L.orc_condense.argtypes = [i64, i64, I32P, I32P, I64P, I64P, i32,
+                                       I32P, U64P, I32P, I32P, U64P, U64P, I64P,
+                                       U64P, U64P, I32P, I32P,
+                                       ctypes.POINTER(i64), ctypes.POINTER(i32)]
+            _lib = L
+    return _lib
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def csr(src, dst, t, n_vertices):
+    src, dst, t = _c(src, np.int32), _c(dst, np.int32), _c(t, np.int64)
+    E = src.shape[0]
+    out_off = np.zeros(n_vertices + 1, np.int64)
+    in_off = np.zeros(n_vertices + 1, np.int64)
+    out_id = np.zeros(max(E, 1), np.int32)
+    in_id = np.zeros(max(E, 1), np.int32)
+    rc = lib().orc_csr(E, n_vertices, src, dst, t, out_off, out_id, in_off, in_id)
+    if rc:
+        raise ValueError(f"oracle csr rc={rc}")
+    return out_off, out_id[:E], in_off, in_id[:E]
+
+
+def skeleton_raw(src, dst, t, n_vertices):
+    src, dst, t = _c(src, np.int32), _c(dst, np.int32), _c(t, np.int64)
+    E = src.shape[0]
+    cap = 2 * E + 1
+    p = np.zeros(cap, np.int32); q = np.zeros(cap, np.int32)
+    w = np.zeros(cap, np.int64); c = np.zeros(cap, np.int32)
+    n = lib().orc_skeleton_raw(E, n_vertices, src, dst, t, p, q, w, c)
+    if n < 0:
+        raise ValueError("oracle skeleton: bad input")
+    return p[:n], q[:n], w[:n], c[:n]
+
+
+def skeleton(src, dst, t, n_vertices):
+    src, dst, t = _c(src, np.int32), _c(dst, np.int32), _c(t, np.int64)
+    E = src.shape[0]
+    cap = 2 * E + 1
+    u = np.zeros(cap, np.int32); v = np.zeros(cap, np.int32); w = np.zeros(cap, np.int64)
+    n = lib().orc_skeleton(E, n_vertices, src, dst, t, u, v, w)
+    if n < 0:
+        raise ValueError("oracle skeleton: bad input")
+    return u[:n], v[:n], w[:n]
+
+
+def knn(src, dst, t, n_vertices, k, query=None):
+    src, dst, t = _c(src, np.int32), _c(dst, np.int32), _c(t, np.int64)
+    E = src.shape[0]
+    if query is None:
+        query = np.arange(E, dtype=np.int32)
+    query = _c(query, np.int32)
+    nq = query.shape[0]
+    ids = np.zeros(max(nq * k, 1), np.int32)
+    core = np.zeros(max(nq, 1), np.int64)
+    rc = lib().orc_knn(E, n_vertices, src, dst, t, k, nq, query, ids, core)
+    if rc:
+        raise ValueError(f"oracle knn rc={rc}")
+    return ids[:nq * k].reshape(nq, k), core[:nq]
+
+
+def mst(n_nodes, u, v, w):
+    u, v, w = _c(u, np.int32), _c(v, np.int32), _c(w, np.int64)
+    n = u.shape[0]
+    mu = np.zeros(max(n_nodes, 1), np.int32); mv = np.zeros(max(n_nodes, 1), np.int32)
+    mw = np.zeros(max(n_nodes, 1), np.int64)
+    m = lib().orc_mst(n_nodes, n, u, v, w, mu, mv, mw)
+    if m < 0:
+        raise MemoryError("oracle mst")
+    return mu[:m], mv[:m], mw[:m]
+
+
+def linkage(n_nodes, mu, mv):
+    mu, mv = _c(mu, np.int32), _c(mv, np.int32)
+    n = mu.shape[0]
+    a = np.zeros(max(n, 1), np.int32); b = np.zeros(max(n, 1), np.int32)
+    s = np.zeros(max(n, 1), np.int64)
+    rc = lib().orc_linkage(n_nodes, n, mu, mv, a, b, s)
+    if rc:
+        raise MemoryError("oracle linkage")
+    return a[:n], b[:n], s[:n]
+
+
+def condense(n_nodes, a, b, w, size, M):
+    a, b, w, size = _c(a, np.int32), _c(b, np.int32), _c(w, np.int64), _c(size, np.int64)
+    n = a.shape[0]
+    n_all = n_nodes + n + 1
+    fall_cluster = np.zeros(max(n_nodes, 1), np.int32)
+    fall_lambda = np.zeros(max(n_nodes, 1), np.uint64)
+    cl_id = np.zeros(n_all, np.int32); cl_parent = np.zeros(n_all, np.int32)
+    cl_birth = np.zeros(n_all, np.uint64); cl_death = np.zeros(n_all, np.uint64)
+    cl_size = np.zeros(n_all, np.int64)
+    hi = np.zeros(n_all, np.uint64); lo = np.zeros(n_all, np.uint64)
+    sel = np.zeros(n_all, np.int32)
+    labels = np.zeros(max(n_nodes, 1), np.int32)
+    ncl = ctypes.c_int64(0); nlab = ctypes.c_int32(0)
+    rc = lib().orc_condense(n_nodes, n, a, b, w, size, M, fall_cluster, fall_lambda,
+                            cl_id, cl_parent, cl_birth, cl_death, cl_size, hi, lo, sel,
+                            labels, ctypes.byref(ncl), ctypes.byref(nlab))
+    if rc:
+        raise ValueError(f"oracle condense rc={rc}")
+    c = ncl.value
+    return dict(fall_cluster=fall_cluster[:n_nodes], fall_lambda=fall_lambda[:n_nodes],
+                cl_id=cl_id[:c], cl_parent=cl_parent[:c], cl_birth=cl_birth[:c],
+                cl_death=cl_death[:c], cl_size=cl_size[:c], cl_stab_hi=hi[:c],
+                cl_stab_lo=lo[:c], cl_selected=sel[:c], labels=labels[:n_nodes],
+                n_clusters=nlab.value)
+
+
+def run(src, dst, t, n_vertices, k, M, knn_query=None):
+    """Alg. 4 end to end: skeleton (Alg. 3) -> Alg. 1 on it; plus kNN/core."""
+    E = len(src)
+    out = {}
+    out["csr"] = csr(src, dst, t, n_vertices)
+    out["skeleton"] = skeleton(src, dst, t, n_vertices)
+    out["knn"] = knn(src, dst, t, n_vertices, k, knn_query)
+    u, v, w = out["skeleton"]
+    out["mst"] = mst(E, u, v, w)
+    mu, mv, mw = out["mst"]
+    out["linkage"] = linkage(E, mu, mv)
+    a, b, s = out["linkage"]
+    out["condensed"] = condense(E, a, b, mw, s, M)
+    return out

@@ -1,0 +1,284 @@
+"""Seeded synthetic dynamic multigraphs (temporal edge lists).
+
+This module only draws inputs: it holds none of the clustering arithmetic.
+Both the CUDA path and the CPU oracle read the arrays it returns.
+
+Every random number comes from a counter-based generator (splitmix64 over a
+counter), so a workload is a pure function of its seed and sizes.
+
+The workloads stand in for the paper's two datasets, which are not shipped
+here: the SNAP e-mail network (Sec. 4.1) and the Reddit comment graph
+(Sec. 4.2). They keep the shape the paper reports: directed edges
+(i, j, t) with integer-second times, no self loops, no repeated
+(i, j, t) triple (Sec. 1.2.1), many timestamp ties, bursty conversations of
+5-200 records, and heavy-tailed vertex degrees.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+_MASK = np.uint64(0xFFFFFFFFFFFFFFFF)
+_GOLD = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+BASE_SEED = 0x231110337
+
+
+def _mix(z: np.ndarray) -> np.ndarray:
+    z = z.astype(np.uint64, copy=True)
+    with np.errstate(over="ignore"):
+        z ^= z >> np.uint64(30)
+        z *= _M1
+        z ^= z >> np.uint64(27)
+        z *= _M2
+        z ^= z >> np.uint64(31)
+    return z
+
+
+class Stream:
+    """splitmix64 stream: value n is mix(seed_state + (n + 1) * golden)."""
+
+    def __init__(self, seed: int, tag: int):
+        with np.errstate(over="ignore"):
+            s = np.array([(seed * 0x100000001B3 + tag) & 0xFFFFFFFFFFFFFFFF],
+                         dtype=np.uint64)
+        self.state = _mix(s + _GOLD)[0]
+        self.pos = 0
+
+    def u64(self, n: int) -> np.ndarray:
+        idx = np.arange(self.pos + 1, self.pos + n + 1, dtype=np.uint64)
+        self.pos += n
+        with np.errstate(over="ignore"):
+            return _mix(self.state + idx * _GOLD)
+
+    def uniform(self, n: int) -> np.ndarray:
+        """Doubles in [0, 1) from the top 53 bits."""
+        return (self.u64(n) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+    def integers(self, lo: int, hi: int, n: int) -> np.ndarray:
+        """Integers in [lo, hi)."""
+        span = hi - lo
+        v = np.floor(self.uniform(n) * span).astype(np.int64)
+        np.minimum(v, span - 1, out=v)
+        return v + lo
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    src: np.ndarray   # int32[E]
+    dst: np.ndarray   # int32[E]
+    t: np.ndarray     # int64[E]
+    n_vertices: int
+    k: int
+    min_cluster_size: int
+    recipe: str
+
+    @property
+    def n_edges(self) -> int:
+        return int(self.src.shape[0])
+
+
+def _zipf_ranks(st: Stream, n: int, n_vertices: int, s: float) -> np.ndarray:
+    """Rank-Zipf draw: P(rank r) proportional to r**-s, r = 1..n_vertices (0-based out)."""
+    r = np.arange(1, n_vertices + 1, dtype=np.float64)
+    cdf = np.cumsum(r ** (-s))
+    cdf /= cdf[-1]
+    u = st.uniform(n)
+    idx = np.searchsorted(cdf, u, side="right")
+    return np.minimum(idx, n_vertices - 1).astype(np.int64)
+
+
+def _permutation(st: Stream, n: int) -> np.ndarray:
+    """Seeded random permutation (argsort of fresh 64-bit draws)."""
+    return np.argsort(st.u64(n), kind="stable").astype(np.int64)
+
+
+def _zipf_endpoints(st: Stream, n: int, n_vertices: int, s: float,
+                    perm: np.ndarray):
+    src = perm[_zipf_ranks(st, n, n_vertices, s)]
+    dst = perm[_zipf_ranks(st, n, n_vertices, s)]
+    # resample self loops (the paper excludes them, Sec. 1.2.1)
+    for _ in range(64):
+        bad = np.nonzero(src == dst)[0]
+        if bad.size == 0:
+            break
+        dst[bad] = perm[_zipf_ranks(st, bad.size, n_vertices, s)]
+    bad = np.nonzero(src == dst)[0]
+    if bad.size:
+        dst[bad] = (src[bad] + 1) % n_vertices
+    return src, dst
+
+
+def _dedupe_triples(src, dst, t):
+    """Make every (i, j, t) triple unique by bumping t of repeats by +1 s."""
+    for _ in range(1000):
+        key = np.lexsort((t, dst, src))
+        s, d, tt = src[key], dst[key], t[key]
+        dup = np.nonzero((s[1:] == s[:-1]) & (d[1:] == d[:-1]) & (tt[1:] == tt[:-1]))[0] + 1
+        if dup.size == 0:
+            return t
+        t[key[dup]] += 1
+    raise RuntimeError("could not make triples unique")
+
+
+def _conversations(st: Stream, n_edges: int, n_vertices: int, span: int,
+                   mean_gap: float = 60.0):
+    """Planted conversations: a group of U{3..20} vertices exchanges a burst of
+    U{5..200} records with floor(Exp(mean_gap)) s gaps; the sender is the
+    previous receiver w.p. 0.75, else a uniform member; the receiver is a
+    uniform other member."""
+    src = np.empty(n_edges, np.int64)
+    dst = np.empty(n_edges, np.int64)
+    t = np.empty(n_edges, np.int64)
+    planted = np.empty(n_edges, np.int64)
+    pos = 0
+    conv = 0
+    # draw conversations in chunks to keep this vectorised
+    while pos < n_edges:
+        chunk = max(1024, (n_edges - pos) // 100 + 1)
+        gsize = st.integers(3, 21, chunk)
+        blen = st.integers(5, 201, chunk)
+        start = st.integers(0, span, chunk)
+        tot = int(blen.sum())
+        # members: gsize uniform vertices per conversation (repeats allowed
+        # across conversations; within one, resample collisions below)
+        mem_off = np.concatenate([[0], np.cumsum(gsize)])
+        members = st.integers(0, n_vertices, int(mem_off[-1]))
+        conv_of = np.repeat(np.arange(chunk), blen)
+        step = np.arange(tot) - np.repeat(np.concatenate([[0], np.cumsum(blen)[:-1]]), blen)
+        gaps = np.floor(-mean_gap * np.log1p(-st.uniform(tot))).astype(np.int64)
+        gaps[step == 0] = 0
+        # time = start + running sum of gaps within the burst
+        csum = np.cumsum(gaps)
+        first = np.concatenate([[0], np.cumsum(blen)[:-1]])
+        base = np.repeat(csum[first] - gaps[first], blen)
+        times = np.repeat(start, blen) + (csum - base)
+        # sender / receiver chain, stepped across all bursts at once
+        keep_prev = st.uniform(tot) < 0.75
+        pick_s = st.integers(0, 1 << 30, tot)
+        pick_r = st.integers(0, 1 << 30, tot)
+        s_loc = np.empty(tot, np.int64)
+        r_loc = np.empty(tot, np.int64)
+        prev_r = np.zeros(chunk, np.int64)
+        for x in range(int(blen.max())):
+            cidx = np.nonzero(blen > x)[0]
+            at = first[cidx] + x
+            g = gsize[cidx]
+            fresh = pick_s[at] % g
+            sl = np.where((x == 0) | ~keep_prev[at], fresh, prev_r[cidx])
+            rl = pick_r[at] % (g - 1)
+            rl = rl + (rl >= sl)
+            s_loc[at] = sl
+            r_loc[at] = rl
+            prev_r[cidx] = rl
+        moff = np.repeat(mem_off[:-1], blen)
+        s_v = members[moff + s_loc]
+        r_v = members[moff + r_loc]
+        take = min(tot, n_edges - pos)
+        src[pos:pos + take] = s_v[:take]
+        dst[pos:pos + take] = r_v[:take]
+        t[pos:pos + take] = times[:take]
+        planted[pos:pos + take] = conv + conv_of[:take]
+        pos += take
+        conv += chunk
+    # two members of one group may coincide: move the receiver to a neighbour id
+    same = src == dst
+    dst[same] = (dst[same] + 1) % n_vertices
+    return src, dst, t, planted
+
+
+def tiny(seed_offset: int = 0, n_edges: int = 20_000, n_vertices: int = 2_000,
+         zipf_s: float = 2.1, t_max: int = 1_000_000, k: int = 4,
+         min_cluster_size: int = 5) -> Workload:
+    """Endpoints rank-Zipf(2.1) by degree, t uniform integer in [0, 1e6)."""
+    seed = BASE_SEED + 0 + 1000 * seed_offset
+    st = Stream(seed, 1)
+    perm = _permutation(Stream(seed, 2), n_vertices)
+    src, dst = _zipf_endpoints(st, n_edges, n_vertices, zipf_s, perm)
+    t = Stream(seed, 3).integers(0, t_max, n_edges)
+    t = _dedupe_triples(src, dst, t)
+    return Workload("tiny", src.astype(np.int32), dst.astype(np.int32), t,
+                    n_vertices, k, min_cluster_size,
+                    f"E={n_edges} V={n_vertices} zipf={zipf_s} t~U[0,{t_max})")
+
+
+def mid(scale: float = 1.0, seed_offset: int = 0, k: int = 8,
+        min_cluster_size: int = 5) -> Workload:
+    """1M vertices, 50M edges at scale 1: 70% planted conversations over a
+    30-day span, 30% Poisson background with Zipf(2.1) endpoints."""
+    seed = BASE_SEED + 1 + 1000 * seed_offset
+    n_edges = int(round(50_000_000 * scale))
+    n_vertices = max(64, int(round(1_000_000 * scale)))
+    span = 30 * 86400
+    n_conv = int(round(0.7 * n_edges))
+    n_bg = n_edges - n_conv
+    cs, cd, ct, _ = _conversations(Stream(seed, 11), n_conv, n_vertices, span)
+    perm = _permutation(Stream(seed, 12), n_vertices)
+    bs, bd = _zipf_endpoints(Stream(seed, 13), n_bg, n_vertices, 2.1, perm)
+    bt = Stream(seed, 14).integers(0, span, n_bg)
+    src = np.concatenate([cs, bs])
+    dst = np.concatenate([cd, bd])
+    t = np.concatenate([ct, bt])
+    order = _permutation(Stream(seed, 15), n_edges)
+    src, dst, t = src[order], dst[order], t[order]
+    t = _dedupe_triples(src, dst, t)
+    return Workload("mid", src.astype(np.int32), dst.astype(np.int32), t,
+                    n_vertices, k, min_cluster_size,
+                    f"E={n_edges} V={n_vertices} span=30d conv=70% bg=30% zipf=2.1")
+
+
+def hub(scale: float = 1.0, seed_offset: int = 0, k: int = 8,
+        min_cluster_size: int = 5) -> Workload:
+    """10M vertices, 200M edges at scale 1: 50% Zipf(1.8) background with t
+    quantised to 60 s, 40% planted conversations, 10% replayed (i, j) pairs
+    on an hourly grid."""
+    seed = BASE_SEED + 2 + 1000 * seed_offset
+    n_edges = int(round(200_000_000 * scale))
+    n_vertices = max(64, int(round(10_000_000 * scale)))
+    span = 30 * 86400
+    n_bg = n_edges // 2
+    n_conv = int(round(0.4 * n_edges))
+    n_rep = n_edges - n_bg - n_conv
+    perm = _permutation(Stream(seed, 21), n_vertices)
+    bs, bd = _zipf_endpoints(Stream(seed, 22), n_bg, n_vertices, 1.8, perm)
+    bt = Stream(seed, 23).integers(0, span // 60, n_bg) * 60
+    cs, cd, ct, _ = _conversations(Stream(seed, 24), n_conv, n_vertices, span)
+    # replayed pairs: a pool of pairs, each used at many hourly slots
+    st = Stream(seed, 25)
+    n_pairs = max(1, n_rep // 50)
+    ps, pd = _zipf_endpoints(st, n_pairs, n_vertices, 1.8, perm)
+    which = st.integers(0, n_pairs, n_rep)
+    rs, rd = ps[which], pd[which]
+    rt = st.integers(0, span // 3600, n_rep) * 3600
+    src = np.concatenate([bs, cs, rs])
+    dst = np.concatenate([bd, cd, rd])
+    t = np.concatenate([bt, ct, rt])
+    order = _permutation(Stream(seed, 26), n_edges)
+    src, dst, t = src[order], dst[order], t[order]
+    t = _dedupe_triples(src, dst, t)
+    return Workload("hub", src.astype(np.int32), dst.astype(np.int32), t,
+                    n_vertices, k, min_cluster_size,
+                    f"E={n_edges} V={n_vertices} bg=50% zipf=1.8 t%60==0, conv=40%, replay=10% hourly")
+
+
+def random_small(n_edges: int, n_vertices: int, t_max: int, seed: int,
+                 zipf_s: float = 0.0) -> Workload:
+    """Small tie-heavy graphs for brute-force checks (t uniform in [0, t_max))."""
+    st = Stream(BASE_SEED + 77 + seed, 31)
+    if zipf_s > 0:
+        perm = _permutation(Stream(BASE_SEED + 77 + seed, 32), n_vertices)
+        src, dst = _zipf_endpoints(st, n_edges, n_vertices, zipf_s, perm)
+    else:
+        src = st.integers(0, n_vertices, n_edges)
+        dst = st.integers(0, n_vertices - 1, n_edges)
+        dst[dst >= src] += 1
+    t = Stream(BASE_SEED + 77 + seed, 33).integers(0, t_max, n_edges)
+    if n_edges:
+        t = _dedupe_triples(src, dst, t)
+    return Workload(f"rand{seed}", src.astype(np.int32), dst.astype(np.int32),
+                    t.astype(np.int64), n_vertices, 3, 3,
+                    f"E={n_edges} V={n_vertices} t~U[0,{t_max})")

@@ -1,0 +1,107 @@
+"""Brute-force constructions on tiny inputs, written from the paper's
+definitions and independent of both the oracle and the CUDA path.
+
+They build the explicit increment-weighted line graph (Def. 1), which the
+method itself never forms, and answer questions about it directly.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def line_graph_arcs(src, dst, t):
+    """All arcs (r, s, w) of L_G (Def. 1): j_r == i_s (P1), t_r <= t_s (P2),
+    w = t_s - t_r (P3)."""
+    src = np.asarray(src); dst = np.asarray(dst); t = np.asarray(t, np.int64)
+    r, s = np.nonzero((dst[:, None] == src[None, :]) & (t[:, None] <= t[None, :]))
+    return r, s, t[s] - t[r]
+
+
+def undirected_edges(src, dst, t):
+    """Undirected version of L_G as a dict {(min, max): w} (weak connectivity,
+    Sec. 2.2). Two arcs between one pair exist only for a reciprocal,
+    concurrent pair; both then weigh 0."""
+    r, s, w = line_graph_arcs(src, dst, t)
+    out = {}
+    for a, b, x in zip(r.tolist(), s.tolist(), w.tolist()):
+        key = (min(a, b), max(a, b))
+        if key in out:
+            assert out[key] == x
+        out[key] = x
+    return out
+
+
+def local_arcs(src, dst, t, i):
+    """Arcs of the node-local line graph L_G(i) (Def. 2) read as the arcs
+    that pass through vertex i: in-edge p of i, out-edge q of i, t_p <= t_q."""
+    src = np.asarray(src); dst = np.asarray(dst); t = np.asarray(t, np.int64)
+    ins = np.nonzero(dst == i)[0]
+    outs = np.nonzero(src == i)[0]
+    arcs = [(int(p), int(q), int(t[q] - t[p])) for p in ins for q in outs if t[p] <= t[q]]
+    return ins, outs, arcs
+
+
+class UnionFind:
+    def __init__(self, n):
+        self.p = list(range(n))
+
+    def find(self, x):
+        while self.p[x] != x:
+            self.p[x] = self.p[self.p[x]]
+            x = self.p[x]
+        return x
+
+    def union(self, a, b):
+        ra, rb = self.find(a), self.find(b)
+        if ra == rb:
+            return False
+        self.p[ra] = rb
+        return True
+
+
+def components(n, edges, omega):
+    """comps(H, omega) (appendix): partition of range(n) by the edges with
+    weight <= omega, as a canonical label array (label = smallest member)."""
+    uf = UnionFind(n)
+    for (a, b), w in edges.items():
+        if w <= omega:
+            uf.union(a, b)
+    root = [uf.find(x) for x in range(n)]
+    first = {}
+    lab = np.empty(n, np.int64)
+    for x in range(n):
+        lab[x] = first.setdefault(root[x], x)
+    return lab
+
+
+def minimax(n, edges):
+    """All-pairs minimax path weight (the smallest omega at which two nodes
+    share a component of comps(H, omega)); inf where never connected."""
+    INF = np.iinfo(np.int64).max
+    D = np.full((n, n), INF, np.int64)
+    np.fill_diagonal(D, 0)
+    for (a, b), w in edges.items():
+        D[a, b] = min(D[a, b], w)
+        D[b, a] = min(D[b, a], w)
+    for k in range(n):
+        D = np.minimum(D, np.maximum(D[:, k:k + 1], D[k:k + 1, :]))
+    return D
+
+
+def knn_bruteforce(src, dst, t, k):
+    """Neighbours of each node in the undirected L_G ranked by (w, id)."""
+    E = len(src)
+    und = undirected_edges(src, dst, t)
+    nb = [[] for _ in range(E)]
+    for (a, b), w in und.items():
+        nb[a].append((w, b))
+        nb[b].append((w, a))
+    ids = np.full((E, k), -1, np.int32)
+    core = np.full(E, np.iinfo(np.int64).max, np.int64)
+    for e in range(E):
+        lst = sorted(nb[e])
+        for x, (w, s) in enumerate(lst[:k]):
+            ids[e, x] = s
+        if len(lst) >= k:
+            core[e] = lst[k - 1][0]
+    return ids, core
