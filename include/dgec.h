@@ -1,0 +1,151 @@
+/*
+ * dgec.h -- C ABI of the GB300 (sm_103a) implementation of the edge
+ * clustering method of "Scalable Edge Clustering of Dynamic Graphs via
+ * Weighted Line Graphs" (arXiv 2311.10337).
+ *
+ * The problem (Sec. 1.2.1, Alg. 4): a dynamic multigraph is a list of
+ * directed temporal edges e = (i_e, j_e, t_e); no self loops; no two edges
+ * share (i, j, t). Each edge is a node of the increment-weighted line graph
+ * L_G (Def. 1): arc r -> s iff j_r == i_s and t_r <= t_s, weight t_s - t_r.
+ * The library clusters the edges by running hierarchical agglomerative
+ * clustering (Alg. 1) on the line-graph skeleton L*_G (Alg. 2-3), which has
+ * the same weighted connectivity as L_G (Thm. 3) but at most 2|E| - |V|
+ * edges, so L_G is never formed.
+ *
+ * Conventions for every call:
+ *   - an edge's id is its position in the input arrays (0 .. n_edges-1);
+ *     ids are the line-graph nodes and the final tie-break everywhere;
+ *   - pointers named d_* are device pointers, h_* host pointers; the caller
+ *     owns all input memory and the workspace; the library never frees it;
+ *   - the library reads inputs and never writes them;
+ *   - all arithmetic is integer, so results are exact and reproducible;
+ *   - every call runs on the given CUDA stream and returns once its results
+ *     are complete (it synchronises that stream before returning);
+ *   - on error the call returns a status != DGEC_OK and a message is kept in
+ *     the context (dgec_last_error); outputs are then unspecified.
+ */
+#ifndef DGEC_H
+#define DGEC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DGEC_OK = 0,
+    DGEC_ERR_INVALID_ARG = 1,   /* null pointer, negative size, k or M out of range */
+    DGEC_ERR_VERTEX_RANGE = 2,  /* a src/dst outside [0, n_vertices) */
+    DGEC_ERR_SELF_LOOP = 3,     /* an edge (i, i, t): excluded by Sec. 1.2.1 */
+    DGEC_ERR_TOO_LARGE = 4,     /* n_edges >= 2^30, or time span too wide (see below) */
+    DGEC_ERR_OOM = 5,           /* workspace smaller than dgec_workspace_size() */
+    DGEC_ERR_CUDA = 6,          /* a CUDA runtime call failed */
+    DGEC_ERR_TIMEOUT = 7,       /* an iterative stage exceeded its round bound */
+    DGEC_ERR_INTERNAL = 9
+} dgec_status;
+
+typedef struct {
+    int32_t k;                /* neighbours per edge for the kNN output, 1 <= k <= 16 */
+    int32_t min_cluster_size; /* M of Alg. 1 step 4, M >= 2 */
+    uint32_t flags;           /* reserved, must be 0 */
+} dgec_params;
+
+typedef struct dgec_ctx dgec_ctx;
+
+/* Results of dgec_run. Device arrays point into the caller's workspace and
+ * stay valid until that workspace is reused. Counts are host values. */
+typedef struct {
+    /* Alg. 3 first line: incidence lists. Vertex v's out-edges are
+     * out_id[out_off[v] .. out_off[v+1]) with times out_t[..], sorted by
+     * (t, id); likewise in-edges via in_off/in_t/in_id. */
+    const int64_t *out_off, *in_off;   /* [n_vertices + 1] */
+    const int64_t *out_t, *in_t;       /* [n_edges] */
+    const int32_t *out_id, *in_id;     /* [n_edges] */
+    /* Alg. 3: skeleton L*_G as undirected edges (u < v, w = |t_u - t_v|),
+     * each line-graph edge once, in a deterministic order (see DESIGN). */
+    const int32_t *sk_u, *sk_v;        /* [n_skeleton] */
+    const int64_t *sk_w;
+    /* k nearest line-graph neighbours in time: knn_id[e*k + x], ranked by
+     * (|dt|, id), -1 padded; core[e] = |dt| of the k-th, INT64_MAX if the
+     * node has fewer than k neighbours. */
+    const int32_t *knn_id;             /* [n_edges * k] */
+    const int64_t *core;               /* [n_edges] */
+    /* Alg. 1 steps 1-2: minimum spanning forest of L*_G under the strict
+     * order (w, u, v), sorted by that order. */
+    const int32_t *mst_u, *mst_v;      /* [n_mst] */
+    const int64_t *mst_w;
+    /* Alg. 1 step 3: dendrogram. Row s merges clusters link_a[s] < link_b[s]
+     * (a leaf id < n_edges, or n_edges + s' for the cluster row s' formed)
+     * at weight mst_w[s]; link_size[s] leaves below it. */
+    const int32_t *link_a, *link_b;    /* [n_mst] */
+    const int64_t *link_size;
+    /* Alg. 1 steps 4-5: condensed tree (min cluster size M) and excess of
+     * mass selection. lambda(w) = floor((2^64-1)/(w+1)); lambda 0 at a
+     * virtual root (id n_edges + n_mst) above the components. Point e
+     * leaves cluster fall_cluster[e] at lambda fall_lambda[e]. Clusters,
+     * sorted by id (the dendrogram node where each is born): parent id
+     * (-1 for the root), birth and death lambda (death 0 if it never
+     * splits), size at birth, stability as a 128-bit integer (hi, lo),
+     * selected = 2 final, 1 selected but inside a selected ancestor, 0 no. */
+    const int32_t *fall_cluster;       /* [n_edges] */
+    const uint64_t *fall_lambda;       /* [n_edges] */
+    const int32_t *cl_id, *cl_parent;  /* [n_condensed] */
+    const uint64_t *cl_birth, *cl_death, *cl_stab_hi, *cl_stab_lo;
+    const int64_t *cl_size;
+    const int32_t *cl_selected;
+    /* Alg. 4 output: edge clusters; -1 = noise; clusters numbered
+     * 0 .. n_clusters-1 by their smallest member id. */
+    const int32_t *labels;             /* [n_edges] */
+    int64_t n_skeleton, n_mst, n_condensed;
+    int32_t n_clusters;
+} dgec_result;
+
+/* Context bound to one CUDA device. Owns only host memory and a small
+ * pinned buffer; never allocates device memory. */
+dgec_status dgec_create(dgec_ctx **out, int device);
+dgec_status dgec_destroy(dgec_ctx *ctx);
+/* Message of the last failed call on ctx ("" if none). */
+const char *dgec_last_error(const dgec_ctx *ctx);
+const char *dgec_status_string(dgec_status s);
+
+/* Bytes of device workspace dgec_run needs for these sizes. The bound is
+ * independent of the edge values. n_edges < 2^30, n_vertices >= 0. */
+dgec_status dgec_workspace_size(int64_t n_edges, int32_t n_vertices,
+                                const dgec_params *params, size_t *bytes);
+
+/*
+ * Alg. 4 end to end on device-resident edges: incidence lists (Alg. 3
+ * first line), skeleton (Alg. 2-3), kNN and core distances, minimum
+ * spanning forest, dendrogram, condensed tree, labels (Alg. 1).
+ * d_src, d_dst: int32[n_edges] vertex ids in [0, n_vertices);
+ * d_t: int64[n_edges] times. The time span (max t - min t) must satisfy
+ * bits(span) + bits(n_edges - 1) <= 64. d_workspace: >= ws_bytes bytes,
+ * 256-byte aligned, from dgec_workspace_size. Fills *out.
+ */
+dgec_status dgec_run(dgec_ctx *ctx, const int32_t *d_src, const int32_t *d_dst,
+                     const int64_t *d_t, int64_t n_edges, int32_t n_vertices,
+                     const dgec_params *params, void *d_workspace,
+                     size_t ws_bytes, void *cuda_stream, dgec_result *out);
+
+/*
+ * Same computation from host memory: copies h_src/h_dst/h_t (pinned memory
+ * makes the copies asynchronous) into the workspace, runs dgec_run, and
+ * copies the labels back to h_labels (int32[n_edges]). The workspace must
+ * hold dgec_workspace_size() + 16 * n_edges + 1024 bytes.
+ */
+dgec_status dgec_run_host(dgec_ctx *ctx, const int32_t *h_src,
+                          const int32_t *h_dst, const int64_t *h_t,
+                          int64_t n_edges, int32_t n_vertices,
+                          const dgec_params *params, void *d_workspace,
+                          size_t ws_bytes, void *cuda_stream,
+                          int32_t *h_labels, int32_t *h_n_clusters);
+
+/* Number of kernel launches the last dgec_run on ctx issued (for reporting). */
+int64_t dgec_last_launch_count(const dgec_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGEC_H */

@@ -1,0 +1,127 @@
+// Shared internals of the dgec CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "../../include/dgec.h"
+
+namespace dgec {
+
+constexpr int kBlock = 256;     // threads per CTA for streaming kernels
+constexpr int kItems = 8;       // items per thread in tiled kernels
+constexpr int kTile = kBlock * kItems;
+// Upper bound on any pointer walk in a kernel (the walks follow forests,
+// so a bound is never reached on valid state; it only guarantees exit).
+constexpr int kMaxWalk = 1 << 26;
+
+struct Ctx {
+    int device = 0;
+    int num_sms = 152;
+    char msg[512] = {0};
+    int64_t launches = 0;
+    int64_t *h_pinned = nullptr;    // small pinned buffer for counter reads
+    cudaStream_t stream = nullptr;
+};
+
+dgec_status set_err(Ctx *c, dgec_status s, const char *fmt, ...);
+
+#define DG_TRY(expr)                                   \
+    do {                                               \
+        dgec_status _s = (expr);                       \
+        if (_s != DGEC_OK) return _s;                  \
+    } while (0)
+
+#define CU_TRY(c, expr)                                                          \
+    do {                                                                         \
+        cudaError_t _e = (expr);                                                 \
+        if (_e != cudaSuccess)                                                   \
+            return ::dgec::set_err((c), DGEC_ERR_CUDA, "%s:%d %s: %s", __FILE__, \
+                                   __LINE__, #expr, cudaGetErrorString(_e));     \
+    } while (0)
+
+// Check the last launch (asynchronous errors surface at the next sync).
+#define LAUNCH_CHECK(c)                                                           \
+    do {                                                                          \
+        (c)->launches++;                                                          \
+        cudaError_t _e = cudaGetLastError();                                      \
+        if (_e != cudaSuccess)                                                    \
+            return ::dgec::set_err((c), DGEC_ERR_CUDA, "%s:%d launch: %s", __FILE__, \
+                                   __LINE__, cudaGetErrorString(_e));             \
+    } while (0)
+
+// Bump allocator over the caller's workspace. With base == nullptr it only
+// measures, so dgec_workspace_size and dgec_run share one layout.
+struct Arena {
+    char *base;
+    size_t cap;
+    size_t off = 0;
+    Arena(void *b, size_t c) : base((char *)b), cap(c) {}
+    template <class T>
+    T *take(size_t n) {
+        off = (off + 255) & ~(size_t)255;
+        T *p = base ? (T *)(base + off) : nullptr;
+        off += n * sizeof(T) + 16;
+        return p;
+    }
+    bool ok() const { return off <= cap; }
+};
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+inline int grid_for(int64_t n, int block = kBlock, int64_t max_blocks = 1 << 20) {
+    int64_t g = cdiv(n, block);
+    if (g < 1) g = 1;
+    if (g > max_blocks) g = max_blocks;
+    return (int)g;
+}
+
+inline int bits_for(uint64_t maxval) {  // bits to hold values 0..maxval
+    int b = 0;
+    while (b < 64 && (maxval >> b) != 0) b++;
+    return b;
+}
+
+// Read n int64 counters from device memory (synchronises the stream).
+dgec_status read_counters(Ctx *c, const int64_t *d, int n, int64_t *host);
+
+// ---------------------------------------------------------------- device
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ unsigned long long atomic_min_u64(unsigned long long *p,
+                                                             unsigned long long v) {
+    return atomicMin(p, v);
+}
+
+// Warp-aggregated increment of counter[key] by 1 per lane; returns this
+// lane's slot (old value + rank among lanes with the same key). All lanes
+// in `active` must call it.
+__device__ __forceinline__ int warp_agg_inc(int *counter, int key, unsigned active) {
+    unsigned peers = __match_any_sync(active, key);
+    int leader = __ffs(peers) - 1;
+    unsigned lt = peers & ((1u << lane_id()) - 1u);
+    int base = 0;
+    if ((int)lane_id() == leader) base = atomicAdd(&counter[key], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    return base + __popc(lt);
+}
+
+// 128-bit unsigned add into (hi, lo) words; exact and order independent.
+__device__ __forceinline__ void atomic_add_u128(unsigned long long *hi,
+                                                unsigned long long *lo,
+                                                unsigned long long add_hi,
+                                                unsigned long long add_lo) {
+    unsigned long long old = atomicAdd(lo, add_lo);
+    unsigned long long carry = (old + add_lo < old) ? 1ull : 0ull;
+    if (add_hi | carry) atomicAdd(hi, add_hi + carry);
+}
+
+// lambda(w) = floor((2^64 - 1) / (w + 1)) for w >= 0; 0 stands for w = inf.
+__device__ __forceinline__ unsigned long long lambda_of(long long w) {
+    return 0xFFFFFFFFFFFFFFFFull / ((unsigned long long)w + 1ull);
+}
+
+}  // namespace dgec

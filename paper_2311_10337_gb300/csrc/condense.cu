@@ -1,0 +1,645 @@
+// Stage D2: condensed tree with minimum cluster size M (Alg. 1 step 4),
+// excess-of-mass selection (Alg. 1 step 5, "volume in dendrogram space")
+// and the edge-cluster labels of Alg. 4.
+//
+// The paper defines these steps by citation to HDBSCAN. Readings kept
+// here, identical to the oracle's:
+//   - merges of equal weight are one multi-way merge (only the top merge of
+//     an equal-weight run is kept), so labels depend only on the weighted
+//     connectivity that Thm. 3 preserves;
+//   - lambda(w) = floor((2^64 - 1) / (w + 1)); a virtual root of weight
+//     infinity (lambda 0) has the components as children;
+//   - top-down: a kept merge X of cluster K with >= 2 children of size >= M
+//     ends K and starts one cluster per such child; with exactly one such
+//     child, that child continues K; every point under a smaller child
+//     leaves K at lambda(X);
+//   - stabilities are exact 128-bit integers; EOM keeps a cluster when its
+//     stability is >= the best total of its children; the root is never
+//     kept; clusters are numbered by their smallest member id.
+//
+// Everything is computed by data-parallel passes: pointer jumping for the
+// equal-weight runs and for "which cluster does this merge belong to",
+// short upward walks (< M steps) for where a point leaves, 128-bit atomics
+// for stabilities, and a rake-and-compress tree contraction over the
+// cluster tree for the EOM maximisation, whose per-node update
+// S = max(stab, sum of children) composes along unary chains as
+// x -> max(a, c + x).
+#include "stages.cuh"
+
+namespace dgec {
+
+typedef unsigned __int128 u128;
+
+__device__ __forceinline__ unsigned long long lam_node(int64_t X, int64_t R, int64_t E,
+                                                       const int64_t *w) {
+    return X == R ? 0ull : lambda_of(w[X - E]);
+}
+
+__device__ __forceinline__ int64_t node_size(int64_t X, int64_t R, int64_t E, const int64_t *size) {
+    return X == R ? E : (X < E ? 1 : size[X - E]);
+}
+
+__global__ void k_c_up(int64_t E, int64_t n, const int32_t *parent, const int64_t *w, int32_t *up,
+                       int *isrep) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        int P = parent[E + s];
+        bool rep = P < 0 || w[P - E] != w[s];
+        isrep[s] = rep;
+        up[s] = rep ? (int32_t)s : (int32_t)(P - E);
+    }
+}
+
+// Walk a pointer array to its fixed point, compressing the start pointer.
+__device__ __forceinline__ int walk_to_fixed(int32_t *ptr, int x) {
+    int r = ptr[x];
+    for (int it = 0; it < kMaxWalk; it++) {  // bounded: pointers form a forest
+        int rr = ptr[r];
+        if (rr == r) break;
+        r = rr;
+        ptr[x] = r;
+    }
+    return r;
+}
+
+__global__ void k_c_top(int64_t n, int32_t *up) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x)
+        walk_to_fixed(up, (int)s);
+}
+
+// collapsed parent of every leaf and kept merge; nbig counts big children
+__global__ void k_c_cpar(int64_t E, int64_t n, int32_t M, const int32_t *parent, const int32_t *up,
+                         const int *isrep, const int64_t *size, int32_t *cpar, int *nbig) {
+    const int64_t R = E + n;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < E + n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        if (x >= E && !isrep[x - E]) continue;
+        int P = parent[x];
+        int64_t cp = P < 0 ? R : E + up[P - E];
+        cpar[x] = (int32_t)cp;
+        if (x >= E && size[x - E] >= M) atomicAdd(&nbig[cp], 1);
+    }
+}
+
+// link: a big kept merge continues its parent's cluster when it is the
+// parent's only big child, else it starts a cluster (link to itself).
+__global__ void k_c_link(int64_t E, int64_t n, int32_t M, const int *isrep, const int64_t *size,
+                         const int32_t *cpar, const int *nbig, int32_t *link) {
+    const int64_t R = E + n;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s <= n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        if (s == n) {
+            link[R] = (int32_t)R;
+            continue;
+        }
+        if (!isrep[s] || size[s] < M) continue;
+        int64_t X = cpar[E + s];
+        link[E + s] = nbig[X] >= 2 ? (int32_t)(E + s) : (int32_t)X;
+    }
+}
+
+__global__ void k_c_cl(int64_t E, int64_t n, int32_t M, const int *isrep, const int64_t *size,
+                       int32_t *link) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        if (!isrep[s] || size[s] < M) continue;
+        walk_to_fixed(link, (int)(E + s));
+    }
+}
+
+// cluster records, indexed by node id
+__global__ void k_c_clusters(int64_t E, int64_t n, int32_t M, const int *isrep, const int64_t *size,
+                             const int64_t *w, const int32_t *cpar, const int *nbig,
+                             const int32_t *link, int *isc, unsigned long long *cbirth,
+                             unsigned long long *cdeath, int32_t *cparent) {
+    const int64_t R = E + n;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s <= n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        int64_t X = E + s;
+        bool big;
+        if (s == n) big = true;  // the virtual root
+        else big = isrep[s] && size[s] >= M;
+        if (!big) continue;
+        int K = link[X];
+        if (nbig[X] >= 2) cdeath[K] = lam_node(X, R, E, w);
+        if (K == (int)X) {
+            isc[X] = 1;
+            if (X == R) {
+                cbirth[X] = 0;
+                cparent[X] = -1;
+            } else {
+                int64_t P = cpar[X];
+                cbirth[X] = lam_node(P, R, E, w);
+                cparent[X] = link[P];
+            }
+        }
+    }
+}
+
+// where each point leaves: the lowest kept ancestor of size >= M
+__global__ void k_c_points(int64_t E, int64_t n, int32_t M, const int32_t *cpar, const int64_t *size,
+                           const int64_t *w, const int32_t *link, const unsigned long long *cbirth,
+                           int32_t *fall_cluster, uint64_t *fall_lambda,
+                           unsigned long long *st_hi, unsigned long long *st_lo) {
+    const int64_t R = E + n;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < E;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        int64_t X = cpar[p];
+        for (int it = 0; it < kMaxWalk && X != R && size[X - E] < M; it++) X = cpar[X];
+        int K = link[X];
+        unsigned long long L = lam_node(X, R, E, w);
+        fall_cluster[p] = K;
+        fall_lambda[p] = L;
+        atomic_add_u128(&st_hi[K], &st_lo[K], 0ull, L - cbirth[K]);
+    }
+}
+
+// a child cluster's points leave the parent at the parent's death
+__global__ void k_c_child_stab(int64_t N, const int *isc, const int32_t *cparent,
+                               const int64_t *size, int64_t E, int64_t R,
+                               const unsigned long long *cbirth, const unsigned long long *cdeath,
+                               unsigned long long *st_hi, unsigned long long *st_lo) {
+    for (int64_t K = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; K < N;
+         K += (int64_t)gridDim.x * blockDim.x) {
+        if (!isc[K] || K == R) continue;
+        int P = cparent[K];
+        unsigned long long span = cdeath[P] - cbirth[P];
+        unsigned long long sz = (unsigned long long)size[K - E];
+        unsigned long long lo = sz * span, hi = __umul64hi(sz, span);
+        atomic_add_u128(&st_hi[P], &st_lo[P], hi, lo);
+    }
+}
+
+// compact cluster list (ascending node id) and per-cluster arrays
+__global__ void k_c_compact(int64_t N, const int *isc, const long long *cpos, int32_t *clist,
+                            int32_t *cidx) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        if (!isc[x]) continue;
+        clist[cpos[x]] = (int32_t)x;
+        cidx[x] = (int32_t)cpos[x];
+    }
+}
+
+struct Eom {
+    int64_t ncl;
+    int rootc;
+    const int32_t *clist, *cidx, *cparent;  // cparent by node id
+    int32_t *par;                            // compact parent, -1 root
+    int *pending, *done, *state;             // state: 1 done this phase
+    u128 *stab, *S, *Fa, *Fc, *Fa2, *Fc2;
+    unsigned long long *acc_hi, *acc_lo;
+    int32_t *ucand, *nxt, *nxt2;
+};
+
+__global__ void k_e_init(Eom e, const unsigned long long *st_hi, const unsigned long long *st_lo) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < e.ncl;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int node = e.clist[c];
+        int pn = e.cparent[node];
+        e.par[c] = pn < 0 ? -1 : e.cidx[pn];
+        e.stab[c] = ((u128)st_hi[node] << 64) | st_lo[node];
+        e.done[c] = 0;
+        e.acc_hi[c] = 0;
+        e.acc_lo[c] = 0;
+        if (pn >= 0) atomicAdd(&e.pending[e.cidx[pn]], 1);
+    }
+}
+
+__device__ __forceinline__ u128 acc_of(const Eom &e, int64_t c) {
+    return ((u128)e.acc_hi[c] << 64) | e.acc_lo[c];
+}
+
+// unary clusters learn their one pending child; F = (stab, acc)
+__global__ void k_e_unary(Eom e) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < e.ncl;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        e.state[c] = 0;
+        if (e.done[c]) continue;
+        int p = e.par[c];
+        if (p >= 0 && e.pending[p] == 1) e.ucand[p] = (int32_t)c;
+    }
+}
+
+__global__ void k_e_fninit(Eom e) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < e.ncl;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        if (!e.done[c] && e.pending[c] == 1) {
+            e.nxt[c] = e.ucand[c];
+            e.Fa[c] = e.stab[c];
+            e.Fc[c] = acc_of(e, c);
+        } else {
+            e.nxt[c] = -1;
+        }
+    }
+}
+
+// one synchronous doubling step: F(c) <- F(c) o F(nxt c) while nxt is unary
+__global__ void k_e_double(Eom e, const int32_t *nin, int32_t *nout, const u128 *ain, const u128 *cin,
+                           u128 *aout, u128 *cout) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < e.ncl;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int x = nin[c];
+        u128 a = ain[c], cc = cin[c];
+        if (x >= 0 && nin[x] >= 0) {
+            // x is unary: compose (apply x's function first)
+            u128 a2 = ain[x], c2 = cin[x];
+            u128 t = cc + a2;
+            a = a > t ? a : t;
+            cc = cc + c2;
+            x = nin[x];
+        }
+        nout[c] = x;
+        aout[c] = a;
+        cout[c] = cc;
+    }
+}
+
+// rake ready clusters (all children done)
+__global__ void k_e_rake(Eom e) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < e.ncl;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        if (e.done[c] || e.pending[c] != 0) continue;
+        u128 acc = acc_of(e, c);
+        e.S[c] = e.stab[c] > acc ? e.stab[c] : acc;
+        e.state[c] = 1;
+    }
+}
+
+// unary clusters whose chain bottom was just raked resolve through F
+__global__ void k_e_resolve(Eom e, const int32_t *nfin, const u128 *afin, const u128 *cfin) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < e.ncl;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        if (e.done[c] || e.pending[c] != 1) continue;
+        int x = nfin[c];
+        if (x < 0 || e.state[x] != 1 || e.pending[x] != 0) continue;
+        u128 t = cfin[c] + e.S[x];
+        e.S[c] = afin[c] > t ? afin[c] : t;
+        e.state[c] = 2;
+    }
+}
+
+// clusters finished this phase report to a parent that is still open
+__global__ void k_e_report(Eom e) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < e.ncl;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        if (!e.state[c]) continue;
+        int p = e.par[c];
+        if (p >= 0 && !e.state[p] && !e.done[p]) {
+            u128 s = e.S[c];
+            atomic_add_u128(&e.acc_hi[p], &e.acc_lo[p], (unsigned long long)(s >> 64),
+                            (unsigned long long)s);
+            atomicSub(&e.pending[p], 1);
+        }
+    }
+}
+
+__global__ void k_e_commit(Eom e, unsigned long long *n_open) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < e.ncl;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        if (e.state[c]) e.done[c] = 1;
+        if (!e.done[c] && !e.state[c]) atomicAdd(n_open, 1ull);
+    }
+}
+
+// selection: stab(K) >= sum of children's S (ties to the parent)
+__global__ void k_e_childsum(Eom e) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < e.ncl;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        e.acc_hi[c] = 0;
+        e.acc_lo[c] = 0;
+    }
+}
+__global__ void k_e_childsum2(Eom e) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < e.ncl;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int p = e.par[c];
+        if (p < 0) continue;
+        u128 s = e.S[c];
+        atomic_add_u128(&e.acc_hi[p], &e.acc_lo[p], (unsigned long long)(s >> 64), (unsigned long long)s);
+    }
+}
+__global__ void k_e_select(Eom e, int32_t *H, int32_t *J) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < e.ncl;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        bool sel = (c != e.rootc) && e.stab[c] >= acc_of(e, c);
+        H[c] = sel ? (int32_t)c : -1;
+        J[c] = e.par[c];
+    }
+}
+
+// highest selected ancestor-or-self, by synchronous doubling
+__global__ void k_e_hdouble(int64_t ncl, const int32_t *Hin, const int32_t *Jin, int32_t *Hout,
+                            int32_t *Jout) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncl;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int j = Jin[c];
+        if (j >= 0) {
+            int h = Hin[j];
+            Hout[c] = h >= 0 ? h : Hin[c];
+            Jout[c] = Jin[j];
+        } else {
+            Hout[c] = Hin[c];
+            Jout[c] = -1;
+        }
+    }
+}
+
+__global__ void k_e_labels(int64_t E, const int32_t *fall_cluster, const int32_t *cidx,
+                           const int32_t *H, int32_t *lab, int *minmem) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < E;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        int L = H[cidx[fall_cluster[p]]];
+        lab[p] = L;
+        if (L >= 0) atomicMin(&minmem[L], (int)p);
+    }
+}
+
+__global__ void k_e_final_keys(int64_t ncl, const int32_t *H, const int *minmem, int *flag) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c <= ncl;
+         c += (int64_t)gridDim.x * blockDim.x)
+        flag[c] = (c < ncl && H[c] == (int32_t)c) ? 1 : 0;
+}
+
+__global__ void k_e_final_emit(int64_t ncl, const int *flag, const long long *pos, const int *minmem,
+                               unsigned long long *k, unsigned long long *v) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncl;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[c]) continue;
+        k[pos[c]] = (unsigned long long)minmem[c];
+        v[pos[c]] = (unsigned long long)c;
+    }
+}
+
+__global__ void k_e_rank(int64_t nf, const unsigned long long *v, int32_t *rank) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nf;
+         x += (int64_t)gridDim.x * blockDim.x)
+        rank[v[x]] = (int32_t)x;
+}
+
+__global__ void k_e_relabel(int64_t E, const int32_t *rank, int32_t *lab) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < E;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        int L = lab[p];
+        lab[p] = L < 0 ? -1 : rank[L];
+    }
+}
+
+__global__ void k_e_out(Eom e, int64_t E, const int64_t *size, int64_t R,
+                        const unsigned long long *cbirth, const unsigned long long *cdeath,
+                        const int32_t *H, int32_t *cl_id, int32_t *cl_parent, uint64_t *cl_birth,
+                        uint64_t *cl_death, int64_t *cl_size, uint64_t *cl_hi, uint64_t *cl_lo,
+                        int32_t *cl_sel) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < e.ncl;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int node = e.clist[c];
+        cl_id[c] = node;
+        cl_parent[c] = e.cparent[node];
+        cl_birth[c] = cbirth[node];
+        cl_death[c] = cdeath[node];
+        cl_size[c] = node == R ? E : size[node - E];
+        cl_hi[c] = (uint64_t)(e.stab[c] >> 64);
+        cl_lo[c] = (uint64_t)e.stab[c];
+        bool sel = (c != e.rootc) && e.stab[c] >= acc_of(e, c);
+        cl_sel[c] = !sel ? 0 : (H[c] == (int32_t)c ? 2 : 1);
+    }
+}
+
+void plan_condensed(Arena &ws, const Problem &p, Condensed &o) {
+    int64_t E = p.E;
+    o.fall_cluster = ws.take<int32_t>(E);
+    o.fall_lambda = ws.take<uint64_t>(E);
+    o.cl_id = ws.take<int32_t>(E + 1);
+    o.cl_parent = ws.take<int32_t>(E + 1);
+    o.cl_birth = ws.take<uint64_t>(E + 1);
+    o.cl_death = ws.take<uint64_t>(E + 1);
+    o.cl_stab_hi = ws.take<uint64_t>(E + 1);
+    o.cl_stab_lo = ws.take<uint64_t>(E + 1);
+    o.cl_size = ws.take<int64_t>(E + 1);
+    o.cl_selected = ws.take<int32_t>(E + 1);
+    o.labels = ws.take<int32_t>(E);
+}
+
+struct CScratch {
+    int32_t *up, *cpar, *link, *cparent, *clist, *cidx, *par, *ucand, *nxt, *nxt2, *H, *J, *H2, *J2,
+        *rank;
+    int *isrep, *nbig, *isc, *pending, *done, *state, *minmem, *flag;
+    unsigned long long *cbirth, *cdeath, *st_hi, *st_lo, *acc_hi, *acc_lo, *cnt, *k1, *k2, *v1, *v2;
+    long long *cpos, *scan_tmp;
+    u128 *stab, *S, *Fa, *Fc, *Fa2, *Fc2;
+    void *radix;
+};
+static CScratch carve_condense(Arena &a, const Problem &p) {
+    CScratch s;
+    int64_t E = p.E, N = 2 * E + 2;  // nodes: leaves, merges, virtual root
+    s.up = a.take<int32_t>(E);
+    s.isrep = a.take<int>(E);
+    s.cpar = a.take<int32_t>(N);
+    s.nbig = a.take<int>(N);
+    s.link = a.take<int32_t>(N);
+    s.isc = a.take<int>(N + 1);
+    s.cbirth = a.take<unsigned long long>(N);
+    s.cdeath = a.take<unsigned long long>(N);
+    s.cparent = a.take<int32_t>(N);
+    s.st_hi = a.take<unsigned long long>(N);
+    s.st_lo = a.take<unsigned long long>(N);
+    s.cpos = a.take<long long>(N + 1);
+    s.scan_tmp = a.take<long long>(scan_scratch_elems(N + 1));
+    s.clist = a.take<int32_t>(E + 1);
+    s.cidx = a.take<int32_t>(N);
+    s.par = a.take<int32_t>(E + 1);
+    s.pending = a.take<int>(E + 1);
+    s.done = a.take<int>(E + 1);
+    s.state = a.take<int>(E + 1);
+    s.ucand = a.take<int32_t>(E + 1);
+    s.nxt = a.take<int32_t>(E + 1);
+    s.nxt2 = a.take<int32_t>(E + 1);
+    s.stab = a.take<u128>(E + 1);
+    s.S = a.take<u128>(E + 1);
+    s.Fa = a.take<u128>(E + 1);
+    s.Fc = a.take<u128>(E + 1);
+    s.Fa2 = a.take<u128>(E + 1);
+    s.Fc2 = a.take<u128>(E + 1);
+    s.acc_hi = a.take<unsigned long long>(E + 1);
+    s.acc_lo = a.take<unsigned long long>(E + 1);
+    s.H = a.take<int32_t>(E + 1);
+    s.J = a.take<int32_t>(E + 1);
+    s.H2 = a.take<int32_t>(E + 1);
+    s.J2 = a.take<int32_t>(E + 1);
+    s.minmem = a.take<int>(E + 1);
+    s.flag = a.take<int>(E + 2);
+    s.rank = a.take<int32_t>(E + 1);
+    s.cnt = a.take<unsigned long long>(4);
+    s.k1 = a.take<unsigned long long>(E + 1);
+    s.k2 = a.take<unsigned long long>(E + 1);
+    s.v1 = a.take<unsigned long long>(E + 1);
+    s.v2 = a.take<unsigned long long>(E + 1);
+    s.radix = a.take<char>(radix_scratch_bytes(E + 1));
+    return s;
+}
+size_t condense_scratch_bytes(const Problem &p) {
+    Arena a(nullptr, 0);
+    carve_condense(a, p);
+    return a.off;
+}
+
+__global__ void k_fill_i32(int *p, int64_t n, int v) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x)
+        p[x] = v;
+}
+
+dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro &d, Condensed &o,
+                           void *scratch) {
+    cudaStream_t st = c->stream;
+    int64_t E = p.E, n = m.n, R = E + n, N = E + n + 1;
+    o.n_cl = 0;
+    o.n_clusters = 0;
+    if (E == 0) return DGEC_OK;
+    Arena a(scratch, SIZE_MAX);
+    CScratch s = carve_condense(a, p);
+    const int gN = grid_for(N, kBlock, 65536), gE = grid_for(E, kBlock, 65536),
+              gn = grid_for(n + 1, kBlock, 65536);
+    CU_TRY(c, cudaMemsetAsync(s.nbig, 0, sizeof(int) * N, st));
+    CU_TRY(c, cudaMemsetAsync(s.isc, 0, sizeof(int) * (N + 1), st));
+    CU_TRY(c, cudaMemsetAsync(s.cdeath, 0, sizeof(unsigned long long) * N, st));
+    CU_TRY(c, cudaMemsetAsync(s.st_hi, 0, sizeof(unsigned long long) * N, st));
+    CU_TRY(c, cudaMemsetAsync(s.st_lo, 0, sizeof(unsigned long long) * N, st));
+    if (n > 0) {
+        k_c_up<<<gn, kBlock, 0, st>>>(E, n, d.parent, m.w, s.up, s.isrep);
+        LAUNCH_CHECK(c);
+        k_c_top<<<gn, kBlock, 0, st>>>(n, s.up);
+        LAUNCH_CHECK(c);
+    }
+    k_c_cpar<<<gN, kBlock, 0, st>>>(E, n, p.M, d.parent, s.up, s.isrep, d.size, s.cpar, s.nbig);
+    LAUNCH_CHECK(c);
+    k_c_link<<<gn, kBlock, 0, st>>>(E, n, p.M, s.isrep, d.size, s.cpar, s.nbig, s.link);
+    LAUNCH_CHECK(c);
+    k_c_cl<<<gn, kBlock, 0, st>>>(E, n, p.M, s.isrep, d.size, s.link);
+    LAUNCH_CHECK(c);
+    k_c_clusters<<<gn, kBlock, 0, st>>>(E, n, p.M, s.isrep, d.size, m.w, s.cpar, s.nbig, s.link, s.isc,
+                                        s.cbirth, s.cdeath, s.cparent);
+    LAUNCH_CHECK(c);
+    k_c_points<<<gE, kBlock, 0, st>>>(E, n, p.M, s.cpar, d.size, m.w, s.link, s.cbirth, o.fall_cluster,
+                                      o.fall_lambda, s.st_hi, s.st_lo);
+    LAUNCH_CHECK(c);
+    k_c_child_stab<<<gN, kBlock, 0, st>>>(N, s.isc, s.cparent, d.size, E, R, s.cbirth, s.cdeath, s.st_hi,
+                                          s.st_lo);
+    LAUNCH_CHECK(c);
+    DG_TRY(exclusive_scan_i32(c, s.isc, s.cpos, N + 1, s.scan_tmp));
+    int64_t ncl;
+    DG_TRY(read_counters(c, (const int64_t *)(s.cpos + N), 1, &ncl));
+    k_c_compact<<<gN, kBlock, 0, st>>>(N, s.isc, s.cpos, s.clist, s.cidx);
+    LAUNCH_CHECK(c);
+    o.n_cl = ncl;
+    // ---- excess of mass over the cluster tree
+    Eom e;
+    e.ncl = ncl;
+    e.rootc = (int)(ncl - 1);  // the root has the largest node id
+    e.clist = s.clist;
+    e.cidx = s.cidx;
+    e.cparent = s.cparent;
+    e.par = s.par;
+    e.pending = s.pending;
+    e.done = s.done;
+    e.state = s.state;
+    e.stab = s.stab;
+    e.S = s.S;
+    e.Fa = s.Fa;
+    e.Fc = s.Fc;
+    e.Fa2 = s.Fa2;
+    e.Fc2 = s.Fc2;
+    e.acc_hi = s.acc_hi;
+    e.acc_lo = s.acc_lo;
+    e.ucand = s.ucand;
+    e.nxt = s.nxt;
+    e.nxt2 = s.nxt2;
+    const int gc = grid_for(ncl + 1, kBlock, 65536);
+    CU_TRY(c, cudaMemsetAsync(s.pending, 0, sizeof(int) * (ncl + 1), st));
+    k_e_init<<<gc, kBlock, 0, st>>>(e, s.st_hi, s.st_lo);
+    LAUNCH_CHECK(c);
+    int dbl = 1;
+    while ((1ll << dbl) < ncl + 1) dbl++;
+    dbl += 1;
+    for (int phase = 0;; phase++) {
+        if (phase > 4096) return set_err(c, DGEC_ERR_TIMEOUT, "EOM contraction exceeded 4096 phases");
+        k_e_unary<<<gc, kBlock, 0, st>>>(e);
+        LAUNCH_CHECK(c);
+        k_e_fninit<<<gc, kBlock, 0, st>>>(e);
+        LAUNCH_CHECK(c);
+        int32_t *ni = s.nxt, *no = s.nxt2;
+        u128 *ai = s.Fa, *ao = s.Fa2, *ci = s.Fc, *co = s.Fc2;
+        for (int it = 0; it < dbl; it++) {
+            k_e_double<<<gc, kBlock, 0, st>>>(e, ni, no, ai, ci, ao, co);
+            LAUNCH_CHECK(c);
+            int32_t *t = ni;
+            ni = no;
+            no = t;
+            u128 *ta = ai;
+            ai = ao;
+            ao = ta;
+            ta = ci;
+            ci = co;
+            co = ta;
+        }
+        k_e_rake<<<gc, kBlock, 0, st>>>(e);
+        LAUNCH_CHECK(c);
+        k_e_resolve<<<gc, kBlock, 0, st>>>(e, ni, ai, ci);
+        LAUNCH_CHECK(c);
+        k_e_report<<<gc, kBlock, 0, st>>>(e);
+        LAUNCH_CHECK(c);
+        CU_TRY(c, cudaMemsetAsync(s.cnt, 0, sizeof(unsigned long long), st));
+        k_e_commit<<<gc, kBlock, 0, st>>>(e, s.cnt);
+        LAUNCH_CHECK(c);
+        int64_t open;
+        DG_TRY(read_counters(c, (const int64_t *)s.cnt, 1, &open));
+        if (open == 0) break;
+    }
+    k_e_childsum<<<gc, kBlock, 0, st>>>(e);
+    LAUNCH_CHECK(c);
+    k_e_childsum2<<<gc, kBlock, 0, st>>>(e);
+    LAUNCH_CHECK(c);
+    k_e_select<<<gc, kBlock, 0, st>>>(e, s.H, s.J);
+    LAUNCH_CHECK(c);
+    int32_t *Hi = s.H, *Ji = s.J, *Ho = s.H2, *Jo = s.J2;
+    for (int it = 0; it < dbl; it++) {
+        k_e_hdouble<<<gc, kBlock, 0, st>>>(ncl, Hi, Ji, Ho, Jo);
+        LAUNCH_CHECK(c);
+        int32_t *t = Hi;
+        Hi = Ho;
+        Ho = t;
+        t = Ji;
+        Ji = Jo;
+        Jo = t;
+    }
+    k_fill_i32<<<gc, kBlock, 0, st>>>(s.minmem, ncl + 1, INT_MAX);
+    LAUNCH_CHECK(c);
+    k_e_labels<<<gE, kBlock, 0, st>>>(E, o.fall_cluster, s.cidx, Hi, o.labels, s.minmem);
+    LAUNCH_CHECK(c);
+    k_e_final_keys<<<gc, kBlock, 0, st>>>(ncl, Hi, s.minmem, s.flag);
+    LAUNCH_CHECK(c);
+    DG_TRY(exclusive_scan_i32(c, s.flag, s.cpos, ncl + 1, s.scan_tmp));
+    int64_t nf;
+    DG_TRY(read_counters(c, (const int64_t *)(s.cpos + ncl), 1, &nf));
+    o.n_clusters = (int32_t)nf;
+    if (nf > 0) {
+        k_e_final_emit<<<gc, kBlock, 0, st>>>(ncl, s.flag, s.cpos, s.minmem, s.k1, s.v1);
+        LAUNCH_CHECK(c);
+        bool in_b;
+        DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, s.v1, s.v2}, nf, 0, p.idbits > 0 ? p.idbits : 1,
+                          s.radix, &in_b));
+        unsigned long long *vv = in_b ? s.v2 : s.v1;
+        k_e_rank<<<grid_for(nf, kBlock, 65536), kBlock, 0, st>>>(nf, vv, s.rank);
+        LAUNCH_CHECK(c);
+        k_e_relabel<<<gE, kBlock, 0, st>>>(E, s.rank, o.labels);
+        LAUNCH_CHECK(c);
+    }
+    k_e_out<<<gc, kBlock, 0, st>>>(e, E, d.size, R, s.cbirth, s.cdeath, Hi, o.cl_id, o.cl_parent,
+                                   o.cl_birth, o.cl_death, o.cl_size, o.cl_stab_hi, o.cl_stab_lo,
+                                   o.cl_selected);
+    LAUNCH_CHECK(c);
+    return DGEC_OK;
+}
+
+}  // namespace dgec

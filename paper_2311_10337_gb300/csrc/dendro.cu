@@ -1,0 +1,310 @@
+// Stage D1: single-linkage dendrogram (Alg. 1 step 3) of the sorted
+// forest, built in parallel rounds instead of one union-find sweep.
+//
+// Merge s is the s-th forest edge in (w, u, v) order; its dendrogram node is
+// n_edges + s. Every round works on the super-vertices (already merged
+// subtrees) and the forest edges not yet placed:
+//   1. each super-vertex takes its smallest incident edge (its "pointer");
+//      pointers form trees whose root is the one mutual pair, and along a
+//      pointer path the edge ranks decrease toward that pair;
+//   2. tau(G) = smallest non-pointer edge touching pointer tree G;
+//   3. the pointer edges of G below tau(G) are accepted. They form a
+//      connected top part of G, and no other edge below them touches it, so
+//      in rank order g_1 < g_2 < ... they merge as a chain: g_1 joins the
+//      mutual pair's two subtrees, g_k joins g_{k-1} with the subtree of the
+//      super-vertex whose pointer g_k is;
+//   4. sizes along a chain are a segmented prefix sum; the accepted part of
+//      G becomes one super-vertex whose dendrogram root is its last merge.
+// Each round accepts at least the mutual edge of every pointer tree, and a
+// pointer tree with no interfering edge is placed whole (a star is one
+// round), so the round count follows the depth of interference, not the
+// dendrogram height.
+#include "stages.cuh"
+
+namespace dgec {
+
+__device__ __forceinline__ int find_label(int32_t *svpar, int x) {
+    int r = x;
+    for (int it = 0; it < kMaxWalk; it++) {  // bounded: labels form a forest
+        int p = svpar[r];
+        if (p == r) break;
+        r = p;
+    }
+    if (svpar[x] != r) svpar[x] = r;
+    return r;
+}
+
+__global__ void k_d_init(int64_t E, int64_t n, int32_t *svpar, int32_t *sroot, int64_t *ssize,
+                         int32_t *minr, int32_t *tau, int32_t *parent, int32_t *act) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < E + n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        parent[x] = -1;
+        if (x < E) {
+            svpar[x] = (int32_t)x;
+            sroot[x] = (int32_t)x;
+            ssize[x] = 1;
+            minr[x] = INT_MAX;
+            tau[x] = INT_MAX;
+        }
+        if (x < n) act[x] = (int32_t)x;
+    }
+}
+
+__global__ void k_d_find(const int32_t *act, int64_t na, const int32_t *mu, const int32_t *mv,
+                         int32_t *svpar, int32_t *ecu, int32_t *ecv, int32_t *minr) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < na;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        int s = act[j];
+        int cu = find_label(svpar, mu[s]), cv = find_label(svpar, mv[s]);
+        ecu[j] = cu;
+        ecv[j] = cv;
+        atomicMin(&minr[cu], s);
+        atomicMin(&minr[cv], s);
+    }
+}
+
+__global__ void k_d_ptr(const int32_t *act, int64_t na, const int32_t *ecu, const int32_t *ecv,
+                        const int32_t *minr, int32_t *gp) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < na;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        int s = act[j], cu = ecu[j], cv = ecv[j];
+        bool pu = minr[cu] == s, pv = minr[cv] == s;
+        if (pu && pv) {
+            int r = cu < cv ? cu : cv;
+            gp[cu] = r;
+            gp[cv] = r;
+        } else {
+            if (pu) gp[cu] = cv;
+            if (pv) gp[cv] = cu;
+        }
+    }
+}
+
+__global__ void k_d_gjump(const int32_t *act, int64_t na, const int32_t *ecu, const int32_t *ecv,
+                          const int32_t *minr, int32_t *gp) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < na;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        int s = act[j];
+#pragma unroll
+        for (int side = 0; side < 2; side++) {
+            int c = side ? ecv[j] : ecu[j];
+            if (minr[c] != s) continue;
+            int r = gp[c];
+            for (int it = 0; it < kMaxWalk; it++) {  // bounded: pointer trees
+                int rr = gp[r];
+                if (rr == r) break;
+                r = rr;
+                gp[c] = r;
+            }
+        }
+    }
+}
+
+__global__ void k_d_tau(const int32_t *act, int64_t na, const int32_t *ecu, const int32_t *ecv,
+                        const int32_t *minr, const int32_t *gp, int32_t *tau) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < na;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        int s = act[j], cu = ecu[j], cv = ecv[j];
+        if (minr[cu] != s && minr[cv] != s) {
+            atomicMin(&tau[gp[cu]], s);
+            atomicMin(&tau[gp[cv]], s);
+        }
+    }
+}
+
+__global__ void k_d_accept(const int32_t *act, int64_t na, const int32_t *ecu, const int32_t *ecv,
+                           const int32_t *minr, const int32_t *gp, const int32_t *tau, int *flag) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j <= na;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        if (j == na) {
+            flag[j] = 0;
+            continue;
+        }
+        int s = act[j], cu = ecu[j], cv = ecv[j];
+        bool ptr = minr[cu] == s || minr[cv] == s;
+        flag[j] = ptr && s < tau[gp[cu]];
+    }
+}
+
+__global__ void k_d_emit(const int32_t *act, int64_t na, const int32_t *ecu, const int32_t *gp,
+                         const int *flag, const long long *pos, unsigned long long *key,
+                         unsigned long long *val) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < na;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[j]) continue;
+        int64_t at = pos[j];
+        key[at] = (unsigned long long)gp[ecu[j]];
+        val[at] = ((unsigned long long)(unsigned)act[j] << 32) | (unsigned long long)j;
+    }
+}
+
+__global__ void k_d_chain(const unsigned long long *key, const unsigned long long *val, int64_t nacc,
+                          int64_t E, const int32_t *ecu, const int32_t *ecv, const int32_t *minr,
+                          const int32_t *sroot, const int64_t *ssize, int32_t *la, int32_t *lb,
+                          int32_t *parent, long long *contrib, int *head) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nacc;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long G = key[x];
+        int s = (int)(val[x] >> 32);
+        int j = (int)(val[x] & 0xffffffffu);
+        int cu = ecu[j], cv = ecv[j];
+        bool h = (x == 0) || key[x - 1] != G;
+        int c1, c2;
+        long long add;
+        if (h) {
+            c1 = sroot[cu];
+            c2 = sroot[cv];
+            add = ssize[cu] + ssize[cv];
+        } else {
+            int Y = (minr[cu] == s) ? cu : cv;
+            c1 = (int)(E + (int64_t)(val[x - 1] >> 32));
+            c2 = sroot[Y];
+            add = ssize[Y];
+        }
+        la[s] = c1 < c2 ? c1 : c2;
+        lb[s] = c1 < c2 ? c2 : c1;
+        parent[c1] = (int32_t)(E + s);
+        parent[c2] = (int32_t)(E + s);
+        contrib[x] = add;
+        head[x] = h;
+    }
+}
+
+__global__ void k_d_sizes(const unsigned long long *key, const unsigned long long *val, int64_t nacc,
+                          int64_t E, const int32_t *ecu, const int32_t *ecv, const long long *csum,
+                          int64_t *lsize, int32_t *svpar, int32_t *sroot, int64_t *ssize) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nacc;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long G = key[x];
+        int s = (int)(val[x] >> 32);
+        int j = (int)(val[x] & 0xffffffffu);
+        lsize[s] = csum[x];
+        svpar[ecu[j]] = (int32_t)G;
+        svpar[ecv[j]] = (int32_t)G;
+        bool tail = (x == nacc - 1) || key[x + 1] != G;
+        if (tail) {
+            sroot[G] = (int32_t)(E + s);
+            ssize[G] = csum[x];
+        }
+    }
+}
+
+__global__ void k_d_keep(const int32_t *act, int64_t na, const int *flag, const long long *pos,
+                         int32_t *act2, const int32_t *ecu, const int32_t *ecv, int32_t *minr,
+                         int32_t *tau) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < na;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[j]) act2[j - pos[j]] = act[j];
+        minr[ecu[j]] = INT_MAX;
+        minr[ecv[j]] = INT_MAX;
+        tau[ecu[j]] = INT_MAX;
+        tau[ecv[j]] = INT_MAX;
+    }
+}
+
+void plan_dendro(Arena &ws, const Problem &p, Dendro &o) {
+    o.a = ws.take<int32_t>(p.E);
+    o.b = ws.take<int32_t>(p.E);
+    o.size = ws.take<int64_t>(p.E);
+    o.parent = ws.take<int32_t>(2 * p.E + 1);
+}
+
+struct DScratch {
+    int32_t *svpar, *sroot, *minr, *tau, *gp, *act, *act2, *ecu, *ecv;
+    int64_t *ssize;
+    int *flag, *head;
+    long long *pos, *contrib, *csum, *scan_tmp;
+    SegVal *seg_tmp;
+    unsigned long long *k1, *k2, *v1, *v2;
+    void *radix;
+};
+static DScratch carve_dendro(Arena &a, const Problem &p) {
+    DScratch s;
+    int64_t E = p.E;
+    s.svpar = a.take<int32_t>(E);
+    s.sroot = a.take<int32_t>(E);
+    s.minr = a.take<int32_t>(E);
+    s.tau = a.take<int32_t>(E);
+    s.gp = a.take<int32_t>(E);
+    s.ssize = a.take<int64_t>(E);
+    s.act = a.take<int32_t>(E);
+    s.act2 = a.take<int32_t>(E);
+    s.ecu = a.take<int32_t>(E);
+    s.ecv = a.take<int32_t>(E);
+    s.flag = a.take<int>(E + 1);
+    s.head = a.take<int>(E + 1);
+    s.pos = a.take<long long>(E + 1);
+    s.contrib = a.take<long long>(E + 1);
+    s.csum = a.take<long long>(E + 1);
+    s.scan_tmp = a.take<long long>(scan_scratch_elems(E + 1));
+    s.seg_tmp = a.take<SegVal>(scan_scratch_elems(E + 1));
+    s.k1 = a.take<unsigned long long>(E);
+    s.k2 = a.take<unsigned long long>(E);
+    s.v1 = a.take<unsigned long long>(E);
+    s.v2 = a.take<unsigned long long>(E);
+    s.radix = a.take<char>(radix_scratch_bytes(E));
+    return s;
+}
+size_t dendro_scratch_bytes(const Problem &p) {
+    Arena a(nullptr, 0);
+    carve_dendro(a, p);
+    return a.off;
+}
+
+dgec_status stage_dendro(Ctx *c, const Problem &p, const Msf &m, Dendro &o, void *scratch) {
+    cudaStream_t st = c->stream;
+    int64_t E = p.E, n = m.n;
+    o.rounds = 0;
+    if (E == 0) return DGEC_OK;
+    Arena a(scratch, SIZE_MAX);
+    DScratch s = carve_dendro(a, p);
+    k_d_init<<<grid_for(E + n, kBlock, 65536), kBlock, 0, st>>>(E, n, s.svpar, s.sroot, s.ssize, s.minr,
+                                                               s.tau, o.parent, s.act);
+    LAUNCH_CHECK(c);
+    int64_t na = n;
+    int32_t *act = s.act, *act2 = s.act2;
+    const int lb = p.idbits > 0 ? p.idbits : 1;
+    for (int64_t round = 0; na > 0; round++) {
+        if (round >= (1 << 16))
+            return set_err(c, DGEC_ERR_TIMEOUT, "dendrogram rounds exceeded %d", 1 << 16);
+        const int g = grid_for(na, kBlock, 65536);
+        k_d_find<<<g, kBlock, 0, st>>>(act, na, m.u, m.v, s.svpar, s.ecu, s.ecv, s.minr);
+        LAUNCH_CHECK(c);
+        k_d_ptr<<<g, kBlock, 0, st>>>(act, na, s.ecu, s.ecv, s.minr, s.gp);
+        LAUNCH_CHECK(c);
+        k_d_gjump<<<g, kBlock, 0, st>>>(act, na, s.ecu, s.ecv, s.minr, s.gp);
+        LAUNCH_CHECK(c);
+        k_d_tau<<<g, kBlock, 0, st>>>(act, na, s.ecu, s.ecv, s.minr, s.gp, s.tau);
+        LAUNCH_CHECK(c);
+        k_d_accept<<<grid_for(na + 1, kBlock, 65536), kBlock, 0, st>>>(act, na, s.ecu, s.ecv, s.minr, s.gp,
+                                                                      s.tau, s.flag);
+        LAUNCH_CHECK(c);
+        DG_TRY(exclusive_scan_i32(c, s.flag, s.pos, na + 1, s.scan_tmp));
+        int64_t nacc;
+        DG_TRY(read_counters(c, (const int64_t *)(s.pos + na), 1, &nacc));
+        if (nacc <= 0) return set_err(c, DGEC_ERR_INTERNAL, "dendrogram round accepted no edge");
+        k_d_emit<<<g, kBlock, 0, st>>>(act, na, s.ecu, s.gp, s.flag, s.pos, s.k1, s.v1);
+        LAUNCH_CHECK(c);
+        bool in_b;
+        DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, s.v1, s.v2}, nacc, 0, lb, s.radix, &in_b));
+        unsigned long long *key = in_b ? s.k2 : s.k1, *val = in_b ? s.v2 : s.v1;
+        const int ga = grid_for(nacc, kBlock, 65536);
+        k_d_chain<<<ga, kBlock, 0, st>>>(key, val, nacc, E, s.ecu, s.ecv, s.minr, s.sroot, s.ssize, o.a,
+                                         o.b, o.parent, s.contrib, s.head);
+        LAUNCH_CHECK(c);
+        DG_TRY(segmented_inclusive_sum(c, s.contrib, s.head, s.csum, nacc, s.seg_tmp));
+        k_d_sizes<<<ga, kBlock, 0, st>>>(key, val, nacc, E, s.ecu, s.ecv, s.csum, o.size, s.svpar,
+                                         s.sroot, s.ssize);
+        LAUNCH_CHECK(c);
+        k_d_keep<<<g, kBlock, 0, st>>>(act, na, s.flag, s.pos, act2, s.ecu, s.ecv, s.minr, s.tau);
+        LAUNCH_CHECK(c);
+        na -= nacc;
+        int32_t *t = act;
+        act = act2;
+        act2 = t;
+        o.rounds = round + 1;
+    }
+    return DGEC_OK;
+}
+
+}  // namespace dgec

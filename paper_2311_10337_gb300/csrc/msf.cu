@@ -1,0 +1,261 @@
+// Stage C: minimum spanning forest of the undirected skeleton (Alg. 1
+// step 1) by Borůvka rounds, then sorted by (w, u, v) (Alg. 1 step 2).
+//
+// The order (w, min id, max id) is strict (a pair appears once in L*), so
+// the forest is unique. Each round: every live edge between two components
+// bids its w into both components with atomicMin, then the edges that match
+// a component's best w bid their packed (u << 32 | v); each component hooks
+// along its winning edge, a mutual pair keeps the smaller label as root,
+// labels are pointer-jumped to their roots, and edges inside one component
+// are dropped while the survivors are compacted for the next round.
+#include "stages.cuh"
+
+namespace dgec {
+
+constexpr unsigned long long kMax64 = 0xFFFFFFFFFFFFFFFFull;
+
+// Drop edges inside one component; compact the rest; bid w.
+__global__ void k_filter_bid(const int32_t *u, const int32_t *v, const int64_t *w, int64_t n,
+                             const int32_t *comp, int32_t *u2, int32_t *v2, int64_t *w2,
+                             unsigned long long *cnt, unsigned long long *bw) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t wb = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; wb < n;
+         wb += stride) {
+        int64_t x = wb + lane_id();
+        bool keep = false;
+        int a = 0, b = 0, ca = 0, cb = 0;
+        int64_t ww = 0;
+        if (x < n) {
+            a = u[x];
+            b = v[x];
+            ww = w[x];
+            ca = comp[a];
+            cb = comp[b];
+            keep = ca != cb;
+        }
+        unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (m == 0) continue;
+        int leader = __ffs(m) - 1;
+        unsigned long long base = 0;
+        if ((int)lane_id() == leader) base = atomicAdd(cnt, (unsigned long long)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (keep) {
+            int64_t at = (int64_t)base + __popc(m & ((1u << lane_id()) - 1u));
+            u2[at] = a;
+            v2[at] = b;
+            w2[at] = ww;
+            atomicMin(&bw[ca], (unsigned long long)ww);
+            atomicMin(&bw[cb], (unsigned long long)ww);
+        }
+    }
+}
+
+__global__ void k_bid_uv(const int32_t *u, const int32_t *v, const int64_t *w, int64_t n,
+                         const int32_t *comp, const unsigned long long *bw,
+                         unsigned long long *buv) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        int a = u[x], b = v[x];
+        unsigned long long ww = (unsigned long long)w[x];
+        int ca = comp[a], cb = comp[b];
+        unsigned long long key = ((unsigned long long)(unsigned)a << 32) | (unsigned)b;
+        if (ww == bw[ca]) atomicMin(&buv[ca], key);
+        if (ww == bw[cb]) atomicMin(&buv[cb], key);
+    }
+}
+
+// Each component root with a winning edge hooks to the other side and, once
+// per forest edge, appends it to the output.
+__global__ void k_hook(int64_t E, const int32_t *comp, const unsigned long long *bw,
+                       const unsigned long long *buv, int32_t *par, int32_t *mu, int32_t *mv,
+                       int64_t *mw, unsigned long long *n_out) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < E;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        if (comp[x] != (int32_t)x) continue;
+        if (bw[x] == kMax64) {
+            par[x] = (int32_t)x;
+            continue;
+        }
+        unsigned long long key = buv[x];
+        int a = (int)(key >> 32), b = (int)(key & 0xffffffffu);
+        int ca = comp[a], cb = comp[b];
+        int partner = ca == (int)x ? cb : ca;
+        bool mutual = buv[partner] == key;
+        par[x] = (mutual && (int)x < partner) ? (int32_t)x : partner;
+        if (!mutual || (int)x < partner) {
+            unsigned long long at = atomicAdd(n_out, 1ull);
+            mu[at] = a;
+            mv[at] = b;
+            mw[at] = (int64_t)bw[x];
+        }
+    }
+}
+
+// Pointer jumping: every root walks to its new root, compressing its own
+// pointer as it goes (pointers only ever move toward a root).
+__global__ void k_jump(int64_t E, const int32_t *comp, int32_t *par) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < E;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        if (comp[x] != (int32_t)x) continue;
+        int r = par[x];
+        for (int it = 0; it < kMaxWalk; it++) {  // bounded: pointers form a forest
+            int rr = par[r];
+            if (rr == r) break;
+            r = rr;
+            par[x] = r;
+        }
+    }
+}
+
+__global__ void k_relabel(int64_t E, int32_t *comp, const int32_t *par, unsigned long long *bw,
+                          unsigned long long *buv) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < E;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        int c = comp[x];
+        comp[x] = par[c];
+    }
+}
+
+__global__ void k_reset_best(int64_t E, unsigned long long *bw, unsigned long long *buv) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < E;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        bw[x] = kMax64;
+        buv[x] = kMax64;
+    }
+}
+
+__global__ void k_iota(int64_t E, int32_t *comp) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < E;
+         x += (int64_t)gridDim.x * blockDim.x)
+        comp[x] = (int32_t)x;
+}
+
+__global__ void k_pack_uv(const int32_t *u, const int32_t *v, const int64_t *w, int64_t n,
+                          int idbits, unsigned long long *k, unsigned long long *val) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        k[x] = ((unsigned long long)u[x] << idbits) | (unsigned long long)v[x];
+        val[x] = (unsigned long long)w[x];
+    }
+}
+
+__global__ void k_unpack_msf(const unsigned long long *wkey, const unsigned long long *uv, int64_t n,
+                             int idbits, int32_t *u, int32_t *v, int64_t *w) {
+    const unsigned long long mask = (1ull << idbits) - 1ull;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        u[x] = (int32_t)(uv[x] >> idbits);
+        v[x] = (int32_t)(uv[x] & mask);
+        w[x] = (int64_t)wkey[x];
+    }
+}
+
+void plan_msf(Arena &ws, const Problem &p, Msf &o) {
+    o.u = ws.take<int32_t>(p.E);
+    o.v = ws.take<int32_t>(p.E);
+    o.w = ws.take<int64_t>(p.E);
+}
+
+struct MsfScratch {
+    int32_t *comp, *par, *ua, *va, *ub, *vb, *tu, *tv;
+    int64_t *wa, *wb, *tw;
+    unsigned long long *bw, *buv, *cnt;
+    unsigned long long *k1, *k2, *v1, *v2;
+    void *radix;
+};
+static MsfScratch carve_msf(Arena &a, const Problem &p) {
+    MsfScratch s;
+    int64_t E = p.E, S = 2 * p.E;
+    s.comp = a.take<int32_t>(E);
+    s.par = a.take<int32_t>(E);
+    s.ua = a.take<int32_t>(S);
+    s.va = a.take<int32_t>(S);
+    s.wa = a.take<int64_t>(S);
+    s.ub = a.take<int32_t>(S);
+    s.vb = a.take<int32_t>(S);
+    s.wb = a.take<int64_t>(S);
+    s.tu = a.take<int32_t>(E);
+    s.tv = a.take<int32_t>(E);
+    s.tw = a.take<int64_t>(E);
+    s.bw = a.take<unsigned long long>(E);
+    s.buv = a.take<unsigned long long>(E);
+    s.cnt = a.take<unsigned long long>(4);
+    s.k1 = a.take<unsigned long long>(E);
+    s.k2 = a.take<unsigned long long>(E);
+    s.v1 = a.take<unsigned long long>(E);
+    s.v2 = a.take<unsigned long long>(E);
+    s.radix = a.take<char>(radix_scratch_bytes(E));
+    return s;
+}
+size_t msf_scratch_bytes(const Problem &p) {
+    Arena a(nullptr, 0);
+    carve_msf(a, p);
+    return a.off;
+}
+
+dgec_status stage_msf(Ctx *c, const Problem &p, const Skel &sk, Msf &o, void *scratch) {
+    cudaStream_t st = c->stream;
+    o.n = 0;
+    int64_t E = p.E;
+    if (E == 0 || sk.n == 0) return DGEC_OK;
+    Arena a(scratch, SIZE_MAX);
+    MsfScratch s = carve_msf(a, p);
+    const int gE = grid_for(E, kBlock, 65536);
+    k_iota<<<gE, kBlock, 0, st>>>(E, s.comp);
+    LAUNCH_CHECK(c);
+    k_reset_best<<<gE, kBlock, 0, st>>>(E, s.bw, s.buv);
+    LAUNCH_CHECK(c);
+    CU_TRY(c, cudaMemsetAsync(s.cnt, 0, 4 * sizeof(unsigned long long), st));
+    const int32_t *cu = sk.u, *cv = sk.v;
+    const int64_t *cw = sk.w;
+    int64_t n = sk.n;
+    int32_t *nu = s.ua, *nv = s.va;
+    int64_t *nw = s.wa;
+    for (int round = 0; round < 64; round++) {
+        CU_TRY(c, cudaMemsetAsync(s.cnt, 0, sizeof(unsigned long long), st));
+        k_filter_bid<<<grid_for(n, kBlock, 65536), kBlock, 0, st>>>(cu, cv, cw, n, s.comp, nu, nv, nw,
+                                                                    s.cnt, s.bw);
+        LAUNCH_CHECK(c);
+        int64_t live;
+        DG_TRY(read_counters(c, (const int64_t *)s.cnt, 1, &live));
+        if (live == 0) break;
+        k_bid_uv<<<grid_for(live, kBlock, 65536), kBlock, 0, st>>>(nu, nv, nw, live, s.comp, s.bw, s.buv);
+        LAUNCH_CHECK(c);
+        k_hook<<<gE, kBlock, 0, st>>>(E, s.comp, s.bw, s.buv, s.par, s.tu, s.tv, s.tw, s.cnt + 1);
+        LAUNCH_CHECK(c);
+        k_jump<<<gE, kBlock, 0, st>>>(E, s.comp, s.par);
+        LAUNCH_CHECK(c);
+        k_relabel<<<gE, kBlock, 0, st>>>(E, s.comp, s.par, s.bw, s.buv);
+        LAUNCH_CHECK(c);
+        k_reset_best<<<gE, kBlock, 0, st>>>(E, s.bw, s.buv);
+        LAUNCH_CHECK(c);
+        cu = nu;
+        cv = nv;
+        cw = nw;
+        n = live;
+        nu = (nu == s.ua) ? s.ub : s.ua;
+        nv = (nv == s.va) ? s.vb : s.va;
+        nw = (nw == s.wa) ? s.wb : s.wa;
+        if (round == 63) return set_err(c, DGEC_ERR_TIMEOUT, "Boruvka did not finish in 64 rounds");
+    }
+    int64_t m;
+    DG_TRY(read_counters(c, (const int64_t *)(s.cnt + 1), 1, &m));
+    o.n = m;
+    if (m == 0) return DGEC_OK;
+    // sort by (u, v) then stably by w
+    int gm = grid_for(m, kBlock, 65536);
+    k_pack_uv<<<gm, kBlock, 0, st>>>(s.tu, s.tv, s.tw, m, p.idbits, s.k1, s.v1);
+    LAUNCH_CHECK(c);
+    bool in_b;
+    DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, s.v1, s.v2}, m, 0, 2 * p.idbits, s.radix, &in_b));
+    unsigned long long *uv = in_b ? s.k2 : s.k1, *ws_ = in_b ? s.v2 : s.v1;
+    unsigned long long *uvo = in_b ? s.k1 : s.k2, *wso = in_b ? s.v1 : s.v2;
+    int wbits = p.tbits > 0 ? p.tbits : 1;
+    DG_TRY(radix_sort(c, RadixBuffers{ws_, wso, uv, uvo}, m, 0, wbits, s.radix, &in_b));
+    unsigned long long *wk = in_b ? wso : ws_, *uvk = in_b ? uvo : uv;
+    k_unpack_msf<<<gm, kBlock, 0, st>>>(wk, uvk, m, p.idbits, o.u, o.v, o.w);
+    LAUNCH_CHECK(c);
+    return DGEC_OK;
+}
+
+}  // namespace dgec

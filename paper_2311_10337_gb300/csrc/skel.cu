@@ -1,0 +1,327 @@
+// Stage B: the line-graph skeleton L*_G (Alg. 2 per vertex, Alg. 3 union)
+// and the k nearest line-graph neighbours in time.
+//
+// Alg. 2 as rank arithmetic. At vertex i, with in-edges p_0..p_{n-1} and
+// out-edges q_0..q_{m-1} each sorted by (t, id), and in-edges ordered before
+// out-edges at equal t, let b_m = #{x : t(p_x) <= t(q_m)}. When the sweep
+// reaches q_m its buffer W holds p_x for x in [max(b_{m-1} - 1, 0), b_m)
+// (b_{-1} = 0), so every emitted line-graph edge is one of:
+//   type 1: each in-edge p_x with a later out-edge links to the first one,
+//           q_{a_x}, a_x = #{m : t(q_m) < t(p_x)};
+//   type 2: each out-edge q_m, m >= 1, links to the retained in-edge
+//           p_{b_{m-1} - 1} when b_{m-1} >= 1.
+// So each edge emits at most one type-1 link (at its destination) and one
+// type-2 link (at its source): one thread per edge, no load imbalance on
+// hubs, and |L*| <= sum_i (|E_i| - 1) (Sec. 3) falls out directly.
+//
+// The union of Alg. 3 is a set: a pair emitted at two vertices is a
+// reciprocal, concurrent pair (i, j, t), (j, i, t) with w = 0; it is kept
+// at the vertex whose in-edge has the smaller id.
+#include "stages.cuh"
+
+namespace dgec {
+
+__device__ __forceinline__ int64_t upper_bound_t(const int64_t *a, int64_t n, int64_t x) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (a[mid] <= x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+__device__ __forceinline__ int64_t lower_bound_t(const int64_t *a, int64_t n, int64_t x) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// brank[e] = #in-edges of src[e] with t <= t_e; arank[e] = #out-edges of
+// dst[e] with t < t_e.
+__global__ void k_ranks(const int32_t *src, const int32_t *dst, const int64_t *t, int64_t E,
+                        const int64_t *out_off, const int64_t *out_t, const int64_t *in_off,
+                        const int64_t *in_t, int32_t *brank, int32_t *arank) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int i = src[e], j = dst[e];
+        int64_t te = t[e];
+        int64_t ib = in_off[i], ob = out_off[j];
+        brank[e] = (int32_t)upper_bound_t(in_t + ib, in_off[i + 1] - ib, te);
+        arank[e] = (int32_t)lower_bound_t(out_t + ob, out_off[j + 1] - ob, te);
+    }
+}
+
+struct SkView {
+    const int32_t *src, *dst;
+    const int64_t *out_off, *in_off;
+    const int32_t *out_id, *in_id, *slot_out;
+    const int32_t *brank, *arank;
+};
+
+// Does Alg. 2 at vertex x emit the pair (in-edge pin, out-edge qout)?
+__device__ __forceinline__ bool emitted_at(const SkView &g, int x, int pin, int qout) {
+    int64_t ob = g.out_off[x], nout = g.out_off[x + 1] - ob;
+    int a = g.arank[pin];
+    if (a < nout && g.out_id[ob + a] == qout) return true;  // type 1
+    int64_t sq = g.slot_out[qout];
+    if (sq > ob) {                                          // type 2
+        int b = g.brank[g.out_id[sq - 1]];
+        if (b >= 1 && g.in_id[g.in_off[x] + b - 1] == pin) return true;
+    }
+    return false;
+}
+
+// part[e] / part[E + e]: partner of edge e through its type-1 / type-2
+// link (-1 if none), wgt the P3 weight.
+__global__ void k_links(SkView g, const int64_t *t, const int64_t *out_t, const int64_t *in_t,
+                        int64_t E, int32_t *part, int64_t *wgt, int *flag) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int i = g.src[e], j = g.dst[e];
+        int64_t te = t[e];
+        // type 1: e is p_x at j, linked to q_{a_x}
+        int32_t p1 = -1;
+        int64_t w1 = 0;
+        {
+            int64_t ob = g.out_off[j], nout = g.out_off[j + 1] - ob;
+            int a = g.arank[e];
+            if (a < nout) {
+                int q = g.out_id[ob + a];
+                int64_t w = out_t[ob + a] - te;
+                bool drop = (w == 0) && g.dst[q] == i && (int)e > q && emitted_at(g, i, q, (int)e);
+                if (!drop) {
+                    p1 = q;
+                    w1 = w;
+                }
+            }
+        }
+        // type 2: e is q_m (m >= 1) at i, linked to p_{b_{m-1} - 1}
+        int32_t p2 = -1;
+        int64_t w2 = 0;
+        {
+            int64_t sl = g.slot_out[e];
+            if (sl > g.out_off[i]) {
+                int b = g.brank[g.out_id[sl - 1]];
+                if (b >= 1) {
+                    int64_t pp = g.in_off[i] + b - 1;
+                    int p = g.in_id[pp];
+                    int64_t w = te - in_t[pp];
+                    bool drop = (w == 0) && g.src[p] == j && p > (int)e && emitted_at(g, j, (int)e, p);
+                    if (!drop) {
+                        p2 = p;
+                        w2 = w;
+                    }
+                }
+            }
+        }
+        part[e] = p1;
+        wgt[e] = w1;
+        part[E + e] = p2;
+        wgt[E + e] = w2;
+        flag[e] = p1 >= 0;
+        flag[E + e] = p2 >= 0;
+    }
+}
+
+__global__ void k_compact_links(const int32_t *part, const int64_t *wgt, const int *flag,
+                                const long long *pos, int64_t E, int32_t *u, int32_t *v,
+                                int64_t *w) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < 2 * E;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[x]) continue;
+        int self = (int)(x < E ? x : x - E), o = part[x];
+        int64_t at = pos[x];
+        u[at] = self < o ? self : o;
+        v[at] = self < o ? o : self;
+        w[at] = wgt[x];
+    }
+}
+
+// ---------------------------------------------------------------- kNN
+// Neighbours of e = (i, j, t_e) in the undirected L_G: in-edges r of i with
+// t_r <= t_e (prefix of i's in-list of length brank[e]) and out-edges s of
+// j with t_s >= t_e (suffix of j's out-list from arank[e]). Ranked by
+// (|dt|, id). The K best of each side suffice: the successor side is
+// already in (w, id) order from arank; on the predecessor side the last K
+// of the prefix, except that when the boundary tie group crosses the
+// window its smallest ids are taken instead of its largest. The 2K
+// candidates are sorted in registers (bitonic network); the one node that
+// can appear on both sides (the reciprocal concurrent edge, w = 0) is
+// counted once.
+
+struct Cand {
+    long long w;
+    int id;
+};
+__device__ __forceinline__ bool cand_less(const Cand &a, const Cand &b) {
+    return a.w < b.w || (a.w == b.w && a.id < b.id);
+}
+
+template <int K>
+__global__ void __launch_bounds__(128) k_knn(const int32_t *src, const int32_t *dst, const int64_t *t,
+                                             int64_t E, const int64_t *out_off, const int64_t *out_t,
+                                             const int32_t *out_id, const int64_t *in_off,
+                                             const int64_t *in_t, const int32_t *in_id,
+                                             const int32_t *brank, const int32_t *arank, int k,
+                                             int32_t *knn, int64_t *core) {
+    constexpr int N = 2 * K;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int i = src[e], j = dst[e];
+        long long te = t[e];
+        int64_t ib = in_off[i];
+        int64_t b = brank[e];
+        int64_t ob = out_off[j], nout = out_off[j + 1] - ob;
+        int64_t a = arank[e];
+        Cand c[N];
+        // predecessor window
+        int64_t lo = b - K > 0 ? b - K : 0;
+        int64_t g0 = lo, g1 = lo, take_grp = 0;
+        bool cross = lo > 0 && in_t[ib + lo] == in_t[ib + lo - 1];
+        if (cross) {
+            long long T = in_t[ib + lo];
+            g0 = lower_bound_t(in_t + ib, lo, T);
+            g1 = lo + upper_bound_t(in_t + ib + lo, b - lo, T);
+            take_grp = g1 - lo;  // = K - (b - g1)
+        }
+#pragma unroll
+        for (int x = 0; x < K; x++) {
+            int64_t idx;
+            if (cross) idx = x < take_grp ? g0 + x : g1 + (x - take_grp);
+            else idx = lo + x;
+            if (idx < b) {
+                c[x].w = te - in_t[ib + idx];
+                c[x].id = in_id[ib + idx];
+            } else {
+                c[x].w = LLONG_MAX;
+                c[x].id = INT_MAX;
+            }
+        }
+#pragma unroll
+        for (int x = 0; x < K; x++) {
+            int64_t idx = a + x;
+            if (idx < nout) {
+                c[K + x].w = out_t[ob + idx] - te;
+                c[K + x].id = out_id[ob + idx];
+            } else {
+                c[K + x].w = LLONG_MAX;
+                c[K + x].id = INT_MAX;
+            }
+        }
+        // bitonic sort of N candidates, ascending by (w, id)
+#pragma unroll
+        for (int size = 2; size <= N; size <<= 1) {
+#pragma unroll
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+#pragma unroll
+                for (int lo2 = 0; lo2 < N; lo2++) {
+                    int hi2 = lo2 ^ stride;
+                    if (hi2 > lo2) {
+                        bool up = (lo2 & size) == 0;
+                        bool sw = up ? cand_less(c[hi2], c[lo2]) : cand_less(c[lo2], c[hi2]);
+                        if (sw) {
+                            Cand tmp = c[lo2];
+                            c[lo2] = c[hi2];
+                            c[hi2] = tmp;
+                        }
+                    }
+                }
+            }
+        }
+        int cnt = 0;
+        long long last_w = LLONG_MAX;
+        int prev = -1;
+#pragma unroll
+        for (int x = 0; x < N; x++) {
+            if (c[x].id != INT_MAX && c[x].id != prev && cnt < k) {
+                knn[e * k + cnt] = c[x].id;
+                last_w = c[x].w;
+                cnt++;
+            }
+            prev = c[x].id;
+        }
+        for (int x = cnt; x < k; x++) knn[e * k + x] = -1;
+        core[e] = cnt == k ? last_w : LLONG_MAX;
+    }
+}
+
+void plan_skel(Arena &ws, const Problem &p, Skel &o) {
+    o.brank = ws.take<int32_t>(p.E);
+    o.arank = ws.take<int32_t>(p.E);
+    o.u = ws.take<int32_t>(2 * p.E);
+    o.v = ws.take<int32_t>(2 * p.E);
+    o.w = ws.take<int64_t>(2 * p.E);
+    o.knn = ws.take<int32_t>(p.E * (int64_t)p.k);
+    o.core = ws.take<int64_t>(p.E);
+}
+
+struct SkScratch {
+    int32_t *part;
+    int64_t *wgt;
+    int *flag;
+    long long *pos, *scan_tmp;
+};
+static SkScratch carve_skel(Arena &a, const Problem &p) {
+    SkScratch s;
+    s.part = a.take<int32_t>(2 * p.E);
+    s.wgt = a.take<int64_t>(2 * p.E);
+    s.flag = a.take<int>(2 * p.E + 1);
+    s.pos = a.take<long long>(2 * p.E + 1);
+    s.scan_tmp = a.take<long long>(scan_scratch_elems(2 * p.E + 1));
+    return s;
+}
+size_t skel_scratch_bytes(const Problem &p) {
+    Arena a(nullptr, 0);
+    carve_skel(a, p);
+    return a.off;
+}
+
+__global__ void k_zero_i32(int *p) { *p = 0; }
+
+dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void *scratch) {
+    cudaStream_t st = c->stream;
+    o.n = 0;
+    if (p.E == 0) return DGEC_OK;
+    Arena a(scratch, SIZE_MAX);
+    SkScratch s = carve_skel(a, p);
+    int64_t E = p.E;
+    k_ranks<<<grid_for(E, kBlock, 65536), kBlock, 0, st>>>(p.src, p.dst, p.t, E, g.out_off, g.out_t,
+                                                          g.in_off, g.in_t, o.brank, o.arank);
+    LAUNCH_CHECK(c);
+    SkView v{p.src, p.dst, g.out_off, g.in_off, g.out_id, g.in_id, g.slot_out, o.brank, o.arank};
+    k_links<<<grid_for(E, kBlock, 65536), kBlock, 0, st>>>(v, p.t, g.out_t, g.in_t, E, s.part, s.wgt,
+                                                          s.flag);
+    LAUNCH_CHECK(c);
+    k_zero_i32<<<1, 1, 0, st>>>(s.flag + 2 * E);
+    LAUNCH_CHECK(c);
+    DG_TRY(exclusive_scan_i32(c, s.flag, s.pos, 2 * E + 1, s.scan_tmp));
+    k_compact_links<<<grid_for(2 * E, kBlock, 65536), kBlock, 0, st>>>(s.part, s.wgt, s.flag, s.pos, E,
+                                                                      o.u, o.v, o.w);
+    LAUNCH_CHECK(c);
+    int64_t n;
+    DG_TRY(read_counters(c, (const int64_t *)(s.pos + 2 * E), 1, &n));
+    o.n = n;
+    return DGEC_OK;
+}
+
+dgec_status stage_knn(Ctx *c, const Problem &p, const Csr &g, Skel &o) {
+    if (p.E == 0) return DGEC_OK;
+    cudaStream_t st = c->stream;
+    int64_t E = p.E;
+    int grid = grid_for(E, 128, 1 << 20);
+#define KNN_ARGS                                                                              \
+    p.src, p.dst, p.t, E, g.out_off, g.out_t, g.out_id, g.in_off, g.in_t, g.in_id, o.brank, \
+        o.arank, p.k, o.knn, o.core
+    if (p.k <= 4) k_knn<4><<<grid, 128, 0, st>>>(KNN_ARGS);
+    else if (p.k <= 8) k_knn<8><<<grid, 128, 0, st>>>(KNN_ARGS);
+    else k_knn<16><<<grid, 128, 0, st>>>(KNN_ARGS);
+#undef KNN_ARGS
+    LAUNCH_CHECK(c);
+    return DGEC_OK;
+}
+
+}  // namespace dgec

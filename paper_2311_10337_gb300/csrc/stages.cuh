@@ -1,0 +1,86 @@
+// Stage interfaces of the dgec pipeline (one translation unit per stage).
+#pragma once
+
+#include "prims.cuh"
+
+namespace dgec {
+
+// Problem description shared by the stages.
+struct Problem {
+    const int32_t *src, *dst;
+    const int64_t *t;
+    int64_t E;
+    int32_t V;
+    int32_t k, M;
+    int64_t tmin = 0;
+    int idbits = 1, tbits = 0;
+};
+
+// Stage A: incidence lists (Alg. 3 first line), per-vertex lists sorted by
+// (t, id), plus each edge's slot in its source's out-list and in its
+// destination's in-list.
+struct Csr {
+    int64_t *out_off, *in_off;  // [V+1]
+    int64_t *out_t, *in_t;      // [E]
+    int32_t *out_id, *in_id;    // [E]
+    int32_t *slot_out, *slot_in;  // [E] global slot of edge e in out_id / in_id
+};
+void plan_csr(Arena &ws, const Problem &p, Csr &o);
+size_t csr_scratch_bytes(const Problem &p);
+dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch);
+
+// Stage B: skeleton (Alg. 2 as rank arithmetic + Alg. 3 union) and the
+// k-nearest-in-time neighbours.
+struct Skel {
+    int32_t *brank, *arank;  // [E] ranks from the per-vertex merges
+    int32_t *u, *v;          // [2E] capacity
+    int64_t *w;
+    int64_t n = 0;
+    int32_t *knn;  // [E*k]
+    int64_t *core;  // [E]
+};
+void plan_skel(Arena &ws, const Problem &p, Skel &o);
+size_t skel_scratch_bytes(const Problem &p);
+dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void *scratch);
+dgec_status stage_knn(Ctx *c, const Problem &p, const Csr &g, Skel &o);
+
+// Stage C: minimum spanning forest of the skeleton (Borůvka), sorted by
+// (w, u, v).
+struct Msf {
+    int32_t *u, *v;  // [E]
+    int64_t *w;
+    int64_t n = 0;
+};
+void plan_msf(Arena &ws, const Problem &p, Msf &o);
+size_t msf_scratch_bytes(const Problem &p);
+dgec_status stage_msf(Ctx *c, const Problem &p, const Skel &s, Msf &o, void *scratch);
+
+// Stage D1: single-linkage dendrogram of the sorted forest.
+struct Dendro {
+    int32_t *a, *b;     // [E]
+    int64_t *size;      // [E]
+    int32_t *parent;    // [2E] parent node of every node (leaf or merge), -1 = none
+    int64_t rounds = 0;
+};
+void plan_dendro(Arena &ws, const Problem &p, Dendro &o);
+size_t dendro_scratch_bytes(const Problem &p);
+dgec_status stage_dendro(Ctx *c, const Problem &p, const Msf &m, Dendro &o, void *scratch);
+
+// Stage D2: condensed tree, excess-of-mass selection and labels.
+struct Condensed {
+    int32_t *fall_cluster;  // [E]
+    uint64_t *fall_lambda;  // [E]
+    int32_t *cl_id, *cl_parent;  // [E+1]
+    uint64_t *cl_birth, *cl_death, *cl_stab_hi, *cl_stab_lo;
+    int64_t *cl_size;
+    int32_t *cl_selected;
+    int32_t *labels;  // [E]
+    int64_t n_cl = 0;
+    int32_t n_clusters = 0;
+};
+void plan_condensed(Arena &ws, const Problem &p, Condensed &o);
+size_t condense_scratch_bytes(const Problem &p);
+dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro &d, Condensed &o,
+                           void *scratch);
+
+}  // namespace dgec

@@ -1,0 +1,223 @@
+"""Thin ctypes binding of libdgec.so (include/dgec.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library. PyTorch supplies device memory (the workspace) and the stream.
+There is no CPU path: if the library is missing or no GPU is present the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libdgec.so")
+
+DGEC_OK = 0
+STATUS = {0: "DGEC_OK", 1: "DGEC_ERR_INVALID_ARG", 2: "DGEC_ERR_VERTEX_RANGE",
+          3: "DGEC_ERR_SELF_LOOP", 4: "DGEC_ERR_TOO_LARGE", 5: "DGEC_ERR_OOM",
+          6: "DGEC_ERR_CUDA", 7: "DGEC_ERR_TIMEOUT", 9: "DGEC_ERR_INTERNAL"}
+
+EXPORTS = ["dgec_create", "dgec_destroy", "dgec_last_error", "dgec_status_string",
+           "dgec_workspace_size", "dgec_run", "dgec_run_host", "dgec_last_launch_count"]
+
+
+class DgecError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("min_cluster_size", ctypes.c_int32),
+                ("flags", ctypes.c_uint32)]
+
+
+_P = ctypes.c_void_p
+
+
+class Result(ctypes.Structure):
+    _fields_ = [(n, _P) for n in (
+        "out_off", "in_off", "out_t", "in_t", "out_id", "in_id", "sk_u", "sk_v", "sk_w",
+        "knn_id", "core", "mst_u", "mst_v", "mst_w", "link_a", "link_b", "link_size",
+        "fall_cluster", "fall_lambda", "cl_id", "cl_parent", "cl_birth", "cl_death",
+        "cl_stab_hi", "cl_stab_lo", "cl_size", "cl_selected", "labels")] + [
+        ("n_skeleton", ctypes.c_int64), ("n_mst", ctypes.c_int64),
+        ("n_condensed", ctypes.c_int64), ("n_clusters", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libdgec.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"dgec CUDA library not built ({path}); run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    L.dgec_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int]
+    L.dgec_destroy.argtypes = [_P]
+    L.dgec_last_error.argtypes = [_P]
+    L.dgec_last_error.restype = ctypes.c_char_p
+    L.dgec_status_string.argtypes = [ctypes.c_int]
+    L.dgec_status_string.restype = ctypes.c_char_p
+    L.dgec_workspace_size.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(Params),
+                                      ctypes.POINTER(ctypes.c_size_t)]
+    L.dgec_run.argtypes = [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32,
+                           ctypes.POINTER(Params), _P, ctypes.c_size_t, _P,
+                           ctypes.POINTER(Result)]
+    L.dgec_run_host.argtypes = [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32,
+                                ctypes.POINTER(Params), _P, ctypes.c_size_t, _P, _P,
+                                ctypes.POINTER(ctypes.c_int32)]
+    L.dgec_last_launch_count.argtypes = [_P]
+    L.dgec_last_launch_count.restype = ctypes.c_int64
+    _lib = L
+    return L
+
+
+def workspace_size(n_edges: int, n_vertices: int, k: int, min_cluster_size: int) -> int:
+    L = load()
+    p = Params(k, min_cluster_size, 0)
+    out = ctypes.c_size_t(0)
+    rc = L.dgec_workspace_size(n_edges, n_vertices, ctypes.byref(p), ctypes.byref(out))
+    if rc != DGEC_OK:
+        raise DgecError(rc, L.dgec_status_string(rc).decode())
+    return int(out.value)
+
+
+class Context:
+    """A dgec context on one CUDA device plus a reusable torch workspace."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("dgec needs a CUDA device; there is no CPU path")
+        self.torch = torch
+        self.L = load()
+        self.device = device
+        h = _P()
+        rc = self.L.dgec_create(ctypes.byref(h), device)
+        if rc != DGEC_OK:
+            raise DgecError(rc, "dgec_create failed")
+        self.h = h
+        self.ws = None
+
+    def close(self):
+        if self.h:
+            self.L.dgec_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != DGEC_OK:
+            raise DgecError(rc, self.L.dgec_last_error(self.h).decode())
+
+    def workspace(self, nbytes: int):
+        torch = self.torch
+        if self.ws is None or self.ws.numel() < nbytes:
+            self.ws = None
+            self.ws = torch.empty(nbytes, dtype=torch.uint8, device=f"cuda:{self.device}")
+        return self.ws
+
+    def launches(self) -> int:
+        return int(self.L.dgec_last_launch_count(self.h))
+
+    def run(self, src, dst, t, n_vertices: int, k: int, min_cluster_size: int, stream=None):
+        """Alg. 4 on device tensors (int32 src/dst, int64 t). Returns an
+        Output whose tensors view the workspace (valid until the next run)."""
+        torch = self.torch
+        E = int(src.shape[0])
+        for x, dt in ((src, torch.int32), (dst, torch.int32), (t, torch.int64)):
+            if x.dtype != dt or not x.is_cuda or not x.is_contiguous():
+                raise ValueError("src/dst must be contiguous cuda int32, t cuda int64")
+        p = Params(k, min_cluster_size, 0)
+        need = workspace_size(E, n_vertices, k, min_cluster_size)
+        ws = self.workspace(need)
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        res = Result()
+        rc = self.L.dgec_run(self.h, src.data_ptr(), dst.data_ptr(), t.data_ptr(), E, n_vertices,
+                             ctypes.byref(p), ws.data_ptr(), ws.numel(), st.cuda_stream,
+                             ctypes.byref(res))
+        self._check(rc)
+        return Output(res, ws, E, n_vertices, k)
+
+    def run_host(self, src: np.ndarray, dst: np.ndarray, t: np.ndarray, n_vertices: int, k: int,
+                 min_cluster_size: int, labels_out: np.ndarray | None = None, stream=None):
+        """Alg. 4 from host arrays (pinned numpy views avoid staging copies);
+        returns (labels, n_clusters)."""
+        torch = self.torch
+        E = int(src.shape[0])
+        p = Params(k, min_cluster_size, 0)
+        need = workspace_size(E, n_vertices, k, min_cluster_size) + 16 * E + 4096
+        ws = self.workspace(need)
+        if labels_out is None:
+            labels_out = np.empty(E, np.int32)
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        ncl = ctypes.c_int32(0)
+        rc = self.L.dgec_run_host(self.h, src.ctypes.data, dst.ctypes.data, t.ctypes.data, E,
+                                  n_vertices, ctypes.byref(p), ws.data_ptr(), ws.numel(),
+                                  st.cuda_stream, labels_out.ctypes.data, ctypes.byref(ncl))
+        self._check(rc)
+        return labels_out, int(ncl.value)
+
+
+class Output:
+    """Device-resident results of one run, as torch views of the workspace."""
+
+    _SPEC = {  # name -> (dtype, length expression)
+        "out_off": ("int64", "V+1"), "in_off": ("int64", "V+1"),
+        "out_t": ("int64", "E"), "in_t": ("int64", "E"),
+        "out_id": ("int32", "E"), "in_id": ("int32", "E"),
+        "sk_u": ("int32", "nsk"), "sk_v": ("int32", "nsk"), "sk_w": ("int64", "nsk"),
+        "knn_id": ("int32", "E*k"), "core": ("int64", "E"),
+        "mst_u": ("int32", "nmst"), "mst_v": ("int32", "nmst"), "mst_w": ("int64", "nmst"),
+        "link_a": ("int32", "nmst"), "link_b": ("int32", "nmst"), "link_size": ("int64", "nmst"),
+        "fall_cluster": ("int32", "E"), "fall_lambda": ("uint64", "E"),
+        "cl_id": ("int32", "ncl"), "cl_parent": ("int32", "ncl"),
+        "cl_birth": ("uint64", "ncl"), "cl_death": ("uint64", "ncl"),
+        "cl_stab_hi": ("uint64", "ncl"), "cl_stab_lo": ("uint64", "ncl"),
+        "cl_size": ("int64", "ncl"), "cl_selected": ("int32", "ncl"),
+        "labels": ("int32", "E"),
+    }
+
+    def __init__(self, res: Result, ws, E, V, k):
+        import torch
+        self.n_skeleton = int(res.n_skeleton)
+        self.n_mst = int(res.n_mst)
+        self.n_condensed = int(res.n_condensed)
+        self.n_clusters = int(res.n_clusters)
+        env = dict(E=E, V=V, k=k, nsk=self.n_skeleton, nmst=self.n_mst, ncl=self.n_condensed)
+        base = ws.data_ptr()
+        dts = {"int32": (torch.int32, 4), "int64": (torch.int64, 8), "uint64": (torch.int64, 8)}
+        self._raw = {}
+        for name, (dt, expr) in self._SPEC.items():
+            ptr = getattr(res, name)
+            n = int(eval(expr, {}, env))
+            tdt, sz = dts[dt]
+            if n == 0 or ptr is None:
+                self._raw[name] = (torch.empty(0, dtype=tdt, device=ws.device), dt)
+                continue
+            off = ptr - base
+            self._raw[name] = (ws[off:off + n * sz].view(tdt), dt)
+        self.E, self.V, self.k = E, V, k
+
+    def tensor(self, name):
+        return self._raw[name][0]
+
+    def numpy(self, name):
+        t, dt = self._raw[name]
+        a = t.cpu().numpy()
+        if dt == "uint64":
+            a = a.view(np.uint64)
+        if name == "knn_id":
+            a = a.reshape(self.E, self.k)
+        return a

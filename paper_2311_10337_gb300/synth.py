@@ -114,15 +114,36 @@ def _zipf_endpoints(st: Stream, n: int, n_vertices: int, s: float,
 
 
 def _dedupe_triples(src, dst, t):
-    """Make every (i, j, t) triple unique by bumping t of repeats by +1 s."""
-    for _ in range(1000):
-        key = np.lexsort((t, dst, src))
-        s, d, tt = src[key], dst[key], t[key]
-        dup = np.nonzero((s[1:] == s[:-1]) & (d[1:] == d[:-1]) & (tt[1:] == tt[:-1]))[0] + 1
-        if dup.size == 0:
-            return t
-        t[key[dup]] += 1
-    raise RuntimeError("could not make triples unique")
+    """Make every (i, j, t) triple unique (Sec. 1.2.1): within each (i, j)
+    pair that has a repeat, times are made strictly increasing by moving a
+    repeat to one second after its predecessor. Pairs with repeats are found
+    by sorting a 64-bit hash of the triple and checking candidates exactly."""
+    pair = (src.astype(np.uint64) << np.uint64(32)) | dst.astype(np.uint64)
+    with np.errstate(over="ignore"):
+        h = _mix(pair) ^ _mix(t.astype(np.uint64) * _GOLD + _M1)
+    order = np.argsort(h, kind="stable")
+    hs = h[order]
+    cand = np.nonzero(hs[1:] == hs[:-1])[0]
+    if cand.size == 0:
+        return t
+    a, b = order[cand], order[cand + 1]
+    same = (src[a] == src[b]) & (dst[a] == dst[b]) & (t[a] == t[b])
+    if not same.any():
+        return t
+    idx = np.nonzero(np.isin(pair, np.unique(pair[b[same]])))[0]
+    o = idx[np.lexsort((idx, t[idx], pair[idx]))]
+    pk, tt = pair[o], t[o]
+    head = np.ones(len(o), bool)
+    head[1:] = pk[1:] != pk[:-1]
+    gid = np.cumsum(head) - 1
+    start = np.nonzero(head)[0]
+    r = np.arange(len(o)) - start[gid]
+    big = np.int64(1) << np.int64(40)
+    v = (tt - tt.min()) - r + gid.astype(np.int64) * big
+    v = np.maximum.accumulate(v)
+    t = t.copy()
+    t[o] = v - gid.astype(np.int64) * big + r + tt.min()
+    return t
 
 
 def _conversations(st: Stream, n_edges: int, n_vertices: int, span: int,
