@@ -1,0 +1,279 @@
+"""Benchmark: temporal edges/s of the whole edge-clustering path (Alg. 4:
+incidence lists, skeleton, kNN + core distances, minimum spanning forest,
+dendrogram, condensed tree, labels) on the synthetic 'mid' workload
+(1M vertices, 50M edges, k = 8, M = 5).
+
+One step = one full pass of the path over the 50M edges, inputs resident in
+HBM. Prints one JSON line (rank 0). Multi-GPU runs are independent replicas
+(one graph per rank, no collective on the data path).
+
+--impl reference times the CPU oracle (the reference arm for this path) on
+a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "temporal edges/s end-to-end (kNN+MST+dendrogram)"
+UNIT = "edges/s"
+# algorithmic bytes per edge of the dominant kernel, see the roofline table
+# in the design notes: k_knn reads src, dst, t, brank, arank (24 B), the
+# candidate windows (k in-list and k out-list entries of t + id, 24 B each
+# for k = 8 -> 2*8*12 = 192 B) and writes k ids + core (4k + 8 = 40 B).
+KNN_BYTES_PER_EDGE = {4: 24 + 2 * 4 * 12 + 4 * 4 + 8, 8: 24 + 2 * 8 * 12 + 4 * 8 + 8,
+                      16: 24 + 2 * 16 * 12 + 4 * 16 + 8}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="dgec", choices=["dgec", "reference"])
+    ap.add_argument("--workload", default="mid", choices=["mid", "tiny", "hub"])
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--dominant", default="k_knn",
+                    help="kernel timed live for the roofline object")
+    ap.add_argument("--cpu-sample-minutes", type=float, default=120.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--breakdown", action="store_true",
+                    help="also time every kernel in one extra (untimed) step")
+    return ap.parse_args()
+
+
+def make_workload(name, scale, rank):
+    from paper_2311_10337_gb300 import synth
+    if name == "mid":
+        return synth.mid(scale=scale, seed_offset=rank)
+    if name == "hub":
+        return synth.hub(scale=scale, seed_offset=rank)
+    return synth.tiny(seed_offset=rank)
+
+
+def time_window_sample(w, minutes):
+    """Bounded sample for the CPU oracle: the edges of the first `minutes`
+    of the workload's time span (a sub-window of the same stream)."""
+    tmax = int(w.t.min()) + int(minutes * 60)
+    sel = np.nonzero(w.t < tmax)[0]
+    return w.src[sel], w.dst[sel], w.t[sel]
+
+
+def cpu_baseline(w, minutes):
+    from oracle import oracle as O
+    O.build()
+    s, d, t = time_window_sample(w, minutes)
+    t0 = time.perf_counter()
+    O.run(s, d, t, w.n_vertices, w.k, w.min_cluster_size)
+    dt = time.perf_counter() - t0
+    return {"value": len(s) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {minutes:g} min of the {w.name} stream: {len(s)} edges "
+                      f"(of {w.n_edges}), single-threaded C oracle, {dt:.2f} s"}
+
+
+class Clocks:
+    """Sample nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle, as it stands, on a bounded sample."""
+    if rank != 0:
+        return
+    w = make_workload(args.workload, args.scale, 0)
+    per_step = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        info = cpu_baseline(w, args.cpu_sample_minutes)
+        if i >= args.warmup:
+            per_step.append(info["value"])
+    v = float(np.median(per_step))
+    n_sample = int(info["sample"].split(": ")[1].split(" ")[0])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * n_sample / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"{w.name}: {w.recipe}, k={w.k}, M={w.min_cluster_size}",
+                       "sample": info["sample"]},
+            "cpu_baseline": dict(info, value=v),
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    import torch.distributed as dist
+    from paper_2311_10337_gb300 import dgec
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    w = make_workload(args.workload, args.scale, rank)
+    E, V, k, M = w.n_edges, w.n_vertices, w.k, w.min_cluster_size
+    ctx = dgec.Context(local)
+    src = torch.from_numpy(w.src).cuda()
+    dst = torch.from_numpy(w.dst).cuda()
+    tt = torch.from_numpy(w.t).cuda()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        out = ctx.run(src, dst, tt, V, k, M)
+    launches = ctx.launches()
+    if args.breakdown:
+        ctx.set_kernel_timing(2)
+        ctx.run(src, dst, tt, V, k, M)
+        bd = ctx.kernel_timing()
+        ctx.set_kernel_timing(0)
+    ctx.set_kernel_timing(1, args.dominant)
+    clocks = Clocks(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        out = ctx.run(src, dst, tt, V, k, M)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    dom = ctx.kernel_timing().get(args.dominant, (0.0, 0))
+    ctx.set_kernel_timing(0)
+    if world > 1:
+        tmax = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        ms = float(tmax.item())
+        dist.barrier()
+    clk = clocks.stop()
+    n_clusters = out.n_clusters
+    # end to end through the host entry point: pinned host inputs in, labels out
+    e2e = None
+    if not args.no_e2e:
+        hs = torch.from_numpy(w.src).pin_memory().numpy()
+        hd = torch.from_numpy(w.dst).pin_memory().numpy()
+        ht = torch.from_numpy(w.t).pin_memory().numpy()
+        lab = torch.empty(E, dtype=torch.int32).pin_memory().numpy()
+        ctx.run_host(hs, hd, ht, V, k, M, labels_out=lab)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.run_host(hs, hd, ht, V, k, M, labels_out=lab)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        if world > 1:
+            tm = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+            e2e_s = float(tm.item())
+        e2e = {"value": world * E / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * E,
+               "d2h_bytes_per_step": 4 * E}
+    if rank == 0:
+        peak, peak_kind = peaks()
+        dom_ms, dom_n = dom
+        kb = KNN_BYTES_PER_EDGE[4 if k <= 4 else 8 if k <= 8 else 16]
+        achieved = (kb * E) / (dom_ms / max(dom_n, 1) / 1000.0) / 1e9 if dom_n else None
+        roof = {"bound": "hbm", "kernel": args.dominant, "achieved": achieved, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "algorithmic_bytes_per_launch": kb * E,
+                "avg_launch_ms": dom_ms / max(dom_n, 1) if dom_n else None}
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            try:
+                cpu = cpu_baseline(w, args.cpu_sample_minutes)
+            except Exception as ex:  # the baseline is a report, never the product path
+                cpu = {"error": str(ex)}
+        line = {"metric": METRIC, "value": world * E / (ms / 1000.0), "unit": UNIT,
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+                "config": {"workload": f"{w.name}: {w.recipe}, k={k}, M={M}",
+                           "edges_per_gpu": E, "parallelism": "replicas only",
+                           "l2": "inputs (16 B/edge = %.0f MB) exceed L2; no flush" % (16 * E / 1e6),
+                           "n_clusters": n_clusters},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches * args.steps, "clocks": clk}
+        if args.breakdown:
+            line["kernel_breakdown_ms"] = {n: [round(v[0], 3), v[1]] for n, v in
+                                           sorted(bd.items(), key=lambda kv: -kv[1][0])}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -64,7 +64,9 @@ typedef struct {
     const int64_t *out_t, *in_t;       /* [n_edges] */
     const int32_t *out_id, *in_id;     /* [n_edges] */
     /* Alg. 3: skeleton L*_G as undirected edges (u < v, w = |t_u - t_v|),
-     * each line-graph edge once, in a deterministic order (see DESIGN). */
+     * each line-graph edge once. Deterministic order: first every edge's
+     * link to the first later out-edge at its head, by edge id, then every
+     * edge's link to the retained in-edge at its tail, by edge id. */
     const int32_t *sk_u, *sk_v;        /* [n_skeleton] */
     const int64_t *sk_w;
     /* k nearest line-graph neighbours in time: knn_id[e*k + x], ranked by
@@ -144,6 +146,16 @@ dgec_status dgec_run_host(dgec_ctx *ctx, const int32_t *h_src,
 
 /* Number of kernel launches the last dgec_run on ctx issued (for reporting). */
 int64_t dgec_last_launch_count(const dgec_ctx *ctx);
+
+/* Measurement aid: time kernels with CUDA events recorded on the run's
+ * stream around each launch. mode 0 = off, 1 = only launches of the kernel
+ * called `name` (e.g. "k_knn"), 2 = every launch. Resets the totals. */
+dgec_status dgec_set_kernel_timing(dgec_ctx *ctx, int mode, const char *name);
+/* Totals since the last reset for the i-th kernel name seen (0-based):
+ * its name (static string), summed milliseconds and launch count.
+ * Returns DGEC_ERR_INVALID_ARG when i is past the last name. */
+dgec_status dgec_kernel_timing(dgec_ctx *ctx, int i, const char **name, double *total_ms,
+                               int64_t *launches);
 
 #ifdef __cplusplus
 }

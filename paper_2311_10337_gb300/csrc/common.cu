@@ -22,4 +22,52 @@ dgec_status read_counters(Ctx *c, const int64_t *d, int n, int64_t *host) {
     return DGEC_OK;
 }
 
+int kt_begin(Ctx *c, const char *name) {
+    KernelTimer *k = c->kt;
+    if (!k || k->mode == 0) return -1;
+    if (k->mode == 1 && strcmp(k->only, name) != 0) return -1;
+    if (k->used >= kMaxTimed) return -1;
+    if (!k->ev) {
+        k->ev = (cudaEvent_t *)calloc(2 * kMaxTimed, sizeof(cudaEvent_t));
+        if (!k->ev) return -1;
+    }
+    int slot = k->used++;
+    int id = -1;
+    for (int i = 0; i < k->n_names; i++)
+        if (k->names[i] == name || strcmp(k->names[i], name) == 0) id = i;
+    if (id < 0 && k->n_names < kMaxNames) {
+        id = k->n_names++;
+        k->names[id] = name;
+        k->ms[id] = 0;
+        k->count[id] = 0;
+    }
+    k->name_of[slot] = id;
+    for (int e = 0; e < 2; e++)
+        if (!k->ev[2 * slot + e]) cudaEventCreate(&k->ev[2 * slot + e]);
+    cudaEventRecord(k->ev[2 * slot], c->stream);
+    return slot;
+}
+
+void kt_end(Ctx *c, int slot) {
+    if (slot < 0) return;
+    cudaEventRecord(c->kt->ev[2 * slot + 1], c->stream);
+}
+
+// Fold recorded event pairs into per-name totals (synchronises on them).
+void kt_collect(Ctx *c) {
+    KernelTimer *k = c->kt;
+    if (!k) return;
+    for (int s = 0; s < k->used; s++) {
+        float ms = 0;
+        cudaEventSynchronize(k->ev[2 * s + 1]);
+        cudaEventElapsedTime(&ms, k->ev[2 * s], k->ev[2 * s + 1]);
+        int id = k->name_of[s];
+        if (id >= 0) {
+            k->ms[id] += ms;
+            k->count[id] += 1;
+        }
+    }
+    k->used = 0;
+}
+
 }  // namespace dgec

@@ -17,6 +17,21 @@ constexpr int kTile = kBlock * kItems;
 // so a bound is never reached on valid state; it only guarantees exit).
 constexpr int kMaxWalk = 1 << 26;
 
+// Per-kernel CUDA-event timing: off, one named kernel, or every launch.
+constexpr int kMaxTimed = 1 << 14;
+constexpr int kMaxNames = 128;
+struct KernelTimer {
+    int mode = 0;              // 0 off, 1 only `only`, 2 all
+    char only[64] = {0};
+    cudaEvent_t *ev = nullptr;  // 2 * kMaxTimed events, created on first use
+    int used = 0;
+    int name_of[kMaxTimed];
+    const char *names[kMaxNames];
+    int n_names = 0;
+    double ms[kMaxNames];
+    long long count[kMaxNames];
+};
+
 struct Ctx {
     int device = 0;
     int num_sms = 152;
@@ -24,7 +39,12 @@ struct Ctx {
     int64_t launches = 0;
     int64_t *h_pinned = nullptr;    // small pinned buffer for counter reads
     cudaStream_t stream = nullptr;
+    KernelTimer *kt = nullptr;
 };
+
+int kt_begin(Ctx *c, const char *name);
+void kt_end(Ctx *c, int slot);
+void kt_collect(Ctx *c);
 
 dgec_status set_err(Ctx *c, dgec_status s, const char *fmt, ...);
 
@@ -50,6 +70,16 @@ dgec_status set_err(Ctx *c, dgec_status s, const char *fmt, ...);
         if (_e != cudaSuccess)                                                    \
             return ::dgec::set_err((c), DGEC_ERR_CUDA, "%s:%d launch: %s", __FILE__, \
                                    __LINE__, cudaGetErrorString(_e));             \
+    } while (0)
+
+// Launch a kernel (the variadic part is the whole launch expression),
+// bracketed by timing events when timing is on, then check it.
+#define TK(c, name, ...)                                  \
+    do {                                                  \
+        int _slot = ::dgec::kt_begin((c), (name));        \
+        __VA_ARGS__;                                      \
+        ::dgec::kt_end((c), _slot);                       \
+        LAUNCH_CHECK(c);                                  \
     } while (0)
 
 // Bump allocator over the caller's workspace. With base == nullptr it only

@@ -507,31 +507,22 @@ dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro 
     CU_TRY(c, cudaMemsetAsync(s.st_hi, 0, sizeof(unsigned long long) * N, st));
     CU_TRY(c, cudaMemsetAsync(s.st_lo, 0, sizeof(unsigned long long) * N, st));
     if (n > 0) {
-        k_c_up<<<gn, kBlock, 0, st>>>(E, n, d.parent, m.w, s.up, s.isrep);
-        LAUNCH_CHECK(c);
-        k_c_top<<<gn, kBlock, 0, st>>>(n, s.up);
-        LAUNCH_CHECK(c);
+        TK(c, "k_c_up", k_c_up<<<gn, kBlock, 0, st>>>(E, n, d.parent, m.w, s.up, s.isrep));
+        TK(c, "k_c_top", k_c_top<<<gn, kBlock, 0, st>>>(n, s.up));
     }
-    k_c_cpar<<<gN, kBlock, 0, st>>>(E, n, p.M, d.parent, s.up, s.isrep, d.size, s.cpar, s.nbig);
-    LAUNCH_CHECK(c);
-    k_c_link<<<gn, kBlock, 0, st>>>(E, n, p.M, s.isrep, d.size, s.cpar, s.nbig, s.link);
-    LAUNCH_CHECK(c);
-    k_c_cl<<<gn, kBlock, 0, st>>>(E, n, p.M, s.isrep, d.size, s.link);
-    LAUNCH_CHECK(c);
-    k_c_clusters<<<gn, kBlock, 0, st>>>(E, n, p.M, s.isrep, d.size, m.w, s.cpar, s.nbig, s.link, s.isc,
-                                        s.cbirth, s.cdeath, s.cparent);
-    LAUNCH_CHECK(c);
-    k_c_points<<<gE, kBlock, 0, st>>>(E, n, p.M, s.cpar, d.size, m.w, s.link, s.cbirth, o.fall_cluster,
-                                      o.fall_lambda, s.st_hi, s.st_lo);
-    LAUNCH_CHECK(c);
-    k_c_child_stab<<<gN, kBlock, 0, st>>>(N, s.isc, s.cparent, d.size, E, R, s.cbirth, s.cdeath, s.st_hi,
-                                          s.st_lo);
-    LAUNCH_CHECK(c);
+    TK(c, "k_c_cpar", k_c_cpar<<<gN, kBlock, 0, st>>>(E, n, p.M, d.parent, s.up, s.isrep, d.size, s.cpar, s.nbig));
+    TK(c, "k_c_link", k_c_link<<<gn, kBlock, 0, st>>>(E, n, p.M, s.isrep, d.size, s.cpar, s.nbig, s.link));
+    TK(c, "k_c_cl", k_c_cl<<<gn, kBlock, 0, st>>>(E, n, p.M, s.isrep, d.size, s.link));
+    TK(c, "k_c_clusters", k_c_clusters<<<gn, kBlock, 0, st>>>(E, n, p.M, s.isrep, d.size, m.w, s.cpar, s.nbig, s.link, s.isc,
+                                        s.cbirth, s.cdeath, s.cparent));
+    TK(c, "k_c_points", k_c_points<<<gE, kBlock, 0, st>>>(E, n, p.M, s.cpar, d.size, m.w, s.link, s.cbirth, o.fall_cluster,
+                                      o.fall_lambda, s.st_hi, s.st_lo));
+    TK(c, "k_c_child_stab", k_c_child_stab<<<gN, kBlock, 0, st>>>(N, s.isc, s.cparent, d.size, E, R, s.cbirth, s.cdeath, s.st_hi,
+                                          s.st_lo));
     DG_TRY(exclusive_scan_i32(c, s.isc, s.cpos, N + 1, s.scan_tmp));
     int64_t ncl;
     DG_TRY(read_counters(c, (const int64_t *)(s.cpos + N), 1, &ncl));
-    k_c_compact<<<gN, kBlock, 0, st>>>(N, s.isc, s.cpos, s.clist, s.cidx);
-    LAUNCH_CHECK(c);
+    TK(c, "k_c_compact", k_c_compact<<<gN, kBlock, 0, st>>>(N, s.isc, s.cpos, s.clist, s.cidx));
     o.n_cl = ncl;
     // ---- excess of mass over the cluster tree
     Eom e;
@@ -557,22 +548,18 @@ dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro 
     e.nxt2 = s.nxt2;
     const int gc = grid_for(ncl + 1, kBlock, 65536);
     CU_TRY(c, cudaMemsetAsync(s.pending, 0, sizeof(int) * (ncl + 1), st));
-    k_e_init<<<gc, kBlock, 0, st>>>(e, s.st_hi, s.st_lo);
-    LAUNCH_CHECK(c);
+    TK(c, "k_e_init", k_e_init<<<gc, kBlock, 0, st>>>(e, s.st_hi, s.st_lo));
     int dbl = 1;
     while ((1ll << dbl) < ncl + 1) dbl++;
     dbl += 1;
     for (int phase = 0;; phase++) {
         if (phase > 4096) return set_err(c, DGEC_ERR_TIMEOUT, "EOM contraction exceeded 4096 phases");
-        k_e_unary<<<gc, kBlock, 0, st>>>(e);
-        LAUNCH_CHECK(c);
-        k_e_fninit<<<gc, kBlock, 0, st>>>(e);
-        LAUNCH_CHECK(c);
+        TK(c, "k_e_unary", k_e_unary<<<gc, kBlock, 0, st>>>(e));
+        TK(c, "k_e_fninit", k_e_fninit<<<gc, kBlock, 0, st>>>(e));
         int32_t *ni = s.nxt, *no = s.nxt2;
         u128 *ai = s.Fa, *ao = s.Fa2, *ci = s.Fc, *co = s.Fc2;
         for (int it = 0; it < dbl; it++) {
-            k_e_double<<<gc, kBlock, 0, st>>>(e, ni, no, ai, ci, ao, co);
-            LAUNCH_CHECK(c);
+            TK(c, "k_e_double", k_e_double<<<gc, kBlock, 0, st>>>(e, ni, no, ai, ci, ao, co));
             int32_t *t = ni;
             ni = no;
             no = t;
@@ -583,29 +570,21 @@ dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro 
             ci = co;
             co = ta;
         }
-        k_e_rake<<<gc, kBlock, 0, st>>>(e);
-        LAUNCH_CHECK(c);
-        k_e_resolve<<<gc, kBlock, 0, st>>>(e, ni, ai, ci);
-        LAUNCH_CHECK(c);
-        k_e_report<<<gc, kBlock, 0, st>>>(e);
-        LAUNCH_CHECK(c);
+        TK(c, "k_e_rake", k_e_rake<<<gc, kBlock, 0, st>>>(e));
+        TK(c, "k_e_resolve", k_e_resolve<<<gc, kBlock, 0, st>>>(e, ni, ai, ci));
+        TK(c, "k_e_report", k_e_report<<<gc, kBlock, 0, st>>>(e));
         CU_TRY(c, cudaMemsetAsync(s.cnt, 0, sizeof(unsigned long long), st));
-        k_e_commit<<<gc, kBlock, 0, st>>>(e, s.cnt);
-        LAUNCH_CHECK(c);
+        TK(c, "k_e_commit", k_e_commit<<<gc, kBlock, 0, st>>>(e, s.cnt));
         int64_t open;
         DG_TRY(read_counters(c, (const int64_t *)s.cnt, 1, &open));
         if (open == 0) break;
     }
-    k_e_childsum<<<gc, kBlock, 0, st>>>(e);
-    LAUNCH_CHECK(c);
-    k_e_childsum2<<<gc, kBlock, 0, st>>>(e);
-    LAUNCH_CHECK(c);
-    k_e_select<<<gc, kBlock, 0, st>>>(e, s.H, s.J);
-    LAUNCH_CHECK(c);
+    TK(c, "k_e_childsum", k_e_childsum<<<gc, kBlock, 0, st>>>(e));
+    TK(c, "k_e_childsum2", k_e_childsum2<<<gc, kBlock, 0, st>>>(e));
+    TK(c, "k_e_select", k_e_select<<<gc, kBlock, 0, st>>>(e, s.H, s.J));
     int32_t *Hi = s.H, *Ji = s.J, *Ho = s.H2, *Jo = s.J2;
     for (int it = 0; it < dbl; it++) {
-        k_e_hdouble<<<gc, kBlock, 0, st>>>(ncl, Hi, Ji, Ho, Jo);
-        LAUNCH_CHECK(c);
+        TK(c, "k_e_hdouble", k_e_hdouble<<<gc, kBlock, 0, st>>>(ncl, Hi, Ji, Ho, Jo));
         int32_t *t = Hi;
         Hi = Ho;
         Ho = t;
@@ -613,32 +592,25 @@ dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro 
         Ji = Jo;
         Jo = t;
     }
-    k_fill_i32<<<gc, kBlock, 0, st>>>(s.minmem, ncl + 1, INT_MAX);
-    LAUNCH_CHECK(c);
-    k_e_labels<<<gE, kBlock, 0, st>>>(E, o.fall_cluster, s.cidx, Hi, o.labels, s.minmem);
-    LAUNCH_CHECK(c);
-    k_e_final_keys<<<gc, kBlock, 0, st>>>(ncl, Hi, s.minmem, s.flag);
-    LAUNCH_CHECK(c);
+    TK(c, "k_fill_i32", k_fill_i32<<<gc, kBlock, 0, st>>>(s.minmem, ncl + 1, INT_MAX));
+    TK(c, "k_e_labels", k_e_labels<<<gE, kBlock, 0, st>>>(E, o.fall_cluster, s.cidx, Hi, o.labels, s.minmem));
+    TK(c, "k_e_final_keys", k_e_final_keys<<<gc, kBlock, 0, st>>>(ncl, Hi, s.minmem, s.flag));
     DG_TRY(exclusive_scan_i32(c, s.flag, s.cpos, ncl + 1, s.scan_tmp));
     int64_t nf;
     DG_TRY(read_counters(c, (const int64_t *)(s.cpos + ncl), 1, &nf));
     o.n_clusters = (int32_t)nf;
     if (nf > 0) {
-        k_e_final_emit<<<gc, kBlock, 0, st>>>(ncl, s.flag, s.cpos, s.minmem, s.k1, s.v1);
-        LAUNCH_CHECK(c);
+        TK(c, "k_e_final_emit", k_e_final_emit<<<gc, kBlock, 0, st>>>(ncl, s.flag, s.cpos, s.minmem, s.k1, s.v1));
         bool in_b;
         DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, s.v1, s.v2}, nf, 0, p.idbits > 0 ? p.idbits : 1,
                           s.radix, &in_b));
         unsigned long long *vv = in_b ? s.v2 : s.v1;
-        k_e_rank<<<grid_for(nf, kBlock, 65536), kBlock, 0, st>>>(nf, vv, s.rank);
-        LAUNCH_CHECK(c);
-        k_e_relabel<<<gE, kBlock, 0, st>>>(E, s.rank, o.labels);
-        LAUNCH_CHECK(c);
+        TK(c, "k_e_rank", k_e_rank<<<grid_for(nf, kBlock, 65536), kBlock, 0, st>>>(nf, vv, s.rank));
+        TK(c, "k_e_relabel", k_e_relabel<<<gE, kBlock, 0, st>>>(E, s.rank, o.labels));
     }
-    k_e_out<<<gc, kBlock, 0, st>>>(e, E, d.size, R, s.cbirth, s.cdeath, Hi, o.cl_id, o.cl_parent,
+    TK(c, "k_e_out", k_e_out<<<gc, kBlock, 0, st>>>(e, E, d.size, R, s.cbirth, s.cdeath, Hi, o.cl_id, o.cl_parent,
                                    o.cl_birth, o.cl_death, o.cl_size, o.cl_stab_hi, o.cl_stab_lo,
-                                   o.cl_selected);
-    LAUNCH_CHECK(c);
+                                   o.cl_selected));
     return DGEC_OK;
 }
 

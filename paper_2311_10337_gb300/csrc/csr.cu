@@ -277,8 +277,7 @@ static dgec_status sort_segments(Ctx *c, const Problem &p, unsigned long long *k
     cudaStream_t st = c->stream;
     int64_t V = p.V;
     CU_TRY(c, cudaMemsetAsync(s.bin_cnt, 0, 8 * sizeof(int), st));
-    k_classify<<<grid_for(V, kBlock, 8192), kBlock, 0, st>>>(off, p.V, s.bin_cnt, s.bin_list, V + 1);
-    LAUNCH_CHECK(c);
+    TK(c, "k_classify", k_classify<<<grid_for(V, kBlock, 8192), kBlock, 0, st>>>(off, p.V, s.bin_cnt, s.bin_list, V + 1));
     int64_t h[4];
     CU_TRY(c, cudaMemcpyAsync(c->h_pinned, s.bin_cnt, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CU_TRY(c, cudaStreamSynchronize(st));
@@ -288,29 +287,24 @@ static dgec_status sort_segments(Ctx *c, const Problem &p, unsigned long long *k
         for (int q = 0; q < 4; q++) h[q] = tmp[q];
     }
     if (h[0]) {
-        k_sort_warp<<<grid_for(h[0] * 32), kBlock, 0, st>>>(keys, off, s.bin_list, (int)h[0]);
-        LAUNCH_CHECK(c);
+        TK(c, "k_sort_warp", k_sort_warp<<<grid_for(h[0] * 32), kBlock, 0, st>>>(keys, off, s.bin_list, (int)h[0]));
     }
     if (h[1]) {
-        k_sort_block<256><<<(unsigned)h[1], 128, 0, st>>>(keys, off, s.bin_list + (V + 1));
-        LAUNCH_CHECK(c);
+        TK(c, "k_sort_block<256>", k_sort_block<256><<<(unsigned)h[1], 128, 0, st>>>(keys, off, s.bin_list + (V + 1)));
     }
     if (h[2]) {
-        k_sort_block<2048><<<(unsigned)h[2], 1024, 0, st>>>(keys, off, s.bin_list + 2 * (V + 1));
-        LAUNCH_CHECK(c);
+        TK(c, "k_sort_block<2048>", k_sort_block<2048><<<(unsigned)h[2], 1024, 0, st>>>(keys, off, s.bin_list + 2 * (V + 1)));
     }
     if (h[3]) {
         const int *hl = s.bin_list + 3 * (V + 1);
         int nh = (int)h[3];
-        k_hub_sizes<<<grid_for(nh + 1), kBlock, 0, st>>>(off, hl, nh, s.hsz);
-        LAUNCH_CHECK(c);
+        TK(c, "k_hub_sizes", k_hub_sizes<<<grid_for(nh + 1), kBlock, 0, st>>>(off, hl, nh, s.hsz));
         DG_TRY(exclusive_scan_i64(c, s.hsz, s.hoff, nh + 1, s.scan_tmp));
         int64_t tot;
         DG_TRY(read_counters(c, (const int64_t *)(s.hoff + nh), 1, &tot));
         long long *hstart = s.hoff;
         dim3 g((unsigned)grid_for(2048 * 64, kBlock, 64), (unsigned)(nh < 65535 ? nh : 65535));
-        k_hub_gather<<<g, kBlock, 0, st>>>(keys, off, hl, nh, hstart, s.hk, s.hv);
-        LAUNCH_CHECK(c);
+        TK(c, "k_hub_gather", k_hub_gather<<<g, kBlock, 0, st>>>(keys, off, hl, nh, hstart, s.hk, s.hv));
         bool in_b;
         RadixBuffers rb{s.hk, s.hk2, s.hv, s.hv2};
         DG_TRY(radix_sort(c, rb, tot, 0, key_bits, s.radix, &in_b));
@@ -322,9 +316,8 @@ static dgec_status sort_segments(Ctx *c, const Problem &p, unsigned long long *k
         if (hb == 0) hb = 1;
         DG_TRY(radix_sort(c, rb2, tot, 0, hb, s.radix, &in_b));
         unsigned long long *hub_of = in_b ? v1o : v1, *key_of = in_b ? k1o : k1;
-        k_hub_scatter<<<grid_for(tot, kBlock, 65536), kBlock, 0, st>>>(hub_of, key_of, tot, off, hl, hstart,
-                                                                       keys);
-        LAUNCH_CHECK(c);
+        TK(c, "k_hub_scatter", k_hub_scatter<<<grid_for(tot, kBlock, 65536), kBlock, 0, st>>>(hub_of, key_of, tot, off, hl, hstart,
+                                                                       keys));
     }
     return DGEC_OK;
 }
@@ -336,12 +329,10 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
     int64_t V = p.V, E = p.E;
     CU_TRY(c, cudaMemsetAsync(s.deg_out, 0, sizeof(int) * (V + 1), st));
     CU_TRY(c, cudaMemsetAsync(s.deg_in, 0, sizeof(int) * (V + 1), st));
-    k_init_flags<<<1, 1, 0, st>>>(s.flags);
-    LAUNCH_CHECK(c);
+    TK(c, "k_init_flags", k_init_flags<<<1, 1, 0, st>>>(s.flags));
     if (E > 0) {
-        k_count<<<grid_for(E, kBlock, (int64_t)c->num_sms * 16), kBlock, 0, st>>>(
-            p.src, p.dst, p.t, E, p.V, s.deg_out, s.deg_in, s.flags);
-        LAUNCH_CHECK(c);
+        TK(c, "k_count", k_count<<<grid_for(E, kBlock, (int64_t)c->num_sms * 16), kBlock, 0, st>>>(
+            p.src, p.dst, p.t, E, p.V, s.deg_out, s.deg_in, s.flags));
     }
     int64_t f[4];
     DG_TRY(read_counters(c, (const int64_t *)s.flags, 4, f));
@@ -360,27 +351,22 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
         DG_TRY(exclusive_scan_i32(c, s.deg_out, (long long *)o.out_off, V, s.scan_tmp));
         DG_TRY(exclusive_scan_i32(c, s.deg_in, (long long *)o.in_off, V, s.scan_tmp));
     }
-    k_set_i64<<<1, 1, 0, st>>>((long long *)o.out_off + V, E);
-    LAUNCH_CHECK(c);
-    k_set_i64<<<1, 1, 0, st>>>((long long *)o.in_off + V, E);
-    LAUNCH_CHECK(c);
+    TK(c, "k_set_i64", k_set_i64<<<1, 1, 0, st>>>((long long *)o.out_off + V, E));
+    TK(c, "k_set_i64", k_set_i64<<<1, 1, 0, st>>>((long long *)o.in_off + V, E));
     if (E == 0) return DGEC_OK;
     // scatter keys (cursors reuse the degree arrays)
     CU_TRY(c, cudaMemsetAsync(s.deg_out, 0, sizeof(int) * (V + 1), st));
     CU_TRY(c, cudaMemsetAsync(s.deg_in, 0, sizeof(int) * (V + 1), st));
-    k_scatter<<<grid_for(E, kBlock, (int64_t)c->num_sms * 16), kBlock, 0, st>>>(
+    TK(c, "k_scatter", k_scatter<<<grid_for(E, kBlock, (int64_t)c->num_sms * 16), kBlock, 0, st>>>(
         p.src, p.dst, p.t, E, p.tmin, p.idbits, o.out_off, o.in_off, s.deg_out, s.deg_in, s.okey,
-        s.ikey);
-    LAUNCH_CHECK(c);
+        s.ikey));
     int key_bits = p.idbits + p.tbits;
     DG_TRY(sort_segments(c, p, s.okey, o.out_off, s, key_bits));
     DG_TRY(sort_segments(c, p, s.ikey, o.in_off, s, key_bits));
-    k_unpack<<<grid_for(E, kBlock, 65536), kBlock, 0, st>>>(s.okey, E, p.tmin, p.idbits, o.out_t, o.out_id,
-                                                           o.slot_out);
-    LAUNCH_CHECK(c);
-    k_unpack<<<grid_for(E, kBlock, 65536), kBlock, 0, st>>>(s.ikey, E, p.tmin, p.idbits, o.in_t, o.in_id,
-                                                           o.slot_in);
-    LAUNCH_CHECK(c);
+    TK(c, "k_unpack", k_unpack<<<grid_for(E, kBlock, 65536), kBlock, 0, st>>>(s.okey, E, p.tmin, p.idbits, o.out_t, o.out_id,
+                                                           o.slot_out));
+    TK(c, "k_unpack", k_unpack<<<grid_for(E, kBlock, 65536), kBlock, 0, st>>>(s.ikey, E, p.tmin, p.idbits, o.in_t, o.in_id,
+                                                           o.slot_in));
     return DGEC_OK;
 }
 

@@ -258,9 +258,8 @@ dgec_status stage_dendro(Ctx *c, const Problem &p, const Msf &m, Dendro &o, void
     if (E == 0) return DGEC_OK;
     Arena a(scratch, SIZE_MAX);
     DScratch s = carve_dendro(a, p);
-    k_d_init<<<grid_for(E + n, kBlock, 65536), kBlock, 0, st>>>(E, n, s.svpar, s.sroot, s.ssize, s.minr,
-                                                               s.tau, o.parent, s.act);
-    LAUNCH_CHECK(c);
+    TK(c, "k_d_init", k_d_init<<<grid_for(E + n, kBlock, 65536), kBlock, 0, st>>>(E, n, s.svpar, s.sroot, s.ssize, s.minr,
+                                                               s.tau, o.parent, s.act));
     int64_t na = n;
     int32_t *act = s.act, *act2 = s.act2;
     const int lb = p.idbits > 0 ? p.idbits : 1;
@@ -268,36 +267,27 @@ dgec_status stage_dendro(Ctx *c, const Problem &p, const Msf &m, Dendro &o, void
         if (round >= (1 << 16))
             return set_err(c, DGEC_ERR_TIMEOUT, "dendrogram rounds exceeded %d", 1 << 16);
         const int g = grid_for(na, kBlock, 65536);
-        k_d_find<<<g, kBlock, 0, st>>>(act, na, m.u, m.v, s.svpar, s.ecu, s.ecv, s.minr);
-        LAUNCH_CHECK(c);
-        k_d_ptr<<<g, kBlock, 0, st>>>(act, na, s.ecu, s.ecv, s.minr, s.gp);
-        LAUNCH_CHECK(c);
-        k_d_gjump<<<g, kBlock, 0, st>>>(act, na, s.ecu, s.ecv, s.minr, s.gp);
-        LAUNCH_CHECK(c);
-        k_d_tau<<<g, kBlock, 0, st>>>(act, na, s.ecu, s.ecv, s.minr, s.gp, s.tau);
-        LAUNCH_CHECK(c);
-        k_d_accept<<<grid_for(na + 1, kBlock, 65536), kBlock, 0, st>>>(act, na, s.ecu, s.ecv, s.minr, s.gp,
-                                                                      s.tau, s.flag);
-        LAUNCH_CHECK(c);
+        TK(c, "k_d_find", k_d_find<<<g, kBlock, 0, st>>>(act, na, m.u, m.v, s.svpar, s.ecu, s.ecv, s.minr));
+        TK(c, "k_d_ptr", k_d_ptr<<<g, kBlock, 0, st>>>(act, na, s.ecu, s.ecv, s.minr, s.gp));
+        TK(c, "k_d_gjump", k_d_gjump<<<g, kBlock, 0, st>>>(act, na, s.ecu, s.ecv, s.minr, s.gp));
+        TK(c, "k_d_tau", k_d_tau<<<g, kBlock, 0, st>>>(act, na, s.ecu, s.ecv, s.minr, s.gp, s.tau));
+        TK(c, "k_d_accept", k_d_accept<<<grid_for(na + 1, kBlock, 65536), kBlock, 0, st>>>(act, na, s.ecu, s.ecv, s.minr, s.gp,
+                                                                      s.tau, s.flag));
         DG_TRY(exclusive_scan_i32(c, s.flag, s.pos, na + 1, s.scan_tmp));
         int64_t nacc;
         DG_TRY(read_counters(c, (const int64_t *)(s.pos + na), 1, &nacc));
         if (nacc <= 0) return set_err(c, DGEC_ERR_INTERNAL, "dendrogram round accepted no edge");
-        k_d_emit<<<g, kBlock, 0, st>>>(act, na, s.ecu, s.gp, s.flag, s.pos, s.k1, s.v1);
-        LAUNCH_CHECK(c);
+        TK(c, "k_d_emit", k_d_emit<<<g, kBlock, 0, st>>>(act, na, s.ecu, s.gp, s.flag, s.pos, s.k1, s.v1));
         bool in_b;
         DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, s.v1, s.v2}, nacc, 0, lb, s.radix, &in_b));
         unsigned long long *key = in_b ? s.k2 : s.k1, *val = in_b ? s.v2 : s.v1;
         const int ga = grid_for(nacc, kBlock, 65536);
-        k_d_chain<<<ga, kBlock, 0, st>>>(key, val, nacc, E, s.ecu, s.ecv, s.minr, s.sroot, s.ssize, o.a,
-                                         o.b, o.parent, s.contrib, s.head);
-        LAUNCH_CHECK(c);
+        TK(c, "k_d_chain", k_d_chain<<<ga, kBlock, 0, st>>>(key, val, nacc, E, s.ecu, s.ecv, s.minr, s.sroot, s.ssize, o.a,
+                                         o.b, o.parent, s.contrib, s.head));
         DG_TRY(segmented_inclusive_sum(c, s.contrib, s.head, s.csum, nacc, s.seg_tmp));
-        k_d_sizes<<<ga, kBlock, 0, st>>>(key, val, nacc, E, s.ecu, s.ecv, s.csum, o.size, s.svpar,
-                                         s.sroot, s.ssize);
-        LAUNCH_CHECK(c);
-        k_d_keep<<<g, kBlock, 0, st>>>(act, na, s.flag, s.pos, act2, s.ecu, s.ecv, s.minr, s.tau);
-        LAUNCH_CHECK(c);
+        TK(c, "k_d_sizes", k_d_sizes<<<ga, kBlock, 0, st>>>(key, val, nacc, E, s.ecu, s.ecv, s.csum, o.size, s.svpar,
+                                         s.sroot, s.ssize));
+        TK(c, "k_d_keep", k_d_keep<<<g, kBlock, 0, st>>>(act, na, s.flag, s.pos, act2, s.ecu, s.ecv, s.minr, s.tau));
         na -= nacc;
         int32_t *t = act;
         act = act2;

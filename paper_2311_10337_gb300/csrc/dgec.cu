@@ -73,6 +73,7 @@ dgec_status run_pipeline(Ctx *c, Problem &p, Layout &L, dgec_result *out) {
     DG_TRY(stage_condense(c, p, L.msf, L.den, L.cond, L.scratch));
     CU_TRY(c, cudaStreamSynchronize(c->stream));
     CU_TRY(c, cudaGetLastError());
+    kt_collect(c);
     out->out_off = L.csr.out_off;
     out->in_off = L.csr.in_off;
     out->out_t = L.csr.out_t;
@@ -122,6 +123,7 @@ dgec_status dgec_create(dgec_ctx **out, int device) {
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_pinned, 4096);
+    c->kt = new (std::nothrow) KernelTimer();
     if (e != cudaSuccess) {
         delete x;
         return DGEC_ERR_CUDA;
@@ -133,6 +135,14 @@ dgec_status dgec_create(dgec_ctx **out, int device) {
 dgec_status dgec_destroy(dgec_ctx *x) {
     if (!x) return DGEC_ERR_INVALID_ARG;
     if (x->c.h_pinned) cudaFreeHost(x->c.h_pinned);
+    if (x->c.kt) {
+        if (x->c.kt->ev) {
+            for (int i = 0; i < 2 * kMaxTimed; i++)
+                if (x->c.kt->ev[i]) cudaEventDestroy(x->c.kt->ev[i]);
+            free(x->c.kt->ev);
+        }
+        delete x->c.kt;
+    }
     delete x;
     return DGEC_OK;
 }
@@ -154,6 +164,29 @@ const char *dgec_status_string(dgec_status s) {
 }
 
 int64_t dgec_last_launch_count(const dgec_ctx *x) { return x ? x->c.launches : -1; }
+
+dgec_status dgec_set_kernel_timing(dgec_ctx *x, int mode, const char *name) {
+    if (!x || !x->c.kt || mode < 0 || mode > 2 || (mode == 1 && !name))
+        return DGEC_ERR_INVALID_ARG;
+    KernelTimer *k = x->c.kt;
+    k->mode = mode;
+    snprintf(k->only, sizeof(k->only), "%s", mode == 1 ? name : "");
+    k->used = 0;
+    k->n_names = 0;
+    return DGEC_OK;
+}
+
+dgec_status dgec_kernel_timing(dgec_ctx *x, int i, const char **name, double *total_ms,
+                               int64_t *launches) {
+    if (!x || !x->c.kt) return DGEC_ERR_INVALID_ARG;
+    kt_collect(&x->c);
+    KernelTimer *k = x->c.kt;
+    if (i < 0 || i >= k->n_names) return DGEC_ERR_INVALID_ARG;
+    if (name) *name = k->names[i];
+    if (total_ms) *total_ms = k->ms[i];
+    if (launches) *launches = k->count[i];
+    return DGEC_OK;
+}
 
 dgec_status dgec_workspace_size(int64_t n_edges, int32_t n_vertices, const dgec_params *params,
                                 size_t *bytes) {

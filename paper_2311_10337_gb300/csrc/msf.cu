@@ -201,10 +201,8 @@ dgec_status stage_msf(Ctx *c, const Problem &p, const Skel &sk, Msf &o, void *sc
     Arena a(scratch, SIZE_MAX);
     MsfScratch s = carve_msf(a, p);
     const int gE = grid_for(E, kBlock, 65536);
-    k_iota<<<gE, kBlock, 0, st>>>(E, s.comp);
-    LAUNCH_CHECK(c);
-    k_reset_best<<<gE, kBlock, 0, st>>>(E, s.bw, s.buv);
-    LAUNCH_CHECK(c);
+    TK(c, "k_iota", k_iota<<<gE, kBlock, 0, st>>>(E, s.comp));
+    TK(c, "k_reset_best", k_reset_best<<<gE, kBlock, 0, st>>>(E, s.bw, s.buv));
     CU_TRY(c, cudaMemsetAsync(s.cnt, 0, 4 * sizeof(unsigned long long), st));
     const int32_t *cu = sk.u, *cv = sk.v;
     const int64_t *cw = sk.w;
@@ -213,22 +211,16 @@ dgec_status stage_msf(Ctx *c, const Problem &p, const Skel &sk, Msf &o, void *sc
     int64_t *nw = s.wa;
     for (int round = 0; round < 64; round++) {
         CU_TRY(c, cudaMemsetAsync(s.cnt, 0, sizeof(unsigned long long), st));
-        k_filter_bid<<<grid_for(n, kBlock, 65536), kBlock, 0, st>>>(cu, cv, cw, n, s.comp, nu, nv, nw,
-                                                                    s.cnt, s.bw);
-        LAUNCH_CHECK(c);
+        TK(c, "k_filter_bid", k_filter_bid<<<grid_for(n, kBlock, 65536), kBlock, 0, st>>>(cu, cv, cw, n, s.comp, nu, nv, nw,
+                                                                    s.cnt, s.bw));
         int64_t live;
         DG_TRY(read_counters(c, (const int64_t *)s.cnt, 1, &live));
         if (live == 0) break;
-        k_bid_uv<<<grid_for(live, kBlock, 65536), kBlock, 0, st>>>(nu, nv, nw, live, s.comp, s.bw, s.buv);
-        LAUNCH_CHECK(c);
-        k_hook<<<gE, kBlock, 0, st>>>(E, s.comp, s.bw, s.buv, s.par, s.tu, s.tv, s.tw, s.cnt + 1);
-        LAUNCH_CHECK(c);
-        k_jump<<<gE, kBlock, 0, st>>>(E, s.comp, s.par);
-        LAUNCH_CHECK(c);
-        k_relabel<<<gE, kBlock, 0, st>>>(E, s.comp, s.par, s.bw, s.buv);
-        LAUNCH_CHECK(c);
-        k_reset_best<<<gE, kBlock, 0, st>>>(E, s.bw, s.buv);
-        LAUNCH_CHECK(c);
+        TK(c, "k_bid_uv", k_bid_uv<<<grid_for(live, kBlock, 65536), kBlock, 0, st>>>(nu, nv, nw, live, s.comp, s.bw, s.buv));
+        TK(c, "k_hook", k_hook<<<gE, kBlock, 0, st>>>(E, s.comp, s.bw, s.buv, s.par, s.tu, s.tv, s.tw, s.cnt + 1));
+        TK(c, "k_jump", k_jump<<<gE, kBlock, 0, st>>>(E, s.comp, s.par));
+        TK(c, "k_relabel", k_relabel<<<gE, kBlock, 0, st>>>(E, s.comp, s.par, s.bw, s.buv));
+        TK(c, "k_reset_best", k_reset_best<<<gE, kBlock, 0, st>>>(E, s.bw, s.buv));
         cu = nu;
         cv = nv;
         cw = nw;
@@ -244,8 +236,7 @@ dgec_status stage_msf(Ctx *c, const Problem &p, const Skel &sk, Msf &o, void *sc
     if (m == 0) return DGEC_OK;
     // sort by (u, v) then stably by w
     int gm = grid_for(m, kBlock, 65536);
-    k_pack_uv<<<gm, kBlock, 0, st>>>(s.tu, s.tv, s.tw, m, p.idbits, s.k1, s.v1);
-    LAUNCH_CHECK(c);
+    TK(c, "k_pack_uv", k_pack_uv<<<gm, kBlock, 0, st>>>(s.tu, s.tv, s.tw, m, p.idbits, s.k1, s.v1));
     bool in_b;
     DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, s.v1, s.v2}, m, 0, 2 * p.idbits, s.radix, &in_b));
     unsigned long long *uv = in_b ? s.k2 : s.k1, *ws_ = in_b ? s.v2 : s.v1;
@@ -253,8 +244,7 @@ dgec_status stage_msf(Ctx *c, const Problem &p, const Skel &sk, Msf &o, void *sc
     int wbits = p.tbits > 0 ? p.tbits : 1;
     DG_TRY(radix_sort(c, RadixBuffers{ws_, wso, uv, uvo}, m, 0, wbits, s.radix, &in_b));
     unsigned long long *wk = in_b ? wso : ws_, *uvk = in_b ? uvo : uv;
-    k_unpack_msf<<<gm, kBlock, 0, st>>>(wk, uvk, m, p.idbits, o.u, o.v, o.w);
-    LAUNCH_CHECK(c);
+    TK(c, "k_unpack_msf", k_unpack_msf<<<gm, kBlock, 0, st>>>(wk, uvk, m, p.idbits, o.u, o.v, o.w));
     return DGEC_OK;
 }
 

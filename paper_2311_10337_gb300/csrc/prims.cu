@@ -160,17 +160,15 @@ dgec_status radix_sort(Ctx *c, RadixBuffers buf, int64_t n, int begin_bit, int e
     for (int shift = begin_bit; shift < end_bit; shift += 8) {
         int nb = end_bit - shift < 8 ? end_bit - shift : 8;
         unsigned mask = (1u << nb) - 1u;
-        k_radix_hist<<<(unsigned)tiles, kBlock, 0, c->stream>>>(kin, n, shift, mask, hist, tiles);
-        LAUNCH_CHECK(c);
+        TK(c, "k_radix_hist", k_radix_hist<<<(unsigned)tiles, kBlock, 0, c->stream>>>(kin, n, shift, mask, hist, tiles));
         DG_TRY(exclusive_scan_i32(c, hist, offs, (int64_t)hist_n, scan_tmp));
         if (vin) {
-            k_radix_scatter<true><<<(unsigned)tiles, kBlock, 0, c->stream>>>(kin, vin, kout, vout, n, shift,
-                                                                           mask, offs, tiles);
+            TK(c, "k_radix_scatter", k_radix_scatter<true><<<(unsigned)tiles, kBlock, 0, c->stream>>>(
+                                         kin, vin, kout, vout, n, shift, mask, offs, tiles));
         } else {
-            k_radix_scatter<false><<<(unsigned)tiles, kBlock, 0, c->stream>>>(kin, nullptr, kout, nullptr, n,
-                                                                            shift, mask, offs, tiles);
+            TK(c, "k_radix_scatter", k_radix_scatter<false><<<(unsigned)tiles, kBlock, 0, c->stream>>>(
+                                         kin, nullptr, kout, nullptr, n, shift, mask, offs, tiles));
         }
-        LAUNCH_CHECK(c);
         unsigned long long *t = kin;
         kin = kout;
         kout = t;

@@ -289,19 +289,15 @@ dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void
     Arena a(scratch, SIZE_MAX);
     SkScratch s = carve_skel(a, p);
     int64_t E = p.E;
-    k_ranks<<<grid_for(E, kBlock, 65536), kBlock, 0, st>>>(p.src, p.dst, p.t, E, g.out_off, g.out_t,
-                                                          g.in_off, g.in_t, o.brank, o.arank);
-    LAUNCH_CHECK(c);
+    TK(c, "k_ranks", k_ranks<<<grid_for(E, kBlock, 65536), kBlock, 0, st>>>(p.src, p.dst, p.t, E, g.out_off, g.out_t,
+                                                          g.in_off, g.in_t, o.brank, o.arank));
     SkView v{p.src, p.dst, g.out_off, g.in_off, g.out_id, g.in_id, g.slot_out, o.brank, o.arank};
-    k_links<<<grid_for(E, kBlock, 65536), kBlock, 0, st>>>(v, p.t, g.out_t, g.in_t, E, s.part, s.wgt,
-                                                          s.flag);
-    LAUNCH_CHECK(c);
-    k_zero_i32<<<1, 1, 0, st>>>(s.flag + 2 * E);
-    LAUNCH_CHECK(c);
+    TK(c, "k_links", k_links<<<grid_for(E, kBlock, 65536), kBlock, 0, st>>>(v, p.t, g.out_t, g.in_t, E, s.part, s.wgt,
+                                                          s.flag));
+    TK(c, "k_zero_i32", k_zero_i32<<<1, 1, 0, st>>>(s.flag + 2 * E));
     DG_TRY(exclusive_scan_i32(c, s.flag, s.pos, 2 * E + 1, s.scan_tmp));
-    k_compact_links<<<grid_for(2 * E, kBlock, 65536), kBlock, 0, st>>>(s.part, s.wgt, s.flag, s.pos, E,
-                                                                      o.u, o.v, o.w);
-    LAUNCH_CHECK(c);
+    TK(c, "k_compact_links", k_compact_links<<<grid_for(2 * E, kBlock, 65536), kBlock, 0, st>>>(s.part, s.wgt, s.flag, s.pos, E,
+                                                                      o.u, o.v, o.w));
     int64_t n;
     DG_TRY(read_counters(c, (const int64_t *)(s.pos + 2 * E), 1, &n));
     o.n = n;
@@ -316,11 +312,10 @@ dgec_status stage_knn(Ctx *c, const Problem &p, const Csr &g, Skel &o) {
 #define KNN_ARGS                                                                              \
     p.src, p.dst, p.t, E, g.out_off, g.out_t, g.out_id, g.in_off, g.in_t, g.in_id, o.brank, \
         o.arank, p.k, o.knn, o.core
-    if (p.k <= 4) k_knn<4><<<grid, 128, 0, st>>>(KNN_ARGS);
-    else if (p.k <= 8) k_knn<8><<<grid, 128, 0, st>>>(KNN_ARGS);
-    else k_knn<16><<<grid, 128, 0, st>>>(KNN_ARGS);
+    if (p.k <= 4) TK(c, "k_knn", k_knn<4><<<grid, 128, 0, st>>>(KNN_ARGS));
+    else if (p.k <= 8) TK(c, "k_knn", k_knn<8><<<grid, 128, 0, st>>>(KNN_ARGS));
+    else TK(c, "k_knn", k_knn<16><<<grid, 128, 0, st>>>(KNN_ARGS));
 #undef KNN_ARGS
-    LAUNCH_CHECK(c);
     return DGEC_OK;
 }
 

@@ -21,7 +21,8 @@ STATUS = {0: "DGEC_OK", 1: "DGEC_ERR_INVALID_ARG", 2: "DGEC_ERR_VERTEX_RANGE",
           6: "DGEC_ERR_CUDA", 7: "DGEC_ERR_TIMEOUT", 9: "DGEC_ERR_INTERNAL"}
 
 EXPORTS = ["dgec_create", "dgec_destroy", "dgec_last_error", "dgec_status_string",
-           "dgec_workspace_size", "dgec_run", "dgec_run_host", "dgec_last_launch_count"]
+           "dgec_workspace_size", "dgec_run", "dgec_run_host", "dgec_last_launch_count",
+           "dgec_set_kernel_timing", "dgec_kernel_timing"]
 
 
 class DgecError(RuntimeError):
@@ -75,6 +76,10 @@ def load(path: str = LIB_PATH):
                                 ctypes.POINTER(ctypes.c_int32)]
     L.dgec_last_launch_count.argtypes = [_P]
     L.dgec_last_launch_count.restype = ctypes.c_int64
+    L.dgec_set_kernel_timing.argtypes = [_P, ctypes.c_int, ctypes.c_char_p]
+    L.dgec_kernel_timing.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
+                                     ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_int64)]
     _lib = L
     return L
 
@@ -130,6 +135,26 @@ class Context:
 
     def launches(self) -> int:
         return int(self.L.dgec_last_launch_count(self.h))
+
+    def set_kernel_timing(self, mode: int, name: str | None = None):
+        """0 off, 1 only kernel `name`, 2 every launch (resets totals)."""
+        self._check(self.L.dgec_set_kernel_timing(self.h, mode, name.encode() if name else None))
+
+    def kernel_timing(self) -> dict:
+        """{kernel name: (total ms, launches)} since the last reset."""
+        out = {}
+        i = 0
+        while True:
+            nm = ctypes.c_char_p()
+            ms = ctypes.c_double()
+            n = ctypes.c_int64()
+            rc = self.L.dgec_kernel_timing(self.h, i, ctypes.byref(nm), ctypes.byref(ms),
+                                           ctypes.byref(n))
+            if rc != DGEC_OK:
+                break
+            out[nm.value.decode()] = (ms.value, n.value)
+            i += 1
+        return out
 
     def run(self, src, dst, t, n_vertices: int, k: int, min_cluster_size: int, stream=None):
         """Alg. 4 on device tensors (int32 src/dst, int64 t). Returns an
