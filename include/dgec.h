@@ -157,6 +157,34 @@ dgec_status dgec_set_kernel_timing(dgec_ctx *ctx, int mode, const char *name);
 dgec_status dgec_kernel_timing(dgec_ctx *ctx, int i, const char **name, double *total_ms,
                                int64_t *launches);
 
+/*
+ * Minimum spanning forest without any device allocation. The paper has no
+ * counterpart to this call: it exists for callers that may not allocate
+ * device memory where they need a forest (a plugin inside a framework that
+ * owns all device memory, a loop that forbids allocation after start-up, a
+ * thread that cannot reach cudaMalloc). Its working memory is one fixed
+ * array of about 22 MB that the library reserves on every device it is
+ * loaded onto, for the life of the process.
+ *
+ * Input: d_u, d_v, d_w: n_edges undirected edges over nodes 0..n_nodes-1,
+ * each written with d_u < d_v (as dgec_result's skeleton is), w >= 0.
+ * Output: the minimum spanning forest under the strict order (w, u, v) --
+ * the same edge set dgec_run returns in mst_u/mst_v/mst_w -- written in no
+ * particular order to d_mst_u/d_mst_v/d_mst_w (capacity n_nodes - 1), its
+ * size to *h_n_mst. Runs on cuda_stream of the current device and
+ * synchronises it before returning.
+ * Limits: n_nodes <= 262,144 and n_edges <= 524,288, else
+ * DGEC_ERR_TOO_LARGE; a bad id or u >= v gives DGEC_ERR_INVALID_ARG.
+ * The first call on a device looks up the array's device address; make it
+ * before any stream capture. Every call reuses the same array (each call
+ * re-initialises what must start from a known value), so calls that
+ * overlap on the GPU race with each other: serialise them.
+ */
+dgec_status dgec_msf_static(const int32_t *d_u, const int32_t *d_v, const int64_t *d_w,
+                            int64_t n_edges, int64_t n_nodes, int32_t *d_mst_u,
+                            int32_t *d_mst_v, int64_t *d_mst_w, int64_t *h_n_mst,
+                            void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,7 +22,7 @@ STATUS = {0: "DGEC_OK", 1: "DGEC_ERR_INVALID_ARG", 2: "DGEC_ERR_VERTEX_RANGE",
 
 EXPORTS = ["dgec_create", "dgec_destroy", "dgec_last_error", "dgec_status_string",
            "dgec_workspace_size", "dgec_run", "dgec_run_host", "dgec_last_launch_count",
-           "dgec_set_kernel_timing", "dgec_kernel_timing"]
+           "dgec_set_kernel_timing", "dgec_kernel_timing", "dgec_msf_static"]
 
 
 class DgecError(RuntimeError):
@@ -80,8 +80,27 @@ def load(path: str = LIB_PATH):
     L.dgec_kernel_timing.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
                                      ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_int64)]
+    L.dgec_msf_static.argtypes = [_P, _P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P, _P,
+                                  ctypes.POINTER(ctypes.c_int64), _P]
     _lib = L
     return L
+
+
+def msf_static(u, v, w, n_nodes: int, out_u, out_v, out_w, stream=None) -> int:
+    """Minimum spanning forest through the allocation-free entry point: the
+    caller's device tensors in (u < v, int32; w int64) and out (capacity
+    n_nodes - 1); the library uses only its fixed internal array. Returns
+    the number of forest edges written."""
+    import torch
+    L = load()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    n = ctypes.c_int64(0)
+    rc = L.dgec_msf_static(u.data_ptr(), v.data_ptr(), w.data_ptr(), int(u.shape[0]), n_nodes,
+                           out_u.data_ptr(), out_v.data_ptr(), out_w.data_ptr(), ctypes.byref(n),
+                           st.cuda_stream)
+    if rc != DGEC_OK:
+        raise DgecError(rc, L.dgec_status_string(rc).decode())
+    return int(n.value)
 
 
 def workspace_size(n_edges: int, n_vertices: int, k: int, min_cluster_size: int) -> int:

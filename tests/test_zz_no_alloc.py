@@ -1,0 +1,56 @@
+"""The allocation-free forest entry point (dgec_msf_static) against the
+regular pipeline's forest, called twice in a row through the C ABI.
+
+The paper has no counterpart to this entry point: it serves callers that
+may not allocate device memory where they need the forest, so it keeps its
+working memory in one fixed array inside the library. This file is
+collected last so that a run stopping at the first failure has already run
+every other test.
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import ctx
+from paper_2311_10337_gb300 import dgec, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _sorted(u, v, w):
+    o = np.lexsort((v, u, w))
+    return u[o], v[o], w[o]
+
+
+def test_static_forest_matches_pipeline_twice():
+    import torch
+    wl = synth.tiny(seed_offset=3)
+    c = ctx()
+    src = torch.from_numpy(wl.src).cuda()
+    dst = torch.from_numpy(wl.dst).cuda()
+    t = torch.from_numpy(wl.t).cuda()
+    out = c.run(src, dst, t, wl.n_vertices, wl.k, wl.min_cluster_size)
+    # copy the skeleton out of the workspace so the pipeline's memory is not touched
+    u = out.tensor("sk_u").clone()
+    v = out.tensor("sk_v").clone()
+    w = out.tensor("sk_w").clone()
+    ref = (out.numpy("mst_u"), out.numpy("mst_v"), out.numpy("mst_w"))
+    E = wl.n_edges
+    for _ in range(2):
+        mu = torch.full((E,), -7, dtype=torch.int32, device="cuda")
+        mv = torch.full((E,), -7, dtype=torch.int32, device="cuda")
+        mw = torch.full((E,), -7, dtype=torch.int64, device="cuda")
+        n = dgec.msf_static(u, v, w, E, mu, mv, mw)
+        torch.cuda.synchronize()
+        got = _sorted(mu[:n].cpu().numpy(), mv[:n].cpu().numpy(), mw[:n].cpu().numpy())
+        assert n == len(ref[0])
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b)
+
+
+def test_static_forest_rejects_oversize():
+    import torch
+    z32 = torch.zeros(4, dtype=torch.int32, device="cuda")
+    z64 = torch.zeros(4, dtype=torch.int64, device="cuda")
+    with pytest.raises(dgec.DgecError) as ei:
+        dgec.msf_static(z32, z32, z64, (1 << 18) + 1, z32, z32, z64)
+    assert ei.value.status == 4
