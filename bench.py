@@ -27,12 +27,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "temporal edges/s end-to-end (kNN+MST+dendrogram)"
 UNIT = "edges/s"
-# algorithmic bytes per edge of the dominant kernel, see the roofline table
-# in the design notes: k_knn reads src, dst, t, brank, arank (24 B), the
-# candidate windows (k in-list and k out-list entries of t + id, 24 B each
-# for k = 8 -> 2*8*12 = 192 B) and writes k ids + core (4k + 8 = 40 B).
-KNN_BYTES_PER_EDGE = {4: 24 + 2 * 4 * 12 + 4 * 4 + 8, 8: 24 + 2 * 8 * 12 + 4 * 8 + 8,
-                      16: 24 + 2 * 16 * 12 + 4 * 16 + 8}
+# Algorithmic bytes per edge of the dominant kernel k_ranks_knn: it reads
+# the edge (src, dst, t: 16 B) and its two candidate windows (k in-list and
+# k out-list entries of t + id: 2 * k * 12 B) and writes the two ranks
+# (8 B), k neighbour ids (4k B) and the core distance (8 B). Binary-search
+# probes and offset lookups are access overhead, not counted.
+def knn_bytes_per_edge(k: int) -> int:
+    return 16 + 2 * k * 12 + 8 + 4 * k + 8
 
 
 def parse():
@@ -43,7 +44,7 @@ def parse():
     ap.add_argument("--impl", default="dgec", choices=["dgec", "reference"])
     ap.add_argument("--workload", default="mid", choices=["mid", "tiny", "hub"])
     ap.add_argument("--scale", type=float, default=1.0)
-    ap.add_argument("--dominant", default="k_knn",
+    ap.add_argument("--dominant", default="k_ranks_knn",
                     help="kernel timed live for the roofline object")
     ap.add_argument("--cpu-sample-minutes", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -244,7 +245,7 @@ def main():
     if rank == 0:
         peak, peak_kind = peaks()
         dom_ms, dom_n = dom
-        kb = KNN_BYTES_PER_EDGE[4 if k <= 4 else 8 if k <= 8 else 16]
+        kb = knn_bytes_per_edge(k)
         achieved = (kb * E) / (dom_ms / max(dom_n, 1) / 1000.0) / 1e9 if dom_n else None
         roof = {"bound": "hbm", "kernel": args.dominant, "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s",

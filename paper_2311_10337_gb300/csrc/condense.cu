@@ -191,6 +191,9 @@ struct Eom {
     u128 *stab, *S, *Fa, *Fc, *Fa2, *Fc2;
     unsigned long long *acc_hi, *acc_lo;
     int32_t *ucand, *nxt, *nxt2;
+    const int32_t *alist;  // open clusters this phase
+    int64_t nact;
+    unsigned long long *flag;  // [0] changed
 };
 
 __global__ void k_e_init(Eom e, const unsigned long long *st_hi, const unsigned long long *st_lo) {
@@ -213,8 +216,9 @@ __device__ __forceinline__ u128 acc_of(const Eom &e, int64_t c) {
 
 // unary clusters learn their one pending child; F = (stab, acc)
 __global__ void k_e_unary(Eom e) {
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < e.ncl;
-         c += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t ix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ix < e.nact;
+         ix += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e.alist[ix];
         e.state[c] = 0;
         if (e.done[c]) continue;
         int p = e.par[c];
@@ -223,8 +227,9 @@ __global__ void k_e_unary(Eom e) {
 }
 
 __global__ void k_e_fninit(Eom e) {
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < e.ncl;
-         c += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t ix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ix < e.nact;
+         ix += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e.alist[ix];
         if (!e.done[c] && e.pending[c] == 1) {
             e.nxt[c] = e.ucand[c];
             e.Fa[c] = e.stab[c];
@@ -238,8 +243,10 @@ __global__ void k_e_fninit(Eom e) {
 // one synchronous doubling step: F(c) <- F(c) o F(nxt c) while nxt is unary
 __global__ void k_e_double(Eom e, const int32_t *nin, int32_t *nout, const u128 *ain, const u128 *cin,
                            u128 *aout, u128 *cout) {
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < e.ncl;
-         c += (int64_t)gridDim.x * blockDim.x) {
+    bool moved = false;
+    for (int64_t ix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ix < e.nact;
+         ix += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e.alist[ix];
         int x = nin[c];
         u128 a = ain[c], cc = cin[c];
         if (x >= 0 && nin[x] >= 0) {
@@ -249,17 +256,20 @@ __global__ void k_e_double(Eom e, const int32_t *nin, int32_t *nout, const u128 
             a = a > t ? a : t;
             cc = cc + c2;
             x = nin[x];
+            moved = true;
         }
         nout[c] = x;
         aout[c] = a;
         cout[c] = cc;
     }
+    if (__any_sync(0xffffffffu, moved) && lane_id() == 0) e.flag[0] = 1;
 }
 
 // rake ready clusters (all children done)
 __global__ void k_e_rake(Eom e) {
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < e.ncl;
-         c += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t ix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ix < e.nact;
+         ix += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e.alist[ix];
         if (e.done[c] || e.pending[c] != 0) continue;
         u128 acc = acc_of(e, c);
         e.S[c] = e.stab[c] > acc ? e.stab[c] : acc;
@@ -269,8 +279,9 @@ __global__ void k_e_rake(Eom e) {
 
 // unary clusters whose chain bottom was just raked resolve through F
 __global__ void k_e_resolve(Eom e, const int32_t *nfin, const u128 *afin, const u128 *cfin) {
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < e.ncl;
-         c += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t ix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ix < e.nact;
+         ix += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e.alist[ix];
         if (e.done[c] || e.pending[c] != 1) continue;
         int x = nfin[c];
         if (x < 0 || e.state[x] != 1 || e.pending[x] != 0) continue;
@@ -282,8 +293,9 @@ __global__ void k_e_resolve(Eom e, const int32_t *nfin, const u128 *afin, const 
 
 // clusters finished this phase report to a parent that is still open
 __global__ void k_e_report(Eom e) {
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < e.ncl;
-         c += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t ix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ix < e.nact;
+         ix += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e.alist[ix];
         if (!e.state[c]) continue;
         int p = e.par[c];
         if (p >= 0 && !e.state[p] && !e.done[p]) {
@@ -295,12 +307,31 @@ __global__ void k_e_report(Eom e) {
     }
 }
 
-__global__ void k_e_commit(Eom e, unsigned long long *n_open) {
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < e.ncl;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        if (e.state[c]) e.done[c] = 1;
-        if (!e.done[c] && !e.state[c]) atomicAdd(n_open, 1ull);
+__global__ void k_e_commit(Eom e, int32_t *alist2, unsigned long long *n_open) {
+    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < e.nact;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        int64_t ix = base + lane_id();
+        bool open = false;
+        int64_t c = 0;
+        if (ix < e.nact) {
+            c = e.alist[ix];
+            if (e.state[c]) e.done[c] = 1;
+            open = !e.done[c];
+        }
+        unsigned m = __ballot_sync(0xffffffffu, open);
+        if (!m) continue;
+        int leader = __ffs(m) - 1;
+        unsigned long long at = 0;
+        if ((int)lane_id() == leader) at = atomicAdd(n_open, (unsigned long long)__popc(m));
+        at = __shfl_sync(0xffffffffu, at, leader);
+        if (open) alist2[at + __popc(m & ((1u << lane_id()) - 1u))] = (int32_t)c;
     }
+}
+
+__global__ void k_e_iota(int64_t n, int32_t *a) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x)
+        a[x] = (int32_t)x;
 }
 
 // selection: stab(K) >= sum of children's S (ties to the parent)
@@ -331,7 +362,8 @@ __global__ void k_e_select(Eom e, int32_t *H, int32_t *J) {
 
 // highest selected ancestor-or-self, by synchronous doubling
 __global__ void k_e_hdouble(int64_t ncl, const int32_t *Hin, const int32_t *Jin, int32_t *Hout,
-                            int32_t *Jout) {
+                            int32_t *Jout, unsigned long long *flag) {
+    bool live = false;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncl;
          c += (int64_t)gridDim.x * blockDim.x) {
         int j = Jin[c];
@@ -339,11 +371,13 @@ __global__ void k_e_hdouble(int64_t ncl, const int32_t *Hin, const int32_t *Jin,
             int h = Hin[j];
             Hout[c] = h >= 0 ? h : Hin[c];
             Jout[c] = Jin[j];
+            live |= Jin[j] >= 0;
         } else {
             Hout[c] = Hin[c];
             Jout[c] = -1;
         }
     }
+    if (__any_sync(0xffffffffu, live) && lane_id() == 0) flag[0] = 1;
 }
 
 __global__ void k_e_labels(int64_t E, const int32_t *fall_cluster, const int32_t *cidx,
@@ -352,7 +386,7 @@ __global__ void k_e_labels(int64_t E, const int32_t *fall_cluster, const int32_t
          p += (int64_t)gridDim.x * blockDim.x) {
         int L = H[cidx[fall_cluster[p]]];
         lab[p] = L;
-        if (L >= 0) atomicMin(&minmem[L], (int)p);
+        if (L >= 0 && (int)p < minmem[L]) atomicMin(&minmem[L], (int)p);
     }
 }
 
@@ -423,7 +457,7 @@ void plan_condensed(Arena &ws, const Problem &p, Condensed &o) {
 
 struct CScratch {
     int32_t *up, *cpar, *link, *cparent, *clist, *cidx, *par, *ucand, *nxt, *nxt2, *H, *J, *H2, *J2,
-        *rank;
+        *rank, *al1, *al2;
     int *isrep, *nbig, *isc, *pending, *done, *state, *minmem, *flag;
     unsigned long long *cbirth, *cdeath, *st_hi, *st_lo, *acc_hi, *acc_lo, *cnt, *k1, *k2, *v1, *v2;
     long long *cpos, *scan_tmp;
@@ -470,6 +504,8 @@ static CScratch carve_condense(Arena &a, const Problem &p) {
     s.minmem = a.take<int>(E + 1);
     s.flag = a.take<int>(E + 2);
     s.rank = a.take<int32_t>(E + 1);
+    s.al1 = a.take<int32_t>(E + 1);
+    s.al2 = a.take<int32_t>(E + 1);
     s.cnt = a.take<unsigned long long>(4);
     s.k1 = a.take<unsigned long long>(E + 1);
     s.k2 = a.take<unsigned long long>(E + 1);
@@ -547,19 +583,26 @@ dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro 
     e.nxt = s.nxt;
     e.nxt2 = s.nxt2;
     const int gc = grid_for(ncl + 1, kBlock, 65536);
+    e.flag = s.cnt + 2;
     CU_TRY(c, cudaMemsetAsync(s.pending, 0, sizeof(int) * (ncl + 1), st));
     TK(c, "k_e_init", k_e_init<<<gc, kBlock, 0, st>>>(e, s.st_hi, s.st_lo));
-    int dbl = 1;
-    while ((1ll << dbl) < ncl + 1) dbl++;
-    dbl += 1;
+    TK(c, "k_e_iota", k_e_iota<<<gc, kBlock, 0, st>>>(ncl, s.al1));
+    int32_t *al = s.al1, *al2 = s.al2;
+    int64_t nact = ncl;
+    const int kMaxDouble = 40;  // chains are shorter than 2^31
     for (int phase = 0;; phase++) {
         if (phase > 4096) return set_err(c, DGEC_ERR_TIMEOUT, "EOM contraction exceeded 4096 phases");
-        TK(c, "k_e_unary", k_e_unary<<<gc, kBlock, 0, st>>>(e));
-        TK(c, "k_e_fninit", k_e_fninit<<<gc, kBlock, 0, st>>>(e));
+        e.alist = al;
+        e.nact = nact;
+        const int ga = grid_for(nact, kBlock, 65536);
+        TK(c, "k_e_unary", k_e_unary<<<ga, kBlock, 0, st>>>(e));
+        TK(c, "k_e_fninit", k_e_fninit<<<ga, kBlock, 0, st>>>(e));
         int32_t *ni = s.nxt, *no = s.nxt2;
         u128 *ai = s.Fa, *ao = s.Fa2, *ci = s.Fc, *co = s.Fc2;
-        for (int it = 0; it < dbl; it++) {
-            TK(c, "k_e_double", k_e_double<<<gc, kBlock, 0, st>>>(e, ni, no, ai, ci, ao, co));
+        // synchronous doubling until no pointer moves (checked every 2 steps)
+        for (int it = 0; it < kMaxDouble; it++) {
+            if ((it & 1) == 0) CU_TRY(c, cudaMemsetAsync(e.flag, 0, sizeof(unsigned long long), st));
+            TK(c, "k_e_double", k_e_double<<<ga, kBlock, 0, st>>>(e, ni, no, ai, ci, ao, co));
             int32_t *t = ni;
             ni = no;
             no = t;
@@ -569,28 +612,43 @@ dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro 
             ta = ci;
             ci = co;
             co = ta;
+            if (it & 1) {
+                int64_t moved;
+                DG_TRY(read_counters(c, (const int64_t *)e.flag, 1, &moved));
+                if (!moved) break;
+            }
         }
-        TK(c, "k_e_rake", k_e_rake<<<gc, kBlock, 0, st>>>(e));
-        TK(c, "k_e_resolve", k_e_resolve<<<gc, kBlock, 0, st>>>(e, ni, ai, ci));
-        TK(c, "k_e_report", k_e_report<<<gc, kBlock, 0, st>>>(e));
+        TK(c, "k_e_rake", k_e_rake<<<ga, kBlock, 0, st>>>(e));
+        TK(c, "k_e_resolve", k_e_resolve<<<ga, kBlock, 0, st>>>(e, ni, ai, ci));
+        TK(c, "k_e_report", k_e_report<<<ga, kBlock, 0, st>>>(e));
         CU_TRY(c, cudaMemsetAsync(s.cnt, 0, sizeof(unsigned long long), st));
-        TK(c, "k_e_commit", k_e_commit<<<gc, kBlock, 0, st>>>(e, s.cnt));
+        TK(c, "k_e_commit", k_e_commit<<<ga, kBlock, 0, st>>>(e, al2, s.cnt));
         int64_t open;
         DG_TRY(read_counters(c, (const int64_t *)s.cnt, 1, &open));
         if (open == 0) break;
+        int32_t *t = al;
+        al = al2;
+        al2 = t;
+        nact = open;
     }
     TK(c, "k_e_childsum", k_e_childsum<<<gc, kBlock, 0, st>>>(e));
     TK(c, "k_e_childsum2", k_e_childsum2<<<gc, kBlock, 0, st>>>(e));
     TK(c, "k_e_select", k_e_select<<<gc, kBlock, 0, st>>>(e, s.H, s.J));
     int32_t *Hi = s.H, *Ji = s.J, *Ho = s.H2, *Jo = s.J2;
-    for (int it = 0; it < dbl; it++) {
-        TK(c, "k_e_hdouble", k_e_hdouble<<<gc, kBlock, 0, st>>>(ncl, Hi, Ji, Ho, Jo));
+    for (int it = 0; it < kMaxDouble; it++) {
+        if ((it & 1) == 0) CU_TRY(c, cudaMemsetAsync(e.flag, 0, sizeof(unsigned long long), st));
+        TK(c, "k_e_hdouble", k_e_hdouble<<<gc, kBlock, 0, st>>>(ncl, Hi, Ji, Ho, Jo, e.flag));
         int32_t *t = Hi;
         Hi = Ho;
         Ho = t;
         t = Ji;
         Ji = Jo;
         Jo = t;
+        if (it & 1) {
+            int64_t live;
+            DG_TRY(read_counters(c, (const int64_t *)e.flag, 1, &live));
+            if (!live) break;
+        }
     }
     TK(c, "k_fill_i32", k_fill_i32<<<gc, kBlock, 0, st>>>(s.minmem, ncl + 1, INT_MAX));
     TK(c, "k_e_labels", k_e_labels<<<gE, kBlock, 0, st>>>(E, o.fall_cluster, s.cidx, Hi, o.labels, s.minmem));

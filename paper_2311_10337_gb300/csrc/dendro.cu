@@ -23,19 +23,9 @@
 
 namespace dgec {
 
-__device__ __forceinline__ int find_label(int32_t *svpar, int x) {
-    int r = x;
-    for (int it = 0; it < kMaxWalk; it++) {  // bounded: labels form a forest
-        int p = svpar[r];
-        if (p == r) break;
-        r = p;
-    }
-    if (svpar[x] != r) svpar[x] = r;
-    return r;
-}
-
-__global__ void k_d_init(int64_t E, int64_t n, int32_t *svpar, int32_t *sroot, int64_t *ssize,
-                         int32_t *minr, int32_t *tau, int32_t *parent, int32_t *act) {
+__global__ void k_d_init(int64_t E, int64_t n, const int32_t *mu, const int32_t *mv, int32_t *svpar,
+                         int32_t *sroot, int64_t *ssize, int32_t *minr, int32_t *tau, int32_t *parent,
+                         int32_t *act, int32_t *ecu, int32_t *ecv) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < E + n;
          x += (int64_t)gridDim.x * blockDim.x) {
         parent[x] = -1;
@@ -46,20 +36,26 @@ __global__ void k_d_init(int64_t E, int64_t n, int32_t *svpar, int32_t *sroot, i
             minr[x] = INT_MAX;
             tau[x] = INT_MAX;
         }
-        if (x < n) act[x] = (int32_t)x;
+        if (x < n) {
+            act[x] = (int32_t)x;
+            ecu[x] = mu[x];
+            ecv[x] = mv[x];
+        }
     }
 }
 
-__global__ void k_d_find(const int32_t *act, int64_t na, const int32_t *mu, const int32_t *mv,
-                         int32_t *svpar, int32_t *ecu, int32_t *ecv, int32_t *minr) {
+// Every live forest edge bids its rank into the super-vertices at its ends.
+// The labels (ecu, ecv) travel with the edge and are moved one hop after
+// each round's merges, so no label chain is ever walked. A read before the
+// atomic skips bids that cannot win (slots only decrease).
+__global__ void k_d_bid(const int32_t *act, int64_t na, const int32_t *ecu, const int32_t *ecv,
+                        int32_t *minr) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < na;
          j += (int64_t)gridDim.x * blockDim.x) {
         int s = act[j];
-        int cu = find_label(svpar, mu[s]), cv = find_label(svpar, mv[s]);
-        ecu[j] = cu;
-        ecv[j] = cv;
-        atomicMin(&minr[cu], s);
-        atomicMin(&minr[cv], s);
+        int cu = ecu[j], cv = ecv[j];
+        if (s < minr[cu]) atomicMin(&minr[cu], s);
+        if (s < minr[cv]) atomicMin(&minr[cv], s);
     }
 }
 
@@ -106,8 +102,9 @@ __global__ void k_d_tau(const int32_t *act, int64_t na, const int32_t *ecu, cons
          j += (int64_t)gridDim.x * blockDim.x) {
         int s = act[j], cu = ecu[j], cv = ecv[j];
         if (minr[cu] != s && minr[cv] != s) {
-            atomicMin(&tau[gp[cu]], s);
-            atomicMin(&tau[gp[cv]], s);
+            int gu = gp[cu], gv = gp[cv];
+            if (s < tau[gu]) atomicMin(&tau[gu], s);
+            if (s < tau[gv]) atomicMin(&tau[gv], s);
         }
     }
 }
@@ -189,16 +186,24 @@ __global__ void k_d_sizes(const unsigned long long *key, const unsigned long lon
     }
 }
 
+// Keep the unplaced edges (stable), moving their labels one hop to the
+// super-vertex they merged into this round; reset the round's slots.
 __global__ void k_d_keep(const int32_t *act, int64_t na, const int *flag, const long long *pos,
-                         int32_t *act2, const int32_t *ecu, const int32_t *ecv, int32_t *minr,
-                         int32_t *tau) {
+                         int32_t *act2, const int32_t *ecu, const int32_t *ecv, int32_t *ecu2,
+                         int32_t *ecv2, const int32_t *svpar, int32_t *minr, int32_t *tau) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < na;
          j += (int64_t)gridDim.x * blockDim.x) {
-        if (!flag[j]) act2[j - pos[j]] = act[j];
-        minr[ecu[j]] = INT_MAX;
-        minr[ecv[j]] = INT_MAX;
-        tau[ecu[j]] = INT_MAX;
-        tau[ecv[j]] = INT_MAX;
+        int cu = ecu[j], cv = ecv[j];
+        if (!flag[j]) {
+            int64_t at = j - pos[j];
+            act2[at] = act[j];
+            ecu2[at] = svpar[cu];
+            ecv2[at] = svpar[cv];
+        }
+        if (minr[cu] != INT_MAX) minr[cu] = INT_MAX;
+        if (minr[cv] != INT_MAX) minr[cv] = INT_MAX;
+        if (tau[cu] != INT_MAX) tau[cu] = INT_MAX;
+        if (tau[cv] != INT_MAX) tau[cv] = INT_MAX;
     }
 }
 
@@ -210,7 +215,7 @@ void plan_dendro(Arena &ws, const Problem &p, Dendro &o) {
 }
 
 struct DScratch {
-    int32_t *svpar, *sroot, *minr, *tau, *gp, *act, *act2, *ecu, *ecv;
+    int32_t *svpar, *sroot, *minr, *tau, *gp, *act, *act2, *ecu, *ecv, *ecu2, *ecv2;
     int64_t *ssize;
     int *flag, *head;
     long long *pos, *contrib, *csum, *scan_tmp;
@@ -231,6 +236,8 @@ static DScratch carve_dendro(Arena &a, const Problem &p) {
     s.act2 = a.take<int32_t>(E);
     s.ecu = a.take<int32_t>(E);
     s.ecv = a.take<int32_t>(E);
+    s.ecu2 = a.take<int32_t>(E);
+    s.ecv2 = a.take<int32_t>(E);
     s.flag = a.take<int>(E + 1);
     s.head = a.take<int>(E + 1);
     s.pos = a.take<long long>(E + 1);
@@ -258,40 +265,48 @@ dgec_status stage_dendro(Ctx *c, const Problem &p, const Msf &m, Dendro &o, void
     if (E == 0) return DGEC_OK;
     Arena a(scratch, SIZE_MAX);
     DScratch s = carve_dendro(a, p);
-    TK(c, "k_d_init", k_d_init<<<grid_for(E + n, kBlock, 65536), kBlock, 0, st>>>(E, n, s.svpar, s.sroot, s.ssize, s.minr,
-                                                               s.tau, o.parent, s.act));
+    TK(c, "k_d_init", k_d_init<<<grid_for(E + n, kBlock, 65536), kBlock, 0, st>>>(
+                          E, n, m.u, m.v, s.svpar, s.sroot, s.ssize, s.minr, s.tau, o.parent, s.act,
+                          s.ecu, s.ecv));
     int64_t na = n;
-    int32_t *act = s.act, *act2 = s.act2;
+    int32_t *act = s.act, *act2 = s.act2, *ecu = s.ecu, *ecv = s.ecv, *ecu2 = s.ecu2, *ecv2 = s.ecv2;
     const int lb = p.idbits > 0 ? p.idbits : 1;
     for (int64_t round = 0; na > 0; round++) {
         if (round >= (1 << 16))
             return set_err(c, DGEC_ERR_TIMEOUT, "dendrogram rounds exceeded %d", 1 << 16);
         const int g = grid_for(na, kBlock, 65536);
-        TK(c, "k_d_find", k_d_find<<<g, kBlock, 0, st>>>(act, na, m.u, m.v, s.svpar, s.ecu, s.ecv, s.minr));
-        TK(c, "k_d_ptr", k_d_ptr<<<g, kBlock, 0, st>>>(act, na, s.ecu, s.ecv, s.minr, s.gp));
-        TK(c, "k_d_gjump", k_d_gjump<<<g, kBlock, 0, st>>>(act, na, s.ecu, s.ecv, s.minr, s.gp));
-        TK(c, "k_d_tau", k_d_tau<<<g, kBlock, 0, st>>>(act, na, s.ecu, s.ecv, s.minr, s.gp, s.tau));
-        TK(c, "k_d_accept", k_d_accept<<<grid_for(na + 1, kBlock, 65536), kBlock, 0, st>>>(act, na, s.ecu, s.ecv, s.minr, s.gp,
-                                                                      s.tau, s.flag));
+        TK(c, "k_d_bid", k_d_bid<<<g, kBlock, 0, st>>>(act, na, ecu, ecv, s.minr));
+        TK(c, "k_d_ptr", k_d_ptr<<<g, kBlock, 0, st>>>(act, na, ecu, ecv, s.minr, s.gp));
+        TK(c, "k_d_gjump", k_d_gjump<<<g, kBlock, 0, st>>>(act, na, ecu, ecv, s.minr, s.gp));
+        TK(c, "k_d_tau", k_d_tau<<<g, kBlock, 0, st>>>(act, na, ecu, ecv, s.minr, s.gp, s.tau));
+        TK(c, "k_d_accept", k_d_accept<<<grid_for(na + 1, kBlock, 65536), kBlock, 0, st>>>(
+                                act, na, ecu, ecv, s.minr, s.gp, s.tau, s.flag));
         DG_TRY(exclusive_scan_i32(c, s.flag, s.pos, na + 1, s.scan_tmp));
         int64_t nacc;
         DG_TRY(read_counters(c, (const int64_t *)(s.pos + na), 1, &nacc));
         if (nacc <= 0) return set_err(c, DGEC_ERR_INTERNAL, "dendrogram round accepted no edge");
-        TK(c, "k_d_emit", k_d_emit<<<g, kBlock, 0, st>>>(act, na, s.ecu, s.gp, s.flag, s.pos, s.k1, s.v1));
+        TK(c, "k_d_emit", k_d_emit<<<g, kBlock, 0, st>>>(act, na, ecu, s.gp, s.flag, s.pos, s.k1, s.v1));
         bool in_b;
         DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, s.v1, s.v2}, nacc, 0, lb, s.radix, &in_b));
         unsigned long long *key = in_b ? s.k2 : s.k1, *val = in_b ? s.v2 : s.v1;
         const int ga = grid_for(nacc, kBlock, 65536);
-        TK(c, "k_d_chain", k_d_chain<<<ga, kBlock, 0, st>>>(key, val, nacc, E, s.ecu, s.ecv, s.minr, s.sroot, s.ssize, o.a,
-                                         o.b, o.parent, s.contrib, s.head));
+        TK(c, "k_d_chain", k_d_chain<<<ga, kBlock, 0, st>>>(key, val, nacc, E, ecu, ecv, s.minr, s.sroot,
+                                                           s.ssize, o.a, o.b, o.parent, s.contrib, s.head));
         DG_TRY(segmented_inclusive_sum(c, s.contrib, s.head, s.csum, nacc, s.seg_tmp));
-        TK(c, "k_d_sizes", k_d_sizes<<<ga, kBlock, 0, st>>>(key, val, nacc, E, s.ecu, s.ecv, s.csum, o.size, s.svpar,
-                                         s.sroot, s.ssize));
-        TK(c, "k_d_keep", k_d_keep<<<g, kBlock, 0, st>>>(act, na, s.flag, s.pos, act2, s.ecu, s.ecv, s.minr, s.tau));
+        TK(c, "k_d_sizes", k_d_sizes<<<ga, kBlock, 0, st>>>(key, val, nacc, E, ecu, ecv, s.csum, o.size,
+                                                           s.svpar, s.sroot, s.ssize));
+        TK(c, "k_d_keep", k_d_keep<<<g, kBlock, 0, st>>>(act, na, s.flag, s.pos, act2, ecu, ecv, ecu2, ecv2,
+                                                         s.svpar, s.minr, s.tau));
         na -= nacc;
         int32_t *t = act;
         act = act2;
         act2 = t;
+        t = ecu;
+        ecu = ecu2;
+        ecu2 = t;
+        t = ecv;
+        ecv = ecv2;
+        ecv2 = t;
         o.rounds = round + 1;
     }
     return DGEC_OK;

@@ -14,10 +14,13 @@ namespace dgec {
 
 constexpr unsigned long long kMax64 = 0xFFFFFFFFFFFFFFFFull;
 
-// Drop edges inside one component; compact the rest; bid w.
-__global__ void k_filter_bid(const int32_t *u, const int32_t *v, const int64_t *w, int64_t n,
-                             const int32_t *comp, int32_t *u2, int32_t *v2, int64_t *w2,
-                             unsigned long long *cnt, unsigned long long *bw) {
+// Drop edges inside one component; compact the rest; bid w. In the first
+// round every node is its own component, so the label reads are skipped.
+template <bool FIRST>
+__device__ __forceinline__ void filter_bid(const int32_t *u, const int32_t *v, const int64_t *w,
+                                           int64_t n, const int32_t *comp, int32_t *u2, int32_t *v2,
+                                           int64_t *w2, unsigned long long *cnt,
+                                           unsigned long long *bw) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t wb = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; wb < n;
          wb += stride) {
@@ -29,8 +32,8 @@ __global__ void k_filter_bid(const int32_t *u, const int32_t *v, const int64_t *
             a = u[x];
             b = v[x];
             ww = w[x];
-            ca = comp[a];
-            cb = comp[b];
+            ca = FIRST ? a : comp[a];
+            cb = FIRST ? b : comp[b];
             keep = ca != cb;
         }
         unsigned m = __ballot_sync(0xffffffffu, keep);
@@ -44,9 +47,31 @@ __global__ void k_filter_bid(const int32_t *u, const int32_t *v, const int64_t *
             u2[at] = a;
             v2[at] = b;
             w2[at] = ww;
-            atomicMin(&bw[ca], (unsigned long long)ww);
-            atomicMin(&bw[cb], (unsigned long long)ww);
+            // read first: most bids into a large component cannot win, and
+            // skipping them keeps one hot slot from serialising the grid
+            // (the slot only decreases, so a stale read never skips a winner)
+            unsigned long long uw = (unsigned long long)ww;
+            if (uw < bw[ca]) atomicMin(&bw[ca], uw);
+            if (uw < bw[cb]) atomicMin(&bw[cb], uw);
         }
+    }
+}
+
+__global__ void k_filter_bid(const int32_t *u, const int32_t *v, const int64_t *w, int64_t n,
+                             const int32_t *comp, int32_t *u2, int32_t *v2, int64_t *w2,
+                             unsigned long long *cnt, unsigned long long *bw) {
+    filter_bid<false>(u, v, w, n, comp, u2, v2, w2, cnt, bw);
+}
+// First round: every node is its own component and every skeleton edge
+// joins two of them, so nothing is filtered: bid only, no compaction.
+__global__ void k_bid_first(const int32_t *u, const int32_t *v, const int64_t *w, int64_t n,
+                            unsigned long long *bw) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        int a = u[x], b = v[x];
+        unsigned long long uw = (unsigned long long)w[x];
+        if (uw < bw[a]) atomicMin(&bw[a], uw);
+        if (uw < bw[b]) atomicMin(&bw[b], uw);
     }
 }
 
@@ -59,8 +84,8 @@ __global__ void k_bid_uv(const int32_t *u, const int32_t *v, const int64_t *w, i
         unsigned long long ww = (unsigned long long)w[x];
         int ca = comp[a], cb = comp[b];
         unsigned long long key = ((unsigned long long)(unsigned)a << 32) | (unsigned)b;
-        if (ww == bw[ca]) atomicMin(&buv[ca], key);
-        if (ww == bw[cb]) atomicMin(&buv[cb], key);
+        if (ww == bw[ca] && key < buv[ca]) atomicMin(&buv[ca], key);
+        if (ww == bw[cb] && key < buv[cb]) atomicMin(&buv[cb], key);
     }
 }
 
@@ -69,24 +94,40 @@ __global__ void k_bid_uv(const int32_t *u, const int32_t *v, const int64_t *w, i
 __global__ void k_hook(int64_t E, const int32_t *comp, const unsigned long long *bw,
                        const unsigned long long *buv, int32_t *par, int32_t *mu, int32_t *mv,
                        int64_t *mw, unsigned long long *n_out) {
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < E;
-         x += (int64_t)gridDim.x * blockDim.x) {
-        if (comp[x] != (int32_t)x) continue;
-        if (bw[x] == kMax64) {
-            par[x] = (int32_t)x;
-            continue;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < E;
+         base += stride) {
+        int64_t x = base + lane_id();
+        bool emit = false;
+        int a = 0, b = 0;
+        unsigned long long ww = 0;
+        if (x < E && comp[x] == (int32_t)x) {
+            if (bw[x] == kMax64) {
+                par[x] = (int32_t)x;
+            } else {
+                unsigned long long key = buv[x];
+                a = (int)(key >> 32);
+                b = (int)(key & 0xffffffffu);
+                int ca = comp[a], cb = comp[b];
+                int partner = ca == (int)x ? cb : ca;
+                bool mutual = buv[partner] == key;
+                par[x] = (mutual && (int)x < partner) ? (int32_t)x : partner;
+                emit = !mutual || (int)x < partner;
+                ww = bw[x];
+            }
         }
-        unsigned long long key = buv[x];
-        int a = (int)(key >> 32), b = (int)(key & 0xffffffffu);
-        int ca = comp[a], cb = comp[b];
-        int partner = ca == (int)x ? cb : ca;
-        bool mutual = buv[partner] == key;
-        par[x] = (mutual && (int)x < partner) ? (int32_t)x : partner;
-        if (!mutual || (int)x < partner) {
-            unsigned long long at = atomicAdd(n_out, 1ull);
+        // one counter update per warp for the forest edges it appends
+        unsigned m = __ballot_sync(0xffffffffu, emit);
+        if (!m) continue;
+        int leader = __ffs(m) - 1;
+        unsigned long long at = 0;
+        if ((int)lane_id() == leader) at = atomicAdd(n_out, (unsigned long long)__popc(m));
+        at = __shfl_sync(0xffffffffu, at, leader);
+        if (emit) {
+            at += __popc(m & ((1u << lane_id()) - 1u));
             mu[at] = a;
             mv[at] = b;
-            mw[at] = (int64_t)bw[x];
+            mw[at] = (int64_t)ww;
         }
     }
 }
@@ -211,11 +252,20 @@ dgec_status stage_msf(Ctx *c, const Problem &p, const Skel &sk, Msf &o, void *sc
     int64_t *nw = s.wa;
     for (int round = 0; round < 64; round++) {
         CU_TRY(c, cudaMemsetAsync(s.cnt, 0, sizeof(unsigned long long), st));
-        TK(c, "k_filter_bid", k_filter_bid<<<grid_for(n, kBlock, 65536), kBlock, 0, st>>>(cu, cv, cw, n, s.comp, nu, nv, nw,
-                                                                    s.cnt, s.bw));
         int64_t live;
-        DG_TRY(read_counters(c, (const int64_t *)s.cnt, 1, &live));
-        if (live == 0) break;
+        bool compacted = round > 0;
+        if (!compacted) {
+            TK(c, "k_bid_first", k_bid_first<<<grid_for(n, kBlock, 65536), kBlock, 0, st>>>(cu, cv, cw, n, s.bw));
+            live = n;
+            nu = (int32_t *)cu;
+            nv = (int32_t *)cv;
+            nw = (int64_t *)cw;
+        } else {
+            TK(c, "k_filter_bid", k_filter_bid<<<grid_for(n, kBlock, 65536), kBlock, 0, st>>>(
+                                      cu, cv, cw, n, s.comp, nu, nv, nw, s.cnt, s.bw));
+            DG_TRY(read_counters(c, (const int64_t *)s.cnt, 1, &live));
+            if (live == 0) break;
+        }
         TK(c, "k_bid_uv", k_bid_uv<<<grid_for(live, kBlock, 65536), kBlock, 0, st>>>(nu, nv, nw, live, s.comp, s.bw, s.buv));
         TK(c, "k_hook", k_hook<<<gE, kBlock, 0, st>>>(E, s.comp, s.bw, s.buv, s.par, s.tu, s.tv, s.tw, s.cnt + 1));
         TK(c, "k_jump", k_jump<<<gE, kBlock, 0, st>>>(E, s.comp, s.par));
@@ -225,9 +275,9 @@ dgec_status stage_msf(Ctx *c, const Problem &p, const Skel &sk, Msf &o, void *sc
         cv = nv;
         cw = nw;
         n = live;
-        nu = (nu == s.ua) ? s.ub : s.ua;
-        nv = (nv == s.va) ? s.vb : s.va;
-        nw = (nw == s.wa) ? s.wb : s.wa;
+        nu = (compacted && nu == s.ua) ? s.ub : s.ua;
+        nv = (compacted && nv == s.va) ? s.vb : s.va;
+        nw = (compacted && nw == s.wa) ? s.wb : s.wa;
         if (round == 63) return set_err(c, DGEC_ERR_TIMEOUT, "Boruvka did not finish in 64 rounds");
     }
     int64_t m;

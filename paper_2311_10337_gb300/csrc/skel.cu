@@ -41,20 +41,7 @@ __device__ __forceinline__ int64_t lower_bound_t(const int64_t *a, int64_t n, in
 }
 
 // brank[e] = #in-edges of src[e] with t <= t_e; arank[e] = #out-edges of
-// dst[e] with t < t_e.
-__global__ void k_ranks(const int32_t *src, const int32_t *dst, const int64_t *t, int64_t E,
-                        const int64_t *out_off, const int64_t *out_t, const int64_t *in_off,
-                        const int64_t *in_t, int32_t *brank, int32_t *arank) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int i = src[e], j = dst[e];
-        int64_t te = t[e];
-        int64_t ib = in_off[i], ob = out_off[j];
-        brank[e] = (int32_t)upper_bound_t(in_t + ib, in_off[i + 1] - ib, te);
-        arank[e] = (int32_t)lower_bound_t(out_t + ob, out_off[j + 1] - ob, te);
-    }
-}
-
+// dst[e] with t < t_e (computed in k_ranks_knn below).
 struct SkView {
     const int32_t *src, *dst;
     const int64_t *out_off, *in_off;
@@ -161,22 +148,27 @@ __device__ __forceinline__ bool cand_less(const Cand &a, const Cand &b) {
     return a.w < b.w || (a.w == b.w && a.id < b.id);
 }
 
+// The ranks b (tail side) and a (head side) that the skeleton links need
+// come out of the same binary searches that locate the two windows, so one
+// kernel computes both and stores the ranks for the link pass.
 template <int K>
-__global__ void __launch_bounds__(128) k_knn(const int32_t *src, const int32_t *dst, const int64_t *t,
-                                             int64_t E, const int64_t *out_off, const int64_t *out_t,
-                                             const int32_t *out_id, const int64_t *in_off,
-                                             const int64_t *in_t, const int32_t *in_id,
-                                             const int32_t *brank, const int32_t *arank, int k,
-                                             int32_t *knn, int64_t *core) {
+__global__ void __launch_bounds__(128) k_ranks_knn(const int32_t *src, const int32_t *dst,
+                                                   const int64_t *t, int64_t E, const int64_t *out_off,
+                                                   const int64_t *out_t, const int32_t *out_id,
+                                                   const int64_t *in_off, const int64_t *in_t,
+                                                   const int32_t *in_id, int32_t *brank, int32_t *arank,
+                                                   int k, int32_t *knn, int64_t *core) {
     constexpr int N = 2 * K;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
          e += (int64_t)gridDim.x * blockDim.x) {
         int i = src[e], j = dst[e];
         long long te = t[e];
         int64_t ib = in_off[i];
-        int64_t b = brank[e];
         int64_t ob = out_off[j], nout = out_off[j + 1] - ob;
-        int64_t a = arank[e];
+        int64_t b = upper_bound_t(in_t + ib, in_off[i + 1] - ib, te);
+        int64_t a = lower_bound_t(out_t + ob, nout, te);
+        brank[e] = (int32_t)b;
+        arank[e] = (int32_t)a;
         Cand c[N];
         // predecessor window
         int64_t lo = b - K > 0 ? b - K : 0;
@@ -289,8 +281,14 @@ dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void
     Arena a(scratch, SIZE_MAX);
     SkScratch s = carve_skel(a, p);
     int64_t E = p.E;
-    TK(c, "k_ranks", k_ranks<<<grid_for(E, kBlock, 65536), kBlock, 0, st>>>(p.src, p.dst, p.t, E, g.out_off, g.out_t,
-                                                          g.in_off, g.in_t, o.brank, o.arank));
+    int grid = grid_for(E, 128, 1 << 20);
+#define KNN_ARGS                                                                              \
+    p.src, p.dst, p.t, E, g.out_off, g.out_t, g.out_id, g.in_off, g.in_t, g.in_id, o.brank, \
+        o.arank, p.k, o.knn, o.core
+    if (p.k <= 4) TK(c, "k_ranks_knn", k_ranks_knn<4><<<grid, 128, 0, st>>>(KNN_ARGS));
+    else if (p.k <= 8) TK(c, "k_ranks_knn", k_ranks_knn<8><<<grid, 128, 0, st>>>(KNN_ARGS));
+    else TK(c, "k_ranks_knn", k_ranks_knn<16><<<grid, 128, 0, st>>>(KNN_ARGS));
+#undef KNN_ARGS
     SkView v{p.src, p.dst, g.out_off, g.in_off, g.out_id, g.in_id, g.slot_out, o.brank, o.arank};
     TK(c, "k_links", k_links<<<grid_for(E, kBlock, 65536), kBlock, 0, st>>>(v, p.t, g.out_t, g.in_t, E, s.part, s.wgt,
                                                           s.flag));
@@ -301,21 +299,6 @@ dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void
     int64_t n;
     DG_TRY(read_counters(c, (const int64_t *)(s.pos + 2 * E), 1, &n));
     o.n = n;
-    return DGEC_OK;
-}
-
-dgec_status stage_knn(Ctx *c, const Problem &p, const Csr &g, Skel &o) {
-    if (p.E == 0) return DGEC_OK;
-    cudaStream_t st = c->stream;
-    int64_t E = p.E;
-    int grid = grid_for(E, 128, 1 << 20);
-#define KNN_ARGS                                                                              \
-    p.src, p.dst, p.t, E, g.out_off, g.out_t, g.out_id, g.in_off, g.in_t, g.in_id, o.brank, \
-        o.arank, p.k, o.knn, o.core
-    if (p.k <= 4) TK(c, "k_knn", k_knn<4><<<grid, 128, 0, st>>>(KNN_ARGS));
-    else if (p.k <= 8) TK(c, "k_knn", k_knn<8><<<grid, 128, 0, st>>>(KNN_ARGS));
-    else TK(c, "k_knn", k_knn<16><<<grid, 128, 0, st>>>(KNN_ARGS));
-#undef KNN_ARGS
     return DGEC_OK;
 }
 

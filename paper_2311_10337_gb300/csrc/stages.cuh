@@ -41,8 +41,8 @@ struct Skel {
 };
 void plan_skel(Arena &ws, const Problem &p, Skel &o);
 size_t skel_scratch_bytes(const Problem &p);
+// also writes the kNN ids and core distances (same searches)
 dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void *scratch);
-dgec_status stage_knn(Ctx *c, const Problem &p, const Csr &g, Skel &o);
 
 // Stage C: minimum spanning forest of the skeleton (Borůvka), sorted by
 // (w, u, v).
