@@ -65,8 +65,9 @@ typedef struct {
     const int32_t *out_id, *in_id;     /* [n_edges] */
     /* Alg. 3: skeleton L*_G as undirected edges (u < v, w = |t_u - t_v|),
      * each line-graph edge once. Deterministic order: first every edge's
-     * link to the first later out-edge at its head, by edge id, then every
-     * edge's link to the retained in-edge at its tail, by edge id. */
+     * link to the first later out-edge at its head, then every edge's link
+     * to the retained in-edge at its tail, each group in (t, id) order of
+     * the edge that emits the link. */
     const int32_t *sk_u, *sk_v;        /* [n_skeleton] */
     const int64_t *sk_w;
     /* k nearest line-graph neighbours in time: knn_id[e*k + x], ranked by

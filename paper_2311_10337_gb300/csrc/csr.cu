@@ -2,15 +2,16 @@
 // representation") with every vertex's in-list and out-list sorted by time
 // (Alg. 2: "Sort E_i by time"; ties by edge id).
 //
-// Each edge becomes one 64-bit key ((t - t_min) << idbits | id), unique and
-// ordered like (t, id), so a list sorts by key alone and t, id unpack from
-// it. Keys are scattered into their vertex's segment through per-vertex
-// cursors (warp-aggregated atomics absorb hub vertices), then each segment
-// is sorted by the bin its length falls in:
+// First a device-wide radix sort of the 64-bit keys ((t - t_min) << idbits
+// | id) ranks all edges in (t, id) order; that rank r is the internal node
+// id of every later stage, and per-vertex lists sorted by (t, id) are just
+// lists sorted by r. Ranks are scattered into their vertex's segment through
+// per-vertex cursors (warp-aggregated atomics absorb hub vertices), then
+// each segment is sorted by the bin its length falls in:
 //   2..32 elements      one warp, bitonic network over shuffles;
 //   33..256, 257..2048  one CTA, bitonic network in shared memory;
 //   > 2048 (hubs)       all hub segments together through the device-wide
-//                       radix sort, keyed (segment, key).
+//                       radix sort, keyed (segment, r).
 #include "stages.cuh"
 
 namespace dgec {
@@ -82,25 +83,47 @@ __global__ void k_init_flags(long long *flags) {
 
 __global__ void k_set_i64(long long *p, long long v) { *p = v; }
 
-__global__ void k_scatter(const int32_t *src, const int32_t *dst, const int64_t *t, int64_t E,
-                          long long tmin, int idbits, const int64_t *out_off, const int64_t *in_off,
-                          int *cur_out, int *cur_in, unsigned long long *okey,
-                          unsigned long long *ikey) {
+// rank r = position of edge (t, id) in the global order; time-ordered
+// copies of the inputs for the later stages
+__global__ void k_rank_init(const unsigned long long *ks, int64_t E, long long tmin, int idbits,
+                            const int32_t *src, const int32_t *dst, int32_t *orig_of,
+                            int32_t *rank_of, int32_t *isrc, int32_t *idst, int64_t *it) {
+    const unsigned long long idmask = (1ull << idbits) - 1ull;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < E;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long k = ks[r];
+        int32_t e = (int32_t)(k & idmask);
+        orig_of[r] = e;
+        rank_of[e] = (int32_t)r;
+        it[r] = (int64_t)(k >> idbits) + tmin;
+        isrc[r] = src[e];
+        idst[r] = dst[e];
+    }
+}
+
+__global__ void k_pack_keys(const int64_t *t, int64_t E, long long tmin, int idbits,
+                            unsigned long long *k) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
+         e += (int64_t)gridDim.x * blockDim.x)
+        k[e] = ((unsigned long long)(t[e] - tmin) << idbits) | (unsigned long long)e;
+}
+
+__global__ void k_scatter(const int32_t *isrc, const int32_t *idst, int64_t E,
+                          const int64_t *out_off, const int64_t *in_off, int *cur_out, int *cur_in,
+                          unsigned long long *okey, unsigned long long *ikey) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = stride >> 5;
     for (int64_t wb = warp_global * 32; wb < E; wb += nwarps * 32) {
-        int64_t e = wb + lane_id();
-        bool ok = e < E;
+        int64_t r = wb + lane_id();
+        bool ok = r < E;
         unsigned act = __ballot_sync(0xffffffffu, ok);
         if (ok) {
-            int s = src[e], d = dst[e];
-            unsigned long long key =
-                ((unsigned long long)(t[e] - tmin) << idbits) | (unsigned long long)e;
+            int s = isrc[r], d = idst[r];
             int ro = warp_agg_inc(cur_out, s, act);
             int ri = warp_agg_inc(cur_in, d, act);
-            okey[out_off[s] + ro] = key;
-            ikey[in_off[d] + ri] = key;
+            okey[out_off[s] + ro] = (unsigned long long)r;
+            ikey[in_off[d] + ri] = (unsigned long long)r;
         }
     }
 }
@@ -214,16 +237,16 @@ __global__ void k_hub_scatter(const unsigned long long *hub_of, const unsigned l
     }
 }
 
-__global__ void k_unpack(const unsigned long long *keys, int64_t E, long long tmin, int idbits,
-                         int64_t *t_out, int32_t *id_out, int32_t *slot_of) {
-    const unsigned long long idmask = (idbits >= 64) ? ~0ull : ((1ull << idbits) - 1ull);
+__global__ void k_unpack(const unsigned long long *keys, int64_t E, const int32_t *orig_of,
+                         const int64_t *it, int64_t *t_out, int32_t *id_out, int32_t *r_out,
+                         int32_t *slot_of) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < E;
          x += (int64_t)gridDim.x * blockDim.x) {
-        unsigned long long k = keys[x];
-        int32_t id = (int32_t)(k & idmask);
-        t_out[x] = (int64_t)(k >> idbits) + tmin;
-        id_out[x] = id;
-        slot_of[id] = (int32_t)x;
+        int32_t r = (int32_t)keys[x];
+        r_out[x] = r;
+        id_out[x] = orig_of[r];
+        t_out[x] = it[r];
+        if (slot_of) slot_of[r] = (int32_t)x;
     }
 }
 
@@ -234,8 +257,14 @@ void plan_csr(Arena &ws, const Problem &p, Csr &o) {
     o.in_t = ws.take<int64_t>(p.E);
     o.out_id = ws.take<int32_t>(p.E);
     o.in_id = ws.take<int32_t>(p.E);
+    o.out_r = ws.take<int32_t>(p.E);
+    o.in_r = ws.take<int32_t>(p.E);
+    o.orig_of = ws.take<int32_t>(p.E);
+    o.rank_of = ws.take<int32_t>(p.E);
+    o.isrc = ws.take<int32_t>(p.E);
+    o.idst = ws.take<int32_t>(p.E);
+    o.it = ws.take<int64_t>(p.E);
     o.slot_out = ws.take<int32_t>(p.E);
-    o.slot_in = ws.take<int32_t>(p.E);
 }
 
 // scratch layout
@@ -354,19 +383,28 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
     TK(c, "k_set_i64", k_set_i64<<<1, 1, 0, st>>>((long long *)o.out_off + V, E));
     TK(c, "k_set_i64", k_set_i64<<<1, 1, 0, st>>>((long long *)o.in_off + V, E));
     if (E == 0) return DGEC_OK;
-    // scatter keys (cursors reuse the degree arrays)
+    // global (t, id) order: internal ids
+    const int gEE = grid_for(E, kBlock, 65536);
+    TK(c, "k_pack_keys", k_pack_keys<<<gEE, kBlock, 0, st>>>(p.t, E, p.tmin, p.idbits, s.okey));
+    {
+        bool in_b;
+        DG_TRY(radix_sort(c, RadixBuffers{s.okey, s.ikey, nullptr, nullptr}, E, 0, p.idbits + p.tbits,
+                          s.radix, &in_b));
+        TK(c, "k_rank_init", k_rank_init<<<gEE, kBlock, 0, st>>>(in_b ? s.ikey : s.okey, E, p.tmin, p.idbits,
+                                                                p.src, p.dst, o.orig_of, o.rank_of,
+                                                                o.isrc, o.idst, o.it));
+    }
+    // scatter ranks into their segments (cursors reuse the degree arrays)
     CU_TRY(c, cudaMemsetAsync(s.deg_out, 0, sizeof(int) * (V + 1), st));
     CU_TRY(c, cudaMemsetAsync(s.deg_in, 0, sizeof(int) * (V + 1), st));
     TK(c, "k_scatter", k_scatter<<<grid_for(E, kBlock, (int64_t)c->num_sms * 16), kBlock, 0, st>>>(
-        p.src, p.dst, p.t, E, p.tmin, p.idbits, o.out_off, o.in_off, s.deg_out, s.deg_in, s.okey,
-        s.ikey));
-    int key_bits = p.idbits + p.tbits;
-    DG_TRY(sort_segments(c, p, s.okey, o.out_off, s, key_bits));
-    DG_TRY(sort_segments(c, p, s.ikey, o.in_off, s, key_bits));
-    TK(c, "k_unpack", k_unpack<<<grid_for(E, kBlock, 65536), kBlock, 0, st>>>(s.okey, E, p.tmin, p.idbits, o.out_t, o.out_id,
-                                                           o.slot_out));
-    TK(c, "k_unpack", k_unpack<<<grid_for(E, kBlock, 65536), kBlock, 0, st>>>(s.ikey, E, p.tmin, p.idbits, o.in_t, o.in_id,
-                                                           o.slot_in));
+                           o.isrc, o.idst, E, o.out_off, o.in_off, s.deg_out, s.deg_in, s.okey, s.ikey));
+    DG_TRY(sort_segments(c, p, s.okey, o.out_off, s, p.idbits));
+    DG_TRY(sort_segments(c, p, s.ikey, o.in_off, s, p.idbits));
+    TK(c, "k_unpack", k_unpack<<<gEE, kBlock, 0, st>>>(s.okey, E, o.orig_of, o.it, o.out_t, o.out_id,
+                                                       o.out_r, o.slot_out));
+    TK(c, "k_unpack", k_unpack<<<gEE, kBlock, 0, st>>>(s.ikey, E, o.orig_of, o.it, o.in_t, o.in_id,
+                                                       o.in_r, nullptr));
     return DGEC_OK;
 }
 

@@ -23,15 +23,18 @@
 
 namespace dgec {
 
-__global__ void k_d_init(int64_t E, int64_t n, const int32_t *mu, const int32_t *mv, int32_t *svpar,
-                         int32_t *sroot, int64_t *ssize, int32_t *minr, int32_t *tau, int32_t *parent,
-                         int32_t *act, int32_t *ecu, int32_t *ecv) {
+// Super-vertex labels are internal ids r (a leaf's label is its own r);
+// sroot holds dendrogram node ids, so a leaf's root is its original id.
+__global__ void k_d_init(int64_t E, int64_t n, const int32_t *mu, const int32_t *mv,
+                         const int32_t *orig_of, int32_t *svpar, int32_t *sroot, int64_t *ssize,
+                         int32_t *minr, int32_t *tau, int32_t *parent, int32_t *act, int32_t *ecu,
+                         int32_t *ecv) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < E + n;
          x += (int64_t)gridDim.x * blockDim.x) {
         parent[x] = -1;
         if (x < E) {
             svpar[x] = (int32_t)x;
-            sroot[x] = (int32_t)x;
+            sroot[x] = orig_of[x];
             ssize[x] = 1;
             minr[x] = INT_MAX;
             tau[x] = INT_MAX;
@@ -123,29 +126,33 @@ __global__ void k_d_accept(const int32_t *act, int64_t na, const int32_t *ecu, c
     }
 }
 
+// accepted edges keyed (group, rank) so a sort puts each group's chain in
+// rank order; the value is the edge's slot in the active list
 __global__ void k_d_emit(const int32_t *act, int64_t na, const int32_t *ecu, const int32_t *gp,
-                         const int *flag, const long long *pos, unsigned long long *key,
+                         const int *flag, const long long *pos, int sbits, unsigned long long *key,
                          unsigned long long *val) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < na;
          j += (int64_t)gridDim.x * blockDim.x) {
         if (!flag[j]) continue;
         int64_t at = pos[j];
-        key[at] = (unsigned long long)gp[ecu[j]];
-        val[at] = ((unsigned long long)(unsigned)act[j] << 32) | (unsigned long long)j;
+        key[at] = ((unsigned long long)gp[ecu[j]] << sbits) | (unsigned long long)act[j];
+        val[at] = (unsigned long long)j;
     }
 }
 
 __global__ void k_d_chain(const unsigned long long *key, const unsigned long long *val, int64_t nacc,
-                          int64_t E, const int32_t *ecu, const int32_t *ecv, const int32_t *minr,
-                          const int32_t *sroot, const int64_t *ssize, int32_t *la, int32_t *lb,
-                          int32_t *parent, long long *contrib, int *head) {
+                          int64_t E, int sbits, const int32_t *ecu, const int32_t *ecv,
+                          const int32_t *minr, const int32_t *sroot, const int64_t *ssize, int32_t *la,
+                          int32_t *lb, int32_t *parent, long long *contrib, int *head) {
+    const unsigned long long smask = (1ull << sbits) - 1ull;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nacc;
          x += (int64_t)gridDim.x * blockDim.x) {
-        unsigned long long G = key[x];
-        int s = (int)(val[x] >> 32);
-        int j = (int)(val[x] & 0xffffffffu);
+        unsigned long long k = key[x];
+        unsigned long long G = k >> sbits;
+        int s = (int)(k & smask);
+        int j = (int)val[x];
         int cu = ecu[j], cv = ecv[j];
-        bool h = (x == 0) || key[x - 1] != G;
+        bool h = (x == 0) || (key[x - 1] >> sbits) != G;
         int c1, c2;
         long long add;
         if (h) {
@@ -154,7 +161,7 @@ __global__ void k_d_chain(const unsigned long long *key, const unsigned long lon
             add = ssize[cu] + ssize[cv];
         } else {
             int Y = (minr[cu] == s) ? cu : cv;
-            c1 = (int)(E + (int64_t)(val[x - 1] >> 32));
+            c1 = (int)(E + (int64_t)(key[x - 1] & smask));
             c2 = sroot[Y];
             add = ssize[Y];
         }
@@ -168,17 +175,20 @@ __global__ void k_d_chain(const unsigned long long *key, const unsigned long lon
 }
 
 __global__ void k_d_sizes(const unsigned long long *key, const unsigned long long *val, int64_t nacc,
-                          int64_t E, const int32_t *ecu, const int32_t *ecv, const long long *csum,
-                          int64_t *lsize, int32_t *svpar, int32_t *sroot, int64_t *ssize) {
+                          int64_t E, int sbits, const int32_t *ecu, const int32_t *ecv,
+                          const long long *csum, int64_t *lsize, int32_t *svpar, int32_t *sroot,
+                          int64_t *ssize) {
+    const unsigned long long smask = (1ull << sbits) - 1ull;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nacc;
          x += (int64_t)gridDim.x * blockDim.x) {
-        unsigned long long G = key[x];
-        int s = (int)(val[x] >> 32);
-        int j = (int)(val[x] & 0xffffffffu);
+        unsigned long long k = key[x];
+        unsigned long long G = k >> sbits;
+        int s = (int)(k & smask);
+        int j = (int)val[x];
         lsize[s] = csum[x];
         svpar[ecu[j]] = (int32_t)G;
         svpar[ecv[j]] = (int32_t)G;
-        bool tail = (x == nacc - 1) || key[x + 1] != G;
+        bool tail = (x == nacc - 1) || (key[x + 1] >> sbits) != G;
         if (tail) {
             sroot[G] = (int32_t)(E + s);
             ssize[G] = csum[x];
@@ -186,8 +196,27 @@ __global__ void k_d_sizes(const unsigned long long *key, const unsigned long lon
     }
 }
 
-// Keep the unplaced edges (stable), moving their labels one hop to the
-// super-vertex they merged into this round; reset the round's slots.
+// the first active list: forest edges ordered by their internal end, so
+// neighbouring threads touch neighbouring labels
+__global__ void k_d_order_keys(const int32_t *ru, int64_t n, unsigned long long *k,
+                               unsigned long long *v) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        k[x] = (unsigned long long)ru[x];
+        v[x] = (unsigned long long)x;
+    }
+}
+__global__ void k_d_order_act(const unsigned long long *v, int64_t n, const int32_t *ru,
+                              const int32_t *rv, int32_t *act, int32_t *ecu, int32_t *ecv) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        int s = (int)v[j];
+        act[j] = s;
+        ecu[j] = ru[s];
+        ecv[j] = rv[s];
+    }
+}
+
 __global__ void k_d_keep(const int32_t *act, int64_t na, const int *flag, const long long *pos,
                          int32_t *act2, const int32_t *ecu, const int32_t *ecv, int32_t *ecu2,
                          int32_t *ecv2, const int32_t *svpar, int32_t *minr, int32_t *tau) {
@@ -258,7 +287,7 @@ size_t dendro_scratch_bytes(const Problem &p) {
     return a.off;
 }
 
-dgec_status stage_dendro(Ctx *c, const Problem &p, const Msf &m, Dendro &o, void *scratch) {
+dgec_status stage_dendro(Ctx *c, const Problem &p, const Csr &g, const Msf &m, Dendro &o, void *scratch) {
     cudaStream_t st = c->stream;
     int64_t E = p.E, n = m.n;
     o.rounds = 0;
@@ -266,11 +295,20 @@ dgec_status stage_dendro(Ctx *c, const Problem &p, const Msf &m, Dendro &o, void
     Arena a(scratch, SIZE_MAX);
     DScratch s = carve_dendro(a, p);
     TK(c, "k_d_init", k_d_init<<<grid_for(E + n, kBlock, 65536), kBlock, 0, st>>>(
-                          E, n, m.u, m.v, s.svpar, s.sroot, s.ssize, s.minr, s.tau, o.parent, s.act,
-                          s.ecu, s.ecv));
+                          E, n, m.ru, m.rv, g.orig_of, s.svpar, s.sroot, s.ssize, s.minr, s.tau,
+                          o.parent, s.act, s.ecu, s.ecv));
+    const int lb = p.idbits > 0 ? p.idbits : 1;
+    const int sbits = bits_for((uint64_t)(n > 1 ? n - 1 : 1));
+    if (n > 1) {
+        const int gn = grid_for(n, kBlock, 65536);
+        TK(c, "k_d_order", k_d_order_keys<<<gn, kBlock, 0, st>>>(m.ru, n, s.k1, s.v1));
+        bool in_b;
+        DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, s.v1, s.v2}, n, 0, lb, s.radix, &in_b));
+        TK(c, "k_d_order", k_d_order_act<<<gn, kBlock, 0, st>>>(in_b ? s.v2 : s.v1, n, m.ru, m.rv, s.act,
+                                                               s.ecu, s.ecv));
+    }
     int64_t na = n;
     int32_t *act = s.act, *act2 = s.act2, *ecu = s.ecu, *ecv = s.ecv, *ecu2 = s.ecu2, *ecv2 = s.ecv2;
-    const int lb = p.idbits > 0 ? p.idbits : 1;
     for (int64_t round = 0; na > 0; round++) {
         if (round >= (1 << 16))
             return set_err(c, DGEC_ERR_TIMEOUT, "dendrogram rounds exceeded %d", 1 << 16);
@@ -285,15 +323,15 @@ dgec_status stage_dendro(Ctx *c, const Problem &p, const Msf &m, Dendro &o, void
         int64_t nacc;
         DG_TRY(read_counters(c, (const int64_t *)(s.pos + na), 1, &nacc));
         if (nacc <= 0) return set_err(c, DGEC_ERR_INTERNAL, "dendrogram round accepted no edge");
-        TK(c, "k_d_emit", k_d_emit<<<g, kBlock, 0, st>>>(act, na, ecu, s.gp, s.flag, s.pos, s.k1, s.v1));
+        TK(c, "k_d_emit", k_d_emit<<<g, kBlock, 0, st>>>(act, na, ecu, s.gp, s.flag, s.pos, sbits, s.k1, s.v1));
         bool in_b;
-        DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, s.v1, s.v2}, nacc, 0, lb, s.radix, &in_b));
+        DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, s.v1, s.v2}, nacc, 0, lb + sbits, s.radix, &in_b));
         unsigned long long *key = in_b ? s.k2 : s.k1, *val = in_b ? s.v2 : s.v1;
         const int ga = grid_for(nacc, kBlock, 65536);
-        TK(c, "k_d_chain", k_d_chain<<<ga, kBlock, 0, st>>>(key, val, nacc, E, ecu, ecv, s.minr, s.sroot,
+        TK(c, "k_d_chain", k_d_chain<<<ga, kBlock, 0, st>>>(key, val, nacc, E, sbits, ecu, ecv, s.minr, s.sroot,
                                                            s.ssize, o.a, o.b, o.parent, s.contrib, s.head));
         DG_TRY(segmented_inclusive_sum(c, s.contrib, s.head, s.csum, nacc, s.seg_tmp));
-        TK(c, "k_d_sizes", k_d_sizes<<<ga, kBlock, 0, st>>>(key, val, nacc, E, ecu, ecv, s.csum, o.size,
+        TK(c, "k_d_sizes", k_d_sizes<<<ga, kBlock, 0, st>>>(key, val, nacc, E, sbits, ecu, ecv, s.csum, o.size,
                                                            s.svpar, s.sroot, s.ssize));
         TK(c, "k_d_keep", k_d_keep<<<g, kBlock, 0, st>>>(act, na, s.flag, s.pos, act2, ecu, ecv, ecu2, ecv2,
                                                          s.svpar, s.minr, s.tau));

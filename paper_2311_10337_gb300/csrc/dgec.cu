@@ -67,8 +67,8 @@ dgec_status check_args(Ctx *c, int64_t E, int32_t V, const dgec_params *prm) {
 dgec_status run_pipeline(Ctx *c, Problem &p, Layout &L, dgec_result *out) {
     DG_TRY(stage_csr(c, p, L.csr, L.scratch));
     DG_TRY(stage_skeleton(c, p, L.csr, L.skel, L.scratch));
-    DG_TRY(stage_msf(c, p, L.skel, L.msf, L.scratch));
-    DG_TRY(stage_dendro(c, p, L.msf, L.den, L.scratch));
+    DG_TRY(stage_msf(c, p, L.csr, L.skel, L.msf, L.scratch));
+    DG_TRY(stage_dendro(c, p, L.csr, L.msf, L.den, L.scratch));
     DG_TRY(stage_condense(c, p, L.msf, L.den, L.cond, L.scratch));
     CU_TRY(c, cudaStreamSynchronize(c->stream));
     CU_TRY(c, cudaGetLastError());

@@ -171,34 +171,152 @@ __global__ void k_iota(int64_t E, int32_t *comp) {
         comp[x] = (int32_t)x;
 }
 
-__global__ void k_pack_uv(const int32_t *u, const int32_t *v, const int64_t *w, int64_t n,
-                          int idbits, unsigned long long *k, unsigned long long *val) {
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
-         x += (int64_t)gridDim.x * blockDim.x) {
-        k[x] = ((unsigned long long)u[x] << idbits) | (unsigned long long)v[x];
-        val[x] = (unsigned long long)w[x];
+// ----- the pipeline's forest stage: nodes are internal ids r; each edge
+// carries its original ends (u < v) for the (w, u, v) tie-break key.
+
+__global__ void k_r_filter_bid(const int32_t *ru, const int32_t *rv, const int32_t *u, const int32_t *v,
+                               const int64_t *w, int64_t n, const int32_t *comp, int32_t *ru2,
+                               int32_t *rv2, int32_t *u2, int32_t *v2, int64_t *w2,
+                               unsigned long long *cnt, unsigned long long *bw) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t wb = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; wb < n;
+         wb += stride) {
+        int64_t x = wb + lane_id();
+        bool keep = false;
+        int a = 0, b = 0, ca = 0, cb = 0;
+        if (x < n) {
+            a = ru[x];
+            b = rv[x];
+            ca = comp[a];
+            cb = comp[b];
+            keep = ca != cb;
+        }
+        unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (m == 0) continue;
+        int leader = __ffs(m) - 1;
+        unsigned long long base = 0;
+        if ((int)lane_id() == leader) base = atomicAdd(cnt, (unsigned long long)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (keep) {
+            int64_t at = (int64_t)base + __popc(m & ((1u << lane_id()) - 1u));
+            unsigned long long uw = (unsigned long long)w[x];
+            ru2[at] = a;
+            rv2[at] = b;
+            u2[at] = u[x];
+            v2[at] = v[x];
+            w2[at] = (int64_t)uw;
+            if (uw < bw[ca]) atomicMin(&bw[ca], uw);
+            if (uw < bw[cb]) atomicMin(&bw[cb], uw);
+        }
     }
 }
 
-__global__ void k_unpack_msf(const unsigned long long *wkey, const unsigned long long *uv, int64_t n,
-                             int idbits, int32_t *u, int32_t *v, int64_t *w) {
-    const unsigned long long mask = (1ull << idbits) - 1ull;
+__global__ void k_r_bid_uv(const int32_t *ru, const int32_t *rv, const int32_t *u, const int32_t *v,
+                           const int64_t *w, int64_t n, const int32_t *comp,
+                           const unsigned long long *bw, unsigned long long *buv) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
-        u[x] = (int32_t)(uv[x] >> idbits);
-        v[x] = (int32_t)(uv[x] & mask);
-        w[x] = (int64_t)wkey[x];
+        unsigned long long ww = (unsigned long long)w[x];
+        int ca = comp[ru[x]], cb = comp[rv[x]];
+        bool wa = ww == bw[ca], wb = ww == bw[cb];
+        if (!wa && !wb) continue;
+        unsigned long long key = ((unsigned long long)(unsigned)u[x] << 32) | (unsigned)v[x];
+        if (wa && key < buv[ca]) atomicMin(&buv[ca], key);
+        if (wb && key < buv[cb]) atomicMin(&buv[cb], key);
+    }
+}
+
+// Component roots hook along their winning edge (named by its original
+// ends; rank_of gives the internal ends) and append it once.
+__global__ void k_r_hook(int64_t E, const int32_t *comp, const int32_t *rank_of,
+                         const unsigned long long *bw, const unsigned long long *buv, int32_t *par,
+                         int32_t *mu, int32_t *mv, int32_t *mru, int32_t *mrv, int64_t *mw,
+                         unsigned long long *n_out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < E;
+         base += stride) {
+        int64_t x = base + lane_id();
+        bool emit = false;
+        int a = 0, b = 0, ra = 0, rb = 0;
+        unsigned long long ww = 0;
+        if (x < E && comp[x] == (int32_t)x) {
+            if (bw[x] == kMax64) {
+                par[x] = (int32_t)x;
+            } else {
+                unsigned long long key = buv[x];
+                a = (int)(key >> 32);
+                b = (int)(key & 0xffffffffu);
+                ra = rank_of[a];
+                rb = rank_of[b];
+                int ca = comp[ra], cb = comp[rb];
+                int partner = ca == (int)x ? cb : ca;
+                bool mutual = buv[partner] == key;
+                par[x] = (mutual && (int)x < partner) ? (int32_t)x : partner;
+                emit = !mutual || (int)x < partner;
+                ww = bw[x];
+            }
+        }
+        unsigned m = __ballot_sync(0xffffffffu, emit);
+        if (!m) continue;
+        int leader = __ffs(m) - 1;
+        unsigned long long at = 0;
+        if ((int)lane_id() == leader) at = atomicAdd(n_out, (unsigned long long)__popc(m));
+        at = __shfl_sync(0xffffffffu, at, leader);
+        if (emit) {
+            at += __popc(m & ((1u << lane_id()) - 1u));
+            mu[at] = a;
+            mv[at] = b;
+            mru[at] = ra;
+            mrv[at] = rb;
+            mw[at] = (int64_t)ww;
+        }
+    }
+}
+
+__global__ void k_pack_uv_idx(const int32_t *u, const int32_t *v, int64_t n, int idbits,
+                              unsigned long long *k, unsigned long long *val) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        k[x] = ((unsigned long long)u[x] << idbits) | (unsigned long long)v[x];
+        val[x] = (unsigned long long)x;
+    }
+}
+
+__global__ void k_gather_w(const int64_t *w, const unsigned long long *idx, int64_t n,
+                           unsigned long long *k, unsigned long long *val) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long i = idx[x];
+        k[x] = (unsigned long long)w[i];
+        val[x] = i;
+    }
+}
+
+__global__ void k_gather_msf(const unsigned long long *idx, int64_t n, const int32_t *tu,
+                             const int32_t *tv, const int32_t *tru, const int32_t *trv,
+                             const int64_t *tw, int32_t *u, int32_t *v, int32_t *ru, int32_t *rv,
+                             int64_t *w) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long i = idx[x];
+        u[x] = tu[i];
+        v[x] = tv[i];
+        ru[x] = tru[i];
+        rv[x] = trv[i];
+        w[x] = tw[i];
     }
 }
 
 void plan_msf(Arena &ws, const Problem &p, Msf &o) {
     o.u = ws.take<int32_t>(p.E);
     o.v = ws.take<int32_t>(p.E);
+    o.ru = ws.take<int32_t>(p.E);
+    o.rv = ws.take<int32_t>(p.E);
     o.w = ws.take<int64_t>(p.E);
 }
 
 struct MsfScratch {
-    int32_t *comp, *par, *ua, *va, *ub, *vb, *tu, *tv;
+    int32_t *comp, *par, *ua, *va, *ub, *vb, *tu, *tv, *rua, *rva, *rub, *rvb, *tru, *trv;
     int64_t *wa, *wb, *tw;
     unsigned long long *bw, *buv, *cnt;
     unsigned long long *k1, *k2, *v1, *v2;
@@ -217,6 +335,12 @@ static MsfScratch carve_msf(Arena &a, const Problem &p) {
     s.wb = a.take<int64_t>(S);
     s.tu = a.take<int32_t>(E);
     s.tv = a.take<int32_t>(E);
+    s.rua = a.take<int32_t>(S);
+    s.rva = a.take<int32_t>(S);
+    s.rub = a.take<int32_t>(S);
+    s.rvb = a.take<int32_t>(S);
+    s.tru = a.take<int32_t>(E);
+    s.trv = a.take<int32_t>(E);
     s.tw = a.take<int64_t>(E);
     s.bw = a.take<unsigned long long>(E);
     s.buv = a.take<unsigned long long>(E);
@@ -234,7 +358,7 @@ size_t msf_scratch_bytes(const Problem &p) {
     return a.off;
 }
 
-dgec_status stage_msf(Ctx *c, const Problem &p, const Skel &sk, Msf &o, void *scratch) {
+dgec_status stage_msf(Ctx *c, const Problem &p, const Csr &g, const Skel &sk, Msf &o, void *scratch) {
     cudaStream_t st = c->stream;
     o.n = 0;
     int64_t E = p.E;
@@ -245,56 +369,61 @@ dgec_status stage_msf(Ctx *c, const Problem &p, const Skel &sk, Msf &o, void *sc
     TK(c, "k_iota", k_iota<<<gE, kBlock, 0, st>>>(E, s.comp));
     TK(c, "k_reset_best", k_reset_best<<<gE, kBlock, 0, st>>>(E, s.bw, s.buv));
     CU_TRY(c, cudaMemsetAsync(s.cnt, 0, 4 * sizeof(unsigned long long), st));
-    const int32_t *cu = sk.u, *cv = sk.v;
+    // live edge list: (ru, rv) internal ends, (u, v) original ends, w
+    const int32_t *cru = sk.ru, *crv = sk.rv, *cu = sk.u, *cv = sk.v;
     const int64_t *cw = sk.w;
     int64_t n = sk.n;
-    int32_t *nu = s.ua, *nv = s.va;
-    int64_t *nw = s.wa;
-    for (int round = 0; round < 64; round++) {
-        CU_TRY(c, cudaMemsetAsync(s.cnt, 0, sizeof(unsigned long long), st));
+    int which = 0;  // next compaction target: 0 -> a buffers, 1 -> b buffers
+    for (int round = 0;; round++) {
+        if (round >= 64) return set_err(c, DGEC_ERR_TIMEOUT, "Boruvka did not finish in 64 rounds");
         int64_t live;
-        bool compacted = round > 0;
-        if (!compacted) {
-            TK(c, "k_bid_first", k_bid_first<<<grid_for(n, kBlock, 65536), kBlock, 0, st>>>(cu, cv, cw, n, s.bw));
+        if (round == 0) {
+            // every node is its own component: nothing to filter, just bid
+            TK(c, "k_bid_first", k_bid_first<<<grid_for(n, kBlock, 65536), kBlock, 0, st>>>(cru, crv, cw, n, s.bw));
             live = n;
-            nu = (int32_t *)cu;
-            nv = (int32_t *)cv;
-            nw = (int64_t *)cw;
         } else {
-            TK(c, "k_filter_bid", k_filter_bid<<<grid_for(n, kBlock, 65536), kBlock, 0, st>>>(
-                                      cu, cv, cw, n, s.comp, nu, nv, nw, s.cnt, s.bw));
+            int32_t *nru = which ? s.rub : s.rua, *nrv = which ? s.rvb : s.rva;
+            int32_t *nu = which ? s.ub : s.ua, *nv = which ? s.vb : s.va;
+            int64_t *nw = which ? s.wb : s.wa;
+            CU_TRY(c, cudaMemsetAsync(s.cnt, 0, sizeof(unsigned long long), st));
+            TK(c, "k_filter_bid", k_r_filter_bid<<<grid_for(n, kBlock, 65536), kBlock, 0, st>>>(
+                                      cru, crv, cu, cv, cw, n, s.comp, nru, nrv, nu, nv, nw, s.cnt, s.bw));
             DG_TRY(read_counters(c, (const int64_t *)s.cnt, 1, &live));
             if (live == 0) break;
+            cru = nru;
+            crv = nrv;
+            cu = nu;
+            cv = nv;
+            cw = nw;
+            which ^= 1;
         }
-        TK(c, "k_bid_uv", k_bid_uv<<<grid_for(live, kBlock, 65536), kBlock, 0, st>>>(nu, nv, nw, live, s.comp, s.bw, s.buv));
-        TK(c, "k_hook", k_hook<<<gE, kBlock, 0, st>>>(E, s.comp, s.bw, s.buv, s.par, s.tu, s.tv, s.tw, s.cnt + 1));
+        n = live;
+        TK(c, "k_bid_uv", k_r_bid_uv<<<grid_for(n, kBlock, 65536), kBlock, 0, st>>>(cru, crv, cu, cv, cw, n, s.comp,
+                                                                                  s.bw, s.buv));
+        TK(c, "k_hook", k_r_hook<<<gE, kBlock, 0, st>>>(E, s.comp, g.rank_of, s.bw, s.buv, s.par, s.tu, s.tv,
+                                                        s.tru, s.trv, s.tw, s.cnt + 1));
         TK(c, "k_jump", k_jump<<<gE, kBlock, 0, st>>>(E, s.comp, s.par));
         TK(c, "k_relabel", k_relabel<<<gE, kBlock, 0, st>>>(E, s.comp, s.par, s.bw, s.buv));
         TK(c, "k_reset_best", k_reset_best<<<gE, kBlock, 0, st>>>(E, s.bw, s.buv));
-        cu = nu;
-        cv = nv;
-        cw = nw;
-        n = live;
-        nu = (compacted && nu == s.ua) ? s.ub : s.ua;
-        nv = (compacted && nv == s.va) ? s.vb : s.va;
-        nw = (compacted && nw == s.wa) ? s.wb : s.wa;
-        if (round == 63) return set_err(c, DGEC_ERR_TIMEOUT, "Boruvka did not finish in 64 rounds");
     }
     int64_t m;
     DG_TRY(read_counters(c, (const int64_t *)(s.cnt + 1), 1, &m));
     o.n = m;
     if (m == 0) return DGEC_OK;
-    // sort by (u, v) then stably by w
+    // order by (w, u, v): stable radix by the packed original ends, then by w,
+    // carrying the edge index; then gather every column
     int gm = grid_for(m, kBlock, 65536);
-    TK(c, "k_pack_uv", k_pack_uv<<<gm, kBlock, 0, st>>>(s.tu, s.tv, s.tw, m, p.idbits, s.k1, s.v1));
+    TK(c, "k_pack_uv", k_pack_uv_idx<<<gm, kBlock, 0, st>>>(s.tu, s.tv, m, p.idbits, s.k1, s.v1));
     bool in_b;
     DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, s.v1, s.v2}, m, 0, 2 * p.idbits, s.radix, &in_b));
-    unsigned long long *uv = in_b ? s.k2 : s.k1, *ws_ = in_b ? s.v2 : s.v1;
-    unsigned long long *uvo = in_b ? s.k1 : s.k2, *wso = in_b ? s.v1 : s.v2;
+    unsigned long long *idx = in_b ? s.v2 : s.v1;
+    unsigned long long *kw = in_b ? s.k1 : s.k2, *vw = in_b ? s.v1 : s.v2;  // the free pair
+    TK(c, "k_gather_w", k_gather_w<<<gm, kBlock, 0, st>>>(s.tw, idx, m, kw, vw));
     int wbits = p.tbits > 0 ? p.tbits : 1;
-    DG_TRY(radix_sort(c, RadixBuffers{ws_, wso, uv, uvo}, m, 0, wbits, s.radix, &in_b));
-    unsigned long long *wk = in_b ? wso : ws_, *uvk = in_b ? uvo : uv;
-    TK(c, "k_unpack_msf", k_unpack_msf<<<gm, kBlock, 0, st>>>(wk, uvk, m, p.idbits, o.u, o.v, o.w));
+    DG_TRY(radix_sort(c, RadixBuffers{kw, in_b ? s.k2 : s.k1, vw, idx}, m, 0, wbits, s.radix, &in_b));
+    unsigned long long *fin = in_b ? idx : vw;
+    TK(c, "k_gather_msf", k_gather_msf<<<gm, kBlock, 0, st>>>(fin, m, s.tu, s.tv, s.tru, s.trv, s.tw, o.u, o.v,
+                                                              o.ru, o.rv, o.w));
     return DGEC_OK;
 }
 

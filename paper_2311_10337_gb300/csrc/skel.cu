@@ -42,10 +42,11 @@ __device__ __forceinline__ int64_t lower_bound_t(const int64_t *a, int64_t n, in
 
 // brank[e] = #in-edges of src[e] with t <= t_e; arank[e] = #out-edges of
 // dst[e] with t < t_e (computed in k_ranks_knn below).
+// All node ids below are internal ids r (see the stage A notes).
 struct SkView {
-    const int32_t *src, *dst;
+    const int32_t *src, *dst;  // isrc, idst (by r)
     const int64_t *out_off, *in_off;
-    const int32_t *out_id, *in_id, *slot_out;
+    const int32_t *out_id, *in_id, *slot_out;  // out_r, in_r, slot_out (by r)
     const int32_t *brank, *arank;
 };
 
@@ -66,6 +67,7 @@ __device__ __forceinline__ bool emitted_at(const SkView &g, int x, int pin, int 
 // link (-1 if none), wgt the P3 weight.
 __global__ void k_links(SkView g, const int64_t *t, const int64_t *out_t, const int64_t *in_t,
                         int64_t E, int32_t *part, int64_t *wgt, int *flag) {
+    // e below is an internal id r; t, src, dst are the r-ordered copies
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
          e += (int64_t)gridDim.x * blockDim.x) {
         int i = g.src[e], j = g.dst[e];
@@ -115,15 +117,18 @@ __global__ void k_links(SkView g, const int64_t *t, const int64_t *out_t, const 
 }
 
 __global__ void k_compact_links(const int32_t *part, const int64_t *wgt, const int *flag,
-                                const long long *pos, int64_t E, int32_t *u, int32_t *v,
-                                int64_t *w) {
+                                const long long *pos, int64_t E, const int32_t *orig_of, int32_t *ru,
+                                int32_t *rv, int32_t *u, int32_t *v, int64_t *w) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < 2 * E;
          x += (int64_t)gridDim.x * blockDim.x) {
         if (!flag[x]) continue;
         int self = (int)(x < E ? x : x - E), o = part[x];
         int64_t at = pos[x];
-        u[at] = self < o ? self : o;
-        v[at] = self < o ? o : self;
+        int es = orig_of[self], eo = orig_of[o];
+        ru[at] = self;
+        rv[at] = o;
+        u[at] = es < eo ? es : eo;
+        v[at] = es < eo ? eo : es;
         w[at] = wgt[x];
     }
 }
@@ -153,22 +158,26 @@ __device__ __forceinline__ bool cand_less(const Cand &a, const Cand &b) {
 // kernel computes both and stores the ranks for the link pass.
 template <int K>
 __global__ void __launch_bounds__(128) k_ranks_knn(const int32_t *src, const int32_t *dst,
-                                                   const int64_t *t, int64_t E, const int64_t *out_off,
-                                                   const int64_t *out_t, const int32_t *out_id,
-                                                   const int64_t *in_off, const int64_t *in_t,
-                                                   const int32_t *in_id, int32_t *brank, int32_t *arank,
-                                                   int k, int32_t *knn, int64_t *core) {
+                                                   const int64_t *t, const int32_t *orig_of, int64_t E,
+                                                   const int64_t *out_off, const int64_t *out_t,
+                                                   const int32_t *out_id, const int64_t *in_off,
+                                                   const int64_t *in_t, const int32_t *in_id,
+                                                   int32_t *brank, int32_t *arank, int k, int32_t *knn,
+                                                   int64_t *core) {
     constexpr int N = 2 * K;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int i = src[e], j = dst[e];
-        long long te = t[e];
+    // r runs over internal ids (src, dst, t are the r-ordered copies); the
+    // neighbour lists are written under the original id, with original ids
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < E;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int i = src[r], j = dst[r];
+        long long te = t[r];
+        const int64_t e = orig_of[r];
         int64_t ib = in_off[i];
         int64_t ob = out_off[j], nout = out_off[j + 1] - ob;
         int64_t b = upper_bound_t(in_t + ib, in_off[i + 1] - ib, te);
         int64_t a = lower_bound_t(out_t + ob, nout, te);
-        brank[e] = (int32_t)b;
-        arank[e] = (int32_t)a;
+        brank[r] = (int32_t)b;
+        arank[r] = (int32_t)a;
         Cand c[N];
         // predecessor window
         int64_t lo = b - K > 0 ? b - K : 0;
@@ -246,6 +255,8 @@ void plan_skel(Arena &ws, const Problem &p, Skel &o) {
     o.arank = ws.take<int32_t>(p.E);
     o.u = ws.take<int32_t>(2 * p.E);
     o.v = ws.take<int32_t>(2 * p.E);
+    o.ru = ws.take<int32_t>(2 * p.E);
+    o.rv = ws.take<int32_t>(2 * p.E);
     o.w = ws.take<int64_t>(2 * p.E);
     o.knn = ws.take<int32_t>(p.E * (int64_t)p.k);
     o.core = ws.take<int64_t>(p.E);
@@ -282,20 +293,20 @@ dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void
     SkScratch s = carve_skel(a, p);
     int64_t E = p.E;
     int grid = grid_for(E, 128, 1 << 20);
-#define KNN_ARGS                                                                              \
-    p.src, p.dst, p.t, E, g.out_off, g.out_t, g.out_id, g.in_off, g.in_t, g.in_id, o.brank, \
-        o.arank, p.k, o.knn, o.core
+#define KNN_ARGS                                                                           \
+    g.isrc, g.idst, g.it, g.orig_of, E, g.out_off, g.out_t, g.out_id, g.in_off, g.in_t, g.in_id, \
+        o.brank, o.arank, p.k, o.knn, o.core
     if (p.k <= 4) TK(c, "k_ranks_knn", k_ranks_knn<4><<<grid, 128, 0, st>>>(KNN_ARGS));
     else if (p.k <= 8) TK(c, "k_ranks_knn", k_ranks_knn<8><<<grid, 128, 0, st>>>(KNN_ARGS));
     else TK(c, "k_ranks_knn", k_ranks_knn<16><<<grid, 128, 0, st>>>(KNN_ARGS));
 #undef KNN_ARGS
-    SkView v{p.src, p.dst, g.out_off, g.in_off, g.out_id, g.in_id, g.slot_out, o.brank, o.arank};
-    TK(c, "k_links", k_links<<<grid_for(E, kBlock, 65536), kBlock, 0, st>>>(v, p.t, g.out_t, g.in_t, E, s.part, s.wgt,
-                                                          s.flag));
+    SkView v{g.isrc, g.idst, g.out_off, g.in_off, g.out_r, g.in_r, g.slot_out, o.brank, o.arank};
+    TK(c, "k_links", k_links<<<grid_for(E, kBlock, 65536), kBlock, 0, st>>>(v, g.it, g.out_t, g.in_t, E, s.part,
+                                                                          s.wgt, s.flag));
     TK(c, "k_zero_i32", k_zero_i32<<<1, 1, 0, st>>>(s.flag + 2 * E));
     DG_TRY(exclusive_scan_i32(c, s.flag, s.pos, 2 * E + 1, s.scan_tmp));
-    TK(c, "k_compact_links", k_compact_links<<<grid_for(2 * E, kBlock, 65536), kBlock, 0, st>>>(s.part, s.wgt, s.flag, s.pos, E,
-                                                                      o.u, o.v, o.w));
+    TK(c, "k_compact_links", k_compact_links<<<grid_for(2 * E, kBlock, 65536), kBlock, 0, st>>>(
+                                 s.part, s.wgt, s.flag, s.pos, E, g.orig_of, o.ru, o.rv, o.u, o.v, o.w));
     int64_t n;
     DG_TRY(read_counters(c, (const int64_t *)(s.pos + 2 * E), 1, &n));
     o.n = n;

@@ -17,13 +17,24 @@ struct Problem {
 };
 
 // Stage A: incidence lists (Alg. 3 first line), per-vertex lists sorted by
-// (t, id), plus each edge's slot in its source's out-list and in its
-// destination's in-list.
+// (t, id).
+//
+// Internal numbering: every later stage names a line-graph node (a temporal
+// edge) by r = its rank in (t, id) order. Skeleton links join edges that are
+// close in time, so under r their two ends sit close in memory and the
+// label/best-edge arrays of the forest and dendrogram stages are read with
+// locality instead of at random. Original ids stay in every output and in
+// every tie-break key.
 struct Csr {
     int64_t *out_off, *in_off;  // [V+1]
     int64_t *out_t, *in_t;      // [E]
-    int32_t *out_id, *in_id;    // [E]
-    int32_t *slot_out, *slot_in;  // [E] global slot of edge e in out_id / in_id
+    int32_t *out_id, *in_id;    // [E] original ids (outputs)
+    int32_t *out_r, *in_r;      // [E] internal ids of the same entries
+    int32_t *orig_of;           // [E] r -> original id
+    int32_t *rank_of;           // [E] original id -> r
+    int32_t *isrc, *idst;       // [E] src, dst in r order
+    int64_t *it;                // [E] t in r order
+    int32_t *slot_out;          // [E] by r: global slot in the out-lists
 };
 void plan_csr(Arena &ws, const Problem &p, Csr &o);
 size_t csr_scratch_bytes(const Problem &p);
@@ -32,8 +43,9 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch);
 // Stage B: skeleton (Alg. 2 as rank arithmetic + Alg. 3 union) and the
 // k-nearest-in-time neighbours.
 struct Skel {
-    int32_t *brank, *arank;  // [E] ranks from the per-vertex merges
-    int32_t *u, *v;          // [2E] capacity
+    int32_t *brank, *arank;  // [E] by r: ranks from the per-vertex merges
+    int32_t *u, *v;          // [2E] capacity; original ids, u < v (output)
+    int32_t *ru, *rv;        // [2E] the same links in internal ids
     int64_t *w;
     int64_t n = 0;
     int32_t *knn;  // [E*k]
@@ -47,13 +59,14 @@ dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void
 // Stage C: minimum spanning forest of the skeleton (Borůvka), sorted by
 // (w, u, v).
 struct Msf {
-    int32_t *u, *v;  // [E]
+    int32_t *u, *v;    // [E] original ids (output)
+    int32_t *ru, *rv;  // [E] internal ids of the same edges
     int64_t *w;
     int64_t n = 0;
 };
 void plan_msf(Arena &ws, const Problem &p, Msf &o);
 size_t msf_scratch_bytes(const Problem &p);
-dgec_status stage_msf(Ctx *c, const Problem &p, const Skel &s, Msf &o, void *scratch);
+dgec_status stage_msf(Ctx *c, const Problem &p, const Csr &g, const Skel &s, Msf &o, void *scratch);
 
 // Stage D1: single-linkage dendrogram of the sorted forest.
 struct Dendro {
@@ -64,7 +77,7 @@ struct Dendro {
 };
 void plan_dendro(Arena &ws, const Problem &p, Dendro &o);
 size_t dendro_scratch_bytes(const Problem &p);
-dgec_status stage_dendro(Ctx *c, const Problem &p, const Msf &m, Dendro &o, void *scratch);
+dgec_status stage_dendro(Ctx *c, const Problem &p, const Csr &g, const Msf &m, Dendro &o, void *scratch);
 
 // Stage D2: condensed tree, excess-of-mass selection and labels.
 struct Condensed {
