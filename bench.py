@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--cpu-sample-minutes", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch-graphs", type=int, default=128,
+                    help="graphs in the batched-vs-plain comparison (0 = skip)")
     ap.add_argument("--breakdown", action="store_true",
                     help="also time every kernel in one extra (untimed) step")
     return ap.parse_args()
@@ -134,6 +136,43 @@ class Clocks:
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def batched_vs_plain(ctx, n_graphs, steps):
+    """Aggregate edges/s of one batched run over n_graphs independent graphs
+    (the batching workload's distribution) against one run per graph, on
+    the same GPU, same graphs, identical output."""
+    import torch
+    from paper_2311_10337_gb300 import synth
+    b = synth.batch(n_graphs)
+    total = int(b.edge_off[-1])
+    s = torch.from_numpy(b.src).cuda()
+    d = torch.from_numpy(b.dst).cuda()
+    t = torch.from_numpy(b.t).cuda()
+    out = ctx.run_batch(s, d, t, b.edge_off, b.n_vertices, b.k, b.min_cluster_size)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        out = ctx.run_batch(s, d, t, b.edge_off, b.n_vertices, b.k, b.min_cluster_size)
+    torch.cuda.synchronize()
+    tb = (time.perf_counter() - t0) / steps
+    labels_b = out.numpy("labels")
+    # one launch sequence per graph, inputs already resident
+    views = [(s[int(b.edge_off[g]):int(b.edge_off[g + 1])], d[int(b.edge_off[g]):int(b.edge_off[g + 1])],
+              t[int(b.edge_off[g]):int(b.edge_off[g + 1])]) for g in range(b.n_graphs)]
+    labels_p = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for g in range(b.n_graphs):
+        o = ctx.run(*views[g], int(b.n_vertices[g]), int(b.k[g]), int(b.min_cluster_size[g]))
+        labels_p.append(o.tensor("labels").clone())
+    torch.cuda.synchronize()
+    tp = time.perf_counter() - t0
+    same = bool(np.array_equal(labels_b, torch.cat(labels_p).cpu().numpy()))
+    return {"graphs": b.n_graphs, "edges": total, "recipe": b.recipe,
+            "batched_edges_per_s": total / tb, "batched_ms": 1000 * tb,
+            "one_run_per_graph_edges_per_s": total / tp, "one_run_per_graph_ms": 1000 * tp,
+            "speedup": tp / tb, "identical_labels": same}
 
 
 def peaks():
@@ -242,6 +281,9 @@ def main():
             e2e_s = float(tm.item())
         e2e = {"value": world * E / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * E,
                "d2h_bytes_per_step": 4 * E}
+    batch = None
+    if args.batch_graphs > 0 and rank == 0:
+        batch = batched_vs_plain(ctx, args.batch_graphs, max(1, min(args.steps, 3)))
     if rank == 0:
         peak, peak_kind = peaks()
         dom_ms, dom_n = dom
@@ -266,7 +308,7 @@ def main():
                            "edges_per_gpu": E, "parallelism": "replicas only",
                            "l2": "inputs (16 B/edge = %.0f MB) exceed L2; no flush" % (16 * E / 1e6),
                            "n_clusters": n_clusters},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "batch": batch,
                 "gpu_launches": launches * args.steps, "clocks": clk}
         if args.breakdown:
             line["kernel_breakdown_ms"] = {n: [round(v[0], 3), v[1]] for n, v in

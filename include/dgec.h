@@ -145,6 +145,51 @@ dgec_status dgec_run_host(dgec_ctx *ctx, const int32_t *h_src,
                           size_t ws_bytes, void *cuda_stream,
                           int32_t *h_labels, int32_t *h_n_clusters);
 
+/*
+ * Batched form: many independent graphs in one pass of the pipeline (the
+ * the benchmark spec's batching pattern; the paper's method per graph is
+ * unchanged, Alg. 4 runs on each graph as if alone). Graph g owns the
+ * input edges [h_edge_off[g], h_edge_off[g+1]) of d_src/d_dst/d_t, with
+ * vertex ids local to the graph in [0, h_n_vertices[g]), its own k and
+ * min cluster size, and its own virtual root. Every result equals the
+ * result of dgec_run on that graph alone.
+ */
+typedef struct {
+    /* per-edge outputs, graph after graph, in each graph's local ids */
+    const int32_t *labels;     /* [total_edges]: -1 noise, else 0..n_clusters[g]-1 */
+    const int32_t *knn_id;     /* graph g's rows start at knn_off[g]; k_g local ids per edge */
+    const int64_t *core;       /* [total_edges] */
+    /* forest and dendrogram rows of graph g: [mst_off[g], mst_off[g+1]),
+     * (w, u, v) order, local ids; a dendrogram child >= E_g is E_g + the
+     * local row that formed it */
+    const int32_t *mst_u, *mst_v;
+    const int64_t *mst_w;
+    const int32_t *link_a, *link_b;
+    const int64_t *link_size;
+    /* per-graph device tables */
+    const int32_t *n_clusters;  /* [n_graphs] */
+    const int64_t *mst_off;     /* [n_graphs + 1] */
+    const int64_t *knn_off;     /* [n_graphs + 1] */
+    int64_t total_edges, total_mst;
+    int32_t total_clusters;
+    /* the whole batch as one dgec_result in global ids (edge id = position
+     * in the batch, vertex id = local id + the vertex counts of earlier
+     * graphs); its condensed-tree arrays carry one virtual root per graph */
+    dgec_result global;
+} dgec_batch_result;
+
+/* Workspace bytes for a batch; the tables are host arrays. */
+dgec_status dgec_batch_workspace_size(int32_t n_graphs, const int64_t *h_edge_off,
+                                      const int32_t *h_n_vertices, const int32_t *h_k,
+                                      const int32_t *h_min_cluster_size, size_t *bytes);
+/* Runs the batch; h_edge_off[0] must be 0; limits and errors as dgec_run
+ * (total edges < 2^30, total vertices < 2^31). */
+dgec_status dgec_run_batch(dgec_ctx *ctx, int32_t n_graphs, const int64_t *h_edge_off,
+                           const int32_t *h_n_vertices, const int32_t *h_k,
+                           const int32_t *h_min_cluster_size, const int32_t *d_src,
+                           const int32_t *d_dst, const int64_t *d_t, void *d_workspace,
+                           size_t ws_bytes, void *cuda_stream, dgec_batch_result *out);
+
 /* Number of kernel launches the last dgec_run on ctx issued (for reporting). */
 int64_t dgec_last_launch_count(const dgec_ctx *ctx);
 

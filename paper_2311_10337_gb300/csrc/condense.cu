@@ -30,13 +30,30 @@ namespace dgec {
 
 typedef unsigned __int128 u128;
 
-__device__ __forceinline__ unsigned long long lam_node(int64_t X, int64_t R, int64_t E,
-                                                       const int64_t *w) {
-    return X == R ? 0ull : lambda_of(w[X - E]);
+// Node ids: leaves [0, E), merges E + s, and one virtual root per graph at
+// R0 + g (R0 = E + number of merges).
+struct Gview {
+    int64_t E, n, R0;
+    int G;
+    const int32_t *egraph;  // graph of each leaf
+    const int32_t *mu;      // original lower end of each merge's forest edge
+    const int64_t *eoff;    // [G+1]
+    const int32_t *gM;      // [G] min cluster size per graph
+};
+
+__device__ __forceinline__ int graph_of(const Gview &g, int64_t x) {
+    return x < g.E ? g.egraph[x] : (x < g.R0 ? g.egraph[g.mu[x - g.E]] : (int)(x - g.R0));
 }
 
-__device__ __forceinline__ int64_t node_size(int64_t X, int64_t R, int64_t E, const int64_t *size) {
-    return X == R ? E : (X < E ? 1 : size[X - E]);
+__device__ __forceinline__ unsigned long long lam_node(int64_t X, const Gview &g, const int64_t *w) {
+    return X >= g.R0 ? 0ull : lambda_of(w[X - g.E]);
+}
+
+__device__ __forceinline__ int64_t node_size(int64_t X, const Gview &g, const int64_t *size) {
+    if (X < g.E) return 1;
+    if (X < g.R0) return size[X - g.E];
+    int gr = (int)(X - g.R0);
+    return g.eoff[gr + 1] - g.eoff[gr];
 }
 
 __global__ void k_c_up(int64_t E, int64_t n, const int32_t *parent, const int64_t *w, int32_t *up,
@@ -69,68 +86,67 @@ __global__ void k_c_top(int64_t n, int32_t *up) {
 }
 
 // collapsed parent of every leaf and kept merge; nbig counts big children
-__global__ void k_c_cpar(int64_t E, int64_t n, int32_t M, const int32_t *parent, const int32_t *up,
-                         const int *isrep, const int64_t *size, int32_t *cpar, int *nbig) {
-    const int64_t R = E + n;
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < E + n;
+__global__ void k_c_cpar(Gview gv, const int32_t *parent, const int32_t *up, const int *isrep,
+                         const int64_t *size, int32_t *cpar, int *nbig) {
+    const int64_t E = gv.E;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < E + gv.n;
          x += (int64_t)gridDim.x * blockDim.x) {
         if (x >= E && !isrep[x - E]) continue;
         int P = parent[x];
-        int64_t cp = P < 0 ? R : E + up[P - E];
+        int64_t cp = P < 0 ? gv.R0 + graph_of(gv, x) : E + up[P - E];
         cpar[x] = (int32_t)cp;
-        if (x >= E && size[x - E] >= M) atomicAdd(&nbig[cp], 1);
+        if (x >= E && size[x - E] >= gv.gM[graph_of(gv, x)]) atomicAdd(&nbig[cp], 1);
     }
 }
 
 // link: a big kept merge continues its parent's cluster when it is the
-// parent's only big child, else it starts a cluster (link to itself).
-__global__ void k_c_link(int64_t E, int64_t n, int32_t M, const int *isrep, const int64_t *size,
-                         const int32_t *cpar, const int *nbig, int32_t *link) {
-    const int64_t R = E + n;
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s <= n;
+// parent's only big child, else it starts a cluster (link to itself);
+// virtual roots link to themselves.
+__global__ void k_c_link(Gview gv, const int *isrep, const int64_t *size, const int32_t *cpar,
+                         const int *nbig, int32_t *link) {
+    const int64_t E = gv.E, n = gv.n;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n + gv.G;
          s += (int64_t)gridDim.x * blockDim.x) {
-        if (s == n) {
-            link[R] = (int32_t)R;
+        if (s >= n) {
+            link[E + s] = (int32_t)(E + s);
             continue;
         }
-        if (!isrep[s] || size[s] < M) continue;
+        if (!isrep[s] || size[s] < gv.gM[graph_of(gv, E + s)]) continue;
         int64_t X = cpar[E + s];
         link[E + s] = nbig[X] >= 2 ? (int32_t)(E + s) : (int32_t)X;
     }
 }
 
-__global__ void k_c_cl(int64_t E, int64_t n, int32_t M, const int *isrep, const int64_t *size,
-                       int32_t *link) {
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+__global__ void k_c_cl(Gview gv, const int *isrep, const int64_t *size, int32_t *link) {
+    const int64_t E = gv.E;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < gv.n;
          s += (int64_t)gridDim.x * blockDim.x) {
-        if (!isrep[s] || size[s] < M) continue;
+        if (!isrep[s] || size[s] < gv.gM[graph_of(gv, E + s)]) continue;
         walk_to_fixed(link, (int)(E + s));
     }
 }
 
 // cluster records, indexed by node id
-__global__ void k_c_clusters(int64_t E, int64_t n, int32_t M, const int *isrep, const int64_t *size,
-                             const int64_t *w, const int32_t *cpar, const int *nbig,
-                             const int32_t *link, int *isc, unsigned long long *cbirth,
-                             unsigned long long *cdeath, int32_t *cparent) {
-    const int64_t R = E + n;
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s <= n;
+__global__ void k_c_clusters(Gview gv, const int *isrep, const int64_t *size, const int64_t *w,
+                             const int32_t *cpar, const int *nbig, const int32_t *link, int *isc,
+                             unsigned long long *cbirth, unsigned long long *cdeath,
+                             int32_t *cparent) {
+    const int64_t E = gv.E, n = gv.n;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n + gv.G;
          s += (int64_t)gridDim.x * blockDim.x) {
         int64_t X = E + s;
-        bool big;
-        if (s == n) big = true;  // the virtual root
-        else big = isrep[s] && size[s] >= M;
+        bool big = s >= n || (isrep[s] && size[s] >= gv.gM[graph_of(gv, X)]);
         if (!big) continue;
         int K = link[X];
-        if (nbig[X] >= 2) cdeath[K] = lam_node(X, R, E, w);
+        if (nbig[X] >= 2) cdeath[K] = lam_node(X, gv, w);
         if (K == (int)X) {
             isc[X] = 1;
-            if (X == R) {
+            if (X >= gv.R0) {
                 cbirth[X] = 0;
                 cparent[X] = -1;
             } else {
                 int64_t P = cpar[X];
-                cbirth[X] = lam_node(P, R, E, w);
+                cbirth[X] = lam_node(P, gv, w);
                 cparent[X] = link[P];
             }
         }
@@ -138,17 +154,18 @@ __global__ void k_c_clusters(int64_t E, int64_t n, int32_t M, const int *isrep, 
 }
 
 // where each point leaves: the lowest kept ancestor of size >= M
-__global__ void k_c_points(int64_t E, int64_t n, int32_t M, const int32_t *cpar, const int64_t *size,
-                           const int64_t *w, const int32_t *link, const unsigned long long *cbirth,
-                           int32_t *fall_cluster, uint64_t *fall_lambda,
-                           unsigned long long *st_hi, unsigned long long *st_lo) {
-    const int64_t R = E + n;
+__global__ void k_c_points(Gview gv, const int32_t *cpar, const int64_t *size, const int64_t *w,
+                           const int32_t *link, const unsigned long long *cbirth,
+                           int32_t *fall_cluster, uint64_t *fall_lambda, unsigned long long *st_hi,
+                           unsigned long long *st_lo) {
+    const int64_t E = gv.E;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < E;
          p += (int64_t)gridDim.x * blockDim.x) {
+        const int M = gv.gM[gv.egraph[p]];
         int64_t X = cpar[p];
-        for (int it = 0; it < kMaxWalk && X != R && size[X - E] < M; it++) X = cpar[X];
+        for (int it = 0; it < kMaxWalk && X < gv.R0 && size[X - E] < M; it++) X = cpar[X];
         int K = link[X];
-        unsigned long long L = lam_node(X, R, E, w);
+        unsigned long long L = lam_node(X, gv, w);
         fall_cluster[p] = K;
         fall_lambda[p] = L;
         atomic_add_u128(&st_hi[K], &st_lo[K], 0ull, L - cbirth[K]);
@@ -156,16 +173,16 @@ __global__ void k_c_points(int64_t E, int64_t n, int32_t M, const int32_t *cpar,
 }
 
 // a child cluster's points leave the parent at the parent's death
-__global__ void k_c_child_stab(int64_t N, const int *isc, const int32_t *cparent,
-                               const int64_t *size, int64_t E, int64_t R,
-                               const unsigned long long *cbirth, const unsigned long long *cdeath,
-                               unsigned long long *st_hi, unsigned long long *st_lo) {
+__global__ void k_c_child_stab(int64_t N, Gview gv, const int *isc, const int32_t *cparent,
+                               const int64_t *size, const unsigned long long *cbirth,
+                               const unsigned long long *cdeath, unsigned long long *st_hi,
+                               unsigned long long *st_lo) {
     for (int64_t K = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; K < N;
          K += (int64_t)gridDim.x * blockDim.x) {
-        if (!isc[K] || K == R) continue;
+        if (!isc[K] || K >= gv.R0) continue;
         int P = cparent[K];
         unsigned long long span = cdeath[P] - cbirth[P];
-        unsigned long long sz = (unsigned long long)size[K - E];
+        unsigned long long sz = (unsigned long long)size[K - gv.E];
         unsigned long long lo = sz * span, hi = __umul64hi(sz, span);
         atomic_add_u128(&st_hi[P], &st_lo[P], hi, lo);
     }
@@ -184,7 +201,7 @@ __global__ void k_c_compact(int64_t N, const int *isc, const long long *cpos, in
 
 struct Eom {
     int64_t ncl;
-    int rootc;
+    int64_t R0;  // node ids >= R0 are virtual roots (never selected)
     const int32_t *clist, *cidx, *cparent;  // cparent by node id
     int32_t *par;                            // compact parent, -1 root
     int *pending, *done, *state;             // state: 1 done this phase
@@ -354,7 +371,7 @@ __global__ void k_e_childsum2(Eom e) {
 __global__ void k_e_select(Eom e, int32_t *H, int32_t *J) {
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < e.ncl;
          c += (int64_t)gridDim.x * blockDim.x) {
-        bool sel = (c != e.rootc) && e.stab[c] >= acc_of(e, c);
+        bool sel = (e.clist[c] < e.R0) && e.stab[c] >= acc_of(e, c);
         H[c] = sel ? (int32_t)c : -1;
         J[c] = e.par[c];
     }
@@ -406,10 +423,26 @@ __global__ void k_e_final_emit(int64_t ncl, const int *flag, const long long *po
     }
 }
 
-__global__ void k_e_rank(int64_t nf, const unsigned long long *v, int32_t *rank) {
+// Final clusters sorted by smallest member (a global edge id, so graphs
+// come in order); a cluster's label is its position within its graph.
+__global__ void k_e_gstart(int64_t nf, const unsigned long long *key, const int32_t *egraph,
+                           int64_t *gstart, int32_t *gcount) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nf;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        int g = egraph[key[x]];
+        if (x == 0 || egraph[key[x - 1]] != g) gstart[g] = x;
+        if (x == nf - 1 || egraph[key[x + 1]] != g) gcount[g] = (int32_t)(x + 1);  // end, fixed below
+    }
+}
+__global__ void k_e_gcount(int G, const int64_t *gstart, int32_t *gcount) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x)
+        if (gcount[g] > 0) gcount[g] -= (int32_t)gstart[g];
+}
+__global__ void k_e_rank(int64_t nf, const unsigned long long *key, const unsigned long long *v,
+                         const int32_t *egraph, const int64_t *gstart, int32_t *rank) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nf;
          x += (int64_t)gridDim.x * blockDim.x)
-        rank[v[x]] = (int32_t)x;
+        rank[v[x]] = (int32_t)(x - gstart[egraph[key[x]]]);
 }
 
 __global__ void k_e_relabel(int64_t E, const int32_t *rank, int32_t *lab) {
@@ -420,11 +453,10 @@ __global__ void k_e_relabel(int64_t E, const int32_t *rank, int32_t *lab) {
     }
 }
 
-__global__ void k_e_out(Eom e, int64_t E, const int64_t *size, int64_t R,
-                        const unsigned long long *cbirth, const unsigned long long *cdeath,
-                        const int32_t *H, int32_t *cl_id, int32_t *cl_parent, uint64_t *cl_birth,
-                        uint64_t *cl_death, int64_t *cl_size, uint64_t *cl_hi, uint64_t *cl_lo,
-                        int32_t *cl_sel) {
+__global__ void k_e_out(Eom e, Gview gv, const int64_t *size, const unsigned long long *cbirth,
+                        const unsigned long long *cdeath, const int32_t *H, int32_t *cl_id,
+                        int32_t *cl_parent, uint64_t *cl_birth, uint64_t *cl_death, int64_t *cl_size,
+                        uint64_t *cl_hi, uint64_t *cl_lo, int32_t *cl_sel) {
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < e.ncl;
          c += (int64_t)gridDim.x * blockDim.x) {
         int node = e.clist[c];
@@ -432,10 +464,10 @@ __global__ void k_e_out(Eom e, int64_t E, const int64_t *size, int64_t R,
         cl_parent[c] = e.cparent[node];
         cl_birth[c] = cbirth[node];
         cl_death[c] = cdeath[node];
-        cl_size[c] = node == R ? E : size[node - E];
+        cl_size[c] = node_size(node, gv, size);
         cl_hi[c] = (uint64_t)(e.stab[c] >> 64);
         cl_lo[c] = (uint64_t)e.stab[c];
-        bool sel = (c != e.rootc) && e.stab[c] >= acc_of(e, c);
+        bool sel = (node < e.R0) && e.stab[c] >= acc_of(e, c);
         cl_sel[c] = !sel ? 0 : (H[c] == (int32_t)c ? 2 : 1);
     }
 }
@@ -444,15 +476,17 @@ void plan_condensed(Arena &ws, const Problem &p, Condensed &o) {
     int64_t E = p.E;
     o.fall_cluster = ws.take<int32_t>(E);
     o.fall_lambda = ws.take<uint64_t>(E);
-    o.cl_id = ws.take<int32_t>(E + 1);
-    o.cl_parent = ws.take<int32_t>(E + 1);
-    o.cl_birth = ws.take<uint64_t>(E + 1);
-    o.cl_death = ws.take<uint64_t>(E + 1);
-    o.cl_stab_hi = ws.take<uint64_t>(E + 1);
-    o.cl_stab_lo = ws.take<uint64_t>(E + 1);
-    o.cl_size = ws.take<int64_t>(E + 1);
-    o.cl_selected = ws.take<int32_t>(E + 1);
+    const int64_t C = E + p.G;  // clusters: at most one per merge plus the virtual roots
+    o.cl_id = ws.take<int32_t>(C);
+    o.cl_parent = ws.take<int32_t>(C);
+    o.cl_birth = ws.take<uint64_t>(C);
+    o.cl_death = ws.take<uint64_t>(C);
+    o.cl_stab_hi = ws.take<uint64_t>(C);
+    o.cl_stab_lo = ws.take<uint64_t>(C);
+    o.cl_size = ws.take<int64_t>(C);
+    o.cl_selected = ws.take<int32_t>(C);
     o.labels = ws.take<int32_t>(E);
+    o.gclusters = ws.take<int32_t>(p.G);
 }
 
 struct CScratch {
@@ -461,12 +495,13 @@ struct CScratch {
     int *isrep, *nbig, *isc, *pending, *done, *state, *minmem, *flag;
     unsigned long long *cbirth, *cdeath, *st_hi, *st_lo, *acc_hi, *acc_lo, *cnt, *k1, *k2, *v1, *v2;
     long long *cpos, *scan_tmp;
+    int64_t *gstart;
     u128 *stab, *S, *Fa, *Fc, *Fa2, *Fc2;
     void *radix;
 };
 static CScratch carve_condense(Arena &a, const Problem &p) {
     CScratch s;
-    int64_t E = p.E, N = 2 * E + 2;  // nodes: leaves, merges, virtual root
+    int64_t E = p.E, N = 2 * E + p.G + 1;  // nodes: leaves, merges, virtual roots
     s.up = a.take<int32_t>(E);
     s.isrep = a.take<int>(E);
     s.cpar = a.take<int32_t>(N);
@@ -480,38 +515,39 @@ static CScratch carve_condense(Arena &a, const Problem &p) {
     s.st_lo = a.take<unsigned long long>(N);
     s.cpos = a.take<long long>(N + 1);
     s.scan_tmp = a.take<long long>(scan_scratch_elems(N + 1));
-    s.clist = a.take<int32_t>(E + 1);
+    s.clist = a.take<int32_t>(E + p.G + 1);
     s.cidx = a.take<int32_t>(N);
-    s.par = a.take<int32_t>(E + 1);
-    s.pending = a.take<int>(E + 1);
-    s.done = a.take<int>(E + 1);
-    s.state = a.take<int>(E + 1);
-    s.ucand = a.take<int32_t>(E + 1);
-    s.nxt = a.take<int32_t>(E + 1);
-    s.nxt2 = a.take<int32_t>(E + 1);
-    s.stab = a.take<u128>(E + 1);
-    s.S = a.take<u128>(E + 1);
-    s.Fa = a.take<u128>(E + 1);
-    s.Fc = a.take<u128>(E + 1);
-    s.Fa2 = a.take<u128>(E + 1);
-    s.Fc2 = a.take<u128>(E + 1);
-    s.acc_hi = a.take<unsigned long long>(E + 1);
-    s.acc_lo = a.take<unsigned long long>(E + 1);
-    s.H = a.take<int32_t>(E + 1);
-    s.J = a.take<int32_t>(E + 1);
-    s.H2 = a.take<int32_t>(E + 1);
-    s.J2 = a.take<int32_t>(E + 1);
-    s.minmem = a.take<int>(E + 1);
-    s.flag = a.take<int>(E + 2);
-    s.rank = a.take<int32_t>(E + 1);
-    s.al1 = a.take<int32_t>(E + 1);
-    s.al2 = a.take<int32_t>(E + 1);
+    s.par = a.take<int32_t>(E + p.G + 1);
+    s.pending = a.take<int>(E + p.G + 1);
+    s.done = a.take<int>(E + p.G + 1);
+    s.state = a.take<int>(E + p.G + 1);
+    s.ucand = a.take<int32_t>(E + p.G + 1);
+    s.nxt = a.take<int32_t>(E + p.G + 1);
+    s.nxt2 = a.take<int32_t>(E + p.G + 1);
+    s.stab = a.take<u128>(E + p.G + 1);
+    s.S = a.take<u128>(E + p.G + 1);
+    s.Fa = a.take<u128>(E + p.G + 1);
+    s.Fc = a.take<u128>(E + p.G + 1);
+    s.Fa2 = a.take<u128>(E + p.G + 1);
+    s.Fc2 = a.take<u128>(E + p.G + 1);
+    s.acc_hi = a.take<unsigned long long>(E + p.G + 1);
+    s.acc_lo = a.take<unsigned long long>(E + p.G + 1);
+    s.H = a.take<int32_t>(E + p.G + 1);
+    s.J = a.take<int32_t>(E + p.G + 1);
+    s.H2 = a.take<int32_t>(E + p.G + 1);
+    s.J2 = a.take<int32_t>(E + p.G + 1);
+    s.minmem = a.take<int>(E + p.G + 1);
+    s.flag = a.take<int>(E + p.G + 2);
+    s.rank = a.take<int32_t>(E + p.G + 1);
+    s.gstart = a.take<int64_t>(p.G + 1);
+    s.al1 = a.take<int32_t>(E + p.G + 1);
+    s.al2 = a.take<int32_t>(E + p.G + 1);
     s.cnt = a.take<unsigned long long>(4);
-    s.k1 = a.take<unsigned long long>(E + 1);
-    s.k2 = a.take<unsigned long long>(E + 1);
-    s.v1 = a.take<unsigned long long>(E + 1);
-    s.v2 = a.take<unsigned long long>(E + 1);
-    s.radix = a.take<char>(radix_scratch_bytes(E + 1));
+    s.k1 = a.take<unsigned long long>(E + p.G + 1);
+    s.k2 = a.take<unsigned long long>(E + p.G + 1);
+    s.v1 = a.take<unsigned long long>(E + p.G + 1);
+    s.v2 = a.take<unsigned long long>(E + p.G + 1);
+    s.radix = a.take<char>(radix_scratch_bytes(E + p.G + 1));
     return s;
 }
 size_t condense_scratch_bytes(const Problem &p) {
@@ -529,14 +565,16 @@ __global__ void k_fill_i32(int *p, int64_t n, int v) {
 dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro &d, Condensed &o,
                            void *scratch) {
     cudaStream_t st = c->stream;
-    int64_t E = p.E, n = m.n, R = E + n, N = E + n + 1;
+    int64_t E = p.E, n = m.n, N = E + n + p.G;
     o.n_cl = 0;
     o.n_clusters = 0;
+    CU_TRY(c, cudaMemsetAsync(o.gclusters, 0, sizeof(int32_t) * p.G, st));
     if (E == 0) return DGEC_OK;
+    Gview gv{E, n, E + n, p.G, p.egraph, m.u, p.eoff, p.gM};
     Arena a(scratch, SIZE_MAX);
     CScratch s = carve_condense(a, p);
     const int gN = grid_for(N, kBlock, 65536), gE = grid_for(E, kBlock, 65536),
-              gn = grid_for(n + 1, kBlock, 65536);
+              gn = grid_for(n + p.G, kBlock, 65536);
     CU_TRY(c, cudaMemsetAsync(s.nbig, 0, sizeof(int) * N, st));
     CU_TRY(c, cudaMemsetAsync(s.isc, 0, sizeof(int) * (N + 1), st));
     CU_TRY(c, cudaMemsetAsync(s.cdeath, 0, sizeof(unsigned long long) * N, st));
@@ -546,15 +584,15 @@ dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro 
         TK(c, "k_c_up", k_c_up<<<gn, kBlock, 0, st>>>(E, n, d.parent, m.w, s.up, s.isrep));
         TK(c, "k_c_top", k_c_top<<<gn, kBlock, 0, st>>>(n, s.up));
     }
-    TK(c, "k_c_cpar", k_c_cpar<<<gN, kBlock, 0, st>>>(E, n, p.M, d.parent, s.up, s.isrep, d.size, s.cpar, s.nbig));
-    TK(c, "k_c_link", k_c_link<<<gn, kBlock, 0, st>>>(E, n, p.M, s.isrep, d.size, s.cpar, s.nbig, s.link));
-    TK(c, "k_c_cl", k_c_cl<<<gn, kBlock, 0, st>>>(E, n, p.M, s.isrep, d.size, s.link));
-    TK(c, "k_c_clusters", k_c_clusters<<<gn, kBlock, 0, st>>>(E, n, p.M, s.isrep, d.size, m.w, s.cpar, s.nbig, s.link, s.isc,
-                                        s.cbirth, s.cdeath, s.cparent));
-    TK(c, "k_c_points", k_c_points<<<gE, kBlock, 0, st>>>(E, n, p.M, s.cpar, d.size, m.w, s.link, s.cbirth, o.fall_cluster,
-                                      o.fall_lambda, s.st_hi, s.st_lo));
-    TK(c, "k_c_child_stab", k_c_child_stab<<<gN, kBlock, 0, st>>>(N, s.isc, s.cparent, d.size, E, R, s.cbirth, s.cdeath, s.st_hi,
-                                          s.st_lo));
+    TK(c, "k_c_cpar", k_c_cpar<<<gN, kBlock, 0, st>>>(gv, d.parent, s.up, s.isrep, d.size, s.cpar, s.nbig));
+    TK(c, "k_c_link", k_c_link<<<gn, kBlock, 0, st>>>(gv, s.isrep, d.size, s.cpar, s.nbig, s.link));
+    TK(c, "k_c_cl", k_c_cl<<<gn, kBlock, 0, st>>>(gv, s.isrep, d.size, s.link));
+    TK(c, "k_c_clusters", k_c_clusters<<<gn, kBlock, 0, st>>>(gv, s.isrep, d.size, m.w, s.cpar, s.nbig, s.link,
+                                                             s.isc, s.cbirth, s.cdeath, s.cparent));
+    TK(c, "k_c_points", k_c_points<<<gE, kBlock, 0, st>>>(gv, s.cpar, d.size, m.w, s.link, s.cbirth,
+                                                         o.fall_cluster, o.fall_lambda, s.st_hi, s.st_lo));
+    TK(c, "k_c_child_stab", k_c_child_stab<<<gN, kBlock, 0, st>>>(N, gv, s.isc, s.cparent, d.size, s.cbirth,
+                                                                 s.cdeath, s.st_hi, s.st_lo));
     DG_TRY(exclusive_scan_i32(c, s.isc, s.cpos, N + 1, s.scan_tmp));
     int64_t ncl;
     DG_TRY(read_counters(c, (const int64_t *)(s.cpos + N), 1, &ncl));
@@ -563,7 +601,7 @@ dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro 
     // ---- excess of mass over the cluster tree
     Eom e;
     e.ncl = ncl;
-    e.rootc = (int)(ncl - 1);  // the root has the largest node id
+    e.R0 = E + n;
     e.clist = s.clist;
     e.cidx = s.cidx;
     e.cparent = s.cparent;
@@ -662,11 +700,14 @@ dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro 
         bool in_b;
         DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, s.v1, s.v2}, nf, 0, p.idbits > 0 ? p.idbits : 1,
                           s.radix, &in_b));
-        unsigned long long *vv = in_b ? s.v2 : s.v1;
-        TK(c, "k_e_rank", k_e_rank<<<grid_for(nf, kBlock, 65536), kBlock, 0, st>>>(nf, vv, s.rank));
+        unsigned long long *kk = in_b ? s.k2 : s.k1, *vv = in_b ? s.v2 : s.v1;
+        const int gf = grid_for(nf, kBlock, 65536);
+        TK(c, "k_e_gstart", k_e_gstart<<<gf, kBlock, 0, st>>>(nf, kk, p.egraph, s.gstart, o.gclusters));
+        TK(c, "k_e_gcount", k_e_gcount<<<grid_for(p.G), kBlock, 0, st>>>(p.G, s.gstart, o.gclusters));
+        TK(c, "k_e_rank", k_e_rank<<<gf, kBlock, 0, st>>>(nf, kk, vv, p.egraph, s.gstart, s.rank));
         TK(c, "k_e_relabel", k_e_relabel<<<gE, kBlock, 0, st>>>(E, s.rank, o.labels));
     }
-    TK(c, "k_e_out", k_e_out<<<gc, kBlock, 0, st>>>(e, E, d.size, R, s.cbirth, s.cdeath, Hi, o.cl_id, o.cl_parent,
+    TK(c, "k_e_out", k_e_out<<<gc, kBlock, 0, st>>>(e, gv, d.size, s.cbirth, s.cdeath, Hi, o.cl_id, o.cl_parent,
                                    o.cl_birth, o.cl_death, o.cl_size, o.cl_stab_hi, o.cl_stab_lo,
                                    o.cl_selected));
     return DGEC_OK;

@@ -19,8 +19,25 @@ namespace dgec {
 constexpr unsigned long long kPad = 0xFFFFFFFFFFFFFFFFull;
 
 // flags: [0] bad vertex count, [1] self loop count, [2] t min, [3] t max
+// graph of every edge (binary search over the batch's edge offsets)
+__global__ void k_egraph(const int64_t *eoff, int G, int64_t E, int32_t *egraph) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = G;  // last g with eoff[g] <= e
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (eoff[mid] <= e) lo = mid;
+            else hi = mid;
+        }
+        egraph[e] = lo;
+    }
+}
+
+// Validates ids against each edge's own graph and counts degrees under
+// global vertex ids (local id + the graph's vertex offset).
 __global__ void k_count(const int32_t *src, const int32_t *dst, const int64_t *t, int64_t E,
-                        int32_t V, int *deg_out, int *deg_in, long long *flags) {
+                        const int32_t *egraph, const int64_t *voff, int *deg_out, int *deg_in,
+                        long long *flags) {
     __shared__ long long smin[kBlock / 32], smax[kBlock / 32];
     long long tmin = LLONG_MAX, tmax = LLONG_MIN;
     int bad = 0, loops = 0;
@@ -32,7 +49,13 @@ __global__ void k_count(const int32_t *src, const int32_t *dst, const int64_t *t
         int64_t e = wb + lane_id();
         bool ok = e < E;
         int s = ok ? src[e] : 0, d = ok ? dst[e] : 0;
-        bool vs = ok && s >= 0 && s < V && d >= 0 && d < V;
+        int64_t vo = 0, nv = 0;
+        if (ok) {
+            int g = egraph[e];
+            vo = voff[g];
+            nv = voff[g + 1] - vo;
+        }
+        bool vs = ok && s >= 0 && s < nv && d >= 0 && d < nv;
         if (ok && !vs) bad++;
         if (vs && s == d) loops++;
         if (ok) {
@@ -42,8 +65,8 @@ __global__ void k_count(const int32_t *src, const int32_t *dst, const int64_t *t
         }
         unsigned act = __ballot_sync(0xffffffffu, vs);
         if (vs) {
-            warp_agg_inc(deg_out, s, act);
-            warp_agg_inc(deg_in, d, act);
+            warp_agg_inc(deg_out, (int)(s + vo), act);
+            warp_agg_inc(deg_in, (int)(d + vo), act);
         }
     }
 #pragma unroll
@@ -86,8 +109,9 @@ __global__ void k_set_i64(long long *p, long long v) { *p = v; }
 // rank r = position of edge (t, id) in the global order; time-ordered
 // copies of the inputs for the later stages
 __global__ void k_rank_init(const unsigned long long *ks, int64_t E, long long tmin, int idbits,
-                            const int32_t *src, const int32_t *dst, int32_t *orig_of,
-                            int32_t *rank_of, int32_t *isrc, int32_t *idst, int64_t *it) {
+                            const int32_t *src, const int32_t *dst, const int32_t *egraph,
+                            const int64_t *voff, int32_t *orig_of, int32_t *rank_of, int32_t *isrc,
+                            int32_t *idst, int64_t *it) {
     const unsigned long long idmask = (1ull << idbits) - 1ull;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < E;
          r += (int64_t)gridDim.x * blockDim.x) {
@@ -96,8 +120,9 @@ __global__ void k_rank_init(const unsigned long long *ks, int64_t E, long long t
         orig_of[r] = e;
         rank_of[e] = (int32_t)r;
         it[r] = (int64_t)(k >> idbits) + tmin;
-        isrc[r] = src[e];
-        idst[r] = dst[e];
+        int32_t vo = (int32_t)voff[egraph[e]];
+        isrc[r] = src[e] + vo;
+        idst[r] = dst[e] + vo;
     }
 }
 
@@ -129,7 +154,7 @@ __global__ void k_scatter(const int32_t *isrc, const int32_t *idst, int64_t E,
 }
 
 // bins: 0 warp (2..32), 1 CTA-256, 2 CTA-2048, 3 hub (> 2048)
-__global__ void k_classify(const int64_t *off, int32_t V, int *bin_cnt, int *bin_list,
+__global__ void k_classify(const int64_t *off, int64_t V, int *bin_cnt, int *bin_list,
                            int64_t list_stride) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t wb = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; wb < V;
@@ -360,13 +385,15 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
     CU_TRY(c, cudaMemsetAsync(s.deg_in, 0, sizeof(int) * (V + 1), st));
     TK(c, "k_init_flags", k_init_flags<<<1, 1, 0, st>>>(s.flags));
     if (E > 0) {
+        if (p.G == 1) CU_TRY(c, cudaMemsetAsync(p.egraph, 0, sizeof(int32_t) * E, st));
+        else TK(c, "k_egraph", k_egraph<<<grid_for(E, kBlock, 65536), kBlock, 0, st>>>(p.eoff, p.G, E, p.egraph));
         TK(c, "k_count", k_count<<<grid_for(E, kBlock, (int64_t)c->num_sms * 16), kBlock, 0, st>>>(
-            p.src, p.dst, p.t, E, p.V, s.deg_out, s.deg_in, s.flags));
+                             p.src, p.dst, p.t, E, p.egraph, p.voff, s.deg_out, s.deg_in, s.flags));
     }
     int64_t f[4];
     DG_TRY(read_counters(c, (const int64_t *)s.flags, 4, f));
-    if (f[0]) return set_err(c, DGEC_ERR_VERTEX_RANGE, "%lld edges have a vertex id outside [0, %d)",
-                             (long long)f[0], p.V);
+    if (f[0]) return set_err(c, DGEC_ERR_VERTEX_RANGE, "%lld edges have a vertex id outside their graph's range",
+                             (long long)f[0]);
     if (f[1]) return set_err(c, DGEC_ERR_SELF_LOOP, "%lld self loops (i, i, t)", (long long)f[1]);
     p.tmin = E > 0 ? f[2] : 0;
     uint64_t span = E > 0 ? (uint64_t)(f[3] - f[2]) : 0;
@@ -391,7 +418,7 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
         DG_TRY(radix_sort(c, RadixBuffers{s.okey, s.ikey, nullptr, nullptr}, E, 0, p.idbits + p.tbits,
                           s.radix, &in_b));
         TK(c, "k_rank_init", k_rank_init<<<gEE, kBlock, 0, st>>>(in_b ? s.ikey : s.okey, E, p.tmin, p.idbits,
-                                                                p.src, p.dst, o.orig_of, o.rank_of,
+                                                                p.src, p.dst, p.egraph, p.voff, o.orig_of, o.rank_of,
                                                                 o.isrc, o.idst, o.it));
     }
     // scatter ranks into their segments (cursors reuse the degree arrays)

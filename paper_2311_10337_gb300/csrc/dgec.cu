@@ -14,38 +14,72 @@ struct dgec_ctx {
 
 namespace {
 
-// Workspace = outputs (kept) followed by one scratch region that every
-// stage reuses in turn (sized for the largest stage).
+// Workspace = per-graph tables and outputs (kept) followed by one scratch
+// region that every stage reuses in turn (sized for the largest stage).
 struct Layout {
+    int64_t *eoff, *voff, *knn_off;
+    int32_t *gk, *gM, *egraph;
     Csr csr;
     Skel skel;
     Msf msf;
     Dendro den;
     Condensed cond;
+    int32_t *lmu, *lmv, *lla, *llb;  // batch outputs in each graph's local ids
     void *scratch = nullptr;
     size_t total = 0;
 };
 
-Problem make_problem(int64_t E, int32_t V, const dgec_params *prm) {
+// Host-side description of a batch (a plain run is one graph).
+struct HostBatch {
+    int32_t G;
+    const int64_t *eoff;  // [G+1]
+    const int32_t *nv;    // [G]
+    const int32_t *k;     // [G]
+    const int32_t *M;     // [G]
+};
+
+Problem make_problem(const HostBatch &hb) {
     Problem p;
     p.src = nullptr;
     p.dst = nullptr;
     p.t = nullptr;
-    p.E = E;
+    p.G = hb.G;
+    p.E = hb.eoff[hb.G];
+    int64_t V = 0;
+    int kmax = 1, Mmin = 1 << 30;
+    for (int g = 0; g < hb.G; g++) {
+        V += hb.nv[g];
+        kmax = std::max(kmax, hb.k[g]);
+        Mmin = std::min(Mmin, hb.M[g]);
+    }
     p.V = V;
-    p.k = prm ? prm->k : 1;
-    p.M = prm ? prm->min_cluster_size : 2;
+    p.k = kmax;
+    p.M = Mmin;
     return p;
 }
 
 Layout plan(void *base, const Problem &p) {
     Layout L;
     Arena a(base, SIZE_MAX);
+    L.eoff = a.take<int64_t>(p.G + 1);
+    L.voff = a.take<int64_t>(p.G + 1);
+    L.knn_off = a.take<int64_t>(p.G + 1);
+    L.gk = a.take<int32_t>(p.G);
+    L.gM = a.take<int32_t>(p.G);
+    L.egraph = a.take<int32_t>(p.E);
     plan_csr(a, p, L.csr);
     plan_skel(a, p, L.skel);
     plan_msf(a, p, L.msf);
     plan_dendro(a, p, L.den);
     plan_condensed(a, p, L.cond);
+    if (p.G > 1) {
+        L.lmu = a.take<int32_t>(p.E);
+        L.lmv = a.take<int32_t>(p.E);
+        L.lla = a.take<int32_t>(p.E);
+        L.llb = a.take<int32_t>(p.E);
+    } else {
+        L.lmu = L.lmv = L.lla = L.llb = nullptr;
+    }
     size_t scr = std::max({csr_scratch_bytes(p), skel_scratch_bytes(p), msf_scratch_bytes(p),
                            dendro_scratch_bytes(p), condense_scratch_bytes(p)});
     L.scratch = a.take<char>(scr);
@@ -53,26 +87,107 @@ Layout plan(void *base, const Problem &p) {
     return L;
 }
 
-dgec_status check_args(Ctx *c, int64_t E, int32_t V, const dgec_params *prm) {
-    if (!prm) return set_err(c, DGEC_ERR_INVALID_ARG, "params is null");
-    if (E < 0 || V < 0) return set_err(c, DGEC_ERR_INVALID_ARG, "negative size");
-    if (E >= (int64_t(1) << 30)) return set_err(c, DGEC_ERR_TOO_LARGE, "n_edges must be < 2^30");
-    if (prm->k < 1 || prm->k > 16) return set_err(c, DGEC_ERR_INVALID_ARG, "k must be in [1, 16]");
-    if (prm->min_cluster_size < 2) return set_err(c, DGEC_ERR_INVALID_ARG, "min_cluster_size must be >= 2");
-    if (prm->flags != 0) return set_err(c, DGEC_ERR_INVALID_ARG, "flags must be 0");
-    if (E > 0 && V == 0) return set_err(c, DGEC_ERR_VERTEX_RANGE, "edges but no vertices");
+dgec_status check_batch(Ctx *c, const HostBatch &hb) {
+    if (hb.G < 1 || !hb.eoff || !hb.nv || !hb.k || !hb.M)
+        return set_err(c, DGEC_ERR_INVALID_ARG, "bad batch description");
+    if (hb.eoff[0] != 0) return set_err(c, DGEC_ERR_INVALID_ARG, "edge offsets must start at 0");
+    int64_t V = 0;
+    for (int g = 0; g < hb.G; g++) {
+        int64_t Eg = hb.eoff[g + 1] - hb.eoff[g];
+        if (Eg < 0 || hb.nv[g] < 0) return set_err(c, DGEC_ERR_INVALID_ARG, "graph %d: negative size", g);
+        if (Eg > 0 && hb.nv[g] == 0) return set_err(c, DGEC_ERR_VERTEX_RANGE, "graph %d: edges but no vertices", g);
+        if (hb.k[g] < 1 || hb.k[g] > 16) return set_err(c, DGEC_ERR_INVALID_ARG, "k must be in [1, 16]");
+        if (hb.M[g] < 2) return set_err(c, DGEC_ERR_INVALID_ARG, "min_cluster_size must be >= 2");
+        V += hb.nv[g];
+    }
+    if (hb.eoff[hb.G] >= (int64_t(1) << 30)) return set_err(c, DGEC_ERR_TOO_LARGE, "total edges must be < 2^30");
+    if (V >= (int64_t(1) << 31)) return set_err(c, DGEC_ERR_TOO_LARGE, "total vertices must be < 2^31");
     return DGEC_OK;
 }
 
-dgec_status run_pipeline(Ctx *c, Problem &p, Layout &L, dgec_result *out) {
+dgec_status check_params(Ctx *c, const dgec_params *prm) {
+    if (!prm) return set_err(c, DGEC_ERR_INVALID_ARG, "params is null");
+    if (prm->flags != 0) return set_err(c, DGEC_ERR_INVALID_ARG, "flags must be 0");
+    return DGEC_OK;
+}
+
+// batch outputs in local ids: forest ends and dendrogram children
+__global__ void k_localize(int64_t n, int64_t E, const int32_t *mu, const int32_t *mv, const int32_t *la,
+                           const int32_t *lb, const int32_t *egraph, const int64_t *eoff,
+                           const int64_t *goff, int32_t *lmu, int32_t *lmv, int32_t *lla,
+                           int32_t *llb) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        int g = egraph[mu[s]];
+        int64_t e0 = eoff[g], Eg = eoff[g + 1] - e0, m0 = goff[g];
+        lmu[s] = (int32_t)(mu[s] - e0);
+        lmv[s] = (int32_t)(mv[s] - e0);
+        int a = la[s], b = lb[s];
+        lla[s] = (int32_t)(a < E ? a - e0 : Eg + (a - E - m0));
+        llb[s] = (int32_t)(b < E ? b - e0 : Eg + (b - E - m0));
+    }
+}
+
+dgec_status run_pipeline(Ctx *c, const HostBatch &hb, const int32_t *d_src, const int32_t *d_dst,
+                         const int64_t *d_t, void *d_ws, size_t ws_bytes, Layout *out_layout,
+                         Problem *out_problem) {
+    Problem p = make_problem(hb);
+    p.src = d_src;
+    p.dst = d_dst;
+    p.t = d_t;
+    if (p.E > 0 && (!d_src || !d_dst || !d_t)) return set_err(c, DGEC_ERR_INVALID_ARG, "null input");
+    if (!d_ws || ((uintptr_t)d_ws & 255))
+        return set_err(c, DGEC_ERR_INVALID_ARG, "workspace null or not 256-byte aligned");
+    size_t need = plan(nullptr, p).total;
+    if (ws_bytes < need) return set_err(c, DGEC_ERR_OOM, "workspace %zu bytes < %zu needed", ws_bytes, need);
+    Layout L = plan(d_ws, p);
+    // per-graph tables: staged through host arrays, one copy each
+    {
+        int G = hb.G;
+        int64_t *hv = (int64_t *)malloc(sizeof(int64_t) * (3 * (size_t)(G + 1)));
+        if (!hv) return set_err(c, DGEC_ERR_OOM, "host memory");
+        int64_t *hvoff = hv, *hknn = hv + (G + 1), *heoff = hv + 2 * (G + 1);
+        hvoff[0] = 0;
+        hknn[0] = 0;
+        for (int g = 0; g < G; g++) {
+            heoff[g] = hb.eoff[g];
+            hvoff[g + 1] = hvoff[g] + hb.nv[g];
+            hknn[g + 1] = hknn[g] + (hb.eoff[g + 1] - hb.eoff[g]) * hb.k[g];
+        }
+        heoff[G] = hb.eoff[G];
+        cudaError_t e1 = cudaMemcpyAsync(L.eoff, heoff, sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, c->stream);
+        cudaError_t e2 = cudaMemcpyAsync(L.voff, hvoff, sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, c->stream);
+        cudaError_t e3 = cudaMemcpyAsync(L.knn_off, hknn, sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, c->stream);
+        cudaError_t e4 = cudaMemcpyAsync(L.gk, hb.k, sizeof(int32_t) * G, cudaMemcpyHostToDevice, c->stream);
+        cudaError_t e5 = cudaMemcpyAsync(L.gM, hb.M, sizeof(int32_t) * G, cudaMemcpyHostToDevice, c->stream);
+        cudaError_t e6 = cudaStreamSynchronize(c->stream);
+        free(hv);
+        if (e1 || e2 || e3 || e4 || e5 || e6) return set_err(c, DGEC_ERR_CUDA, "copying the batch tables failed");
+    }
+    p.eoff = L.eoff;
+    p.voff = L.voff;
+    p.knn_off = L.knn_off;
+    p.gk = L.gk;
+    p.gM = L.gM;
+    p.egraph = L.egraph;
     DG_TRY(stage_csr(c, p, L.csr, L.scratch));
     DG_TRY(stage_skeleton(c, p, L.csr, L.skel, L.scratch));
     DG_TRY(stage_msf(c, p, L.csr, L.skel, L.msf, L.scratch));
     DG_TRY(stage_dendro(c, p, L.csr, L.msf, L.den, L.scratch));
     DG_TRY(stage_condense(c, p, L.msf, L.den, L.cond, L.scratch));
+    if (p.G > 1 && L.msf.n > 0)
+        TK(c, "k_localize", k_localize<<<grid_for(L.msf.n, kBlock, 65536), kBlock, 0, c->stream>>>(
+                                L.msf.n, p.E, L.msf.u, L.msf.v, L.den.a, L.den.b, p.egraph, p.eoff,
+                                L.msf.goff, L.lmu, L.lmv, L.lla, L.llb));
     CU_TRY(c, cudaStreamSynchronize(c->stream));
     CU_TRY(c, cudaGetLastError());
     kt_collect(c);
+    *out_layout = L;
+    *out_problem = p;
+    return DGEC_OK;
+}
+
+void fill_result(const Layout &L, dgec_result *out) {
     out->out_off = L.csr.out_off;
     out->in_off = L.csr.in_off;
     out->out_t = L.csr.out_t;
@@ -105,7 +220,6 @@ dgec_status run_pipeline(Ctx *c, Problem &p, Layout &L, dgec_result *out) {
     out->n_mst = L.msf.n;
     out->n_condensed = L.cond.n_cl;
     out->n_clusters = L.cond.n_clusters;
-    return DGEC_OK;
 }
 
 }  // namespace
@@ -190,10 +304,12 @@ dgec_status dgec_kernel_timing(dgec_ctx *x, int i, const char **name, double *to
 dgec_status dgec_workspace_size(int64_t n_edges, int32_t n_vertices, const dgec_params *params,
                                 size_t *bytes) {
     if (!bytes) return DGEC_ERR_INVALID_ARG;
-    dgec_status s = check_args(nullptr, n_edges, n_vertices, params);
-    if (s != DGEC_OK) return s;
-    Problem p = make_problem(n_edges, n_vertices, params);
-    *bytes = plan(nullptr, p).total;
+    DG_TRY(check_params(nullptr, params));
+    int64_t eoff[2] = {0, n_edges};
+    HostBatch hb{1, eoff, &n_vertices, &params->k, &params->min_cluster_size};
+    if (n_edges < 0) return DGEC_ERR_INVALID_ARG;
+    DG_TRY(check_batch(nullptr, hb));
+    *bytes = plan(nullptr, make_problem(hb)).total;
     return DGEC_OK;
 }
 
@@ -204,22 +320,68 @@ dgec_status dgec_run(dgec_ctx *x, const int32_t *d_src, const int32_t *d_dst, co
     Ctx *c = &x->c;
     c->msg[0] = 0;
     c->launches = 0;
-    DG_TRY(check_args(c, n_edges, n_vertices, params));
+    DG_TRY(check_params(c, params));
     if (!out) return set_err(c, DGEC_ERR_INVALID_ARG, "out is null");
-    if (n_edges > 0 && (!d_src || !d_dst || !d_t)) return set_err(c, DGEC_ERR_INVALID_ARG, "null input");
-    if (!d_ws || ((uintptr_t)d_ws & 255)) return set_err(c, DGEC_ERR_INVALID_ARG, "workspace null or not 256-byte aligned");
+    if (n_edges < 0) return set_err(c, DGEC_ERR_INVALID_ARG, "negative size");
+    int64_t eoff[2] = {0, n_edges};
+    HostBatch hb{1, eoff, &n_vertices, &params->k, &params->min_cluster_size};
+    DG_TRY(check_batch(c, hb));
     CU_TRY(c, cudaSetDevice(c->device));
     c->stream = (cudaStream_t)stream;
-    Problem p = make_problem(n_edges, n_vertices, params);
-    p.src = d_src;
-    p.dst = d_dst;
-    p.t = d_t;
-    size_t need = plan(nullptr, p).total;
-    if (ws_bytes < need)
-        return set_err(c, DGEC_ERR_OOM, "workspace %zu bytes < %zu needed", ws_bytes, need);
-    Layout L = plan(d_ws, p);
+    Layout L;
+    Problem p;
     memset(out, 0, sizeof(*out));
-    return run_pipeline(c, p, L, out);
+    DG_TRY(run_pipeline(c, hb, d_src, d_dst, d_t, d_ws, ws_bytes, &L, &p));
+    fill_result(L, out);
+    return DGEC_OK;
+}
+
+dgec_status dgec_batch_workspace_size(int32_t n_graphs, const int64_t *h_edge_off,
+                                      const int32_t *h_n_vertices, const int32_t *h_k,
+                                      const int32_t *h_min_cluster_size, size_t *bytes) {
+    if (!bytes) return DGEC_ERR_INVALID_ARG;
+    HostBatch hb{n_graphs, h_edge_off, h_n_vertices, h_k, h_min_cluster_size};
+    DG_TRY(check_batch(nullptr, hb));
+    *bytes = plan(nullptr, make_problem(hb)).total;
+    return DGEC_OK;
+}
+
+dgec_status dgec_run_batch(dgec_ctx *x, int32_t n_graphs, const int64_t *h_edge_off,
+                           const int32_t *h_n_vertices, const int32_t *h_k,
+                           const int32_t *h_min_cluster_size, const int32_t *d_src,
+                           const int32_t *d_dst, const int64_t *d_t, void *d_ws, size_t ws_bytes,
+                           void *stream, dgec_batch_result *out) {
+    if (!x) return DGEC_ERR_INVALID_ARG;
+    Ctx *c = &x->c;
+    c->msg[0] = 0;
+    c->launches = 0;
+    if (!out) return set_err(c, DGEC_ERR_INVALID_ARG, "out is null");
+    HostBatch hb{n_graphs, h_edge_off, h_n_vertices, h_k, h_min_cluster_size};
+    DG_TRY(check_batch(c, hb));
+    CU_TRY(c, cudaSetDevice(c->device));
+    c->stream = (cudaStream_t)stream;
+    Layout L;
+    Problem p;
+    memset(out, 0, sizeof(*out));
+    DG_TRY(run_pipeline(c, hb, d_src, d_dst, d_t, d_ws, ws_bytes, &L, &p));
+    fill_result(L, &out->global);
+    bool local = n_graphs > 1;
+    out->labels = L.cond.labels;
+    out->knn_id = L.skel.knn;
+    out->core = L.skel.core;
+    out->mst_u = local ? L.lmu : L.msf.u;
+    out->mst_v = local ? L.lmv : L.msf.v;
+    out->mst_w = L.msf.w;
+    out->link_a = local ? L.lla : L.den.a;
+    out->link_b = local ? L.llb : L.den.b;
+    out->link_size = L.den.size;
+    out->n_clusters = L.cond.gclusters;
+    out->mst_off = L.msf.goff;
+    out->knn_off = L.knn_off;
+    out->total_edges = p.E;
+    out->total_mst = L.msf.n;
+    out->total_clusters = L.cond.n_clusters;
+    return DGEC_OK;
 }
 
 dgec_status dgec_run_host(dgec_ctx *x, const int32_t *h_src, const int32_t *h_dst, const int64_t *h_t,
@@ -228,7 +390,8 @@ dgec_status dgec_run_host(dgec_ctx *x, const int32_t *h_src, const int32_t *h_ds
     if (!x) return DGEC_ERR_INVALID_ARG;
     Ctx *c = &x->c;
     c->msg[0] = 0;
-    DG_TRY(check_args(c, n_edges, n_vertices, params));
+    DG_TRY(check_params(c, params));
+    if (n_edges < 0) return set_err(c, DGEC_ERR_INVALID_ARG, "negative size");
     if (n_edges > 0 && (!h_src || !h_dst || !h_t || !h_labels))
         return set_err(c, DGEC_ERR_INVALID_ARG, "null host pointer");
     if (!d_ws || ((uintptr_t)d_ws & 255)) return set_err(c, DGEC_ERR_INVALID_ARG, "workspace null or not 256-byte aligned");

@@ -292,6 +292,32 @@ __global__ void k_gather_w(const int64_t *w, const unsigned long long *idx, int6
     }
 }
 
+// graph of each sorted forest edge, as a sort key (graph-major output)
+__global__ void k_gather_graph(const int32_t *tu, const int32_t *egraph, const unsigned long long *idx,
+                               int64_t n, unsigned long long *k, unsigned long long *val) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long i = idx[x];
+        k[x] = (unsigned long long)egraph[tu[i]];
+        val[x] = i;
+    }
+}
+
+// goff[g] = first row of graph g in the graph-major forest (binary search)
+__global__ void k_graph_offsets(const int32_t *u, const int32_t *egraph, int64_t n, int G,
+                                int64_t *goff) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g <= G;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = n;  // first row whose graph >= g
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (egraph[u[mid]] < g) lo = mid + 1;
+            else hi = mid;
+        }
+        goff[g] = lo;
+    }
+}
+
 __global__ void k_gather_msf(const unsigned long long *idx, int64_t n, const int32_t *tu,
                              const int32_t *tv, const int32_t *tru, const int32_t *trv,
                              const int64_t *tw, int32_t *u, int32_t *v, int32_t *ru, int32_t *rv,
@@ -308,6 +334,7 @@ __global__ void k_gather_msf(const unsigned long long *idx, int64_t n, const int
 }
 
 void plan_msf(Arena &ws, const Problem &p, Msf &o) {
+    o.goff = ws.take<int64_t>(p.G + 1);
     o.u = ws.take<int32_t>(p.E);
     o.v = ws.take<int32_t>(p.E);
     o.ru = ws.take<int32_t>(p.E);
@@ -362,6 +389,7 @@ dgec_status stage_msf(Ctx *c, const Problem &p, const Csr &g, const Skel &sk, Ms
     cudaStream_t st = c->stream;
     o.n = 0;
     int64_t E = p.E;
+    CU_TRY(c, cudaMemsetAsync(o.goff, 0, sizeof(int64_t) * (p.G + 1), st));
     if (E == 0 || sk.n == 0) return DGEC_OK;
     Arena a(scratch, SIZE_MAX);
     MsfScratch s = carve_msf(a, p);
@@ -411,19 +439,32 @@ dgec_status stage_msf(Ctx *c, const Problem &p, const Csr &g, const Skel &sk, Ms
     o.n = m;
     if (m == 0) return DGEC_OK;
     // order by (w, u, v): stable radix by the packed original ends, then by w,
-    // carrying the edge index; then gather every column
+    // then (batches) by graph, carrying the edge index; then gather columns
     int gm = grid_for(m, kBlock, 65536);
-    TK(c, "k_pack_uv", k_pack_uv_idx<<<gm, kBlock, 0, st>>>(s.tu, s.tv, m, p.idbits, s.k1, s.v1));
+    unsigned long long *K[2] = {s.k1, s.k2}, *Vb[2] = {s.v1, s.v2};
+    int cur = 0;
     bool in_b;
-    DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, s.v1, s.v2}, m, 0, 2 * p.idbits, s.radix, &in_b));
-    unsigned long long *idx = in_b ? s.v2 : s.v1;
-    unsigned long long *kw = in_b ? s.k1 : s.k2, *vw = in_b ? s.v1 : s.v2;  // the free pair
-    TK(c, "k_gather_w", k_gather_w<<<gm, kBlock, 0, st>>>(s.tw, idx, m, kw, vw));
-    int wbits = p.tbits > 0 ? p.tbits : 1;
-    DG_TRY(radix_sort(c, RadixBuffers{kw, in_b ? s.k2 : s.k1, vw, idx}, m, 0, wbits, s.radix, &in_b));
-    unsigned long long *fin = in_b ? idx : vw;
+    TK(c, "k_pack_uv", k_pack_uv_idx<<<gm, kBlock, 0, st>>>(s.tu, s.tv, m, p.idbits, K[0], Vb[0]));
+    DG_TRY(radix_sort(c, RadixBuffers{K[cur], K[1 - cur], Vb[cur], Vb[1 - cur]}, m, 0, 2 * p.idbits,
+                      s.radix, &in_b));
+    if (in_b) cur = 1 - cur;
+    TK(c, "k_gather_w", k_gather_w<<<gm, kBlock, 0, st>>>(s.tw, Vb[cur], m, K[1 - cur], Vb[1 - cur]));
+    cur = 1 - cur;
+    DG_TRY(radix_sort(c, RadixBuffers{K[cur], K[1 - cur], Vb[cur], Vb[1 - cur]}, m, 0,
+                      p.tbits > 0 ? p.tbits : 1, s.radix, &in_b));
+    if (in_b) cur = 1 - cur;
+    if (p.G > 1) {
+        TK(c, "k_gather_graph", k_gather_graph<<<gm, kBlock, 0, st>>>(s.tu, p.egraph, Vb[cur], m, K[1 - cur],
+                                                                     Vb[1 - cur]));
+        cur = 1 - cur;
+        DG_TRY(radix_sort(c, RadixBuffers{K[cur], K[1 - cur], Vb[cur], Vb[1 - cur]}, m, 0,
+                          bits_for((uint64_t)(p.G - 1)), s.radix, &in_b));
+        if (in_b) cur = 1 - cur;
+    }
+    unsigned long long *fin = Vb[cur];
     TK(c, "k_gather_msf", k_gather_msf<<<gm, kBlock, 0, st>>>(fin, m, s.tu, s.tv, s.tru, s.trv, s.tw, o.u, o.v,
                                                               o.ru, o.rv, o.w));
+    TK(c, "k_graph_offsets", k_graph_offsets<<<grid_for(p.G + 1), kBlock, 0, st>>>(o.u, p.egraph, m, p.G, o.goff));
     return DGEC_OK;
 }
 

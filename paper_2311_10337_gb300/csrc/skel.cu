@@ -162,8 +162,10 @@ __global__ void __launch_bounds__(128) k_ranks_knn(const int32_t *src, const int
                                                    const int64_t *out_off, const int64_t *out_t,
                                                    const int32_t *out_id, const int64_t *in_off,
                                                    const int64_t *in_t, const int32_t *in_id,
-                                                   int32_t *brank, int32_t *arank, int k, int32_t *knn,
-                                                   int64_t *core) {
+                                                   int32_t *brank, int32_t *arank,
+                                                   const int32_t *egraph, const int64_t *eoff,
+                                                   const int32_t *gk, const int64_t *knn_off,
+                                                   int32_t *knn, int64_t *core) {
     constexpr int N = 2 * K;
     // r runs over internal ids (src, dst, t are the r-ordered copies); the
     // neighbour lists are written under the original id, with original ids
@@ -172,6 +174,11 @@ __global__ void __launch_bounds__(128) k_ranks_knn(const int32_t *src, const int
         int i = src[r], j = dst[r];
         long long te = t[r];
         const int64_t e = orig_of[r];
+        // the edge's graph: its k, its kNN rows, its local id base
+        const int gr = egraph[e];
+        const int k = gk[gr];
+        const int64_t e0 = eoff[gr];
+        int32_t *row = knn + knn_off[gr] + (e - e0) * k;
         int64_t ib = in_off[i];
         int64_t ob = out_off[j], nout = out_off[j + 1] - ob;
         int64_t b = upper_bound_t(in_t + ib, in_off[i + 1] - ib, te);
@@ -239,13 +246,13 @@ __global__ void __launch_bounds__(128) k_ranks_knn(const int32_t *src, const int
 #pragma unroll
         for (int x = 0; x < N; x++) {
             if (c[x].id != INT_MAX && c[x].id != prev && cnt < k) {
-                knn[e * k + cnt] = c[x].id;
+                row[cnt] = (int32_t)(c[x].id - e0);
                 last_w = c[x].w;
                 cnt++;
             }
             prev = c[x].id;
         }
-        for (int x = cnt; x < k; x++) knn[e * k + x] = -1;
+        for (int x = cnt; x < k; x++) row[x] = -1;
         core[e] = cnt == k ? last_w : LLONG_MAX;
     }
 }
@@ -258,7 +265,7 @@ void plan_skel(Arena &ws, const Problem &p, Skel &o) {
     o.ru = ws.take<int32_t>(2 * p.E);
     o.rv = ws.take<int32_t>(2 * p.E);
     o.w = ws.take<int64_t>(2 * p.E);
-    o.knn = ws.take<int32_t>(p.E * (int64_t)p.k);
+    o.knn = ws.take<int32_t>(p.E * (int64_t)p.k);  // p.k: the largest k of the batch
     o.core = ws.take<int64_t>(p.E);
 }
 
@@ -295,7 +302,7 @@ dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void
     int grid = grid_for(E, 128, 1 << 20);
 #define KNN_ARGS                                                                           \
     g.isrc, g.idst, g.it, g.orig_of, E, g.out_off, g.out_t, g.out_id, g.in_off, g.in_t, g.in_id, \
-        o.brank, o.arank, p.k, o.knn, o.core
+        o.brank, o.arank, p.egraph, p.eoff, p.gk, p.knn_off, o.knn, o.core
     if (p.k <= 4) TK(c, "k_ranks_knn", k_ranks_knn<4><<<grid, 128, 0, st>>>(KNN_ARGS));
     else if (p.k <= 8) TK(c, "k_ranks_knn", k_ranks_knn<8><<<grid, 128, 0, st>>>(KNN_ARGS));
     else TK(c, "k_ranks_knn", k_ranks_knn<16><<<grid, 128, 0, st>>>(KNN_ARGS));

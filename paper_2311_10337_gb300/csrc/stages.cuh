@@ -5,15 +5,26 @@
 
 namespace dgec {
 
-// Problem description shared by the stages.
+// Problem description shared by the stages. A run is a batch of G >= 1
+// independent graphs laid end to end (a plain run is G = 1): graph g owns
+// edges [eoff[g], eoff[g+1]) with local vertex ids in [0, voff[g+1] -
+// voff[g]); stages work on global ids (edge position, vertex + voff[g]).
 struct Problem {
     const int32_t *src, *dst;
     const int64_t *t;
     int64_t E;
-    int32_t V;
-    int32_t k, M;
+    int64_t V;  // total vertices
+    int32_t k, M;  // largest k, smallest M over the graphs (host-side bounds)
     int64_t tmin = 0;
     int idbits = 1, tbits = 0;
+    // per-graph description (device arrays)
+    int32_t G = 1;
+    const int64_t *eoff = nullptr;    // [G+1]
+    const int64_t *voff = nullptr;    // [G+1]
+    const int32_t *gk = nullptr;      // [G] k of each graph
+    const int32_t *gM = nullptr;      // [G] M of each graph
+    const int64_t *knn_off = nullptr; // [G+1] first kNN slot of each graph
+    int32_t *egraph = nullptr;        // [E] graph of each edge (built in stage A)
 };
 
 // Stage A: incidence lists (Alg. 3 first line), per-vertex lists sorted by
@@ -63,6 +74,7 @@ struct Msf {
     int32_t *ru, *rv;  // [E] internal ids of the same edges
     int64_t *w;
     int64_t n = 0;
+    int64_t *goff;     // [G+1] rows of graph g: [goff[g], goff[g+1]) (graph-major order)
 };
 void plan_msf(Arena &ws, const Problem &p, Msf &o);
 size_t msf_scratch_bytes(const Problem &p);
@@ -88,6 +100,7 @@ struct Condensed {
     int64_t *cl_size;
     int32_t *cl_selected;
     int32_t *labels;  // [E]
+    int32_t *gclusters;  // [G] final clusters per graph
     int64_t n_cl = 0;
     int32_t n_clusters = 0;
 };

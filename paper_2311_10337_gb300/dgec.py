@@ -22,7 +22,8 @@ STATUS = {0: "DGEC_OK", 1: "DGEC_ERR_INVALID_ARG", 2: "DGEC_ERR_VERTEX_RANGE",
 
 EXPORTS = ["dgec_create", "dgec_destroy", "dgec_last_error", "dgec_status_string",
            "dgec_workspace_size", "dgec_run", "dgec_run_host", "dgec_last_launch_count",
-           "dgec_set_kernel_timing", "dgec_kernel_timing", "dgec_msf_static"]
+           "dgec_set_kernel_timing", "dgec_kernel_timing", "dgec_msf_static",
+           "dgec_batch_workspace_size", "dgec_run_batch"]
 
 
 class DgecError(RuntimeError):
@@ -47,6 +48,14 @@ class Result(ctypes.Structure):
         "cl_stab_hi", "cl_stab_lo", "cl_size", "cl_selected", "labels")] + [
         ("n_skeleton", ctypes.c_int64), ("n_mst", ctypes.c_int64),
         ("n_condensed", ctypes.c_int64), ("n_clusters", ctypes.c_int32)]
+
+
+class BatchResult(ctypes.Structure):
+    _fields_ = [(n, _P) for n in (
+        "labels", "knn_id", "core", "mst_u", "mst_v", "mst_w", "link_a", "link_b", "link_size",
+        "n_clusters", "mst_off", "knn_off")] + [
+        ("total_edges", ctypes.c_int64), ("total_mst", ctypes.c_int64),
+        ("total_clusters", ctypes.c_int32), ("glob", Result)]
 
 
 _lib = None
@@ -80,6 +89,12 @@ def load(path: str = LIB_PATH):
     L.dgec_kernel_timing.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
                                      ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_int64)]
+    I64A = ctypes.POINTER(ctypes.c_int64)
+    I32A = ctypes.POINTER(ctypes.c_int32)
+    L.dgec_batch_workspace_size.argtypes = [ctypes.c_int32, I64A, I32A, I32A, I32A,
+                                            ctypes.POINTER(ctypes.c_size_t)]
+    L.dgec_run_batch.argtypes = [_P, ctypes.c_int32, I64A, I32A, I32A, I32A, _P, _P, _P, _P,
+                                 ctypes.c_size_t, _P, ctypes.POINTER(BatchResult)]
     L.dgec_msf_static.argtypes = [_P, _P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P, _P,
                                   ctypes.POINTER(ctypes.c_int64), _P]
     _lib = L
@@ -194,6 +209,11 @@ class Context:
         self._check(rc)
         return Output(res, ws, E, n_vertices, k)
 
+    def run_batch(self, src, dst, t, edge_off, n_vertices, k, min_cluster_size, stream=None):
+        """Batched Alg. 4 over graphs laid end to end on the device; tables are
+        host arrays (edge_off[G+1] starting at 0, n_vertices/k/M per graph)."""
+        return _run_batch(self, src, dst, t, edge_off, n_vertices, k, min_cluster_size, stream)
+
     def run_host(self, src: np.ndarray, dst: np.ndarray, t: np.ndarray, n_vertices: int, k: int,
                  min_cluster_size: int, labels_out: np.ndarray | None = None, stream=None):
         """Alg. 4 from host arrays (pinned numpy views avoid staging copies);
@@ -212,6 +232,102 @@ class Context:
                                   st.cuda_stream, labels_out.ctypes.data, ctypes.byref(ncl))
         self._check(rc)
         return labels_out, int(ncl.value)
+
+
+def _i64p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+def _i32p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def batch_workspace_size(edge_off, n_vertices, k, min_cluster_size) -> int:
+    L = load()
+    eo = np.ascontiguousarray(edge_off, np.int64)
+    nv = np.ascontiguousarray(n_vertices, np.int32)
+    kk = np.ascontiguousarray(k, np.int32)
+    mm = np.ascontiguousarray(min_cluster_size, np.int32)
+    out = ctypes.c_size_t(0)
+    rc = L.dgec_batch_workspace_size(len(nv), _i64p(eo), _i32p(nv), _i32p(kk), _i32p(mm),
+                                     ctypes.byref(out))
+    if rc != DGEC_OK:
+        raise DgecError(rc, L.dgec_status_string(rc).decode())
+    return int(out.value)
+
+
+def _run_batch(ctx, src, dst, t, edge_off, n_vertices, k, min_cluster_size, stream=None):
+    torch = ctx.torch
+    eo = np.ascontiguousarray(edge_off, np.int64)
+    nv = np.ascontiguousarray(n_vertices, np.int32)
+    kk = np.ascontiguousarray(k, np.int32)
+    mm = np.ascontiguousarray(min_cluster_size, np.int32)
+    G = len(nv)
+    need = batch_workspace_size(eo, nv, kk, mm)
+    ws = ctx.workspace(need)
+    st = stream if stream is not None else torch.cuda.current_stream(ctx.device)
+    res = BatchResult()
+    rc = ctx.L.dgec_run_batch(ctx.h, G, _i64p(eo), _i32p(nv), _i32p(kk), _i32p(mm),
+                              src.data_ptr(), dst.data_ptr(), t.data_ptr(), ws.data_ptr(),
+                              ws.numel(), st.cuda_stream, ctypes.byref(res))
+    ctx._check(rc)
+    return BatchOutput(res, ws, eo, kk)
+
+
+class BatchOutput:
+    """Per-graph results of a batch (device views of the workspace)."""
+
+    def __init__(self, res, ws, edge_off, k):
+        import torch
+        self.G = len(k)
+        self.edge_off = edge_off
+        self.k = k
+        E = int(res.total_edges)
+        nmst = int(res.total_mst)
+        base = ws.data_ptr()
+
+        def view(ptr, n, dt, sz):
+            if n == 0 or ptr is None:
+                return torch.empty(0, dtype=dt, device=ws.device)
+            off = ptr - base
+            return ws[off:off + n * sz].view(dt)
+        knn_total = int(np.sum((edge_off[1:] - edge_off[:-1]) * k))
+        self.t = {
+            "labels": view(res.labels, E, torch.int32, 4),
+            "knn_id": view(res.knn_id, knn_total, torch.int32, 4),
+            "core": view(res.core, E, torch.int64, 8),
+            "mst_u": view(res.mst_u, nmst, torch.int32, 4),
+            "mst_v": view(res.mst_v, nmst, torch.int32, 4),
+            "mst_w": view(res.mst_w, nmst, torch.int64, 8),
+            "link_a": view(res.link_a, nmst, torch.int32, 4),
+            "link_b": view(res.link_b, nmst, torch.int32, 4),
+            "link_size": view(res.link_size, nmst, torch.int64, 8),
+            "n_clusters": view(res.n_clusters, self.G, torch.int32, 4),
+            "mst_off": view(res.mst_off, self.G + 1, torch.int64, 8),
+            "knn_off": view(res.knn_off, self.G + 1, torch.int64, 8),
+        }
+        self.total_clusters = int(res.total_clusters)
+
+    def numpy(self, name):
+        return self.t[name].cpu().numpy()
+
+    def graph(self, g):
+        """Host copies of graph g's outputs (local ids)."""
+        eo = self.edge_off
+        a, b = int(eo[g]), int(eo[g + 1])
+        mo = self.numpy("mst_off")
+        ko = self.numpy("knn_off")
+        m0, m1 = int(mo[g]), int(mo[g + 1])
+        kk = int(self.k[g])
+        out = {
+            "labels": self.t["labels"][a:b].cpu().numpy(),
+            "core": self.t["core"][a:b].cpu().numpy(),
+            "knn_id": self.t["knn_id"][int(ko[g]):int(ko[g + 1])].cpu().numpy().reshape(b - a, kk),
+            "n_clusters": int(self.numpy("n_clusters")[g]),
+        }
+        for n in ("mst_u", "mst_v", "mst_w", "link_a", "link_b", "link_size"):
+            out[n] = self.t[n][m0:m1].cpu().numpy()
+        return out
 
 
 class Output:

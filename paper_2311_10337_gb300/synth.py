@@ -303,3 +303,70 @@ def random_small(n_edges: int, n_vertices: int, t_max: int, seed: int,
     return Workload(f"rand{seed}", src.astype(np.int32), dst.astype(np.int32),
                     t.astype(np.int64), n_vertices, 3, 3,
                     f"E={n_edges} V={n_vertices} t~U[0,{t_max})")
+
+
+@dataclasses.dataclass
+class Batch:
+    """Independent graphs laid end to end; vertex ids are local per graph."""
+    src: np.ndarray        # int32[total]
+    dst: np.ndarray        # int32[total]
+    t: np.ndarray          # int64[total]
+    edge_off: np.ndarray   # int64[G+1]
+    n_vertices: np.ndarray  # int32[G]
+    k: np.ndarray          # int32[G]
+    min_cluster_size: np.ndarray  # int32[G]
+    recipe: str
+
+    @property
+    def n_graphs(self) -> int:
+        return int(self.n_vertices.shape[0])
+
+    def graph(self, g):
+        a, b = int(self.edge_off[g]), int(self.edge_off[g + 1])
+        return self.src[a:b], self.dst[a:b], self.t[a:b]
+
+
+def batch(n_graphs: int = 4096, log10_min: float = 3.0, log10_max: float = 6.0,
+          seed_offset: int = 0, t_max: int = 1_000_000, zipf_s: float = 2.1) -> Batch:
+    """The batching workload: E_b = round(10^U(log10_min, log10_max)) edges,
+    V_b = max(2, E_b // 10) vertices, each graph drawn like the tiny one at
+    its own size (rank-Zipf(2.1) endpoints, t uniform in [0, t_max)),
+    k_b uniform in {4, 8, 16}, M = 5. All graphs are drawn at once: one
+    inverse-CDF table serves every graph (a rank-Zipf law over V_b ranks is
+    the global law conditioned on rank <= V_b)."""
+    seed = BASE_SEED + 3 + 1000 * seed_offset
+    st = Stream(seed, 41)
+    sizes = np.round(10.0 ** (log10_min + (log10_max - log10_min) * st.uniform(n_graphs)))
+    sizes = np.maximum(sizes.astype(np.int64), 1)
+    nv = np.maximum(sizes // 10, 2).astype(np.int64)
+    k = np.array([4, 8, 16], np.int32)[st.integers(0, 3, n_graphs)]
+    eoff = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    total = int(eoff[-1])
+    gid = np.repeat(np.arange(n_graphs), sizes)
+    vmax = int(nv.max())
+    r = np.arange(1, vmax + 1, dtype=np.float64)
+    cdf = np.cumsum(r ** (-zipf_s))
+    cap = cdf[nv - 1]  # mass of ranks 1..V_b
+
+    def draw(stream):
+        u = stream.uniform(total) * cap[gid]
+        return np.minimum(np.searchsorted(cdf, u, side="right"), nv[gid] - 1).astype(np.int64)
+
+    s_src, s_dst = Stream(seed, 42), Stream(seed, 43)
+    src = draw(s_src)
+    dst = draw(s_dst)
+    for _ in range(64):
+        bad = np.nonzero(src == dst)[0]
+        if bad.size == 0:
+            break
+        u = s_dst.uniform(bad.size) * cap[gid[bad]]
+        dst[bad] = np.minimum(np.searchsorted(cdf, u, side="right"), nv[gid[bad]] - 1)
+    bad = np.nonzero(src == dst)[0]
+    dst[bad] = (src[bad] + 1) % nv[gid[bad]]
+    t = Stream(seed, 44).integers(0, t_max, total)
+    voff = np.concatenate([[0], np.cumsum(nv)])
+    t = _dedupe_triples(src + voff[gid], dst + voff[gid], t)
+    return Batch(src.astype(np.int32), dst.astype(np.int32), t.astype(np.int64), eoff,
+                 nv.astype(np.int32), k, np.full(n_graphs, 5, np.int32),
+                 f"{n_graphs} graphs, E_b=10^U({log10_min},{log10_max}) total {total}, "
+                 f"V_b=E_b/10, zipf={zipf_s}, t~U[0,{t_max}), k in {{4,8,16}}, M=5")

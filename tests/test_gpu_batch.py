@@ -1,0 +1,104 @@
+"""Batched form: many graphs in one pass give, graph by graph, exactly the
+results of running each graph alone (and of the oracle)."""
+import numpy as np
+import pytest
+
+from gpu_helpers import ctx, run_gpu
+from oracle import oracle as O
+from paper_2311_10337_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _with_edge_cases(b):
+    """Insert an empty graph and a one-edge graph into a batch."""
+    G = b.n_graphs
+    parts = []
+    for g in range(G):
+        parts.append((*b.graph(g), int(b.n_vertices[g]), int(b.k[g]), int(b.min_cluster_size[g])))
+        if g == 3:
+            parts.append((np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int64), 3, 4, 5))
+        if g == 7:
+            parts.append((np.array([1], np.int32), np.array([0], np.int32), np.array([5], np.int64), 2, 16, 2))
+    src = np.concatenate([p[0] for p in parts]).astype(np.int32)
+    dst = np.concatenate([p[1] for p in parts]).astype(np.int32)
+    t = np.concatenate([p[2] for p in parts]).astype(np.int64)
+    sizes = np.array([len(p[0]) for p in parts])
+    eoff = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    return synth.Batch(src, dst, t, eoff, np.array([p[3] for p in parts], np.int32),
+                       np.array([p[4] for p in parts], np.int32),
+                       np.array([p[5] for p in parts], np.int32), b.recipe + " + edge cases")
+
+
+def _run_batch(b):
+    import torch
+    s = torch.from_numpy(b.src).cuda()
+    d = torch.from_numpy(b.dst).cuda()
+    t = torch.from_numpy(b.t).cuda()
+    return ctx().run_batch(s, d, t, b.edge_off, b.n_vertices, b.k, b.min_cluster_size)
+
+
+def test_batch_equals_alone():
+    b = _with_edge_cases(synth.batch(40, 1.0, 3.6, seed_offset=5))
+    out = _run_batch(b)
+    # copy out before the per-graph runs reuse the workspace
+    batched = [out.graph(g) for g in range(b.n_graphs)]
+    total_clusters = out.total_clusters
+    alone = []
+    for g in range(b.n_graphs):
+        s, d, t = b.graph(g)
+        alone.append(run_gpu(s, d, t, int(b.n_vertices[g]), int(b.k[g]), int(b.min_cluster_size[g])))
+    total = 0
+    for g in range(b.n_graphs):
+        got = batched[g]
+        ref = alone[g]
+        for key in ("labels", "core", "mst_u", "mst_v", "mst_w", "link_a", "link_b", "link_size"):
+            assert np.array_equal(got[key], ref[key]), (g, key)
+        assert np.array_equal(got["knn_id"], ref["knn_id"]), (g, "knn")
+        assert got["n_clusters"] == ref["n_clusters"], g
+        total += ref["n_clusters"]
+    assert total_clusters == total
+
+
+@pytest.mark.parametrize("g", [0, 5, 11])
+def test_batch_graph_matches_oracle(g):
+    b = synth.batch(16, 2.0, 3.8, seed_offset=6)
+    out = _run_batch(b)
+    s, d, t = b.graph(g)
+    r = O.run(s, d, t, int(b.n_vertices[g]), int(b.k[g]), int(b.min_cluster_size[g]))
+    got = out.graph(g)
+    assert np.array_equal(got["labels"], r["condensed"]["labels"])
+    assert np.array_equal(got["knn_id"], r["knn"][0])
+    assert np.array_equal(got["core"], r["knn"][1])
+    mu, mv, mw = r["mst"]
+    assert np.array_equal(got["mst_u"], mu) and np.array_equal(got["mst_v"], mv)
+    assert np.array_equal(got["mst_w"], mw)
+    a, bb, sz = r["linkage"]
+    assert np.array_equal(got["link_a"], a) and np.array_equal(got["link_b"], bb)
+    assert np.array_equal(got["link_size"], sz)
+
+
+def test_single_graph_batch_is_plain_run():
+    w = synth.tiny(seed_offset=2)
+    b = synth.Batch(w.src, w.dst, w.t, np.array([0, w.n_edges], np.int64),
+                    np.array([w.n_vertices], np.int32), np.array([w.k], np.int32),
+                    np.array([w.min_cluster_size], np.int32), "tiny as a batch of one")
+    got = _run_batch(b).graph(0)  # host copies, taken before the plain run
+    ref = run_gpu(w.src, w.dst, w.t, w.n_vertices, w.k, w.min_cluster_size)
+    for key in ("labels", "core", "knn_id", "mst_u", "mst_v", "mst_w", "link_a", "link_b"):
+        assert np.array_equal(got[key], ref[key]), key
+
+
+def test_batch_rejects_bad_tables():
+    import torch
+    from paper_2311_10337_gb300 import dgec
+    z = torch.zeros(4, dtype=torch.int32, device="cuda")
+    zt = torch.zeros(4, dtype=torch.int64, device="cuda")
+    with pytest.raises(dgec.DgecError):   # offsets must start at 0
+        ctx().run_batch(z, z, zt, np.array([1, 4]), np.array([3]), np.array([4]), np.array([5]))
+    with pytest.raises(dgec.DgecError):   # vertex id out of its graph's range
+        s = torch.tensor([0, 5], dtype=torch.int32, device="cuda")
+        d = torch.tensor([1, 0], dtype=torch.int32, device="cuda")
+        t = torch.tensor([0, 1], dtype=torch.int64, device="cuda")
+        ctx().run_batch(s, d, t, np.array([0, 1, 2]), np.array([2, 3]), np.array([4, 4]),
+                        np.array([5, 5]))
