@@ -51,6 +51,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch-graphs", type=int, default=128,
                     help="graphs in the batched-vs-plain comparison (0 = skip)")
+    ap.add_argument("--serve-jobs", type=int, default=400,
+                    help="jobs in the serving measurement (0 = skip)")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrivals per second")
+    ap.add_argument("--serve-lanes", type=int, default=3)
+    ap.add_argument("--serve-pool-gb", type=float, default=72.0)
     ap.add_argument("--breakdown", action="store_true",
                     help="also time every kernel in one extra (untimed) step")
     return ap.parse_args()
@@ -175,6 +180,61 @@ def batched_vs_plain(ctx, n_graphs, steps):
             "speedup": tp / tb, "identical_labels": same}
 
 
+def serving(w, src, dst, tt, args):
+    """Served form: windowed clustering jobs over the workload's edge stream
+    (in (t, id) order, resident in HBM), Poisson arrivals, window sizes
+    log-uniform in [1e4, 1e7] edges (capped by a lane's capacity), k = 8,
+    M = 5. Latency = submission to labels ready; throughput = window edges
+    / makespan."""
+    import torch
+    from paper_2311_10337_gb300 import dgec
+    order = torch.sort(tt, stable=True).indices
+    S, D, T = src[order].contiguous(), dst[order].contiguous(), tt[order].contiguous()
+    E = int(S.shape[0])
+    srv = dgec.Server(int(args.serve_pool_gb * (1 << 30)), args.serve_lanes, w.n_vertices,
+                      max_jobs_per_batch=64)
+    cap = srv.lane_capacity()
+    rng = np.random.default_rng(0x231110337)
+    n_jobs = args.serve_jobs
+    sizes = np.minimum(np.round(10 ** rng.uniform(4, 7, n_jobs)).astype(np.int64), min(cap, E))
+    starts = np.array([rng.integers(0, E - n + 1) for n in sizes], np.int64)
+    arrivals = np.cumsum(rng.exponential(1.0 / args.serve_rate, n_jobs))
+    outs = [torch.empty(int(n), dtype=torch.int32, device="cuda") for n in sizes]
+    tickets = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for x in range(n_jobs):
+        delay = t0 + arrivals[x] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        a, n = int(starts[x]), int(sizes[x])
+        tickets.append(srv.submit(S[a:a + n], D[a:a + n], T[a:a + n], w.k, w.min_cluster_size, outs[x]))
+    lat, bad = [], 0
+    for tk in tickets:
+        rc, _, ms = srv.wait(tk, 600_000)
+        bad += rc != 0
+        lat.append(ms)
+    torch.cuda.synchronize()
+    makespan = time.perf_counter() - t0
+    srv.close()
+    # a sample of jobs re-run alone: identical labels
+    ctx = dgec.Context(0)
+    same = True
+    for x in list(range(min(3, n_jobs))):
+        a, n = int(starts[x]), int(sizes[x])
+        o = ctx.run(S[a:a + n], D[a:a + n], T[a:a + n], w.n_vertices, w.k, w.min_cluster_size)
+        same &= bool(torch.equal(o.tensor("labels"), outs[x]))
+    ctx.close()
+    lat = np.array(lat)
+    return {"jobs": n_jobs, "failed": int(bad), "arrivals_per_s": args.serve_rate,
+            "lanes": args.serve_lanes, "lane_capacity_edges": cap,
+            "window_edges_total": int(sizes.sum()), "makespan_s": makespan,
+            "edges_per_s": float(sizes.sum() / makespan),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "identical_to_alone_sample": same,
+            "stream": f"{w.name} edges in (t, id) order, {E} edges"}
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -284,6 +344,11 @@ def main():
     batch = None
     if args.batch_graphs > 0 and rank == 0:
         batch = batched_vs_plain(ctx, args.batch_graphs, max(1, min(args.steps, 3)))
+    serve = None
+    if args.serve_jobs > 0 and rank == 0:
+        ctx.ws = None
+        torch.cuda.empty_cache()
+        serve = serving(w, src, dst, tt, args)
     if rank == 0:
         peak, peak_kind = peaks()
         dom_ms, dom_n = dom
@@ -308,7 +373,7 @@ def main():
                            "edges_per_gpu": E, "parallelism": "replicas only",
                            "l2": "inputs (16 B/edge = %.0f MB) exceed L2; no flush" % (16 * E / 1e6),
                            "n_clusters": n_clusters},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "batch": batch,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "batch": batch, "serve": serve,
                 "gpu_launches": launches * args.steps, "clocks": clk}
         if args.breakdown:
             line["kernel_breakdown_ms"] = {n: [round(v[0], 3), v[1]] for n, v in

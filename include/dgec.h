@@ -42,7 +42,8 @@ typedef enum {
     DGEC_ERR_TOO_LARGE = 4,     /* n_edges >= 2^30, or time span too wide (see below) */
     DGEC_ERR_OOM = 5,           /* workspace smaller than dgec_workspace_size() */
     DGEC_ERR_CUDA = 6,          /* a CUDA runtime call failed */
-    DGEC_ERR_TIMEOUT = 7,       /* an iterative stage exceeded its round bound */
+    DGEC_ERR_TIMEOUT = 7,       /* an iterative stage exceeded its round bound, or a wait timed out */
+    DGEC_ERR_ADMISSION = 8,     /* a served job can never fit a lane's memory */
     DGEC_ERR_INTERNAL = 9
 } dgec_status;
 
@@ -189,6 +190,49 @@ dgec_status dgec_run_batch(dgec_ctx *ctx, int32_t n_graphs, const int64_t *h_edg
                            const int32_t *h_min_cluster_size, const int32_t *d_src,
                            const int32_t *d_dst, const int64_t *d_t, void *d_workspace,
                            size_t ws_bytes, void *cuda_stream, dgec_batch_result *out);
+
+/*
+ * Serving: a request loop with continuous batching (the benchmark spec's
+ * serving pattern). The server splits a caller-provided device pool into
+ * n_lanes lanes, each with its own host thread, CUDA stream and workspace.
+ * A free lane takes, in arrival order, every pending job that fits its
+ * memory (admission by memory), renumbers each job's vertices densely on
+ * the device, runs them together as one batch (dgec_run_batch) and writes
+ * each job's labels. Jobs that arrive while lanes are busy are picked up by
+ * the next lane to free up, so their work overlaps on the device. A job's
+ * result is identical whether it runs alone or in a mix.
+ */
+typedef struct dgec_server dgec_server;
+
+typedef struct {
+    const int32_t *d_src, *d_dst;  /* device, caller-owned, read during the job */
+    const int64_t *d_t;
+    int64_t n_edges;
+    int32_t k;                     /* 1..16 */
+    int32_t min_cluster_size;      /* >= 2 */
+    int32_t *d_labels;             /* device, caller-owned, int32[n_edges] output */
+} dgec_job;
+
+/* pool: device memory owned by the caller for the server's lifetime; it is
+ * split into n_lanes equal lanes. Vertex ids of every job must lie in
+ * [0, vertex_bound). max_jobs_per_batch caps a lane's batch. */
+dgec_status dgec_server_create(int device, void *d_pool, size_t pool_bytes, int32_t n_lanes,
+                               int32_t vertex_bound, int32_t max_jobs_per_batch,
+                               dgec_server **out);
+/* Queue a job (thread-safe, returns at once). *ticket names it in dgec_wait. */
+dgec_status dgec_submit(dgec_server *srv, const dgec_job *job, uint64_t *ticket);
+/* Wait for a job (timeout_ms < 0: no limit). On success fills the number of
+ * clusters and the job's latency from submission to labels ready (ms).
+ * Returns the job's own status (e.g. DGEC_ERR_SELF_LOOP for a bad job,
+ * DGEC_ERR_ADMISSION if it can never fit a lane). A ticket can be waited
+ * for once. */
+dgec_status dgec_wait(dgec_server *srv, uint64_t ticket, int32_t timeout_ms,
+                      int32_t *n_clusters, double *latency_ms);
+/* Edge capacity of one lane (the largest job it can admit). */
+int64_t dgec_server_lane_capacity(const dgec_server *srv);
+/* Stops the lanes after the jobs already taken and frees host state; the
+ * pool is untouched. Jobs still queued complete with DGEC_ERR_INVALID_ARG. */
+dgec_status dgec_server_destroy(dgec_server *srv);
 
 /* Number of kernel launches the last dgec_run on ctx issued (for reporting). */
 int64_t dgec_last_launch_count(const dgec_ctx *ctx);

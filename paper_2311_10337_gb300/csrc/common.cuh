@@ -155,3 +155,8 @@ __device__ __forceinline__ unsigned long long lambda_of(long long w) {
 }
 
 }  // namespace dgec
+
+// The C ABI's context handle wraps one internal context.
+struct dgec_ctx {
+    dgec::Ctx c;
+};

@@ -8,10 +8,6 @@
 
 using namespace dgec;
 
-struct dgec_ctx {
-    Ctx c;
-};
-
 namespace {
 
 // Workspace = per-graph tables and outputs (kept) followed by one scratch
@@ -271,7 +267,8 @@ const char *dgec_status_string(dgec_status s) {
         case DGEC_ERR_TOO_LARGE: return "input too large";
         case DGEC_ERR_OOM: return "workspace too small";
         case DGEC_ERR_CUDA: return "CUDA error";
-        case DGEC_ERR_TIMEOUT: return "iteration bound exceeded";
+        case DGEC_ERR_TIMEOUT: return "iteration bound exceeded or wait timed out";
+        case DGEC_ERR_ADMISSION: return "job can never fit a lane";
         default: return "internal error";
     }
 }

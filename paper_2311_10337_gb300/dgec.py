@@ -18,12 +18,14 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libdgec.so")
 DGEC_OK = 0
 STATUS = {0: "DGEC_OK", 1: "DGEC_ERR_INVALID_ARG", 2: "DGEC_ERR_VERTEX_RANGE",
           3: "DGEC_ERR_SELF_LOOP", 4: "DGEC_ERR_TOO_LARGE", 5: "DGEC_ERR_OOM",
-          6: "DGEC_ERR_CUDA", 7: "DGEC_ERR_TIMEOUT", 9: "DGEC_ERR_INTERNAL"}
+          6: "DGEC_ERR_CUDA", 7: "DGEC_ERR_TIMEOUT", 8: "DGEC_ERR_ADMISSION",
+          9: "DGEC_ERR_INTERNAL"}
 
 EXPORTS = ["dgec_create", "dgec_destroy", "dgec_last_error", "dgec_status_string",
            "dgec_workspace_size", "dgec_run", "dgec_run_host", "dgec_last_launch_count",
            "dgec_set_kernel_timing", "dgec_kernel_timing", "dgec_msf_static",
-           "dgec_batch_workspace_size", "dgec_run_batch"]
+           "dgec_batch_workspace_size", "dgec_run_batch", "dgec_server_create", "dgec_submit",
+           "dgec_wait", "dgec_server_lane_capacity", "dgec_server_destroy"]
 
 
 class DgecError(RuntimeError):
@@ -56,6 +58,11 @@ class BatchResult(ctypes.Structure):
         "n_clusters", "mst_off", "knn_off")] + [
         ("total_edges", ctypes.c_int64), ("total_mst", ctypes.c_int64),
         ("total_clusters", ctypes.c_int32), ("glob", Result)]
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("d_src", _P), ("d_dst", _P), ("d_t", _P), ("n_edges", ctypes.c_int64),
+                ("k", ctypes.c_int32), ("min_cluster_size", ctypes.c_int32), ("d_labels", _P)]
 
 
 _lib = None
@@ -95,6 +102,14 @@ def load(path: str = LIB_PATH):
                                             ctypes.POINTER(ctypes.c_size_t)]
     L.dgec_run_batch.argtypes = [_P, ctypes.c_int32, I64A, I32A, I32A, I32A, _P, _P, _P, _P,
                                  ctypes.c_size_t, _P, ctypes.POINTER(BatchResult)]
+    L.dgec_server_create.argtypes = [ctypes.c_int, _P, ctypes.c_size_t, ctypes.c_int32,
+                                     ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_P)]
+    L.dgec_submit.argtypes = [_P, ctypes.POINTER(Job), ctypes.POINTER(ctypes.c_uint64)]
+    L.dgec_wait.argtypes = [_P, ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                            ctypes.POINTER(ctypes.c_double)]
+    L.dgec_server_lane_capacity.argtypes = [_P]
+    L.dgec_server_lane_capacity.restype = ctypes.c_int64
+    L.dgec_server_destroy.argtypes = [_P]
     L.dgec_msf_static.argtypes = [_P, _P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P, _P,
                                   ctypes.POINTER(ctypes.c_int64), _P]
     _lib = L
@@ -328,6 +343,57 @@ class BatchOutput:
         for n in ("mst_u", "mst_v", "mst_w", "link_a", "link_b", "link_size"):
             out[n] = self.t[n][m0:m1].cpu().numpy()
         return out
+
+
+class Server:
+    """Serving loop (continuous batching) over a torch-allocated device pool.
+    Jobs are device tensors (views of a resident stream are fine); submit()
+    returns at once, wait() gives (status, n_clusters, latency_ms)."""
+
+    def __init__(self, pool_bytes: int, n_lanes: int, vertex_bound: int, max_jobs_per_batch: int = 64,
+                 device: int = 0):
+        import torch
+        self.L = load()
+        self.pool = torch.empty(pool_bytes, dtype=torch.uint8, device=f"cuda:{device}")
+        h = _P()
+        rc = self.L.dgec_server_create(device, self.pool.data_ptr(), pool_bytes, n_lanes,
+                                       vertex_bound, max_jobs_per_batch, ctypes.byref(h))
+        if rc != DGEC_OK:
+            raise DgecError(rc, "dgec_server_create failed")
+        self.h = h
+        self._keep = {}
+
+    def lane_capacity(self) -> int:
+        return int(self.L.dgec_server_lane_capacity(self.h))
+
+    def submit(self, src, dst, t, k: int, min_cluster_size: int, labels) -> int:
+        j = Job(src.data_ptr(), dst.data_ptr(), t.data_ptr(), int(src.shape[0]), k,
+                min_cluster_size, labels.data_ptr())
+        tk = ctypes.c_uint64(0)
+        rc = self.L.dgec_submit(self.h, ctypes.byref(j), ctypes.byref(tk))
+        if rc != DGEC_OK:
+            raise DgecError(rc, "dgec_submit failed")
+        self._keep[tk.value] = (src, dst, t, labels)  # keep the tensors alive
+        return int(tk.value)
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        n = ctypes.c_int32(0)
+        lat = ctypes.c_double(0)
+        rc = self.L.dgec_wait(self.h, ticket, timeout_ms, ctypes.byref(n), ctypes.byref(lat))
+        if rc != 7:  # a timed-out job is still pending
+            self._keep.pop(ticket, None)
+        return rc, int(n.value), float(lat.value)
+
+    def close(self):
+        if self.h:
+            self.L.dgec_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Output:
