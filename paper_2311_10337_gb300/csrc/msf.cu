@@ -174,22 +174,40 @@ __global__ void k_iota(int64_t E, int32_t *comp) {
 // ----- the pipeline's forest stage: nodes are internal ids r; each edge
 // carries its original ends (u < v) for the (w, u, v) tie-break key.
 
-__global__ void k_r_filter_bid(const int32_t *ru, const int32_t *rv, const int32_t *u, const int32_t *v,
-                               const int64_t *w, int64_t n, const int32_t *comp, int32_t *ru2,
-                               int32_t *rv2, int32_t *u2, int32_t *v2, int64_t *w2,
+// Edges carry the labels (cu, cv) of the components at their ends; the
+// labels move one hop per round (par of the old root), so no per-node
+// label array is swept. Live edges: (cu, cv) labels, (u, v) original ends
+// (the tie-break key), w.
+
+// Bid w into both ends (round 1: every node is a root and nothing is
+// filtered yet).
+__global__ void k_m_bid(const int32_t *cu, const int32_t *cv, const int64_t *w, int64_t n,
+                        unsigned long long *bw) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        int a = cu[x], b = cv[x];
+        unsigned long long uw = (unsigned long long)w[x];
+        if (uw < bw[a]) atomicMin(&bw[a], uw);
+        if (uw < bw[b]) atomicMin(&bw[b], uw);
+    }
+}
+
+// Move labels one hop to the merged roots, drop edges inside one
+// component, compact the rest and bid w.
+__global__ void k_m_filter_bid(const int32_t *cu, const int32_t *cv, const int32_t *u, const int32_t *v,
+                               const int64_t *w, int64_t n, const int32_t *par, int32_t *cu2,
+                               int32_t *cv2, int32_t *u2, int32_t *v2, int64_t *w2,
                                unsigned long long *cnt, unsigned long long *bw) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t wb = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; wb < n;
          wb += stride) {
         int64_t x = wb + lane_id();
         bool keep = false;
-        int a = 0, b = 0, ca = 0, cb = 0;
+        int a = 0, b = 0;
         if (x < n) {
-            a = ru[x];
-            b = rv[x];
-            ca = comp[a];
-            cb = comp[b];
-            keep = ca != cb;
+            a = par[cu[x]];
+            b = par[cv[x]];
+            keep = a != b;
         }
         unsigned m = __ballot_sync(0xffffffffu, keep);
         if (m == 0) continue;
@@ -200,60 +218,74 @@ __global__ void k_r_filter_bid(const int32_t *ru, const int32_t *rv, const int32
         if (keep) {
             int64_t at = (int64_t)base + __popc(m & ((1u << lane_id()) - 1u));
             unsigned long long uw = (unsigned long long)w[x];
-            ru2[at] = a;
-            rv2[at] = b;
+            cu2[at] = a;
+            cv2[at] = b;
             u2[at] = u[x];
             v2[at] = v[x];
             w2[at] = (int64_t)uw;
-            if (uw < bw[ca]) atomicMin(&bw[ca], uw);
-            if (uw < bw[cb]) atomicMin(&bw[cb], uw);
+            if (uw < bw[a]) atomicMin(&bw[a], uw);
+            if (uw < bw[b]) atomicMin(&bw[b], uw);
         }
     }
 }
 
-__global__ void k_r_bid_uv(const int32_t *ru, const int32_t *rv, const int32_t *u, const int32_t *v,
-                           const int64_t *w, int64_t n, const int32_t *comp,
-                           const unsigned long long *bw, unsigned long long *buv) {
+__global__ void k_m_bid_uv(const int32_t *cu, const int32_t *cv, const int32_t *u, const int32_t *v,
+                           const int64_t *w, int64_t n, const unsigned long long *bw,
+                           unsigned long long *buv) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
         unsigned long long ww = (unsigned long long)w[x];
-        int ca = comp[ru[x]], cb = comp[rv[x]];
-        bool wa = ww == bw[ca], wb = ww == bw[cb];
+        int a = cu[x], b = cv[x];
+        bool wa = ww == bw[a], wb = ww == bw[b];
         if (!wa && !wb) continue;
         unsigned long long key = ((unsigned long long)(unsigned)u[x] << 32) | (unsigned)v[x];
-        if (wa && key < buv[ca]) atomicMin(&buv[ca], key);
-        if (wb && key < buv[cb]) atomicMin(&buv[cb], key);
+        if (wa && key < buv[a]) atomicMin(&buv[a], key);
+        if (wb && key < buv[b]) atomicMin(&buv[b], key);
     }
 }
 
-// Component roots hook along their winning edge (named by its original
-// ends; rank_of gives the internal ends) and append it once.
-__global__ void k_r_hook(int64_t E, const int32_t *comp, const int32_t *rank_of,
-                         const unsigned long long *bw, const unsigned long long *buv, int32_t *par,
-                         int32_t *mu, int32_t *mv, int32_t *mru, int32_t *mrv, int64_t *mw,
-                         unsigned long long *n_out) {
+// The edge that won a root's bid records itself there (one writer: keys
+// are unique), with the label on its other end.
+__global__ void k_m_claim(const int32_t *cu, const int32_t *cv, const int32_t *u, const int32_t *v,
+                          int64_t n, const unsigned long long *buv, int32_t *bp, int32_t *win) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        int a = cu[x], b = cv[x];
+        unsigned long long key = ((unsigned long long)(unsigned)u[x] << 32) | (unsigned)v[x];
+        if (buv[a] == key) {
+            bp[a] = b;
+            win[a] = (int32_t)x;
+        }
+        if (buv[b] == key) {
+            bp[b] = a;
+            win[b] = (int32_t)x;
+        }
+    }
+}
+
+// Over the current roots: hook along the winner (a mutual pair keeps the
+// smaller label), append each forest edge once.
+__global__ void k_m_hook(const int32_t *roots, int64_t nr, const unsigned long long *bw,
+                         const unsigned long long *buv, const int32_t *bp, const int32_t *win,
+                         const int32_t *u, const int32_t *v, const int64_t *w, const int32_t *rank_of,
+                         int32_t *par, int32_t *mu, int32_t *mv, int32_t *mru, int32_t *mrv,
+                         int64_t *mw, unsigned long long *n_out) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < E;
+    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < nr;
          base += stride) {
-        int64_t x = base + lane_id();
+        int64_t ix = base + lane_id();
         bool emit = false;
-        int a = 0, b = 0, ra = 0, rb = 0;
-        unsigned long long ww = 0;
-        if (x < E && comp[x] == (int32_t)x) {
+        int wx = 0;
+        if (ix < nr) {
+            int x = roots[ix];
             if (bw[x] == kMax64) {
-                par[x] = (int32_t)x;
+                par[x] = x;
             } else {
-                unsigned long long key = buv[x];
-                a = (int)(key >> 32);
-                b = (int)(key & 0xffffffffu);
-                ra = rank_of[a];
-                rb = rank_of[b];
-                int ca = comp[ra], cb = comp[rb];
-                int partner = ca == (int)x ? cb : ca;
-                bool mutual = buv[partner] == key;
-                par[x] = (mutual && (int)x < partner) ? (int32_t)x : partner;
-                emit = !mutual || (int)x < partner;
-                ww = bw[x];
+                int p = bp[x];
+                bool mutual = bp[p] == x && buv[p] == buv[x];
+                par[x] = (mutual && x < p) ? x : p;
+                emit = !mutual || x < p;
+                wx = win[x];
             }
         }
         unsigned m = __ballot_sync(0xffffffffu, emit);
@@ -264,12 +296,66 @@ __global__ void k_r_hook(int64_t E, const int32_t *comp, const int32_t *rank_of,
         at = __shfl_sync(0xffffffffu, at, leader);
         if (emit) {
             at += __popc(m & ((1u << lane_id()) - 1u));
+            int a = u[wx], b = v[wx];
             mu[at] = a;
             mv[at] = b;
-            mru[at] = ra;
-            mrv[at] = rb;
-            mw[at] = (int64_t)ww;
+            mru[at] = rank_of[a];
+            mrv[at] = rank_of[b];
+            mw[at] = w[wx];
         }
+    }
+}
+
+// Roots walk to their new root (own pointer compressed on the way).
+__global__ void k_m_jump(const int32_t *roots, int64_t nr, int32_t *par) {
+    for (int64_t ix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ix < nr;
+         ix += (int64_t)gridDim.x * blockDim.x) {
+        int x = roots[ix];
+        int r = par[x];
+        for (int it = 0; it < kMaxWalk; it++) {
+            int rr = par[r];
+            if (rr == r) break;
+            r = rr;
+            par[x] = r;
+        }
+    }
+}
+
+// Next round's roots (old roots that stayed roots); every old root's bid
+// slots are cleared.
+__global__ void k_m_next_roots(const int32_t *roots, int64_t nr, const int32_t *par,
+                               unsigned long long *bw, unsigned long long *buv, int32_t *roots2,
+                               unsigned long long *cnt) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < nr;
+         base += stride) {
+        int64_t ix = base + lane_id();
+        bool keep = false;
+        int x = 0;
+        if (ix < nr) {
+            x = roots[ix];
+            keep = par[x] == x && bw[x] != kMax64;
+            bw[x] = kMax64;
+            buv[x] = kMax64;
+        }
+        unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (!m) continue;
+        int leader = __ffs(m) - 1;
+        unsigned long long at = 0;
+        if ((int)lane_id() == leader) at = atomicAdd(cnt, (unsigned long long)__popc(m));
+        at = __shfl_sync(0xffffffffu, at, leader);
+        if (keep) roots2[at + __popc(m & ((1u << lane_id()) - 1u))] = x;
+    }
+}
+
+__global__ void k_m_init(int64_t E, int32_t *par, int32_t *roots, unsigned long long *bw,
+                         unsigned long long *buv) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < E;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        par[x] = (int32_t)x;
+        roots[x] = (int32_t)x;
+        bw[x] = kMax64;
+        buv[x] = kMax64;
     }
 }
 
@@ -343,8 +429,11 @@ void plan_msf(Arena &ws, const Problem &p, Msf &o) {
 }
 
 struct MsfScratch {
-    int32_t *comp, *par, *ua, *va, *ub, *vb, *tu, *tv, *rua, *rva, *rub, *rvb, *tru, *trv;
-    int64_t *wa, *wb, *tw;
+    int32_t *par, *roots, *roots2, *bp, *win;
+    int32_t *cua, *cva, *ua, *va, *cub, *cvb, *ub, *vb;
+    int64_t *wa, *wb;
+    int32_t *tu, *tv, *tru, *trv;
+    int64_t *tw;
     unsigned long long *bw, *buv, *cnt;
     unsigned long long *k1, *k2, *v1, *v2;
     void *radix;
@@ -352,20 +441,23 @@ struct MsfScratch {
 static MsfScratch carve_msf(Arena &a, const Problem &p) {
     MsfScratch s;
     int64_t E = p.E, S = 2 * p.E;
-    s.comp = a.take<int32_t>(E);
     s.par = a.take<int32_t>(E);
+    s.roots = a.take<int32_t>(E);
+    s.roots2 = a.take<int32_t>(E);
+    s.bp = a.take<int32_t>(E);
+    s.win = a.take<int32_t>(E);
+    s.cua = a.take<int32_t>(S);
+    s.cva = a.take<int32_t>(S);
     s.ua = a.take<int32_t>(S);
     s.va = a.take<int32_t>(S);
     s.wa = a.take<int64_t>(S);
+    s.cub = a.take<int32_t>(S);
+    s.cvb = a.take<int32_t>(S);
     s.ub = a.take<int32_t>(S);
     s.vb = a.take<int32_t>(S);
     s.wb = a.take<int64_t>(S);
     s.tu = a.take<int32_t>(E);
     s.tv = a.take<int32_t>(E);
-    s.rua = a.take<int32_t>(S);
-    s.rva = a.take<int32_t>(S);
-    s.rub = a.take<int32_t>(S);
-    s.rvb = a.take<int32_t>(S);
     s.tru = a.take<int32_t>(E);
     s.trv = a.take<int32_t>(E);
     s.tw = a.take<int64_t>(E);
@@ -394,45 +486,51 @@ dgec_status stage_msf(Ctx *c, const Problem &p, const Csr &g, const Skel &sk, Ms
     Arena a(scratch, SIZE_MAX);
     MsfScratch s = carve_msf(a, p);
     const int gE = grid_for(E, kBlock, 65536);
-    TK(c, "k_iota", k_iota<<<gE, kBlock, 0, st>>>(E, s.comp));
-    TK(c, "k_reset_best", k_reset_best<<<gE, kBlock, 0, st>>>(E, s.bw, s.buv));
+    TK(c, "k_m_init", k_m_init<<<gE, kBlock, 0, st>>>(E, s.par, s.roots, s.bw, s.buv));
     CU_TRY(c, cudaMemsetAsync(s.cnt, 0, 4 * sizeof(unsigned long long), st));
-    // live edge list: (ru, rv) internal ends, (u, v) original ends, w
-    const int32_t *cru = sk.ru, *crv = sk.rv, *cu = sk.u, *cv = sk.v;
+    // live edges: (cu, cv) component labels, (u, v) original ends, w; the
+    // first round reads the skeleton itself (labels = internal ids)
+    const int32_t *ccu = sk.ru, *ccv = sk.rv, *cu = sk.u, *cv = sk.v;
     const int64_t *cw = sk.w;
-    int64_t n = sk.n;
-    int which = 0;  // next compaction target: 0 -> a buffers, 1 -> b buffers
+    int64_t n = sk.n, nr = E;
+    int32_t *roots = s.roots, *roots2 = s.roots2;
+    int which = 0;
     for (int round = 0;; round++) {
         if (round >= 64) return set_err(c, DGEC_ERR_TIMEOUT, "Boruvka did not finish in 64 rounds");
-        int64_t live;
         if (round == 0) {
-            // every node is its own component: nothing to filter, just bid
-            TK(c, "k_bid_first", k_bid_first<<<grid_for(n, kBlock, 65536), kBlock, 0, st>>>(cru, crv, cw, n, s.bw));
-            live = n;
+            TK(c, "k_bid_first", k_m_bid<<<grid_for(n, kBlock, 65536), kBlock, 0, st>>>(ccu, ccv, cw, n, s.bw));
         } else {
-            int32_t *nru = which ? s.rub : s.rua, *nrv = which ? s.rvb : s.rva;
+            int32_t *ncu = which ? s.cub : s.cua, *ncv = which ? s.cvb : s.cva;
             int32_t *nu = which ? s.ub : s.ua, *nv = which ? s.vb : s.va;
             int64_t *nw = which ? s.wb : s.wa;
             CU_TRY(c, cudaMemsetAsync(s.cnt, 0, sizeof(unsigned long long), st));
-            TK(c, "k_filter_bid", k_r_filter_bid<<<grid_for(n, kBlock, 65536), kBlock, 0, st>>>(
-                                      cru, crv, cu, cv, cw, n, s.comp, nru, nrv, nu, nv, nw, s.cnt, s.bw));
-            DG_TRY(read_counters(c, (const int64_t *)s.cnt, 1, &live));
-            if (live == 0) break;
-            cru = nru;
-            crv = nrv;
+            TK(c, "k_filter_bid", k_m_filter_bid<<<grid_for(n, kBlock, 65536), kBlock, 0, st>>>(
+                                      ccu, ccv, cu, cv, cw, n, s.par, ncu, ncv, nu, nv, nw, s.cnt, s.bw));
+            int64_t h[3];
+            DG_TRY(read_counters(c, (const int64_t *)s.cnt, 3, h));
+            n = h[0];
+            nr = h[2];
+            if (n == 0) break;
+            ccu = ncu;
+            ccv = ncv;
             cu = nu;
             cv = nv;
             cw = nw;
             which ^= 1;
         }
-        n = live;
-        TK(c, "k_bid_uv", k_r_bid_uv<<<grid_for(n, kBlock, 65536), kBlock, 0, st>>>(cru, crv, cu, cv, cw, n, s.comp,
-                                                                                  s.bw, s.buv));
-        TK(c, "k_hook", k_r_hook<<<gE, kBlock, 0, st>>>(E, s.comp, g.rank_of, s.bw, s.buv, s.par, s.tu, s.tv,
-                                                        s.tru, s.trv, s.tw, s.cnt + 1));
-        TK(c, "k_jump", k_jump<<<gE, kBlock, 0, st>>>(E, s.comp, s.par));
-        TK(c, "k_relabel", k_relabel<<<gE, kBlock, 0, st>>>(E, s.comp, s.par, s.bw, s.buv));
-        TK(c, "k_reset_best", k_reset_best<<<gE, kBlock, 0, st>>>(E, s.bw, s.buv));
+        const int gn = grid_for(n, kBlock, 65536), gr = grid_for(nr, kBlock, 65536);
+        TK(c, "k_bid_uv", k_m_bid_uv<<<gn, kBlock, 0, st>>>(ccu, ccv, cu, cv, cw, n, s.bw, s.buv));
+        TK(c, "k_claim", k_m_claim<<<gn, kBlock, 0, st>>>(ccu, ccv, cu, cv, n, s.buv, s.bp, s.win));
+        TK(c, "k_hook", k_m_hook<<<gr, kBlock, 0, st>>>(roots, nr, s.bw, s.buv, s.bp, s.win, cu, cv, cw,
+                                                        g.rank_of, s.par, s.tu, s.tv, s.tru, s.trv, s.tw,
+                                                        s.cnt + 1));
+        TK(c, "k_jump", k_m_jump<<<gr, kBlock, 0, st>>>(roots, nr, s.par));
+        CU_TRY(c, cudaMemsetAsync(s.cnt + 2, 0, sizeof(unsigned long long), st));
+        TK(c, "k_next_roots", k_m_next_roots<<<gr, kBlock, 0, st>>>(roots, nr, s.par, s.bw, s.buv, roots2,
+                                                                    s.cnt + 2));
+        int32_t *tr = roots;
+        roots = roots2;
+        roots2 = tr;
     }
     int64_t m;
     DG_TRY(read_counters(c, (const int64_t *)(s.cnt + 1), 1, &m));
