@@ -139,6 +139,32 @@ __device__ __forceinline__ int warp_agg_inc(int *counter, int key, unsigned acti
     return base + __popc(lt);
 }
 
+// Stream compaction slot through ONE atomicAdd per CTA: threads with
+// `take` get consecutive slots of `counter` (order within the CTA follows
+// thread order). Every thread of the CTA must call it the same number of
+// times (use CTA-uniform loops).
+__device__ __forceinline__ long long cta_reserve(bool take, unsigned long long *counter) {
+    __shared__ unsigned s_warp[32];
+    __shared__ unsigned long long s_base;
+    const unsigned m = __ballot_sync(0xffffffffu, take);
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane_id() == 0) s_warp[w] = __popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned tot = 0;
+        for (int i = 0; i < nw; i++) {
+            unsigned c = s_warp[i];
+            s_warp[i] = tot;
+            tot += c;
+        }
+        s_base = tot ? atomicAdd(counter, (unsigned long long)tot) : 0ull;
+    }
+    __syncthreads();
+    long long slot = (long long)(s_base + s_warp[w] + __popc(m & ((1u << lane_id()) - 1u)));
+    __syncthreads();
+    return slot;
+}
+
 // 128-bit unsigned add into (hi, lo) words; exact and order independent.
 __device__ __forceinline__ void atomic_add_u128(unsigned long long *hi,
                                                 unsigned long long *lo,
@@ -147,6 +173,25 @@ __device__ __forceinline__ void atomic_add_u128(unsigned long long *hi,
     unsigned long long old = atomicAdd(lo, add_lo);
     unsigned long long carry = (old + add_lo < old) ? 1ull : 0ull;
     if (add_hi | carry) atomicAdd(hi, add_hi + carry);
+}
+
+// Adds the 64-bit `val` of every lane in `active` to the 128-bit counter
+// (hi[key], lo[key]), summing lanes that share a key first (one atomic pair
+// per distinct key per warp). The sum is exact: values are split into 16-bit
+// limbs whose warp sums fit in 32 bits.
+__device__ __forceinline__ void warp_add_u128(unsigned active, bool has, int key, unsigned long long val,
+                                              unsigned long long *hi, unsigned long long *lo) {
+    const unsigned peers = __match_any_sync(active, has ? key : -1);
+    if (!has) return;
+    unsigned s0 = __reduce_add_sync(peers, (unsigned)(val & 0xffffu));
+    unsigned s1 = __reduce_add_sync(peers, (unsigned)((val >> 16) & 0xffffu));
+    unsigned s2 = __reduce_add_sync(peers, (unsigned)((val >> 32) & 0xffffu));
+    unsigned s3 = __reduce_add_sync(peers, (unsigned)(val >> 48));
+    if ((int)lane_id() == __ffs(peers) - 1) {
+        unsigned __int128 tot = (unsigned __int128)s0 + ((unsigned __int128)s1 << 16) +
+                                ((unsigned __int128)s2 << 32) + ((unsigned __int128)s3 << 48);
+        atomic_add_u128(&hi[key], &lo[key], (unsigned long long)(tot >> 64), (unsigned long long)tot);
+    }
 }
 
 // lambda(w) = floor((2^64 - 1) / (w + 1)) for w >= 0; 0 stands for w = inf.

@@ -159,16 +159,27 @@ __global__ void k_c_points(Gview gv, const int32_t *cpar, const int64_t *size, c
                            int32_t *fall_cluster, uint64_t *fall_lambda, unsigned long long *st_hi,
                            unsigned long long *st_lo) {
     const int64_t E = gv.E;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < E;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        const int M = gv.gM[gv.egraph[p]];
-        int64_t X = cpar[p];
-        for (int it = 0; it < kMaxWalk && X < gv.R0 && size[X - E] < M; it++) X = cpar[X];
-        int K = link[X];
-        unsigned long long L = lam_node(X, gv, w);
-        fall_cluster[p] = K;
-        fall_lambda[p] = L;
-        atomic_add_u128(&st_hi[K], &st_lo[K], 0ull, L - cbirth[K]);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < E;
+         base += stride) {  // warp-uniform
+        const int64_t p = base + lane_id();
+        const bool ok = p < E;
+        const unsigned active = 0xffffffffu;
+        int K = 0;
+        unsigned long long add = 0;
+        if (ok) {
+            const int M = gv.gM[gv.egraph[p]];
+            int64_t X = cpar[p];
+            for (int it = 0; it < kMaxWalk && X < gv.R0 && size[X - E] < M; it++) X = cpar[X];
+            K = link[X];
+            unsigned long long L = lam_node(X, gv, w);
+            fall_cluster[p] = K;
+            fall_lambda[p] = L;
+            add = L - cbirth[K];
+        }
+        // points of one cluster meet in a warp often (the big clusters):
+        // one 128-bit add per cluster per warp
+        warp_add_u128(active, ok, K, add, st_hi, st_lo);
     }
 }
 
@@ -325,9 +336,9 @@ __global__ void k_e_report(Eom e) {
 }
 
 __global__ void k_e_commit(Eom e, int32_t *alist2, unsigned long long *n_open) {
-    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < e.nact;
-         base += (int64_t)gridDim.x * blockDim.x) {
-        int64_t ix = base + lane_id();
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < e.nact;
+         base += (int64_t)gridDim.x * blockDim.x) {  // CTA-uniform
+        int64_t ix = base + threadIdx.x;
         bool open = false;
         int64_t c = 0;
         if (ix < e.nact) {
@@ -335,13 +346,8 @@ __global__ void k_e_commit(Eom e, int32_t *alist2, unsigned long long *n_open) {
             if (e.state[c]) e.done[c] = 1;
             open = !e.done[c];
         }
-        unsigned m = __ballot_sync(0xffffffffu, open);
-        if (!m) continue;
-        int leader = __ffs(m) - 1;
-        unsigned long long at = 0;
-        if ((int)lane_id() == leader) at = atomicAdd(n_open, (unsigned long long)__popc(m));
-        at = __shfl_sync(0xffffffffu, at, leader);
-        if (open) alist2[at + __popc(m & ((1u << lane_id()) - 1u))] = (int32_t)c;
+        long long at = cta_reserve(open, n_open);
+        if (open) alist2[at] = (int32_t)c;
     }
 }
 

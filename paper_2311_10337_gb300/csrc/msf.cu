@@ -199,9 +199,8 @@ __global__ void k_m_filter_bid(const int32_t *cu, const int32_t *cv, const int32
                                int32_t *cv2, int32_t *u2, int32_t *v2, int64_t *w2,
                                unsigned long long *cnt, unsigned long long *bw) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t wb = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; wb < n;
-         wb += stride) {
-        int64_t x = wb + lane_id();
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {  // CTA-uniform
+        int64_t x = base + threadIdx.x;
         bool keep = false;
         int a = 0, b = 0;
         if (x < n) {
@@ -209,14 +208,8 @@ __global__ void k_m_filter_bid(const int32_t *cu, const int32_t *cv, const int32
             b = par[cv[x]];
             keep = a != b;
         }
-        unsigned m = __ballot_sync(0xffffffffu, keep);
-        if (m == 0) continue;
-        int leader = __ffs(m) - 1;
-        unsigned long long base = 0;
-        if ((int)lane_id() == leader) base = atomicAdd(cnt, (unsigned long long)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, leader);
+        long long at = cta_reserve(keep, cnt);
         if (keep) {
-            int64_t at = (int64_t)base + __popc(m & ((1u << lane_id()) - 1u));
             unsigned long long uw = (unsigned long long)w[x];
             cu2[at] = a;
             cv2[at] = b;
@@ -271,9 +264,8 @@ __global__ void k_m_hook(const int32_t *roots, int64_t nr, const unsigned long l
                          int32_t *par, int32_t *mu, int32_t *mv, int32_t *mru, int32_t *mrv,
                          int64_t *mw, unsigned long long *n_out) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < nr;
-         base += stride) {
-        int64_t ix = base + lane_id();
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nr; base += stride) {  // CTA-uniform
+        int64_t ix = base + threadIdx.x;
         bool emit = false;
         int wx = 0;
         if (ix < nr) {
@@ -288,14 +280,8 @@ __global__ void k_m_hook(const int32_t *roots, int64_t nr, const unsigned long l
                 wx = win[x];
             }
         }
-        unsigned m = __ballot_sync(0xffffffffu, emit);
-        if (!m) continue;
-        int leader = __ffs(m) - 1;
-        unsigned long long at = 0;
-        if ((int)lane_id() == leader) at = atomicAdd(n_out, (unsigned long long)__popc(m));
-        at = __shfl_sync(0xffffffffu, at, leader);
+        long long at = cta_reserve(emit, n_out);
         if (emit) {
-            at += __popc(m & ((1u << lane_id()) - 1u));
             int a = u[wx], b = v[wx];
             mu[at] = a;
             mv[at] = b;
@@ -327,9 +313,8 @@ __global__ void k_m_next_roots(const int32_t *roots, int64_t nr, const int32_t *
                                unsigned long long *bw, unsigned long long *buv, int32_t *roots2,
                                unsigned long long *cnt) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < nr;
-         base += stride) {
-        int64_t ix = base + lane_id();
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nr; base += stride) {  // CTA-uniform
+        int64_t ix = base + threadIdx.x;
         bool keep = false;
         int x = 0;
         if (ix < nr) {
@@ -338,13 +323,8 @@ __global__ void k_m_next_roots(const int32_t *roots, int64_t nr, const int32_t *
             bw[x] = kMax64;
             buv[x] = kMax64;
         }
-        unsigned m = __ballot_sync(0xffffffffu, keep);
-        if (!m) continue;
-        int leader = __ffs(m) - 1;
-        unsigned long long at = 0;
-        if ((int)lane_id() == leader) at = atomicAdd(cnt, (unsigned long long)__popc(m));
-        at = __shfl_sync(0xffffffffu, at, leader);
-        if (keep) roots2[at + __popc(m & ((1u << lane_id()) - 1u))] = x;
+        long long at = cta_reserve(keep, cnt);
+        if (keep) roots2[at] = x;
     }
 }
 
