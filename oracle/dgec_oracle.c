@@ -18,6 +18,11 @@
  * Sec. 4.1.3). The condensed-tree / excess-of-mass step (Alg. 1 steps 4-5)
  * is defined by the paper only by citation to HDBSCAN; its pins are the
  * hand-worked golden cases under tests/golden/ and filtration invariants.
+ * The discrete dendrogram (Alg. 5) is pinned against brute-force components
+ * of the explicit line graph at every threshold; condensing it is pinned by
+ * reduction to the continuous condense (one threshold per distinct weight,
+ * and weights rounded up to coarse thresholds) and by a closed form for one
+ * level.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -573,4 +578,241 @@ int orc_condense(int64_t n_nodes, int64_t n_mst, const int32_t *a,
     return ORC_OK;
 #undef NODE_W
 #undef NODE_L
+}
+
+/* ------------------------------------------------------------------ */
+/* Alg. 5: discrete dendrogram. For each threshold omega_i (increasing),  */
+/* comps(H, omega_i) of the graph H restricted to edges of weight         */
+/* <= omega_i (reading: "<=" as in the appendix). Level i of the output   */
+/* names every node's component by its smallest member id; the tree D     */
+/* follows from the labels (component c at level i-1 has parent           */
+/* labels[i][c] at level i).                                              */
+/* ------------------------------------------------------------------ */
+
+static int32_t uf_find_min(int32_t *par, int32_t x)
+{
+    int32_t r = x;
+    while (par[r] != r) r = par[r];
+    while (par[x] != r) { int32_t nx = par[x]; par[x] = r; x = nx; }
+    return r;
+}
+
+int orc_levels(int64_t n_nodes, int64_t n_edges, const int32_t *u, const int32_t *v,
+               const int64_t *w, int32_t q, const int64_t *omega, int32_t *labels)
+{
+    int32_t *par = malloc(sizeof(int32_t) * (size_t)(n_nodes + 1));
+    if (!par) return ORC_ERR_OOM;
+    for (int32_t i = 0; i < q; i++) {
+        /* comps(H, omega_i), computed afresh for every threshold */
+        for (int64_t x = 0; x < n_nodes; x++) par[x] = (int32_t)x;
+        for (int64_t e = 0; e < n_edges; e++) {
+            if (w[e] > omega[i]) continue;
+            int32_t a = uf_find_min(par, u[e]), b = uf_find_min(par, v[e]);
+            if (a == b) continue;
+            if (a < b) par[b] = a; else par[a] = b;   /* smaller id stays the root */
+        }
+        for (int64_t x = 0; x < n_nodes; x++) labels[(int64_t)i * n_nodes + x] = uf_find_min(par, (int32_t)x);
+    }
+    free(par);
+    return ORC_OK;
+}
+
+/* The tree D of Alg. 5 in per-node form. Every component at threshold i is
+ * named by its smallest member, so a node x names a component from level 0
+ * up to the first level at which a smaller node joins its component; there
+ * the containment edge (x's component at level i-1) -> (its component at
+ * level i) is recorded as merge_level[x] = i, merge_parent[x] = the name of
+ * the level-i component. Nodes that name a component at every level get
+ * -1, -1. Levels are 0-based; "level -1" is the singletons. */
+int orc_levels_tree(int64_t n_nodes, int32_t q, const int32_t *labels,
+                    int32_t *merge_level, int32_t *merge_parent)
+{
+    for (int64_t x = 0; x < n_nodes; x++) {
+        merge_level[x] = -1;
+        merge_parent[x] = -1;
+        for (int32_t i = 0; i < q; i++) {
+            int32_t c = labels[(int64_t)i * n_nodes + x];
+            if (c != (int32_t)x) { merge_level[x] = i; merge_parent[x] = c; break; }
+        }
+    }
+    return ORC_OK;
+}
+
+/* Step 4-5 of Alg. 1 on the discrete dendrogram D (Sec. 3, condensing on
+ * the discrete dendrogram): the HDBSCAN condensed tree, stabilities and
+ * excess-of-mass selection, walked top-down over D's nodes. Nodes of D:
+ * the singletons x (id x), the components (i, c) of level i (id
+ * (i + 1) * n + c, c = smallest member) and a virtual root above the last
+ * level (id (q + 1) * n, lambda 0). Going down from a level-i node, its
+ * children are the level-(i-1) components inside it; the event happens at
+ * lambda(omega_i) = floor((2^64 - 1) / (omega_i + 1)). Conventions as in
+ * orc_condense: a cluster splits when two or more children have >= M
+ * members, the only big child otherwise carries the cluster on, small
+ * children's points fall out; stabilities in exact 128-bit arithmetic;
+ * the root is never selected; labels numbered by smallest member. The
+ * cluster table lists clusters in ascending node id. */
+int orc_condense_levels(int64_t n, int32_t q, const int64_t *omega,
+                        const int32_t *lab, int32_t M, int32_t *labels,
+                        int32_t *n_labels, int64_t *n_cl, uint64_t *cl_birth,
+                        uint64_t *cl_death, int64_t *cl_size, uint64_t *cl_stab_hi,
+                        uint64_t *cl_stab_lo, int32_t *cl_selected)
+{
+    if (M < 2 || q < 1) return ORC_ERR_ARG;
+    int64_t N = (int64_t)(q + 1) * n + 1;
+    int64_t root = N - 1;
+    char *exists = calloc((size_t)N, 1);
+    int64_t *parent = malloc(sizeof(int64_t) * (size_t)N);
+    int64_t *nsize = calloc((size_t)N, sizeof(int64_t));
+    int64_t *coff = calloc((size_t)N + 1, sizeof(int64_t));
+    int64_t *kids = malloc(sizeof(int64_t) * (size_t)N);
+    int64_t *node_cl = malloc(sizeof(int64_t) * (size_t)N);
+    int64_t *stack = malloc(sizeof(int64_t) * (size_t)N);
+    int64_t *leafstack = malloc(sizeof(int64_t) * (size_t)N);
+    int64_t *cparent = malloc(sizeof(int64_t) * (size_t)N);
+    uint64_t *cbirth = calloc((size_t)N, sizeof(uint64_t));
+    uint64_t *cdeath = calloc((size_t)N, sizeof(uint64_t));
+    int64_t *csize = calloc((size_t)N, sizeof(int64_t));
+    int32_t *sel = calloc((size_t)N, sizeof(int32_t));
+    u128 *stab = calloc((size_t)N, sizeof(u128));
+    u128 *S = calloc((size_t)N, sizeof(u128));
+    u128 *childsum = calloc((size_t)N, sizeof(u128));
+    int64_t *fall_cluster = malloc(sizeof(int64_t) * (size_t)(n + 1));
+    uint64_t *fall_lambda = malloc(sizeof(uint64_t) * (size_t)(n + 1));
+    int64_t *fin = malloc(sizeof(int64_t) * (size_t)N);
+    int32_t *minmem = malloc(sizeof(int32_t) * (size_t)N);
+    int32_t *rankof = malloc(sizeof(int32_t) * (size_t)N);
+    int64_t *clist = malloc(sizeof(int64_t) * (size_t)N);
+    if (!exists || !parent || !nsize || !coff || !kids || !node_cl || !stack || !leafstack ||
+        !cparent || !cbirth || !cdeath || !csize || !sel || !stab || !S || !childsum ||
+        !fall_cluster || !fall_lambda || !fin || !minmem || !rankof || !clist)
+        return ORC_ERR_OOM;
+#define LEVEL_NODE(i, c) ((int64_t)((i) + 1) * n + (c))
+    /* the nodes of D and their parents */
+    for (int64_t X = 0; X < N; X++) parent[X] = -1;
+    exists[root] = 1;
+    for (int64_t x = 0; x < n; x++) {
+        exists[x] = 1;
+        parent[x] = LEVEL_NODE(0, lab[x]);
+    }
+    for (int32_t i = 0; i < q; i++)
+        for (int64_t c = 0; c < n; c++) {
+            if (lab[(int64_t)i * n + c] != (int32_t)c) continue;
+            int64_t X = LEVEL_NODE(i, c);
+            exists[X] = 1;
+            parent[X] = (i + 1 < q) ? LEVEL_NODE(i + 1, lab[(int64_t)(i + 1) * n + c]) : root;
+        }
+    /* sizes: members of each component */
+    for (int64_t x = 0; x < n; x++) {
+        nsize[x] = 1;
+        for (int32_t i = 0; i < q; i++) nsize[LEVEL_NODE(i, lab[(int64_t)i * n + x])]++;
+    }
+    nsize[root] = n;
+    /* children lists */
+    for (int64_t X = 0; X < N; X++)
+        if (exists[X] && parent[X] >= 0) coff[parent[X] + 1]++;
+    for (int64_t X = 0; X < N; X++) coff[X + 1] += coff[X];
+    {
+        int64_t *f = malloc(sizeof(int64_t) * (size_t)N);
+        if (!f) return ORC_ERR_OOM;
+        memcpy(f, coff, sizeof(int64_t) * (size_t)N);
+        for (int64_t X = 0; X < N; X++)
+            if (exists[X] && parent[X] >= 0) kids[f[parent[X]]++] = X;
+        free(f);
+    }
+#define NODE_LAMBDA(X) ((X) == root ? 0u : lam(omega[(X) / n - 1]))
+    /* top-down walk from the root cluster */
+    for (int64_t X = 0; X < N; X++) node_cl[X] = -1;
+    node_cl[root] = root;
+    cparent[root] = -1; cbirth[root] = 0; csize[root] = n;
+    int64_t sp = 0;
+    stack[sp++] = root;
+    while (sp > 0) {
+        int64_t X = stack[--sp];
+        int64_t K = node_cl[X];
+        uint64_t LX = NODE_LAMBDA(X);
+        int64_t nbig = 0;
+        for (int64_t y = coff[X]; y < coff[X + 1]; y++)
+            if (nsize[kids[y]] >= M) nbig++;
+        if (nbig >= 2) cdeath[K] = LX;
+        for (int64_t y = coff[X]; y < coff[X + 1]; y++) {
+            int64_t C = kids[y];
+            if (nsize[C] >= M) {
+                if (nbig >= 2) {
+                    node_cl[C] = C;
+                    cparent[C] = K; cbirth[C] = LX; csize[C] = nsize[C];
+                } else {
+                    node_cl[C] = K;
+                }
+                stack[sp++] = C;
+            } else {
+                int64_t lp = 0;
+                leafstack[lp++] = C;
+                while (lp > 0) {
+                    int64_t Z = leafstack[--lp];
+                    if (Z < n) { fall_cluster[Z] = K; fall_lambda[Z] = LX; }
+                    else for (int64_t t = coff[Z]; t < coff[Z + 1]; t++) leafstack[lp++] = kids[t];
+                }
+            }
+        }
+    }
+    /* stabilities */
+    for (int64_t x = 0; x < n; x++)
+        stab[fall_cluster[x]] += (u128)(fall_lambda[x] - cbirth[fall_cluster[x]]);
+    int64_t ncl = 0;
+    for (int64_t X = 0; X < N; X++)
+        if (node_cl[X] == X) clist[ncl++] = X;          /* ascending: children first */
+    for (int64_t c = 0; c < ncl; c++) {
+        int64_t K = clist[c];
+        if (cparent[K] >= 0)
+            stab[cparent[K]] += (u128)csize[K] * (u128)(cdeath[cparent[K]] - cbirth[cparent[K]]);
+    }
+    /* excess of mass, bottom-up */
+    for (int64_t c = 0; c < ncl; c++) {
+        int64_t K = clist[c];
+        if (K == root) continue;
+        if (stab[K] >= childsum[K]) { sel[K] = 1; S[K] = stab[K]; }
+        else { sel[K] = 0; S[K] = childsum[K]; }
+        childsum[cparent[K]] += S[K];
+    }
+    /* final clusters: selected with no selected ancestor below the root */
+    for (int64_t c = ncl - 1; c >= 0; c--) {
+        int64_t K = clist[c];
+        if (K == root) { fin[K] = -1; continue; }
+        int64_t up = fin[cparent[K]];
+        if (up >= 0) fin[K] = up;
+        else if (sel[K]) { sel[K] = 2; fin[K] = K; }
+        else fin[K] = -1;
+    }
+    for (int64_t X = 0; X < N; X++) { minmem[X] = INT32_MAX; rankof[X] = -1; }
+    for (int64_t x = 0; x < n; x++) {
+        int64_t L = fin[fall_cluster[x]];
+        if (L >= 0 && (int32_t)x < minmem[L]) minmem[L] = (int32_t)x;
+    }
+    int32_t nlab = 0;
+    for (int64_t x = 0; x < n; x++) {
+        int64_t L = fin[fall_cluster[x]];
+        if (L >= 0 && minmem[L] == (int32_t)x) rankof[L] = nlab++;
+    }
+    for (int64_t x = 0; x < n; x++) {
+        int64_t L = fin[fall_cluster[x]];
+        labels[x] = L >= 0 ? rankof[L] : -1;
+    }
+    for (int64_t c = 0; c < ncl; c++) {
+        int64_t K = clist[c];
+        cl_birth[c] = cbirth[K];
+        cl_death[c] = cdeath[K];
+        cl_size[c] = csize[K];
+        cl_stab_hi[c] = (uint64_t)(stab[K] >> 64);
+        cl_stab_lo[c] = (uint64_t)stab[K];
+        cl_selected[c] = (K == root) ? 0 : sel[K];
+    }
+    *n_cl = ncl;
+    *n_labels = nlab;
+    free(exists); free(parent); free(nsize); free(coff); free(kids); free(node_cl);
+    free(stack); free(leafstack); free(cparent); free(cbirth); free(cdeath); free(csize);
+    free(sel); free(stab); free(S); free(childsum); free(fall_cluster); free(fall_lambda);
+    free(fin); free(minmem); free(rankof); free(clist);
+    return ORC_OK;
+#undef LEVEL_NODE
+#undef NODE_LAMBDA
 }

@@ -51,6 +51,11 @@ def lib():
             L.orc_mst.argtypes = [i64, i64, I32P, I32P, I64P, I32P, I32P, I64P]
             L.orc_mst.restype = i64
             L.orc_linkage.argtypes = [i64, i64, I32P, I32P, I32P, I32P, I64P]
+            L.orc_levels.argtypes = [i64, i64, I32P, I32P, I64P, i32, I64P, I32P]
+            L.orc_levels_tree.argtypes = [i64, i32, I32P, I32P, I32P]
+            L.orc_condense_levels.argtypes = [i64, i32, I64P, I32P, i32, I32P,
+                                              ctypes.POINTER(i32), ctypes.POINTER(i64),
+                                              U64P, U64P, I64P, U64P, U64P, I32P]
             L.orc_condense.argtypes = [i64, i64, I32P, I32P, I64P, I64P, i32,
                                        I32P, U64P, I32P, I32P, U64P, U64P, I64P,
                                        U64P, U64P, I32P, I32P,
@@ -176,3 +181,46 @@ def run(src, dst, t, n_vertices, k, M, knn_query=None):
     a, b, s = out["linkage"]
     out["condensed"] = condense(E, a, b, mw, s, M)
     return out
+
+
+def levels(n_nodes, u, v, w, omega):
+    """Alg. 5 on the graph (u, v, w): per threshold, every node's component
+    named by its smallest member; shape (len(omega), n_nodes)."""
+    u, v, w = _c(u, np.int32), _c(v, np.int32), _c(w, np.int64)
+    om = _c(omega, np.int64)
+    out = np.zeros(max(len(om) * n_nodes, 1), np.int32)
+    rc = lib().orc_levels(n_nodes, len(u), u, v, w, len(om), om, out)
+    if rc:
+        raise MemoryError("oracle levels")
+    return out[:len(om) * n_nodes].reshape(len(om), n_nodes)
+
+
+def levels_tree(labels):
+    """The tree D of Alg. 5 per node: (merge_level, merge_parent), -1 where a
+    node names its component at every level."""
+    lab = _c(labels, np.int32)
+    q, n = lab.shape
+    ml = np.zeros(max(n, 1), np.int32); mp = np.zeros(max(n, 1), np.int32)
+    lib().orc_levels_tree(n, q, lab.reshape(-1), ml, mp)
+    return ml[:n], mp[:n]
+
+
+def condense_levels(labels, omega, M):
+    """Condensed tree, excess of mass and labels on the discrete dendrogram
+    given by per-level labels (levels() output)."""
+    lab = _c(labels, np.int32)
+    q, n = lab.shape
+    om = _c(omega, np.int64)
+    N = (q + 1) * n + 1
+    out = np.zeros(max(n, 1), np.int32)
+    birth = np.zeros(N, np.uint64); death = np.zeros(N, np.uint64)
+    size = np.zeros(N, np.int64); hi = np.zeros(N, np.uint64); lo = np.zeros(N, np.uint64)
+    sel = np.zeros(N, np.int32)
+    nlab = ctypes.c_int32(0); ncl = ctypes.c_int64(0)
+    rc = lib().orc_condense_levels(n, q, om, lab.reshape(-1), M, out, ctypes.byref(nlab),
+                                   ctypes.byref(ncl), birth, death, size, hi, lo, sel)
+    if rc:
+        raise ValueError(f"oracle condense_levels rc={rc}")
+    c = ncl.value
+    return dict(labels=out[:n], n_clusters=nlab.value, cl_birth=birth[:c], cl_death=death[:c],
+                cl_size=size[:c], cl_stab_hi=hi[:c], cl_stab_lo=lo[:c], cl_selected=sel[:c])

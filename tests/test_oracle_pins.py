@@ -313,3 +313,129 @@ def test_empty_graph():
     z32 = np.zeros(0, np.int32)
     r = O.run(z32, z32, np.zeros(0, np.int64), 4, 3, 5)
     assert len(r["skeleton"][0]) == 0 and r["condensed"]["n_clusters"] == 0
+
+
+@pytest.mark.parametrize("g", GRAPHS[::3], ids=lambda g: g.name)
+def test_discrete_levels_match_line_graph(g):
+    """Alg. 5 on the skeleton gives, at every threshold, the components of
+    the explicit L_G (Thm. 3), each named by its smallest member."""
+    E = g.n_edges
+    u, v, w = O.skeleton(g.src, g.dst, g.t, g.n_vertices)
+    full = bf.undirected_edges(g.src, g.dst, g.t)
+    omega = np.array(sorted(set(full.values()) | {0, 1, 2, 4, 8}), np.int64)
+    lv = O.levels(E, u, v, w, omega)
+    for i, om in enumerate(omega.tolist()):
+        assert np.array_equal(lv[i], bf.components(E, full, om)), om
+
+
+def test_discrete_levels_nested():
+    """Levels are nested: a component at a lower threshold lies inside one
+    component at every higher threshold (the containment tree D)."""
+    g = synth.random_small(300, 20, 200, 3)
+    u, v, w = O.skeleton(g.src, g.dst, g.t, g.n_vertices)
+    omega = np.array([0, 1, 3, 7, 15, 31, 63, 127], np.int64)
+    lv = O.levels(g.n_edges, u, v, w, omega)
+    for i in range(1, len(omega)):
+        parent = {}
+        for x in range(g.n_edges):
+            assert parent.setdefault(lv[i - 1][x], lv[i][x]) == lv[i][x]
+
+
+def _cluster_rows(d):
+    """Cluster table as a sorted list of (birth, death, size, stability,
+    selected): ids are numbering conventions, these values are not."""
+    rows = zip(d["cl_birth"].tolist(), d["cl_death"].tolist(), d["cl_size"].tolist(),
+               d["cl_stab_hi"].tolist(), d["cl_stab_lo"].tolist(), d["cl_selected"].tolist())
+    return sorted(rows)
+
+
+def _continuous(g, M, rounding=None):
+    """Alg. 1 on the skeleton; with `rounding`, every weight is first
+    replaced by the smallest threshold >= it and edges above the last
+    threshold are dropped."""
+    E = g.n_edges
+    u, v, w = O.skeleton(g.src, g.dst, g.t, g.n_vertices)
+    if rounding is not None:
+        om = np.asarray(rounding, np.int64)
+        b = np.searchsorted(om, w, side="left")
+        keep = b < len(om)
+        u, v, w = u[keep], v[keep], om[b[keep]]
+    mu, mv, mw = O.mst(E, u, v, w)
+    a, bb, s = O.linkage(E, mu, mv)
+    return O.condense(E, a, bb, mw, s, M)
+
+
+@pytest.mark.parametrize("g", GRAPHS[::4], ids=lambda g: g.name)
+@pytest.mark.parametrize("M", [2, 3, 5])
+def test_discrete_condense_full_resolution(g, M):
+    """With one threshold per distinct weight of L*, the discrete dendrogram
+    loses nothing (Sec. 3): condensing it gives the continuous result."""
+    u, v, w = O.skeleton(g.src, g.dst, g.t, g.n_vertices)
+    if len(w) == 0:
+        pytest.skip("no skeleton edges")
+    omega = np.unique(w)
+    lv = O.levels(g.n_edges, u, v, w, omega)
+    d = O.condense_levels(lv, omega, M)
+    c = _continuous(g, M)
+    assert np.array_equal(d["labels"], c["labels"])
+    assert d["n_clusters"] == c["n_clusters"]
+    assert _cluster_rows(d) == _cluster_rows(c)
+
+
+@pytest.mark.parametrize("g", GRAPHS[1::4], ids=lambda g: g.name)
+@pytest.mark.parametrize("omega", [[0, 2, 9], [1, 4, 16, 64], [3], [0, 1, 2, 3, 5, 8, 13, 21]])
+def test_discrete_condense_is_rounded_continuous(g, omega):
+    """Coarse thresholds: the discrete dendrogram is the single-linkage
+    dendrogram of weights rounded up to the next threshold (edges above the
+    last one never join), so both condense to the same clusters."""
+    u, v, w = O.skeleton(g.src, g.dst, g.t, g.n_vertices)
+    om = np.array(omega, np.int64)
+    lv = O.levels(g.n_edges, u, v, w, om)
+    d = O.condense_levels(lv, om, 3)
+    c = _continuous(g, 3, rounding=om)
+    assert np.array_equal(d["labels"], c["labels"])
+    assert _cluster_rows(d) == _cluster_rows(c)
+
+
+def test_discrete_condense_one_level_closed_form():
+    """One level above every weight: the clusters are the components of L*
+    with >= M members (when there are two or more of them), each born at
+    lambda 0 with stability |C| * lambda(omega_1)."""
+    lam = lambda x: (2**64 - 1) // (x + 1)
+    for seed in range(6):
+        g = synth.random_small(90, 40, 50, 100 + seed)
+        u, v, w = O.skeleton(g.src, g.dst, g.t, g.n_vertices)
+        om = np.array([int(w.max()) + 7 if len(w) else 7], np.int64)
+        lv = O.levels(g.n_edges, u, v, w, om)
+        M = 4
+        d = O.condense_levels(lv, om, M)
+        comp = bf.components(g.n_edges, {(a, b): x for a, b, x in zip(u.tolist(), v.tolist(), w.tolist())}, INF)
+        sizes = np.bincount(comp, minlength=g.n_edges)
+        big = [c for c in range(g.n_edges) if sizes[c] >= M]
+        want = np.full(g.n_edges, -1, np.int32)
+        if len(big) >= 2:
+            for r, c in enumerate(sorted(big)):      # a component's name is its smallest member
+                want[comp == c] = r
+            stab = [int(sizes[c]) * lam(int(om[0])) for c in big]      # exact, may pass 2^64
+            rows = [(0, 0, int(sizes[c]), s >> 64, s & (2**64 - 1), 2) for c, s in zip(big, stab)]
+            assert [r for r in _cluster_rows(d) if r[2] < g.n_edges] == sorted(rows)
+        assert np.array_equal(d["labels"], want), seed
+
+
+@pytest.mark.parametrize("g", GRAPHS[2::5], ids=lambda g: g.name)
+def test_levels_tree(g):
+    """D per node: x stops naming its component exactly at the first level
+    whose component has a smaller member, and is then inside the component
+    named merge_parent; per level the names are the nodes not yet merged."""
+    u, v, w = O.skeleton(g.src, g.dst, g.t, g.n_vertices)
+    omega = np.array([0, 1, 2, 4, 8, 16], np.int64)
+    lv = O.levels(g.n_edges, u, v, w, omega)
+    ml, mp = O.levels_tree(lv)
+    full = bf.undirected_edges(g.src, g.dst, g.t)
+    for i, om in enumerate(omega.tolist()):
+        comp = bf.components(g.n_edges, full, om)
+        names = set(int(c) for c in comp)
+        assert names == {x for x in range(g.n_edges) if ml[x] == -1 or ml[x] > i}
+        for x in range(g.n_edges):
+            if ml[x] == i:
+                assert mp[x] == comp[x] and mp[x] < x
