@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrivals per second")
     ap.add_argument("--serve-lanes", type=int, default=3)
     ap.add_argument("--serve-pool-gb", type=float, default=72.0)
+    ap.add_argument("--no-levels", action="store_true",
+                    help="skip the discrete-dendrogram (Alg. 5) measurement")
     ap.add_argument("--breakdown", action="store_true",
                     help="also time every kernel in one extra (untimed) step")
     return ap.parse_args()
@@ -178,6 +180,44 @@ def batched_vs_plain(ctx, n_graphs, steps):
             "batched_edges_per_s": total / tb, "batched_ms": 1000 * tb,
             "one_run_per_graph_edges_per_s": total / tp, "one_run_per_graph_ms": 1000 * tp,
             "speedup": tp / tb, "identical_labels": same}
+
+
+def discrete_levels(ctx, src, dst, tt, w, steps, breakdown=False):
+    """Edges/s of the discrete-dendrogram path (Alg. 5: incidence lists,
+    skeleton, components at omega = 2^0 .. 2^28 s and the tree D), alone
+    and with condensing on D (M of the workload); inputs resident."""
+    import torch
+    omega = np.array([2 ** i for i in range(29)], np.int64)
+    E, V, M = w.n_edges, w.n_vertices, w.min_cluster_size
+    stream = torch.cuda.current_stream()
+    res = {"thresholds": "2^0 .. 2^28 (29 levels)"}
+    for name, m in (("levels", 0), ("levels_condensed", M)):
+        out = ctx.run_levels(src, dst, tt, V, omega, m)
+        launches = ctx.launches()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            out = ctx.run_levels(src, dst, tt, V, omega, m)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        res[name] = {"edges_per_s": E / (ms / 1000.0), "ms": ms, "gpu_launches_per_run": launches}
+        if m:
+            res[name]["n_clusters"] = out.n_clusters
+        else:
+            nc = out.numpy("n_components")
+            res["n_merges"] = out.n_merges
+            res["components_at"] = {"1s": int(nc[0]), "2^10s": int(nc[10]), "2^20s": int(nc[20]),
+                                    "2^28s": int(nc[28])}
+    if breakdown:
+        ctx.set_kernel_timing(2)
+        ctx.run_levels(src, dst, tt, V, omega, M)
+        res["kernel_breakdown_ms"] = {n: [round(v[0], 3), v[1]] for n, v in
+                                      sorted(ctx.kernel_timing().items(), key=lambda kv: -kv[1][0])}
+        ctx.set_kernel_timing(0)
+    return res
 
 
 def serving(w, src, dst, tt, args):
@@ -341,6 +381,9 @@ def main():
             e2e_s = float(tm.item())
         e2e = {"value": world * E / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * E,
                "d2h_bytes_per_step": 4 * E}
+    levels = None
+    if not args.no_levels and rank == 0:
+        levels = discrete_levels(ctx, src, dst, tt, w, max(1, min(args.steps, 3)), args.breakdown)
     batch = None
     if args.batch_graphs > 0 and rank == 0:
         batch = batched_vs_plain(ctx, args.batch_graphs, max(1, min(args.steps, 3)))
@@ -373,7 +416,8 @@ def main():
                            "edges_per_gpu": E, "parallelism": "replicas only",
                            "l2": "inputs (16 B/edge = %.0f MB) exceed L2; no flush" % (16 * E / 1e6),
                            "n_clusters": n_clusters},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "batch": batch, "serve": serve,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "discrete_dendrogram": levels,
+                "batch": batch, "serve": serve,
                 "gpu_launches": launches * args.steps, "clocks": clk}
         if args.breakdown:
             line["kernel_breakdown_ms"] = {n: [round(v[0], 3), v[1]] for n, v in

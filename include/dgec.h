@@ -275,6 +275,71 @@ dgec_status dgec_msf_static(const int32_t *d_u, const int32_t *d_v, const int64_
                             int32_t *d_mst_v, int64_t *d_mst_w, int64_t *h_n_mst,
                             void *cuda_stream);
 
+/* ---------------------------------------------------------------------
+ * Discrete dendrogram (Alg. 5, Sec. 3).
+ *
+ * Given thresholds omega_0 < omega_1 < ... < omega_{q-1}, level i is the
+ * partition comps(L*_G, omega_i) of the edges: two edges share a component
+ * when a path of skeleton links of weight <= omega_i joins them (Alg. 5
+ * writes "less than"; the appendix's "<=" is used, so a threshold equal to
+ * a weight admits it). By Thm. 3 these are the components of L_G itself.
+ * Components are named by their smallest member edge id; levels are nested
+ * and D is the tree of containments between consecutive levels.
+ *
+ * D in per-edge form: edge x names its component at every level below
+ * merge_level[x]; at level merge_level[x] its component becomes part of the
+ * component named merge_parent[x] (< x). Both are -1 for an edge that names
+ * its component at every level. The label of x at level i is found by
+ * following merge_parent while merge_level <= i.
+ *
+ * With min_cluster_size M >= 2, the HDBSCAN condensed tree is built on D
+ * (Sec. 3, condensing on the discrete dendrogram): every event of level i
+ * happens at lambda(omega_i) = floor((2^64 - 1) / (omega_i + 1)), a
+ * virtual root at lambda 0 joins the last level's components, and the
+ * excess-of-mass selection and labels follow the conventions of dgec_run
+ * (-1 noise, clusters numbered by smallest member, root never selected).
+ * --------------------------------------------------------------------- */
+#define DGEC_MAX_LEVELS 64
+#define DGEC_LEVELS_DENSE 1u  /* also write every level's labels */
+
+typedef struct {
+    int32_t n_levels;          /* q, 1 <= q <= DGEC_MAX_LEVELS */
+    const int64_t *h_omega;    /* host int64[q], 0 <= omega_0 < omega_1 < ... */
+    int32_t min_cluster_size;  /* 0: no condensing; else M >= 2 */
+    uint32_t flags;            /* 0 or DGEC_LEVELS_DENSE */
+} dgec_levels_params;
+
+/* Results of dgec_run_levels: device arrays in the caller's workspace,
+ * valid until it is reused; counts are host values. */
+typedef struct {
+    const int32_t *sk_u, *sk_v;       /* skeleton, as in dgec_result */
+    const int64_t *sk_w;
+    const int32_t *merge_level;       /* [n_edges] */
+    const int32_t *merge_parent;      /* [n_edges] */
+    const int64_t *n_components;      /* [q] components at each level */
+    const int32_t *level_labels;      /* [q * n_edges], row i = level i; NULL without DGEC_LEVELS_DENSE */
+    const int32_t *labels;            /* [n_edges] condensed labels; NULL when M == 0 */
+    int64_t n_skeleton;
+    int64_t n_merges;                 /* edges of D = n_edges - components at the last level */
+    int32_t n_clusters;
+} dgec_levels_result;
+
+/* Bytes of device workspace dgec_run_levels needs. */
+dgec_status dgec_levels_workspace_size(int64_t n_edges, int32_t n_vertices,
+                                       const dgec_levels_params *params, size_t *bytes);
+
+/*
+ * Incidence lists, skeleton (Alg. 2-3), the discrete dendrogram D (Alg. 5)
+ * and, when M >= 2, its condensed labels, on device-resident edges (same
+ * input rules as dgec_run; no kNN lists are computed). Thresholds that are
+ * not strictly increasing, negative, or more than DGEC_MAX_LEVELS give
+ * DGEC_ERR_INVALID_ARG. Fills *out.
+ */
+dgec_status dgec_run_levels(dgec_ctx *ctx, const int32_t *d_src, const int32_t *d_dst,
+                            const int64_t *d_t, int64_t n_edges, int32_t n_vertices,
+                            const dgec_levels_params *params, void *d_workspace,
+                            size_t ws_bytes, void *cuda_stream, dgec_levels_result *out);
+
 #ifdef __cplusplus
 }
 #endif

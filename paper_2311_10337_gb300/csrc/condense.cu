@@ -67,23 +67,86 @@ __global__ void k_c_up(int64_t E, int64_t n, const int32_t *parent, const int64_
     }
 }
 
-// Walk a pointer array to its fixed point, compressing the start pointer.
-__device__ __forceinline__ int walk_to_fixed(int32_t *ptr, int x) {
-    int r = ptr[x];
-    for (int it = 0; it < kMaxWalk; it++) {  // bounded: pointers form a forest
-        int rr = ptr[r];
-        if (rr == r) break;
-        r = rr;
-        ptr[x] = r;
+// One round of in-place pointer jumping over the pointers selected by
+// `Sel`: ptr[x] = ptr[ptr[x]]. Pointers only move to ancestors and fixed
+// points are never written, so reading a neighbour's new or old value is
+// equally valid, and every distance to the fixed point at least halves per
+// round. *moved is set when any pointer changed.
+struct SelAll {
+    __device__ bool operator()(int64_t) const { return true; }
+};
+struct SelBigRep {  // big kept merges (the nodes whose cluster link is set)
+    Gview gv;
+    const int *isrep;
+    const int64_t *size;
+    __device__ bool operator()(int64_t s) const {
+        return isrep[s] && size[s] >= gv.gM[graph_of(gv, gv.E + s)];
     }
-    return r;
+};
+template <class Sel>
+__global__ void k_c_jump(int64_t n, int64_t off, Sel sel, int32_t *ptr, unsigned long long *moved) {
+    bool any = false;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        if (!sel(s)) continue;
+        const int64_t x = off + s;
+        const int p = *(volatile int32_t *)(ptr + x);
+        const int pp = *(volatile int32_t *)(ptr + p);
+        if (pp != p) {
+            *(volatile int32_t *)(ptr + x) = pp;
+            any = true;
+        }
+    }
+    if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(moved, 1ull);
 }
 
-__global__ void k_c_top(int64_t n, int32_t *up) {
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
-         s += (int64_t)gridDim.x * blockDim.x)
-        walk_to_fixed(up, (int)s);
+// One pass of start-compressing walks, in descending index order: parents
+// have larger ids than their children, so ancestors tend to be resolved
+// first and later walks stop after a few steps. A walk that exceeds
+// kTopWalk steps stores the ancestor it reached and flags *moved.
+constexpr int kTopWalk = 1 << 12;
+template <class Sel>
+__global__ void k_c_top(int64_t n, int64_t off, Sel sel, int32_t *ptr, unsigned long long *moved) {
+    bool cut = false;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = n - 1 - t;
+        if (!sel(s)) continue;
+        const int64_t x = off + s;
+        int r = ptr[x];
+        int it = 0;
+        for (; it < kTopWalk; it++) {
+            const int rr = ptr[r];
+            if (rr == r) break;
+            r = rr;
+            ptr[x] = r;
+        }
+        cut |= it == kTopWalk;
+    }
+    if (__syncthreads_or(cut) && threadIdx.x == 0) atomicOr(moved, 1ull);
 }
+
+// Every selected pointer to its fixed point: one walk pass, then jumping
+// rounds (checked every two) only if some walk was cut short.
+template <class Sel>
+static dgec_status jump_to_fixed(Ctx *c, int64_t n, int64_t off, Sel sel, int32_t *ptr,
+                                 unsigned long long *moved) {
+    if (n <= 0) return DGEC_OK;
+    const int g = grid_for(n, kBlock, 65536);
+    CU_TRY(c, cudaMemsetAsync(moved, 0, sizeof(unsigned long long), c->stream));
+    TK(c, "k_c_top", k_c_top<Sel><<<g, kBlock, 0, c->stream>>>(n, off, sel, ptr, moved));
+    int64_t m;
+    DG_TRY(read_counters(c, (const int64_t *)moved, 1, &m));
+    for (int it = 0; m && it < 128; it += 2) {
+        CU_TRY(c, cudaMemsetAsync(moved, 0, sizeof(unsigned long long), c->stream));
+        TK(c, "k_c_jump", k_c_jump<Sel><<<g, kBlock, 0, c->stream>>>(n, off, sel, ptr, moved));
+        TK(c, "k_c_jump", k_c_jump<Sel><<<g, kBlock, 0, c->stream>>>(n, off, sel, ptr, moved));
+        DG_TRY(read_counters(c, (const int64_t *)moved, 1, &m));
+    }
+    if (m) return set_err(c, DGEC_ERR_TIMEOUT, "pointer jumping did not converge");
+    return DGEC_OK;
+}
+
 
 // collapsed parent of every leaf and kept merge; nbig counts big children
 __global__ void k_c_cpar(Gview gv, const int32_t *parent, const int32_t *up, const int *isrep,
@@ -117,14 +180,6 @@ __global__ void k_c_link(Gview gv, const int *isrep, const int64_t *size, const 
     }
 }
 
-__global__ void k_c_cl(Gview gv, const int *isrep, const int64_t *size, int32_t *link) {
-    const int64_t E = gv.E;
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < gv.n;
-         s += (int64_t)gridDim.x * blockDim.x) {
-        if (!isrep[s] || size[s] < gv.gM[graph_of(gv, E + s)]) continue;
-        walk_to_fixed(link, (int)(E + s));
-    }
-}
 
 // cluster records, indexed by node id
 __global__ void k_c_clusters(Gview gv, const int *isrep, const int64_t *size, const int64_t *w,
@@ -499,7 +554,7 @@ struct CScratch {
     int32_t *up, *cpar, *link, *cparent, *clist, *cidx, *par, *ucand, *nxt, *nxt2, *H, *J, *H2, *J2,
         *rank, *al1, *al2;
     int *isrep, *nbig, *isc, *pending, *done, *state, *minmem, *flag;
-    unsigned long long *cbirth, *cdeath, *st_hi, *st_lo, *acc_hi, *acc_lo, *cnt, *k1, *k2, *v1, *v2;
+    unsigned long long *cbirth, *cdeath, *st_hi, *st_lo, *acc_hi, *acc_lo, *cnt, *k1, *k2, *v1, *v2, *jflag;
     long long *cpos, *scan_tmp;
     int64_t *gstart;
     u128 *stab, *S, *Fa, *Fc, *Fa2, *Fc2;
@@ -549,6 +604,7 @@ static CScratch carve_condense(Arena &a, const Problem &p) {
     s.al1 = a.take<int32_t>(E + p.G + 1);
     s.al2 = a.take<int32_t>(E + p.G + 1);
     s.cnt = a.take<unsigned long long>(4);
+    s.jflag = a.take<unsigned long long>(1);
     s.k1 = a.take<unsigned long long>(E + p.G + 1);
     s.k2 = a.take<unsigned long long>(E + p.G + 1);
     s.v1 = a.take<unsigned long long>(E + p.G + 1);
@@ -588,11 +644,11 @@ dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro 
     CU_TRY(c, cudaMemsetAsync(s.st_lo, 0, sizeof(unsigned long long) * N, st));
     if (n > 0) {
         TK(c, "k_c_up", k_c_up<<<gn, kBlock, 0, st>>>(E, n, d.parent, m.w, s.up, s.isrep));
-        TK(c, "k_c_top", k_c_top<<<gn, kBlock, 0, st>>>(n, s.up));
+        DG_TRY(jump_to_fixed(c, n, 0, SelAll{}, s.up, s.jflag));
     }
     TK(c, "k_c_cpar", k_c_cpar<<<gN, kBlock, 0, st>>>(gv, d.parent, s.up, s.isrep, d.size, s.cpar, s.nbig));
     TK(c, "k_c_link", k_c_link<<<gn, kBlock, 0, st>>>(gv, s.isrep, d.size, s.cpar, s.nbig, s.link));
-    TK(c, "k_c_cl", k_c_cl<<<gn, kBlock, 0, st>>>(gv, s.isrep, d.size, s.link));
+    DG_TRY(jump_to_fixed(c, n, E, SelBigRep{gv, s.isrep, d.size}, s.link, s.jflag));
     TK(c, "k_c_clusters", k_c_clusters<<<gn, kBlock, 0, st>>>(gv, s.isrep, d.size, m.w, s.cpar, s.nbig, s.link,
                                                              s.isc, s.cbirth, s.cdeath, s.cparent));
     TK(c, "k_c_points", k_c_points<<<gE, kBlock, 0, st>>>(gv, s.cpar, d.size, m.w, s.link, s.cbirth,

@@ -4,7 +4,7 @@
 
 #include <algorithm>
 
-#include "stages.cuh"
+#include "levels.cuh"
 
 using namespace dgec;
 
@@ -124,6 +124,32 @@ __global__ void k_localize(int64_t n, int64_t E, const int32_t *mu, const int32_
     }
 }
 
+// Per-graph tables, staged through host arrays, one copy each.
+dgec_status upload_tables(Ctx *c, const HostBatch &hb, int64_t *eoff, int64_t *voff, int64_t *knn_off,
+                          int32_t *gk, int32_t *gM) {
+    int G = hb.G;
+    int64_t *hv = (int64_t *)malloc(sizeof(int64_t) * (3 * (size_t)(G + 1)));
+    if (!hv) return set_err(c, DGEC_ERR_OOM, "host memory");
+    int64_t *hvoff = hv, *hknn = hv + (G + 1), *heoff = hv + 2 * (G + 1);
+    hvoff[0] = 0;
+    hknn[0] = 0;
+    for (int g = 0; g < G; g++) {
+        heoff[g] = hb.eoff[g];
+        hvoff[g + 1] = hvoff[g] + hb.nv[g];
+        hknn[g + 1] = hknn[g] + (hb.eoff[g + 1] - hb.eoff[g]) * hb.k[g];
+    }
+    heoff[G] = hb.eoff[G];
+    cudaError_t e1 = cudaMemcpyAsync(eoff, heoff, sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e2 = cudaMemcpyAsync(voff, hvoff, sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e3 = cudaMemcpyAsync(knn_off, hknn, sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e4 = cudaMemcpyAsync(gk, hb.k, sizeof(int32_t) * G, cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e5 = cudaMemcpyAsync(gM, hb.M, sizeof(int32_t) * G, cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e6 = cudaStreamSynchronize(c->stream);
+    free(hv);
+    if (e1 || e2 || e3 || e4 || e5 || e6) return set_err(c, DGEC_ERR_CUDA, "copying the batch tables failed");
+    return DGEC_OK;
+}
+
 dgec_status run_pipeline(Ctx *c, const HostBatch &hb, const int32_t *d_src, const int32_t *d_dst,
                          const int64_t *d_t, void *d_ws, size_t ws_bytes, Layout *out_layout,
                          Problem *out_problem) {
@@ -137,29 +163,7 @@ dgec_status run_pipeline(Ctx *c, const HostBatch &hb, const int32_t *d_src, cons
     size_t need = plan(nullptr, p).total;
     if (ws_bytes < need) return set_err(c, DGEC_ERR_OOM, "workspace %zu bytes < %zu needed", ws_bytes, need);
     Layout L = plan(d_ws, p);
-    // per-graph tables: staged through host arrays, one copy each
-    {
-        int G = hb.G;
-        int64_t *hv = (int64_t *)malloc(sizeof(int64_t) * (3 * (size_t)(G + 1)));
-        if (!hv) return set_err(c, DGEC_ERR_OOM, "host memory");
-        int64_t *hvoff = hv, *hknn = hv + (G + 1), *heoff = hv + 2 * (G + 1);
-        hvoff[0] = 0;
-        hknn[0] = 0;
-        for (int g = 0; g < G; g++) {
-            heoff[g] = hb.eoff[g];
-            hvoff[g + 1] = hvoff[g] + hb.nv[g];
-            hknn[g + 1] = hknn[g] + (hb.eoff[g + 1] - hb.eoff[g]) * hb.k[g];
-        }
-        heoff[G] = hb.eoff[G];
-        cudaError_t e1 = cudaMemcpyAsync(L.eoff, heoff, sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, c->stream);
-        cudaError_t e2 = cudaMemcpyAsync(L.voff, hvoff, sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, c->stream);
-        cudaError_t e3 = cudaMemcpyAsync(L.knn_off, hknn, sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, c->stream);
-        cudaError_t e4 = cudaMemcpyAsync(L.gk, hb.k, sizeof(int32_t) * G, cudaMemcpyHostToDevice, c->stream);
-        cudaError_t e5 = cudaMemcpyAsync(L.gM, hb.M, sizeof(int32_t) * G, cudaMemcpyHostToDevice, c->stream);
-        cudaError_t e6 = cudaStreamSynchronize(c->stream);
-        free(hv);
-        if (e1 || e2 || e3 || e4 || e5 || e6) return set_err(c, DGEC_ERR_CUDA, "copying the batch tables failed");
-    }
+    DG_TRY(upload_tables(c, hb, L.eoff, L.voff, L.knn_off, L.gk, L.gM));
     p.eoff = L.eoff;
     p.voff = L.voff;
     p.knn_off = L.knn_off;
@@ -216,6 +220,80 @@ void fill_result(const Layout &L, dgec_result *out) {
     out->n_mst = L.msf.n;
     out->n_condensed = L.cond.n_cl;
     out->n_clusters = L.cond.n_clusters;
+}
+
+
+// ------------------------------------------------- discrete dendrogram run
+
+struct LvLayout {
+    int64_t *eoff, *voff, *knn_off;
+    int32_t *gk, *gM, *egraph;
+    Csr csr;
+    Skel skel;
+    Levels lv;
+    Dendro den;
+    Condensed cond;
+    void *scratch = nullptr;
+    size_t total = 0;
+};
+
+LvLayout plan_lv(void *base, const Problem &p, int q, bool dense, bool condense) {
+    LvLayout L;
+    Arena a(base, SIZE_MAX);
+    L.eoff = a.take<int64_t>(2);
+    L.voff = a.take<int64_t>(2);
+    L.knn_off = a.take<int64_t>(2);
+    L.gk = a.take<int32_t>(1);
+    L.gM = a.take<int32_t>(1);
+    L.egraph = a.take<int32_t>(p.E);
+    plan_csr(a, p, L.csr);
+    plan_skel(a, p, L.skel);
+    plan_levels(a, p, q, dense, L.lv);
+    size_t scr = std::max({csr_scratch_bytes(p), skel_scratch_bytes(p), levels_scratch_bytes(p)});
+    if (condense) {
+        plan_dendro(a, p, L.den);
+        plan_condensed(a, p, L.cond);
+        scr = std::max({scr, dendro_scratch_bytes(p), condense_scratch_bytes(p)});
+    }
+    L.scratch = a.take<char>(scr);
+    L.total = a.off + 256;
+    return L;
+}
+
+dgec_status check_levels(Ctx *c, const dgec_levels_params *lp) {
+    if (!lp) return set_err(c, DGEC_ERR_INVALID_ARG, "params is null");
+    if (lp->n_levels < 1 || lp->n_levels > kMaxLevels)
+        return set_err(c, DGEC_ERR_INVALID_ARG, "n_levels must be in [1, %d]", kMaxLevels);
+    if (!lp->h_omega) return set_err(c, DGEC_ERR_INVALID_ARG, "thresholds are null");
+    for (int i = 0; i < lp->n_levels; i++) {
+        if (lp->h_omega[i] < 0) return set_err(c, DGEC_ERR_INVALID_ARG, "threshold %d is negative", i);
+        if (i > 0 && lp->h_omega[i] <= lp->h_omega[i - 1])
+            return set_err(c, DGEC_ERR_INVALID_ARG, "thresholds must be strictly increasing");
+    }
+    if (lp->min_cluster_size != 0 && lp->min_cluster_size < 2)
+        return set_err(c, DGEC_ERR_INVALID_ARG, "min_cluster_size must be 0 or >= 2");
+    if (lp->flags & ~DGEC_LEVELS_DENSE) return set_err(c, DGEC_ERR_INVALID_ARG, "unknown flags");
+    return DGEC_OK;
+}
+
+// The batch-of-one description the stages expect; k is unused (no kNN).
+struct LvDesc {
+    int64_t eoff[2];
+    int32_t nv, k = 1, M;
+    HostBatch hb() const { return HostBatch{1, eoff, &nv, &k, &M}; }
+};
+LvDesc lv_desc(int64_t E, int32_t V, const dgec_levels_params *lp) {
+    LvDesc d;
+    d.eoff[0] = 0;
+    d.eoff[1] = E;
+    d.nv = V;
+    d.M = lp->min_cluster_size ? lp->min_cluster_size : 2;
+    return d;
+}
+Problem lv_problem(const LvDesc &d) {
+    Problem p = make_problem(d.hb());
+    p.knn = false;
+    return p;
 }
 
 }  // namespace
@@ -414,6 +492,78 @@ dgec_status dgec_run_host(dgec_ctx *x, const int32_t *h_src, const int32_t *h_ds
         CU_TRY(c, cudaStreamSynchronize(st));
     }
     if (h_n_clusters) *h_n_clusters = r.n_clusters;
+    return DGEC_OK;
+}
+
+dgec_status dgec_levels_workspace_size(int64_t n_edges, int32_t n_vertices, const dgec_levels_params *params,
+                                       size_t *bytes) {
+    if (!bytes || n_edges < 0) return DGEC_ERR_INVALID_ARG;
+    DG_TRY(check_levels(nullptr, params));
+    LvDesc d = lv_desc(n_edges, n_vertices, params);
+    DG_TRY(check_batch(nullptr, d.hb()));
+    *bytes = plan_lv(nullptr, lv_problem(d), params->n_levels, params->flags & DGEC_LEVELS_DENSE,
+                     params->min_cluster_size != 0)
+                 .total;
+    return DGEC_OK;
+}
+
+dgec_status dgec_run_levels(dgec_ctx *x, const int32_t *d_src, const int32_t *d_dst, const int64_t *d_t,
+                            int64_t n_edges, int32_t n_vertices, const dgec_levels_params *params, void *d_ws,
+                            size_t ws_bytes, void *stream, dgec_levels_result *out) {
+    if (!x) return DGEC_ERR_INVALID_ARG;
+    Ctx *c = &x->c;
+    c->msg[0] = 0;
+    c->launches = 0;
+    if (!out) return set_err(c, DGEC_ERR_INVALID_ARG, "out is null");
+    if (n_edges < 0) return set_err(c, DGEC_ERR_INVALID_ARG, "negative size");
+    DG_TRY(check_levels(c, params));
+    LvDesc d = lv_desc(n_edges, n_vertices, params);
+    DG_TRY(check_batch(c, d.hb()));
+    if (n_edges > 0 && (!d_src || !d_dst || !d_t)) return set_err(c, DGEC_ERR_INVALID_ARG, "null input");
+    if (!d_ws || ((uintptr_t)d_ws & 255))
+        return set_err(c, DGEC_ERR_INVALID_ARG, "workspace null or not 256-byte aligned");
+    CU_TRY(c, cudaSetDevice(c->device));
+    c->stream = (cudaStream_t)stream;
+    memset(out, 0, sizeof(*out));
+    const int q = params->n_levels;
+    const bool dense = params->flags & DGEC_LEVELS_DENSE, condense = params->min_cluster_size != 0;
+    Problem p = lv_problem(d);
+    size_t need = plan_lv(nullptr, p, q, dense, condense).total;
+    if (ws_bytes < need) return set_err(c, DGEC_ERR_OOM, "workspace %zu bytes < %zu needed", ws_bytes, need);
+    LvLayout L = plan_lv(d_ws, p, q, dense, condense);
+    p.src = d_src;
+    p.dst = d_dst;
+    p.t = d_t;
+    HostBatch hb = d.hb();
+    DG_TRY(upload_tables(c, hb, L.eoff, L.voff, L.knn_off, L.gk, L.gM));
+    p.eoff = L.eoff;
+    p.voff = L.voff;
+    p.knn_off = L.knn_off;
+    p.gk = L.gk;
+    p.gM = L.gM;
+    p.egraph = L.egraph;
+    DG_TRY(stage_csr(c, p, L.csr, L.scratch));
+    DG_TRY(stage_skeleton(c, p, L.csr, L.skel, L.scratch));
+    DG_TRY(stage_levels(c, p, L.skel, params->h_omega, L.lv, L.scratch));
+    if (condense) {
+        DG_TRY(build_level_rows(c, p, L.csr, L.lv, L.scratch));
+        DG_TRY(stage_dendro(c, p, L.csr, L.lv.rows, L.den, L.scratch));
+        DG_TRY(stage_condense(c, p, L.lv.rows, L.den, L.cond, L.scratch));
+    }
+    CU_TRY(c, cudaStreamSynchronize(c->stream));
+    CU_TRY(c, cudaGetLastError());
+    kt_collect(c);
+    out->sk_u = L.skel.u;
+    out->sk_v = L.skel.v;
+    out->sk_w = L.skel.w;
+    out->n_skeleton = L.skel.n;
+    out->merge_level = L.lv.mlevel;
+    out->merge_parent = L.lv.mparent;
+    out->n_components = L.lv.ncomp;
+    out->level_labels = L.lv.dense;
+    out->n_merges = L.lv.n_merges;
+    out->labels = condense ? L.cond.labels : nullptr;
+    out->n_clusters = condense ? L.cond.n_clusters : 0;
     return DGEC_OK;
 }
 

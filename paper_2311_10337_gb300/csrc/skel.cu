@@ -257,6 +257,21 @@ __global__ void __launch_bounds__(128) k_ranks_knn(const int32_t *src, const int
     }
 }
 
+// The ranks alone, for runs that do not want the kNN lists.
+__global__ void __launch_bounds__(128) k_ranks(const int32_t *src, const int32_t *dst, const int64_t *t,
+                                               int64_t E, const int64_t *out_off, const int64_t *out_t,
+                                               const int64_t *in_off, const int64_t *in_t, int32_t *brank,
+                                               int32_t *arank) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < E;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int i = src[r], j = dst[r];
+        const long long te = t[r];
+        const int64_t ib = in_off[i], ob = out_off[j];
+        brank[r] = (int32_t)upper_bound_t(in_t + ib, in_off[i + 1] - ib, te);
+        arank[r] = (int32_t)lower_bound_t(out_t + ob, out_off[j + 1] - ob, te);
+    }
+}
+
 void plan_skel(Arena &ws, const Problem &p, Skel &o) {
     o.brank = ws.take<int32_t>(p.E);
     o.arank = ws.take<int32_t>(p.E);
@@ -265,8 +280,8 @@ void plan_skel(Arena &ws, const Problem &p, Skel &o) {
     o.ru = ws.take<int32_t>(2 * p.E);
     o.rv = ws.take<int32_t>(2 * p.E);
     o.w = ws.take<int64_t>(2 * p.E);
-    o.knn = ws.take<int32_t>(p.E * (int64_t)p.k);  // p.k: the largest k of the batch
-    o.core = ws.take<int64_t>(p.E);
+    o.knn = p.knn ? ws.take<int32_t>(p.E * (int64_t)p.k) : nullptr;  // p.k: the largest k of the batch
+    o.core = p.knn ? ws.take<int64_t>(p.E) : nullptr;
 }
 
 struct SkScratch {
@@ -303,7 +318,10 @@ dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void
 #define KNN_ARGS                                                                           \
     g.isrc, g.idst, g.it, g.orig_of, E, g.out_off, g.out_t, g.out_id, g.in_off, g.in_t, g.in_id, \
         o.brank, o.arank, p.egraph, p.eoff, p.gk, p.knn_off, o.knn, o.core
-    if (p.k <= 4) TK(c, "k_ranks_knn", k_ranks_knn<4><<<grid, 128, 0, st>>>(KNN_ARGS));
+    if (!p.knn)
+        TK(c, "k_ranks", k_ranks<<<grid, 128, 0, st>>>(g.isrc, g.idst, g.it, E, g.out_off, g.out_t, g.in_off,
+                                                       g.in_t, o.brank, o.arank));
+    else if (p.k <= 4) TK(c, "k_ranks_knn", k_ranks_knn<4><<<grid, 128, 0, st>>>(KNN_ARGS));
     else if (p.k <= 8) TK(c, "k_ranks_knn", k_ranks_knn<8><<<grid, 128, 0, st>>>(KNN_ARGS));
     else TK(c, "k_ranks_knn", k_ranks_knn<16><<<grid, 128, 0, st>>>(KNN_ARGS));
 #undef KNN_ARGS

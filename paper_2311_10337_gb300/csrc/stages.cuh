@@ -25,6 +25,7 @@ struct Problem {
     const int32_t *gM = nullptr;      // [G] M of each graph
     const int64_t *knn_off = nullptr; // [G+1] first kNN slot of each graph
     int32_t *egraph = nullptr;        // [E] graph of each edge (built in stage A)
+    bool knn = true;                  // stage B also writes the kNN lists
 };
 
 // Stage A: incidence lists (Alg. 3 first line), per-vertex lists sorted by
@@ -64,7 +65,7 @@ struct Skel {
 };
 void plan_skel(Arena &ws, const Problem &p, Skel &o);
 size_t skel_scratch_bytes(const Problem &p);
-// also writes the kNN ids and core distances (same searches)
+// also writes the kNN ids and core distances (same searches) unless p.knn is off
 dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void *scratch);
 
 // Stage C: minimum spanning forest of the skeleton (Borůvka), sorted by

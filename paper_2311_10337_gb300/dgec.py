@@ -25,7 +25,11 @@ EXPORTS = ["dgec_create", "dgec_destroy", "dgec_last_error", "dgec_status_string
            "dgec_workspace_size", "dgec_run", "dgec_run_host", "dgec_last_launch_count",
            "dgec_set_kernel_timing", "dgec_kernel_timing", "dgec_msf_static",
            "dgec_batch_workspace_size", "dgec_run_batch", "dgec_server_create", "dgec_submit",
-           "dgec_wait", "dgec_server_lane_capacity", "dgec_server_destroy"]
+           "dgec_wait", "dgec_server_lane_capacity", "dgec_server_destroy",
+           "dgec_levels_workspace_size", "dgec_run_levels"]
+
+LEVELS_DENSE = 1
+MAX_LEVELS = 64
 
 
 class DgecError(RuntimeError):
@@ -58,6 +62,18 @@ class BatchResult(ctypes.Structure):
         "n_clusters", "mst_off", "knn_off")] + [
         ("total_edges", ctypes.c_int64), ("total_mst", ctypes.c_int64),
         ("total_clusters", ctypes.c_int32), ("glob", Result)]
+
+
+class LevelsParams(ctypes.Structure):
+    _fields_ = [("n_levels", ctypes.c_int32), ("h_omega", _P),
+                ("min_cluster_size", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+class LevelsResult(ctypes.Structure):
+    _fields_ = [(n, _P) for n in (
+        "sk_u", "sk_v", "sk_w", "merge_level", "merge_parent", "n_components", "level_labels",
+        "labels")] + [("n_skeleton", ctypes.c_int64), ("n_merges", ctypes.c_int64),
+                      ("n_clusters", ctypes.c_int32)]
 
 
 class Job(ctypes.Structure):
@@ -110,6 +126,12 @@ def load(path: str = LIB_PATH):
     L.dgec_server_lane_capacity.argtypes = [_P]
     L.dgec_server_lane_capacity.restype = ctypes.c_int64
     L.dgec_server_destroy.argtypes = [_P]
+    L.dgec_levels_workspace_size.argtypes = [ctypes.c_int64, ctypes.c_int32,
+                                             ctypes.POINTER(LevelsParams),
+                                             ctypes.POINTER(ctypes.c_size_t)]
+    L.dgec_run_levels.argtypes = [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32,
+                                  ctypes.POINTER(LevelsParams), _P, ctypes.c_size_t, _P,
+                                  ctypes.POINTER(LevelsResult)]
     L.dgec_msf_static.argtypes = [_P, _P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P, _P,
                                   ctypes.POINTER(ctypes.c_int64), _P]
     _lib = L
@@ -223,6 +245,29 @@ class Context:
                              ctypes.byref(res))
         self._check(rc)
         return Output(res, ws, E, n_vertices, k)
+
+    def run_levels(self, src, dst, t, n_vertices: int, omega, min_cluster_size: int = 0,
+                   dense: bool = False, stream=None):
+        """Discrete dendrogram (Alg. 5) at thresholds `omega` on device tensors,
+        plus condensed labels when min_cluster_size >= 2. Returns a
+        LevelsOutput viewing the workspace (valid until the next run)."""
+        torch = self.torch
+        E = int(src.shape[0])
+        for x, dt in ((src, torch.int32), (dst, torch.int32), (t, torch.int64)):
+            if x.dtype != dt or not x.is_cuda or not x.is_contiguous():
+                raise ValueError("src/dst must be contiguous cuda int32, t cuda int64")
+        om = np.ascontiguousarray(omega, dtype=np.int64)
+        p = LevelsParams(len(om), om.ctypes.data, min_cluster_size, LEVELS_DENSE if dense else 0)
+        nb = ctypes.c_size_t(0)
+        self._check(self.L.dgec_levels_workspace_size(E, n_vertices, ctypes.byref(p), ctypes.byref(nb)))
+        ws = self.workspace(nb.value)
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        res = LevelsResult()
+        rc = self.L.dgec_run_levels(self.h, src.data_ptr(), dst.data_ptr(), t.data_ptr(), E,
+                                    n_vertices, ctypes.byref(p), ws.data_ptr(), ws.numel(),
+                                    st.cuda_stream, ctypes.byref(res))
+        self._check(rc)
+        return LevelsOutput(res, ws, E, len(om))
 
     def run_batch(self, src, dst, t, edge_off, n_vertices, k, min_cluster_size, stream=None):
         """Batched Alg. 4 over graphs laid end to end on the device; tables are
@@ -446,4 +491,40 @@ class Output:
             a = a.view(np.uint64)
         if name == "knn_id":
             a = a.reshape(self.E, self.k)
+        return a
+
+
+class LevelsOutput:
+    """Device-resident results of one discrete-dendrogram run."""
+
+    def __init__(self, res: LevelsResult, ws, E, q):
+        import torch
+        self.n_skeleton = int(res.n_skeleton)
+        self.n_merges = int(res.n_merges)
+        self.n_clusters = int(res.n_clusters)
+        self.E, self.q = E, q
+        spec = {"sk_u": (torch.int32, 4, self.n_skeleton), "sk_v": (torch.int32, 4, self.n_skeleton),
+                "sk_w": (torch.int64, 8, self.n_skeleton), "merge_level": (torch.int32, 4, E),
+                "merge_parent": (torch.int32, 4, E), "n_components": (torch.int64, 8, q),
+                "level_labels": (torch.int32, 4, q * E), "labels": (torch.int32, 4, E)}
+        base = ws.data_ptr()
+        self._t = {}
+        for name, (dt, sz, n) in spec.items():
+            ptr = getattr(res, name)
+            if ptr is None or n == 0:
+                self._t[name] = None if ptr is None else torch.empty(0, dtype=dt, device=ws.device)
+                continue
+            off = ptr - base
+            self._t[name] = ws[off:off + n * sz].view(dt)
+
+    def tensor(self, name):
+        return self._t[name]
+
+    def numpy(self, name):
+        t = self._t[name]
+        if t is None:
+            return None
+        a = t.cpu().numpy()
+        if name == "level_labels":
+            a = a.reshape(self.q, self.E)
         return a
