@@ -3,7 +3,9 @@
 // (Alg. 2: "Sort E_i by time"; ties by edge id).
 //
 // First a device-wide radix sort of the 64-bit keys ((t - t_min) << idbits
-// | id) ranks all edges in (t, id) order; that rank r is the internal node
+// | id) ranks all edges in (t, id) order. The keys are laid out in id order
+// and the LSD sort is stable, so only the time bits need passes: equal
+// times keep id order. That rank r is the internal node
 // id of every later stage, and per-vertex lists sorted by (t, id) are just
 // lists sorted by r. Ranks are scattered into their vertex's segment through
 // per-vertex cursors (warp-aggregated atomics absorb hub vertices), then
@@ -415,7 +417,7 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
     TK(c, "k_pack_keys", k_pack_keys<<<gEE, kBlock, 0, st>>>(p.t, E, p.tmin, p.idbits, s.okey));
     {
         bool in_b;
-        DG_TRY(radix_sort(c, RadixBuffers{s.okey, s.ikey, nullptr, nullptr}, E, 0, p.idbits + p.tbits,
+        DG_TRY(radix_sort(c, RadixBuffers{s.okey, s.ikey, nullptr, nullptr}, E, p.idbits, p.idbits + p.tbits,
                           s.radix, &in_b));
         TK(c, "k_rank_init", k_rank_init<<<gEE, kBlock, 0, st>>>(in_b ? s.ikey : s.okey, E, p.tmin, p.idbits,
                                                                 p.src, p.dst, p.egraph, p.voff, o.orig_of, o.rank_of,

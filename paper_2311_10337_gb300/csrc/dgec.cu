@@ -544,7 +544,7 @@ dgec_status dgec_run_levels(dgec_ctx *x, const int32_t *d_src, const int32_t *d_
     p.egraph = L.egraph;
     DG_TRY(stage_csr(c, p, L.csr, L.scratch));
     DG_TRY(stage_skeleton(c, p, L.csr, L.skel, L.scratch));
-    DG_TRY(stage_levels(c, p, L.skel, params->h_omega, L.lv, L.scratch));
+    DG_TRY(stage_levels(c, p, L.csr, L.skel, params->h_omega, L.lv, L.scratch));
     if (condense) {
         DG_TRY(build_level_rows(c, p, L.csr, L.lv, L.scratch));
         DG_TRY(stage_dendro(c, p, L.csr, L.lv.rows, L.den, L.scratch));

@@ -7,9 +7,12 @@
 // (w <= omega_i, the appendix's reading) and bucket i is united on top of
 // the state of level i-1. Every edge is touched once in total, not q times.
 //
-// Union by smaller id: a hook always makes the larger of two roots point to
-// the smaller, so every root is the smallest member of its component, which
-// is the name the outputs use. A root is hooked at most once in the whole
+// Union by smaller id: a hook always makes the root with the larger
+// original id point to the other, so every root is the smallest member of
+// its component, which is the name the outputs use. The forest itself is
+// kept over internal ids (rank in (t, id) order): skeleton links join edges
+// close in time, so the parent reads of one bucket stay close in memory
+// instead of landing at random. A root is hooked at most once in the whole
 // run, at the level where its component first meets a smaller node; that
 // gives D in per-node form: merge_level[x] = that level, merge_parent[x] =
 // the name of the component it joins (the root after the level's hooks).
@@ -81,7 +84,8 @@ __device__ __forceinline__ int ld_par(const int32_t *par, int x) {
     return *(const volatile int32_t *)(par + x);
 }
 
-// Root of x with path halving. Parents only ever move to ancestors, and a
+// Root of x with path halving (internal ids). Parents only ever move to
+// ancestors (original ids strictly decrease toward the root), and a
 // root's own slot is changed only by the hook's compare-and-swap, so the
 // plain halving stores (made on non-roots only) are benign races.
 __device__ __forceinline__ int uf_root(int32_t *par, int x) {
@@ -96,21 +100,21 @@ __device__ __forceinline__ int uf_root(int32_t *par, int x) {
     return -1;
 }
 
-// Unite the bucket of level l. Roots hooked here get merge_level = l and go
-// to the level's list (one reservation per CTA); the CTA-uniform loop keeps
-// every thread in the reservation.
+// Unite the bucket of level l. Roots hooked here get merge_level = l (under
+// their original id) and go to the level's list (one reservation per CTA);
+// the CTA-uniform loop keeps every thread in the reservation.
 __global__ void __launch_bounds__(kBlock) k_lv_hook(const unsigned long long *key, const int64_t *boff,
-                                                    int l, const int32_t *u, const int32_t *v,
-                                                    int32_t *par, int32_t *mlevel, int32_t *list,
-                                                    unsigned long long *tot, int *err) {
+                                                    int l, const int32_t *ru, const int32_t *rv,
+                                                    const int32_t *orig_of, int32_t *par, int32_t *mlevel,
+                                                    int32_t *list, unsigned long long *tot, int *err) {
     const int64_t lo = boff[l], hi = boff[l + 1];
     for (int64_t base = lo + (int64_t)blockIdx.x * blockDim.x; base < hi;
          base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = base + threadIdx.x;
-        int hooked = -1;
+        int hooked = -1, hooked_orig = -1;
         if (s < hi) {
             const int j = (int)(key[s] & 0xffffffffull);
-            int a = u[j], b = v[j];
+            int a = ru[j], b = rv[j];
             for (int it = 0; it < kMaxWalk; it++) {
                 a = uf_root(par, a);
                 b = uf_root(par, b);
@@ -119,10 +123,12 @@ __global__ void __launch_bounds__(kBlock) k_lv_hook(const unsigned long long *ke
                     break;
                 }
                 if (a == b) break;
-                const int big = a > b ? a : b, small = a > b ? b : a;
+                const int oa = orig_of[a], ob = orig_of[b];
+                const int big = oa > ob ? a : b, small = oa > ob ? b : a;
                 const int old = atomicCAS(par + big, big, small);
                 if (old == big) {
                     hooked = big;
+                    hooked_orig = oa > ob ? oa : ob;
                     break;
                 }
                 a = old;  // `big` was hooked meanwhile: continue from its new parent
@@ -131,7 +137,7 @@ __global__ void __launch_bounds__(kBlock) k_lv_hook(const unsigned long long *ke
         }
         const long long slot = cta_reserve(hooked >= 0, tot);
         if (hooked >= 0) {
-            mlevel[hooked] = l;
+            mlevel[hooked_orig] = l;
             list[slot] = hooked;
         }
     }
@@ -141,26 +147,35 @@ __global__ void __launch_bounds__(kBlock) k_lv_hook(const unsigned long long *ke
 // snap[l] = list start of level l; the end is the running total, recorded as
 // snap[l + 1] for the next level.
 __global__ void k_lv_parent(const int32_t *list, int64_t *snap, const unsigned long long *tot, int l,
-                            int32_t *par, int32_t *mparent, int *err) {
+                            const int32_t *orig_of, int32_t *par, int32_t *mparent, int *err) {
     const int64_t lo = snap[l], hi = (int64_t)*tot;
     for (int64_t s = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < hi;
          s += (int64_t)gridDim.x * blockDim.x) {
         const int x = list[s];
         const int r = uf_root(par, x);
-        if (r < 0) atomicExch(err, 2);
-        mparent[x] = r;
+        if (r < 0) {
+            atomicExch(err, 2);
+            continue;
+        }
+        mparent[orig_of[x]] = orig_of[r];
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) snap[l + 1] = hi;
 }
 
-// Dense labels of level l: every node's root, with full compression.
-__global__ void k_lv_dense(int64_t E, int l, int32_t *par, int32_t *dense, int *err) {
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < E;
-         x += (int64_t)gridDim.x * blockDim.x) {
-        const int r = uf_root(par, (int)x);
-        if (r < 0) atomicExch(err, 3);
-        dense[(int64_t)l * E + x] = r;
-        if (r >= 0 && ld_par(par, (int)x) != r) *(volatile int32_t *)(par + x) = r;
+// Dense labels of level l, in original-id order: every node's root, with
+// full compression.
+__global__ void k_lv_dense(int64_t E, int l, const int32_t *rank_of, const int32_t *orig_of, int32_t *par,
+                           int32_t *dense, int *err) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int x = rank_of[e];
+        const int r = uf_root(par, x);
+        if (r < 0) {
+            atomicExch(err, 3);
+            continue;
+        }
+        dense[(int64_t)l * E + e] = orig_of[r];
+        if (ld_par(par, x) != r) *(volatile int32_t *)(par + x) = r;
     }
 }
 
@@ -241,8 +256,8 @@ size_t levels_scratch_bytes(const Problem &p) {
     return a.off;
 }
 
-dgec_status stage_levels(Ctx *c, const Problem &p, const Skel &sk, const int64_t *h_omega, Levels &o,
-                         void *scratch) {
+dgec_status stage_levels(Ctx *c, const Problem &p, const Csr &g, const Skel &sk, const int64_t *h_omega,
+                         Levels &o, void *scratch) {
     cudaStream_t st = c->stream;
     const int64_t E = p.E, n = sk.n;
     const int q = o.q;
@@ -267,14 +282,17 @@ dgec_status stage_levels(Ctx *c, const Problem &p, const Skel &sk, const int64_t
         // hook kernels read their bucket bounds on the device: no host round trip per level
         const int gh = c->num_sms * 8;
         for (int l = 0; l < q; l++) {
-            TK(c, "k_lv_hook", k_lv_hook<<<gh, kBlock, 0, st>>>(key, s.boff, l, sk.u, sk.v, s.par, o.mlevel,
-                                                               s.list, s.tot, s.err));
-            TK(c, "k_lv_parent", k_lv_parent<<<gh, kBlock, 0, st>>>(s.list, s.snap, s.tot, l, s.par, o.mparent,
-                                                                   s.err));
-            if (o.dense) TK(c, "k_lv_dense", k_lv_dense<<<gE, kBlock, 0, st>>>(E, l, s.par, o.dense, s.err));
+            TK(c, "k_lv_hook", k_lv_hook<<<gh, kBlock, 0, st>>>(key, s.boff, l, sk.ru, sk.rv, g.orig_of, s.par,
+                                                               o.mlevel, s.list, s.tot, s.err));
+            TK(c, "k_lv_parent", k_lv_parent<<<gh, kBlock, 0, st>>>(s.list, s.snap, s.tot, l, g.orig_of, s.par,
+                                                                   o.mparent, s.err));
+            if (o.dense)
+                TK(c, "k_lv_dense", k_lv_dense<<<gE, kBlock, 0, st>>>(E, l, g.rank_of, g.orig_of, s.par, o.dense,
+                                                                     s.err));
         }
     } else if (o.dense) {
-        for (int l = 0; l < q; l++) TK(c, "k_lv_dense", k_lv_dense<<<gE, kBlock, 0, st>>>(E, l, s.par, o.dense, s.err));
+        for (int l = 0; l < q; l++)
+            TK(c, "k_lv_dense", k_lv_dense<<<gE, kBlock, 0, st>>>(E, l, g.rank_of, g.orig_of, s.par, o.dense, s.err));
     }
     TK(c, "k_lv_counts", k_lv_counts<<<1, 64, 0, st>>>(E, q, s.snap, o.ncomp));
     int64_t h[2];

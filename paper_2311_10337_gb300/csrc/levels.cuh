@@ -20,8 +20,8 @@ struct Levels {
 };
 void plan_levels(Arena &ws, const Problem &p, int q, bool dense, Levels &o);
 size_t levels_scratch_bytes(const Problem &p);
-dgec_status stage_levels(Ctx *c, const Problem &p, const Skel &sk, const int64_t *h_omega, Levels &o,
-                         void *scratch);
+dgec_status stage_levels(Ctx *c, const Problem &p, const Csr &g, const Skel &sk, const int64_t *h_omega,
+                         Levels &o, void *scratch);
 dgec_status build_level_rows(Ctx *c, const Problem &p, const Csr &g, Levels &o, void *scratch);
 
 }  // namespace dgec
