@@ -1,0 +1,216 @@
+"""Parity at the full benchmark size: the 50M-edge mid workload, run through
+the same entry points and launch configuration the benchmark times (k = 8,
+M = 5, the current stream; the discrete dendrogram at 2^0 .. 2^28 s).
+
+The oracle cannot redo the whole graph in test time, so sampled outputs are
+recomputed one by one (kNN rows of sampled edges; Alg. 2's links at sampled
+vertices) and everything else is checked through properties that hold at
+any size: the incidence lists' order, Def. 1 for every link, the forest's
+size and total weight (Thm. 1) against scipy's components and MST of the
+skeleton, the dendrogram's sizes, the level components (Thm. 3) against
+scipy, and the component counts of every level against the forest."""
+import numpy as np
+import pytest
+
+from gpu_helpers import ctx
+from oracle import oracle as O
+from paper_2311_10337_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+POW2 = np.array([2 ** i for i in range(29)], np.int64)
+
+
+@pytest.fixture(scope="module")
+def full():
+    import torch
+    w = synth.mid(scale=1.0)
+    s = torch.from_numpy(w.src).cuda()
+    d = torch.from_numpy(w.dst).cuda()
+    t = torch.from_numpy(w.t).cuda()
+    out = ctx().run(s, d, t, w.n_vertices, w.k, w.min_cluster_size)
+    names = ["out_off", "in_off", "out_t", "out_id", "in_id", "sk_u", "sk_v", "sk_w", "knn_id", "core",
+             "mst_u", "mst_v", "mst_w", "link_a", "link_b", "link_size", "labels"]
+    r = {n: out.numpy(n) for n in names}
+    r["n_clusters"] = out.n_clusters
+    lv = ctx().run_levels(s, d, t, w.n_vertices, POW2, w.min_cluster_size)
+    r["merge_level"] = lv.numpy("merge_level")
+    r["merge_parent"] = lv.numpy("merge_parent")
+    r["n_components"] = lv.numpy("n_components")
+    r["lv_labels"] = lv.numpy("labels")
+    r["lv_n_clusters"] = lv.n_clusters
+    del s, d, t
+    ctx().ws = None
+    torch.cuda.empty_cache()
+    # shared by several tests: skeleton keys in sorted order, components of L*
+    key = r["sk_u"].astype(np.int64) * w.n_edges + r["sk_v"]
+    r["sk_order"] = np.argsort(key, kind="stable")
+    r["sk_key_sorted"] = key[r["sk_order"]]
+    r["n_comp"], r["comp"] = _components(w.n_edges, r["sk_u"], r["sk_v"])
+    return w, r
+
+
+def _csgraph(E, u, v, w=None):
+    sp = pytest.importorskip("scipy.sparse")
+    data = np.ones(len(u), np.int8) if w is None else w
+    return sp.coo_matrix((data, (u, v)), shape=(E, E)).tocsr()
+
+
+def _components(E, u, v):
+    cg = pytest.importorskip("scipy.sparse.csgraph")
+    n, lab = cg.connected_components(_csgraph(E, u, v), directed=False)
+    return n, lab
+
+
+def _min_member_names(lab):
+    """Name every component by its smallest member."""
+    E = len(lab)
+    first = np.full(lab.max() + 1 if E else 0, E, np.int64)
+    np.minimum.at(first, lab, np.arange(E))
+    return first[lab].astype(np.int32)
+
+
+def test_incidence_lists(full):
+    w, r = full
+    E, V = w.n_edges, w.n_vertices
+    for off, ids, end in (("out_off", "out_id", w.src), ("in_off", "in_id", w.dst)):
+        o, ids_ = r[off], r[ids]
+        assert np.array_equal(o, np.concatenate([[0], np.cumsum(np.bincount(end, minlength=V))]))
+        assert np.array_equal(np.sort(ids_), np.arange(E, dtype=np.int32))
+        seg = np.repeat(np.arange(V, dtype=np.int32), np.diff(o))
+        assert np.array_equal(end[ids_], seg)
+        same = seg[1:] == seg[:-1]
+        ta, tb = w.t[ids_[:-1]], w.t[ids_[1:]]
+        ok = (ta < tb) | ((ta == tb) & (ids_[:-1] < ids_[1:]))
+        assert np.all(ok[same]), off          # Alg. 2: each list sorted by (t, id)
+    assert np.array_equal(r["out_t"], w.t[r["out_id"]])
+
+
+def test_skeleton_links(full):
+    w, r = full
+    u, v, wt = r["sk_u"], r["sk_v"], r["sk_w"]
+    assert np.all(u < v)
+    for lo in range(0, len(u), 1 << 24):                      # Def. 1, P1-P3, one orientation
+        uu, vv, ww = u[lo:lo + (1 << 24)], v[lo:lo + (1 << 24)], wt[lo:lo + (1 << 24)]
+        tu, tv = w.t[uu], w.t[vv]
+        assert np.array_equal(ww, np.abs(tu - tv))
+        fwd = (w.dst[uu] == w.src[vv]) & (tu <= tv)
+        bwd = (w.dst[vv] == w.src[uu]) & (tv <= tu)
+        assert np.all(fwd | bwd)
+    assert np.all(np.diff(r["sk_key_sorted"]) > 0)            # each pair once (Alg. 3 union)
+    deg = np.bincount(w.src, minlength=w.n_vertices) + np.bincount(w.dst, minlength=w.n_vertices)
+    assert len(u) <= int(np.sum(np.maximum(deg - 1, 0)))      # size bound of Sec. 3
+
+
+def test_skeleton_sampled_vertices(full):
+    """Alg. 2 at sampled vertices (hubs included), run by the oracle on the
+    edges incident to the vertex: every link it emits there is in L*."""
+    w, r = full
+    ks = r["sk_key_sorted"]
+    deg = np.bincount(w.src, minlength=w.n_vertices) + np.bincount(w.dst, minlength=w.n_vertices)
+    rng = np.random.default_rng(7)
+    verts = np.concatenate([np.argsort(deg)[-5:], rng.choice(np.nonzero(deg > 1)[0], 200, replace=False)])
+    for i in verts.tolist():
+        inc = np.nonzero((w.src == i) | (w.dst == i))[0]
+        loc_v, inv = np.unique(np.concatenate([w.src[inc], w.dst[inc]]), return_inverse=True)
+        ls, ld = inv[:len(inc)].astype(np.int32), inv[len(inc):].astype(np.int32)
+        p, q, _, c = O.skeleton_raw(ls, ld, w.t[inc], len(loc_v))
+        centre = int(np.searchsorted(loc_v, i))
+        sel = c == centre
+        a, b = inc[p[sel]], inc[q[sel]]
+        keys = np.minimum(a, b).astype(np.int64) * w.n_edges + np.maximum(a, b)
+        pos = np.minimum(np.searchsorted(ks, keys), len(ks) - 1)
+        assert np.all(ks[pos] == keys), i
+
+
+def test_knn_sampled(full):
+    """kNN rows of sampled edges, by the oracle on the sub-multigraph they
+    depend on: the sampled edges, the in-edges of their tails and the
+    out-edges of their heads (local ids keep the original id order)."""
+    w, r = full
+    rng = np.random.default_rng(11)
+    q = np.sort(rng.choice(w.n_edges, 3000, replace=False))
+    tails = np.zeros(w.n_vertices, bool); tails[w.src[q]] = True
+    heads = np.zeros(w.n_vertices, bool); heads[w.dst[q]] = True
+    keep = np.zeros(w.n_edges, bool)
+    keep[q] = True
+    keep |= tails[w.dst] | heads[w.src]
+    sub = np.nonzero(keep)[0]
+    lq = np.searchsorted(sub, q).astype(np.int32)
+    ids, core = O.knn(w.src[sub], w.dst[sub], w.t[sub], w.n_vertices, w.k, lq)
+    ids = np.where(ids >= 0, sub[np.maximum(ids, 0)], -1)
+    knn = r["knn_id"].reshape(w.n_edges, w.k)
+    assert np.array_equal(knn[q], ids)
+    assert np.array_equal(r["core"][q], core)
+
+
+def test_forest_and_dendrogram(full):
+    w, r = full
+    E = w.n_edges
+    mu, mv, mw = r["mst_u"], r["mst_v"], r["mst_w"]
+    # sorted by the strict key (w, u, v)
+    k0 = (mw[1:] > mw[:-1]) | ((mw[1:] == mw[:-1]) & ((mu[1:] > mu[:-1]) | ((mu[1:] == mu[:-1]) & (mv[1:] > mv[:-1]))))
+    assert np.all(k0)
+    ks, order = r["sk_key_sorted"], r["sk_order"]
+    mk = mu.astype(np.int64) * E + mv
+    pos = np.minimum(np.searchsorted(ks, mk), len(ks) - 1)
+    assert np.all(ks[pos] == mk)                                      # forest edges are skeleton links
+    assert np.array_equal(r["sk_w"][order[pos]], mw)
+    ncomp = r["n_comp"]
+    assert len(mu) == E - ncomp                                       # spanning forest of L*
+    ncf, _ = _components(E, mu, mv)
+    assert ncf == ncomp
+    # Thm. 1: the forest has the minimum total weight (scipy on w + 1, as it drops zero weights)
+    cg = pytest.importorskip("scipy.sparse.csgraph")
+    mst = cg.minimum_spanning_tree(_csgraph(E, r["sk_u"], r["sk_v"], r["sk_w"].astype(np.float64) + 1.0))
+    assert int(round(mst.sum())) == int(mw.sum()) + len(mw)
+    # dendrogram: every merge joins two earlier clusters and counts their leaves
+    a, b, sz = r["link_a"].astype(np.int64), r["link_b"].astype(np.int64), r["link_size"]
+    size_of = np.concatenate([np.ones(E, np.int64), sz])
+    assert np.all(a < b) and np.all(b < E + np.arange(len(a)))
+    assert np.array_equal(sz, size_of[a] + size_of[b])
+    kids = np.concatenate([a, b])
+    assert len(np.unique(kids)) == len(kids)
+
+
+def test_labels_lie_in_components(full):
+    w, r = full
+    E = w.n_edges
+    comp = r["comp"]
+    for lab, ncl in ((r["labels"], r["n_clusters"]), (r["lv_labels"], r["lv_n_clusters"])):
+        m = lab >= 0
+        assert lab.max() + 1 == ncl
+        # one component per cluster
+        cmin = np.full(ncl, E, np.int64); cmax = np.full(ncl, -1, np.int64)
+        np.minimum.at(cmin, lab[m], comp[m]); np.maximum.at(cmax, lab[m], comp[m])
+        assert np.array_equal(cmin, cmax)
+        # clusters numbered by their smallest member: first appearances are 0, 1, 2, ...
+        _, first = np.unique(lab[m], return_index=True)
+        assert np.all(np.diff(np.nonzero(m)[0][first]) > 0)
+        assert np.all(np.bincount(lab[m]) >= w.min_cluster_size)
+
+
+def test_levels(full):
+    """Thm. 3 at two thresholds against scipy's components of the skeleton,
+    and every level's component count against the forest (Thm. 1)."""
+    w, r = full
+    E = w.n_edges
+    ml, mp = r["merge_level"], r["merge_parent"]
+    merged = ml >= 0
+    assert np.all(mp[merged] < np.nonzero(merged)[0]) and np.all(mp[~merged] == -1)
+    nmst_at = np.searchsorted(np.sort(r["mst_w"]), POW2, side="right")
+    assert np.array_equal(r["n_components"], E - nmst_at)
+    for li in (0, 10):
+        keep = r["sk_w"] <= POW2[li]
+        _, comp = _components(E, r["sk_u"][keep], r["sk_v"][keep])
+        want = _min_member_names(comp)
+        lab = np.arange(E, dtype=np.int32)
+        step = (ml >= 0) & (ml <= li)
+        lab[step] = mp[step]
+        for _ in range(64):                      # follow D up to level li
+            nxt = lab.copy()
+            go = (ml[lab] >= 0) & (ml[lab] <= li)
+            nxt[go] = mp[lab[go]]
+            if np.array_equal(nxt, lab):
+                break
+            lab = nxt
+        assert np.array_equal(lab, want), li
