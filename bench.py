@@ -28,12 +28,13 @@ sys.path.insert(0, ROOT)
 METRIC = "temporal edges/s end-to-end (kNN+MST+dendrogram)"
 UNIT = "edges/s"
 # Algorithmic bytes per edge of the dominant kernel k_ranks_knn: it reads
-# the edge (src, dst, t: 16 B) and its two candidate windows (k in-list and
-# k out-list entries of t + id: 2 * k * 12 B) and writes the two ranks
-# (8 B), k neighbour ids (4k B) and the core distance (8 B). Binary-search
-# probes and offset lookups are access overhead, not counted.
+# the edge (src, dst, t: 16 B), the k nearest (t, id) entries plus the one
+# entry past the k-th on each side that ends the merge (12 (k + 2) B), and
+# writes the two ranks (8 B), k neighbour ids (4k B) and the core distance
+# (8 B). Binary-search probes and offset lookups are access overhead, not
+# counted.
 def knn_bytes_per_edge(k: int) -> int:
-    return 16 + 2 * k * 12 + 8 + 4 * k + 8
+    return 16 + 12 * (k + 2) + 8 + 4 * k + 8
 
 
 def parse():
