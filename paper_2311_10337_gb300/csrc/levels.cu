@@ -31,10 +31,13 @@ namespace dgec {
 
 // ---------------------------------------------------------------- buckets
 
-// key = (bucket << 32) | edge index, bucket = first i with w <= omega[i]
-// (q when w exceeds every threshold: never united).
-__global__ void k_lv_keys(const int64_t *w, int64_t n, const int64_t *omega, int q,
-                          unsigned long long *key) {
+// key = bucket = first i with w <= omega[i] (q when w exceeds every
+// threshold: never united); val = the link's two internal ids, the end with
+// the smaller original id in the high word. The sort carries the pair, so a
+// bucket's hooks read one contiguous run instead of gathering.
+__global__ void k_lv_keys(const int64_t *w, const int32_t *ru, const int32_t *rv, const int32_t *u,
+                          const int32_t *orig_of, int64_t n, const int64_t *omega, int q,
+                          unsigned long long *key, unsigned long long *val) {
     __shared__ long long om[kMaxLevels];
     for (int i = threadIdx.x; i < q; i += blockDim.x) om[i] = omega[i];
     __syncthreads();
@@ -47,7 +50,10 @@ __global__ void k_lv_keys(const int64_t *w, int64_t n, const int64_t *omega, int
             if (om[mid] >= x) hi = mid;
             else lo = mid + 1;
         }
-        key[j] = ((unsigned long long)lo << 32) | (unsigned long long)j;
+        const int a = ru[j], b = rv[j];
+        const bool a_first = orig_of[a] == u[j];
+        key[j] = (unsigned long long)lo;
+        val[j] = ((unsigned long long)(uint32_t)(a_first ? a : b) << 32) | (uint32_t)(a_first ? b : a);
     }
 }
 
@@ -55,8 +61,8 @@ __global__ void k_lv_keys(const int64_t *w, int64_t n, const int64_t *omega, int
 __global__ void k_lv_bounds(const unsigned long long *key, int64_t n, int q, int64_t *boff) {
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s <= n;
          s += (int64_t)gridDim.x * blockDim.x) {
-        int b = s < n ? (int)(key[s] >> 32) : q + 1;
-        int prev = s > 0 ? (int)(key[s - 1] >> 32) : -1;
+        int b = s < n ? (int)key[s] : q + 1;
+        int prev = s > 0 ? (int)key[s - 1] : -1;
         for (int x = prev + 1; x <= b; x++) boff[x] = s;
     }
 }
@@ -103,41 +109,46 @@ __device__ __forceinline__ int uf_root(int32_t *par, int x) {
 // Unite the bucket of level l. Roots hooked here get merge_level = l (under
 // their original id) and go to the level's list (one reservation per CTA);
 // the CTA-uniform loop keeps every thread in the reservation.
-__global__ void __launch_bounds__(kBlock) k_lv_hook(const unsigned long long *key, const int64_t *boff,
-                                                    int l, const int32_t *ru, const int32_t *rv,
-                                                    const int32_t *orig_of, int32_t *par, int32_t *mlevel,
-                                                    int32_t *list, unsigned long long *tot, int *err) {
+__global__ void __launch_bounds__(kBlock) k_lv_hook(const unsigned long long *val, const int64_t *boff,
+                                                    int l, const int32_t *orig_of, int32_t *par,
+                                                    int32_t *mlevel, int32_t *list, unsigned long long *tot,
+                                                    int *err) {
     const int64_t lo = boff[l], hi = boff[l + 1];
     for (int64_t base = lo + (int64_t)blockIdx.x * blockDim.x; base < hi;
          base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = base + threadIdx.x;
         int hooked = -1, hooked_orig = -1;
         if (s < hi) {
-            const int j = (int)(key[s] & 0xffffffffull);
-            int a = ru[j], b = rv[j];
-            for (int it = 0; it < kMaxWalk; it++) {
-                a = uf_root(par, a);
-                b = uf_root(par, b);
-                if (a < 0 || b < 0) {
-                    atomicExch(err, 1);
-                    break;
+            const unsigned long long pr = val[s];
+            int a = (int)(pr >> 32), b = (int)(pr & 0xffffffffull);  // orig(a) < orig(b)
+            // both ends still roots: the larger original id is b, no lookup needed
+            if (ld_par(par, a) == a && ld_par(par, b) == b && atomicCAS(par + b, b, a) == b) {
+                hooked = b;
+            } else {
+                for (int it = 0; it < kMaxWalk; it++) {
+                    a = uf_root(par, a);
+                    b = uf_root(par, b);
+                    if (a < 0 || b < 0) {
+                        atomicExch(err, 1);
+                        break;
+                    }
+                    if (a == b) break;
+                    const int oa = orig_of[a], ob = orig_of[b];
+                    const int big = oa > ob ? a : b, small = oa > ob ? b : a;
+                    const int old = atomicCAS(par + big, big, small);
+                    if (old == big) {
+                        hooked = big;
+                        hooked_orig = oa > ob ? oa : ob;
+                        break;
+                    }
+                    a = old;  // `big` was hooked meanwhile: continue from its new parent
+                    b = small;
                 }
-                if (a == b) break;
-                const int oa = orig_of[a], ob = orig_of[b];
-                const int big = oa > ob ? a : b, small = oa > ob ? b : a;
-                const int old = atomicCAS(par + big, big, small);
-                if (old == big) {
-                    hooked = big;
-                    hooked_orig = oa > ob ? oa : ob;
-                    break;
-                }
-                a = old;  // `big` was hooked meanwhile: continue from its new parent
-                b = small;
             }
         }
         const long long slot = cta_reserve(hooked >= 0, tot);
         if (hooked >= 0) {
-            mlevel[hooked_orig] = l;
+            mlevel[hooked_orig >= 0 ? hooked_orig : orig_of[hooked]] = l;
             list[slot] = hooked;
         }
     }
@@ -231,7 +242,7 @@ void plan_levels(Arena &ws, const Problem &p, int q, bool dense, Levels &o) {
 
 struct LvScratch {
     int32_t *par, *list;
-    unsigned long long *k1, *k2, *tot;
+    unsigned long long *k1, *k2, *v1, *v2, *tot;
     int64_t *boff, *snap;
     int *err;
     void *radix;
@@ -243,6 +254,8 @@ static LvScratch carve_levels(Arena &a, const Problem &p) {
     s.list = a.take<int32_t>(p.E);
     s.k1 = a.take<unsigned long long>(n);
     s.k2 = a.take<unsigned long long>(n);
+    s.v1 = a.take<unsigned long long>(n);
+    s.v2 = a.take<unsigned long long>(n);
     s.tot = a.take<unsigned long long>(1);
     s.boff = a.take<int64_t>(kMaxLevels + 2);
     s.snap = a.take<int64_t>(kMaxLevels + 1);
@@ -273,17 +286,17 @@ dgec_status stage_levels(Ctx *c, const Problem &p, const Csr &g, const Skel &sk,
     TK(c, "k_lv_init", k_lv_init<<<gE, kBlock, 0, st>>>(E, s.par, o.mlevel, o.mparent, q, s.tot, s.snap, s.err));
     if (n > 0) {
         const int gn = grid_for(n, kBlock, 65536);
-        TK(c, "k_lv_keys", k_lv_keys<<<gn, kBlock, 0, st>>>(sk.w, n, o.omega, q, s.k1));
+        TK(c, "k_lv_keys", k_lv_keys<<<gn, kBlock, 0, st>>>(sk.w, sk.ru, sk.rv, sk.u, g.orig_of, n, o.omega, q,
+                                                           s.k1, s.v1));
         bool in_b;
-        DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, nullptr, nullptr}, n, 32, 32 + bits_for(q), s.radix,
-                          &in_b));
-        const unsigned long long *key = in_b ? s.k2 : s.k1;
+        DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, s.v1, s.v2}, n, 0, bits_for(q), s.radix, &in_b));
+        const unsigned long long *key = in_b ? s.k2 : s.k1, *val = in_b ? s.v2 : s.v1;
         TK(c, "k_lv_bounds", k_lv_bounds<<<grid_for(n + 1, kBlock, 65536), kBlock, 0, st>>>(key, n, q, s.boff));
         // hook kernels read their bucket bounds on the device: no host round trip per level
         const int gh = c->num_sms * 8;
         for (int l = 0; l < q; l++) {
-            TK(c, "k_lv_hook", k_lv_hook<<<gh, kBlock, 0, st>>>(key, s.boff, l, sk.ru, sk.rv, g.orig_of, s.par,
-                                                               o.mlevel, s.list, s.tot, s.err));
+            TK(c, "k_lv_hook", k_lv_hook<<<gh, kBlock, 0, st>>>(val, s.boff, l, g.orig_of, s.par, o.mlevel, s.list,
+                                                               s.tot, s.err));
             TK(c, "k_lv_parent", k_lv_parent<<<gh, kBlock, 0, st>>>(s.list, s.snap, s.tot, l, g.orig_of, s.par,
                                                                    o.mparent, s.err));
             if (o.dense)
