@@ -12,7 +12,7 @@
 //           p_{b_{m-1} - 1} when b_{m-1} >= 1.
 // So each edge emits at most one type-1 link (at its destination) and one
 // type-2 link (at its source): one thread per edge, no load imbalance on
-// hubs, and |L*| <= sum_i (|E_i| - 1) (Sec. 3) falls out directly.
+// hubs, and |L*| <= sum_i (|E_i| - 1) (Sec. 2) falls out directly.
 //
 // The union of Alg. 3 is a set: a pair emitted at two vertices is a
 // reciprocal, concurrent pair (i, j, t), (j, i, t) with w = 0; it is kept

@@ -19,7 +19,7 @@ def line_graph_arcs(src, dst, t):
 
 def undirected_edges(src, dst, t):
     """Undirected version of L_G as a dict {(min, max): w} (weak connectivity,
-    Sec. 2.2). Two arcs between one pair exist only for a reciprocal,
+    Sec. 1.2.3). Two arcs between one pair exist only for a reciprocal,
     concurrent pair; both then weigh 0."""
     r, s, w = line_graph_arcs(src, dst, t)
     out = {}

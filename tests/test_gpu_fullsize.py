@@ -98,7 +98,7 @@ def test_skeleton_links(full):
         assert np.all(fwd | bwd)
     assert np.all(np.diff(r["sk_key_sorted"]) > 0)            # each pair once (Alg. 3 union)
     deg = np.bincount(w.src, minlength=w.n_vertices) + np.bincount(w.dst, minlength=w.n_vertices)
-    assert len(u) <= int(np.sum(np.maximum(deg - 1, 0)))      # size bound of Sec. 3
+    assert len(u) <= int(np.sum(np.maximum(deg - 1, 0)))      # size bound of Sec. 2
 
 
 def test_skeleton_sampled_vertices(full):

@@ -9,7 +9,7 @@ from paper_2311_10337_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-POW2 = np.array([2 ** i for i in range(29)], np.int64)   # 1 s .. 2^28 s, as in Sec. 4.3
+POW2 = np.array([2 ** i for i in range(29)], np.int64)   # 1 s .. 2^28 s, as in Sec. 4.2.2
 
 
 def run_levels(src, dst, t, V, omega, M=0, dense=True):

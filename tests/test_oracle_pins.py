@@ -2,7 +2,7 @@
 
 Each test checks the oracle against something other than itself: brute
 force on the explicit line graph (Def. 1), Thm. 1-3 of the appendix, the
-size bound of Sec. 3, and the worked examples printed in the paper.
+size bound of Sec. 2, and the worked examples printed in the paper.
 """
 import json
 import os
@@ -100,7 +100,7 @@ def test_thm2_local_mst_equals_kruskal(g):
 @pytest.mark.parametrize("g", GRAPHS, ids=lambda g: g.name)
 def test_thm3_weighted_connectivity(g):
     """Thm. 3: comps(L*, w) == comps(L_G, w) for every threshold w, and the
-    size bound |L*| <= sum_i (|E_i| - 1) of Sec. 3."""
+    size bound |L*| <= sum_i (|E_i| - 1) of Sec. 2."""
     E = g.n_edges
     full = bf.undirected_edges(g.src, g.dst, g.t)
     u, v, w = O.skeleton(g.src, g.dst, g.t, g.n_vertices)
