@@ -47,7 +47,7 @@ def lib():
             L.orc_skeleton_raw.restype = i64
             L.orc_skeleton.argtypes = [i64, i32, I32P, I32P, I64P, I32P, I32P, I64P]
             L.orc_skeleton.restype = i64
-            L.orc_knn.argtypes = [i64, i32, I32P, I32P, I64P, i32, i64, I32P, I32P, I64P]
+            L.orc_knn.argtypes = [i64, i32, I32P, I32P, I64P, i32, i64, I32P, i64, I32P, I64P]
             L.orc_mst.argtypes = [i64, i64, I32P, I32P, I64P, I32P, I32P, I64P]
             L.orc_mst.restype = i64
             L.orc_linkage.argtypes = [i64, i64, I32P, I32P, I32P, I32P, I64P]
@@ -104,7 +104,12 @@ def skeleton(src, dst, t, n_vertices):
     return u[:n], v[:n], w[:n]
 
 
-def knn(src, dst, t, n_vertices, k, query=None):
+INT64_MAX = np.iinfo(np.int64).max
+
+
+def knn(src, dst, t, n_vertices, k, query=None, delta_max=None):
+    """k nearest line-graph neighbours by (w, id); with delta_max, only arcs
+    with w <= delta_max exist (the cutoff of Sec. 4.3)."""
     src, dst, t = _c(src, np.int32), _c(dst, np.int32), _c(t, np.int64)
     E = src.shape[0]
     if query is None:
@@ -113,7 +118,8 @@ def knn(src, dst, t, n_vertices, k, query=None):
     nq = query.shape[0]
     ids = np.zeros(max(nq * k, 1), np.int32)
     core = np.zeros(max(nq, 1), np.int64)
-    rc = lib().orc_knn(E, n_vertices, src, dst, t, k, nq, query, ids, core)
+    dmax = INT64_MAX if delta_max is None else int(delta_max)
+    rc = lib().orc_knn(E, n_vertices, src, dst, t, k, nq, query, dmax, ids, core)
     if rc:
         raise ValueError(f"oracle knn rc={rc}")
     return ids[:nq * k].reshape(nq, k), core[:nq]
@@ -167,13 +173,27 @@ def condense(n_nodes, a, b, w, size, M):
                 n_clusters=nlab.value)
 
 
-def run(src, dst, t, n_vertices, k, M, knn_query=None):
-    """Alg. 4 end to end: skeleton (Alg. 3) -> Alg. 1 on it; plus kNN/core."""
+def skeleton_cutoff(src, dst, t, n_vertices, delta_max):
+    """Skeleton of the line graph with the time cutoff of Sec. 4.3 (only arcs
+    with w <= delta_max): the links of L* with w <= delta_max. By Thm. 3
+    comps(L*, w) = comps(L_G, w) for every w, so for every threshold the
+    filtered links have the components of the filtered line graph."""
+    u, v, w = skeleton(src, dst, t, n_vertices)
+    keep = w <= delta_max
+    return u[keep], v[keep], w[keep]
+
+
+def run(src, dst, t, n_vertices, k, M, knn_query=None, delta_max=None):
+    """Alg. 4 end to end: skeleton (Alg. 3) -> Alg. 1 on it; plus kNN/core.
+    With delta_max, on the cutoff line graph of Sec. 4.3."""
     E = len(src)
     out = {}
     out["csr"] = csr(src, dst, t, n_vertices)
-    out["skeleton"] = skeleton(src, dst, t, n_vertices)
-    out["knn"] = knn(src, dst, t, n_vertices, k, knn_query)
+    if delta_max is None:
+        out["skeleton"] = skeleton(src, dst, t, n_vertices)
+    else:
+        out["skeleton"] = skeleton_cutoff(src, dst, t, n_vertices, delta_max)
+    out["knn"] = knn(src, dst, t, n_vertices, k, knn_query, delta_max)
     u, v, w = out["skeleton"]
     out["mst"] = mst(E, u, v, w)
     mu, mv, mw = out["mst"]

@@ -88,10 +88,13 @@ def minimax(n, edges):
     return D
 
 
-def knn_bruteforce(src, dst, t, k):
-    """Neighbours of each node in the undirected L_G ranked by (w, id)."""
+def knn_bruteforce(src, dst, t, k, delta_max=None):
+    """Neighbours of each node in the undirected L_G ranked by (w, id); with
+    delta_max, in the line graph keeping only arcs with w <= delta_max."""
     E = len(src)
     und = undirected_edges(src, dst, t)
+    if delta_max is not None:
+        und = {key: w for key, w in und.items() if w <= delta_max}
     nb = [[] for _ in range(E)]
     for (a, b), w in und.items():
         nb[a].append((w, b))

@@ -439,3 +439,35 @@ def test_levels_tree(g):
         for x in range(g.n_edges):
             if ml[x] == i:
                 assert mp[x] == comp[x] and mp[x] < x
+
+
+@pytest.mark.parametrize("g", GRAPHS[::3], ids=lambda g: g.name)
+@pytest.mark.parametrize("delta", [0, 1, 3, 10])
+def test_cutoff_line_graph(g, delta):
+    """Time cutoff of Sec. 4.3 (arcs with w <= delta_max only): the filtered
+    skeleton has the components of the explicit filtered L_G at every
+    threshold, its forest the weights of Kruskal on the filtered L_G, and the
+    kNN lists those of enumerating the filtered L_G."""
+    E = g.n_edges
+    full = {k: w for k, w in bf.undirected_edges(g.src, g.dst, g.t).items() if w <= delta}
+    u, v, w = O.skeleton_cutoff(g.src, g.dst, g.t, g.n_vertices, delta)
+    sk = {(a, b): x for a, b, x in zip(u.tolist(), v.tolist(), w.tolist())}
+    assert all(full[key] == x for key, x in sk.items())
+    for om in sorted(set(full.values())) + [INF]:
+        assert np.array_equal(bf.components(E, full, om), bf.components(E, sk, om))
+    mu, mv, mw = O.mst(E, u, v, w)
+    uf = bf.UnionFind(E)
+    wf = [x for (a, b), x in sorted(full.items(), key=lambda kv: (kv[1], kv[0])) if uf.union(a, b)]
+    assert wf == sorted(mw.tolist())
+    for k in (1, 4):
+        ids, core = O.knn(g.src, g.dst, g.t, g.n_vertices, k, delta_max=delta)
+        bids, bcore = bf.knn_bruteforce(g.src, g.dst, g.t, k, delta_max=delta)
+        assert np.array_equal(ids, bids) and np.array_equal(core, bcore)
+
+
+def test_cutoff_above_every_weight_is_no_cutoff():
+    g = synth.random_small(200, 20, 60, 31)
+    a = O.run(g.src, g.dst, g.t, g.n_vertices, 4, 3)
+    b = O.run(g.src, g.dst, g.t, g.n_vertices, 4, 3, delta_max=10 ** 12)
+    assert np.array_equal(a["condensed"]["labels"], b["condensed"]["labels"])
+    assert all(np.array_equal(x, y) for x, y in zip(a["knn"], b["knn"]))
