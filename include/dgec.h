@@ -47,10 +47,17 @@ typedef enum {
     DGEC_ERR_INTERNAL = 9
 } dgec_status;
 
+/* flags of dgec_params */
+#define DGEC_CUTOFF 1u  /* time cutoff of Sec. 4.3: keep only line-graph arcs with w <= delta_max */
+
 typedef struct {
     int32_t k;                /* neighbours per edge for the kNN output, 1 <= k <= 16 */
     int32_t min_cluster_size; /* M of Alg. 1 step 4, M >= 2 */
-    uint32_t flags;           /* reserved, must be 0 */
+    uint32_t flags;           /* 0 or DGEC_CUTOFF */
+    int64_t delta_max;        /* with DGEC_CUTOFF: the cutoff, >= 0 (ignored otherwise). Only arcs
+                                 with w <= delta_max are in the line graph: the skeleton keeps the
+                                 links with w <= delta_max (exact by Thm. 3), the kNN lists only
+                                 neighbours within delta_max, and everything downstream follows. */
 } dgec_params;
 
 typedef struct dgec_ctx dgec_ctx;

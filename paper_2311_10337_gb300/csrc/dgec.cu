@@ -32,6 +32,7 @@ struct HostBatch {
     const int32_t *nv;    // [G]
     const int32_t *k;     // [G]
     const int32_t *M;     // [G]
+    int64_t dmax = INT64_MAX;  // time cutoff, INT64_MAX = none
 };
 
 Problem make_problem(const HostBatch &hb) {
@@ -51,6 +52,7 @@ Problem make_problem(const HostBatch &hb) {
     p.V = V;
     p.k = kmax;
     p.M = Mmin;
+    p.dmax = hb.dmax;
     return p;
 }
 
@@ -103,7 +105,9 @@ dgec_status check_batch(Ctx *c, const HostBatch &hb) {
 
 dgec_status check_params(Ctx *c, const dgec_params *prm) {
     if (!prm) return set_err(c, DGEC_ERR_INVALID_ARG, "params is null");
-    if (prm->flags != 0) return set_err(c, DGEC_ERR_INVALID_ARG, "flags must be 0");
+    if (prm->flags & ~DGEC_CUTOFF) return set_err(c, DGEC_ERR_INVALID_ARG, "unknown flags");
+    if ((prm->flags & DGEC_CUTOFF) && prm->delta_max < 0)
+        return set_err(c, DGEC_ERR_INVALID_ARG, "delta_max must be >= 0");
     return DGEC_OK;
 }
 
@@ -400,6 +404,7 @@ dgec_status dgec_run(dgec_ctx *x, const int32_t *d_src, const int32_t *d_dst, co
     if (n_edges < 0) return set_err(c, DGEC_ERR_INVALID_ARG, "negative size");
     int64_t eoff[2] = {0, n_edges};
     HostBatch hb{1, eoff, &n_vertices, &params->k, &params->min_cluster_size};
+    if (params->flags & DGEC_CUTOFF) hb.dmax = params->delta_max;
     DG_TRY(check_batch(c, hb));
     CU_TRY(c, cudaSetDevice(c->device));
     c->stream = (cudaStream_t)stream;

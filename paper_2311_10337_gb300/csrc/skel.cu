@@ -64,9 +64,12 @@ __device__ __forceinline__ bool emitted_at(const SkView &g, int x, int pin, int 
 }
 
 // part[e] / part[E + e]: partner of edge e through its type-1 / type-2
-// link (-1 if none), wgt the P3 weight.
+// link (-1 if none), wgt the P3 weight. With the time cutoff of Sec. 4.3
+// only links with w <= dmax are kept: by Thm. 3 the kept links have, at
+// every threshold, the components of the line graph without the longer
+// arcs.
 __global__ void k_links(SkView g, const int64_t *t, const int64_t *out_t, const int64_t *in_t,
-                        int64_t E, int32_t *part, int64_t *wgt, int *flag) {
+                        int64_t E, int64_t dmax, int32_t *part, int64_t *wgt, int *flag) {
     // e below is an internal id r; t, src, dst are the r-ordered copies
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -111,8 +114,8 @@ __global__ void k_links(SkView g, const int64_t *t, const int64_t *out_t, const 
         wgt[e] = w1;
         part[E + e] = p2;
         wgt[E + e] = w2;
-        flag[e] = p1 >= 0;
-        flag[E + e] = p2 >= 0;
+        flag[e] = p1 >= 0 && w1 <= dmax;
+        flag[E + e] = p2 >= 0 && w2 <= dmax;
     }
 }
 
@@ -143,7 +146,8 @@ __global__ void k_compact_links(const int32_t *part, const int64_t *wgt, const i
 // window its smallest ids are taken instead of its largest. The 2K
 // candidates are sorted in registers (bitonic network); the one node that
 // can appear on both sides (the reciprocal concurrent edge, w = 0) is
-// counted once.
+// counted once. Under the time cutoff (Sec. 4.3) only neighbours with
+// w <= dmax exist; they are a prefix of the sorted candidates.
 
 struct Cand {
     long long w;
@@ -165,7 +169,7 @@ __global__ void __launch_bounds__(128) k_ranks_knn(const int32_t *src, const int
                                                    int32_t *brank, int32_t *arank,
                                                    const int32_t *egraph, const int64_t *eoff,
                                                    const int32_t *gk, const int64_t *knn_off,
-                                                   int32_t *knn, int64_t *core) {
+                                                   int64_t dmax, int32_t *knn, int64_t *core) {
     constexpr int N = 2 * K;
     // r runs over internal ids (src, dst, t are the r-ordered copies); the
     // neighbour lists are written under the original id, with original ids
@@ -245,7 +249,7 @@ __global__ void __launch_bounds__(128) k_ranks_knn(const int32_t *src, const int
         int prev = -1;
 #pragma unroll
         for (int x = 0; x < N; x++) {
-            if (c[x].id != INT_MAX && c[x].id != prev && cnt < k) {
+            if (c[x].id != INT_MAX && c[x].id != prev && cnt < k && c[x].w <= dmax) {
                 row[cnt] = (int32_t)(c[x].id - e0);
                 last_w = c[x].w;
                 cnt++;
@@ -317,7 +321,7 @@ dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void
     int grid = grid_for(E, 128, 1 << 20);
 #define KNN_ARGS                                                                           \
     g.isrc, g.idst, g.it, g.orig_of, E, g.out_off, g.out_t, g.out_id, g.in_off, g.in_t, g.in_id, \
-        o.brank, o.arank, p.egraph, p.eoff, p.gk, p.knn_off, o.knn, o.core
+        o.brank, o.arank, p.egraph, p.eoff, p.gk, p.knn_off, p.dmax, o.knn, o.core
     if (!p.knn)
         TK(c, "k_ranks", k_ranks<<<grid, 128, 0, st>>>(g.isrc, g.idst, g.it, E, g.out_off, g.out_t, g.in_off,
                                                        g.in_t, o.brank, o.arank));
@@ -326,8 +330,8 @@ dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void
     else TK(c, "k_ranks_knn", k_ranks_knn<16><<<grid, 128, 0, st>>>(KNN_ARGS));
 #undef KNN_ARGS
     SkView v{g.isrc, g.idst, g.out_off, g.in_off, g.out_r, g.in_r, g.slot_out, o.brank, o.arank};
-    TK(c, "k_links", k_links<<<grid_for(E, kBlock, 65536), kBlock, 0, st>>>(v, g.it, g.out_t, g.in_t, E, s.part,
-                                                                          s.wgt, s.flag));
+    TK(c, "k_links", k_links<<<grid_for(E, kBlock, 65536), kBlock, 0, st>>>(v, g.it, g.out_t, g.in_t, E, p.dmax,
+                                                                          s.part, s.wgt, s.flag));
     TK(c, "k_zero_i32", k_zero_i32<<<1, 1, 0, st>>>(s.flag + 2 * E));
     DG_TRY(exclusive_scan_i32(c, s.flag, s.pos, 2 * E + 1, s.scan_tmp));
     TK(c, "k_compact_links", k_compact_links<<<grid_for(2 * E, kBlock, 65536), kBlock, 0, st>>>(

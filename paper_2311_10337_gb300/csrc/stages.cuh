@@ -26,6 +26,7 @@ struct Problem {
     const int64_t *knn_off = nullptr; // [G+1] first kNN slot of each graph
     int32_t *egraph = nullptr;        // [E] graph of each edge (built in stage A)
     bool knn = true;                  // stage B also writes the kNN lists
+    int64_t dmax = INT64_MAX;         // time cutoff (Sec. 4.3): only links with w <= dmax
 };
 
 // Stage A: incidence lists (Alg. 3 first line), per-vertex lists sorted by

@@ -38,9 +38,18 @@ class DgecError(RuntimeError):
         self.status = status
 
 
+CUTOFF = 1
+
+
 class Params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("min_cluster_size", ctypes.c_int32),
-                ("flags", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("delta_max", ctypes.c_int64)]
+
+
+def _params(k, min_cluster_size, delta_max=None):
+    if delta_max is None:
+        return Params(k, min_cluster_size, 0, 0)
+    return Params(k, min_cluster_size, CUTOFF, int(delta_max))
 
 
 _P = ctypes.c_void_p
@@ -157,7 +166,7 @@ def msf_static(u, v, w, n_nodes: int, out_u, out_v, out_w, stream=None) -> int:
 
 def workspace_size(n_edges: int, n_vertices: int, k: int, min_cluster_size: int) -> int:
     L = load()
-    p = Params(k, min_cluster_size, 0)
+    p = _params(k, min_cluster_size)
     out = ctypes.c_size_t(0)
     rc = L.dgec_workspace_size(n_edges, n_vertices, ctypes.byref(p), ctypes.byref(out))
     if rc != DGEC_OK:
@@ -227,15 +236,17 @@ class Context:
             i += 1
         return out
 
-    def run(self, src, dst, t, n_vertices: int, k: int, min_cluster_size: int, stream=None):
+    def run(self, src, dst, t, n_vertices: int, k: int, min_cluster_size: int, stream=None,
+            delta_max=None):
         """Alg. 4 on device tensors (int32 src/dst, int64 t). Returns an
-        Output whose tensors view the workspace (valid until the next run)."""
+        Output whose tensors view the workspace (valid until the next run).
+        delta_max: the time cutoff of Sec. 4.3 (None = no cutoff)."""
         torch = self.torch
         E = int(src.shape[0])
         for x, dt in ((src, torch.int32), (dst, torch.int32), (t, torch.int64)):
             if x.dtype != dt or not x.is_cuda or not x.is_contiguous():
                 raise ValueError("src/dst must be contiguous cuda int32, t cuda int64")
-        p = Params(k, min_cluster_size, 0)
+        p = _params(k, min_cluster_size, delta_max)
         need = workspace_size(E, n_vertices, k, min_cluster_size)
         ws = self.workspace(need)
         st = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -275,12 +286,13 @@ class Context:
         return _run_batch(self, src, dst, t, edge_off, n_vertices, k, min_cluster_size, stream)
 
     def run_host(self, src: np.ndarray, dst: np.ndarray, t: np.ndarray, n_vertices: int, k: int,
-                 min_cluster_size: int, labels_out: np.ndarray | None = None, stream=None):
+                 min_cluster_size: int, labels_out: np.ndarray | None = None, stream=None,
+                 delta_max=None):
         """Alg. 4 from host arrays (pinned numpy views avoid staging copies);
         returns (labels, n_clusters)."""
         torch = self.torch
         E = int(src.shape[0])
-        p = Params(k, min_cluster_size, 0)
+        p = _params(k, min_cluster_size, delta_max)
         need = workspace_size(E, n_vertices, k, min_cluster_size) + 16 * E + 4096
         ws = self.workspace(need)
         if labels_out is None:

@@ -17,13 +17,13 @@ def ctx():
     return _CTX
 
 
-def run_gpu(src, dst, t, V, k, M):
+def run_gpu(src, dst, t, V, k, M, delta_max=None):
     import torch
     c = ctx()
     s = torch.from_numpy(np.ascontiguousarray(src, np.int32)).cuda()
     d = torch.from_numpy(np.ascontiguousarray(dst, np.int32)).cuda()
     tt = torch.from_numpy(np.ascontiguousarray(t, np.int64)).cuda()
-    out = c.run(s, d, tt, V, k, M)
+    out = c.run(s, d, tt, V, k, M, delta_max=delta_max)
     torch.cuda.synchronize()
     names = ["out_off", "in_off", "out_t", "in_t", "out_id", "in_id", "sk_u", "sk_v", "sk_w",
              "knn_id", "core", "mst_u", "mst_v", "mst_w", "link_a", "link_b", "link_size",
@@ -39,10 +39,10 @@ def sorted_skeleton(u, v, w):
     return u[o], v[o], w[o]
 
 
-def compare_all(src, dst, t, V, k, M, knn_query=None, what=None):
+def compare_all(src, dst, t, V, k, M, knn_query=None, what=None, delta_max=None):
     """Element-wise comparison of every output array (bit-exact: all integer)."""
-    g = run_gpu(src, dst, t, V, k, M)
-    r = O.run(src, dst, t, V, k, M, knn_query)
+    g = run_gpu(src, dst, t, V, k, M, delta_max)
+    r = O.run(src, dst, t, V, k, M, knn_query, delta_max)
     E = len(src)
     oo, oi, io_, ii = r["csr"]
     assert np.array_equal(g["out_off"], oo), "out_off"
