@@ -818,3 +818,125 @@ int orc_condense_levels(int64_t n, int32_t q, const int64_t *omega,
 #undef LEVEL_NODE
 #undef NODE_LAMBDA
 }
+
+/* ------------------------------------------------------------------ */
+/* Dynamic hypergraphs (Sec. 4.4). Hyperedge r = (S_r, t_r) with its    */
+/* members as CSR rows: s_off[E + 1], s_vert[s_off[E]]. The line graph */
+/* joins two hyperedges that share a vertex, weight |t_r - t_s|.       */
+/* Undirected: at every vertex the clique of incident hyperedges has   */
+/* the time-sorted path as a local MST (ties by id). Directed: r also  */
+/* has targets R_r (d_off, d_vert); at a vertex i the in-list holds the */
+/* hyperedges with i in R (arriving) and the out-list those with i in  */
+/* S (leaving), and Alg. 2 runs on them as for a graph. The skeleton   */
+/* is the union over vertices as a set (u < v), sorted by (w, u, v).   */
+/* Returns the link count, or -(error code). Capacity: s_off[E] +      */
+/* d_off[E] links. Reading: a vertex listed twice in one member set, or */
+/* (directed) in both S_r and R_r, is rejected like a self loop.       */
+/* ------------------------------------------------------------------ */
+
+static int cmp_i32(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+static int hyper_check(int64_t E, int32_t V, const int64_t *off, const int32_t *vert,
+                       int32_t *tmp)
+{
+    for (int64_t e = 0; e < E; e++) {
+        int64_t n = off[e + 1] - off[e];
+        if (n < 0) return ORC_ERR_ARG;
+        for (int64_t x = 0; x < n; x++) {
+            int32_t a = vert[off[e] + x];
+            if (a < 0 || a >= V) return ORC_ERR_VERTEX;
+            tmp[x] = a;
+        }
+        qsort(tmp, (size_t)n, sizeof(int32_t), cmp_i32);
+        for (int64_t x = 1; x < n; x++)
+            if (tmp[x] == tmp[x - 1]) return ORC_ERR_SELF_LOOP;
+    }
+    return ORC_OK;
+}
+
+int64_t orc_hyper_skeleton(int64_t E, int32_t V, const int64_t *t, int32_t directed,
+                           const int64_t *s_off, const int32_t *s_vert,
+                           const int64_t *d_off, const int32_t *d_vert,
+                           int32_t *u_out, int32_t *v_out, int64_t *w_out)
+{
+    if (E < 0 || V < 0 || s_off[0] != 0 || (directed && d_off[0] != 0)) return -ORC_ERR_ARG;
+    int64_t Ms = s_off[E], Md = directed ? d_off[E] : 0;
+    int64_t cap = Ms + Md + 1;
+    int32_t *tmp = malloc(sizeof(int32_t) * (size_t)cap);
+    int64_t *deg = calloc((size_t)V + 1, sizeof(int64_t));
+    inc_rec *all = malloc(sizeof(inc_rec) * (size_t)cap);
+    int64_t *fill = malloc(sizeof(int64_t) * ((size_t)V + 1));
+    int32_t *W = malloc(sizeof(int32_t) * (size_t)cap);
+    wedge *links = malloc(sizeof(wedge) * (size_t)cap);
+    if (!tmp || !deg || !all || !fill || !W || !links) return -ORC_ERR_OOM;
+    int rc = hyper_check(E, V, s_off, s_vert, tmp);
+    if (!rc && directed) rc = hyper_check(E, V, d_off, d_vert, tmp);
+    if (!rc && directed) {                              /* no vertex in both S_r and R_r */
+        for (int64_t e = 0; e < E && !rc; e++) {
+            int64_t ns = s_off[e + 1] - s_off[e], nd = d_off[e + 1] - d_off[e];
+            for (int64_t x = 0; x < ns && !rc; x++)
+                for (int64_t y = 0; y < nd; y++)
+                    if (s_vert[s_off[e] + x] == d_vert[d_off[e] + y]) { rc = ORC_ERR_SELF_LOOP; break; }
+        }
+    }
+    if (rc) { free(tmp); free(deg); free(all); free(fill); free(W); free(links); return -rc; }
+    /* incidence records per vertex: dir 1 = the vertex is in S (leaving),
+     * dir 0 = in R (arriving); undirected members are all dir 1 */
+    for (int64_t m = 0; m < Ms; m++) deg[s_vert[m] + 1]++;
+    for (int64_t m = 0; m < Md; m++) deg[d_vert[m] + 1]++;
+    for (int32_t i = 0; i < V; i++) deg[i + 1] += deg[i];
+    memcpy(fill, deg, sizeof(int64_t) * ((size_t)V + 1));
+    for (int64_t e = 0; e < E; e++) {
+        inc_rec r;
+        r.t = t[e]; r.id = (int32_t)e;
+        r.dir = 1;
+        for (int64_t m = s_off[e]; m < s_off[e + 1]; m++) all[fill[s_vert[m]]++] = r;
+        r.dir = 0;
+        if (directed)
+            for (int64_t m = d_off[e]; m < d_off[e + 1]; m++) all[fill[d_vert[m]]++] = r;
+    }
+    int64_t n = 0;
+    for (int32_t i = 0; i < V; i++) {
+        inc_rec *Ei = all + deg[i];
+        int64_t di = deg[i + 1] - deg[i];
+        qsort(Ei, (size_t)di, sizeof(inc_rec), cmp_inc);   /* sort by time, ties by id */
+        if (!directed) {
+            for (int64_t x = 1; x < di; x++) {              /* the path through E_i */
+                int32_t a = Ei[x - 1].id, b = Ei[x].id;
+                links[n].u = a < b ? a : b;
+                links[n].v = a < b ? b : a;
+                links[n].w = Ei[x].t - Ei[x - 1].t;
+                n++;
+            }
+        } else {
+            int64_t wlen = 0;                               /* Alg. 2 with W */
+            for (int64_t x = 0; x < di; x++) {
+                if (Ei[x].dir == 0) {
+                    W[wlen++] = Ei[x].id;
+                } else {
+                    for (int64_t y = 0; y < wlen; y++) {
+                        int32_t a = W[y], b = Ei[x].id;
+                        links[n].u = a < b ? a : b;
+                        links[n].v = a < b ? b : a;
+                        links[n].w = Ei[x].t - t[W[y]];
+                        n++;
+                    }
+                    if (wlen > 0) { W[0] = W[wlen - 1]; wlen = 1; }
+                }
+            }
+        }
+    }
+    qsort(links, (size_t)n, sizeof(wedge), cmp_wedge);     /* the union, as a set */
+    int64_t m = 0;
+    for (int64_t x = 0; x < n; x++) {
+        if (m > 0 && cmp_wedge(&links[m - 1], &links[x]) == 0) continue;
+        links[m++] = links[x];
+    }
+    for (int64_t x = 0; x < m; x++) { u_out[x] = links[x].u; v_out[x] = links[x].v; w_out[x] = links[x].w; }
+    free(tmp); free(deg); free(all); free(fill); free(W); free(links);
+    return m;
+}

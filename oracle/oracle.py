@@ -53,6 +53,9 @@ def lib():
             L.orc_linkage.argtypes = [i64, i64, I32P, I32P, I32P, I32P, I64P]
             L.orc_levels.argtypes = [i64, i64, I32P, I32P, I64P, i32, I64P, I32P]
             L.orc_levels_tree.argtypes = [i64, i32, I32P, I32P, I32P]
+            L.orc_hyper_skeleton.argtypes = [i64, i32, I64P, i32, I64P, I32P, I64P, I32P,
+                                             I32P, I32P, I64P]
+            L.orc_hyper_skeleton.restype = i64
             L.orc_condense_levels.argtypes = [i64, i32, I64P, I32P, i32, I32P,
                                               ctypes.POINTER(i32), ctypes.POINTER(i64),
                                               U64P, U64P, I64P, U64P, U64P, I32P]
@@ -244,3 +247,39 @@ def condense_levels(labels, omega, M):
     c = ncl.value
     return dict(labels=out[:n], n_clusters=nlab.value, cl_birth=birth[:c], cl_death=death[:c],
                 cl_size=size[:c], cl_stab_hi=hi[:c], cl_stab_lo=lo[:c], cl_selected=sel[:c])
+
+
+def hyper_skeleton(t, n_vertices, s_off, s_vert, d_off=None, d_vert=None):
+    """Skeleton of a dynamic hypergraph (Sec. 4.4): undirected when d_off is
+    None (members s_off/s_vert), else directed (sources s_*, targets d_*)."""
+    t = _c(t, np.int64)
+    E = t.shape[0]
+    s_off, s_vert = _c(s_off, np.int64), _c(s_vert, np.int32)
+    directed = d_off is not None
+    if directed:
+        d_off, d_vert = _c(d_off, np.int64), _c(d_vert, np.int32)
+    else:
+        d_off, d_vert = np.zeros(E + 1, np.int64), np.zeros(1, np.int32)
+    if len(s_vert) == 0:
+        s_vert = np.zeros(1, np.int32)
+    if len(d_vert) == 0:
+        d_vert = np.zeros(1, np.int32)
+    cap = int(s_off[-1]) + (int(d_off[-1]) if directed else 0) + 1
+    u = np.zeros(cap, np.int32); v = np.zeros(cap, np.int32); w = np.zeros(cap, np.int64)
+    n = lib().orc_hyper_skeleton(E, n_vertices, t, int(directed), s_off, s_vert, d_off, d_vert, u, v, w)
+    if n < 0:
+        raise ValueError(f"oracle hyper_skeleton rc={-n}")
+    return u[:n], v[:n], w[:n]
+
+
+def hyper_run(t, n_vertices, s_off, s_vert, d_off=None, d_vert=None, M=5):
+    """Alg. 1 on the hypergraph skeleton (Sec. 4.4)."""
+    E = len(t)
+    out = {"skeleton": hyper_skeleton(t, n_vertices, s_off, s_vert, d_off, d_vert)}
+    u, v, w = out["skeleton"]
+    out["mst"] = mst(E, u, v, w)
+    mu, mv, mw = out["mst"]
+    out["linkage"] = linkage(E, mu, mv)
+    a, b, s = out["linkage"]
+    out["condensed"] = condense(E, a, b, mw, s, M)
+    return out

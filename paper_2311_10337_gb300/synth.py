@@ -370,3 +370,177 @@ def batch(n_graphs: int = 4096, log10_min: float = 3.0, log10_max: float = 6.0,
                  nv.astype(np.int32), k, np.full(n_graphs, 5, np.int32),
                  f"{n_graphs} graphs, E_b=10^U({log10_min},{log10_max}) total {total}, "
                  f"V_b=E_b/10, zipf={zipf_s}, t~U[0,{t_max}), k in {{4,8,16}}, M=5")
+
+
+# ------------------------------------------------------------ hypergraphs
+
+@dataclasses.dataclass
+class HyperWorkload:
+    """Dynamic hypergraph (Sec. 4.4): hyperedge e at time t[e] with members
+    s_vert[s_off[e]:s_off[e+1]] (undirected), or sources there and targets
+    d_vert[d_off[e]:d_off[e+1]] (directed)."""
+    name: str
+    t: np.ndarray
+    s_off: np.ndarray
+    s_vert: np.ndarray
+    d_off: np.ndarray | None
+    d_vert: np.ndarray | None
+    n_vertices: int
+    min_cluster_size: int
+    recipe: str
+
+    @property
+    def n_edges(self) -> int:
+        return int(self.t.shape[0])
+
+    @property
+    def directed(self) -> bool:
+        return self.d_off is not None
+
+
+def _distinct_rows(st: Stream, row: np.ndarray, vert: np.ndarray, fixed: np.ndarray,
+                   n_vertices: int) -> np.ndarray:
+    """Redraw (uniformly) members that repeat a vertex within their row;
+    `fixed` marks entries that must not move (a sender)."""
+    vert = vert.copy()
+    for _ in range(64):
+        o = np.lexsort((~fixed, vert, row))
+        dup = np.zeros(len(o), bool)
+        dup[1:] = (row[o][1:] == row[o][:-1]) & (vert[o][1:] == vert[o][:-1])
+        bad = o[dup]
+        if bad.size == 0:
+            return vert
+        vert[bad] = st.integers(0, n_vertices, bad.size)
+    raise RuntimeError("could not draw distinct members")
+
+
+def _split_rows(n_rows, sizes, vert):
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    return off, vert.astype(np.int32)
+
+
+def hyper_small(n_edges: int, n_vertices: int, t_max: int, seed: int, directed: bool,
+                max_members: int = 4, min_cluster_size: int = 3) -> HyperWorkload:
+    """Small tie-heavy hypergraphs for brute-force checks: member counts
+    uniform in [1, max_members] (sources in [1, 2] when directed), members
+    uniform and distinct within a hyperedge, t uniform in [0, t_max)."""
+    st = Stream(BASE_SEED + 91 + seed, 41)
+    assert n_vertices >= 2 * max_members + 2
+    t = st.integers(0, t_max, n_edges).astype(np.int64)
+    if not directed:
+        sz = st.integers(1, max_members + 1, n_edges)
+        row = np.repeat(np.arange(n_edges), sz)
+        vert = _distinct_rows(st, row, st.integers(0, n_vertices, int(sz.sum())),
+                              np.zeros(int(sz.sum()), bool), n_vertices)
+        s_off, s_vert = _split_rows(n_edges, sz, vert)
+        return HyperWorkload(f"hyp{seed}", t, s_off, s_vert, None, None, n_vertices,
+                             min_cluster_size, f"undirected E={n_edges} V={n_vertices} t~U[0,{t_max})")
+    ns = st.integers(1, 3, n_edges)
+    nd = st.integers(1, max_members + 1, n_edges)
+    # sources and targets of a hyperedge drawn as one distinct row, then split
+    tot = ns + nd
+    row = np.repeat(np.arange(n_edges), tot)
+    vert = _distinct_rows(st, row, st.integers(0, n_vertices, int(tot.sum())),
+                          np.zeros(int(tot.sum()), bool), n_vertices)
+    first = np.concatenate([[0], np.cumsum(tot)[:-1]])
+    pos = np.arange(int(tot.sum())) - np.repeat(first, tot)
+    is_src = pos < np.repeat(ns, tot)
+    s_off, s_vert = _split_rows(n_edges, ns, vert[is_src])
+    d_off, d_vert = _split_rows(n_edges, nd, vert[~is_src])
+    return HyperWorkload(f"dhyp{seed}", t, s_off, s_vert, d_off, d_vert, n_vertices,
+                         min_cluster_size, f"directed E={n_edges} V={n_vertices} t~U[0,{t_max})")
+
+
+def hyper(scale: float = 1.0, directed: bool = True, seed_offset: int = 0,
+          min_cluster_size: int = 5) -> HyperWorkload:
+    """Broadcast messages (Sec. 4.4's single sender, many receivers): 20M
+    hyperedges over 1M vertices at scale 1, a 30-day span. 70% in planted
+    groups of U{3..12} members exchanging bursts of U{5..100} messages with
+    Exp(60 s) gaps: the sender a uniform member, the receivers the next
+    1 + Geom(1/2) members after it (cyclically, capped at the group). 30%
+    background: sender rank-Zipf(2.1), 1 + Geom(1/2) receivers (at most 8)
+    rank-Zipf(2.1) and distinct, t uniform. Undirected: members = sender and
+    receivers together."""
+    seed = BASE_SEED + 5 + 1000 * seed_offset
+    n_edges = int(round(20_000_000 * scale))
+    n_vertices = max(64, int(round(1_000_000 * scale)))
+    span = 30 * 86400
+    st = Stream(seed, 51)
+    n_conv = int(round(0.7 * n_edges))
+    n_bg = n_edges - n_conv
+    # planted groups
+    snd, rcv_cnt, t_parts, rcv_parts = [], [], [], []
+    pos = 0
+    while pos < n_conv:
+        chunk = max(1024, (n_conv - pos) // 50 + 1)
+        g = st.integers(3, 13, chunk)
+        blen = st.integers(5, 101, chunk)
+        start = st.integers(0, span, chunk)
+        mem_off = np.concatenate([[0], np.cumsum(g)])
+        members = st.integers(0, n_vertices, int(mem_off[-1]))
+        row = np.repeat(np.arange(chunk), g)
+        members = _distinct_rows(st, row, members, np.zeros(len(members), bool), n_vertices)
+        tot = int(blen.sum())
+        conv_of = np.repeat(np.arange(chunk), blen)
+        first = np.concatenate([[0], np.cumsum(blen)[:-1]])
+        gaps = np.floor(-60.0 * np.log1p(-st.uniform(tot))).astype(np.int64)
+        gaps[first] = 0
+        csum = np.cumsum(gaps)
+        times = np.repeat(start, blen) + csum - np.repeat(csum[first], blen)
+        gg = g[conv_of]
+        sl = st.integers(0, 1 << 30, tot) % gg
+        geo = np.floor(np.log1p(-st.uniform(tot)) / np.log(0.5)).astype(np.int64)
+        nr = np.minimum(1 + geo, gg - 1)
+        take = min(tot, n_conv - pos)
+        sl, nr, gg, times, conv_of = sl[:take], nr[:take], gg[:take], times[:take], conv_of[:take]
+        base = mem_off[conv_of]
+        snd.append(members[base + sl])
+        rcv_cnt.append(nr)
+        x = np.arange(int(nr.sum())) - np.repeat(np.concatenate([[0], np.cumsum(nr)[:-1]]), nr)
+        rl = (np.repeat(sl, nr) + 1 + x) % np.repeat(gg, nr)
+        rcv_parts.append(members[np.repeat(base, nr) + rl])
+        t_parts.append(times)
+        pos += take
+    perm = _permutation(Stream(seed, 52), n_vertices)
+    bs = perm[_zipf_ranks(st, n_bg, n_vertices, 2.1)]
+    geo = np.floor(np.log1p(-st.uniform(n_bg)) / np.log(0.5)).astype(np.int64)
+    bn = np.minimum(1 + geo, 8)
+    brow = np.repeat(np.arange(n_bg), bn + 1)
+    bv = np.empty(int((bn + 1).sum()), np.int64)
+    bfirst = np.concatenate([[0], np.cumsum(bn + 1)[:-1]])
+    bv[:] = perm[_zipf_ranks(st, len(bv), n_vertices, 2.1)]
+    bv[bfirst] = bs
+    fixed = np.zeros(len(bv), bool)
+    fixed[bfirst] = True
+    bv = _distinct_rows(st, brow, bv, fixed, n_vertices)
+    brcv = np.delete(bv, bfirst)
+    bt = st.integers(0, span, n_bg)
+    snd.append(bs); rcv_cnt.append(bn); rcv_parts.append(brcv); t_parts.append(bt)
+    sender = np.concatenate(snd)
+    nr = np.concatenate(rcv_cnt)
+    rcv = np.concatenate(rcv_parts)
+    t = np.concatenate(t_parts).astype(np.int64)
+    # hyperedges in a seeded random order
+    order = _permutation(Stream(seed, 53), n_edges)
+    r_off = np.concatenate([[0], np.cumsum(nr)]).astype(np.int64)
+    nr_o = nr[order]
+    idx = np.repeat(r_off[order], nr_o) + (np.arange(int(nr_o.sum())) -
+                                           np.repeat(np.concatenate([[0], np.cumsum(nr_o)[:-1]]), nr_o))
+    rcv_o = rcv[idx]
+    sender, t = sender[order], t[order]
+    recipe = (f"E={n_edges} V={n_vertices} span=30d groups=70% (U3..12 members, bursts U5..100, "
+              f"Exp(60s) gaps) bg=30% zipf=2.1, receivers 1+Geom(1/2)")
+    if directed:
+        s_off = np.arange(n_edges + 1, dtype=np.int64)
+        d_off = np.concatenate([[0], np.cumsum(nr_o)]).astype(np.int64)
+        return HyperWorkload("mail", t, s_off, sender.astype(np.int32), d_off, rcv_o.astype(np.int32),
+                             n_vertices, min_cluster_size, "directed " + recipe)
+    sz = nr_o + 1
+    m_off = np.concatenate([[0], np.cumsum(sz)]).astype(np.int64)
+    mv = np.empty(int(m_off[-1]), np.int64)
+    mv[m_off[:-1]] = sender
+    rest = np.ones(len(mv), bool)
+    rest[m_off[:-1]] = False
+    mv[rest] = rcv_o
+    return HyperWorkload("mail_u", t, m_off, mv.astype(np.int32), None, None, n_vertices,
+                         min_cluster_size, "undirected " + recipe)

@@ -108,3 +108,34 @@ def knn_bruteforce(src, dst, t, k, delta_max=None):
         if len(lst) >= k:
             core[e] = lst[k - 1][0]
     return ids, core
+
+
+def hyper_line_graph(h):
+    """Explicit line graph of a dynamic hypergraph (Sec. 4.4) as an undirected
+    dict {(min, max): w}. Undirected: two hyperedges sharing a vertex, w =
+    |t_r - t_s|. Directed: an arc r -> s when a target of r is a source of s
+    and t_r <= t_s, w = t_s - t_r (weak connectivity as for graphs)."""
+    E = h.n_edges
+    src_of = {}   # vertex -> hyperedges with it as member / source
+    dst_of = {}   # vertex -> hyperedges with it as target
+    for e in range(E):
+        for i in h.s_vert[h.s_off[e]:h.s_off[e + 1]].tolist():
+            src_of.setdefault(i, []).append(e)
+        if h.directed:
+            for i in h.d_vert[h.d_off[e]:h.d_off[e + 1]].tolist():
+                dst_of.setdefault(i, []).append(e)
+    out = {}
+    t = h.t.tolist()
+    if not h.directed:
+        for i, lst in src_of.items():
+            for x in range(len(lst)):
+                for y in range(x + 1, len(lst)):
+                    a, b = lst[x], lst[y]
+                    out[(min(a, b), max(a, b))] = abs(t[a] - t[b])
+        return out
+    for i, ins in dst_of.items():
+        for r in ins:
+            for s in src_of.get(i, []):
+                if r != s and t[r] <= t[s]:
+                    out[(min(r, s), max(r, s))] = t[s] - t[r]
+    return out
