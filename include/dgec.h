@@ -347,6 +347,66 @@ dgec_status dgec_run_levels(dgec_ctx *ctx, const int32_t *d_src, const int32_t *
                             const dgec_levels_params *params, void *d_workspace,
                             size_t ws_bytes, void *cuda_stream, dgec_levels_result *out);
 
+/* ---------------------------------------------------------------------
+ * Dynamic hypergraphs (Sec. 4.4).
+ *
+ * A dynamic hyperedge e = (S_e, t_e) is a set of vertices observed at time
+ * t_e; hyperedges are the nodes of the line graph, and two hyperedges that
+ * share a vertex are joined with weight |t_r - t_s|. Directed hyperedges
+ * have sources S_e and targets R_e; an arc r -> s exists when a target of r
+ * is a source of s and t_r <= t_s (weight t_s - t_r), clustered by weak
+ * connectivity as for graphs. The skeleton is the union over vertices of a
+ * local MST (undirected: the path through the vertex's hyperedges in (t, id)
+ * order; directed: Alg. 2 on the vertex's in-list R and out-list S), with
+ * the same weighted connectivity as the line graph and at most
+ * sum_i (d_i - 1) links; Alg. 1 then runs on it (forest, dendrogram,
+ * condensed tree, labels; no kNN lists).
+ *
+ * Members are CSR rows: hyperedge e's sources (or members) are
+ * d_src_vert[d_src_off[e] .. d_src_off[e+1]), its targets likewise in the
+ * dst arrays (directed only; pass NULL and 0 otherwise). Offsets start at 0,
+ * do not decrease and end at the member count. A vertex listed twice in one
+ * member set, or in both S_e and R_e, gives DGEC_ERR_SELF_LOOP (the analogue
+ * of Sec. 1.2.1's excluded self loops). Empty member sets are allowed.
+ * --------------------------------------------------------------------- */
+typedef struct {
+    int32_t directed;          /* 0: undirected, 1: directed */
+    int32_t min_cluster_size;  /* M >= 2 */
+    uint32_t flags;            /* reserved, must be 0 */
+} dgec_hyper_params;
+
+/* Results of dgec_run_hyper: device arrays in the caller's workspace, valid
+ * until it is reused; counts are host values. */
+typedef struct {
+    /* per vertex, the hyperedges having it as a member (directed: as a
+     * source), in (t, id) order: src_list[src_voff[v] .. src_voff[v+1]) */
+    const int64_t *src_voff;           /* [n_vertices + 1] */
+    const int32_t *src_list;           /* [n_src_members] */
+    const int64_t *dst_voff;           /* directed: as a target; NULL otherwise */
+    const int32_t *dst_list;           /* [n_dst_members] */
+    const int32_t *sk_u, *sk_v;        /* skeleton links u < v, w = |t_u - t_v|, [n_skeleton], */
+    const int64_t *sk_w;               /* ordered by the (t, id) ranks of their two ends (earlier end first) */
+    const int32_t *mst_u, *mst_v;      /* forest in (w, u, v) order, as in dgec_result */
+    const int64_t *mst_w;
+    const int32_t *link_a, *link_b;    /* dendrogram, as in dgec_result */
+    const int64_t *link_size;
+    const int32_t *labels;             /* [n_hyperedges], -1 noise */
+    int64_t n_skeleton, n_mst;
+    int32_t n_clusters;
+} dgec_hyper_result;
+
+dgec_status dgec_hyper_workspace_size(int64_t n_hyperedges, int32_t n_vertices,
+                                      int64_t n_src_members, int64_t n_dst_members,
+                                      const dgec_hyper_params *params, size_t *bytes);
+
+dgec_status dgec_run_hyper(dgec_ctx *ctx, const int64_t *d_t, int64_t n_hyperedges,
+                           int32_t n_vertices, const int64_t *d_src_off,
+                           const int32_t *d_src_vert, int64_t n_src_members,
+                           const int64_t *d_dst_off, const int32_t *d_dst_vert,
+                           int64_t n_dst_members, const dgec_hyper_params *params,
+                           void *d_workspace, size_t ws_bytes, void *cuda_stream,
+                           dgec_hyper_result *out);
+
 #ifdef __cplusplus
 }
 #endif

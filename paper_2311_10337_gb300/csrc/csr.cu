@@ -294,11 +294,25 @@ void plan_csr(Arena &ws, const Problem &p, Csr &o) {
     o.slot_out = ws.take<int32_t>(p.E);
 }
 
+void carve_segsort(Arena &a, int64_t V, int64_t n, SegSort &s) {
+    s.bin_cnt = a.take<int>(8);
+    s.bin_list = a.take<int>(4 * (V + 1));
+    s.scan_tmp = a.take<long long>(scan_scratch_elems(n / 2048 + 8));
+    s.hoff = a.take<long long>(n / 2048 + 8);
+    s.hsz = a.take<long long>(n / 2048 + 8);
+    s.hk = a.take<unsigned long long>(n);
+    s.hv = a.take<unsigned long long>(n);
+    s.hk2 = a.take<unsigned long long>(n);
+    s.hv2 = a.take<unsigned long long>(n);
+    s.radix = a.take<char>(radix_scratch_bytes(n));
+}
+
 // scratch layout
 struct CsrScratch {
-    int *deg_out, *deg_in, *bin_cnt, *bin_list;
-    long long *flags, *scan_tmp, *hoff, *hsz;
-    unsigned long long *okey, *ikey, *hk, *hv, *hk2, *hv2;
+    int *deg_out, *deg_in;
+    long long *flags, *scan_tmp;
+    unsigned long long *okey, *ikey;
+    SegSort seg;
     void *radix;
 };
 static CsrScratch carve_csr(Arena &a, const Problem &p) {
@@ -306,18 +320,11 @@ static CsrScratch carve_csr(Arena &a, const Problem &p) {
     int64_t V = p.V, E = p.E;
     s.deg_out = a.take<int>(V + 1);
     s.deg_in = a.take<int>(V + 1);
-    s.bin_cnt = a.take<int>(8);
-    s.bin_list = a.take<int>(4 * (V + 1));
     s.flags = a.take<long long>(8);
-    s.scan_tmp = a.take<long long>(scan_scratch_elems(V + 1) + scan_scratch_elems(E / 2048 + 8));
-    s.hoff = a.take<long long>(E / 2048 + 8);
-    s.hsz = a.take<long long>(E / 2048 + 8);
+    s.scan_tmp = a.take<long long>(scan_scratch_elems(V + 1));
     s.okey = a.take<unsigned long long>(E);
     s.ikey = a.take<unsigned long long>(E);
-    s.hk = a.take<unsigned long long>(E);
-    s.hv = a.take<unsigned long long>(E);
-    s.hk2 = a.take<unsigned long long>(E);
-    s.hv2 = a.take<unsigned long long>(E);
+    carve_segsort(a, V, E, s.seg);
     s.radix = a.take<char>(radix_scratch_bytes(E));
     return s;
 }
@@ -328,12 +335,11 @@ size_t csr_scratch_bytes(const Problem &p) {
     return a.off;
 }
 
-static dgec_status sort_segments(Ctx *c, const Problem &p, unsigned long long *keys,
-                                 const int64_t *off, CsrScratch &s, int key_bits) {
+dgec_status sort_segments(Ctx *c, int64_t V, unsigned long long *keys, const int64_t *off, SegSort &s,
+                          int key_bits) {
     cudaStream_t st = c->stream;
-    int64_t V = p.V;
     CU_TRY(c, cudaMemsetAsync(s.bin_cnt, 0, 8 * sizeof(int), st));
-    TK(c, "k_classify", k_classify<<<grid_for(V, kBlock, 8192), kBlock, 0, st>>>(off, p.V, s.bin_cnt, s.bin_list, V + 1));
+    TK(c, "k_classify", k_classify<<<grid_for(V, kBlock, 8192), kBlock, 0, st>>>(off, V, s.bin_cnt, s.bin_list, V + 1));
     int64_t h[4];
     CU_TRY(c, cudaMemcpyAsync(c->h_pinned, s.bin_cnt, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CU_TRY(c, cudaStreamSynchronize(st));
@@ -428,8 +434,8 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
     CU_TRY(c, cudaMemsetAsync(s.deg_in, 0, sizeof(int) * (V + 1), st));
     TK(c, "k_scatter", k_scatter<<<grid_for(E, kBlock, (int64_t)c->num_sms * 16), kBlock, 0, st>>>(
                            o.isrc, o.idst, E, o.out_off, o.in_off, s.deg_out, s.deg_in, s.okey, s.ikey));
-    DG_TRY(sort_segments(c, p, s.okey, o.out_off, s, p.idbits));
-    DG_TRY(sort_segments(c, p, s.ikey, o.in_off, s, p.idbits));
+    DG_TRY(sort_segments(c, V, s.okey, o.out_off, s.seg, p.idbits));
+    DG_TRY(sort_segments(c, V, s.ikey, o.in_off, s.seg, p.idbits));
     TK(c, "k_unpack", k_unpack<<<gEE, kBlock, 0, st>>>(s.okey, E, o.orig_of, o.it, o.out_t, o.out_id,
                                                        o.out_r, o.slot_out));
     TK(c, "k_unpack", k_unpack<<<gEE, kBlock, 0, st>>>(s.ikey, E, o.orig_of, o.it, o.in_t, o.in_id,

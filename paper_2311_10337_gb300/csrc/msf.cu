@@ -420,7 +420,7 @@ struct MsfScratch {
 };
 static MsfScratch carve_msf(Arena &a, const Problem &p) {
     MsfScratch s;
-    int64_t E = p.E, S = 2 * p.E;
+    int64_t E = p.E, S = link_cap(p);
     s.par = a.take<int32_t>(E);
     s.roots = a.take<int32_t>(E);
     s.roots2 = a.take<int32_t>(E);

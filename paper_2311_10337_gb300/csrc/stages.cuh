@@ -27,7 +27,22 @@ struct Problem {
     int32_t *egraph = nullptr;        // [E] graph of each edge (built in stage A)
     bool knn = true;                  // stage B also writes the kNN lists
     int64_t dmax = INT64_MAX;         // time cutoff (Sec. 4.3): only links with w <= dmax
+    int64_t links_cap = -1;           // skeleton capacity; -1 = 2E (graphs: <= 2 links per edge)
 };
+
+inline int64_t link_cap(const Problem &p) { return p.links_cap >= 0 ? p.links_cap : 2 * p.E; }
+
+// Sorting u64 keys within per-vertex segments (off[V+1]) by the bin their
+// length falls in (warp / CTA bitonic networks, hubs through the radix sort).
+struct SegSort {
+    int *bin_cnt, *bin_list;
+    long long *scan_tmp, *hoff, *hsz;
+    unsigned long long *hk, *hv, *hk2, *hv2;
+    void *radix;
+};
+void carve_segsort(Arena &a, int64_t V, int64_t n, SegSort &s);
+dgec_status sort_segments(Ctx *c, int64_t V, unsigned long long *keys, const int64_t *off, SegSort &s,
+                          int key_bits);
 
 // Stage A: incidence lists (Alg. 3 first line), per-vertex lists sorted by
 // (t, id).

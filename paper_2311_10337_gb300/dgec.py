@@ -26,7 +26,8 @@ EXPORTS = ["dgec_create", "dgec_destroy", "dgec_last_error", "dgec_status_string
            "dgec_set_kernel_timing", "dgec_kernel_timing", "dgec_msf_static",
            "dgec_batch_workspace_size", "dgec_run_batch", "dgec_server_create", "dgec_submit",
            "dgec_wait", "dgec_server_lane_capacity", "dgec_server_destroy",
-           "dgec_levels_workspace_size", "dgec_run_levels"]
+           "dgec_levels_workspace_size", "dgec_run_levels", "dgec_hyper_workspace_size",
+           "dgec_run_hyper"]
 
 LEVELS_DENSE = 1
 MAX_LEVELS = 64
@@ -85,6 +86,18 @@ class LevelsResult(ctypes.Structure):
                       ("n_clusters", ctypes.c_int32)]
 
 
+class HyperParams(ctypes.Structure):
+    _fields_ = [("directed", ctypes.c_int32), ("min_cluster_size", ctypes.c_int32),
+                ("flags", ctypes.c_uint32)]
+
+
+class HyperResult(ctypes.Structure):
+    _fields_ = [(n, _P) for n in (
+        "src_voff", "src_list", "dst_voff", "dst_list", "sk_u", "sk_v", "sk_w", "mst_u", "mst_v",
+        "mst_w", "link_a", "link_b", "link_size", "labels")] + [
+        ("n_skeleton", ctypes.c_int64), ("n_mst", ctypes.c_int64), ("n_clusters", ctypes.c_int32)]
+
+
 class Job(ctypes.Structure):
     _fields_ = [("d_src", _P), ("d_dst", _P), ("d_t", _P), ("n_edges", ctypes.c_int64),
                 ("k", ctypes.c_int32), ("min_cluster_size", ctypes.c_int32), ("d_labels", _P)]
@@ -141,6 +154,12 @@ def load(path: str = LIB_PATH):
     L.dgec_run_levels.argtypes = [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32,
                                   ctypes.POINTER(LevelsParams), _P, ctypes.c_size_t, _P,
                                   ctypes.POINTER(LevelsResult)]
+    L.dgec_hyper_workspace_size.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
+                                            ctypes.c_int64, ctypes.POINTER(HyperParams),
+                                            ctypes.POINTER(ctypes.c_size_t)]
+    L.dgec_run_hyper.argtypes = [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P, ctypes.c_int64, _P, _P,
+                                 ctypes.c_int64, ctypes.POINTER(HyperParams), _P, ctypes.c_size_t, _P,
+                                 ctypes.POINTER(HyperResult)]
     L.dgec_msf_static.argtypes = [_P, _P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P, _P,
                                   ctypes.POINTER(ctypes.c_int64), _P]
     _lib = L
@@ -279,6 +298,35 @@ class Context:
                                     st.cuda_stream, ctypes.byref(res))
         self._check(rc)
         return LevelsOutput(res, ws, E, len(om))
+
+    def run_hyper(self, t, s_off, s_vert, n_vertices: int, min_cluster_size: int, d_off=None,
+                  d_vert=None, stream=None):
+        """Alg. 1 on a dynamic hypergraph (Sec. 4.4) given as device tensors:
+        t int64[E], member rows s_off int64[E+1] / s_vert int32[Ms], and for a
+        directed hypergraph target rows d_off / d_vert (sources in s_*)."""
+        torch = self.torch
+        E = int(t.shape[0])
+        directed = d_off is not None
+        arrays = [(t, torch.int64), (s_off, torch.int64), (s_vert, torch.int32)]
+        if directed:
+            arrays += [(d_off, torch.int64), (d_vert, torch.int32)]
+        for x, dt in arrays:
+            if x.dtype != dt or not x.is_cuda or not x.is_contiguous():
+                raise ValueError("hypergraph arrays must be contiguous cuda tensors (int64 t/offsets, int32 members)")
+        Ms = int(s_vert.shape[0])
+        Md = int(d_vert.shape[0]) if directed else 0
+        p = HyperParams(1 if directed else 0, min_cluster_size, 0)
+        nb = ctypes.c_size_t(0)
+        self._check(self.L.dgec_hyper_workspace_size(E, n_vertices, Ms, Md, ctypes.byref(p), ctypes.byref(nb)))
+        ws = self.workspace(nb.value)
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        res = HyperResult()
+        rc = self.L.dgec_run_hyper(self.h, t.data_ptr(), E, n_vertices, s_off.data_ptr(), s_vert.data_ptr(), Ms,
+                                   d_off.data_ptr() if directed else None,
+                                   d_vert.data_ptr() if directed else None, Md, ctypes.byref(p),
+                                   ws.data_ptr(), ws.numel(), st.cuda_stream, ctypes.byref(res))
+        self._check(rc)
+        return HyperOutput(res, ws, E, n_vertices, Ms, Md)
 
     def run_batch(self, src, dst, t, edge_off, n_vertices, k, min_cluster_size, stream=None):
         """Batched Alg. 4 over graphs laid end to end on the device; tables are
@@ -540,3 +588,36 @@ class LevelsOutput:
         if name == "level_labels":
             a = a.reshape(self.q, self.E)
         return a
+
+
+class HyperOutput:
+    """Device-resident results of one hypergraph run."""
+
+    def __init__(self, res: HyperResult, ws, E, V, Ms, Md):
+        import torch
+        self.n_skeleton = int(res.n_skeleton)
+        self.n_mst = int(res.n_mst)
+        self.n_clusters = int(res.n_clusters)
+        i32, i64 = (torch.int32, 4), (torch.int64, 8)
+        spec = {"src_voff": (i64, V + 1), "src_list": (i32, Ms), "dst_voff": (i64, V + 1),
+                "dst_list": (i32, Md), "sk_u": (i32, self.n_skeleton), "sk_v": (i32, self.n_skeleton),
+                "sk_w": (i64, self.n_skeleton), "mst_u": (i32, self.n_mst), "mst_v": (i32, self.n_mst),
+                "mst_w": (i64, self.n_mst), "link_a": (i32, self.n_mst), "link_b": (i32, self.n_mst),
+                "link_size": (i64, self.n_mst), "labels": (i32, E)}
+        base = ws.data_ptr()
+        self._t = {}
+        for name, ((dt, sz), n) in spec.items():
+            ptr = getattr(res, name)
+            if ptr is None:
+                self._t[name] = None
+            elif n == 0:
+                self._t[name] = torch.empty(0, dtype=dt, device=ws.device)
+            else:
+                self._t[name] = ws[ptr - base:ptr - base + n * sz].view(dt)
+
+    def tensor(self, name):
+        return self._t[name]
+
+    def numpy(self, name):
+        t = self._t[name]
+        return None if t is None else t.cpu().numpy()
