@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrivals per second")
     ap.add_argument("--serve-lanes", type=int, default=3)
     ap.add_argument("--serve-pool-gb", type=float, default=72.0)
+    ap.add_argument("--hyper-scale", type=float, default=1.0,
+                    help="scale of the hypergraph (broadcast message) measurement; 0 = skip")
     ap.add_argument("--no-levels", action="store_true",
                     help="skip the discrete-dendrogram (Alg. 5) measurement")
     ap.add_argument("--breakdown", action="store_true",
@@ -218,6 +220,41 @@ def discrete_levels(ctx, src, dst, tt, w, steps, breakdown=False):
         res["kernel_breakdown_ms"] = {n: [round(v[0], 3), v[1]] for n, v in
                                       sorted(ctx.kernel_timing().items(), key=lambda kv: -kv[1][0])}
         ctx.set_kernel_timing(0)
+    return res
+
+
+def hypergraphs(ctx, scale, steps):
+    """Hyperedges/s of Alg. 1 on the dynamic-hypergraph skeleton (Sec. 4.4):
+    the broadcast-message workload, directed (one sender, receivers) and
+    the same hyperedges undirected; inputs resident, CUDA events."""
+    import torch
+    from paper_2311_10337_gb300 import synth
+    hd = synth.hyper(scale=scale, directed=True)
+    res = {"recipe": hd.recipe, "hyperedges": hd.n_edges}
+    stream = torch.cuda.current_stream()
+    for name, h in (("directed", hd), ("undirected", synth.undirected_of(hd))):
+        dev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dt)).cuda()
+        args = (dev(h.t, np.int64), dev(h.s_off, np.int64), dev(h.s_vert, np.int32), h.n_vertices,
+                h.min_cluster_size)
+        kw = dict(d_off=dev(h.d_off, np.int64), d_vert=dev(h.d_vert, np.int32)) if h.directed else {}
+        out = ctx.run_hyper(*args, **kw)
+        launches = ctx.launches()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            out = ctx.run_hyper(*args, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        memb = int(h.s_off[-1]) + (int(h.d_off[-1]) if h.directed else 0)
+        res[name] = {"hyperedges_per_s": h.n_edges / (ms / 1000.0), "ms": ms, "memberships": memb,
+                     "skeleton_links": out.n_skeleton, "n_clusters": out.n_clusters,
+                     "gpu_launches_per_run": launches}
+        del args, kw, out
+    ctx.ws = None
+    torch.cuda.empty_cache()
     return res
 
 
@@ -385,6 +422,9 @@ def main():
     levels = None
     if not args.no_levels and rank == 0:
         levels = discrete_levels(ctx, src, dst, tt, w, max(1, min(args.steps, 3)), args.breakdown)
+    hyper = None
+    if args.hyper_scale > 0 and rank == 0:
+        hyper = hypergraphs(ctx, args.hyper_scale, max(1, min(args.steps, 3)))
     batch = None
     if args.batch_graphs > 0 and rank == 0:
         batch = batched_vs_plain(ctx, args.batch_graphs, max(1, min(args.steps, 3)))
@@ -417,7 +457,7 @@ def main():
                            "edges_per_gpu": E, "parallelism": "replicas only",
                            "l2": "inputs (16 B/edge = %.0f MB) exceed L2; no flush" % (16 * E / 1e6),
                            "n_clusters": n_clusters},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "discrete_dendrogram": levels,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "discrete_dendrogram": levels, "hypergraph": hyper,
                 "batch": batch, "serve": serve,
                 "gpu_launches": launches * args.steps, "clocks": clk}
         if args.breakdown:

@@ -544,3 +544,18 @@ def hyper(scale: float = 1.0, directed: bool = True, seed_offset: int = 0,
     mv[rest] = rcv_o
     return HyperWorkload("mail_u", t, m_off, mv.astype(np.int32), None, None, n_vertices,
                          min_cluster_size, "undirected " + recipe)
+
+
+def undirected_of(h: HyperWorkload) -> HyperWorkload:
+    """The same hyperedges with sources and targets merged into one member
+    set (sources first)."""
+    E = h.n_edges
+    ns, nd = np.diff(h.s_off), np.diff(h.d_off)
+    m_off = np.concatenate([[0], np.cumsum(ns + nd)]).astype(np.int64)
+    first_d = np.repeat(m_off[:-1] + ns, nd) + (np.arange(int(nd.sum())) - np.repeat(h.d_off[:-1], nd))
+    first_s = np.repeat(m_off[:-1], ns) + (np.arange(int(ns.sum())) - np.repeat(h.s_off[:-1], ns))
+    mv = np.empty(int(m_off[-1]), np.int32)
+    mv[first_s] = h.s_vert
+    mv[first_d] = h.d_vert
+    return HyperWorkload(h.name + "_u", h.t, m_off, mv, None, None, h.n_vertices, h.min_cluster_size,
+                         "undirected of " + h.recipe)
