@@ -42,6 +42,7 @@ struct Gview {
 };
 
 __device__ __forceinline__ int graph_of(const Gview &g, int64_t x) {
+    if (g.G == 1) return 0;  // one graph: no lookup (a merge's lookup is a random read)
     return x < g.E ? g.egraph[x] : (x < g.R0 ? g.egraph[g.mu[x - g.E]] : (int)(x - g.R0));
 }
 

@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(128) k_ranks_knn(const int32_t *src, const int
                                                    const int64_t *out_off, const int64_t *out_t,
                                                    const int32_t *out_id, const int64_t *in_off,
                                                    const int64_t *in_t, const int32_t *in_id,
-                                                   int32_t *brank, int32_t *arank,
+                                                   int32_t *brank, int32_t *arank, int G,
                                                    const int32_t *egraph, const int64_t *eoff,
                                                    const int32_t *gk, const int64_t *knn_off,
                                                    int64_t dmax, int32_t *knn, int64_t *core) {
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(128) k_ranks_knn(const int32_t *src, const int
         long long te = t[r];
         const int64_t e = orig_of[r];
         // the edge's graph: its k, its kNN rows, its local id base
-        const int gr = egraph[e];
+        const int gr = G > 1 ? egraph[e] : 0;  // one graph: no random lookup
         const int k = gk[gr];
         const int64_t e0 = eoff[gr];
         int32_t *row = knn + knn_off[gr] + (e - e0) * k;
@@ -321,7 +321,7 @@ dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void
     int grid = grid_for(E, 128, 1 << 20);
 #define KNN_ARGS                                                                           \
     g.isrc, g.idst, g.it, g.orig_of, E, g.out_off, g.out_t, g.out_id, g.in_off, g.in_t, g.in_id, \
-        o.brank, o.arank, p.egraph, p.eoff, p.gk, p.knn_off, p.dmax, o.knn, o.core
+        o.brank, o.arank, p.G, p.egraph, p.eoff, p.gk, p.knn_off, p.dmax, o.knn, o.core
     if (!p.knn)
         TK(c, "k_ranks", k_ranks<<<grid, 128, 0, st>>>(g.isrc, g.idst, g.it, E, g.out_off, g.out_t, g.in_off,
                                                        g.in_t, o.brank, o.arank));
