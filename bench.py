@@ -37,6 +37,13 @@ def knn_bytes_per_edge(k: int) -> int:
     return 16 + 12 * (k + 2) + 8 + 4 * k + 8
 
 
+# DRAM bytes (read + write) per edge of k_ranks_knn (k = 8) from one ncu
+# capture of the current kernel on the mid graph at scale 0.2 (10M edges:
+# 1.2518 GB read + 0.7023 GB written per launch), scaled to a launch by the
+# edges it processes; see profiles/k_ranks_knn_mid_small.md.
+KNN_TRAFFIC_BYTES_PER_EDGE_K8 = 1.954122e9 / 10_000_000
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -440,7 +447,9 @@ def main():
         achieved = (kb * E) / (dom_ms / max(dom_n, 1) / 1000.0) / 1e9 if dom_n else None
         roof = {"bound": "hbm", "kernel": args.dominant, "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": (KNN_TRAFFIC_BYTES_PER_EDGE_K8 * E
+                            if args.dominant == "k_ranks_knn" and k == 8 and args.workload == "mid" else None),
                 "algorithmic_bytes_per_launch": kb * E,
                 "avg_launch_ms": dom_ms / max(dom_n, 1) if dom_n else None}
         cpu = None
