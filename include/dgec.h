@@ -71,6 +71,10 @@ typedef struct {
     const int64_t *out_off, *in_off;   /* [n_vertices + 1] */
     const int64_t *out_t, *in_t;       /* [n_edges] */
     const int32_t *out_id, *in_id;     /* [n_edges] */
+    /* Each edge's place in those arrays: out_id[pos_out[e]] == e and
+     * in_id[pos_in[e]] == e; its index within src's list is
+     * pos_out[e] - out_off[src[e]] (likewise for dst's in-list). */
+    const int32_t *pos_out, *pos_in;   /* [n_edges] */
     /* Alg. 3: skeleton L*_G as undirected edges (u < v, w = |t_u - t_v|),
      * each line-graph edge once. Deterministic order: first every edge's
      * link to the first later out-edge at its head, then every edge's link

@@ -266,14 +266,16 @@ __global__ void k_hub_scatter(const unsigned long long *hub_of, const unsigned l
 
 __global__ void k_unpack(const unsigned long long *keys, int64_t E, const int32_t *orig_of,
                          const int64_t *it, int64_t *t_out, int32_t *id_out, int32_t *r_out,
-                         int32_t *slot_of) {
+                         int32_t *slot_of, int32_t *pos_of) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < E;
          x += (int64_t)gridDim.x * blockDim.x) {
         int32_t r = (int32_t)keys[x];
+        const int32_t e = orig_of[r];
         r_out[x] = r;
-        id_out[x] = orig_of[r];
+        id_out[x] = e;
         t_out[x] = it[r];
         if (slot_of) slot_of[r] = (int32_t)x;
+        pos_of[e] = (int32_t)x;  // the edge's place in this list array
     }
 }
 
@@ -292,6 +294,8 @@ void plan_csr(Arena &ws, const Problem &p, Csr &o) {
     o.idst = ws.take<int32_t>(p.E);
     o.it = ws.take<int64_t>(p.E);
     o.slot_out = ws.take<int32_t>(p.E);
+    o.pos_out = ws.take<int32_t>(p.E);
+    o.pos_in = ws.take<int32_t>(p.E);
 }
 
 void carve_segsort(Arena &a, int64_t V, int64_t n, SegSort &s) {
@@ -437,9 +441,9 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
     DG_TRY(sort_segments(c, V, s.okey, o.out_off, s.seg, p.idbits));
     DG_TRY(sort_segments(c, V, s.ikey, o.in_off, s.seg, p.idbits));
     TK(c, "k_unpack", k_unpack<<<gEE, kBlock, 0, st>>>(s.okey, E, o.orig_of, o.it, o.out_t, o.out_id,
-                                                       o.out_r, o.slot_out));
+                                                       o.out_r, o.slot_out, o.pos_out));
     TK(c, "k_unpack", k_unpack<<<gEE, kBlock, 0, st>>>(s.ikey, E, o.orig_of, o.it, o.in_t, o.in_id,
-                                                       o.in_r, nullptr));
+                                                       o.in_r, nullptr, o.pos_in));
     return DGEC_OK;
 }
 

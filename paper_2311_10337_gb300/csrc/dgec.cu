@@ -198,6 +198,8 @@ void fill_result(const Layout &L, dgec_result *out) {
     out->in_t = L.csr.in_t;
     out->out_id = L.csr.out_id;
     out->in_id = L.csr.in_id;
+    out->pos_out = L.csr.pos_out;
+    out->pos_in = L.csr.pos_in;
     out->sk_u = L.skel.u;
     out->sk_v = L.skel.v;
     out->sk_w = L.skel.w;

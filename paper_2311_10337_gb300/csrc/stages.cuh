@@ -63,6 +63,7 @@ struct Csr {
     int32_t *isrc, *idst;       // [E] src, dst in r order
     int64_t *it;                // [E] t in r order
     int32_t *slot_out;          // [E] by r: global slot in the out-lists
+    int32_t *pos_out, *pos_in;  // [E] by original id: position in out_id / in_id (outputs)
 };
 void plan_csr(Arena &ws, const Problem &p, Csr &o);
 size_t csr_scratch_bytes(const Problem &p);

@@ -58,7 +58,7 @@ _P = ctypes.c_void_p
 
 class Result(ctypes.Structure):
     _fields_ = [(n, _P) for n in (
-        "out_off", "in_off", "out_t", "in_t", "out_id", "in_id", "sk_u", "sk_v", "sk_w",
+        "out_off", "in_off", "out_t", "in_t", "out_id", "in_id", "pos_out", "pos_in", "sk_u", "sk_v", "sk_w",
         "knn_id", "core", "mst_u", "mst_v", "mst_w", "link_a", "link_b", "link_size",
         "fall_cluster", "fall_lambda", "cl_id", "cl_parent", "cl_birth", "cl_death",
         "cl_stab_hi", "cl_stab_lo", "cl_size", "cl_selected", "labels")] + [
@@ -508,6 +508,7 @@ class Output:
         "out_off": ("int64", "V+1"), "in_off": ("int64", "V+1"),
         "out_t": ("int64", "E"), "in_t": ("int64", "E"),
         "out_id": ("int32", "E"), "in_id": ("int32", "E"),
+        "pos_out": ("int32", "E"), "pos_in": ("int32", "E"),
         "sk_u": ("int32", "nsk"), "sk_v": ("int32", "nsk"), "sk_w": ("int64", "nsk"),
         "knn_id": ("int32", "E*k"), "core": ("int64", "E"),
         "mst_u": ("int32", "nmst"), "mst_v": ("int32", "nmst"), "mst_w": ("int64", "nmst"),

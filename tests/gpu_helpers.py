@@ -25,7 +25,7 @@ def run_gpu(src, dst, t, V, k, M, delta_max=None):
     tt = torch.from_numpy(np.ascontiguousarray(t, np.int64)).cuda()
     out = c.run(s, d, tt, V, k, M, delta_max=delta_max)
     torch.cuda.synchronize()
-    names = ["out_off", "in_off", "out_t", "in_t", "out_id", "in_id", "sk_u", "sk_v", "sk_w",
+    names = ["out_off", "in_off", "out_t", "in_t", "out_id", "in_id", "pos_out", "pos_in", "sk_u", "sk_v", "sk_w",
              "knn_id", "core", "mst_u", "mst_v", "mst_w", "link_a", "link_b", "link_size",
              "fall_cluster", "fall_lambda", "cl_id", "cl_parent", "cl_birth", "cl_death",
              "cl_stab_hi", "cl_stab_lo", "cl_size", "cl_selected", "labels"]
@@ -51,6 +51,10 @@ def compare_all(src, dst, t, V, k, M, knn_query=None, what=None, delta_max=None)
     assert np.array_equal(g["in_id"], ii), "in_id"
     assert np.array_equal(g["out_t"], t[oi]), "out_t"
     assert np.array_equal(g["in_t"], t[ii]), "in_t"
+    for pos, lst in (("pos_out", oi), ("pos_in", ii)):    # inverse of the list permutation
+        want = np.empty(E, np.int32)
+        want[lst] = np.arange(E, dtype=np.int32)
+        assert np.array_equal(g[pos], want), pos
     su, sv, sw = r["skeleton"]
     gu, gv, gw = sorted_skeleton(g["sk_u"], g["sk_v"], g["sk_w"])
     assert len(gu) == len(su), f"skeleton size {len(gu)} vs {len(su)}"
