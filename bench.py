@@ -73,7 +73,25 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The slowest rank's value (timings are max over ranks); x itself at N = 1."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: int, seconds: float) -> float:
+    """Whole-job throughput of N replicas: every rank's units over the slowest
+    rank's time (weak scaling: each rank runs its own graph)."""
+    return world * units_per_rank / seconds
+
+
 def make_workload(name, scale, rank):
+    """Rank r's graph: the same recipe and size, its own seed."""
     from paper_2311_10337_gb300 import synth
     if name == "mid":
         return synth.mid(scale=scale, seed_offset=rank)
@@ -397,10 +415,8 @@ def main():
     ms = ev0.elapsed_time(ev1) / args.steps
     dom = ctx.kernel_timing().get(args.dominant, (0.0, 0))
     ctx.set_kernel_timing(0)
+    ms = max_over_ranks(ms, world, "cuda")
     if world > 1:
-        tmax = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        ms = float(tmax.item())
         dist.barrier()
     clk = clocks.stop()
     n_clusters = out.n_clusters
@@ -420,11 +436,8 @@ def main():
             ctx.run_host(hs, hd, ht, V, k, M, labels_out=lab)
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / args.steps
-        if world > 1:
-            tm = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-            e2e_s = float(tm.item())
-        e2e = {"value": world * E / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * E,
+        e2e_s = max_over_ranks(e2e_s, world, "cuda")
+        e2e = {"value": job_rate(world, E, e2e_s), "unit": UNIT, "h2d_bytes_per_step": 16 * E,
                "d2h_bytes_per_step": 4 * E}
     levels = None
     if not args.no_levels and rank == 0:
@@ -458,7 +471,7 @@ def main():
                 cpu = cpu_baseline(w, args.cpu_sample_minutes)
             except Exception as ex:  # the baseline is a report, never the product path
                 cpu = {"error": str(ex)}
-        line = {"metric": METRIC, "value": world * E / (ms / 1000.0), "unit": UNIT,
+        line = {"metric": METRIC, "value": job_rate(world, E, ms / 1000.0), "unit": UNIT,
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "int64", "data": "synthetic",
