@@ -283,3 +283,42 @@ def hyper_run(t, n_vertices, s_off, s_vert, d_off=None, d_vert=None, M=5):
     a, b, s = out["linkage"]
     out["condensed"] = condense(E, a, b, mw, s, M)
     return out
+
+
+def mrd_graph(src, dst, t, n_vertices, k, delta_max=None):
+    """Mutual-reachability mode (an approximation; not in the paper): the
+    graph H = L* together with every edge's kNN pairs, each pair once, weighed
+    max(core_a, core_b, |t_a - t_b|) (HDBSCAN's mutual reachability with the
+    kNN core distances); pairs with an endpoint of infinite core (fewer than
+    k neighbours) are dropped. Returns (u, v, w) with u < v, sorted by
+    (u, v)."""
+    src, dst, t = _c(src, np.int32), _c(dst, np.int32), _c(t, np.int64)
+    E = src.shape[0]
+    if delta_max is None:
+        u, v, _ = skeleton(src, dst, t, n_vertices)
+    else:
+        u, v, _ = skeleton_cutoff(src, dst, t, n_vertices, delta_max)
+    ids, core = knn(src, dst, t, n_vertices, k, None, delta_max)
+    a = np.repeat(np.arange(E, dtype=np.int64), k)
+    b = ids.reshape(-1).astype(np.int64)
+    a, b = a[b >= 0], b[b >= 0]
+    lo = np.concatenate([u.astype(np.int64), np.minimum(a, b)])
+    hi = np.concatenate([v.astype(np.int64), np.maximum(a, b)])
+    pairs = np.unique(lo * max(E, 1) + hi)                     # the union, as a set
+    lo, hi = pairs // max(E, 1), pairs % max(E, 1)
+    w = np.maximum(np.maximum(core[lo], core[hi]), np.abs(t[lo] - t[hi]))
+    keep = w != INT64_MAX
+    return lo[keep].astype(np.int32), hi[keep].astype(np.int32), w[keep].astype(np.int64)
+
+
+def mrd_run(src, dst, t, n_vertices, k, M, delta_max=None):
+    """Alg. 1 on the mutual-reachability graph H (see mrd_graph)."""
+    E = len(src)
+    out = {"graph": mrd_graph(src, dst, t, n_vertices, k, delta_max)}
+    u, v, w = out["graph"]
+    out["mst"] = mst(E, u, v, w)
+    mu, mv, mw = out["mst"]
+    out["linkage"] = linkage(E, mu, mv)
+    a, b, s = out["linkage"]
+    out["condensed"] = condense(E, a, b, mw, s, M)
+    return out
