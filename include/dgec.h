@@ -49,11 +49,21 @@ typedef enum {
 
 /* flags of dgec_params */
 #define DGEC_CUTOFF 1u  /* time cutoff of Sec. 4.3: keep only line-graph arcs with w <= delta_max */
+/* Mutual-reachability mode -- an approximation with no counterpart in the
+ * paper: cluster the graph H = L*_G together with every edge's kNN pairs
+ * (each pair once), weighed max(core_a, core_b, |t_a - t_b|) as in HDBSCAN,
+ * instead of L*_G under P3. Pairs with an endpoint of infinite core (fewer
+ * than k neighbours) are dropped. Thm. 3 does not hold for these weights, so
+ * H does not reproduce clustering the full line graph with them; with k = 1
+ * the result equals the plain method. The skeleton outputs stay L*_G; the
+ * forest, dendrogram, condensed tree and labels refer to H. Uses about
+ * (2 + k) * 40 more workspace bytes per edge. */
+#define DGEC_MRD 2u
 
 typedef struct {
     int32_t k;                /* neighbours per edge for the kNN output, 1 <= k <= 16 */
     int32_t min_cluster_size; /* M of Alg. 1 step 4, M >= 2 */
-    uint32_t flags;           /* 0 or DGEC_CUTOFF */
+    uint32_t flags;           /* 0, or DGEC_CUTOFF and/or DGEC_MRD */
     int64_t delta_max;        /* with DGEC_CUTOFF: the cutoff, >= 0 (ignored otherwise). Only arcs
                                  with w <= delta_max are in the line graph: the skeleton keeps the
                                  links with w <= delta_max (exact by Thm. 3), the kNN lists only

@@ -17,6 +17,7 @@ struct Layout {
     int32_t *gk, *gM, *egraph;
     Csr csr;
     Skel skel;
+    Skel mrd;  // stage M output (mutual-reachability mode only)
     Msf msf;
     Dendro den;
     Condensed cond;
@@ -33,6 +34,7 @@ struct HostBatch {
     const int32_t *k;     // [G]
     const int32_t *M;     // [G]
     int64_t dmax = INT64_MAX;  // time cutoff, INT64_MAX = none
+    bool mrd = false;          // mutual-reachability mode (one graph only)
 };
 
 Problem make_problem(const HostBatch &hb) {
@@ -53,6 +55,8 @@ Problem make_problem(const HostBatch &hb) {
     p.k = kmax;
     p.M = Mmin;
     p.dmax = hb.dmax;
+    p.mrd = hb.mrd;
+    if (p.mrd) p.links_cap = 2 * p.E + p.E * (int64_t)p.k;
     return p;
 }
 
@@ -67,6 +71,7 @@ Layout plan(void *base, const Problem &p) {
     L.egraph = a.take<int32_t>(p.E);
     plan_csr(a, p, L.csr);
     plan_skel(a, p, L.skel);
+    if (p.mrd) plan_mrd(a, p, L.mrd);
     plan_msf(a, p, L.msf);
     plan_dendro(a, p, L.den);
     plan_condensed(a, p, L.cond);
@@ -80,6 +85,7 @@ Layout plan(void *base, const Problem &p) {
     }
     size_t scr = std::max({csr_scratch_bytes(p), skel_scratch_bytes(p), msf_scratch_bytes(p),
                            dendro_scratch_bytes(p), condense_scratch_bytes(p)});
+    if (p.mrd) scr = std::max(scr, mrd_scratch_bytes(p));
     L.scratch = a.take<char>(scr);
     L.total = a.off + 256;
     return L;
@@ -105,7 +111,7 @@ dgec_status check_batch(Ctx *c, const HostBatch &hb) {
 
 dgec_status check_params(Ctx *c, const dgec_params *prm) {
     if (!prm) return set_err(c, DGEC_ERR_INVALID_ARG, "params is null");
-    if (prm->flags & ~DGEC_CUTOFF) return set_err(c, DGEC_ERR_INVALID_ARG, "unknown flags");
+    if (prm->flags & ~(DGEC_CUTOFF | DGEC_MRD)) return set_err(c, DGEC_ERR_INVALID_ARG, "unknown flags");
     if ((prm->flags & DGEC_CUTOFF) && prm->delta_max < 0)
         return set_err(c, DGEC_ERR_INVALID_ARG, "delta_max must be >= 0");
     return DGEC_OK;
@@ -176,7 +182,12 @@ dgec_status run_pipeline(Ctx *c, const HostBatch &hb, const int32_t *d_src, cons
     p.egraph = L.egraph;
     DG_TRY(stage_csr(c, p, L.csr, L.scratch));
     DG_TRY(stage_skeleton(c, p, L.csr, L.skel, L.scratch));
-    DG_TRY(stage_msf(c, p, L.csr, L.skel, L.msf, L.scratch));
+    const Skel *forest_in = &L.skel;
+    if (p.mrd) {
+        DG_TRY(stage_mrd(c, p, L.csr, L.skel, L.mrd, L.scratch));
+        forest_in = &L.mrd;
+    }
+    DG_TRY(stage_msf(c, p, L.csr, *forest_in, L.msf, L.scratch));
     DG_TRY(stage_dendro(c, p, L.csr, L.msf, L.den, L.scratch));
     DG_TRY(stage_condense(c, p, L.msf, L.den, L.cond, L.scratch));
     if (p.G > 1 && L.msf.n > 0)
@@ -388,6 +399,7 @@ dgec_status dgec_workspace_size(int64_t n_edges, int32_t n_vertices, const dgec_
     DG_TRY(check_params(nullptr, params));
     int64_t eoff[2] = {0, n_edges};
     HostBatch hb{1, eoff, &n_vertices, &params->k, &params->min_cluster_size};
+    hb.mrd = params->flags & DGEC_MRD;
     if (n_edges < 0) return DGEC_ERR_INVALID_ARG;
     DG_TRY(check_batch(nullptr, hb));
     *bytes = plan(nullptr, make_problem(hb)).total;
@@ -407,6 +419,7 @@ dgec_status dgec_run(dgec_ctx *x, const int32_t *d_src, const int32_t *d_dst, co
     int64_t eoff[2] = {0, n_edges};
     HostBatch hb{1, eoff, &n_vertices, &params->k, &params->min_cluster_size};
     if (params->flags & DGEC_CUTOFF) hb.dmax = params->delta_max;
+    hb.mrd = params->flags & DGEC_MRD;
     DG_TRY(check_batch(c, hb));
     CU_TRY(c, cudaSetDevice(c->device));
     c->stream = (cudaStream_t)stream;

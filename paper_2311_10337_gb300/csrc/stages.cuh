@@ -28,6 +28,7 @@ struct Problem {
     bool knn = true;                  // stage B also writes the kNN lists
     int64_t dmax = INT64_MAX;         // time cutoff (Sec. 4.3): only links with w <= dmax
     int64_t links_cap = -1;           // skeleton capacity; -1 = 2E (graphs: <= 2 links per edge)
+    bool mrd = false;                 // cluster the mutual-reachability graph (stage M)
 };
 
 inline int64_t link_cap(const Problem &p) { return p.links_cap >= 0 ? p.links_cap : 2 * p.E; }
@@ -84,6 +85,13 @@ void plan_skel(Arena &ws, const Problem &p, Skel &o);
 size_t skel_scratch_bytes(const Problem &p);
 // also writes the kNN ids and core distances (same searches) unless p.knn is off
 dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void *scratch);
+
+// Stage M (optional): the mutual-reachability graph H = L* plus every kNN
+// pair, weighed max(core_a, core_b, |dt|); an approximation (Thm. 3 does not
+// hold for these weights). Capacity: link_cap(p) = 2E + E k.
+void plan_mrd(Arena &ws, const Problem &p, Skel &h);
+size_t mrd_scratch_bytes(const Problem &p);
+dgec_status stage_mrd(Ctx *c, const Problem &p, const Csr &g, const Skel &sk, Skel &h, void *scratch);
 
 // Stage C: minimum spanning forest of the skeleton (Borůvka), sorted by
 // (w, u, v).

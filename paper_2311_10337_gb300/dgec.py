@@ -40,6 +40,7 @@ class DgecError(RuntimeError):
 
 
 CUTOFF = 1
+MRD = 2
 
 
 class Params(ctypes.Structure):
@@ -47,10 +48,9 @@ class Params(ctypes.Structure):
                 ("flags", ctypes.c_uint32), ("delta_max", ctypes.c_int64)]
 
 
-def _params(k, min_cluster_size, delta_max=None):
-    if delta_max is None:
-        return Params(k, min_cluster_size, 0, 0)
-    return Params(k, min_cluster_size, CUTOFF, int(delta_max))
+def _params(k, min_cluster_size, delta_max=None, mrd=False):
+    flags = (CUTOFF if delta_max is not None else 0) | (MRD if mrd else 0)
+    return Params(k, min_cluster_size, flags, int(delta_max) if delta_max is not None else 0)
 
 
 _P = ctypes.c_void_p
@@ -183,9 +183,9 @@ def msf_static(u, v, w, n_nodes: int, out_u, out_v, out_w, stream=None) -> int:
     return int(n.value)
 
 
-def workspace_size(n_edges: int, n_vertices: int, k: int, min_cluster_size: int) -> int:
+def workspace_size(n_edges: int, n_vertices: int, k: int, min_cluster_size: int, mrd: bool = False) -> int:
     L = load()
-    p = _params(k, min_cluster_size)
+    p = _params(k, min_cluster_size, None, mrd)
     out = ctypes.c_size_t(0)
     rc = L.dgec_workspace_size(n_edges, n_vertices, ctypes.byref(p), ctypes.byref(out))
     if rc != DGEC_OK:
@@ -256,17 +256,18 @@ class Context:
         return out
 
     def run(self, src, dst, t, n_vertices: int, k: int, min_cluster_size: int, stream=None,
-            delta_max=None):
+            delta_max=None, mrd: bool = False):
         """Alg. 4 on device tensors (int32 src/dst, int64 t). Returns an
         Output whose tensors view the workspace (valid until the next run).
-        delta_max: the time cutoff of Sec. 4.3 (None = no cutoff)."""
+        delta_max: the time cutoff of Sec. 4.3 (None = no cutoff); mrd: cluster
+        the mutual-reachability graph (an approximation, see dgec.h)."""
         torch = self.torch
         E = int(src.shape[0])
         for x, dt in ((src, torch.int32), (dst, torch.int32), (t, torch.int64)):
             if x.dtype != dt or not x.is_cuda or not x.is_contiguous():
                 raise ValueError("src/dst must be contiguous cuda int32, t cuda int64")
-        p = _params(k, min_cluster_size, delta_max)
-        need = workspace_size(E, n_vertices, k, min_cluster_size)
+        p = _params(k, min_cluster_size, delta_max, mrd)
+        need = workspace_size(E, n_vertices, k, min_cluster_size, mrd)
         ws = self.workspace(need)
         st = stream if stream is not None else torch.cuda.current_stream(self.device)
         res = Result()
@@ -335,13 +336,13 @@ class Context:
 
     def run_host(self, src: np.ndarray, dst: np.ndarray, t: np.ndarray, n_vertices: int, k: int,
                  min_cluster_size: int, labels_out: np.ndarray | None = None, stream=None,
-                 delta_max=None):
+                 delta_max=None, mrd: bool = False):
         """Alg. 4 from host arrays (pinned numpy views avoid staging copies);
         returns (labels, n_clusters)."""
         torch = self.torch
         E = int(src.shape[0])
-        p = _params(k, min_cluster_size, delta_max)
-        need = workspace_size(E, n_vertices, k, min_cluster_size) + 16 * E + 4096
+        p = _params(k, min_cluster_size, delta_max, mrd)
+        need = workspace_size(E, n_vertices, k, min_cluster_size, mrd) + 16 * E + 4096
         ws = self.workspace(need)
         if labels_out is None:
             labels_out = np.empty(E, np.int32)
