@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--serve-pool-gb", type=float, default=72.0)
     ap.add_argument("--hyper-scale", type=float, default=1.0,
                     help="scale of the hypergraph (broadcast message) measurement; 0 = skip")
+    ap.add_argument("--no-mrd", action="store_true",
+                    help="skip the mutual-reachability mode measurement")
     ap.add_argument("--no-levels", action="store_true",
                     help="skip the discrete-dendrogram (Alg. 5) measurement")
     ap.add_argument("--breakdown", action="store_true",
@@ -245,6 +247,31 @@ def discrete_levels(ctx, src, dst, tt, w, steps, breakdown=False):
         res["kernel_breakdown_ms"] = {n: [round(v[0], 3), v[1]] for n, v in
                                       sorted(ctx.kernel_timing().items(), key=lambda kv: -kv[1][0])}
         ctx.set_kernel_timing(0)
+    return res
+
+
+def mutual_reachability(ctx, src, dst, tt, w, steps):
+    """Edges/s of the whole path in the mutual-reachability mode (the
+    skeleton plus every kNN pair, weights max(core, core, |dt|)) on the same
+    graph; inputs resident, CUDA events."""
+    import torch
+    E, V, k, M = w.n_edges, w.n_vertices, w.k, w.min_cluster_size
+    out = ctx.run(src, dst, tt, V, k, M, mrd=True)
+    launches = ctx.launches()
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        out = ctx.run(src, dst, tt, V, k, M, mrd=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    res = {"edges_per_s": E / (ms / 1000.0), "ms": ms, "forest_edges": out.n_mst,
+           "n_clusters": out.n_clusters, "gpu_launches_per_run": launches}
+    ctx.ws = None
+    torch.cuda.empty_cache()
     return res
 
 
@@ -442,6 +469,9 @@ def main():
     levels = None
     if not args.no_levels and rank == 0:
         levels = discrete_levels(ctx, src, dst, tt, w, max(1, min(args.steps, 3)), args.breakdown)
+    mrd = None
+    if not args.no_mrd and rank == 0:
+        mrd = mutual_reachability(ctx, src, dst, tt, w, max(1, min(args.steps, 3)))
     hyper = None
     if args.hyper_scale > 0 and rank == 0:
         hyper = hypergraphs(ctx, args.hyper_scale, max(1, min(args.steps, 3)))
@@ -480,6 +510,7 @@ def main():
                            "l2": "inputs (16 B/edge = %.0f MB) exceed L2; no flush" % (16 * E / 1e6),
                            "n_clusters": n_clusters},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "discrete_dendrogram": levels, "hypergraph": hyper,
+                "mutual_reachability": mrd,
                 "batch": batch, "serve": serve,
                 "gpu_launches": launches * args.steps, "clocks": clk}
         if args.breakdown:
