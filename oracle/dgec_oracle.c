@@ -232,10 +232,13 @@ static int cmp_cand(const void *a, const void *b)
 
 /* Queries: n_query edge ids; knn_out[n_query * k], core_out[n_query].
  * dmax: the time cutoff of Sec. 4.3 -- only arcs with w <= dmax are in
- * the line graph, so only such neighbours count (INT64_MAX: no cutoff). */
+ * the line graph, so only such neighbours count (INT64_MAX: no cutoff).
+ * dnc: the nearly-causal tolerance of Sec. 4.3 -- an arc r -> s also
+ * exists when s is at most dnc earlier than r (t_s >= t_r - dnc), weighed
+ * |t_s - t_r| (0: the causal line graph of Def. 1). */
 int orc_knn(int64_t n_edges, int32_t n_vertices, const int32_t *src,
             const int32_t *dst, const int64_t *t, int32_t k,
-            int64_t n_query, const int32_t *query, int64_t dmax,
+            int64_t n_query, const int32_t *query, int64_t dmax, int64_t dnc,
             int32_t *knn_out, int64_t *core_out)
 {
     if (k < 1) return ORC_ERR_ARG;
@@ -260,11 +263,15 @@ int orc_knn(int64_t n_edges, int32_t n_vertices, const int32_t *src,
         int64_t nc = 0;
         for (int64_t x = in_off[i]; x < in_off[i + 1]; x++) {   /* predecessors */
             int32_t r = in_id[x];
-            if (t[r] <= t[e] && t[e] - t[r] <= dmax) { c[nc].w = t[e] - t[r]; c[nc].id = r; nc++; }
+            int64_t d = t[e] - t[r];                             /* arc r -> e: t_e >= t_r - dnc */
+            int64_t w = d < 0 ? -d : d;
+            if (d >= -dnc && w <= dmax) { c[nc].w = w; c[nc].id = r; nc++; }
         }
         for (int64_t x = out_off[j]; x < out_off[j + 1]; x++) { /* successors */
             int32_t s = out_id[x];
-            if (t[s] >= t[e] && t[s] - t[e] <= dmax) { c[nc].w = t[s] - t[e]; c[nc].id = s; nc++; }
+            int64_t d = t[s] - t[e];                             /* arc e -> s: t_s >= t_e - dnc */
+            int64_t w = d < 0 ? -d : d;
+            if (d >= -dnc && w <= dmax) { c[nc].w = w; c[nc].id = s; nc++; }
         }
         qsort(c, (size_t)nc, sizeof(cand), cmp_cand);
         int32_t got = 0;

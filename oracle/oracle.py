@@ -47,7 +47,7 @@ def lib():
             L.orc_skeleton_raw.restype = i64
             L.orc_skeleton.argtypes = [i64, i32, I32P, I32P, I64P, I32P, I32P, I64P]
             L.orc_skeleton.restype = i64
-            L.orc_knn.argtypes = [i64, i32, I32P, I32P, I64P, i32, i64, I32P, i64, I32P, I64P]
+            L.orc_knn.argtypes = [i64, i32, I32P, I32P, I64P, i32, i64, I32P, i64, i64, I32P, I64P]
             L.orc_mst.argtypes = [i64, i64, I32P, I32P, I64P, I32P, I32P, I64P]
             L.orc_mst.restype = i64
             L.orc_linkage.argtypes = [i64, i64, I32P, I32P, I32P, I32P, I64P]
@@ -110,9 +110,11 @@ def skeleton(src, dst, t, n_vertices):
 INT64_MAX = np.iinfo(np.int64).max
 
 
-def knn(src, dst, t, n_vertices, k, query=None, delta_max=None):
+def knn(src, dst, t, n_vertices, k, query=None, delta_max=None, delta_nc=0):
     """k nearest line-graph neighbours by (w, id); with delta_max, only arcs
-    with w <= delta_max exist (the cutoff of Sec. 4.3)."""
+    with w <= delta_max exist (the cutoff of Sec. 4.3); with delta_nc > 0 an
+    arc may also point up to delta_nc back in time (nearly causal, Sec. 4.3),
+    weighed |dt|."""
     src, dst, t = _c(src, np.int32), _c(dst, np.int32), _c(t, np.int64)
     E = src.shape[0]
     if query is None:
@@ -122,7 +124,7 @@ def knn(src, dst, t, n_vertices, k, query=None, delta_max=None):
     ids = np.zeros(max(nq * k, 1), np.int32)
     core = np.zeros(max(nq, 1), np.int64)
     dmax = INT64_MAX if delta_max is None else int(delta_max)
-    rc = lib().orc_knn(E, n_vertices, src, dst, t, k, nq, query, dmax, ids, core)
+    rc = lib().orc_knn(E, n_vertices, src, dst, t, k, nq, query, dmax, int(delta_nc), ids, core)
     if rc:
         raise ValueError(f"oracle knn rc={rc}")
     return ids[:nq * k].reshape(nq, k), core[:nq]
@@ -316,6 +318,48 @@ def mrd_run(src, dst, t, n_vertices, k, M, delta_max=None):
     E = len(src)
     out = {"graph": mrd_graph(src, dst, t, n_vertices, k, delta_max)}
     u, v, w = out["graph"]
+    out["mst"] = mst(E, u, v, w)
+    mu, mv, mw = out["mst"]
+    out["linkage"] = linkage(E, mu, mv)
+    a, b, s = out["linkage"]
+    out["condensed"] = condense(E, a, b, mw, s, M)
+    return out
+
+
+def skeleton_nearly_causal(src, dst, t, n_vertices, delta_nc, delta_max=None):
+    """Skeleton of the nearly-causal line graph of Sec. 4.3: an arc r -> s
+    (dst r = src s) exists when t_s >= t_r - delta_nc, weighed |t_s - t_r|.
+    At a vertex these arcs are the causal ones (t_r <= t_s) and the backward
+    ones (t_s < t_r <= t_s + delta_nc). An MST of a union of two graphs lies
+    in the union of their MSTs, Alg. 2 gives the causal part's (Thm. 2), and
+    Alg. 2 on the graph with negated times gives the MST of all backward
+    pairs, whose links with w <= delta_nc are the MSF of the capped family
+    (Kruskal stopped at delta_nc). So the union of L*(G) and the links of
+    L*(G with -t) with w <= delta_nc keeps the weighted connectivity. With
+    delta_max, only links with w <= delta_max are kept. Sorted (w, u, v)."""
+    u1, v1, w1 = skeleton(src, dst, t, n_vertices)
+    u2, v2, w2 = skeleton(src, dst, -np.asarray(t, np.int64), n_vertices)
+    keep = w2 <= delta_nc
+    u = np.concatenate([u1, u2[keep]]).astype(np.int64)
+    v = np.concatenate([v1, v2[keep]]).astype(np.int64)
+    w = np.concatenate([w1, w2[keep]])
+    E = max(len(src), 1)
+    key, first = np.unique(u * E + v, return_index=True)      # the union, as a set
+    u, v, w = u[first], v[first], w[first]
+    if delta_max is not None:
+        m = w <= delta_max
+        u, v, w = u[m], v[m], w[m]
+    o = np.lexsort((v, u, w))
+    return u[o].astype(np.int32), v[o].astype(np.int32), w[o].astype(np.int64)
+
+
+def run_nearly_causal(src, dst, t, n_vertices, k, M, delta_nc, delta_max=None):
+    """Alg. 4 on the nearly-causal line graph (Sec. 4.3)."""
+    E = len(src)
+    out = {"csr": csr(src, dst, t, n_vertices)}
+    out["skeleton"] = skeleton_nearly_causal(src, dst, t, n_vertices, delta_nc, delta_max)
+    out["knn"] = knn(src, dst, t, n_vertices, k, None, delta_max, delta_nc)
+    u, v, w = out["skeleton"]
     out["mst"] = mst(E, u, v, w)
     mu, mv, mw = out["mst"]
     out["linkage"] = linkage(E, mu, mv)

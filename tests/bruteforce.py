@@ -17,6 +17,18 @@ def line_graph_arcs(src, dst, t):
     return r, s, t[s] - t[r]
 
 
+def undirected_edges_nc(src, dst, t, delta_nc):
+    """Undirected nearly-causal line graph (Sec. 4.3): r and s joined when
+    dst r = src s and t_s >= t_r - delta_nc, weight |t_s - t_r|."""
+    E = len(src)
+    out = {}
+    for r in range(E):
+        for s in range(E):
+            if r != s and dst[r] == src[s] and int(t[s]) >= int(t[r]) - delta_nc:
+                out[(min(r, s), max(r, s))] = abs(int(t[s]) - int(t[r]))
+    return out
+
+
 def undirected_edges(src, dst, t):
     """Undirected version of L_G as a dict {(min, max): w} (weak connectivity,
     Sec. 1.2.3). Two arcs between one pair exist only for a reciprocal,
@@ -88,11 +100,12 @@ def minimax(n, edges):
     return D
 
 
-def knn_bruteforce(src, dst, t, k, delta_max=None):
+def knn_bruteforce(src, dst, t, k, delta_max=None, delta_nc=0):
     """Neighbours of each node in the undirected L_G ranked by (w, id); with
-    delta_max, in the line graph keeping only arcs with w <= delta_max."""
+    delta_max, in the line graph keeping only arcs with w <= delta_max; with
+    delta_nc, in the nearly-causal line graph."""
     E = len(src)
-    und = undirected_edges(src, dst, t)
+    und = undirected_edges(src, dst, t) if not delta_nc else undirected_edges_nc(src, dst, t, delta_nc)
     if delta_max is not None:
         und = {key: w for key, w in und.items() if w <= delta_max}
     nb = [[] for _ in range(E)]
