@@ -59,15 +59,26 @@ typedef enum {
  * forest, dendrogram, condensed tree and labels refer to H. Uses about
  * (2 + k) * 40 more workspace bytes per edge. */
 #define DGEC_MRD 2u
+/* Nearly-causal line graph of Sec. 4.3: an arc r -> s (dst r = src s) also
+ * exists when s is at most delta_nc earlier than r (t_s >= t_r - delta_nc),
+ * weighed |t_s - t_r|, to absorb timestamp error. Its skeleton is L*_G
+ * together with the links of the skeleton of G with negated times whose
+ * weight is <= delta_nc (an MST of a union of graphs lies in the union of
+ * their MSTs; on negated times Alg. 2 gives the backward arcs' MST), which
+ * keeps the weighted connectivity; the kNN lists count backward neighbours
+ * within delta_nc too. The skeleton outputs are then ordered by (u, v).
+ * delta_nc = 0 is the causal method. Not combined with DGEC_MRD. */
+#define DGEC_NEARLY_CAUSAL 4u
 
 typedef struct {
     int32_t k;                /* neighbours per edge for the kNN output, 1 <= k <= 16 */
     int32_t min_cluster_size; /* M of Alg. 1 step 4, M >= 2 */
-    uint32_t flags;           /* 0, or DGEC_CUTOFF and/or DGEC_MRD */
+    uint32_t flags;           /* 0, or any of DGEC_CUTOFF, DGEC_MRD, DGEC_NEARLY_CAUSAL */
     int64_t delta_max;        /* with DGEC_CUTOFF: the cutoff, >= 0 (ignored otherwise). Only arcs
                                  with w <= delta_max are in the line graph: the skeleton keeps the
                                  links with w <= delta_max (exact by Thm. 3), the kNN lists only
                                  neighbours within delta_max, and everything downstream follows. */
+    int64_t delta_nc;         /* with DGEC_NEARLY_CAUSAL: the tolerance, >= 0 (ignored otherwise) */
 } dgec_params;
 
 typedef struct dgec_ctx dgec_ctx;

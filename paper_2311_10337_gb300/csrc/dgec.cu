@@ -18,6 +18,10 @@ struct Layout {
     Csr csr;
     Skel skel;
     Skel mrd;  // stage M output (mutual-reachability mode only)
+    bool nc = false;  // nearly-causal mode: stage A/B again on negated times, stage N
+    int64_t *tneg = nullptr;
+    Csr csr2;
+    Skel skel2, ncs;
     Msf msf;
     Dendro den;
     Condensed cond;
@@ -35,6 +39,7 @@ struct HostBatch {
     const int32_t *M;     // [G]
     int64_t dmax = INT64_MAX;  // time cutoff, INT64_MAX = none
     bool mrd = false;          // mutual-reachability mode (one graph only)
+    int64_t dnc = 0;           // nearly-causal tolerance (one graph only), 0 = causal
 };
 
 Problem make_problem(const HostBatch &hb) {
@@ -56,7 +61,9 @@ Problem make_problem(const HostBatch &hb) {
     p.M = Mmin;
     p.dmax = hb.dmax;
     p.mrd = hb.mrd;
+    p.dnc = hb.dnc;
     if (p.mrd) p.links_cap = 2 * p.E + p.E * (int64_t)p.k;
+    if (p.dnc > 0) p.links_cap = 4 * p.E;
     return p;
 }
 
@@ -72,6 +79,13 @@ Layout plan(void *base, const Problem &p) {
     plan_csr(a, p, L.csr);
     plan_skel(a, p, L.skel);
     if (p.mrd) plan_mrd(a, p, L.mrd);
+    if (p.dnc > 0) {
+        L.nc = true;
+        L.tneg = a.take<int64_t>(p.E);
+        plan_csr(a, p, L.csr2);
+        plan_skel(a, p, L.skel2);
+        plan_nc(a, p, L.ncs);
+    }
     plan_msf(a, p, L.msf);
     plan_dendro(a, p, L.den);
     plan_condensed(a, p, L.cond);
@@ -86,6 +100,7 @@ Layout plan(void *base, const Problem &p) {
     size_t scr = std::max({csr_scratch_bytes(p), skel_scratch_bytes(p), msf_scratch_bytes(p),
                            dendro_scratch_bytes(p), condense_scratch_bytes(p)});
     if (p.mrd) scr = std::max(scr, mrd_scratch_bytes(p));
+    if (p.dnc > 0) scr = std::max(scr, nc_scratch_bytes(p));
     L.scratch = a.take<char>(scr);
     L.total = a.off + 256;
     return L;
@@ -111,7 +126,12 @@ dgec_status check_batch(Ctx *c, const HostBatch &hb) {
 
 dgec_status check_params(Ctx *c, const dgec_params *prm) {
     if (!prm) return set_err(c, DGEC_ERR_INVALID_ARG, "params is null");
-    if (prm->flags & ~(DGEC_CUTOFF | DGEC_MRD)) return set_err(c, DGEC_ERR_INVALID_ARG, "unknown flags");
+    if (prm->flags & ~(DGEC_CUTOFF | DGEC_MRD | DGEC_NEARLY_CAUSAL))
+        return set_err(c, DGEC_ERR_INVALID_ARG, "unknown flags");
+    if ((prm->flags & DGEC_NEARLY_CAUSAL) && prm->delta_nc < 0)
+        return set_err(c, DGEC_ERR_INVALID_ARG, "delta_nc must be >= 0");
+    if ((prm->flags & DGEC_NEARLY_CAUSAL) && (prm->flags & DGEC_MRD))
+        return set_err(c, DGEC_ERR_INVALID_ARG, "the nearly-causal and mutual-reachability modes do not combine");
     if ((prm->flags & DGEC_CUTOFF) && prm->delta_max < 0)
         return set_err(c, DGEC_ERR_INVALID_ARG, "delta_max must be >= 0");
     return DGEC_OK;
@@ -183,6 +203,15 @@ dgec_status run_pipeline(Ctx *c, const HostBatch &hb, const int32_t *d_src, cons
     DG_TRY(stage_csr(c, p, L.csr, L.scratch));
     DG_TRY(stage_skeleton(c, p, L.csr, L.skel, L.scratch));
     const Skel *forest_in = &L.skel;
+    if (p.dnc > 0) {
+        DG_TRY(stage_nc_negate(c, p, L.tneg));
+        Problem p2 = p;
+        p2.t = L.tneg;
+        DG_TRY(stage_csr(c, p2, L.csr2, L.scratch));
+        DG_TRY(stage_skeleton(c, p2, L.csr2, L.skel2, L.scratch));
+        DG_TRY(stage_nc(c, p, L.csr, L.skel, L.skel2, L.ncs, L.scratch));
+        forest_in = &L.ncs;
+    }
     if (p.mrd) {
         DG_TRY(stage_mrd(c, p, L.csr, L.skel, L.mrd, L.scratch));
         forest_in = &L.mrd;
@@ -211,11 +240,12 @@ void fill_result(const Layout &L, dgec_result *out) {
     out->in_id = L.csr.in_id;
     out->pos_out = L.csr.pos_out;
     out->pos_in = L.csr.pos_in;
-    out->sk_u = L.skel.u;
-    out->sk_v = L.skel.v;
-    out->sk_w = L.skel.w;
-    out->knn_id = L.skel.knn;
-    out->core = L.skel.core;
+    const Skel &sk = L.nc ? L.ncs : L.skel;
+    out->sk_u = sk.u;
+    out->sk_v = sk.v;
+    out->sk_w = sk.w;
+    out->knn_id = sk.knn;
+    out->core = sk.core;
     out->mst_u = L.msf.u;
     out->mst_v = L.msf.v;
     out->mst_w = L.msf.w;
@@ -233,7 +263,7 @@ void fill_result(const Layout &L, dgec_result *out) {
     out->cl_size = L.cond.cl_size;
     out->cl_selected = L.cond.cl_selected;
     out->labels = L.cond.labels;
-    out->n_skeleton = L.skel.n;
+    out->n_skeleton = sk.n;
     out->n_mst = L.msf.n;
     out->n_condensed = L.cond.n_cl;
     out->n_clusters = L.cond.n_clusters;
@@ -400,6 +430,7 @@ dgec_status dgec_workspace_size(int64_t n_edges, int32_t n_vertices, const dgec_
     int64_t eoff[2] = {0, n_edges};
     HostBatch hb{1, eoff, &n_vertices, &params->k, &params->min_cluster_size};
     hb.mrd = params->flags & DGEC_MRD;
+    if (params->flags & DGEC_NEARLY_CAUSAL) hb.dnc = params->delta_nc;
     if (n_edges < 0) return DGEC_ERR_INVALID_ARG;
     DG_TRY(check_batch(nullptr, hb));
     *bytes = plan(nullptr, make_problem(hb)).total;
@@ -420,6 +451,7 @@ dgec_status dgec_run(dgec_ctx *x, const int32_t *d_src, const int32_t *d_dst, co
     HostBatch hb{1, eoff, &n_vertices, &params->k, &params->min_cluster_size};
     if (params->flags & DGEC_CUTOFF) hb.dmax = params->delta_max;
     hb.mrd = params->flags & DGEC_MRD;
+    if (params->flags & DGEC_NEARLY_CAUSAL) hb.dnc = params->delta_nc;
     DG_TRY(check_batch(c, hb));
     CU_TRY(c, cudaSetDevice(c->device));
     c->stream = (cudaStream_t)stream;

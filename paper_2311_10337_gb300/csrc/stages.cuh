@@ -29,6 +29,7 @@ struct Problem {
     int64_t dmax = INT64_MAX;         // time cutoff (Sec. 4.3): only links with w <= dmax
     int64_t links_cap = -1;           // skeleton capacity; -1 = 2E (graphs: <= 2 links per edge)
     bool mrd = false;                 // cluster the mutual-reachability graph (stage M)
+    int64_t dnc = 0;                  // nearly-causal tolerance (Sec. 4.3); 0 = causal (stage N off)
 };
 
 inline int64_t link_cap(const Problem &p) { return p.links_cap >= 0 ? p.links_cap : 2 * p.E; }
@@ -92,6 +93,16 @@ dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void
 void plan_mrd(Arena &ws, const Problem &p, Skel &h);
 size_t mrd_scratch_bytes(const Problem &p);
 dgec_status stage_mrd(Ctx *c, const Problem &p, const Csr &g, const Skel &sk, Skel &h, void *scratch);
+
+// Stage N (optional): the nearly-causal line graph (Sec. 4.3). Stages A and
+// B run again on the negated times (stage_nc_negate fills tn); stage_nc
+// unites the two skeletons (backward links with w <= dnc) and merges the two
+// kNN rows of every edge into h.knn / h.core. Capacity 4E links.
+void plan_nc(Arena &ws, const Problem &p, Skel &h);
+size_t nc_scratch_bytes(const Problem &p);
+dgec_status stage_nc_negate(Ctx *c, const Problem &p, int64_t *tn);
+dgec_status stage_nc(Ctx *c, const Problem &p, const Csr &g, const Skel &s1, const Skel &s2, Skel &h,
+                     void *scratch);
 
 // Stage C: minimum spanning forest of the skeleton (Borůvka), sorted by
 // (w, u, v).

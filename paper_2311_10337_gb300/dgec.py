@@ -41,16 +41,19 @@ class DgecError(RuntimeError):
 
 CUTOFF = 1
 MRD = 2
+NEARLY_CAUSAL = 4
 
 
 class Params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("min_cluster_size", ctypes.c_int32),
-                ("flags", ctypes.c_uint32), ("delta_max", ctypes.c_int64)]
+                ("flags", ctypes.c_uint32), ("delta_max", ctypes.c_int64), ("delta_nc", ctypes.c_int64)]
 
 
-def _params(k, min_cluster_size, delta_max=None, mrd=False):
-    flags = (CUTOFF if delta_max is not None else 0) | (MRD if mrd else 0)
-    return Params(k, min_cluster_size, flags, int(delta_max) if delta_max is not None else 0)
+def _params(k, min_cluster_size, delta_max=None, mrd=False, delta_nc=None):
+    flags = ((CUTOFF if delta_max is not None else 0) | (MRD if mrd else 0) |
+             (NEARLY_CAUSAL if delta_nc is not None else 0))
+    return Params(k, min_cluster_size, flags, int(delta_max) if delta_max is not None else 0,
+                  int(delta_nc) if delta_nc is not None else 0)
 
 
 _P = ctypes.c_void_p
@@ -183,9 +186,10 @@ def msf_static(u, v, w, n_nodes: int, out_u, out_v, out_w, stream=None) -> int:
     return int(n.value)
 
 
-def workspace_size(n_edges: int, n_vertices: int, k: int, min_cluster_size: int, mrd: bool = False) -> int:
+def workspace_size(n_edges: int, n_vertices: int, k: int, min_cluster_size: int, mrd: bool = False,
+                   delta_nc=None) -> int:
     L = load()
-    p = _params(k, min_cluster_size, None, mrd)
+    p = _params(k, min_cluster_size, None, mrd, delta_nc)
     out = ctypes.c_size_t(0)
     rc = L.dgec_workspace_size(n_edges, n_vertices, ctypes.byref(p), ctypes.byref(out))
     if rc != DGEC_OK:
@@ -256,18 +260,19 @@ class Context:
         return out
 
     def run(self, src, dst, t, n_vertices: int, k: int, min_cluster_size: int, stream=None,
-            delta_max=None, mrd: bool = False):
+            delta_max=None, mrd: bool = False, delta_nc=None):
         """Alg. 4 on device tensors (int32 src/dst, int64 t). Returns an
         Output whose tensors view the workspace (valid until the next run).
         delta_max: the time cutoff of Sec. 4.3 (None = no cutoff); mrd: cluster
-        the mutual-reachability graph (an approximation, see dgec.h)."""
+        the mutual-reachability graph (an approximation, see dgec.h);
+        delta_nc: the nearly-causal tolerance of Sec. 4.3 (None = causal)."""
         torch = self.torch
         E = int(src.shape[0])
         for x, dt in ((src, torch.int32), (dst, torch.int32), (t, torch.int64)):
             if x.dtype != dt or not x.is_cuda or not x.is_contiguous():
                 raise ValueError("src/dst must be contiguous cuda int32, t cuda int64")
-        p = _params(k, min_cluster_size, delta_max, mrd)
-        need = workspace_size(E, n_vertices, k, min_cluster_size, mrd)
+        p = _params(k, min_cluster_size, delta_max, mrd, delta_nc)
+        need = workspace_size(E, n_vertices, k, min_cluster_size, mrd, delta_nc)
         ws = self.workspace(need)
         st = stream if stream is not None else torch.cuda.current_stream(self.device)
         res = Result()
@@ -336,13 +341,13 @@ class Context:
 
     def run_host(self, src: np.ndarray, dst: np.ndarray, t: np.ndarray, n_vertices: int, k: int,
                  min_cluster_size: int, labels_out: np.ndarray | None = None, stream=None,
-                 delta_max=None, mrd: bool = False):
+                 delta_max=None, mrd: bool = False, delta_nc=None):
         """Alg. 4 from host arrays (pinned numpy views avoid staging copies);
         returns (labels, n_clusters)."""
         torch = self.torch
         E = int(src.shape[0])
-        p = _params(k, min_cluster_size, delta_max, mrd)
-        need = workspace_size(E, n_vertices, k, min_cluster_size, mrd) + 16 * E + 4096
+        p = _params(k, min_cluster_size, delta_max, mrd, delta_nc)
+        need = workspace_size(E, n_vertices, k, min_cluster_size, mrd, delta_nc) + 16 * E + 4096
         ws = self.workspace(need)
         if labels_out is None:
             labels_out = np.empty(E, np.int32)
