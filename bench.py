@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--serve-pool-gb", type=float, default=72.0)
     ap.add_argument("--hyper-scale", type=float, default=1.0,
                     help="scale of the hypergraph (broadcast message) measurement; 0 = skip")
+    ap.add_argument("--nc-delta", type=int, default=60,
+                    help="tolerance (s) of the nearly-causal measurement; < 0 = skip")
     ap.add_argument("--no-mrd", action="store_true",
                     help="skip the mutual-reachability mode measurement")
     ap.add_argument("--no-levels", action="store_true",
@@ -247,6 +249,30 @@ def discrete_levels(ctx, src, dst, tt, w, steps, breakdown=False):
         res["kernel_breakdown_ms"] = {n: [round(v[0], 3), v[1]] for n, v in
                                       sorted(ctx.kernel_timing().items(), key=lambda kv: -kv[1][0])}
         ctx.set_kernel_timing(0)
+    return res
+
+
+def variant_rate(ctx, src, dst, tt, w, steps, **kw):
+    """Edges/s of the whole path in one variant (keyword options of
+    Context.run) on the same graph; inputs resident, CUDA events."""
+    import torch
+    E, V, k, M = w.n_edges, w.n_vertices, w.k, w.min_cluster_size
+    out = ctx.run(src, dst, tt, V, k, M, **kw)
+    launches = ctx.launches()
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        out = ctx.run(src, dst, tt, V, k, M, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    res = {"edges_per_s": E / (ms / 1000.0), "ms": ms, "skeleton_links": out.n_skeleton,
+           "forest_edges": out.n_mst, "n_clusters": out.n_clusters, "gpu_launches_per_run": launches}
+    ctx.ws = None
+    torch.cuda.empty_cache()
     return res
 
 
@@ -472,6 +498,10 @@ def main():
     mrd = None
     if not args.no_mrd and rank == 0:
         mrd = mutual_reachability(ctx, src, dst, tt, w, max(1, min(args.steps, 3)))
+    nearly = None
+    if args.nc_delta >= 0 and rank == 0:
+        nearly = dict(variant_rate(ctx, src, dst, tt, w, max(1, min(args.steps, 3)), delta_nc=args.nc_delta),
+                      delta_s=args.nc_delta)
     hyper = None
     if args.hyper_scale > 0 and rank == 0:
         hyper = hypergraphs(ctx, args.hyper_scale, max(1, min(args.steps, 3)))
@@ -510,7 +540,7 @@ def main():
                            "l2": "inputs (16 B/edge = %.0f MB) exceed L2; no flush" % (16 * E / 1e6),
                            "n_clusters": n_clusters},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "discrete_dendrogram": levels, "hypergraph": hyper,
-                "mutual_reachability": mrd,
+                "mutual_reachability": mrd, "nearly_causal": nearly,
                 "batch": batch, "serve": serve,
                 "gpu_launches": launches * args.steps, "clocks": clk}
         if args.breakdown:
