@@ -33,6 +33,13 @@ UNIT = "edges/s"
 # writes the two ranks (8 B), k neighbour ids (4k B) and the core distance
 # (8 B). Binary-search probes and offset lookups are access overhead, not
 # counted.
+# Algorithmic bytes per input edge of the whole path (what it must move: CSR
+# 40 B, skeleton + kNN 56 + 4k B, forest 48 B, dendrogram + condensed tree +
+# labels 64 B), for the pipeline's share of the HBM roofline.
+def pipeline_bytes_per_edge(k: int) -> int:
+    return 40 + (24 + 32 + 4 * k + 8) + 48 + 64
+
+
 def knn_bytes_per_edge(k: int) -> int:
     return 16 + 12 * (k + 2) + 8 + 4 * k + 8
 
@@ -524,6 +531,9 @@ def main():
                 "traffic": (KNN_TRAFFIC_BYTES_PER_EDGE_K8 * E
                             if args.dominant == "k_ranks_knn" and k == 8 and args.workload == "mid" else None),
                 "algorithmic_bytes_per_launch": kb * E,
+                "pipeline": {"bytes_per_edge": pipeline_bytes_per_edge(k),
+                             "achieved": pipeline_bytes_per_edge(k) * E / (ms / 1000.0) / 1e9,
+                             "frac": pipeline_bytes_per_edge(k) * E / (ms / 1000.0) / 1e9 / peak},
                 "avg_launch_ms": dom_ms / max(dom_n, 1) if dom_n else None}
         cpu = None
         if not args.no_cpu_baseline and world == 1:
