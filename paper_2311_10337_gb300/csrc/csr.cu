@@ -5,15 +5,16 @@
 // First a device-wide radix sort of the 64-bit keys ((t - t_min) << idbits
 // | id) ranks all edges in (t, id) order. The keys are laid out in id order
 // and the LSD sort is stable, so only the time bits need passes: equal
-// times keep id order. That rank r is the internal node
-// id of every later stage, and per-vertex lists sorted by (t, id) are just
-// lists sorted by r. Ranks are scattered into their vertex's segment through
-// per-vertex cursors (warp-aggregated atomics absorb hub vertices), then
-// each segment is sorted by the bin its length falls in:
-//   2..32 elements      one warp, bitonic network over shuffles;
-//   33..256, 257..2048  one CTA, bitonic network in shared memory;
-//   > 2048 (hubs)       all hub segments together through the device-wide
-//                       radix sort, keyed (segment, r).
+// times keep id order. That rank r is the internal node id of every later
+// stage, and per-vertex lists sorted by (t, id) are just lists sorted by r.
+// With the edges in r order, the keys (vertex << idbits) | r sorted stably
+// over the vertex bits alone give every vertex's list in r order, for the
+// out-lists (by src) and the in-lists (by dst); the list offsets are the run
+// boundaries of the sorted keys. No atomics and no per-segment sorts.
+//
+// The segment sort below (bins by length: one warp for 2..32 keys, one CTA
+// for 33..2048, hubs through the radix sort keyed (segment, key)) serves the
+// hypergraph membership lists, whose members arrive unordered.
 #include "stages.cuh"
 
 namespace dgec {
@@ -65,10 +66,12 @@ __global__ void k_count(const int32_t *src, const int32_t *dst, const int64_t *t
             tmin = x < tmin ? x : tmin;
             tmax = x > tmax ? x : tmax;
         }
-        unsigned act = __ballot_sync(0xffffffffu, vs);
-        if (vs) {
-            warp_agg_inc(deg_out, (int)(s + vo), act);
-            warp_agg_inc(deg_in, (int)(d + vo), act);
+        if (deg_out) {  // degrees only when the caller wants them
+            unsigned act = __ballot_sync(0xffffffffu, vs);
+            if (vs) {
+                warp_agg_inc(deg_out, (int)(s + vo), act);
+                warp_agg_inc(deg_in, (int)(d + vo), act);
+            }
         }
     }
 #pragma unroll
@@ -133,26 +136,6 @@ __global__ void k_pack_keys(const int64_t *t, int64_t E, long long tmin, int idb
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
          e += (int64_t)gridDim.x * blockDim.x)
         k[e] = ((unsigned long long)(t[e] - tmin) << idbits) | (unsigned long long)e;
-}
-
-__global__ void k_scatter(const int32_t *isrc, const int32_t *idst, int64_t E,
-                          const int64_t *out_off, const int64_t *in_off, int *cur_out, int *cur_in,
-                          unsigned long long *okey, unsigned long long *ikey) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = stride >> 5;
-    for (int64_t wb = warp_global * 32; wb < E; wb += nwarps * 32) {
-        int64_t r = wb + lane_id();
-        bool ok = r < E;
-        unsigned act = __ballot_sync(0xffffffffu, ok);
-        if (ok) {
-            int s = isrc[r], d = idst[r];
-            int ro = warp_agg_inc(cur_out, s, act);
-            int ri = warp_agg_inc(cur_in, d, act);
-            okey[out_off[s] + ro] = (unsigned long long)r;
-            ikey[in_off[d] + ri] = (unsigned long long)r;
-        }
-    }
 }
 
 // bins: 0 warp (2..32), 1 CTA-256, 2 CTA-2048, 3 hub (> 2048)
@@ -264,18 +247,36 @@ __global__ void k_hub_scatter(const unsigned long long *hub_of, const unsigned l
     }
 }
 
-__global__ void k_unpack(const unsigned long long *keys, int64_t E, const int32_t *orig_of,
-                         const int64_t *it, int64_t *t_out, int32_t *id_out, int32_t *r_out,
-                         int32_t *slot_of, int32_t *pos_of) {
+__global__ void k_unpack(const unsigned long long *keys, unsigned long long rmask, int64_t E,
+                         const int32_t *orig_of, const int64_t *it, int64_t *t_out, int32_t *id_out,
+                         int32_t *r_out, int32_t *slot_of, int32_t *pos_of) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < E;
          x += (int64_t)gridDim.x * blockDim.x) {
-        int32_t r = (int32_t)keys[x];
+        int32_t r = (int32_t)(keys[x] & rmask);
         const int32_t e = orig_of[r];
         r_out[x] = r;
         id_out[x] = e;
         t_out[x] = it[r];
         if (slot_of) slot_of[r] = (int32_t)x;
         pos_of[e] = (int32_t)x;  // the edge's place in this list array
+    }
+}
+
+// key = (vertex << idbits) | r for every edge r (edges are in r order, so a
+// stable sort over the vertex bits alone leaves each vertex's run in r order)
+__global__ void k_vkeys(const int32_t *vert, int64_t E, int idbits, unsigned long long *key) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < E;
+         r += (int64_t)gridDim.x * blockDim.x)
+        key[r] = ((unsigned long long)(unsigned)vert[r] << idbits) | (unsigned long long)r;
+}
+
+// off[v] = first sorted position whose vertex is >= v, for v in [0, V]
+__global__ void k_voffsets(const unsigned long long *key, int64_t E, int64_t V, int idbits, int64_t *off) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x <= E;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = x < E ? (int64_t)(key[x] >> idbits) : V;
+        const int64_t prev = x > 0 ? (int64_t)(key[x - 1] >> idbits) : -1;
+        for (int64_t u = prev + 1; u <= v; u++) off[u] = x;
     }
 }
 
@@ -313,22 +314,18 @@ void carve_segsort(Arena &a, int64_t V, int64_t n, SegSort &s) {
 
 // scratch layout
 struct CsrScratch {
-    int *deg_out, *deg_in;
-    long long *flags, *scan_tmp;
-    unsigned long long *okey, *ikey;
-    SegSort seg;
+    long long *flags;
+    unsigned long long *okey, *ikey, *okey2, *ikey2;
     void *radix;
 };
 static CsrScratch carve_csr(Arena &a, const Problem &p) {
     CsrScratch s;
-    int64_t V = p.V, E = p.E;
-    s.deg_out = a.take<int>(V + 1);
-    s.deg_in = a.take<int>(V + 1);
+    int64_t E = p.E > 0 ? p.E : 1;
     s.flags = a.take<long long>(8);
-    s.scan_tmp = a.take<long long>(scan_scratch_elems(V + 1));
     s.okey = a.take<unsigned long long>(E);
     s.ikey = a.take<unsigned long long>(E);
-    carve_segsort(a, V, E, s.seg);
+    s.okey2 = a.take<unsigned long long>(E);
+    s.ikey2 = a.take<unsigned long long>(E);
     s.radix = a.take<char>(radix_scratch_bytes(E));
     return s;
 }
@@ -393,14 +390,12 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
     Arena a(scratch, SIZE_MAX);
     CsrScratch s = carve_csr(a, p);
     int64_t V = p.V, E = p.E;
-    CU_TRY(c, cudaMemsetAsync(s.deg_out, 0, sizeof(int) * (V + 1), st));
-    CU_TRY(c, cudaMemsetAsync(s.deg_in, 0, sizeof(int) * (V + 1), st));
     TK(c, "k_init_flags", k_init_flags<<<1, 1, 0, st>>>(s.flags));
     if (E > 0) {
         if (p.G == 1) CU_TRY(c, cudaMemsetAsync(p.egraph, 0, sizeof(int32_t) * E, st));
         else TK(c, "k_egraph", k_egraph<<<grid_for(E, kBlock, 65536), kBlock, 0, st>>>(p.eoff, p.G, E, p.egraph));
         TK(c, "k_count", k_count<<<grid_for(E, kBlock, (int64_t)c->num_sms * 16), kBlock, 0, st>>>(
-                             p.src, p.dst, p.t, E, p.egraph, p.voff, s.deg_out, s.deg_in, s.flags));
+                             p.src, p.dst, p.t, E, p.egraph, p.voff, nullptr, nullptr, s.flags));
     }
     int64_t f[4];
     DG_TRY(read_counters(c, (const int64_t *)s.flags, 4, f));
@@ -414,14 +409,11 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
     if (p.idbits + p.tbits > 64)
         return set_err(c, DGEC_ERR_TOO_LARGE, "time span %llu needs %d bits + %d id bits > 64",
                        (unsigned long long)span, p.tbits, p.idbits);
-    // offsets
-    if (V > 0) {
-        DG_TRY(exclusive_scan_i32(c, s.deg_out, (long long *)o.out_off, V, s.scan_tmp));
-        DG_TRY(exclusive_scan_i32(c, s.deg_in, (long long *)o.in_off, V, s.scan_tmp));
+    if (E == 0) {
+        CU_TRY(c, cudaMemsetAsync(o.out_off, 0, sizeof(int64_t) * (V + 1), st));
+        CU_TRY(c, cudaMemsetAsync(o.in_off, 0, sizeof(int64_t) * (V + 1), st));
+        return DGEC_OK;
     }
-    TK(c, "k_set_i64", k_set_i64<<<1, 1, 0, st>>>((long long *)o.out_off + V, E));
-    TK(c, "k_set_i64", k_set_i64<<<1, 1, 0, st>>>((long long *)o.in_off + V, E));
-    if (E == 0) return DGEC_OK;
     // global (t, id) order: internal ids
     const int gEE = grid_for(E, kBlock, 65536);
     TK(c, "k_pack_keys", k_pack_keys<<<gEE, kBlock, 0, st>>>(p.t, E, p.tmin, p.idbits, s.okey));
@@ -433,17 +425,27 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
                                                                 p.src, p.dst, p.egraph, p.voff, o.orig_of, o.rank_of,
                                                                 o.isrc, o.idst, o.it));
     }
-    // scatter ranks into their segments (cursors reuse the degree arrays)
-    CU_TRY(c, cudaMemsetAsync(s.deg_out, 0, sizeof(int) * (V + 1), st));
-    CU_TRY(c, cudaMemsetAsync(s.deg_in, 0, sizeof(int) * (V + 1), st));
-    TK(c, "k_scatter", k_scatter<<<grid_for(E, kBlock, (int64_t)c->num_sms * 16), kBlock, 0, st>>>(
-                           o.isrc, o.idst, E, o.out_off, o.in_off, s.deg_out, s.deg_in, s.okey, s.ikey));
-    DG_TRY(sort_segments(c, V, s.okey, o.out_off, s.seg, p.idbits));
-    DG_TRY(sort_segments(c, V, s.ikey, o.in_off, s.seg, p.idbits));
-    TK(c, "k_unpack", k_unpack<<<gEE, kBlock, 0, st>>>(s.okey, E, o.orig_of, o.it, o.out_t, o.out_id,
-                                                       o.out_r, o.slot_out, o.pos_out));
-    TK(c, "k_unpack", k_unpack<<<gEE, kBlock, 0, st>>>(s.ikey, E, o.orig_of, o.it, o.in_t, o.in_id,
-                                                       o.in_r, nullptr, o.pos_in));
+    // per-vertex lists: stable sort of (vertex, r) over the vertex bits only
+    const int vbits = bits_for((uint64_t)(V > 1 ? V - 1 : 1));
+    const unsigned long long rmask = (1ull << p.idbits) - 1ull;
+    struct Side {
+        const int32_t *vert;
+        unsigned long long *k1, *k2;
+        int64_t *off;
+        int64_t *t_out;
+        int32_t *id_out, *r_out, *slot_of, *pos_of;
+    } sides[2] = {{o.isrc, s.okey, s.okey2, o.out_off, o.out_t, o.out_id, o.out_r, o.slot_out, o.pos_out},
+                  {o.idst, s.ikey, s.ikey2, o.in_off, o.in_t, o.in_id, o.in_r, nullptr, o.pos_in}};
+    for (const Side &d : sides) {
+        TK(c, "k_vkeys", k_vkeys<<<gEE, kBlock, 0, st>>>(d.vert, E, p.idbits, d.k1));
+        bool in_b;
+        DG_TRY(radix_sort(c, RadixBuffers{d.k1, d.k2, nullptr, nullptr}, E, p.idbits, p.idbits + vbits, s.radix,
+                          &in_b));
+        const unsigned long long *key = in_b ? d.k2 : d.k1;
+        TK(c, "k_voffsets", k_voffsets<<<grid_for(E + 1, kBlock, 65536), kBlock, 0, st>>>(key, E, V, p.idbits, d.off));
+        TK(c, "k_unpack", k_unpack<<<gEE, kBlock, 0, st>>>(key, rmask, E, o.orig_of, o.it, d.t_out, d.id_out, d.r_out,
+                                                           d.slot_of, d.pos_of));
+    }
     return DGEC_OK;
 }
 
