@@ -115,7 +115,7 @@ __global__ void k_set_i64(long long *p, long long v) { *p = v; }
 // copies of the inputs for the later stages
 __global__ void k_rank_init(const unsigned long long *ks, int64_t E, long long tmin, int idbits,
                             const int32_t *src, const int32_t *dst, const int32_t *egraph,
-                            const int64_t *voff, int32_t *orig_of, int32_t *rank_of, int32_t *isrc,
+                            const int64_t *voff, int G, int32_t *orig_of, int32_t *rank_of, int32_t *isrc,
                             int32_t *idst, int64_t *it) {
     const unsigned long long idmask = (1ull << idbits) - 1ull;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < E;
@@ -125,7 +125,7 @@ __global__ void k_rank_init(const unsigned long long *ks, int64_t E, long long t
         orig_of[r] = e;
         rank_of[e] = (int32_t)r;
         it[r] = (int64_t)(k >> idbits) + tmin;
-        int32_t vo = (int32_t)voff[egraph[e]];
+        int32_t vo = G > 1 ? (int32_t)voff[egraph[e]] : 0;  // one graph: no random lookup
         isrc[r] = src[e] + vo;
         idst[r] = dst[e] + vo;
     }
@@ -422,7 +422,7 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
         DG_TRY(radix_sort(c, RadixBuffers{s.okey, s.ikey, nullptr, nullptr}, E, p.idbits, p.idbits + p.tbits,
                           s.radix, &in_b));
         TK(c, "k_rank_init", k_rank_init<<<gEE, kBlock, 0, st>>>(in_b ? s.ikey : s.okey, E, p.tmin, p.idbits,
-                                                                p.src, p.dst, p.egraph, p.voff, o.orig_of, o.rank_of,
+                                                                p.src, p.dst, p.egraph, p.voff, p.G, o.orig_of, o.rank_of,
                                                                 o.isrc, o.idst, o.it));
     }
     // per-vertex lists: stable sort of (vertex, r) over the vertex bits only

@@ -198,19 +198,19 @@ __global__ void k_d_sizes(const unsigned long long *key, const unsigned long lon
 
 // the first active list: forest edges ordered by their internal end, so
 // neighbouring threads touch neighbouring labels
-__global__ void k_d_order_keys(const int32_t *ru, int64_t n, unsigned long long *k,
-                               unsigned long long *v) {
+// Rows arrive in rank order s, so the key (ru << sbits) | s sorted stably
+// over the ru bits alone orders them by ru with ties in s order (no values).
+__global__ void k_d_order_keys(const int32_t *ru, int64_t n, int sbits, unsigned long long *k) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
-         x += (int64_t)gridDim.x * blockDim.x) {
-        k[x] = (unsigned long long)ru[x];
-        v[x] = (unsigned long long)x;
-    }
+         x += (int64_t)gridDim.x * blockDim.x)
+        k[x] = ((unsigned long long)(unsigned)ru[x] << sbits) | (unsigned long long)x;
 }
-__global__ void k_d_order_act(const unsigned long long *v, int64_t n, const int32_t *ru,
+__global__ void k_d_order_act(const unsigned long long *k, int64_t n, int sbits, const int32_t *ru,
                               const int32_t *rv, int32_t *act, int32_t *ecu, int32_t *ecv) {
+    const unsigned long long smask = (1ull << sbits) - 1ull;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
          j += (int64_t)gridDim.x * blockDim.x) {
-        int s = (int)v[j];
+        int s = (int)(k[j] & smask);
         act[j] = s;
         ecu[j] = ru[s];
         ecv[j] = rv[s];
@@ -301,10 +301,10 @@ dgec_status stage_dendro(Ctx *c, const Problem &p, const Csr &g, const Msf &m, D
     const int sbits = bits_for((uint64_t)(n > 1 ? n - 1 : 1));
     if (n > 1) {
         const int gn = grid_for(n, kBlock, 65536);
-        TK(c, "k_d_order", k_d_order_keys<<<gn, kBlock, 0, st>>>(m.ru, n, s.k1, s.v1));
+        TK(c, "k_d_order", k_d_order_keys<<<gn, kBlock, 0, st>>>(m.ru, n, sbits, s.k1));
         bool in_b;
-        DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, s.v1, s.v2}, n, 0, lb, s.radix, &in_b));
-        TK(c, "k_d_order", k_d_order_act<<<gn, kBlock, 0, st>>>(in_b ? s.v2 : s.v1, n, m.ru, m.rv, s.act,
+        DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, nullptr, nullptr}, n, sbits, sbits + lb, s.radix, &in_b));
+        TK(c, "k_d_order", k_d_order_act<<<gn, kBlock, 0, st>>>(in_b ? s.k2 : s.k1, n, sbits, m.ru, m.rv, s.act,
                                                                s.ecu, s.ecv));
     }
     int64_t na = n;
