@@ -2,13 +2,16 @@
 the same entry points and launch configuration the benchmark times (k = 8,
 M = 5, the current stream; the discrete dendrogram at 2^0 .. 2^28 s).
 
-The oracle cannot redo the whole graph in test time, so sampled outputs are
-recomputed one by one (kNN rows of sampled edges; Alg. 2's links at sampled
-vertices) and everything else is checked through properties that hold at
-any size: the incidence lists' order, Def. 1 for every link, the forest's
-size and total weight (Thm. 1) against scipy's components and MST of the
-skeleton, the dendrogram's sizes, the level components (Thm. 3) against
-scipy, and the component counts of every level against the forest."""
+The oracle's chain runs on the whole graph (Alg. 3's skeleton, then Alg. 1's
+Kruskal forest, union-find dendrogram and condensing: a few minutes of
+single-core C), so the skeleton set, the forest, the dendrogram rows, every
+condensed-tree array and the labels are compared element by element. The
+oracle's kNN rows are recomputed one by one for sampled edges. The incidence
+lists are fixed exactly by their defining properties (offsets from the
+degrees; each list a permutation sorted by (t, id)). The discrete dendrogram,
+whose oracle repeats a union-find per threshold, is checked through Thm. 3 at
+two thresholds against scipy's components of the skeleton and through every
+level's component count against the forest."""
 import numpy as np
 import pytest
 
@@ -18,6 +21,8 @@ from paper_2311_10337_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 POW2 = np.array([2 ** i for i in range(29)], np.int64)
+CONDENSED = ["fall_cluster", "fall_lambda", "cl_id", "cl_parent", "cl_birth", "cl_death",
+             "cl_stab_hi", "cl_stab_lo", "cl_size", "cl_selected"]
 
 
 @pytest.fixture(scope="module")
@@ -28,8 +33,9 @@ def full():
     d = torch.from_numpy(w.dst).cuda()
     t = torch.from_numpy(w.t).cuda()
     out = ctx().run(s, d, t, w.n_vertices, w.k, w.min_cluster_size)
-    names = ["out_off", "in_off", "out_t", "out_id", "in_id", "sk_u", "sk_v", "sk_w", "knn_id", "core",
-             "mst_u", "mst_v", "mst_w", "link_a", "link_b", "link_size", "labels"]
+    names = ["out_off", "in_off", "out_t", "in_t", "out_id", "in_id", "pos_out", "pos_in", "sk_u", "sk_v",
+             "sk_w", "knn_id", "core", "mst_u", "mst_v", "mst_w", "link_a", "link_b", "link_size",
+             "labels"] + CONDENSED
     r = {n: out.numpy(n) for n in names}
     r["n_clusters"] = out.n_clusters
     lv = ctx().run_levels(s, d, t, w.n_vertices, POW2, w.min_cluster_size)
@@ -38,21 +44,34 @@ def full():
     r["n_components"] = lv.numpy("n_components")
     r["lv_labels"] = lv.numpy("labels")
     r["lv_n_clusters"] = lv.n_clusters
-    del s, d, t
+    del s, d, t, out, lv
     ctx().ws = None
     torch.cuda.empty_cache()
-    # shared by several tests: skeleton keys in sorted order, components of L*
-    key = r["sk_u"].astype(np.int64) * w.n_edges + r["sk_v"]
-    r["sk_order"] = np.argsort(key, kind="stable")
-    r["sk_key_sorted"] = key[r["sk_order"]]
     r["n_comp"], r["comp"] = _components(w.n_edges, r["sk_u"], r["sk_v"])
     return w, r
 
 
-def _csgraph(E, u, v, w=None):
+@pytest.fixture(scope="module")
+def chain(full):
+    """The oracle's whole clustering chain on the same graph."""
+    w, _ = full
+    E = w.n_edges
+    u, v, wt = O.skeleton(w.src, w.dst, w.t, w.n_vertices)       # sorted by (w, u, v)
+    mu, mv, mw = O.mst(E, u, v, wt)
+    a, b, s = O.linkage(E, mu, mv)
+    c = O.condense(E, a, b, mw, s, w.min_cluster_size)
+    return dict(skeleton=(u, v, wt), mst=(mu, mv, mw), linkage=(a, b, s), condensed=c)
+
+
+def _pair_order(E, u, v):
+    key = u.astype(np.int64) * E + v
+    o = np.argsort(key, kind="stable")
+    return key[o], o
+
+
+def _csgraph(E, u, v):
     sp = pytest.importorskip("scipy.sparse")
-    data = np.ones(len(u), np.int8) if w is None else w
-    return sp.coo_matrix((data, (u, v)), shape=(E, E)).tocsr()
+    return sp.coo_matrix((np.ones(len(u), np.int8), (u, v)), shape=(E, E)).tocsr()
 
 
 def _components(E, u, v):
@@ -72,54 +91,32 @@ def _min_member_names(lab):
 def test_incidence_lists(full):
     w, r = full
     E, V = w.n_edges, w.n_vertices
-    for off, ids, end in (("out_off", "out_id", w.src), ("in_off", "in_id", w.dst)):
+    for off, ids, tt, pos, end in (("out_off", "out_id", "out_t", "pos_out", w.src),
+                                   ("in_off", "in_id", "in_t", "pos_in", w.dst)):
         o, ids_ = r[off], r[ids]
         assert np.array_equal(o, np.concatenate([[0], np.cumsum(np.bincount(end, minlength=V))]))
-        assert np.array_equal(np.sort(ids_), np.arange(E, dtype=np.int32))
+        assert np.all(np.bincount(ids_, minlength=E) == 1)          # a permutation of the edges
         seg = np.repeat(np.arange(V, dtype=np.int32), np.diff(o))
         assert np.array_equal(end[ids_], seg)
         same = seg[1:] == seg[:-1]
         ta, tb = w.t[ids_[:-1]], w.t[ids_[1:]]
         ok = (ta < tb) | ((ta == tb) & (ids_[:-1] < ids_[1:]))
         assert np.all(ok[same]), off          # Alg. 2: each list sorted by (t, id)
-    assert np.array_equal(r["out_t"], w.t[r["out_id"]])
+        assert np.array_equal(r[tt], w.t[ids_]), tt
+        assert np.array_equal(r[pos][ids_], np.arange(E, dtype=np.int32)), pos
 
 
-def test_skeleton_links(full):
+def test_skeleton(full, chain):
+    """Alg. 3's skeleton: the same set of (u, v, w) links as the oracle's."""
     w, r = full
-    u, v, wt = r["sk_u"], r["sk_v"], r["sk_w"]
-    assert np.all(u < v)
-    for lo in range(0, len(u), 1 << 24):                      # Def. 1, P1-P3, one orientation
-        uu, vv, ww = u[lo:lo + (1 << 24)], v[lo:lo + (1 << 24)], wt[lo:lo + (1 << 24)]
-        tu, tv = w.t[uu], w.t[vv]
-        assert np.array_equal(ww, np.abs(tu - tv))
-        fwd = (w.dst[uu] == w.src[vv]) & (tu <= tv)
-        bwd = (w.dst[vv] == w.src[uu]) & (tv <= tu)
-        assert np.all(fwd | bwd)
-    assert np.all(np.diff(r["sk_key_sorted"]) > 0)            # each pair once (Alg. 3 union)
-    deg = np.bincount(w.src, minlength=w.n_vertices) + np.bincount(w.dst, minlength=w.n_vertices)
-    assert len(u) <= int(np.sum(np.maximum(deg - 1, 0)))      # size bound of Sec. 2
-
-
-def test_skeleton_sampled_vertices(full):
-    """Alg. 2 at sampled vertices (hubs included), run by the oracle on the
-    edges incident to the vertex: every link it emits there is in L*."""
-    w, r = full
-    ks = r["sk_key_sorted"]
-    deg = np.bincount(w.src, minlength=w.n_vertices) + np.bincount(w.dst, minlength=w.n_vertices)
-    rng = np.random.default_rng(7)
-    verts = np.concatenate([np.argsort(deg)[-5:], rng.choice(np.nonzero(deg > 1)[0], 200, replace=False)])
-    for i in verts.tolist():
-        inc = np.nonzero((w.src == i) | (w.dst == i))[0]
-        loc_v, inv = np.unique(np.concatenate([w.src[inc], w.dst[inc]]), return_inverse=True)
-        ls, ld = inv[:len(inc)].astype(np.int32), inv[len(inc):].astype(np.int32)
-        p, q, _, c = O.skeleton_raw(ls, ld, w.t[inc], len(loc_v))
-        centre = int(np.searchsorted(loc_v, i))
-        sel = c == centre
-        a, b = inc[p[sel]], inc[q[sel]]
-        keys = np.minimum(a, b).astype(np.int64) * w.n_edges + np.maximum(a, b)
-        pos = np.minimum(np.searchsorted(ks, keys), len(ks) - 1)
-        assert np.all(ks[pos] == keys), i
+    E = w.n_edges
+    ou, ov, ow = chain["skeleton"]
+    assert len(r["sk_u"]) == len(ou)
+    assert np.all(r["sk_u"] < r["sk_v"])
+    gk, go = _pair_order(E, r["sk_u"], r["sk_v"])
+    ok, oo = _pair_order(E, ou, ov)
+    assert np.array_equal(gk, ok)
+    assert np.array_equal(r["sk_w"][go], ow[oo])
 
 
 def test_knn_sampled(full):
@@ -143,33 +140,33 @@ def test_knn_sampled(full):
     assert np.array_equal(r["core"][q], core)
 
 
-def test_forest_and_dendrogram(full):
+def test_forest(full, chain):
+    """Alg. 1 step 1: the oracle's Kruskal forest, element by element, and
+    one tree per component of the skeleton."""
     w, r = full
-    E = w.n_edges
-    mu, mv, mw = r["mst_u"], r["mst_v"], r["mst_w"]
-    # sorted by the strict key (w, u, v)
-    k0 = (mw[1:] > mw[:-1]) | ((mw[1:] == mw[:-1]) & ((mu[1:] > mu[:-1]) | ((mu[1:] == mu[:-1]) & (mv[1:] > mv[:-1]))))
-    assert np.all(k0)
-    ks, order = r["sk_key_sorted"], r["sk_order"]
-    mk = mu.astype(np.int64) * E + mv
-    pos = np.minimum(np.searchsorted(ks, mk), len(ks) - 1)
-    assert np.all(ks[pos] == mk)                                      # forest edges are skeleton links
-    assert np.array_equal(r["sk_w"][order[pos]], mw)
-    ncomp = r["n_comp"]
-    assert len(mu) == E - ncomp                                       # spanning forest of L*
-    ncf, _ = _components(E, mu, mv)
-    assert ncf == ncomp
-    # Thm. 1: the forest has the minimum total weight (scipy on w + 1, as it drops zero weights)
-    cg = pytest.importorskip("scipy.sparse.csgraph")
-    mst = cg.minimum_spanning_tree(_csgraph(E, r["sk_u"], r["sk_v"], r["sk_w"].astype(np.float64) + 1.0))
-    assert int(round(mst.sum())) == int(mw.sum()) + len(mw)
-    # dendrogram: every merge joins two earlier clusters and counts their leaves
-    a, b, sz = r["link_a"].astype(np.int64), r["link_b"].astype(np.int64), r["link_size"]
-    size_of = np.concatenate([np.ones(E, np.int64), sz])
-    assert np.all(a < b) and np.all(b < E + np.arange(len(a)))
-    assert np.array_equal(sz, size_of[a] + size_of[b])
-    kids = np.concatenate([a, b])
-    assert len(np.unique(kids)) == len(kids)
+    mu, mv, mw = chain["mst"]
+    assert np.array_equal(r["mst_u"], mu) and np.array_equal(r["mst_v"], mv)
+    assert np.array_equal(r["mst_w"], mw)
+    assert len(mu) == w.n_edges - r["n_comp"]
+
+
+def test_dendrogram(full, chain):
+    """Alg. 1 steps 2-3: the union-find replay's rows."""
+    _, r = full
+    a, b, s = chain["linkage"]
+    assert np.array_equal(r["link_a"], a) and np.array_equal(r["link_b"], b)
+    assert np.array_equal(r["link_size"], s)
+
+
+def test_condensed_tree_and_labels(full, chain):
+    """Alg. 1 steps 4-5: every condensed-tree array, the stabilities and
+    the selection, and the labels."""
+    _, r = full
+    c = chain["condensed"]
+    for key in CONDENSED:
+        assert np.array_equal(r[key], c[key]), key
+    assert np.array_equal(r["labels"], c["labels"])
+    assert r["n_clusters"] == c["n_clusters"]
 
 
 def test_labels_lie_in_components(full):
@@ -197,7 +194,7 @@ def test_levels(full):
     ml, mp = r["merge_level"], r["merge_parent"]
     merged = ml >= 0
     assert np.all(mp[merged] < np.nonzero(merged)[0]) and np.all(mp[~merged] == -1)
-    nmst_at = np.searchsorted(np.sort(r["mst_w"]), POW2, side="right")
+    nmst_at = np.searchsorted(r["mst_w"], POW2, side="right")    # the forest is sorted by w
     assert np.array_equal(r["n_components"], E - nmst_at)
     for li in (0, 10):
         keep = r["sk_w"] <= POW2[li]
