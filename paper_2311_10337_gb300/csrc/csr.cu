@@ -109,8 +109,6 @@ __global__ void k_init_flags(long long *flags) {
     flags[3] = LLONG_MIN;
 }
 
-__global__ void k_set_i64(long long *p, long long v) { *p = v; }
-
 // rank r = position of edge (t, id) in the global order; time-ordered
 // copies of the inputs for the later stages
 __global__ void k_rank_init(const unsigned long long *ks, int64_t E, long long tmin, int idbits,

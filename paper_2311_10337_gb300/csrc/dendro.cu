@@ -301,10 +301,10 @@ dgec_status stage_dendro(Ctx *c, const Problem &p, const Csr &g, const Msf &m, D
     const int sbits = bits_for((uint64_t)(n > 1 ? n - 1 : 1));
     if (n > 1) {
         const int gn = grid_for(n, kBlock, 65536);
-        TK(c, "k_d_order", k_d_order_keys<<<gn, kBlock, 0, st>>>(m.ru, n, sbits, s.k1));
+        TK(c, "k_d_order_keys", k_d_order_keys<<<gn, kBlock, 0, st>>>(m.ru, n, sbits, s.k1));
         bool in_b;
         DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, nullptr, nullptr}, n, sbits, sbits + lb, s.radix, &in_b));
-        TK(c, "k_d_order", k_d_order_act<<<gn, kBlock, 0, st>>>(in_b ? s.k2 : s.k1, n, sbits, m.ru, m.rv, s.act,
+        TK(c, "k_d_order_act", k_d_order_act<<<gn, kBlock, 0, st>>>(in_b ? s.k2 : s.k1, n, sbits, m.ru, m.rv, s.act,
                                                                s.ecu, s.ecv));
     }
     int64_t na = n;

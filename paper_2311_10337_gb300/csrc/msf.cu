@@ -62,19 +62,6 @@ __global__ void k_filter_bid(const int32_t *u, const int32_t *v, const int64_t *
                              unsigned long long *cnt, unsigned long long *bw) {
     filter_bid<false>(u, v, w, n, comp, u2, v2, w2, cnt, bw);
 }
-// First round: every node is its own component and every skeleton edge
-// joins two of them, so nothing is filtered: bid only, no compaction.
-__global__ void k_bid_first(const int32_t *u, const int32_t *v, const int64_t *w, int64_t n,
-                            unsigned long long *bw) {
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
-         x += (int64_t)gridDim.x * blockDim.x) {
-        int a = u[x], b = v[x];
-        unsigned long long uw = (unsigned long long)w[x];
-        if (uw < bw[a]) atomicMin(&bw[a], uw);
-        if (uw < bw[b]) atomicMin(&bw[b], uw);
-    }
-}
-
 __global__ void k_bid_uv(const int32_t *u, const int32_t *v, const int64_t *w, int64_t n,
                          const int32_t *comp, const unsigned long long *bw,
                          unsigned long long *buv) {
@@ -478,13 +465,13 @@ dgec_status stage_msf(Ctx *c, const Problem &p, const Csr &g, const Skel &sk, Ms
     for (int round = 0;; round++) {
         if (round >= 64) return set_err(c, DGEC_ERR_TIMEOUT, "Boruvka did not finish in 64 rounds");
         if (round == 0) {
-            TK(c, "k_bid_first", k_m_bid<<<grid_for(n, kBlock, 65536), kBlock, 0, st>>>(ccu, ccv, cw, n, s.bw));
+            TK(c, "k_m_bid", k_m_bid<<<grid_for(n, kBlock, 65536), kBlock, 0, st>>>(ccu, ccv, cw, n, s.bw));
         } else {
             int32_t *ncu = which ? s.cub : s.cua, *ncv = which ? s.cvb : s.cva;
             int32_t *nu = which ? s.ub : s.ua, *nv = which ? s.vb : s.va;
             int64_t *nw = which ? s.wb : s.wa;
             CU_TRY(c, cudaMemsetAsync(s.cnt, 0, sizeof(unsigned long long), st));
-            TK(c, "k_filter_bid", k_m_filter_bid<<<grid_for(n, kBlock, 65536), kBlock, 0, st>>>(
+            TK(c, "k_m_filter_bid", k_m_filter_bid<<<grid_for(n, kBlock, 65536), kBlock, 0, st>>>(
                                       ccu, ccv, cu, cv, cw, n, s.par, ncu, ncv, nu, nv, nw, s.cnt, s.bw));
             int64_t h[3];
             DG_TRY(read_counters(c, (const int64_t *)s.cnt, 3, h));
@@ -499,14 +486,14 @@ dgec_status stage_msf(Ctx *c, const Problem &p, const Csr &g, const Skel &sk, Ms
             which ^= 1;
         }
         const int gn = grid_for(n, kBlock, 65536), gr = grid_for(nr, kBlock, 65536);
-        TK(c, "k_bid_uv", k_m_bid_uv<<<gn, kBlock, 0, st>>>(ccu, ccv, cu, cv, cw, n, s.bw, s.buv));
-        TK(c, "k_claim", k_m_claim<<<gn, kBlock, 0, st>>>(ccu, ccv, cu, cv, n, s.buv, s.bp, s.win));
-        TK(c, "k_hook", k_m_hook<<<gr, kBlock, 0, st>>>(roots, nr, s.bw, s.buv, s.bp, s.win, cu, cv, cw,
+        TK(c, "k_m_bid_uv", k_m_bid_uv<<<gn, kBlock, 0, st>>>(ccu, ccv, cu, cv, cw, n, s.bw, s.buv));
+        TK(c, "k_m_claim", k_m_claim<<<gn, kBlock, 0, st>>>(ccu, ccv, cu, cv, n, s.buv, s.bp, s.win));
+        TK(c, "k_m_hook", k_m_hook<<<gr, kBlock, 0, st>>>(roots, nr, s.bw, s.buv, s.bp, s.win, cu, cv, cw,
                                                         g.rank_of, s.par, s.tu, s.tv, s.tru, s.trv, s.tw,
                                                         s.cnt + 1));
-        TK(c, "k_jump", k_m_jump<<<gr, kBlock, 0, st>>>(roots, nr, s.par));
+        TK(c, "k_m_jump", k_m_jump<<<gr, kBlock, 0, st>>>(roots, nr, s.par));
         CU_TRY(c, cudaMemsetAsync(s.cnt + 2, 0, sizeof(unsigned long long), st));
-        TK(c, "k_next_roots", k_m_next_roots<<<gr, kBlock, 0, st>>>(roots, nr, s.par, s.bw, s.buv, roots2,
+        TK(c, "k_m_next_roots", k_m_next_roots<<<gr, kBlock, 0, st>>>(roots, nr, s.par, s.bw, s.buv, roots2,
                                                                     s.cnt + 2));
         int32_t *tr = roots;
         roots = roots2;
@@ -522,7 +509,7 @@ dgec_status stage_msf(Ctx *c, const Problem &p, const Csr &g, const Skel &sk, Ms
     unsigned long long *K[2] = {s.k1, s.k2}, *Vb[2] = {s.v1, s.v2};
     int cur = 0;
     bool in_b;
-    TK(c, "k_pack_uv", k_pack_uv_idx<<<gm, kBlock, 0, st>>>(s.tu, s.tv, m, p.idbits, K[0], Vb[0]));
+    TK(c, "k_pack_uv_idx", k_pack_uv_idx<<<gm, kBlock, 0, st>>>(s.tu, s.tv, m, p.idbits, K[0], Vb[0]));
     DG_TRY(radix_sort(c, RadixBuffers{K[cur], K[1 - cur], Vb[cur], Vb[1 - cur]}, m, 0, 2 * p.idbits,
                       s.radix, &in_b));
     if (in_b) cur = 1 - cur;
