@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--dominant", default="k_ranks_knn",
                     help="kernel timed live for the roofline object")
-    ap.add_argument("--cpu-sample-minutes", type=float, default=120.0)
+    ap.add_argument("--cpu-sample-minutes", type=float, default=150.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch-graphs", type=int, default=128,
@@ -119,6 +119,19 @@ def time_window_sample(w, minutes):
     return w.src[sel], w.dst[sel], w.t[sel]
 
 
+def cpu_model() -> str:
+    """The host CPU's model name as lscpu prints it (machine type if unknown)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.machine() or "unknown"
+
+
 def cpu_baseline(w, minutes):
     from oracle import oracle as O
     O.build()
@@ -128,7 +141,8 @@ def cpu_baseline(w, minutes):
     dt = time.perf_counter() - t0
     return {"value": len(s) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {minutes:g} min of the {w.name} stream: {len(s)} edges "
-                      f"(of {w.n_edges}), single-threaded C oracle, {dt:.2f} s"}
+                      f"(of {w.n_edges}), single-threaded C oracle, {dt:.2f} s",
+            "host": f"{cpu_model()}, {os.cpu_count()} cores, 1 used"}
 
 
 class Clocks:
