@@ -197,6 +197,27 @@ def workspace_size(n_edges: int, n_vertices: int, k: int, min_cluster_size: int,
     return int(out.value)
 
 
+def _dev(name, x, dtype, n, device):
+    """A device argument must be a contiguous 1-D tensor of `dtype` with `n`
+    elements on cuda:`device`: the kernels read exactly that many."""
+    if (not hasattr(x, "is_cuda") or x.dtype != dtype or not x.is_cuda or not x.is_contiguous()
+            or x.dim() != 1 or x.device.index != device):
+        raise ValueError(f"{name} must be a contiguous 1-D {dtype} tensor on cuda:{device}")
+    if n is not None and int(x.shape[0]) != n:
+        raise ValueError(f"{name} has {int(x.shape[0])} elements, expected {n}")
+
+
+def _host(name, a, dtype, n, writeable=False):
+    """A host argument must be a C-contiguous 1-D numpy array of `dtype` with
+    `n` elements: the library copies exactly that many bytes from (or to) it."""
+    if (not isinstance(a, np.ndarray) or a.dtype != dtype or a.ndim != 1 or not a.flags.c_contiguous
+            or (writeable and not a.flags.writeable)):
+        raise ValueError(f"{name} must be a {'writeable ' if writeable else ''}C-contiguous 1-D numpy "
+                         f"{np.dtype(dtype).name} array")
+    if a.shape[0] != n:
+        raise ValueError(f"{name} has {a.shape[0]} elements, expected {n}")
+
+
 class Context:
     """A dgec context on one CUDA device plus a reusable torch workspace."""
 
@@ -236,6 +257,25 @@ class Context:
             self.ws = torch.empty(nbytes, dtype=torch.uint8, device=f"cuda:{self.device}")
         return self.ws
 
+    def _stream(self, stream, ws):
+        """The launch stream: the current one by default. A workspace used on
+        another stream is recorded there, so that the caching allocator does
+        not hand its memory out again while that stream still uses it."""
+        cur = self.torch.cuda.current_stream(self.device)
+        if stream is None:
+            return cur
+        if stream != cur:
+            ws.record_stream(stream)
+        return stream
+
+    def _graph_args(self, src, dst, t):
+        torch = self.torch
+        E = int(src.shape[0]) if hasattr(src, "shape") and len(src.shape) == 1 else -1
+        _dev("src", src, torch.int32, None, self.device)
+        _dev("dst", dst, torch.int32, E, self.device)
+        _dev("t", t, torch.int64, E, self.device)
+        return E
+
     def launches(self) -> int:
         return int(self.L.dgec_last_launch_count(self.h))
 
@@ -266,15 +306,11 @@ class Context:
         delta_max: the time cutoff of Sec. 4.3 (None = no cutoff); mrd: cluster
         the mutual-reachability graph (an approximation, see dgec.h);
         delta_nc: the nearly-causal tolerance of Sec. 4.3 (None = causal)."""
-        torch = self.torch
-        E = int(src.shape[0])
-        for x, dt in ((src, torch.int32), (dst, torch.int32), (t, torch.int64)):
-            if x.dtype != dt or not x.is_cuda or not x.is_contiguous():
-                raise ValueError("src/dst must be contiguous cuda int32, t cuda int64")
+        E = self._graph_args(src, dst, t)
         p = _params(k, min_cluster_size, delta_max, mrd, delta_nc)
         need = workspace_size(E, n_vertices, k, min_cluster_size, mrd, delta_nc)
         ws = self.workspace(need)
-        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        st = self._stream(stream, ws)
         res = Result()
         rc = self.L.dgec_run(self.h, src.data_ptr(), dst.data_ptr(), t.data_ptr(), E, n_vertices,
                              ctypes.byref(p), ws.data_ptr(), ws.numel(), st.cuda_stream,
@@ -287,17 +323,13 @@ class Context:
         """Discrete dendrogram (Alg. 5) at thresholds `omega` on device tensors,
         plus condensed labels when min_cluster_size >= 2. Returns a
         LevelsOutput viewing the workspace (valid until the next run)."""
-        torch = self.torch
-        E = int(src.shape[0])
-        for x, dt in ((src, torch.int32), (dst, torch.int32), (t, torch.int64)):
-            if x.dtype != dt or not x.is_cuda or not x.is_contiguous():
-                raise ValueError("src/dst must be contiguous cuda int32, t cuda int64")
+        E = self._graph_args(src, dst, t)
         om = np.ascontiguousarray(omega, dtype=np.int64)
         p = LevelsParams(len(om), om.ctypes.data, min_cluster_size, LEVELS_DENSE if dense else 0)
         nb = ctypes.c_size_t(0)
         self._check(self.L.dgec_levels_workspace_size(E, n_vertices, ctypes.byref(p), ctypes.byref(nb)))
         ws = self.workspace(nb.value)
-        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        st = self._stream(stream, ws)
         res = LevelsResult()
         rc = self.L.dgec_run_levels(self.h, src.data_ptr(), dst.data_ptr(), t.data_ptr(), E,
                                     n_vertices, ctypes.byref(p), ws.data_ptr(), ws.numel(),
@@ -311,21 +343,24 @@ class Context:
         t int64[E], member rows s_off int64[E+1] / s_vert int32[Ms], and for a
         directed hypergraph target rows d_off / d_vert (sources in s_*)."""
         torch = self.torch
-        E = int(t.shape[0])
         directed = d_off is not None
-        arrays = [(t, torch.int64), (s_off, torch.int64), (s_vert, torch.int32)]
-        if directed:
-            arrays += [(d_off, torch.int64), (d_vert, torch.int32)]
-        for x, dt in arrays:
-            if x.dtype != dt or not x.is_cuda or not x.is_contiguous():
-                raise ValueError("hypergraph arrays must be contiguous cuda tensors (int64 t/offsets, int32 members)")
+        if directed != (d_vert is not None):
+            raise ValueError("a directed hypergraph needs both d_off and d_vert")
+        _dev("t", t, torch.int64, None, self.device)
+        E = int(t.shape[0])
+        _dev("s_off", s_off, torch.int64, E + 1, self.device)
+        _dev("s_vert", s_vert, torch.int32, None, self.device)
         Ms = int(s_vert.shape[0])
-        Md = int(d_vert.shape[0]) if directed else 0
+        Md = 0
+        if directed:
+            _dev("d_off", d_off, torch.int64, E + 1, self.device)
+            _dev("d_vert", d_vert, torch.int32, None, self.device)
+            Md = int(d_vert.shape[0])
         p = HyperParams(1 if directed else 0, min_cluster_size, 0)
         nb = ctypes.c_size_t(0)
         self._check(self.L.dgec_hyper_workspace_size(E, n_vertices, Ms, Md, ctypes.byref(p), ctypes.byref(nb)))
         ws = self.workspace(nb.value)
-        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        st = self._stream(stream, ws)
         res = HyperResult()
         rc = self.L.dgec_run_hyper(self.h, t.data_ptr(), E, n_vertices, s_off.data_ptr(), s_vert.data_ptr(), Ms,
                                    d_off.data_ptr() if directed else None,
@@ -344,14 +379,17 @@ class Context:
                  delta_max=None, mrd: bool = False, delta_nc=None):
         """Alg. 4 from host arrays (pinned numpy views avoid staging copies);
         returns (labels, n_clusters)."""
-        torch = self.torch
+        _host("src", src, np.int32, src.shape[0] if isinstance(src, np.ndarray) and src.ndim == 1 else -1)
         E = int(src.shape[0])
+        _host("dst", dst, np.int32, E)
+        _host("t", t, np.int64, E)
+        if labels_out is None:
+            labels_out = np.empty(E, np.int32)
+        _host("labels_out", labels_out, np.int32, E, writeable=True)
         p = _params(k, min_cluster_size, delta_max, mrd, delta_nc)
         need = workspace_size(E, n_vertices, k, min_cluster_size, mrd, delta_nc) + 16 * E + 4096
         ws = self.workspace(need)
-        if labels_out is None:
-            labels_out = np.empty(E, np.int32)
-        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        st = self._stream(stream, ws)
         ncl = ctypes.c_int32(0)
         rc = self.L.dgec_run_host(self.h, src.ctypes.data, dst.ctypes.data, t.ctypes.data, E,
                                   n_vertices, ctypes.byref(p), ws.data_ptr(), ws.numel(),
@@ -389,9 +427,13 @@ def _run_batch(ctx, src, dst, t, edge_off, n_vertices, k, min_cluster_size, stre
     kk = np.ascontiguousarray(k, np.int32)
     mm = np.ascontiguousarray(min_cluster_size, np.int32)
     G = len(nv)
+    n = int(eo[-1]) if len(eo) else 0
+    _dev("src", src, torch.int32, n, ctx.device)
+    _dev("dst", dst, torch.int32, n, ctx.device)
+    _dev("t", t, torch.int64, n, ctx.device)
     need = batch_workspace_size(eo, nv, kk, mm)
     ws = ctx.workspace(need)
-    st = stream if stream is not None else torch.cuda.current_stream(ctx.device)
+    st = ctx._stream(stream, ws)
     res = BatchResult()
     rc = ctx.L.dgec_run_batch(ctx.h, G, _i64p(eo), _i32p(nv), _i32p(kk), _i32p(mm),
                               src.data_ptr(), dst.data_ptr(), t.data_ptr(), ws.data_ptr(),
@@ -472,12 +514,19 @@ class Server:
         if rc != DGEC_OK:
             raise DgecError(rc, "dgec_server_create failed")
         self.h = h
+        self.device = device
         self._keep = {}
 
     def lane_capacity(self) -> int:
         return int(self.L.dgec_server_lane_capacity(self.h))
 
     def submit(self, src, dst, t, k: int, min_cluster_size: int, labels) -> int:
+        import torch
+        E = int(src.shape[0]) if hasattr(src, "shape") and len(src.shape) == 1 else -1
+        _dev("src", src, torch.int32, None, self.device)
+        _dev("dst", dst, torch.int32, E, self.device)
+        _dev("t", t, torch.int64, E, self.device)
+        _dev("labels", labels, torch.int32, E, self.device)
         j = Job(src.data_ptr(), dst.data_ptr(), t.data_ptr(), int(src.shape[0]), k,
                 min_cluster_size, labels.data_ptr())
         tk = ctypes.c_uint64(0)

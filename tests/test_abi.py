@@ -4,6 +4,7 @@ import glob
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2311_10337_gb300 import build as B
@@ -53,3 +54,30 @@ def test_workspace_size_and_argument_checks(lib):
 def test_status_strings(lib):
     assert lib.dgec_status_string(0) == b"ok"
     assert lib.dgec_status_string(3) == b"self loop"
+
+
+def test_host_arguments_are_checked_before_any_copy():
+    """The host entry point copies exactly E elements from each array, so a
+    wrong dtype, a strided view or a short array is rejected in the binding."""
+    ok = np.zeros(5, np.int32)
+    dgec._host("src", ok, np.int32, 5)
+    for bad in (np.zeros(5, np.int64), np.zeros(10, np.int32)[::2], np.zeros((5, 1), np.int32),
+                np.zeros(4, np.int32), [0, 0, 0, 0, 0]):
+        with pytest.raises(ValueError):
+            dgec._host("src", bad, np.int32, 5)
+    ro = np.zeros(5, np.int32)
+    ro.flags.writeable = False
+    dgec._host("labels_out", ro, np.int32, 5)
+    with pytest.raises(ValueError):
+        dgec._host("labels_out", ro, np.int32, 5, writeable=True)
+
+
+def test_device_arguments_are_checked_before_any_launch():
+    """Device arguments must be contiguous 1-D CUDA tensors of the right dtype
+    and length on the context's device; host tensors and numpy arrays are
+    rejected (there is no CPU path)."""
+    import torch
+    for bad in (torch.zeros(5, dtype=torch.int32), np.zeros(5, np.int32),
+                torch.zeros(5, dtype=torch.int64), torch.zeros(10, dtype=torch.int32)[::2]):
+        with pytest.raises(ValueError):
+            dgec._dev("src", bad, torch.int32, 5, 0)
