@@ -180,8 +180,8 @@ dgec_status dgec_run_host(dgec_ctx *ctx, const int32_t *h_src,
 
 /*
  * Batched form: many independent graphs in one pass of the pipeline (the
- * the benchmark spec's batching pattern; the paper's method per graph is
- * unchanged, Alg. 4 runs on each graph as if alone). Graph g owns the
+ * paper has no batched form; its method per graph is unchanged, Alg. 4
+ * runs on each graph as if alone). Graph g owns the
  * input edges [h_edge_off[g], h_edge_off[g+1]) of d_src/d_dst/d_t, with
  * vertex ids local to the graph in [0, h_n_vertices[g]), its own k and
  * min cluster size, and its own virtual root. Every result equals the
@@ -224,9 +224,10 @@ dgec_status dgec_run_batch(dgec_ctx *ctx, int32_t n_graphs, const int64_t *h_edg
                            size_t ws_bytes, void *cuda_stream, dgec_batch_result *out);
 
 /*
- * Serving: a request loop with continuous batching (the benchmark spec's
- * serving pattern). The server splits a caller-provided device pool into
- * n_lanes lanes, each with its own host thread, CUDA stream and workspace.
+ * Serving: a request loop with continuous batching of windowed clustering
+ * jobs (no counterpart in the paper). The server splits a caller-provided
+ * device pool into n_lanes lanes, each with its own host thread, CUDA
+ * stream and workspace.
  * A free lane takes, in arrival order, every pending job that fits its
  * memory (admission by memory), renumbers each job's vertices densely on
  * the device, runs them together as one batch (dgec_run_batch) and writes
