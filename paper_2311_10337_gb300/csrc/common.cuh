@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <string.h>
@@ -52,6 +53,22 @@ dgec_status set_err(Ctx *c, dgec_status s, const char *fmt, ...);
     do {                                               \
         dgec_status _s = (expr);                       \
         if (_s != DGEC_OK) return _s;                  \
+    } while (0)
+
+// A named range over one pipeline stage on the host timeline (NVTX), for
+// profilers that record NVTX ranges; nothing is recorded when none is
+// attached. The range closes on every exit, the error returns included.
+struct StageRange {
+    explicit StageRange(const char *name) { nvtxRangePushA(name); }
+    ~StageRange() { nvtxRangePop(); }
+    StageRange(const StageRange &) = delete;
+    StageRange &operator=(const StageRange &) = delete;
+};
+
+#define DG_STAGE(name, expr)        \
+    do {                            \
+        StageRange _range(name);    \
+        DG_TRY(expr);               \
     } while (0)
 
 #define CU_TRY(c, expr)                                                          \

@@ -200,25 +200,25 @@ dgec_status run_pipeline(Ctx *c, const HostBatch &hb, const int32_t *d_src, cons
     p.gk = L.gk;
     p.gM = L.gM;
     p.egraph = L.egraph;
-    DG_TRY(stage_csr(c, p, L.csr, L.scratch));
-    DG_TRY(stage_skeleton(c, p, L.csr, L.skel, L.scratch));
+    DG_STAGE("A incidence lists", stage_csr(c, p, L.csr, L.scratch));
+    DG_STAGE("B skeleton and kNN", stage_skeleton(c, p, L.csr, L.skel, L.scratch));
     const Skel *forest_in = &L.skel;
     if (p.dnc > 0) {
-        DG_TRY(stage_nc_negate(c, p, L.tneg));
+        DG_STAGE("N negated times", stage_nc_negate(c, p, L.tneg));
         Problem p2 = p;
         p2.t = L.tneg;
-        DG_TRY(stage_csr(c, p2, L.csr2, L.scratch));
-        DG_TRY(stage_skeleton(c, p2, L.csr2, L.skel2, L.scratch));
-        DG_TRY(stage_nc(c, p, L.csr, L.skel, L.skel2, L.ncs, L.scratch));
+        DG_STAGE("A incidence lists", stage_csr(c, p2, L.csr2, L.scratch));
+        DG_STAGE("B skeleton and kNN", stage_skeleton(c, p2, L.csr2, L.skel2, L.scratch));
+        DG_STAGE("N nearly-causal union", stage_nc(c, p, L.csr, L.skel, L.skel2, L.ncs, L.scratch));
         forest_in = &L.ncs;
     }
     if (p.mrd) {
-        DG_TRY(stage_mrd(c, p, L.csr, L.skel, L.mrd, L.scratch));
+        DG_STAGE("R mutual-reachability graph", stage_mrd(c, p, L.csr, L.skel, L.mrd, L.scratch));
         forest_in = &L.mrd;
     }
-    DG_TRY(stage_msf(c, p, L.csr, *forest_in, L.msf, L.scratch));
-    DG_TRY(stage_dendro(c, p, L.csr, L.msf, L.den, L.scratch));
-    DG_TRY(stage_condense(c, p, L.msf, L.den, L.cond, L.scratch));
+    DG_STAGE("C spanning forest", stage_msf(c, p, L.csr, *forest_in, L.msf, L.scratch));
+    DG_STAGE("D1 dendrogram", stage_dendro(c, p, L.csr, L.msf, L.den, L.scratch));
+    DG_STAGE("D2 condense and labels", stage_condense(c, p, L.msf, L.den, L.cond, L.scratch));
     if (p.G > 1 && L.msf.n > 0)
         TK(c, "k_localize", k_localize<<<grid_for(L.msf.n, kBlock, 65536), kBlock, 0, c->stream>>>(
                                 L.msf.n, p.E, L.msf.u, L.msf.v, L.den.a, L.den.b, p.egraph, p.eoff,
@@ -594,13 +594,13 @@ dgec_status dgec_run_levels(dgec_ctx *x, const int32_t *d_src, const int32_t *d_
     p.gk = L.gk;
     p.gM = L.gM;
     p.egraph = L.egraph;
-    DG_TRY(stage_csr(c, p, L.csr, L.scratch));
-    DG_TRY(stage_skeleton(c, p, L.csr, L.skel, L.scratch));
-    DG_TRY(stage_levels(c, p, L.csr, L.skel, params->h_omega, L.lv, L.scratch));
+    DG_STAGE("A incidence lists", stage_csr(c, p, L.csr, L.scratch));
+    DG_STAGE("B skeleton and kNN", stage_skeleton(c, p, L.csr, L.skel, L.scratch));
+    DG_STAGE("L discrete levels", stage_levels(c, p, L.csr, L.skel, params->h_omega, L.lv, L.scratch));
     if (condense) {
-        DG_TRY(build_level_rows(c, p, L.csr, L.lv, L.scratch));
-        DG_TRY(stage_dendro(c, p, L.csr, L.lv.rows, L.den, L.scratch));
-        DG_TRY(stage_condense(c, p, L.lv.rows, L.den, L.cond, L.scratch));
+        DG_STAGE("L rows of D", build_level_rows(c, p, L.csr, L.lv, L.scratch));
+        DG_STAGE("D1 dendrogram", stage_dendro(c, p, L.csr, L.lv.rows, L.den, L.scratch));
+        DG_STAGE("D2 condense and labels", stage_condense(c, p, L.lv.rows, L.den, L.cond, L.scratch));
     }
     CU_TRY(c, cudaStreamSynchronize(c->stream));
     CU_TRY(c, cudaGetLastError());

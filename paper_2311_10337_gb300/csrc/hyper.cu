@@ -532,10 +532,10 @@ dgec_status dgec_run_hyper(dgec_ctx *x, const int64_t *d_t, int64_t n_hyperedges
     p.gk = L.gk;
     p.gM = L.gM;
     p.egraph = L.egraph;
-    DG_TRY(stage_hyper(c, p, h, L.csr, L.S, L.D, L.skel, L.scratch));
-    DG_TRY(stage_msf(c, p, L.csr, L.skel, L.msf, L.scratch));
-    DG_TRY(stage_dendro(c, p, L.csr, L.msf, L.den, L.scratch));
-    DG_TRY(stage_condense(c, p, L.msf, L.den, L.cond, L.scratch));
+    DG_STAGE("H hypergraph skeleton", stage_hyper(c, p, h, L.csr, L.S, L.D, L.skel, L.scratch));
+    DG_STAGE("C spanning forest", stage_msf(c, p, L.csr, L.skel, L.msf, L.scratch));
+    DG_STAGE("D1 dendrogram", stage_dendro(c, p, L.csr, L.msf, L.den, L.scratch));
+    DG_STAGE("D2 condense and labels", stage_condense(c, p, L.msf, L.den, L.cond, L.scratch));
     CU_TRY(c, cudaStreamSynchronize(c->stream));
     CU_TRY(c, cudaGetLastError());
     kt_collect(c);
