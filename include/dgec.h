@@ -72,7 +72,7 @@ typedef enum {
 
 typedef struct {
     int32_t k;                /* neighbours per edge for the kNN output, 1 <= k <= 16 */
-    int32_t min_cluster_size; /* M of Alg. 1 step 4, M >= 2 */
+    int32_t min_cluster_size; /* M of Alg. 1's condensing, M >= 2 */
     uint32_t flags;           /* 0, or any of DGEC_CUTOFF, DGEC_MRD, DGEC_NEARLY_CAUSAL */
     int64_t delta_max;        /* with DGEC_CUTOFF: the cutoff, >= 0 (ignored otherwise). Only arcs
                                  with w <= delta_max are in the line graph: the skeleton keeps the
@@ -86,7 +86,7 @@ typedef struct dgec_ctx dgec_ctx;
 /* Results of dgec_run. Device arrays point into the caller's workspace and
  * stay valid until that workspace is reused. Counts are host values. */
 typedef struct {
-    /* Alg. 3 first line: incidence lists. Vertex v's out-edges are
+    /* Incidence lists (the adjacency lists Alg. 3 starts from). Vertex v's out-edges are
      * out_id[out_off[v] .. out_off[v+1]) with times out_t[..], sorted by
      * (t, id); likewise in-edges via in_off/in_t/in_id. */
     const int64_t *out_off, *in_off;   /* [n_vertices + 1] */
@@ -108,16 +108,16 @@ typedef struct {
      * node has fewer than k neighbours. */
     const int32_t *knn_id;             /* [n_edges * k] */
     const int64_t *core;               /* [n_edges] */
-    /* Alg. 1 steps 1-2: minimum spanning forest of L*_G under the strict
+    /* Alg. 1, forest and its weight order: minimum spanning forest of L*_G under the strict
      * order (w, u, v), sorted by that order. */
     const int32_t *mst_u, *mst_v;      /* [n_mst] */
     const int64_t *mst_w;
-    /* Alg. 1 step 3: dendrogram. Row s merges clusters link_a[s] < link_b[s]
+    /* Alg. 1, union-find dendrogram. Row s merges clusters link_a[s] < link_b[s]
      * (a leaf id < n_edges, or n_edges + s' for the cluster row s' formed)
      * at weight mst_w[s]; link_size[s] leaves below it. */
     const int32_t *link_a, *link_b;    /* [n_mst] */
     const int64_t *link_size;
-    /* Alg. 1 steps 4-5: condensed tree (min cluster size M) and excess of
+    /* Alg. 1, condensing and cluster extraction: condensed tree (min cluster size M) and excess of
      * mass selection. lambda(w) = floor((2^64-1)/(w+1)); lambda 0 at a
      * virtual root (id n_edges + n_mst) above the components. Point e
      * leaves cluster fall_cluster[e] at lambda fall_lambda[e]. Clusters,
@@ -152,8 +152,8 @@ dgec_status dgec_workspace_size(int64_t n_edges, int32_t n_vertices,
                                 const dgec_params *params, size_t *bytes);
 
 /*
- * Alg. 4 end to end on device-resident edges: incidence lists (Alg. 3
- * first line), skeleton (Alg. 2-3), kNN and core distances, minimum
+ * Alg. 4 end to end on device-resident edges: incidence lists (the
+ * adjacency lists Alg. 3 starts from), skeleton (Alg. 2-3), kNN and core distances, minimum
  * spanning forest, dendrogram, condensed tree, labels (Alg. 1).
  * d_src, d_dst: int32[n_edges] vertex ids in [0, n_vertices);
  * d_t: int64[n_edges] times. The time span (max t - min t) must satisfy
@@ -314,8 +314,8 @@ dgec_status dgec_msf_static(const int32_t *d_u, const int32_t *d_v, const int64_
  * Given thresholds omega_0 < omega_1 < ... < omega_{q-1}, level i is the
  * partition comps(L*_G, omega_i) of the edges: two edges share a component
  * when a path of skeleton links of weight <= omega_i joins them (Alg. 5
- * writes "less than"; the appendix's "<=" is used, so a threshold equal to
- * a weight admits it). By Thm. 3 these are the components of L_G itself.
+ * admits links strictly below the threshold, the appendix links up to it;
+ * the latter is used, so a threshold equal to a weight admits it). By Thm. 3 these are the components of L_G itself.
  * Components are named by their smallest member edge id; levels are nested
  * and D is the tree of containments between consecutive levels.
  *

@@ -15,7 +15,7 @@
  * Parity pins: every function below is pinned by tests in tests/ against
  * brute force on the explicit line graph (Def. 1), against Thm. 1-3, and
  * against the worked example printed in the paper (the chain table of
- * Sec. 4.1.3). The condensed-tree / excess-of-mass step (Alg. 1 steps 4-5)
+ * Sec. 4.1.3). The condensed-tree / excess-of-mass step of Alg. 1
  * is defined by the paper only by citation to HDBSCAN; its pins are the
  * hand-worked golden cases under tests/golden/ and filtration invariants.
  * The discrete dendrogram (Alg. 5) is pinned against brute-force components
@@ -35,9 +35,9 @@
 #define ORC_ERR_OOM 5
 
 /* ------------------------------------------------------------------ */
-/* Incidence lists (Alg. 3 first line: adjacency list of G).           */
+/* Incidence lists (the adjacency lists of G that Alg. 3 starts from).  */
 /* Each vertex keeps its in-list and out-list sorted by (t, id)        */
-/* ("Sort E_i by time", Alg. 2; ties by id, a reading).                 */
+/* (Alg. 2's time order; ties by id, a reading).                       */
 /* ------------------------------------------------------------------ */
 
 static const int64_t *g_t; /* comparator context */
@@ -146,7 +146,7 @@ int64_t orc_skeleton_raw(int64_t n_edges, int32_t n_vertices,
     for (int32_t i = 0; i < n_vertices; i++) {
         inc_rec *Ei = all + deg[i];
         int64_t di = deg[i + 1] - deg[i];
-        qsort(Ei, (size_t)di, sizeof(inc_rec), cmp_inc); /* "Sort E_i by time" */
+        qsort(Ei, (size_t)di, sizeof(inc_rec), cmp_inc); /* Alg. 2: E_i in time order */
         int64_t wlen = 0;                                /* W = [] */
         for (int64_t x = 0; x < di; x++) {
             if (Ei[x].dir == 0) {
@@ -290,8 +290,8 @@ int orc_knn(int64_t n_edges, int32_t n_vertices, const int32_t *src,
 }
 
 /* ------------------------------------------------------------------ */
-/* Alg. 1 step 1: minimum spanning forest by Kruskal's algorithm on    */
-/* the undirected skeleton, edges taken in (w, u, v) order (a strict   */
+/* Alg. 1, spanning forest: minimum spanning forest by Kruskal on the  */
+/* undirected skeleton, edges taken in (w, u, v) order (a strict       */
 /* total order, so the forest is unique).                             */
 /* ------------------------------------------------------------------ */
 
@@ -316,7 +316,7 @@ int64_t orc_mst(int64_t n_nodes, int64_t n_sk, const int32_t *u,
         all[x].u = u[x] < v[x] ? u[x] : v[x];
         all[x].v = u[x] < v[x] ? v[x] : u[x];
     }
-    qsort(all, (size_t)n_sk, sizeof(wedge), cmp_wedge); /* Alg. 1 step 2 order */
+    qsort(all, (size_t)n_sk, sizeof(wedge), cmp_wedge); /* Alg. 1's weight order */
     for (int64_t x = 0; x < n_nodes; x++) par[x] = (int32_t)x;
     int64_t m = 0;
     for (int64_t x = 0; x < n_sk; x++) {
@@ -330,7 +330,7 @@ int64_t orc_mst(int64_t n_nodes, int64_t n_sk, const int32_t *u,
 }
 
 /* ------------------------------------------------------------------ */
-/* Alg. 1 step 3: dendrogram by union-find replay of the sorted forest. */
+/* Alg. 1, dendrogram: union-find replay of the sorted forest.         */
 /* Row s merges the clusters holding mu[s] and mv[s]; a cluster is     */
 /* named by a leaf id (< n_nodes) or n_nodes + (row that formed it).   */
 /* a = smaller name, b = larger name, size = leaves below the row.     */
@@ -360,8 +360,9 @@ int orc_linkage(int64_t n_nodes, int64_t n_mst, const int32_t *mu,
 }
 
 /* ------------------------------------------------------------------ */
-/* Alg. 1 steps 4-5: condensed tree with minimum cluster size M and    */
-/* excess-of-mass ("volume in dendrogram space") cluster selection.    */
+/* Alg. 1, condensing and extraction: condensed tree with minimum      */
+/* cluster size M and excess-of-mass cluster selection (the paper's    */
+/* volume in dendrogram space).                                       */
 /* The paper defines these steps by citation to HDBSCAN; readings:     */
 /*  - merges of equal weight are one multi-way merge (level collapse), */
 /*    so the result depends only on the weighted connectivity;         */

@@ -1,5 +1,6 @@
-// Stage D2: condensed tree with minimum cluster size M (Alg. 1 step 4),
-// excess-of-mass selection (Alg. 1 step 5, "volume in dendrogram space")
+// Stage D2: condensed tree with minimum cluster size M (Alg. 1, condensing),
+// excess-of-mass selection (Alg. 1, clusters chosen by their volume in the
+// dendrogram)
 // and the edge-cluster labels of Alg. 4.
 //
 // The paper defines these steps by citation to HDBSCAN. Readings kept

@@ -1,6 +1,6 @@
-// Stage A: incidence lists (Alg. 3, first line: "Generate adjacency list
-// representation") with every vertex's in-list and out-list sorted by time
-// (Alg. 2: "Sort E_i by time"; ties by edge id).
+// Stage A: incidence lists (the adjacency lists Alg. 3 starts from) with
+// every vertex's in-list and out-list sorted by time as Alg. 2 needs them
+// (ties by edge id).
 //
 // First a device-wide radix sort of the 64-bit keys ((t - t_min) << idbits
 // | id) ranks all edges in (t, id) order. The keys are laid out in id order

@@ -1,4 +1,4 @@
-// Stage D1: single-linkage dendrogram (Alg. 1 step 3) of the sorted
+// Stage D1: single-linkage dendrogram (Alg. 1, union-find dendrogram) of the sorted
 // forest, built in parallel rounds instead of one union-find sweep.
 //
 // Merge s is the s-th forest edge in (w, u, v) order; its dendrogram node is

@@ -1,5 +1,5 @@
-// Stage C: minimum spanning forest of the undirected skeleton (Alg. 1
-// step 1) by Borůvka rounds, then sorted by (w, u, v) (Alg. 1 step 2).
+// Stage C: minimum spanning forest of the undirected skeleton (Alg. 1)
+// by Borůvka rounds, then sorted by (w, u, v) as Alg. 1 orders it.
 //
 // The order (w, min id, max id) is strict (a pair appears once in L*), so
 // the forest is unique. Each round: every live edge between two components

@@ -46,7 +46,7 @@ void carve_segsort(Arena &a, int64_t V, int64_t n, SegSort &s);
 dgec_status sort_segments(Ctx *c, int64_t V, unsigned long long *keys, const int64_t *off, SegSort &s,
                           int key_bits);
 
-// Stage A: incidence lists (Alg. 3 first line), per-vertex lists sorted by
+// Stage A: incidence lists (Alg. 3's adjacency lists), per-vertex lists sorted by
 // (t, id).
 //
 // Internal numbering: every later stage names a line-graph node (a temporal

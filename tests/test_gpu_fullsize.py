@@ -141,7 +141,7 @@ def test_knn_sampled(full):
 
 
 def test_forest(full, chain):
-    """Alg. 1 step 1: the oracle's Kruskal forest, element by element, and
+    """Alg. 1, spanning forest: the oracle's Kruskal forest, element by element, and
     one tree per component of the skeleton."""
     w, r = full
     mu, mv, mw = chain["mst"]
@@ -151,7 +151,7 @@ def test_forest(full, chain):
 
 
 def test_dendrogram(full, chain):
-    """Alg. 1 steps 2-3: the union-find replay's rows."""
+    """Alg. 1, dendrogram: the union-find replay's rows."""
     _, r = full
     a, b, s = chain["linkage"]
     assert np.array_equal(r["link_a"], a) and np.array_equal(r["link_b"], b)
@@ -159,7 +159,7 @@ def test_dendrogram(full, chain):
 
 
 def test_condensed_tree_and_labels(full, chain):
-    """Alg. 1 steps 4-5: every condensed-tree array, the stabilities and
+    """Alg. 1, condensing and extraction: every condensed-tree array, the stabilities and
     the selection, and the labels."""
     _, r = full
     c = chain["condensed"]

@@ -157,7 +157,7 @@ def _path_max_key(adj, a, b):
 
 @pytest.mark.parametrize("g", GRAPHS, ids=lambda g: g.name)
 def test_mst_cycle_property(g):
-    """Alg. 1 step 1 on L*: the forest spans L*'s components, and every
+    """Alg. 1's spanning forest on L*: the forest spans L*'s components, and every
     skeleton edge outside it is the largest (w, u, v) key on the cycle it
     closes (the cycle characterisation of the unique MSF under a strict
     order); Thm. 1: its weight multiset equals that of an MSF of L_G."""
@@ -188,7 +188,7 @@ def test_mst_cycle_property(g):
 
 @pytest.mark.parametrize("g", GRAPHS[::2], ids=lambda g: g.name)
 def test_linkage_ultrametric(g):
-    """Alg. 1 step 3: the height at which two nodes first share a cluster of
+    """Alg. 1's dendrogram: the height at which two nodes first share a cluster of
     the dendrogram equals their minimax distance in L_G (Thm. 1 + 3)."""
     E = g.n_edges
     if E > 90:
