@@ -358,9 +358,11 @@ dgec_status dgec_create(dgec_ctx **out, int device) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_pinned, 4096);
     c->kt = new (std::nothrow) KernelTimer();
-    if (e != cudaSuccess) {
+    if (e != cudaSuccess || !c->kt) {
+        if (c->h_pinned) cudaFreeHost(c->h_pinned);
+        delete c->kt;
         delete x;
-        return DGEC_ERR_CUDA;
+        return e != cudaSuccess ? DGEC_ERR_CUDA : DGEC_ERR_OOM;
     }
     *out = x;
     return DGEC_OK;

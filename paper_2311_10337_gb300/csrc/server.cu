@@ -265,7 +265,7 @@ dgec_status dgec_server_create(int device, void *d_pool, size_t pool_bytes, int3
         L->bytes = slice;
         if (dgec_create(&L->ctx, device) != DGEC_OK ||
             cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking) != cudaSuccess) {
-            delete L;
+            s->lanes.push_back(L);  // released with the others (no thread yet)
             dgec_server_destroy(s);
             return DGEC_ERR_CUDA;
         }
@@ -279,7 +279,7 @@ dgec_status dgec_server_create(int device, void *d_pool, size_t pool_bytes, int3
         L->nv_dev = a.take<long long>(max_jobs_per_batch);
         size_t fixed = a.off;
         if (fixed >= slice) {
-            delete L;
+            s->lanes.push_back(L);  // released with the others (no thread yet)
             dgec_server_destroy(s);
             return DGEC_ERR_OOM;
         }
@@ -306,7 +306,7 @@ dgec_status dgec_server_create(int device, void *d_pool, size_t pool_bytes, int3
         L->ws_bytes = slice > used ? slice - used : 0;
         if (cudaMemsetAsync(L->flag, 0, sizeof(int) * (vb + 1), L->stream) != cudaSuccess ||
             cudaStreamSynchronize(L->stream) != cudaSuccess) {
-            delete L;
+            s->lanes.push_back(L);  // released with the others (no thread yet)
             dgec_server_destroy(s);
             return DGEC_ERR_CUDA;
         }
