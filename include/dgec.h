@@ -22,7 +22,12 @@
  *   - every call runs on the given CUDA stream and returns once its results
  *     are complete (it synchronises that stream before returning);
  *   - on error the call returns a status != DGEC_OK and a message is kept in
- *     the context (dgec_last_error); outputs are then unspecified.
+ *     the context (dgec_last_error); outputs are then unspecified;
+ *   - a context serves one call at a time (it holds that call's stream,
+ *     message, launch count and timers): threads that share one must
+ *     serialise their calls, or each use its own context, as the server's
+ *     lanes do. The size queries and dgec_status_string are safe from any
+ *     thread; the server calls and dgec_msf_static state their own rules.
  */
 #ifndef DGEC_H
 #define DGEC_H
@@ -86,9 +91,9 @@ typedef struct dgec_ctx dgec_ctx;
 /* Results of dgec_run. Device arrays point into the caller's workspace and
  * stay valid until that workspace is reused. Counts are host values. */
 typedef struct {
-    /* Incidence lists (the adjacency lists Alg. 3 starts from). Vertex v's out-edges are
-     * out_id[out_off[v] .. out_off[v+1]) with times out_t[..], sorted by
-     * (t, id); likewise in-edges via in_off/in_t/in_id. */
+    /* Incidence lists (the adjacency lists Alg. 3 starts from). Vertex v's
+     * out-edges are out_id[out_off[v] .. out_off[v+1]) with times
+     * out_t[..], sorted by (t, id); likewise in-edges via in_off/in_t/in_id. */
     const int64_t *out_off, *in_off;   /* [n_vertices + 1] */
     const int64_t *out_t, *in_t;       /* [n_edges] */
     const int32_t *out_id, *in_id;     /* [n_edges] */
@@ -108,17 +113,17 @@ typedef struct {
      * node has fewer than k neighbours. */
     const int32_t *knn_id;             /* [n_edges * k] */
     const int64_t *core;               /* [n_edges] */
-    /* Alg. 1, forest and its weight order: minimum spanning forest of L*_G under the strict
-     * order (w, u, v), sorted by that order. */
+    /* Alg. 1, forest and its weight order: minimum spanning forest of L*_G
+     * under the strict order (w, u, v), sorted by that order. */
     const int32_t *mst_u, *mst_v;      /* [n_mst] */
     const int64_t *mst_w;
-    /* Alg. 1, union-find dendrogram. Row s merges clusters link_a[s] < link_b[s]
-     * (a leaf id < n_edges, or n_edges + s' for the cluster row s' formed)
-     * at weight mst_w[s]; link_size[s] leaves below it. */
+    /* Alg. 1, union-find dendrogram. Row s merges clusters link_a[s] <
+     * link_b[s] (a leaf id < n_edges, or n_edges + s' for the cluster row s'
+     * formed) at weight mst_w[s]; link_size[s] leaves below it. */
     const int32_t *link_a, *link_b;    /* [n_mst] */
     const int64_t *link_size;
-    /* Alg. 1, condensing and cluster extraction: condensed tree (min cluster size M) and excess of
-     * mass selection. lambda(w) = floor((2^64-1)/(w+1)); lambda 0 at a
+    /* Alg. 1, condensing and cluster extraction: condensed tree (min cluster
+     * size M) and excess of mass selection. lambda(w) = floor((2^64-1)/(w+1)); lambda 0 at a
      * virtual root (id n_edges + n_mst) above the components. Point e
      * leaves cluster fall_cluster[e] at lambda fall_lambda[e]. Clusters,
      * sorted by id (the dendrogram node where each is born): parent id
