@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--dominant", default="k_ranks_knn",
                     help="kernel timed live for the roofline object")
-    ap.add_argument("--cpu-sample-minutes", type=float, default=150.0)
+    ap.add_argument("--cpu-sample-minutes", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch-graphs", type=int, default=128,
@@ -420,15 +420,31 @@ def peaks():
     return 6800.0, "fallback"
 
 
+CPU_SAMPLE_MINUTES = 150.0
+
+
+def reference_sample_minutes(args) -> float:
+    """Window of the reference arm's per-step sample. Unless one is given,
+    it shrinks as warm-up + timed steps grow, so that the whole run stays
+    near two and a half minutes of one core (the oracle's cost grows faster
+    than the window: about 14 s at 150 minutes of the mid stream, 8 s at
+    120)."""
+    if args.cpu_sample_minutes is not None:
+        return args.cpu_sample_minutes
+    n = args.warmup + args.steps
+    return 150.0 if n <= 10 else 120.0 if n <= 20 else 90.0 if n <= 40 else 60.0
+
+
 def run_reference(args, rank, world):
     """The reference arm: the CPU oracle, as it stands, on a bounded sample."""
     if rank != 0:
         return
     w = make_workload(args.workload, args.scale, 0)
+    minutes = reference_sample_minutes(args)
     per_step = []
     info = None
     for i in range(args.warmup + args.steps):
-        info = cpu_baseline(w, args.cpu_sample_minutes)
+        info = cpu_baseline(w, minutes)
         if i >= args.warmup:
             per_step.append(info["value"])
     v = float(np.median(per_step))
@@ -552,7 +568,7 @@ def main():
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             try:
-                cpu = cpu_baseline(w, args.cpu_sample_minutes)
+                cpu = cpu_baseline(w, args.cpu_sample_minutes or CPU_SAMPLE_MINUTES)
             except Exception as ex:  # the baseline is a report, never the product path
                 cpu = {"error": str(ex)}
         line = {"metric": METRIC, "value": job_rate(world, E, ms / 1000.0), "unit": UNIT,

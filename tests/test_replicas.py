@@ -71,3 +71,15 @@ def test_reference_arm_under_torchrun_prints_once():
     lines = [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
     assert len(lines) == 1
     assert lines[0]["impl"] == "reference" and lines[0]["n_gpus"] == 2 and lines[0]["value"] > 0
+
+
+def test_reference_sample_shrinks_with_step_count():
+    """The reference arm keeps its whole run to a few minutes of one core:
+    unless a window is given, more steps take a shorter window each."""
+    import argparse
+    import bench
+    win = [bench.reference_sample_minutes(argparse.Namespace(cpu_sample_minutes=None, steps=s, warmup=3))
+           for s in (5, 10, 20, 50)]
+    assert win == sorted(win, reverse=True) and win[0] == bench.CPU_SAMPLE_MINUTES
+    given = argparse.Namespace(cpu_sample_minutes=42.0, steps=100, warmup=3)
+    assert bench.reference_sample_minutes(given) == 42.0
