@@ -114,3 +114,18 @@ def test_broadcast_messages_have_one_sender():
     assert np.all(np.diff(h.s_off) == 1)
     nr = np.diff(h.d_off)
     assert nr.min() >= 1
+
+
+@pytest.mark.parametrize("make", [lambda: synth.mid(scale=0.002), lambda: synth.hub(scale=0.001)],
+                         ids=["mid", "hub"])
+def test_skeleton_to_edge_ratio_is_plausible(make):
+    """The paper's graphs have 1.78 (Reddit, Sec. 4.2.2) to 1.96 (e-mail,
+    Sec. 4.1.2) skeleton links per edge; the synthetic stand-ins should look
+    alike (about 1.9 at full size), within the bound of Sec. 2: at most
+    sum_i (d_i - 1) = 2E - (vertices with an edge) links."""
+    from oracle import oracle as O
+    w = make()
+    u, _, _ = O.skeleton(w.src, w.dst, w.t, w.n_vertices)
+    deg = np.bincount(w.src, minlength=w.n_vertices) + np.bincount(w.dst, minlength=w.n_vertices)
+    assert len(u) <= 2 * w.n_edges - int(np.sum(deg > 0))
+    assert 1.75 < len(u) / w.n_edges < 2.0
