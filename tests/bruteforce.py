@@ -152,3 +152,130 @@ def hyper_line_graph(h):
                 if r != s and t[r] <= t[s]:
                     out[(min(r, s), max(r, s))] = t[s] - t[r]
     return out
+
+
+def lam(w):
+    """Lambda of a merge at weight w: floor((2^64 - 1) / (w + 1)), exact."""
+    return ((1 << 64) - 1) // (w + 1)
+
+
+def condense_bruteforce(n, edges, M):
+    """Condensed tree, excess-of-mass selection and labels read directly off
+    the filtration comps(H, w) of an explicit graph H (no linkage, no
+    union-find replay): top down from a virtual root at w = inf (lambda 0)
+    whose children are H's components; a node is a component at the
+    smallest weight that connects it, and its children are its parts one
+    distinct weight lower. At a node of lambda L inside cluster K: two or
+    more children of size >= M end K and start one cluster each; exactly one
+    continues K; the points of the other children leave K at L. Stability
+    of K = sum over points leaving K of (L_p - birth) + sum over child
+    clusters of size * (death - birth); EOM bottom up with ties to the
+    parent, root never selected; labels by the selected ancestor, numbered
+    by smallest member. Returns labels, number of clusters, each point's
+    leaving lambda, and the clusters as (birth, death, size, stability,
+    selected) with selected 2 final / 1 covered / 0."""
+    ws = sorted(set(edges.values()))
+    levels = [components(n, edges, w) for w in ws]          # levels[i]: weight <= ws[i]
+
+    def merge_level(S, top):
+        """Smallest level at which the points S form one component."""
+        for i in range(top + 1):
+            if len(set(levels[i][S].tolist())) == 1:
+                return i
+        raise AssertionError("not a component")
+
+    def parts(S, i):
+        """Components of S one distinct weight below ws[i]."""
+        if i == 0:
+            return [[x] for x in S]
+        lab = levels[i - 1][S]
+        out = {}
+        for x, l in zip(S, lab.tolist()):
+            out.setdefault(l, []).append(x)
+        return list(out.values())
+
+    clusters = []            # dicts: birth, death, size, points (leaving), children, members
+    fall = np.zeros(n, dtype=object)
+    fall_of = np.full(n, -1, np.int64)
+
+    def new_cluster(members, birth):
+        clusters.append(dict(birth=birth, death=0, size=len(members), leave=[], children=[],
+                             members=list(members)))
+        return len(clusters) - 1
+
+    def leave(K, pts, L):
+        for p in pts:
+            clusters[K]["leave"].append(L)
+            fall[p] = L
+            fall_of[p] = K
+
+    def split(K, kids, L):
+        """Apply the condensing rule at one node; return (cluster, set) pairs to go on with."""
+        big = [c for c in kids if len(c) >= M]
+        small = [c for c in kids if len(c) < M]
+        for c in small:
+            leave(K, c, L)
+        if len(big) >= 2:
+            clusters[K]["death"] = L
+            todo = []
+            for c in big:
+                C = new_cluster(c, L)
+                clusters[K]["children"].append(C)
+                todo.append((C, sorted(c)))
+            return todo
+        if len(big) == 1:
+            return [(K, sorted(big[0]))]
+        return []
+
+    top = len(ws) - 1
+    root = new_cluster(range(n), 0)
+    if top >= 0:
+        comps = {}
+        for x, l in enumerate(levels[top].tolist()):
+            comps.setdefault(l, []).append(x)
+        kids = list(comps.values())
+    else:
+        kids = [[x] for x in range(n)]
+    todo = split(root, kids, 0)
+    while todo:
+        K, S = todo.pop()
+        i = merge_level(S, top)
+        todo.extend(split(K, parts(S, i), lam(ws[i])))
+
+    stab = []
+    for c in clusters:
+        s = sum(L - c["birth"] for L in c["leave"])
+        s += sum(clusters[ch]["size"] * (c["death"] - c["birth"]) for ch in c["children"])
+        stab.append(s)
+    score = [0] * len(clusters)
+    sel = [0] * len(clusters)
+    for K in range(len(clusters) - 1, -1, -1):          # children are created after parents
+        sumc = sum(score[ch] for ch in clusters[K]["children"])
+        if K != root and stab[K] >= sumc:
+            sel[K] = 1
+            score[K] = stab[K]
+        else:
+            score[K] = sumc
+    parent = {ch: K for K, c in enumerate(clusters) for ch in c["children"]}
+    final = []
+    for K in range(len(clusters)):
+        if sel[K]:
+            a, covered = parent.get(K), False
+            while a is not None:
+                covered |= bool(sel[a])
+                a = parent.get(a)
+            if not covered:
+                sel[K] = 2
+                final.append(K)
+    final.sort(key=lambda K: min(clusters[K]["members"]))
+    number = {K: x for x, K in enumerate(final)}
+    labels = np.full(n, -1, np.int32)
+    for p in range(n):
+        a = int(fall_of[p])
+        while a is not None and a >= 0:
+            if sel[a] == 2:
+                labels[p] = number[a]
+                break
+            a = parent.get(a)
+    table = sorted((c["birth"], c["death"], c["size"], stab[K], sel[K]) for K, c in enumerate(clusters))
+    return labels, len(final), [int(x) for x in fall], table

@@ -62,3 +62,54 @@ def test_oracle_sweep_against_bruteforce():
             _check(g)
         except AssertionError as ex:
             raise AssertionError(f"graph seed {seed} (E={g.n_edges}, V={g.n_vertices}): {ex}") from ex
+
+
+def _medium(seed):
+    rng = np.random.default_rng(50_000 + seed)
+    E = int(rng.integers(100, 301))
+    V = int(rng.integers(10, 31))
+    t_max = int(rng.integers(20, 201))
+    return synth.random_small(E, V, t_max, 20_000 + seed, zipf_s=1.2 if seed % 3 == 0 else 0.0)
+
+
+def test_condense_sweep_against_the_filtration():
+    """Alg. 1's condensing and cluster extraction (the readings of HDBSCAN's
+    condensed tree and excess of mass) against a restatement read directly
+    off the filtration comps(L_G, w): labels, cluster count, every point's
+    leaving lambda, and every cluster's birth, death, size, exact 128-bit
+    stability and selection, for M = 2, 3, 4 and 5, on the small graphs and
+    on 100 larger ones with deeper hierarchies."""
+    graphs = [(_graph(s), 2 + s % 3) for s in range(N_GRAPHS)]
+    graphs += [(_medium(s), 2 + s % 4) for s in range(100)]
+    for seed, (g, M) in enumerate(graphs):
+        full = bf.undirected_edges(g.src, g.dst, g.t)
+        lab, ncl, fall, table = bf.condense_bruteforce(g.n_edges, full, M)
+        c = O.run(g.src, g.dst, g.t, g.n_vertices, 2, M)["condensed"]
+        got = sorted((int(b), int(d), int(s), (int(h) << 64) | int(lo), int(x)) for b, d, s, h, lo, x in
+                     zip(c["cl_birth"], c["cl_death"], c["cl_size"], c["cl_stab_hi"], c["cl_stab_lo"],
+                         c["cl_selected"]))
+        where = f"graph {seed} (E={g.n_edges}, M={M})"
+        assert np.array_equal(c["labels"], lab), where
+        assert c["n_clusters"] == ncl, where
+        assert [int(x) for x in c["fall_lambda"]] == fall, where
+        assert got == table, where
+
+
+def test_condense_tie_goes_to_the_parent():
+    """An exact EOM tie (random graphs never give one): on the graph with
+    links {0,1}, {2,3}, {4,5} at w = 2, {1,2} at 4 and {3,4} at 14, the
+    lambdas are N/3, N/5, N/15 for N = 2^64 - 1 and 2 N/5 = N/3 + N/15, so
+    the cluster {0..3} has exactly its children's summed stability. The
+    oracle's chain and the filtration restatement both keep the parent."""
+    edges = {(0, 1): 2, (2, 3): 2, (4, 5): 2, (1, 2): 4, (3, 4): 14}
+    lab, ncl, _, table = bf.condense_bruteforce(6, edges, 2)
+    u = np.array([a for a, _ in edges], np.int32)
+    v = np.array([b for _, b in edges], np.int32)
+    w = np.array(list(edges.values()), np.int64)
+    mu, mv, mw = O.mst(6, u, v, w)
+    a, b, s = O.linkage(6, mu, mv)
+    c = O.condense(6, a, b, mw, s, 2)
+    assert lab.tolist() == c["labels"].tolist() == [0, 0, 0, 0, 1, 1]
+    assert ncl == c["n_clusters"] == 2
+    selected = sorted(x[4] for x in table)
+    assert selected == [0, 1, 1, 2, 2]                  # root, two covered children, two final
