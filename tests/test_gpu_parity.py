@@ -79,6 +79,17 @@ def test_star_and_chain():
     compare_all(src, dst, t, m + 1, 4, 5)
 
 
+def test_exact_eom_tie_goes_to_the_parent():
+    """A relay chain at t = 0, 2, 6, 8, 22, 24 has the skeleton path with
+    weights 2, 4, 2, 14, 2: lambdas N/3, N/5, N/15 (N = 2^64 - 1) with
+    2 N/5 = N/3 + N/15, so the cluster of the first four edges has exactly
+    its children's summed stability; EOM keeps the parent."""
+    src = np.arange(6, dtype=np.int32)
+    g, _ = compare_all(src, src + 1, np.array([0, 2, 6, 8, 22, 24], np.int64), 7, 1, 2)
+    assert g["labels"].tolist() == [0, 0, 0, 0, 1, 1]
+    assert sorted(g["cl_selected"].tolist()) == [0, 1, 1, 2, 2]
+
+
 def test_large_timestamps_and_negative():
     w = synth.random_small(2000, 50, 1000, 9)
     compare_all(w.src, w.dst, w.t * 1_000_003 - 10**12, w.n_vertices, 4, 3)
