@@ -113,3 +113,33 @@ def test_condense_tie_goes_to_the_parent():
     assert ncl == c["n_clusters"] == 2
     selected = sorted(x[4] for x in table)
     assert selected == [0, 1, 1, 2, 2]                  # root, two covered children, two final
+
+
+def test_discrete_condense_sweep_against_the_filtration():
+    """Alg. 5 and condensing on D: with thresholds omega, D's levels are the
+    filtration of L_G with every weight rounded up to the next threshold
+    (links above the last one never join). The oracle's levels on L* and
+    its condensing on D equal the restatement on that rounded explicit L_G:
+    labels, cluster count and every cluster's birth, death, size, stability
+    and selection."""
+    omegas = [[0], [1, 4, 16, 64], [0, 2, 9], [0, 1, 2, 3, 5, 8, 13, 21], [2 ** i for i in range(29)]]
+    for seed in range(0, N_GRAPHS, 4):
+        g = _graph(seed)
+        E, M = g.n_edges, 2 + seed % 3
+        om = np.array(omegas[seed % len(omegas)], np.int64)
+        full = bf.undirected_edges(g.src, g.dst, g.t)
+        rounded = {}
+        for key, x in full.items():
+            i = int(np.searchsorted(om, x, side="left"))         # first threshold >= x
+            if i < len(om):
+                rounded[key] = int(om[i])
+        lab, ncl, _, table = bf.condense_bruteforce(E, rounded, M)
+        u, v, w = O.skeleton(g.src, g.dst, g.t, g.n_vertices)
+        d = O.condense_levels(O.levels(E, u, v, w, om), om, M)
+        got = sorted((int(b), int(dd), int(s), (int(h) << 64) | int(lo), int(x)) for b, dd, s, h, lo, x in
+                     zip(d["cl_birth"], d["cl_death"], d["cl_size"], d["cl_stab_hi"], d["cl_stab_lo"],
+                         d["cl_selected"]))
+        where = f"graph seed {seed} (E={E}, M={M}, omega={om.tolist()})"
+        assert np.array_equal(d["labels"], lab), where
+        assert d["n_clusters"] == ncl, where
+        assert got == table, where
