@@ -143,3 +143,44 @@ def test_discrete_condense_sweep_against_the_filtration():
         assert np.array_equal(d["labels"], lab), where
         assert d["n_clusters"] == ncl, where
         assert got == table, where
+
+
+def _same_condensed(c, ref, where):
+    lab, ncl, fall, table = ref
+    got = sorted((int(b), int(d), int(s), (int(h) << 64) | int(lo), int(x)) for b, d, s, h, lo, x in
+                 zip(c["cl_birth"], c["cl_death"], c["cl_size"], c["cl_stab_hi"], c["cl_stab_lo"],
+                     c["cl_selected"]))
+    assert np.array_equal(c["labels"], lab), where
+    assert c["n_clusters"] == ncl, where
+    assert [int(x) for x in c["fall_lambda"]] == fall, where
+    assert got == table, where
+
+
+def test_variant_clusters_against_the_filtration():
+    """The variants end to end against the restatement on their explicit
+    line graphs: the time cutoff (only arcs with w <= delta, Sec. 4.3), the
+    nearly-causal line graph (arcs back in time by at most delta, weighed
+    |dt|, Sec. 4.3) and dynamic hypergraphs, undirected and directed
+    (Sec. 4.4): labels, leaving lambdas and every cluster's birth, death,
+    size, stability and selection."""
+    for seed in range(0, N_GRAPHS, 5):
+        g = _graph(seed)
+        E, M = g.n_edges, 2 + seed % 3
+        full = bf.undirected_edges(g.src, g.dst, g.t)
+        delta = seed % 6
+        cut = {key: x for key, x in full.items() if x <= delta}
+        c = O.run(g.src, g.dst, g.t, g.n_vertices, 2, M, delta_max=delta)["condensed"]
+        _same_condensed(c, bf.condense_bruteforce(E, cut, M), f"cutoff, graph seed {seed}, delta {delta}")
+        dnc = 1 + seed % 4
+        nc = bf.undirected_edges_nc(g.src, g.dst, g.t, dnc)
+        c = O.run_nearly_causal(g.src, g.dst, g.t, g.n_vertices, 2, M, dnc)["condensed"]
+        _same_condensed(c, bf.condense_bruteforce(E, nc, M), f"nearly causal, graph seed {seed}, delta {dnc}")
+    for seed in range(200):
+        rng = np.random.default_rng(70_000 + seed)
+        mm = int(rng.integers(1, 5))                              # members per hyperedge, at most
+        h = synth.hyper_small(int(rng.integers(1, 31)), int(rng.integers(2 * mm + 2, 2 * mm + 9)),
+                              int(rng.integers(1, 13)), 30_000 + seed, directed=seed % 2 == 0, max_members=mm)
+        M = 2 + seed % 3
+        c = O.hyper_run(h.t, h.n_vertices, h.s_off, h.s_vert, h.d_off, h.d_vert, M)["condensed"]
+        _same_condensed(c, bf.condense_bruteforce(h.n_edges, bf.hyper_line_graph(h), M),
+                        f"hypergraph seed {seed}, directed {h.directed}")
