@@ -198,6 +198,30 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def tiny_latency(ctx, runs):
+    """Latency of one whole pass on the 20,000-edge tiny graph, which sits in
+    L2 and is bound by launches and host round trips rather than bandwidth:
+    CUDA events around each call on the launching stream, after a warm-up."""
+    import torch
+    from paper_2311_10337_gb300 import synth
+    w = synth.tiny()
+    s, d, t = (torch.from_numpy(x).cuda() for x in (w.src, w.dst, w.t))
+    stream = torch.cuda.current_stream()
+    ctx.run(s, d, t, w.n_vertices, w.k, w.min_cluster_size)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(runs):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.run(s, d, t, w.n_vertices, w.k, w.min_cluster_size)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return {"edges": w.n_edges, "k": w.k, "runs": runs, "latency_ms_p50": float(np.median(ms)),
+            "latency_ms_min": float(np.min(ms)), "launches": ctx.launches()}
+
+
 def batched_vs_plain(ctx, n_graphs, steps):
     """Aggregate edges/s of one batched run over n_graphs independent graphs
     (the batching workload's distribution) against one run per graph, on
@@ -529,6 +553,12 @@ def main():
         e2e_s = max_over_ranks(e2e_s, world, "cuda")
         e2e = {"value": job_rate(world, E, e2e_s), "unit": UNIT, "h2d_bytes_per_step": 16 * E,
                "d2h_bytes_per_step": 4 * E}
+    tiny = None
+    if rank == 0:
+        try:
+            tiny = tiny_latency(ctx, max(10, args.steps))
+        except Exception as ex:  # a side report: never costs the main line
+            tiny = {"error": str(ex)[:200]}
     levels = None
     if not args.no_levels and rank == 0:
         levels = discrete_levels(ctx, src, dst, tt, w, max(1, min(args.steps, 3)), args.breakdown)
@@ -579,7 +609,7 @@ def main():
                            "edges_per_gpu": E, "parallelism": "replicas only",
                            "l2": "inputs (16 B/edge = %.0f MB) exceed L2; no flush" % (16 * E / 1e6),
                            "n_clusters": n_clusters},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "discrete_dendrogram": levels, "hypergraph": hyper,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "tiny": tiny, "discrete_dendrogram": levels, "hypergraph": hyper,
                 "mutual_reachability": mrd, "nearly_causal": nearly,
                 "batch": batch, "serve": serve,
                 "gpu_launches": launches * args.steps, "clocks": clk}
