@@ -184,3 +184,28 @@ def test_variant_clusters_against_the_filtration():
         c = O.hyper_run(h.t, h.n_vertices, h.s_off, h.s_vert, h.d_off, h.d_vert, M)["condensed"]
         _same_condensed(c, bf.condense_bruteforce(h.n_edges, bf.hyper_line_graph(h), M),
                         f"hypergraph seed {seed}, directed {h.directed}")
+
+
+def test_mutual_reachability_clusters_against_the_filtration():
+    """The mutual-reachability mode end to end (an approximation; reading
+    R-19): H = L* together with every node's kNN pairs taken by brute force
+    from the explicit L_G, each pair once, weighed max(core_a, core_b, |dt|)
+    with brute-force core distances, pairs with an infinite core dropped;
+    the oracle's clusters equal the restatement's on that H, k = 1, 2, 3."""
+    for seed in range(0, N_GRAPHS, 7):
+        g = _graph(seed)
+        E, M, k = g.n_edges, 2 + seed % 3, 1 + seed % 3
+        u, v, _ = O.skeleton(g.src, g.dst, g.t, g.n_vertices)
+        ids, core = bf.knn_bruteforce(g.src, g.dst, g.t, k)
+        pairs = set(zip(u.tolist(), v.tolist()))
+        for e in range(E):
+            for nb in ids[e].tolist():
+                if nb >= 0:
+                    pairs.add((min(e, nb), max(e, nb)))
+        H = {}
+        for a, b in pairs:
+            x = max(int(core[a]), int(core[b]), abs(int(g.t[a]) - int(g.t[b])))
+            if x != INF:
+                H[(a, b)] = x
+        c = O.mrd_run(g.src, g.dst, g.t, g.n_vertices, k, M)["condensed"]
+        _same_condensed(c, bf.condense_bruteforce(E, H, M), f"mutual reachability, graph seed {seed}, k {k}")
