@@ -16,6 +16,8 @@ here: the SNAP e-mail network (Sec. 4.1) and the Reddit comment graph
 from __future__ import annotations
 
 import dataclasses
+import os
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -27,7 +29,7 @@ _M2 = np.uint64(0x94D049BB133111EB)
 BASE_SEED = 0x231110337
 
 
-def _mix(z: np.ndarray) -> np.ndarray:
+def _mix_serial(z: np.ndarray) -> np.ndarray:
     z = z.astype(np.uint64, copy=True)
     with np.errstate(over="ignore"):
         z ^= z >> np.uint64(30)
@@ -36,6 +38,48 @@ def _mix(z: np.ndarray) -> np.ndarray:
         z *= _M2
         z ^= z >> np.uint64(31)
     return z
+
+
+_CHUNK = 1 << 22
+
+
+def _mix(z: np.ndarray) -> np.ndarray:
+    """splitmix64's finaliser, elementwise (large arrays in parallel chunks;
+    the result does not depend on the chunking)."""
+    z = np.asarray(z)
+    if z.size <= 2 * _CHUNK:
+        return _mix_serial(z)
+    out = np.empty(z.shape, np.uint64)
+
+    def one(a):
+        out[a:a + _CHUNK] = _mix_serial(z[a:a + _CHUNK])
+
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        list(ex.map(one, range(0, z.size, _CHUNK)))
+    return out
+
+
+def _argsort_u64(h: np.ndarray) -> np.ndarray:
+    """Stable argsort of uint64 keys (equal to np.argsort(h, kind="stable")),
+    through torch's multi-threaded CPU sort: flipping the top bit maps the
+    unsigned order onto the signed one."""
+    import torch
+    k = (np.asarray(h, np.uint64) ^ np.uint64(1 << 63)).view(np.int64)
+    return torch.sort(torch.from_numpy(k), stable=True).indices.numpy()
+
+
+def _argsort_i64(k: np.ndarray) -> np.ndarray:
+    """Stable argsort of int64 keys (equal to np.argsort(k, kind="stable"))."""
+    import torch
+    return torch.sort(torch.from_numpy(np.ascontiguousarray(k, np.int64)), stable=True).indices.numpy()
+
+
+def _searchsorted_right(cdf: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """np.searchsorted(cdf, u, side="right") for float64 arrays, multi-threaded."""
+    import torch
+    return torch.searchsorted(torch.from_numpy(np.ascontiguousarray(cdf, np.float64)),
+                              torch.from_numpy(np.ascontiguousarray(u, np.float64)),
+                              right=True).numpy()
 
 
 class Stream:
@@ -88,13 +132,13 @@ def _zipf_ranks(st: Stream, n: int, n_vertices: int, s: float) -> np.ndarray:
     cdf = np.cumsum(r ** (-s))
     cdf /= cdf[-1]
     u = st.uniform(n)
-    idx = np.searchsorted(cdf, u, side="right")
+    idx = _searchsorted_right(cdf, u)
     return np.minimum(idx, n_vertices - 1).astype(np.int64)
 
 
 def _permutation(st: Stream, n: int) -> np.ndarray:
     """Seeded random permutation (argsort of fresh 64-bit draws)."""
-    return np.argsort(st.u64(n), kind="stable").astype(np.int64)
+    return _argsort_u64(st.u64(n)).astype(np.int64)
 
 
 def _zipf_endpoints(st: Stream, n: int, n_vertices: int, s: float,
@@ -116,25 +160,24 @@ def _zipf_endpoints(st: Stream, n: int, n_vertices: int, s: float,
 def _dedupe_triples(src, dst, t):
     """Make every (i, j, t) triple unique (Sec. 1.2.1): within each (i, j)
     pair that has a repeat, times are made strictly increasing by moving a
-    repeat to one second after its predecessor. Pairs with repeats are found
-    by sorting a 64-bit hash of the triple and checking candidates exactly."""
-    pair = (src.astype(np.uint64) << np.uint64(32)) | dst.astype(np.uint64)
-    with np.errstate(over="ignore"):
-        h = _mix(pair) ^ _mix(t.astype(np.uint64) * _GOLD + _M1)
-    order = np.argsort(h, kind="stable")
-    hs = h[order]
-    cand = np.nonzero(hs[1:] == hs[:-1])[0]
-    if cand.size == 0:
-        return t
-    a, b = order[cand], order[cand + 1]
-    same = (src[a] == src[b]) & (dst[a] == dst[b]) & (t[a] == t[b])
-    if not same.any():
-        return t
-    idx = np.nonzero(np.isin(pair, np.unique(pair[b[same]])))[0]
-    o = idx[np.lexsort((idx, t[idx], pair[idx]))]
+    repeat to one second after its predecessor. The edges are ordered by
+    (pair, t, position) with two stable sorts; a pair has a repeat when two
+    neighbours in that order share (pair, t)."""
+    pair = ((src.astype(np.uint64) << np.uint64(32)) | dst.astype(np.uint64)).view(np.int64)
+    by_t = _argsort_i64(t)
+    o = by_t[_argsort_i64(pair[by_t])]
     pk, tt = pair[o], t[o]
+    rep = (pk[1:] == pk[:-1]) & (tt[1:] == tt[:-1])
+    if not rep.any():
+        return t
     head = np.ones(len(o), bool)
     head[1:] = pk[1:] != pk[:-1]
+    gid_all = np.cumsum(head) - 1
+    bad = np.zeros(int(gid_all[-1]) + 1, bool)
+    bad[gid_all[1:][rep]] = True
+    sel = bad[gid_all]
+    o, pk, tt = o[sel], pk[sel], tt[sel]
+    head = head[sel]
     gid = np.cumsum(head) - 1
     start = np.nonzero(head)[0]
     r = np.arange(len(o)) - start[gid]
@@ -350,7 +393,7 @@ def batch(n_graphs: int = 4096, log10_min: float = 3.0, log10_max: float = 6.0,
 
     def draw(stream):
         u = stream.uniform(total) * cap[gid]
-        return np.minimum(np.searchsorted(cdf, u, side="right"), nv[gid] - 1).astype(np.int64)
+        return np.minimum(_searchsorted_right(cdf, u), nv[gid] - 1).astype(np.int64)
 
     s_src, s_dst = Stream(seed, 42), Stream(seed, 43)
     src = draw(s_src)
@@ -360,7 +403,7 @@ def batch(n_graphs: int = 4096, log10_min: float = 3.0, log10_max: float = 6.0,
         if bad.size == 0:
             break
         u = s_dst.uniform(bad.size) * cap[gid[bad]]
-        dst[bad] = np.minimum(np.searchsorted(cdf, u, side="right"), nv[gid[bad]] - 1)
+        dst[bad] = np.minimum(_searchsorted_right(cdf, u), nv[gid[bad]] - 1)
     bad = np.nonzero(src == dst)[0]
     dst[bad] = (src[bad] + 1) % nv[gid[bad]]
     t = Stream(seed, 44).integers(0, t_max, total)
