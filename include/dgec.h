@@ -302,7 +302,8 @@ dgec_status dgec_kernel_timing(dgec_ctx *ctx, int i, const char **name, double *
  * size to *h_n_mst. Runs on cuda_stream of the current device and
  * synchronises it before returning.
  * Limits: n_nodes <= 262,144 and n_edges <= 524,288, else
- * DGEC_ERR_TOO_LARGE; a bad id or u >= v gives DGEC_ERR_INVALID_ARG.
+ * DGEC_ERR_TOO_LARGE; a bad id, u >= v or w < 0 gives
+ * DGEC_ERR_INVALID_ARG (nothing is written to the outputs then).
  * The first call on a device looks up the array's device address; make it
  * before any stream capture. Every call reuses the same array (each call
  * re-initialises what must start from a known value), so calls that

@@ -62,13 +62,14 @@ constexpr size_t kStaticBytes = kOffCnt + al(4 * 8);  // about 22 MB
 static __device__ __align__(256) unsigned char g_msf_scratch[kStaticBytes];
 
 // Checks the caller's edge list: counter[0] += edges with an id out of
-// range or with u >= v.
-__global__ void k_static_check(const int32_t *u, const int32_t *v, int64_t n, int64_t n_nodes,
-                               unsigned long long *bad) {
+// range, with u >= v, or with a negative weight (weights are compared as
+// unsigned in the bids, so w < 0 would sort after every valid weight).
+__global__ void k_static_check(const int32_t *u, const int32_t *v, const int64_t *w, int64_t n,
+                               int64_t n_nodes, unsigned long long *bad) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
         int a = u[x], b = v[x];
-        if (a < 0 || b >= n_nodes || a >= b) atomicAdd(bad, 1ull);
+        if (a < 0 || b >= n_nodes || a >= b || w[x] < 0) atomicAdd(bad, 1ull);
     }
 }
 
@@ -125,7 +126,7 @@ extern "C" dgec_status dgec_msf_static(const int32_t *d_u, const int32_t *d_v, c
     unsigned long long *cnt = (unsigned long long *)(base + kOffCnt);  // [0] live/bad, [1] out
     // clear what must start from a known value: counters, labels, best slots
     if (cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned long long), st) != cudaSuccess) return DGEC_ERR_CUDA;
-    k_static_check<<<grid_for(n_edges), kBlock, 0, st>>>(d_u, d_v, n_edges, n_nodes, cnt);
+    k_static_check<<<grid_for(n_edges), kBlock, 0, st>>>(d_u, d_v, d_w, n_edges, n_nodes, cnt);
     if (cudaGetLastError() != cudaSuccess) return DGEC_ERR_CUDA;
     unsigned long long bad = 0;
     if ((s = read_u64(st, cnt, &bad)) != DGEC_OK) return s;

@@ -171,19 +171,35 @@ def load(path: str = LIB_PATH):
 
 def msf_static(u, v, w, n_nodes: int, out_u, out_v, out_w, stream=None) -> int:
     """Minimum spanning forest through the allocation-free entry point: the
-    caller's device tensors in (u < v, int32; w int64) and out (capacity
-    n_nodes - 1); the library uses only its fixed internal array. Returns
-    the number of forest edges written."""
+    caller's device tensors in (u < v, int32; w >= 0, int64; all of one
+    length) and out (int32, int32, int64, each with room for n_nodes - 1
+    edges), all on one device; the library uses only its fixed internal
+    array. Runs on `stream` (default: that device's current stream).
+    Returns the number of forest edges written."""
     import torch
     L = load()
-    st = stream if stream is not None else torch.cuda.current_stream()
-    n = ctypes.c_int64(0)
-    rc = L.dgec_msf_static(u.data_ptr(), v.data_ptr(), w.data_ptr(), int(u.shape[0]), n_nodes,
-                           out_u.data_ptr(), out_v.data_ptr(), out_w.data_ptr(), ctypes.byref(n),
-                           st.cuda_stream)
+    if not hasattr(u, "is_cuda") or not u.is_cuda:
+        raise ValueError("u must be a CUDA tensor")
+    dev = u.device.index
+    n = int(u.shape[0]) if u.dim() == 1 else -1
+    _dev("u", u, torch.int32, n, dev)
+    _dev("v", v, torch.int32, n, dev)
+    _dev("w", w, torch.int64, n, dev)
+    need = max(int(n_nodes) - 1, 0)
+    for name, x, dt in (("out_u", out_u, torch.int32), ("out_v", out_v, torch.int32),
+                        ("out_w", out_w, torch.int64)):
+        _dev(name, x, dt, None, dev)
+        if int(x.shape[0]) < need:
+            raise ValueError(f"{name} has {int(x.shape[0])} elements, needs at least {need}")
+    with torch.cuda.device(dev):
+        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        m = ctypes.c_int64(0)
+        rc = L.dgec_msf_static(u.data_ptr(), v.data_ptr(), w.data_ptr(), n, int(n_nodes),
+                               out_u.data_ptr(), out_v.data_ptr(), out_w.data_ptr(), ctypes.byref(m),
+                               st.cuda_stream)
     if rc != DGEC_OK:
         raise DgecError(rc, L.dgec_status_string(rc).decode())
-    return int(n.value)
+    return int(m.value)
 
 
 def workspace_size(n_edges: int, n_vertices: int, k: int, min_cluster_size: int, mrd: bool = False,

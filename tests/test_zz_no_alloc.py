@@ -47,6 +47,66 @@ def test_static_forest_matches_pipeline_twice():
             assert np.array_equal(a, b)
 
 
+def _pipeline_forest(wl, delta_max=None):
+    """The pipeline's skeleton (copied out of its workspace) and forest."""
+    import torch
+    c = ctx()
+    src = torch.from_numpy(wl.src).cuda()
+    dst = torch.from_numpy(wl.dst).cuda()
+    t = torch.from_numpy(wl.t).cuda()
+    out = c.run(src, dst, t, wl.n_vertices, wl.k, wl.min_cluster_size, delta_max=delta_max)
+    sk = (out.tensor("sk_u").clone(), out.tensor("sk_v").clone(), out.tensor("sk_w").clone())
+    ref = (out.numpy("mst_u"), out.numpy("mst_v"), out.numpy("mst_w"))
+    return sk, ref
+
+
+def _static(sk, n_nodes):
+    import torch
+    mu = torch.full((n_nodes,), -7, dtype=torch.int32, device="cuda")
+    mv = torch.full((n_nodes,), -7, dtype=torch.int32, device="cuda")
+    mw = torch.full((n_nodes,), -7, dtype=torch.int64, device="cuda")
+    n = dgec.msf_static(*sk, n_nodes, mu, mv, mw)
+    torch.cuda.synchronize()
+    return _sorted(mu[:n].cpu().numpy(), mv[:n].cpu().numpy(), mw[:n].cpu().numpy())
+
+
+def test_static_forest_larger_then_smaller_and_disconnected():
+    """A larger call leaves its contents in the shared array; a smaller call
+    after it must not see them. The smaller graph runs with a time cutoff, so
+    its skeleton is disconnected and the forest has many trees."""
+    big = synth.mid(scale=0.002)                       # 100,000 edges
+    small = synth.tiny(seed_offset=5)                  # 20,000 edges
+    sk_big, ref_big = _pipeline_forest(big)
+    sk_small, ref_small = _pipeline_forest(small, delta_max=2_000)
+    assert len(ref_small[0]) < small.n_edges - 100     # many trees
+    for sk, ref, E in ((sk_big, ref_big, big.n_edges), (sk_small, ref_small, small.n_edges),
+                       (sk_big, ref_big, big.n_edges)):
+        got = _static(sk, E)
+        assert len(got[0]) == len(ref[0])
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("case", ["u_ge_v", "id_out_of_range", "negative_w"])
+def test_static_forest_rejects_bad_edges(case):
+    import torch
+    u = torch.tensor([0, 1, 2], dtype=torch.int32, device="cuda")
+    v = torch.tensor([1, 2, 3], dtype=torch.int32, device="cuda")
+    w = torch.tensor([5, 6, 7], dtype=torch.int64, device="cuda")
+    n_nodes = 4
+    if case == "u_ge_v":
+        u[1], v[1] = 2, 1
+    elif case == "id_out_of_range":
+        n_nodes = 3
+    else:
+        w[2] = -1
+    out32 = torch.zeros(4, dtype=torch.int32, device="cuda")
+    out64 = torch.zeros(4, dtype=torch.int64, device="cuda")
+    with pytest.raises(dgec.DgecError) as ei:
+        dgec.msf_static(u, v, w, n_nodes, out32, out32.clone(), out64)
+    assert ei.value.status == 1                        # DGEC_ERR_INVALID_ARG
+
+
 def test_static_forest_rejects_oversize():
     import torch
     z32 = torch.zeros(4, dtype=torch.int32, device="cuda")
