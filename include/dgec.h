@@ -272,6 +272,15 @@ int64_t dgec_server_lane_capacity(const dgec_server *srv);
  * pool is untouched. Jobs still queued complete with DGEC_ERR_INVALID_ARG. */
 dgec_status dgec_server_destroy(dgec_server *srv);
 
+/* Device time of each pipeline stage of the last completed call on ctx
+ * (dgec_run, dgec_run_host, dgec_run_batch, dgec_run_levels,
+ * dgec_run_hyper), from CUDA events recorded on the call's stream at the
+ * stage boundaries: the i-th stage's name (static string, e.g. "A incidence
+ * lists", "B skeleton and kNN", "C spanning forest", "D1 dendrogram",
+ * "D2 condense and labels") and its milliseconds. Returns
+ * DGEC_ERR_INVALID_ARG when i is past the last stage. */
+dgec_status dgec_stage_timing(const dgec_ctx *ctx, int i, const char **name, double *ms);
+
 /* Number of kernel launches the last dgec_run on ctx issued (for reporting). */
 int64_t dgec_last_launch_count(const dgec_ctx *ctx);
 

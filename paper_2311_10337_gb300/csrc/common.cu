@@ -70,4 +70,32 @@ void kt_collect(Ctx *c) {
     k->used = 0;
 }
 
+void stage_start(Ctx *c) {
+    StageTimer &t = c->stages;
+    t.n = 0;
+    if (!t.ev[0] && cudaEventCreate(&t.ev[0]) != cudaSuccess) return;
+    cudaEventRecord(t.ev[0], c->stream);
+}
+
+void stage_mark(Ctx *c, const char *name) {
+    StageTimer &t = c->stages;
+    if (!t.ev[0] || t.n >= kMaxStages) return;
+    if (!t.ev[t.n + 1] && cudaEventCreate(&t.ev[t.n + 1]) != cudaSuccess) return;
+    cudaEventRecord(t.ev[t.n + 1], c->stream);
+    t.name[t.n] = name;
+    t.n++;
+}
+
+// Per-stage milliseconds from consecutive events (synchronises on the last).
+void stage_collect(Ctx *c) {
+    StageTimer &t = c->stages;
+    if (t.n == 0) return;
+    cudaEventSynchronize(t.ev[t.n]);
+    for (int i = 0; i < t.n; i++) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, t.ev[i], t.ev[i + 1]);
+        t.ms[i] = ms;
+    }
+}
+
 }  // namespace dgec

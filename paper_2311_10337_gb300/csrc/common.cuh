@@ -33,6 +33,16 @@ struct KernelTimer {
     long long count[kMaxNames];
 };
 
+// CUDA events at the boundaries of the pipeline stages of the last call
+// (always on: a handful of events per call).
+constexpr int kMaxStages = 16;
+struct StageTimer {
+    cudaEvent_t ev[kMaxStages + 1] = {};
+    const char *name[kMaxStages] = {};
+    float ms[kMaxStages] = {};
+    int n = 0;
+};
+
 struct Ctx {
     int device = 0;
     int num_sms = 152;
@@ -41,7 +51,12 @@ struct Ctx {
     int64_t *h_pinned = nullptr;    // small pinned buffer for counter reads
     cudaStream_t stream = nullptr;
     KernelTimer *kt = nullptr;
+    StageTimer stages;
 };
+
+void stage_start(Ctx *c);
+void stage_mark(Ctx *c, const char *name);
+void stage_collect(Ctx *c);
 
 int kt_begin(Ctx *c, const char *name);
 void kt_end(Ctx *c, int slot);
@@ -58,6 +73,8 @@ dgec_status set_err(Ctx *c, dgec_status s, const char *fmt, ...);
 // A named range over one pipeline stage on the host timeline (NVTX), for
 // profilers that record NVTX ranges; nothing is recorded when none is
 // attached. The range closes on every exit, the error returns included.
+// A completed stage also records a CUDA event on the call's stream, so the
+// device time of every stage of the last call can be read back.
 struct StageRange {
     explicit StageRange(const char *name) { nvtxRangePushA(name); }
     ~StageRange() { nvtxRangePop(); }
@@ -69,6 +86,7 @@ struct StageRange {
     do {                            \
         StageRange _range(name);    \
         DG_TRY(expr);               \
+        ::dgec::stage_mark(c, name); \
     } while (0)
 
 #define CU_TRY(c, expr)                                                          \

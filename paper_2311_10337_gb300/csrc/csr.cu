@@ -1,16 +1,28 @@
 // Stage A: incidence lists (the adjacency lists Alg. 3 starts from) with
 // every vertex's in-list and out-list sorted by time as Alg. 2 needs them
-// (ties by edge id).
+// (ties by edge id), and the two merge ranks Alg. 2's sweep depends on.
 //
 // First a device-wide radix sort of the 64-bit keys ((t - t_min) << idbits
 // | id) ranks all edges in (t, id) order. The keys are laid out in id order
 // and the LSD sort is stable, so only the time bits need passes: equal
 // times keep id order. That rank r is the internal node id of every later
-// stage, and per-vertex lists sorted by (t, id) are just lists sorted by r.
-// With the edges in r order, the keys (vertex << idbits) | r sorted stably
-// over the vertex bits alone give every vertex's list in r order, for the
-// out-lists (by src) and the in-lists (by dst); the list offsets are the run
-// boundaries of the sorted keys. No atomics and no per-segment sorts.
+// stage. (When the time span and the ids do not fit one 64-bit key, the
+// time alone is the key and the id rides along as the sort's value: the
+// same order, one more word per pass.)
+//
+// Then every edge contributes two incidence items: an in-item at its head
+// and an out-item at its tail. Laid out in the order (t, in-before-out, r)
+// -- the order Alg. 2 sweeps a vertex's merged list in, in-edges first at
+// equal times -- and sorted stably over the vertex bits alone, the items
+// form every vertex's merged list. From it, by positions alone and with no
+// search:
+//   - the out-list (in-list) of v is the sequence of out-items (in-items)
+//     of v's segment, already in (t, id) order;
+//   - b of an out-item q = the in-items before it in the segment
+//     = #{in-edges p of v : t_p <= t_q};
+//   - a of an in-item p = the out-items before it in the segment
+//     = #{out-edges q of v : t_q < t_p}.
+// No atomics and no per-segment sorts, so hub vertices cost nothing extra.
 //
 // The segment sort below (bins by length: one warp for 2..32 keys, one CTA
 // for 33..2048, hubs through the radix sort keyed (segment, key)) serves the
@@ -126,6 +138,111 @@ __global__ void k_rank_init(const unsigned long long *ks, int64_t E, long long t
         int32_t vo = G > 1 ? (int32_t)voff[egraph[e]] : 0;  // one graph: no random lookup
         isrc[r] = src[e] + vo;
         idst[r] = dst[e] + vo;
+    }
+}
+
+// the same from a (t - tmin) key sorted with the edge id as its value
+__global__ void k_rank_init_kv(const unsigned long long *ks, const unsigned long long *vs, int64_t E,
+                               long long tmin, const int32_t *src, const int32_t *dst,
+                               const int32_t *egraph, const int64_t *voff, int G, int32_t *orig_of,
+                               int32_t *rank_of, int32_t *isrc, int32_t *idst, int64_t *it) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < E;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int32_t e = (int32_t)vs[r];
+        orig_of[r] = e;
+        rank_of[e] = (int32_t)r;
+        it[r] = (int64_t)(long long)(ks[r] + (unsigned long long)tmin);
+        int32_t vo = G > 1 ? (int32_t)voff[egraph[e]] : 0;
+        isrc[r] = src[e] + vo;
+        idst[r] = dst[e] + vo;
+    }
+}
+
+__global__ void k_pack_t(const int64_t *t, int64_t E, long long tmin, unsigned long long *k,
+                         unsigned long long *v) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        k[e] = (unsigned long long)t[e] - (unsigned long long)tmin;
+        v[e] = (unsigned long long)e;
+    }
+}
+
+// Time groups of the (t, id) order: flag[r] = 1 where a new time starts.
+__global__ void k_thead(const int64_t *it, int64_t E, int *flag) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= E;
+         r += (int64_t)gridDim.x * blockDim.x)
+        flag[r] = r < E && (r == 0 || it[r] != it[r - 1]);
+}
+// gstart[g] = first r of time group g; gstart[#groups] = E
+__global__ void k_tgstart(const int *flag, const long long *gpos, int64_t E, int32_t *gstart) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= E;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        if (r == E) gstart[gpos[E]] = (int32_t)E;
+        else if (flag[r]) gstart[gpos[r]] = (int32_t)r;
+    }
+}
+// Incidence items in the order (t, in-before-out, r): time group [gs, ge)
+// puts its in-items at 2 gs + (r - gs) and its out-items after them.
+// key = (vertex << cb) | (2 r + dir), dir 0 = in-item (at dst), 1 = out-item.
+__global__ void k_mkeys(const int32_t *isrc, const int32_t *idst, const int *flag, const long long *gpos,
+                        const int32_t *gstart, int64_t E, int cb, unsigned long long *key) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < E;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const long long g = gpos[r] + flag[r] - 1;
+        const int64_t gs = gstart[g], ge = gstart[g + 1];
+        const unsigned long long code = 2ull * (unsigned long long)r;
+        key[r + gs] = ((unsigned long long)(unsigned)idst[r] << cb) | code;
+        key[r + ge] = ((unsigned long long)(unsigned)isrc[r] << cb) | (code | 1ull);
+    }
+}
+// out_off[v] = out-items before v's segment; in_off[v] = in-items before it
+__global__ void k_moff_split(const int64_t *moff, const int32_t *oidx, int64_t V, int64_t *out_off,
+                             int64_t *in_off) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= V;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = moff[v];
+        const int64_t o = oidx[m];
+        out_off[v] = o;
+        in_off[v] = m - o;
+    }
+}
+// Every item of the merged lists goes to its slot in the out- or in-list
+// arrays; its rank in the other list is its position difference.
+__global__ void k_munpack(const unsigned long long *key, int64_t n2, int cb, const int64_t *moff,
+                          const int32_t *oidx, const int64_t *out_off, const int32_t *orig_of,
+                          const int64_t *it, int64_t *out_t, int32_t *out_id, int32_t *out_r,
+                          int32_t *slot_out, int32_t *pos_out, int64_t *in_t, int32_t *in_id,
+                          int32_t *in_r, int32_t *pos_in, unsigned char *in_head, int32_t *brank,
+                          int32_t *arank) {
+    const unsigned long long cmask = (1ull << cb) - 1ull;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n2;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long k = key[x];
+        const int64_t v = (int64_t)(k >> cb);
+        const unsigned long long code = k & cmask;
+        const int32_t r = (int32_t)(code >> 1);
+        const int64_t ob = oidx[x];              // out-items before x
+        const int64_t seg = x - moff[v];         // position in v's merged list
+        const int64_t obv = ob - out_off[v];     // out-items before x within v's list
+        const int32_t e = orig_of[r];
+        const int64_t tt = it[r];
+        if (code & 1ull) {
+            const int64_t slot = ob;
+            out_t[slot] = tt;
+            out_id[slot] = e;
+            out_r[slot] = r;
+            slot_out[r] = (int32_t)slot;
+            pos_out[e] = (int32_t)slot;
+            brank[r] = (int32_t)(seg - obv);     // in-edges of v with t <= t_r
+        } else {
+            const int64_t slot = x - ob;
+            in_t[slot] = tt;
+            in_id[slot] = e;
+            in_r[slot] = r;
+            pos_in[e] = (int32_t)slot;
+            in_head[slot] = (seg - obv) == 0;    // first entry of v's in-list
+            arank[r] = (int32_t)obv;             // out-edges of v with t < t_r
+        }
     }
 }
 
@@ -245,30 +362,7 @@ __global__ void k_hub_scatter(const unsigned long long *hub_of, const unsigned l
     }
 }
 
-__global__ void k_unpack(const unsigned long long *keys, unsigned long long rmask, int64_t E,
-                         const int32_t *orig_of, const int64_t *it, int64_t *t_out, int32_t *id_out,
-                         int32_t *r_out, int32_t *slot_of, int32_t *pos_of) {
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < E;
-         x += (int64_t)gridDim.x * blockDim.x) {
-        int32_t r = (int32_t)(keys[x] & rmask);
-        const int32_t e = orig_of[r];
-        r_out[x] = r;
-        id_out[x] = e;
-        t_out[x] = it[r];
-        if (slot_of) slot_of[r] = (int32_t)x;
-        pos_of[e] = (int32_t)x;  // the edge's place in this list array
-    }
-}
-
-// key = (vertex << idbits) | r for every edge r (edges are in r order, so a
-// stable sort over the vertex bits alone leaves each vertex's run in r order)
-__global__ void k_vkeys(const int32_t *vert, int64_t E, int idbits, unsigned long long *key) {
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < E;
-         r += (int64_t)gridDim.x * blockDim.x)
-        key[r] = ((unsigned long long)(unsigned)vert[r] << idbits) | (unsigned long long)r;
-}
-
-// off[v] = first sorted position whose vertex is >= v, for v in [0, V]
+// off[v] = first sorted position whose vertex (key >> idbits) is >= v, for v in [0, V]
 __global__ void k_voffsets(const unsigned long long *key, int64_t E, int64_t V, int idbits, int64_t *off) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x <= E;
          x += (int64_t)gridDim.x * blockDim.x) {
@@ -295,6 +389,9 @@ void plan_csr(Arena &ws, const Problem &p, Csr &o) {
     o.slot_out = ws.take<int32_t>(p.E);
     o.pos_out = ws.take<int32_t>(p.E);
     o.pos_in = ws.take<int32_t>(p.E);
+    o.brank = ws.take<int32_t>(p.E);
+    o.arank = ws.take<int32_t>(p.E);
+    o.in_gs = ws.take<int32_t>(p.E);
 }
 
 void carve_segsort(Arena &a, int64_t V, int64_t n, SegSort &s) {
@@ -313,18 +410,29 @@ void carve_segsort(Arena &a, int64_t V, int64_t n, SegSort &s) {
 // scratch layout
 struct CsrScratch {
     long long *flags;
-    unsigned long long *okey, *ikey, *okey2, *ikey2;
+    unsigned long long *mk, *mk2;  // [2E] incidence-item keys (the first sort uses both halves)
+    int *gflag;                    // [E+1] time-group heads
+    long long *gpos, *scan_tmp;    // [E+1] group index (exclusive)
+    int32_t *gstart;               // [E+1]
+    int64_t *moff;                 // [V+1] merged-list offsets
+    int32_t *oidx;                 // [2E+1] out-items before each item
+    unsigned char *in_head;        // [E] first entry of an in-list
     void *radix;
 };
 static CsrScratch carve_csr(Arena &a, const Problem &p) {
     CsrScratch s;
     int64_t E = p.E > 0 ? p.E : 1;
     s.flags = a.take<long long>(8);
-    s.okey = a.take<unsigned long long>(E);
-    s.ikey = a.take<unsigned long long>(E);
-    s.okey2 = a.take<unsigned long long>(E);
-    s.ikey2 = a.take<unsigned long long>(E);
-    s.radix = a.take<char>(radix_scratch_bytes(E));
+    s.mk = a.take<unsigned long long>(2 * E);
+    s.mk2 = a.take<unsigned long long>(2 * E);
+    s.gflag = a.take<int>(E + 1);
+    s.gpos = a.take<long long>(E + 1);
+    s.gstart = a.take<int32_t>(E + 1);
+    s.scan_tmp = a.take<long long>(scan_scratch_elems(2 * E + 1));
+    s.moff = a.take<int64_t>(p.V + 1);
+    s.oidx = a.take<int32_t>(2 * E + 1);
+    s.in_head = a.take<unsigned char>(E);
+    s.radix = a.take<char>(radix_scratch_bytes(2 * E));
     return s;
 }
 
@@ -383,6 +491,30 @@ dgec_status sort_segments(Ctx *c, int64_t V, unsigned long long *keys, const int
     return DGEC_OK;
 }
 
+// Scan loaders and stores for the merged lists.
+struct LoadOutBit {  // 1 for an out-item, 0 for an in-item or past the end
+    const unsigned long long *k;
+    int64_t n;
+    __device__ __forceinline__ long long operator()(int64_t i) const { return i < n ? (long long)(k[i] & 1ull) : 0ll; }
+};
+struct StoreI32 {
+    int32_t *p;
+    __device__ __forceinline__ void operator()(int64_t i, long long v) const { p[i] = (int32_t)v; }
+};
+// y where a time group starts in the in-lists (a list's first entry, or a
+// time different from the entry before), 0 elsewhere: the running maximum
+// is then the start of y's tie group.
+struct LoadInGroupHead {
+    const int64_t *t;
+    const unsigned char *head;
+    __device__ __forceinline__ long long operator()(int64_t y) const {
+        return (head[y] || y == 0 || t[y] != t[y - 1]) ? (long long)y : 0ll;
+    }
+};
+struct MaxI64 {
+    __device__ __forceinline__ long long operator()(long long a, long long b) const { return a > b ? a : b; }
+};
+
 dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
     cudaStream_t st = c->stream;
     Arena a(scratch, SIZE_MAX);
@@ -401,12 +533,9 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
                              (long long)f[0]);
     if (f[1]) return set_err(c, DGEC_ERR_SELF_LOOP, "%lld self loops (i, i, t)", (long long)f[1]);
     p.tmin = E > 0 ? f[2] : 0;
-    uint64_t span = E > 0 ? (uint64_t)(f[3] - f[2]) : 0;
+    uint64_t span = E > 0 ? (uint64_t)f[3] - (uint64_t)f[2] : 0;
     p.idbits = bits_for((uint64_t)(E > 1 ? E - 1 : 1));
     p.tbits = bits_for(span);
-    if (p.idbits + p.tbits > 64)
-        return set_err(c, DGEC_ERR_TOO_LARGE, "time span %llu needs %d bits + %d id bits > 64",
-                       (unsigned long long)span, p.tbits, p.idbits);
     if (E == 0) {
         CU_TRY(c, cudaMemsetAsync(o.out_off, 0, sizeof(int64_t) * (V + 1), st));
         CU_TRY(c, cudaMemsetAsync(o.in_off, 0, sizeof(int64_t) * (V + 1), st));
@@ -414,36 +543,46 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
     }
     // global (t, id) order: internal ids
     const int gEE = grid_for(E, kBlock, 65536);
-    TK(c, "k_pack_keys", k_pack_keys<<<gEE, kBlock, 0, st>>>(p.t, E, p.tmin, p.idbits, s.okey));
-    {
+    if (p.idbits + p.tbits <= 64) {
+        TK(c, "k_pack_keys", k_pack_keys<<<gEE, kBlock, 0, st>>>(p.t, E, p.tmin, p.idbits, s.mk));
         bool in_b;
-        DG_TRY(radix_sort(c, RadixBuffers{s.okey, s.ikey, nullptr, nullptr}, E, p.idbits, p.idbits + p.tbits,
+        DG_TRY(radix_sort(c, RadixBuffers{s.mk, s.mk2, nullptr, nullptr}, E, p.idbits, p.idbits + p.tbits,
                           s.radix, &in_b));
-        TK(c, "k_rank_init", k_rank_init<<<gEE, kBlock, 0, st>>>(in_b ? s.ikey : s.okey, E, p.tmin, p.idbits,
+        TK(c, "k_rank_init", k_rank_init<<<gEE, kBlock, 0, st>>>(in_b ? s.mk2 : s.mk, E, p.tmin, p.idbits,
                                                                 p.src, p.dst, p.egraph, p.voff, p.G, o.orig_of, o.rank_of,
                                                                 o.isrc, o.idst, o.it));
-    }
-    // per-vertex lists: stable sort of (vertex, r) over the vertex bits only
-    const int vbits = bits_for((uint64_t)(V > 1 ? V - 1 : 1));
-    const unsigned long long rmask = (1ull << p.idbits) - 1ull;
-    struct Side {
-        const int32_t *vert;
-        unsigned long long *k1, *k2;
-        int64_t *off;
-        int64_t *t_out;
-        int32_t *id_out, *r_out, *slot_of, *pos_of;
-    } sides[2] = {{o.isrc, s.okey, s.okey2, o.out_off, o.out_t, o.out_id, o.out_r, o.slot_out, o.pos_out},
-                  {o.idst, s.ikey, s.ikey2, o.in_off, o.in_t, o.in_id, o.in_r, nullptr, o.pos_in}};
-    for (const Side &d : sides) {
-        TK(c, "k_vkeys", k_vkeys<<<gEE, kBlock, 0, st>>>(d.vert, E, p.idbits, d.k1));
+    } else {
+        // wide span: the time is the whole key, the id its value (second halves of the item buffers)
+        TK(c, "k_pack_t", k_pack_t<<<gEE, kBlock, 0, st>>>(p.t, E, p.tmin, s.mk, s.mk + E));
         bool in_b;
-        DG_TRY(radix_sort(c, RadixBuffers{d.k1, d.k2, nullptr, nullptr}, E, p.idbits, p.idbits + vbits, s.radix,
-                          &in_b));
-        const unsigned long long *key = in_b ? d.k2 : d.k1;
-        TK(c, "k_voffsets", k_voffsets<<<grid_for(E + 1, kBlock, 65536), kBlock, 0, st>>>(key, E, V, p.idbits, d.off));
-        TK(c, "k_unpack", k_unpack<<<gEE, kBlock, 0, st>>>(key, rmask, E, o.orig_of, o.it, d.t_out, d.id_out, d.r_out,
-                                                           d.slot_of, d.pos_of));
+        DG_TRY(radix_sort(c, RadixBuffers{s.mk, s.mk2, s.mk + E, s.mk2 + E}, E, 0, p.tbits, s.radix, &in_b));
+        TK(c, "k_rank_init_kv", k_rank_init_kv<<<gEE, kBlock, 0, st>>>(
+                                    in_b ? s.mk2 : s.mk, in_b ? s.mk2 + E : s.mk + E, E, p.tmin, p.src, p.dst,
+                                    p.egraph, p.voff, p.G, o.orig_of, o.rank_of, o.isrc, o.idst, o.it));
     }
+    // time groups of the r order, then the incidence items in (t, in-before-out, r) order
+    TK(c, "k_thead", k_thead<<<grid_for(E + 1, kBlock, 65536), kBlock, 0, st>>>(o.it, E, s.gflag));
+    DG_TRY(exclusive_scan_i32(c, s.gflag, s.gpos, E + 1, s.scan_tmp));
+    TK(c, "k_tgstart", k_tgstart<<<grid_for(E + 1, kBlock, 65536), kBlock, 0, st>>>(s.gflag, s.gpos, E, s.gstart));
+    const int cb = p.idbits + 1;  // bits of an item code 2r + dir
+    const int vbits = bits_for((uint64_t)(V > 1 ? V - 1 : 1));
+    TK(c, "k_mkeys", k_mkeys<<<gEE, kBlock, 0, st>>>(o.isrc, o.idst, s.gflag, s.gpos, s.gstart, E, cb, s.mk));
+    // every vertex's merged list: a stable sort over the vertex bits alone
+    bool in_b;
+    DG_TRY(radix_sort(c, RadixBuffers{s.mk, s.mk2, nullptr, nullptr}, 2 * E, cb, cb + vbits, s.radix, &in_b));
+    const unsigned long long *key = in_b ? s.mk2 : s.mk;
+    TK(c, "k_voffsets", k_voffsets<<<grid_for(2 * E + 1, kBlock, 65536), kBlock, 0, st>>>(key, 2 * E, V, cb, s.moff));
+    DG_TRY((device_scan<long long, SumI64, LoadOutBit, StoreI32>(c, LoadOutBit{key, 2 * E}, StoreI32{s.oidx},
+                                                                 2 * E + 1, SumI64{}, 0ll, false, s.scan_tmp)));
+    TK(c, "k_moff_split", k_moff_split<<<grid_for(V + 1, kBlock, 65536), kBlock, 0, st>>>(s.moff, s.oidx, V, o.out_off,
+                                                                                        o.in_off));
+    TK(c, "k_munpack", k_munpack<<<grid_for(2 * E, kBlock, 65536), kBlock, 0, st>>>(
+                           key, 2 * E, cb, s.moff, s.oidx, o.out_off, o.orig_of, o.it, o.out_t, o.out_id, o.out_r,
+                           o.slot_out, o.pos_out, o.in_t, o.in_id, o.in_r, o.pos_in, s.in_head, o.brank, o.arank));
+    // start of every in-list entry's tie group (the kNN window takes a crossing group's smallest ids)
+    DG_TRY((device_scan<long long, MaxI64, LoadInGroupHead, StoreI32>(c, LoadInGroupHead{o.in_t, s.in_head},
+                                                                      StoreI32{o.in_gs}, E, MaxI64{}, 0ll, true,
+                                                                      s.scan_tmp)));
     return DGEC_OK;
 }
 

@@ -200,6 +200,7 @@ dgec_status run_pipeline(Ctx *c, const HostBatch &hb, const int32_t *d_src, cons
     p.gk = L.gk;
     p.gM = L.gM;
     p.egraph = L.egraph;
+    stage_start(c);
     DG_STAGE("A incidence lists", stage_csr(c, p, L.csr, L.scratch));
     DG_STAGE("B skeleton and kNN", stage_skeleton(c, p, L.csr, L.skel, L.scratch));
     const Skel *forest_in = &L.skel;
@@ -226,6 +227,7 @@ dgec_status run_pipeline(Ctx *c, const HostBatch &hb, const int32_t *d_src, cons
     CU_TRY(c, cudaStreamSynchronize(c->stream));
     CU_TRY(c, cudaGetLastError());
     kt_collect(c);
+    stage_collect(c);
     *out_layout = L;
     *out_problem = p;
     return DGEC_OK;
@@ -371,6 +373,8 @@ dgec_status dgec_create(dgec_ctx **out, int device) {
 dgec_status dgec_destroy(dgec_ctx *x) {
     if (!x) return DGEC_ERR_INVALID_ARG;
     if (x->c.h_pinned) cudaFreeHost(x->c.h_pinned);
+    for (int i = 0; i <= kMaxStages; i++)
+        if (x->c.stages.ev[i]) cudaEventDestroy(x->c.stages.ev[i]);
     if (x->c.kt) {
         if (x->c.kt->ev) {
             for (int i = 0; i < 2 * kMaxTimed; i++)
@@ -422,6 +426,15 @@ dgec_status dgec_kernel_timing(dgec_ctx *x, int i, const char **name, double *to
     if (name) *name = k->names[i];
     if (total_ms) *total_ms = k->ms[i];
     if (launches) *launches = k->count[i];
+    return DGEC_OK;
+}
+
+dgec_status dgec_stage_timing(const dgec_ctx *x, int i, const char **name, double *ms) {
+    if (!x) return DGEC_ERR_INVALID_ARG;
+    const StageTimer &t = x->c.stages;
+    if (i < 0 || i >= t.n) return DGEC_ERR_INVALID_ARG;
+    if (name) *name = t.name[i];
+    if (ms) *ms = t.ms[i];
     return DGEC_OK;
 }
 
@@ -596,6 +609,7 @@ dgec_status dgec_run_levels(dgec_ctx *x, const int32_t *d_src, const int32_t *d_
     p.gk = L.gk;
     p.gM = L.gM;
     p.egraph = L.egraph;
+    stage_start(c);
     DG_STAGE("A incidence lists", stage_csr(c, p, L.csr, L.scratch));
     DG_STAGE("B skeleton and kNN", stage_skeleton(c, p, L.csr, L.skel, L.scratch));
     DG_STAGE("L discrete levels", stage_levels(c, p, L.csr, L.skel, params->h_omega, L.lv, L.scratch));
@@ -607,6 +621,7 @@ dgec_status dgec_run_levels(dgec_ctx *x, const int32_t *d_src, const int32_t *d_
     CU_TRY(c, cudaStreamSynchronize(c->stream));
     CU_TRY(c, cudaGetLastError());
     kt_collect(c);
+    stage_collect(c);
     out->sk_u = L.skel.u;
     out->sk_v = L.skel.v;
     out->sk_w = L.skel.w;

@@ -532,6 +532,7 @@ dgec_status dgec_run_hyper(dgec_ctx *x, const int64_t *d_t, int64_t n_hyperedges
     p.gk = L.gk;
     p.gM = L.gM;
     p.egraph = L.egraph;
+    stage_start(c);
     DG_STAGE("H hypergraph skeleton", stage_hyper(c, p, h, L.csr, L.S, L.D, L.skel, L.scratch));
     DG_STAGE("C spanning forest", stage_msf(c, p, L.csr, L.skel, L.msf, L.scratch));
     DG_STAGE("D1 dendrogram", stage_dendro(c, p, L.csr, L.msf, L.den, L.scratch));
@@ -539,6 +540,7 @@ dgec_status dgec_run_hyper(dgec_ctx *x, const int64_t *d_t, int64_t n_hyperedges
     CU_TRY(c, cudaStreamSynchronize(c->stream));
     CU_TRY(c, cudaGetLastError());
     kt_collect(c);
+    stage_collect(c);
     out->src_voff = L.S.voff;
     out->src_list = L.S.id;
     out->dst_voff = directed ? L.D.voff : nullptr;

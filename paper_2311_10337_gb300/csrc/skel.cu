@@ -21,27 +21,8 @@
 
 namespace dgec {
 
-__device__ __forceinline__ int64_t upper_bound_t(const int64_t *a, int64_t n, int64_t x) {
-    int64_t lo = 0, hi = n;
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (a[mid] <= x) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-__device__ __forceinline__ int64_t lower_bound_t(const int64_t *a, int64_t n, int64_t x) {
-    int64_t lo = 0, hi = n;
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (a[mid] < x) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
 // brank[e] = #in-edges of src[e] with t <= t_e; arank[e] = #out-edges of
-// dst[e] with t < t_e (computed in k_ranks_knn below).
+// dst[e] with t < t_e (both from stage A's merged lists).
 // All node ids below are internal ids r (see the stage A notes).
 struct SkView {
     const int32_t *src, *dst;  // isrc, idst (by r)
@@ -143,11 +124,13 @@ __global__ void k_compact_links(const int32_t *part, const int64_t *wgt, const i
 // (|dt|, id). The K best of each side suffice: the successor side is
 // already in (w, id) order from arank; on the predecessor side the last K
 // of the prefix, except that when the boundary tie group crosses the
-// window its smallest ids are taken instead of its largest. The 2K
-// candidates are sorted in registers (bitonic network); the one node that
-// can appear on both sides (the reciprocal concurrent edge, w = 0) is
-// counted once. Under the time cutoff (Sec. 4.3) only neighbours with
-// w <= dmax exist; they are a prefix of the sorted candidates.
+// window its smallest ids are taken instead of its largest (the group's
+// first slot comes from stage A's in_gs). The two ranks come from stage A,
+// so the kernel only gathers two windows of K contiguous entries: no
+// search. The 2K candidates are sorted in registers (bitonic network); the
+// one node that can appear on both sides (the reciprocal concurrent edge,
+// w = 0) is counted once. Under the time cutoff (Sec. 4.3) only neighbours
+// with w <= dmax exist; they are a prefix of the sorted candidates.
 
 struct Cand {
     long long w;
@@ -157,54 +140,48 @@ __device__ __forceinline__ bool cand_less(const Cand &a, const Cand &b) {
     return a.w < b.w || (a.w == b.w && a.id < b.id);
 }
 
-// The ranks b (tail side) and a (head side) that the skeleton links need
-// come out of the same binary searches that locate the two windows, so one
-// kernel computes both and stores the ranks for the link pass.
 template <int K>
-__global__ void __launch_bounds__(128) k_ranks_knn(const int32_t *src, const int32_t *dst,
-                                                   const int64_t *t, const int32_t *orig_of, int64_t E,
-                                                   const int64_t *out_off, const int64_t *out_t,
-                                                   const int32_t *out_id, const int64_t *in_off,
-                                                   const int64_t *in_t, const int32_t *in_id,
-                                                   int32_t *brank, int32_t *arank, int G,
-                                                   const int32_t *egraph, const int64_t *eoff,
-                                                   const int32_t *gk, const int64_t *knn_off,
-                                                   int64_t dmax, int32_t *knn, int64_t *core) {
+__global__ void __launch_bounds__(128) k_knn(const int32_t *src, const int32_t *dst, const int64_t *t,
+                                             const int32_t *orig_of, int64_t E, const int64_t *out_off,
+                                             const int64_t *out_t, const int32_t *out_id,
+                                             const int64_t *in_off, const int64_t *in_t,
+                                             const int32_t *in_id, const int32_t *in_gs,
+                                             const int32_t *brank, const int32_t *arank, int G,
+                                             const int32_t *egraph, const int64_t *eoff,
+                                             const int32_t *gk, const int64_t *knn_off, int64_t dmax,
+                                             int32_t *knn, int64_t *core) {
     constexpr int N = 2 * K;
     // r runs over internal ids (src, dst, t are the r-ordered copies); the
     // neighbour lists are written under the original id, with original ids
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < E;
          r += (int64_t)gridDim.x * blockDim.x) {
-        int i = src[r], j = dst[r];
-        long long te = t[r];
+        const int i = src[r], j = dst[r];
+        const long long te = t[r];
         const int64_t e = orig_of[r];
         // the edge's graph: its k, its kNN rows, its local id base
         const int gr = G > 1 ? egraph[e] : 0;  // one graph: no random lookup
         const int k = gk[gr];
         const int64_t e0 = eoff[gr];
         int32_t *row = knn + knn_off[gr] + (e - e0) * k;
-        int64_t ib = in_off[i];
-        int64_t ob = out_off[j], nout = out_off[j + 1] - ob;
-        int64_t b = upper_bound_t(in_t + ib, in_off[i + 1] - ib, te);
-        int64_t a = lower_bound_t(out_t + ob, nout, te);
-        brank[r] = (int32_t)b;
-        arank[r] = (int32_t)a;
+        const int64_t ib = in_off[i];
+        const int64_t ob = out_off[j], nout = out_off[j + 1] - ob;
+        const int64_t b = brank[r], a = arank[r];
         Cand c[N];
-        // predecessor window
-        int64_t lo = b - K > 0 ? b - K : 0;
-        int64_t g0 = lo, g1 = lo, take_grp = 0;
-        bool cross = lo > 0 && in_t[ib + lo] == in_t[ib + lo - 1];
+        // predecessor window: the last K of the prefix [0, b); a tie group
+        // that crosses its start contributes its smallest ids
+        const int64_t lo = b - K > 0 ? b - K : 0;
+        int64_t g0 = lo, take_grp = 0;
+        const bool cross = lo > 0 && in_t[ib + lo] == in_t[ib + lo - 1];
         if (cross) {
-            long long T = in_t[ib + lo];
-            g0 = lower_bound_t(in_t + ib, lo, T);
-            g1 = lo + upper_bound_t(in_t + ib + lo, b - lo, T);
-            take_grp = g1 - lo;  // = K - (b - g1)
+            const long long T = in_t[ib + lo];
+            g0 = (int64_t)in_gs[ib + lo] - ib;
+            int64_t g1 = lo;
+            while (g1 < b && in_t[ib + g1] == T) g1++;  // at most K steps
+            take_grp = g1 - lo;
         }
 #pragma unroll
         for (int x = 0; x < K; x++) {
-            int64_t idx;
-            if (cross) idx = x < take_grp ? g0 + x : g1 + (x - take_grp);
-            else idx = lo + x;
+            const int64_t idx = x < take_grp ? g0 + x : lo + x;
             if (idx < b) {
                 c[x].w = te - in_t[ib + idx];
                 c[x].id = in_id[ib + idx];
@@ -215,7 +192,7 @@ __global__ void __launch_bounds__(128) k_ranks_knn(const int32_t *src, const int
         }
 #pragma unroll
         for (int x = 0; x < K; x++) {
-            int64_t idx = a + x;
+            const int64_t idx = a + x;
             if (idx < nout) {
                 c[K + x].w = out_t[ob + idx] - te;
                 c[K + x].id = out_id[ob + idx];
@@ -261,24 +238,8 @@ __global__ void __launch_bounds__(128) k_ranks_knn(const int32_t *src, const int
     }
 }
 
-// The ranks alone, for runs that do not want the kNN lists.
-__global__ void __launch_bounds__(128) k_ranks(const int32_t *src, const int32_t *dst, const int64_t *t,
-                                               int64_t E, const int64_t *out_off, const int64_t *out_t,
-                                               const int64_t *in_off, const int64_t *in_t, int32_t *brank,
-                                               int32_t *arank) {
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < E;
-         r += (int64_t)gridDim.x * blockDim.x) {
-        const int i = src[r], j = dst[r];
-        const long long te = t[r];
-        const int64_t ib = in_off[i], ob = out_off[j];
-        brank[r] = (int32_t)upper_bound_t(in_t + ib, in_off[i + 1] - ib, te);
-        arank[r] = (int32_t)lower_bound_t(out_t + ob, out_off[j + 1] - ob, te);
-    }
-}
-
 void plan_skel(Arena &ws, const Problem &p, Skel &o) {
-    o.brank = ws.take<int32_t>(p.E);
-    o.arank = ws.take<int32_t>(p.E);
+    o.brank = o.arank = nullptr;  // the ranks live in stage A's output
     o.u = ws.take<int32_t>(2 * p.E);
     o.v = ws.take<int32_t>(2 * p.E);
     o.ru = ws.take<int32_t>(2 * p.E);
@@ -319,15 +280,16 @@ dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void
     SkScratch s = carve_skel(a, p);
     int64_t E = p.E;
     int grid = grid_for(E, 128, 1 << 20);
-#define KNN_ARGS                                                                           \
-    g.isrc, g.idst, g.it, g.orig_of, E, g.out_off, g.out_t, g.out_id, g.in_off, g.in_t, g.in_id, \
-        o.brank, o.arank, p.G, p.egraph, p.eoff, p.gk, p.knn_off, p.dmax, o.knn, o.core
-    if (!p.knn)
-        TK(c, "k_ranks", k_ranks<<<grid, 128, 0, st>>>(g.isrc, g.idst, g.it, E, g.out_off, g.out_t, g.in_off,
-                                                       g.in_t, o.brank, o.arank));
-    else if (p.k <= 4) TK(c, "k_ranks_knn", k_ranks_knn<4><<<grid, 128, 0, st>>>(KNN_ARGS));
-    else if (p.k <= 8) TK(c, "k_ranks_knn", k_ranks_knn<8><<<grid, 128, 0, st>>>(KNN_ARGS));
-    else TK(c, "k_ranks_knn", k_ranks_knn<16><<<grid, 128, 0, st>>>(KNN_ARGS));
+    o.brank = g.brank;
+    o.arank = g.arank;
+#define KNN_ARGS                                                                                   \
+    g.isrc, g.idst, g.it, g.orig_of, E, g.out_off, g.out_t, g.out_id, g.in_off, g.in_t, g.in_id, g.in_gs, \
+        g.brank, g.arank, p.G, p.egraph, p.eoff, p.gk, p.knn_off, p.dmax, o.knn, o.core
+    if (p.knn) {
+        if (p.k <= 4) TK(c, "k_knn", k_knn<4><<<grid, 128, 0, st>>>(KNN_ARGS));
+        else if (p.k <= 8) TK(c, "k_knn", k_knn<8><<<grid, 128, 0, st>>>(KNN_ARGS));
+        else TK(c, "k_knn", k_knn<16><<<grid, 128, 0, st>>>(KNN_ARGS));
+    }
 #undef KNN_ARGS
     SkView v{g.isrc, g.idst, g.out_off, g.in_off, g.out_r, g.in_r, g.slot_out, o.brank, o.arank};
     TK(c, "k_links", k_links<<<grid_for(E, kBlock, 65536), kBlock, 0, st>>>(v, g.it, g.out_t, g.in_t, E, p.dmax,

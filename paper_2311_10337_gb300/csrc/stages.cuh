@@ -47,7 +47,7 @@ dgec_status sort_segments(Ctx *c, int64_t V, unsigned long long *keys, const int
                           int key_bits);
 
 // Stage A: incidence lists (Alg. 3's adjacency lists), per-vertex lists sorted by
-// (t, id).
+// (t, id), and the merge ranks of Alg. 2 (from one sort of the merged lists).
 //
 // Internal numbering: every later stage names a line-graph node (a temporal
 // edge) by r = its rank in (t, id) order. Skeleton links join edges that are
@@ -66,6 +66,8 @@ struct Csr {
     int64_t *it;                // [E] t in r order
     int32_t *slot_out;          // [E] by r: global slot in the out-lists
     int32_t *pos_out, *pos_in;  // [E] by original id: position in out_id / in_id (outputs)
+    int32_t *brank, *arank;     // [E] by r: #in-edges of src with t <= t_r; #out-edges of dst with t < t_r
+    int32_t *in_gs;             // [E] by in-list slot: first slot of its tie group (same vertex, same t)
 };
 void plan_csr(Arena &ws, const Problem &p, Csr &o);
 size_t csr_scratch_bytes(const Problem &p);

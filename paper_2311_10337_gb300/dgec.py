@@ -23,7 +23,7 @@ STATUS = {0: "DGEC_OK", 1: "DGEC_ERR_INVALID_ARG", 2: "DGEC_ERR_VERTEX_RANGE",
 
 EXPORTS = ["dgec_create", "dgec_destroy", "dgec_last_error", "dgec_status_string",
            "dgec_workspace_size", "dgec_run", "dgec_run_host", "dgec_last_launch_count",
-           "dgec_set_kernel_timing", "dgec_kernel_timing", "dgec_msf_static",
+           "dgec_set_kernel_timing", "dgec_kernel_timing", "dgec_stage_timing", "dgec_msf_static",
            "dgec_batch_workspace_size", "dgec_run_batch", "dgec_server_create", "dgec_submit",
            "dgec_wait", "dgec_server_lane_capacity", "dgec_server_destroy",
            "dgec_levels_workspace_size", "dgec_run_levels", "dgec_hyper_workspace_size",
@@ -137,6 +137,8 @@ def load(path: str = LIB_PATH):
     L.dgec_kernel_timing.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
                                      ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_int64)]
+    L.dgec_stage_timing.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
+                                    ctypes.POINTER(ctypes.c_double)]
     I64A = ctypes.POINTER(ctypes.c_int64)
     I32A = ctypes.POINTER(ctypes.c_int32)
     L.dgec_batch_workspace_size.argtypes = [ctypes.c_int32, I64A, I32A, I32A, I32A,
@@ -312,6 +314,19 @@ class Context:
             if rc != DGEC_OK:
                 break
             out[nm.value.decode()] = (ms.value, n.value)
+            i += 1
+        return out
+
+    def stage_timing(self) -> list:
+        """[(stage name, device ms)] of the last completed call, in order."""
+        out = []
+        i = 0
+        while True:
+            nm = ctypes.c_char_p()
+            ms = ctypes.c_double()
+            if self.L.dgec_stage_timing(self.h, i, ctypes.byref(nm), ctypes.byref(ms)) != DGEC_OK:
+                break
+            out.append((nm.value.decode(), ms.value))
             i += 1
         return out
 

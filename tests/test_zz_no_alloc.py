@@ -111,6 +111,9 @@ def test_static_forest_rejects_oversize():
     import torch
     z32 = torch.zeros(4, dtype=torch.int32, device="cuda")
     z64 = torch.zeros(4, dtype=torch.int64, device="cuda")
+    n_nodes = (1 << 18) + 1                            # one node over the fixed array's limit
+    o32 = torch.zeros(n_nodes, dtype=torch.int32, device="cuda")
+    o64 = torch.zeros(n_nodes, dtype=torch.int64, device="cuda")
     with pytest.raises(dgec.DgecError) as ei:
-        dgec.msf_static(z32, z32, z64, (1 << 18) + 1, z32, z32, z64)
+        dgec.msf_static(z32, z32, z64, n_nodes, o32, o32.clone(), o64)
     assert ei.value.status == 4
