@@ -272,6 +272,19 @@ int64_t dgec_server_lane_capacity(const dgec_server *srv);
  * pool is untouched. Jobs still queued complete with DGEC_ERR_INVALID_ARG. */
 dgec_status dgec_server_destroy(dgec_server *srv);
 
+/* Launch configuration of the calls made on ctx (no counterpart in the
+ * paper; it changes speed, never results): threads per CTA of the kNN kernel
+ * (64, 128 or 256; default 128) and the number of CTAs of each grid-stride
+ * streaming kernel (1 .. 2^20; default 65,536). The autotuner of the Python
+ * package picks them per GPU model and workload. Invalid values give
+ * DGEC_ERR_INVALID_ARG and leave the configuration unchanged. */
+typedef struct {
+    int32_t knn_block;
+    int32_t stream_ctas;
+} dgec_launch_config;
+dgec_status dgec_set_launch_config(dgec_ctx *ctx, const dgec_launch_config *cfg);
+dgec_status dgec_get_launch_config(const dgec_ctx *ctx, dgec_launch_config *cfg);
+
 /* Device time of each pipeline stage of the last completed call on ctx
  * (dgec_run, dgec_run_host, dgec_run_batch, dgec_run_levels,
  * dgec_run_hyper), from CUDA events recorded on the call's stream at the

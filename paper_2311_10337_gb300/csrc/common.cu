@@ -5,6 +5,8 @@
 
 namespace dgec {
 
+thread_local int64_t tl_stream_ctas = 65536;
+
 dgec_status set_err(Ctx *c, dgec_status s, const char *fmt, ...) {
     if (c) {
         va_list ap;

@@ -45,6 +45,8 @@ struct StageTimer {
 
 struct Ctx {
     int device = 0;
+    int knn_block = 128;           // launch configuration (dgec_set_launch_config)
+    int64_t stream_ctas = 65536;
     int num_sms = 152;
     char msg[512] = {0};
     int64_t launches = 0;
@@ -136,7 +138,14 @@ struct Arena {
 
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// CTA count of the grid-stride streaming kernels launched by this thread's
+// current call (set from the context's launch configuration when a call
+// starts; each server lane runs its calls on its own thread).
+extern thread_local int64_t tl_stream_ctas;
+constexpr int64_t kStreamCap = -1;  // max_blocks sentinel: use tl_stream_ctas
+
 inline int grid_for(int64_t n, int block = kBlock, int64_t max_blocks = 1 << 20) {
+    if (max_blocks == kStreamCap) max_blocks = tl_stream_ctas;
     int64_t g = cdiv(n, block);
     if (g < 1) g = 1;
     if (g > max_blocks) g = max_blocks;

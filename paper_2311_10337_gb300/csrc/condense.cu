@@ -134,7 +134,7 @@ template <class Sel>
 static dgec_status jump_to_fixed(Ctx *c, int64_t n, int64_t off, Sel sel, int32_t *ptr,
                                  unsigned long long *moved) {
     if (n <= 0) return DGEC_OK;
-    const int g = grid_for(n, kBlock, 65536);
+    const int g = grid_for(n, kBlock, kStreamCap);
     CU_TRY(c, cudaMemsetAsync(moved, 0, sizeof(unsigned long long), c->stream));
     TK(c, "k_c_top", k_c_top<Sel><<<g, kBlock, 0, c->stream>>>(n, off, sel, ptr, moved));
     int64_t m;
@@ -637,8 +637,8 @@ dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro 
     Gview gv{E, n, E + n, p.G, p.egraph, m.u, p.eoff, p.gM};
     Arena a(scratch, SIZE_MAX);
     CScratch s = carve_condense(a, p);
-    const int gN = grid_for(N, kBlock, 65536), gE = grid_for(E, kBlock, 65536),
-              gn = grid_for(n + p.G, kBlock, 65536);
+    const int gN = grid_for(N, kBlock, kStreamCap), gE = grid_for(E, kBlock, kStreamCap),
+              gn = grid_for(n + p.G, kBlock, kStreamCap);
     CU_TRY(c, cudaMemsetAsync(s.nbig, 0, sizeof(int) * N, st));
     CU_TRY(c, cudaMemsetAsync(s.isc, 0, sizeof(int) * (N + 1), st));
     CU_TRY(c, cudaMemsetAsync(s.cdeath, 0, sizeof(unsigned long long) * N, st));
@@ -684,7 +684,7 @@ dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro 
     e.ucand = s.ucand;
     e.nxt = s.nxt;
     e.nxt2 = s.nxt2;
-    const int gc = grid_for(ncl + 1, kBlock, 65536);
+    const int gc = grid_for(ncl + 1, kBlock, kStreamCap);
     e.flag = s.cnt + 2;
     CU_TRY(c, cudaMemsetAsync(s.pending, 0, sizeof(int) * (ncl + 1), st));
     TK(c, "k_e_init", k_e_init<<<gc, kBlock, 0, st>>>(e, s.st_hi, s.st_lo));
@@ -696,7 +696,7 @@ dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro 
         if (phase > 4096) return set_err(c, DGEC_ERR_TIMEOUT, "EOM contraction exceeded 4096 phases");
         e.alist = al;
         e.nact = nact;
-        const int ga = grid_for(nact, kBlock, 65536);
+        const int ga = grid_for(nact, kBlock, kStreamCap);
         TK(c, "k_e_unary", k_e_unary<<<ga, kBlock, 0, st>>>(e));
         TK(c, "k_e_fninit", k_e_fninit<<<ga, kBlock, 0, st>>>(e));
         int32_t *ni = s.nxt, *no = s.nxt2;
@@ -765,7 +765,7 @@ dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro 
         DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, s.v1, s.v2}, nf, 0, p.idbits > 0 ? p.idbits : 1,
                           s.radix, &in_b));
         unsigned long long *kk = in_b ? s.k2 : s.k1, *vv = in_b ? s.v2 : s.v1;
-        const int gf = grid_for(nf, kBlock, 65536);
+        const int gf = grid_for(nf, kBlock, kStreamCap);
         TK(c, "k_e_gstart", k_e_gstart<<<gf, kBlock, 0, st>>>(nf, kk, p.egraph, s.gstart, o.gclusters));
         TK(c, "k_e_gcount", k_e_gcount<<<grid_for(p.G), kBlock, 0, st>>>(p.G, s.gstart, o.gclusters));
         TK(c, "k_e_rank", k_e_rank<<<gf, kBlock, 0, st>>>(nf, kk, vv, p.egraph, s.gstart, s.rank));

@@ -485,7 +485,7 @@ dgec_status sort_segments(Ctx *c, int64_t V, unsigned long long *keys, const int
         if (hb == 0) hb = 1;
         DG_TRY(radix_sort(c, rb2, tot, 0, hb, s.radix, &in_b));
         unsigned long long *hub_of = in_b ? v1o : v1, *key_of = in_b ? k1o : k1;
-        TK(c, "k_hub_scatter", k_hub_scatter<<<grid_for(tot, kBlock, 65536), kBlock, 0, st>>>(hub_of, key_of, tot, off, hl, hstart,
+        TK(c, "k_hub_scatter", k_hub_scatter<<<grid_for(tot, kBlock, kStreamCap), kBlock, 0, st>>>(hub_of, key_of, tot, off, hl, hstart,
                                                                        keys));
     }
     return DGEC_OK;
@@ -523,7 +523,7 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
     TK(c, "k_init_flags", k_init_flags<<<1, 1, 0, st>>>(s.flags));
     if (E > 0) {
         if (p.G == 1) CU_TRY(c, cudaMemsetAsync(p.egraph, 0, sizeof(int32_t) * E, st));
-        else TK(c, "k_egraph", k_egraph<<<grid_for(E, kBlock, 65536), kBlock, 0, st>>>(p.eoff, p.G, E, p.egraph));
+        else TK(c, "k_egraph", k_egraph<<<grid_for(E, kBlock, kStreamCap), kBlock, 0, st>>>(p.eoff, p.G, E, p.egraph));
         TK(c, "k_count", k_count<<<grid_for(E, kBlock, (int64_t)c->num_sms * 16), kBlock, 0, st>>>(
                              p.src, p.dst, p.t, E, p.egraph, p.voff, nullptr, nullptr, s.flags));
     }
@@ -542,7 +542,7 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
         return DGEC_OK;
     }
     // global (t, id) order: internal ids
-    const int gEE = grid_for(E, kBlock, 65536);
+    const int gEE = grid_for(E, kBlock, kStreamCap);
     if (p.idbits + p.tbits <= 64) {
         TK(c, "k_pack_keys", k_pack_keys<<<gEE, kBlock, 0, st>>>(p.t, E, p.tmin, p.idbits, s.mk));
         bool in_b;
@@ -561,9 +561,9 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
                                     p.egraph, p.voff, p.G, o.orig_of, o.rank_of, o.isrc, o.idst, o.it));
     }
     // time groups of the r order, then the incidence items in (t, in-before-out, r) order
-    TK(c, "k_thead", k_thead<<<grid_for(E + 1, kBlock, 65536), kBlock, 0, st>>>(o.it, E, s.gflag));
+    TK(c, "k_thead", k_thead<<<grid_for(E + 1, kBlock, kStreamCap), kBlock, 0, st>>>(o.it, E, s.gflag));
     DG_TRY(exclusive_scan_i32(c, s.gflag, s.gpos, E + 1, s.scan_tmp));
-    TK(c, "k_tgstart", k_tgstart<<<grid_for(E + 1, kBlock, 65536), kBlock, 0, st>>>(s.gflag, s.gpos, E, s.gstart));
+    TK(c, "k_tgstart", k_tgstart<<<grid_for(E + 1, kBlock, kStreamCap), kBlock, 0, st>>>(s.gflag, s.gpos, E, s.gstart));
     const int cb = p.idbits + 1;  // bits of an item code 2r + dir
     const int vbits = bits_for((uint64_t)(V > 1 ? V - 1 : 1));
     TK(c, "k_mkeys", k_mkeys<<<gEE, kBlock, 0, st>>>(o.isrc, o.idst, s.gflag, s.gpos, s.gstart, E, cb, s.mk));
@@ -571,12 +571,12 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
     bool in_b;
     DG_TRY(radix_sort(c, RadixBuffers{s.mk, s.mk2, nullptr, nullptr}, 2 * E, cb, cb + vbits, s.radix, &in_b));
     const unsigned long long *key = in_b ? s.mk2 : s.mk;
-    TK(c, "k_voffsets", k_voffsets<<<grid_for(2 * E + 1, kBlock, 65536), kBlock, 0, st>>>(key, 2 * E, V, cb, s.moff));
+    TK(c, "k_voffsets", k_voffsets<<<grid_for(2 * E + 1, kBlock, kStreamCap), kBlock, 0, st>>>(key, 2 * E, V, cb, s.moff));
     DG_TRY((device_scan<long long, SumI64, LoadOutBit, StoreI32>(c, LoadOutBit{key, 2 * E}, StoreI32{s.oidx},
                                                                  2 * E + 1, SumI64{}, 0ll, false, s.scan_tmp)));
-    TK(c, "k_moff_split", k_moff_split<<<grid_for(V + 1, kBlock, 65536), kBlock, 0, st>>>(s.moff, s.oidx, V, o.out_off,
+    TK(c, "k_moff_split", k_moff_split<<<grid_for(V + 1, kBlock, kStreamCap), kBlock, 0, st>>>(s.moff, s.oidx, V, o.out_off,
                                                                                         o.in_off));
-    TK(c, "k_munpack", k_munpack<<<grid_for(2 * E, kBlock, 65536), kBlock, 0, st>>>(
+    TK(c, "k_munpack", k_munpack<<<grid_for(2 * E, kBlock, kStreamCap), kBlock, 0, st>>>(
                            key, 2 * E, cb, s.moff, s.oidx, o.out_off, o.orig_of, o.it, o.out_t, o.out_id, o.out_r,
                            o.slot_out, o.pos_out, o.in_t, o.in_id, o.in_r, o.pos_in, s.in_head, o.brank, o.arank));
     // start of every in-list entry's tie group (the kNN window takes a crossing group's smallest ids)

@@ -294,13 +294,13 @@ dgec_status stage_dendro(Ctx *c, const Problem &p, const Csr &g, const Msf &m, D
     if (E == 0) return DGEC_OK;
     Arena a(scratch, SIZE_MAX);
     DScratch s = carve_dendro(a, p);
-    TK(c, "k_d_init", k_d_init<<<grid_for(E + n, kBlock, 65536), kBlock, 0, st>>>(
+    TK(c, "k_d_init", k_d_init<<<grid_for(E + n, kBlock, kStreamCap), kBlock, 0, st>>>(
                           E, n, m.ru, m.rv, g.orig_of, s.svpar, s.sroot, s.ssize, s.minr, s.tau,
                           o.parent, s.act, s.ecu, s.ecv));
     const int lb = p.idbits > 0 ? p.idbits : 1;
     const int sbits = bits_for((uint64_t)(n > 1 ? n - 1 : 1));
     if (n > 1) {
-        const int gn = grid_for(n, kBlock, 65536);
+        const int gn = grid_for(n, kBlock, kStreamCap);
         TK(c, "k_d_order_keys", k_d_order_keys<<<gn, kBlock, 0, st>>>(m.ru, n, sbits, s.k1));
         bool in_b;
         DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, nullptr, nullptr}, n, sbits, sbits + lb, s.radix, &in_b));
@@ -312,12 +312,12 @@ dgec_status stage_dendro(Ctx *c, const Problem &p, const Csr &g, const Msf &m, D
     for (int64_t round = 0; na > 0; round++) {
         if (round >= (1 << 16))
             return set_err(c, DGEC_ERR_TIMEOUT, "dendrogram rounds exceeded %d", 1 << 16);
-        const int g = grid_for(na, kBlock, 65536);
+        const int g = grid_for(na, kBlock, kStreamCap);
         TK(c, "k_d_bid", k_d_bid<<<g, kBlock, 0, st>>>(act, na, ecu, ecv, s.minr));
         TK(c, "k_d_ptr", k_d_ptr<<<g, kBlock, 0, st>>>(act, na, ecu, ecv, s.minr, s.gp));
         TK(c, "k_d_gjump", k_d_gjump<<<g, kBlock, 0, st>>>(act, na, ecu, ecv, s.minr, s.gp));
         TK(c, "k_d_tau", k_d_tau<<<g, kBlock, 0, st>>>(act, na, ecu, ecv, s.minr, s.gp, s.tau));
-        TK(c, "k_d_accept", k_d_accept<<<grid_for(na + 1, kBlock, 65536), kBlock, 0, st>>>(
+        TK(c, "k_d_accept", k_d_accept<<<grid_for(na + 1, kBlock, kStreamCap), kBlock, 0, st>>>(
                                 act, na, ecu, ecv, s.minr, s.gp, s.tau, s.flag));
         DG_TRY(exclusive_scan_i32(c, s.flag, s.pos, na + 1, s.scan_tmp));
         int64_t nacc;
@@ -327,7 +327,7 @@ dgec_status stage_dendro(Ctx *c, const Problem &p, const Csr &g, const Msf &m, D
         bool in_b;
         DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, s.v1, s.v2}, nacc, 0, lb + sbits, s.radix, &in_b));
         unsigned long long *key = in_b ? s.k2 : s.k1, *val = in_b ? s.v2 : s.v1;
-        const int ga = grid_for(nacc, kBlock, 65536);
+        const int ga = grid_for(nacc, kBlock, kStreamCap);
         TK(c, "k_d_chain", k_d_chain<<<ga, kBlock, 0, st>>>(key, val, nacc, E, sbits, ecu, ecv, s.minr, s.sroot,
                                                            s.ssize, o.a, o.b, o.parent, s.contrib, s.head));
         DG_TRY(segmented_inclusive_sum(c, s.contrib, s.head, s.csum, nacc, s.seg_tmp));

@@ -200,6 +200,7 @@ dgec_status run_pipeline(Ctx *c, const HostBatch &hb, const int32_t *d_src, cons
     p.gk = L.gk;
     p.gM = L.gM;
     p.egraph = L.egraph;
+    tl_stream_ctas = c->stream_ctas;
     stage_start(c);
     DG_STAGE("A incidence lists", stage_csr(c, p, L.csr, L.scratch));
     DG_STAGE("B skeleton and kNN", stage_skeleton(c, p, L.csr, L.skel, L.scratch));
@@ -221,7 +222,7 @@ dgec_status run_pipeline(Ctx *c, const HostBatch &hb, const int32_t *d_src, cons
     DG_STAGE("D1 dendrogram", stage_dendro(c, p, L.csr, L.msf, L.den, L.scratch));
     DG_STAGE("D2 condense and labels", stage_condense(c, p, L.msf, L.den, L.cond, L.scratch));
     if (p.G > 1 && L.msf.n > 0)
-        TK(c, "k_localize", k_localize<<<grid_for(L.msf.n, kBlock, 65536), kBlock, 0, c->stream>>>(
+        TK(c, "k_localize", k_localize<<<grid_for(L.msf.n, kBlock, kStreamCap), kBlock, 0, c->stream>>>(
                                 L.msf.n, p.E, L.msf.u, L.msf.v, L.den.a, L.den.b, p.egraph, p.eoff,
                                 L.msf.goff, L.lmu, L.lmv, L.lla, L.llb));
     CU_TRY(c, cudaStreamSynchronize(c->stream));
@@ -429,6 +430,24 @@ dgec_status dgec_kernel_timing(dgec_ctx *x, int i, const char **name, double *to
     return DGEC_OK;
 }
 
+dgec_status dgec_set_launch_config(dgec_ctx *x, const dgec_launch_config *cfg) {
+    if (!x || !cfg) return DGEC_ERR_INVALID_ARG;
+    if (cfg->knn_block != 64 && cfg->knn_block != 128 && cfg->knn_block != 256)
+        return set_err(&x->c, DGEC_ERR_INVALID_ARG, "knn_block must be 64, 128 or 256");
+    if (cfg->stream_ctas < 1 || cfg->stream_ctas > (1 << 20))
+        return set_err(&x->c, DGEC_ERR_INVALID_ARG, "stream_ctas must be in [1, 2^20]");
+    x->c.knn_block = cfg->knn_block;
+    x->c.stream_ctas = cfg->stream_ctas;
+    return DGEC_OK;
+}
+
+dgec_status dgec_get_launch_config(const dgec_ctx *x, dgec_launch_config *cfg) {
+    if (!x || !cfg) return DGEC_ERR_INVALID_ARG;
+    cfg->knn_block = x->c.knn_block;
+    cfg->stream_ctas = (int32_t)x->c.stream_ctas;
+    return DGEC_OK;
+}
+
 dgec_status dgec_stage_timing(const dgec_ctx *x, int i, const char **name, double *ms) {
     if (!x) return DGEC_ERR_INVALID_ARG;
     const StageTimer &t = x->c.stages;
@@ -609,6 +628,7 @@ dgec_status dgec_run_levels(dgec_ctx *x, const int32_t *d_src, const int32_t *d_
     p.gk = L.gk;
     p.gM = L.gM;
     p.egraph = L.egraph;
+    tl_stream_ctas = c->stream_ctas;
     stage_start(c);
     DG_STAGE("A incidence lists", stage_csr(c, p, L.csr, L.scratch));
     DG_STAGE("B skeleton and kNN", stage_skeleton(c, p, L.csr, L.skel, L.scratch));

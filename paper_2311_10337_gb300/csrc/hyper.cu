@@ -304,7 +304,7 @@ static dgec_status build_lists(Ctx *c, const HyperProblem &h, const int64_t *off
     TK(c, "k_h_scatter", k_h_scatter<<<grid_for(M, kBlock, (int64_t)c->num_sms * 16), kBlock, 0, st>>>(
                              off, h.E, vert, M, g.rank_of, L.voff, deg, s.k1, L.vx));
     DG_TRY(sort_segments(c, V, s.k1, L.voff, s.seg, idbits));
-    TK(c, "k_h_unpack", k_h_unpack<<<grid_for(M, kBlock, 65536), kBlock, 0, st>>>(s.k1, M, g.orig_of, g.it, L, s.f));
+    TK(c, "k_h_unpack", k_h_unpack<<<grid_for(M, kBlock, kStreamCap), kBlock, 0, st>>>(s.k1, M, g.orig_of, g.it, L, s.f));
     return DGEC_OK;
 }
 
@@ -318,9 +318,9 @@ dgec_status stage_hyper(Ctx *c, Problem &p, const HyperProblem &h, Csr &g, Hyper
     TK(c, "k_h_init_flags", k_h_init_flags<<<1, 1, 0, st>>>(s.f));
     CU_TRY(c, cudaMemsetAsync(s.deg_s, 0, sizeof(int) * (V + 1), st));
     CU_TRY(c, cudaMemsetAsync(s.deg_d, 0, sizeof(int) * (V + 1), st));
-    TK(c, "k_h_check_off", k_h_check_off<<<grid_for(E + 1, kBlock, 65536), kBlock, 0, st>>>(h.s_off, E, h.Ms, s.f));
+    TK(c, "k_h_check_off", k_h_check_off<<<grid_for(E + 1, kBlock, kStreamCap), kBlock, 0, st>>>(h.s_off, E, h.Ms, s.f));
     if (h.directed)
-        TK(c, "k_h_check_off", k_h_check_off<<<grid_for(E + 1, kBlock, 65536), kBlock, 0, st>>>(h.d_off, E, h.Md, s.f));
+        TK(c, "k_h_check_off", k_h_check_off<<<grid_for(E + 1, kBlock, kStreamCap), kBlock, 0, st>>>(h.d_off, E, h.Md, s.f));
     if (h.Ms > 0)
         TK(c, "k_h_count", k_h_count<<<grid_for(h.Ms, kBlock, (int64_t)c->num_sms * 16), kBlock, 0, st>>>(
                                h.s_vert, h.Ms, V, s.deg_s, s.f));
@@ -345,7 +345,7 @@ dgec_status stage_hyper(Ctx *c, Problem &p, const HyperProblem &h, Csr &g, Hyper
         return DGEC_OK;
     }
     // hyperedges in (t, id) order: internal ids
-    const int gE = grid_for(E, kBlock, 65536);
+    const int gE = grid_for(E, kBlock, kStreamCap);
     TK(c, "k_h_pack", k_h_pack<<<gE, kBlock, 0, st>>>(h.t, E, p.tmin, p.idbits, s.k1));
     {
         bool in_b;
@@ -364,12 +364,12 @@ dgec_status stage_hyper(Ctx *c, Problem &p, const HyperProblem &h, Csr &g, Hyper
         return DGEC_OK;
     }
     if (!h.directed) {
-        TK(c, "k_h_path", k_h_path<<<grid_for(h.Ms, kBlock, 65536), kBlock, 0, st>>>(S, h.Ms, p.idbits, s.k1));
+        TK(c, "k_h_path", k_h_path<<<grid_for(h.Ms, kBlock, kStreamCap), kBlock, 0, st>>>(S, h.Ms, p.idbits, s.k1));
     } else {
         if (h.Md > 0)
-            TK(c, "k_h_type1", k_h_type1<<<grid_for(h.Md, kBlock, 65536), kBlock, 0, st>>>(D, h.Md, S, p.idbits, s.k1));
+            TK(c, "k_h_type1", k_h_type1<<<grid_for(h.Md, kBlock, kStreamCap), kBlock, 0, st>>>(D, h.Md, S, p.idbits, s.k1));
         if (h.Ms > 0)
-            TK(c, "k_h_type2", k_h_type2<<<grid_for(h.Ms, kBlock, 65536), kBlock, 0, st>>>(D, S, h.Ms, h.Md, p.idbits,
+            TK(c, "k_h_type2", k_h_type2<<<grid_for(h.Ms, kBlock, kStreamCap), kBlock, 0, st>>>(D, S, h.Ms, h.Md, p.idbits,
                                                                                       s.k1, s.f));
     }
     DG_TRY(read_counters(c, (const int64_t *)s.f, kHFlags, f));
@@ -379,9 +379,9 @@ dgec_status stage_hyper(Ctx *c, Problem &p, const HyperProblem &h, Csr &g, Hyper
     bool in_b;
     DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, nullptr, nullptr}, L, 0, 2 * p.idbits, s.radix, &in_b));
     const unsigned long long *lk = in_b ? s.k2 : s.k1;
-    TK(c, "k_h_uflag", k_h_uflag<<<grid_for(L + 1, kBlock, 65536), kBlock, 0, st>>>(lk, L, s.flag));
+    TK(c, "k_h_uflag", k_h_uflag<<<grid_for(L + 1, kBlock, kStreamCap), kBlock, 0, st>>>(lk, L, s.flag));
     DG_TRY(exclusive_scan_i32(c, s.flag, s.pos, L + 1, s.scan_tmp));
-    TK(c, "k_h_links", k_h_links<<<grid_for(L, kBlock, 65536), kBlock, 0, st>>>(lk, L, s.flag, s.pos, p.idbits,
+    TK(c, "k_h_links", k_h_links<<<grid_for(L, kBlock, kStreamCap), kBlock, 0, st>>>(lk, L, s.flag, s.pos, p.idbits,
                                                                                g.orig_of, g.it, sk));
     int64_t n;
     DG_TRY(read_counters(c, (const int64_t *)(s.pos + L), 1, &n));
@@ -532,6 +532,7 @@ dgec_status dgec_run_hyper(dgec_ctx *x, const int64_t *d_t, int64_t n_hyperedges
     p.gk = L.gk;
     p.gM = L.gM;
     p.egraph = L.egraph;
+    tl_stream_ctas = c->stream_ctas;
     stage_start(c);
     DG_STAGE("H hypergraph skeleton", stage_hyper(c, p, h, L.csr, L.S, L.D, L.skel, L.scratch));
     DG_STAGE("C spanning forest", stage_msf(c, p, L.csr, L.skel, L.msf, L.scratch));

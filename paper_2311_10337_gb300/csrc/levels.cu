@@ -282,16 +282,16 @@ dgec_status stage_levels(Ctx *c, const Problem &p, const Csr &g, const Skel &sk,
     }
     Arena a(scratch, SIZE_MAX);
     LvScratch s = carve_levels(a, p);
-    const int gE = grid_for(E, kBlock, 65536);
+    const int gE = grid_for(E, kBlock, kStreamCap);
     TK(c, "k_lv_init", k_lv_init<<<gE, kBlock, 0, st>>>(E, s.par, o.mlevel, o.mparent, q, s.tot, s.snap, s.err));
     if (n > 0) {
-        const int gn = grid_for(n, kBlock, 65536);
+        const int gn = grid_for(n, kBlock, kStreamCap);
         TK(c, "k_lv_keys", k_lv_keys<<<gn, kBlock, 0, st>>>(sk.w, sk.ru, sk.rv, sk.u, g.orig_of, n, o.omega, q,
                                                            s.k1, s.v1));
         bool in_b;
         DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, s.v1, s.v2}, n, 0, bits_for(q), s.radix, &in_b));
         const unsigned long long *key = in_b ? s.k2 : s.k1, *val = in_b ? s.v2 : s.v1;
-        TK(c, "k_lv_bounds", k_lv_bounds<<<grid_for(n + 1, kBlock, 65536), kBlock, 0, st>>>(key, n, q, s.boff));
+        TK(c, "k_lv_bounds", k_lv_bounds<<<grid_for(n + 1, kBlock, kStreamCap), kBlock, 0, st>>>(key, n, q, s.boff));
         // hook kernels read their bucket bounds on the device: no host round trip per level
         const int gh = c->num_sms * 8;
         for (int l = 0; l < q; l++) {
@@ -331,12 +331,12 @@ dgec_status build_level_rows(Ctx *c, const Problem &p, const Csr &g, Levels &o, 
     }
     Arena a(scratch, SIZE_MAX);
     LvScratch s = carve_levels(a, p);
-    const int gE = grid_for(E, kBlock, 65536);
+    const int gE = grid_for(E, kBlock, kStreamCap);
     TK(c, "k_lv_row_keys", k_lv_row_keys<<<gE, kBlock, 0, st>>>(E, o.mlevel, s.k1));
     bool in_b;
     DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, nullptr, nullptr}, E, 32, 32 + bits_for(o.q), s.radix, &in_b));
     const unsigned long long *key = in_b ? s.k2 : s.k1;
-    TK(c, "k_lv_rows", k_lv_rows<<<grid_for(o.rows.n > 0 ? o.rows.n : 1, kBlock, 65536), kBlock, 0, st>>>(
+    TK(c, "k_lv_rows", k_lv_rows<<<grid_for(o.rows.n > 0 ? o.rows.n : 1, kBlock, kStreamCap), kBlock, 0, st>>>(
                            key, E - o.rows.n, o.rows.n, o.mparent, g.rank_of, o.omega, o.rows));
     return DGEC_OK;
 }

@@ -120,13 +120,13 @@ dgec_status stage_mrd(Ctx *c, const Problem &p, const Csr &g, const Skel &sk, Sk
     if (L > link_cap(p)) return set_err(c, DGEC_ERR_INTERNAL, "mutual-reachability graph over capacity");
     Arena a(scratch, SIZE_MAX);
     MrdScratch s = carve_mrd(a, p);
-    const int gL = grid_for(L, kBlock, 65536);
+    const int gL = grid_for(L, kBlock, kStreamCap);
     TK(c, "k_mrd_keys", k_mrd_keys<<<gL, kBlock, 0, st>>>(sk.ru, sk.rv, sk.n, sk.knn, E, p.k, g.rank_of, p.idbits,
                                                          s.k1));
     bool in_b;
     DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, nullptr, nullptr}, L, 0, 2 * p.idbits, s.radix, &in_b));
     const unsigned long long *key = in_b ? s.k2 : s.k1;
-    TK(c, "k_mrd_flag", k_mrd_flag<<<grid_for(L + 1, kBlock, 65536), kBlock, 0, st>>>(key, L, p.idbits, g.orig_of,
+    TK(c, "k_mrd_flag", k_mrd_flag<<<grid_for(L + 1, kBlock, kStreamCap), kBlock, 0, st>>>(key, L, p.idbits, g.orig_of,
                                                                                     g.it, sk.core, s.flag));
     DG_TRY(exclusive_scan_i32(c, s.flag, s.pos, L + 1, s.scan_tmp));
     TK(c, "k_mrd_emit", k_mrd_emit<<<gL, kBlock, 0, st>>>(key, L, s.flag, s.pos, p.idbits, g.orig_of, g.it, sk.core,

@@ -452,7 +452,7 @@ dgec_status stage_msf(Ctx *c, const Problem &p, const Csr &g, const Skel &sk, Ms
     if (E == 0 || sk.n == 0) return DGEC_OK;
     Arena a(scratch, SIZE_MAX);
     MsfScratch s = carve_msf(a, p);
-    const int gE = grid_for(E, kBlock, 65536);
+    const int gE = grid_for(E, kBlock, kStreamCap);
     TK(c, "k_m_init", k_m_init<<<gE, kBlock, 0, st>>>(E, s.par, s.roots, s.bw, s.buv));
     CU_TRY(c, cudaMemsetAsync(s.cnt, 0, 4 * sizeof(unsigned long long), st));
     // live edges: (cu, cv) component labels, (u, v) original ends, w; the
@@ -465,13 +465,13 @@ dgec_status stage_msf(Ctx *c, const Problem &p, const Csr &g, const Skel &sk, Ms
     for (int round = 0;; round++) {
         if (round >= 64) return set_err(c, DGEC_ERR_TIMEOUT, "Boruvka did not finish in 64 rounds");
         if (round == 0) {
-            TK(c, "k_m_bid", k_m_bid<<<grid_for(n, kBlock, 65536), kBlock, 0, st>>>(ccu, ccv, cw, n, s.bw));
+            TK(c, "k_m_bid", k_m_bid<<<grid_for(n, kBlock, kStreamCap), kBlock, 0, st>>>(ccu, ccv, cw, n, s.bw));
         } else {
             int32_t *ncu = which ? s.cub : s.cua, *ncv = which ? s.cvb : s.cva;
             int32_t *nu = which ? s.ub : s.ua, *nv = which ? s.vb : s.va;
             int64_t *nw = which ? s.wb : s.wa;
             CU_TRY(c, cudaMemsetAsync(s.cnt, 0, sizeof(unsigned long long), st));
-            TK(c, "k_m_filter_bid", k_m_filter_bid<<<grid_for(n, kBlock, 65536), kBlock, 0, st>>>(
+            TK(c, "k_m_filter_bid", k_m_filter_bid<<<grid_for(n, kBlock, kStreamCap), kBlock, 0, st>>>(
                                       ccu, ccv, cu, cv, cw, n, s.par, ncu, ncv, nu, nv, nw, s.cnt, s.bw));
             int64_t h[3];
             DG_TRY(read_counters(c, (const int64_t *)s.cnt, 3, h));
@@ -485,7 +485,7 @@ dgec_status stage_msf(Ctx *c, const Problem &p, const Csr &g, const Skel &sk, Ms
             cw = nw;
             which ^= 1;
         }
-        const int gn = grid_for(n, kBlock, 65536), gr = grid_for(nr, kBlock, 65536);
+        const int gn = grid_for(n, kBlock, kStreamCap), gr = grid_for(nr, kBlock, kStreamCap);
         TK(c, "k_m_bid_uv", k_m_bid_uv<<<gn, kBlock, 0, st>>>(ccu, ccv, cu, cv, cw, n, s.bw, s.buv));
         TK(c, "k_m_claim", k_m_claim<<<gn, kBlock, 0, st>>>(ccu, ccv, cu, cv, n, s.buv, s.bp, s.win));
         TK(c, "k_m_hook", k_m_hook<<<gr, kBlock, 0, st>>>(roots, nr, s.bw, s.buv, s.bp, s.win, cu, cv, cw,
@@ -505,7 +505,7 @@ dgec_status stage_msf(Ctx *c, const Problem &p, const Csr &g, const Skel &sk, Ms
     if (m == 0) return DGEC_OK;
     // order by (w, u, v): stable radix by the packed original ends, then by w,
     // then (batches) by graph, carrying the edge index; then gather columns
-    int gm = grid_for(m, kBlock, 65536);
+    int gm = grid_for(m, kBlock, kStreamCap);
     unsigned long long *K[2] = {s.k1, s.k2}, *Vb[2] = {s.v1, s.v2};
     int cur = 0;
     bool in_b;

@@ -145,7 +145,7 @@ size_t nc_scratch_bytes(const Problem &p) {
 
 dgec_status stage_nc_negate(Ctx *c, const Problem &p, int64_t *tn) {
     if (p.E > 0)
-        TK(c, "k_nc_negate", k_nc_negate<<<grid_for(p.E, kBlock, 65536), kBlock, 0, c->stream>>>(p.t, p.E, tn));
+        TK(c, "k_nc_negate", k_nc_negate<<<grid_for(p.E, kBlock, kStreamCap), kBlock, 0, c->stream>>>(p.t, p.E, tn));
     return DGEC_OK;
 }
 
@@ -158,16 +158,16 @@ dgec_status stage_nc(Ctx *c, const Problem &p, const Csr &g, const Skel &s1, con
     if (L > 4 * E) return set_err(c, DGEC_ERR_INTERNAL, "nearly-causal skeleton over capacity");
     Arena a(scratch, SIZE_MAX);
     NcScratch s = carve_nc(a, p);
-    TK(c, "k_nc_knn", k_nc_knn<<<grid_for(E, kBlock, 65536), kBlock, 0, st>>>(E, p.k, p.t, s1.knn, s2.knn, p.dnc,
+    TK(c, "k_nc_knn", k_nc_knn<<<grid_for(E, kBlock, kStreamCap), kBlock, 0, st>>>(E, p.k, p.t, s1.knn, s2.knn, p.dnc,
                                                                              h.knn, h.core));
     if (L == 0) return DGEC_OK;
-    const int gL = grid_for(L, kBlock, 65536);
+    const int gL = grid_for(L, kBlock, kStreamCap);
     TK(c, "k_nc_keys", k_nc_keys<<<gL, kBlock, 0, st>>>(s1.u, s1.v, s1.n, s2.u, s2.v, s2.w, s2.n, p.dnc, p.idbits,
                                                        s.k1));
     bool in_b;
     DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, nullptr, nullptr}, L, 0, 2 * p.idbits, s.radix, &in_b));
     const unsigned long long *key = in_b ? s.k2 : s.k1;
-    TK(c, "k_nc_flag", k_nc_flag<<<grid_for(L + 1, kBlock, 65536), kBlock, 0, st>>>(key, L, s.flag));
+    TK(c, "k_nc_flag", k_nc_flag<<<grid_for(L + 1, kBlock, kStreamCap), kBlock, 0, st>>>(key, L, s.flag));
     DG_TRY(exclusive_scan_i32(c, s.flag, s.pos, L + 1, s.scan_tmp));
     TK(c, "k_nc_emit", k_nc_emit<<<gL, kBlock, 0, st>>>(key, L, s.flag, s.pos, p.idbits, g.rank_of, p.t, h));
     int64_t n;

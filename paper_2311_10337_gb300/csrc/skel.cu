@@ -141,7 +141,7 @@ __device__ __forceinline__ bool cand_less(const Cand &a, const Cand &b) {
 }
 
 template <int K>
-__global__ void __launch_bounds__(128) k_knn(const int32_t *src, const int32_t *dst, const int64_t *t,
+__global__ void __launch_bounds__(256) k_knn(const int32_t *src, const int32_t *dst, const int64_t *t,
                                              const int32_t *orig_of, int64_t E, const int64_t *out_off,
                                              const int64_t *out_t, const int32_t *out_id,
                                              const int64_t *in_off, const int64_t *in_t,
@@ -279,24 +279,25 @@ dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void
     Arena a(scratch, SIZE_MAX);
     SkScratch s = carve_skel(a, p);
     int64_t E = p.E;
-    int grid = grid_for(E, 128, 1 << 20);
+    const int kb = c->knn_block;
+    int grid = grid_for(E, kb, 1 << 20);
     o.brank = g.brank;
     o.arank = g.arank;
 #define KNN_ARGS                                                                                   \
     g.isrc, g.idst, g.it, g.orig_of, E, g.out_off, g.out_t, g.out_id, g.in_off, g.in_t, g.in_id, g.in_gs, \
         g.brank, g.arank, p.G, p.egraph, p.eoff, p.gk, p.knn_off, p.dmax, o.knn, o.core
     if (p.knn) {
-        if (p.k <= 4) TK(c, "k_knn", k_knn<4><<<grid, 128, 0, st>>>(KNN_ARGS));
-        else if (p.k <= 8) TK(c, "k_knn", k_knn<8><<<grid, 128, 0, st>>>(KNN_ARGS));
-        else TK(c, "k_knn", k_knn<16><<<grid, 128, 0, st>>>(KNN_ARGS));
+        if (p.k <= 4) TK(c, "k_knn", k_knn<4><<<grid, kb, 0, st>>>(KNN_ARGS));
+        else if (p.k <= 8) TK(c, "k_knn", k_knn<8><<<grid, kb, 0, st>>>(KNN_ARGS));
+        else TK(c, "k_knn", k_knn<16><<<grid, kb, 0, st>>>(KNN_ARGS));
     }
 #undef KNN_ARGS
     SkView v{g.isrc, g.idst, g.out_off, g.in_off, g.out_r, g.in_r, g.slot_out, o.brank, o.arank};
-    TK(c, "k_links", k_links<<<grid_for(E, kBlock, 65536), kBlock, 0, st>>>(v, g.it, g.out_t, g.in_t, E, p.dmax,
+    TK(c, "k_links", k_links<<<grid_for(E, kBlock, kStreamCap), kBlock, 0, st>>>(v, g.it, g.out_t, g.in_t, E, p.dmax,
                                                                           s.part, s.wgt, s.flag));
     TK(c, "k_zero_i32", k_zero_i32<<<1, 1, 0, st>>>(s.flag + 2 * E));
     DG_TRY(exclusive_scan_i32(c, s.flag, s.pos, 2 * E + 1, s.scan_tmp));
-    TK(c, "k_compact_links", k_compact_links<<<grid_for(2 * E, kBlock, 65536), kBlock, 0, st>>>(
+    TK(c, "k_compact_links", k_compact_links<<<grid_for(2 * E, kBlock, kStreamCap), kBlock, 0, st>>>(
                                  s.part, s.wgt, s.flag, s.pos, E, g.orig_of, o.ru, o.rv, o.u, o.v, o.w));
     int64_t n;
     DG_TRY(read_counters(c, (const int64_t *)(s.pos + 2 * E), 1, &n));

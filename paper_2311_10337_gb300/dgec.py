@@ -23,7 +23,8 @@ STATUS = {0: "DGEC_OK", 1: "DGEC_ERR_INVALID_ARG", 2: "DGEC_ERR_VERTEX_RANGE",
 
 EXPORTS = ["dgec_create", "dgec_destroy", "dgec_last_error", "dgec_status_string",
            "dgec_workspace_size", "dgec_run", "dgec_run_host", "dgec_last_launch_count",
-           "dgec_set_kernel_timing", "dgec_kernel_timing", "dgec_stage_timing", "dgec_msf_static",
+           "dgec_set_kernel_timing", "dgec_kernel_timing", "dgec_stage_timing", "dgec_set_launch_config",
+           "dgec_get_launch_config", "dgec_msf_static",
            "dgec_batch_workspace_size", "dgec_run_batch", "dgec_server_create", "dgec_submit",
            "dgec_wait", "dgec_server_lane_capacity", "dgec_server_destroy",
            "dgec_levels_workspace_size", "dgec_run_levels", "dgec_hyper_workspace_size",
@@ -31,6 +32,10 @@ EXPORTS = ["dgec_create", "dgec_destroy", "dgec_last_error", "dgec_status_string
 
 LEVELS_DENSE = 1
 MAX_LEVELS = 64
+
+
+class LaunchConfig(ctypes.Structure):
+    _fields_ = [("knn_block", ctypes.c_int32), ("stream_ctas", ctypes.c_int32)]
 
 
 class DgecError(RuntimeError):
@@ -139,6 +144,8 @@ def load(path: str = LIB_PATH):
                                      ctypes.POINTER(ctypes.c_int64)]
     L.dgec_stage_timing.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
                                     ctypes.POINTER(ctypes.c_double)]
+    L.dgec_set_launch_config.argtypes = [_P, ctypes.POINTER(LaunchConfig)]
+    L.dgec_get_launch_config.argtypes = [_P, ctypes.POINTER(LaunchConfig)]
     I64A = ctypes.POINTER(ctypes.c_int64)
     I32A = ctypes.POINTER(ctypes.c_int32)
     L.dgec_batch_workspace_size.argtypes = [ctypes.c_int32, I64A, I32A, I32A, I32A,
@@ -317,6 +324,16 @@ class Context:
             i += 1
         return out
 
+    def set_launch_config(self, knn_block: int, stream_ctas: int):
+        """Threads per CTA of the kNN kernel and CTAs of the grid-stride
+        streaming kernels for the calls on this context (speed only)."""
+        self._check(self.L.dgec_set_launch_config(self.h, ctypes.byref(LaunchConfig(knn_block, stream_ctas))))
+
+    def launch_config(self) -> tuple:
+        c = LaunchConfig()
+        self._check(self.L.dgec_get_launch_config(self.h, ctypes.byref(c)))
+        return int(c.knn_block), int(c.stream_ctas)
+
     def stage_timing(self) -> list:
         """[(stage name, device ms)] of the last completed call, in order."""
         out = []
@@ -404,6 +421,39 @@ class Context:
         """Batched Alg. 4 over graphs laid end to end on the device; tables are
         host arrays (edge_off[G+1] starting at 0, n_vertices/k/M per graph)."""
         return _run_batch(self, src, dst, t, edge_off, n_vertices, k, min_cluster_size, stream)
+
+    def run_batch_passes(self, src, dst, t, edge_off, n_vertices, k, min_cluster_size, max_edges: int,
+                         labels_out, stream=None):
+        """Every graph of a batch too large for one workspace, in passes of
+        consecutive graphs holding at most max_edges edges (a larger graph
+        gets a pass of its own). Graph g's labels land in labels_out (device
+        int32[total]) at edge_off[g], exactly as dgec_run_batch (or dgec_run)
+        gives them for that graph alone. Returns (n_clusters per graph as a
+        host array, number of passes)."""
+        torch = self.torch
+        eo = np.ascontiguousarray(edge_off, np.int64)
+        G = len(eo) - 1
+        total = int(eo[-1]) if G >= 0 else 0
+        _dev("labels_out", labels_out, torch.int32, total, self.device)
+        nv = np.ascontiguousarray(n_vertices, np.int32)
+        kk = np.ascontiguousarray(k, np.int32)
+        mm = np.ascontiguousarray(min_cluster_size, np.int32)
+        ncl = np.zeros(max(G, 0), np.int32)
+        passes = 0
+        g0 = 0
+        while g0 < G:
+            g1 = int(np.searchsorted(eo, eo[g0] + int(max_edges), side="right")) - 1
+            g1 = min(max(g1, g0 + 1), G)
+            a, b = int(eo[g0]), int(eo[g1])
+            out = _run_batch(self, src[a:b], dst[a:b], t[a:b], eo[g0:g1 + 1] - a, nv[g0:g1], kk[g0:g1],
+                             mm[g0:g1], stream)
+            st = self._stream(stream, out.t["labels"])
+            with torch.cuda.stream(st):
+                labels_out[a:b].copy_(out.t["labels"])
+                ncl[g0:g1] = out.t["n_clusters"].cpu().numpy()
+            passes += 1
+            g0 = g1
+        return ncl, passes
 
     def run_host(self, src: np.ndarray, dst: np.ndarray, t: np.ndarray, n_vertices: int, k: int,
                  min_cluster_size: int, labels_out: np.ndarray | None = None, stream=None,

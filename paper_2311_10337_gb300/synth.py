@@ -102,6 +102,14 @@ class Stream:
         """Doubles in [0, 1) from the top 53 bits."""
         return (self.u64(n) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
 
+    def uniform_at(self, pos: int, n: int) -> np.ndarray:
+        """The n doubles a fresh stream would give from draw `pos` on (the
+        stream's own position is not moved)."""
+        idx = np.arange(pos + 1, pos + n + 1, dtype=np.uint64)
+        with np.errstate(over="ignore"):
+            z = _mix(self.state + idx * _GOLD)
+        return (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
     def integers(self, lo: int, hi: int, n: int) -> np.ndarray:
         """Integers in [lo, hi)."""
         span = hi - lo
@@ -162,29 +170,33 @@ def _dedupe_triples(src, dst, t):
     pair that has a repeat, times are made strictly increasing by moving a
     repeat to one second after its predecessor. The edges are ordered by
     (pair, t, position) with two stable sorts; a pair has a repeat when two
-    neighbours in that order share (pair, t)."""
-    pair = ((src.astype(np.uint64) << np.uint64(32)) | dst.astype(np.uint64)).view(np.int64)
-    by_t = _argsort_i64(t)
-    o = by_t[_argsort_i64(pair[by_t])]
-    pk, tt = pair[o], t[o]
+    neighbours in that order share (pair, t). The full-size steps run as
+    torch CPU ops (multi-threaded); the pairs with repeats in numpy."""
+    import torch
+    S = torch.from_numpy(np.ascontiguousarray(src, np.int64))
+    D = torch.from_numpy(np.ascontiguousarray(dst, np.int64))
+    T = torch.from_numpy(np.ascontiguousarray(t, np.int64))
+    pair = (S << 32) | D
+    by_t = torch.sort(T, stable=True).indices
+    o = by_t[torch.sort(pair[by_t], stable=True).indices]
+    pk, tt = pair[o], T[o]
     rep = (pk[1:] == pk[:-1]) & (tt[1:] == tt[:-1])
-    if not rep.any():
+    if not bool(rep.any()):
         return t
-    head = np.ones(len(o), bool)
+    head = torch.ones(len(o), dtype=torch.bool)
     head[1:] = pk[1:] != pk[:-1]
-    gid_all = np.cumsum(head) - 1
-    bad = np.zeros(int(gid_all[-1]) + 1, bool)
+    gid_all = torch.cumsum(head, 0) - 1
+    bad = torch.zeros(int(gid_all[-1]) + 1, dtype=torch.bool)
     bad[gid_all[1:][rep]] = True
     sel = bad[gid_all]
-    o, pk, tt = o[sel], pk[sel], tt[sel]
-    head = head[sel]
+    o, tt, head = o[sel].numpy(), tt[sel].numpy(), head[sel].numpy()
     gid = np.cumsum(head) - 1
     start = np.nonzero(head)[0]
     r = np.arange(len(o)) - start[gid]
     big = np.int64(1) << np.int64(40)
     v = (tt - tt.min()) - r + gid.astype(np.int64) * big
     v = np.maximum.accumulate(v)
-    t = t.copy()
+    t = np.array(t, np.int64, copy=True)
     t[o] = v - gid.astype(np.int64) * big + r + tt.min()
     return t
 
@@ -329,6 +341,52 @@ def hub(scale: float = 1.0, seed_offset: int = 0, k: int = 8,
                     f"E={n_edges} V={n_vertices} bg=50% zipf=1.8 t%60==0, conv=40%, replay=10% hourly")
 
 
+def stream(scale: float = 6.0, days: int = 180, seed_offset: int = 0, k: int = 8,
+           min_cluster_size: int = 5) -> Workload:
+    """The serving stream: drawn as mid (70% planted conversations, 30%
+    Zipf(2.1) background) at `scale` times its size -- 300M edges over 6M
+    vertices at scale 6 -- over a `days`-day span, returned in (t, id)
+    order (a stable sort of the drawn edges by time)."""
+    seed = BASE_SEED + 4 + 1000 * seed_offset
+    n_edges = int(round(50_000_000 * scale))
+    n_vertices = max(64, int(round(1_000_000 * scale)))
+    span = days * 86400
+    n_conv = int(round(0.7 * n_edges))
+    n_bg = n_edges - n_conv
+    cs, cd, ct, _ = _conversations(Stream(seed, 11), n_conv, n_vertices, span)
+    perm = _permutation(Stream(seed, 12), n_vertices)
+    bs, bd = _zipf_endpoints(Stream(seed, 13), n_bg, n_vertices, 2.1, perm)
+    bt = Stream(seed, 14).integers(0, span, n_bg)
+    src = np.concatenate([cs, bs])
+    del cs, bs
+    dst = np.concatenate([cd, bd])
+    del cd, bd
+    t = np.concatenate([ct, bt])
+    del ct, bt
+    order = _permutation(Stream(seed, 15), n_edges)
+    src, dst, t = src[order], dst[order], t[order]
+    t = _dedupe_triples(src, dst, t)
+    by_t = _argsort_i64(t)
+    return Workload("stream", src[by_t].astype(np.int32), dst[by_t].astype(np.int32), t[by_t],
+                    n_vertices, k, min_cluster_size,
+                    f"E={n_edges} V={n_vertices} span={days}d conv=70% bg=30% zipf=2.1, (t, id) order")
+
+
+def serve_jobs(n_jobs: int, n_stream: int, rate: float, log10_min: float = 4.0,
+               log10_max: float = 7.0, seed_offset: int = 0):
+    """Windowed clustering jobs over a stream of n_stream edges: window sizes
+    round(10^U(log10_min, log10_max)) edges (at most the stream), uniform
+    starts, Poisson arrivals at `rate` per second. Returns (starts, sizes,
+    arrival times in s)."""
+    st = Stream(BASE_SEED + 6 + 1000 * seed_offset, 61)
+    sizes = np.round(10.0 ** (log10_min + (log10_max - log10_min) * st.uniform(n_jobs))).astype(np.int64)
+    sizes = np.clip(sizes, 1, n_stream)
+    starts = np.floor(st.uniform(n_jobs) * (n_stream - sizes + 1)).astype(np.int64)
+    starts = np.minimum(starts, n_stream - sizes)
+    gaps = -np.log1p(-st.uniform(n_jobs)) / rate
+    return starts, sizes, np.cumsum(gaps)
+
+
 def random_small(n_edges: int, n_vertices: int, t_max: int, seed: int,
                  zipf_s: float = 0.0) -> Workload:
     """Small tie-heavy graphs for brute-force checks (t uniform in [0, t_max))."""
@@ -369,14 +427,29 @@ class Batch:
         return self.src[a:b], self.dst[a:b], self.t[a:b]
 
 
+def _graph_chunks(eoff: np.ndarray, max_edges: int = 1 << 25):
+    """Consecutive graph ranges [g0, g1) of at most max_edges edges each
+    (a single larger graph forms a range of its own)."""
+    G = len(eoff) - 1
+    g0 = 0
+    while g0 < G:
+        g1 = int(np.searchsorted(eoff, eoff[g0] + max_edges, side="right")) - 1
+        g1 = min(max(g1, g0 + 1), G)
+        yield g0, g1
+        g0 = g1
+
+
 def batch(n_graphs: int = 4096, log10_min: float = 3.0, log10_max: float = 6.0,
           seed_offset: int = 0, t_max: int = 1_000_000, zipf_s: float = 2.1) -> Batch:
     """The batching workload: E_b = round(10^U(log10_min, log10_max)) edges,
     V_b = max(2, E_b // 10) vertices, each graph drawn like the tiny one at
     its own size (rank-Zipf(2.1) endpoints, t uniform in [0, t_max)),
-    k_b uniform in {4, 8, 16}, M = 5. All graphs are drawn at once: one
-    inverse-CDF table serves every graph (a rank-Zipf law over V_b ranks is
-    the global law conditioned on rank <= V_b)."""
+    k_b uniform in {4, 8, 16}, M = 5. One inverse-CDF table serves every
+    graph (a rank-Zipf law over V_b ranks is the global law conditioned on
+    rank <= V_b). Draw n of a stream belongs to edge n of the batch, so the
+    graphs are drawn in chunks of whole graphs with bounded host memory; a
+    repeated triple can only repeat within one graph, so the repeats are
+    resolved chunk by chunk."""
     seed = BASE_SEED + 3 + 1000 * seed_offset
     st = Stream(seed, 41)
     sizes = np.round(10.0 ** (log10_min + (log10_max - log10_min) * st.uniform(n_graphs)))
@@ -385,31 +458,56 @@ def batch(n_graphs: int = 4096, log10_min: float = 3.0, log10_max: float = 6.0,
     k = np.array([4, 8, 16], np.int32)[st.integers(0, 3, n_graphs)]
     eoff = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
     total = int(eoff[-1])
-    gid = np.repeat(np.arange(n_graphs), sizes)
     vmax = int(nv.max())
     r = np.arange(1, vmax + 1, dtype=np.float64)
     cdf = np.cumsum(r ** (-zipf_s))
     cap = cdf[nv - 1]  # mass of ranks 1..V_b
+    chunks = list(_graph_chunks(eoff))
 
-    def draw(stream):
-        u = stream.uniform(total) * cap[gid]
-        return np.minimum(_searchsorted_right(cdf, u), nv[gid] - 1).astype(np.int64)
+    def gid_of(g0, g1):
+        return np.repeat(np.arange(g0, g1), sizes[g0:g1])
 
-    s_src, s_dst = Stream(seed, 42), Stream(seed, 43)
-    src = draw(s_src)
-    dst = draw(s_dst)
+    s_src, s_dst, s_t = Stream(seed, 42), Stream(seed, 43), Stream(seed, 44)
+    src = np.empty(total, np.int64)
+    dst = np.empty(total, np.int64)
+
+    def endpoints(ch):  # each chunk fills its own slice: the order of chunks does not matter
+        g0, g1 = ch
+        a, b = int(eoff[g0]), int(eoff[g1])
+        gid = gid_of(g0, g1)
+        for stream, out in ((s_src, src), (s_dst, dst)):
+            u = stream.uniform_at(a, b - a) * cap[gid]
+            out[a:b] = np.minimum(_searchsorted_right(cdf, u), nv[gid] - 1)
+
+    workers = max(1, min(len(chunks), (os.cpu_count() or 1) // 2))
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        list(ex.map(endpoints, chunks))
+    s_src.pos = s_dst.pos = total
+    # self loops are resampled; only an entry that was bad can be bad again
+    bad = np.nonzero(src == dst)[0]
     for _ in range(64):
-        bad = np.nonzero(src == dst)[0]
         if bad.size == 0:
             break
-        u = s_dst.uniform(bad.size) * cap[gid[bad]]
-        dst[bad] = np.minimum(_searchsorted_right(cdf, u), nv[gid[bad]] - 1)
-    bad = np.nonzero(src == dst)[0]
-    dst[bad] = (src[bad] + 1) % nv[gid[bad]]
-    t = Stream(seed, 44).integers(0, t_max, total)
+        gb = np.searchsorted(eoff, bad, side="right") - 1
+        u = s_dst.uniform(bad.size) * cap[gb]
+        dst[bad] = np.minimum(_searchsorted_right(cdf, u), nv[gb] - 1)
+        bad = bad[src[bad] == dst[bad]]
+    gb = np.searchsorted(eoff, bad, side="right") - 1
+    dst[bad] = (src[bad] + 1) % nv[gb]
     voff = np.concatenate([[0], np.cumsum(nv)])
-    t = _dedupe_triples(src + voff[gid], dst + voff[gid], t)
-    return Batch(src.astype(np.int32), dst.astype(np.int32), t.astype(np.int64), eoff,
+    t = np.empty(total, np.int64)
+
+    def times(ch):
+        g0, g1 = ch
+        a, b = int(eoff[g0]), int(eoff[g1])
+        v = np.floor(s_t.uniform_at(a, b - a) * t_max).astype(np.int64)
+        np.minimum(v, t_max - 1, out=v)
+        gid = gid_of(g0, g1)
+        t[a:b] = _dedupe_triples(src[a:b] + voff[gid], dst[a:b] + voff[gid], v)
+
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        list(ex.map(times, chunks))
+    return Batch(src.astype(np.int32), dst.astype(np.int32), t, eoff,
                  nv.astype(np.int32), k, np.full(n_graphs, 5, np.int32),
                  f"{n_graphs} graphs, E_b=10^U({log10_min},{log10_max}) total {total}, "
                  f"V_b=E_b/10, zipf={zipf_s}, t~U[0,{t_max}), k in {{4,8,16}}, M=5")

@@ -1,19 +1,19 @@
-"""The largest configuration: the 200M-edge hub workload (10M vertices; half
-the edges a Zipf(1.8) background on a 60 s grid, so top vertices carry ~10^8
-edges and tie groups of thousands), through the benchmark's entry point and
-launch configuration (k = 8, M = 5, the current stream).
+"""Parity at the largest configuration: the 200M-edge hub workload (10M
+vertices; half the edges a Zipf(1.8) background on a 60 s grid, so the top
+vertices carry ~10^8 edges and tie groups of thousands), run through the
+benchmark's entry point and launch configuration (k = 8, M = 5, the current
+stream).
 
-Generating the graph takes minutes of one host core and the oracle's chain
-would take several more, so the module runs only with DGEC_HUB_FULL=1 and
-checks properties that hold at any size, each O(E) or one sort:
-the incidence lists exactly (offsets from the degrees; each list a
-permutation sorted by (t, id)); Def. 1 for every skeleton link, each pair
-once, and the size bound of Sec. 2; kNN rows of sampled edges against the
-oracle; the forest's order, its membership in the skeleton and one tree per
-component of the skeleton (scipy); the dendrogram's sizes; the clusters'
-sizes and components; every level's component count against the forest."""
-import os
-
+The oracle's chain runs on the whole graph (Alg. 3's skeleton, then Alg. 1's
+Kruskal forest, union-find dendrogram and condensing: minutes of single-core
+C), so the skeleton set, the forest, the dendrogram rows, every
+condensed-tree array and the labels are compared element by element. kNN
+rows are recomputed one by one by the oracle for sampled edges, among them
+edges whose tail or head is one of the largest hubs (their candidate sets
+hold ~10^8 entries and their windows cross tie groups of thousands). The
+incidence lists are fixed exactly by their defining properties (offsets
+from the degrees; each list a permutation sorted by (t, id)). The discrete
+dendrogram's per-level component counts are checked against the forest."""
 import numpy as np
 import pytest
 
@@ -21,10 +21,10 @@ from gpu_helpers import ctx
 from oracle import oracle as O
 from paper_2311_10337_gb300 import synth
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("DGEC_HUB_FULL") != "1",
-                                 reason="200M-edge graph: set DGEC_HUB_FULL=1 to run")]
+pytestmark = pytest.mark.gpu
 POW2 = np.array([2 ** i for i in range(29)], np.int64)
+CONDENSED = ["fall_cluster", "fall_lambda", "cl_id", "cl_parent", "cl_birth", "cl_death",
+             "cl_stab_hi", "cl_stab_lo", "cl_size", "cl_selected"]
 
 
 @pytest.fixture(scope="module")
@@ -36,21 +36,36 @@ def hub():
     t = torch.from_numpy(w.t).cuda()
     out = ctx().run(s, d, t, w.n_vertices, w.k, w.min_cluster_size)
     names = ["out_off", "in_off", "out_t", "out_id", "in_id", "pos_out", "pos_in", "sk_u", "sk_v", "sk_w",
-             "knn_id", "core", "mst_u", "mst_v", "mst_w", "link_a", "link_b", "link_size", "labels"]
+             "knn_id", "core", "mst_u", "mst_v", "mst_w", "link_a", "link_b", "link_size", "labels"] + CONDENSED
     r = {n: out.numpy(n) for n in names}
     r["n_clusters"] = out.n_clusters
+    del out
     lv = ctx().run_levels(s, d, t, w.n_vertices, POW2, 0)
     r["n_components"] = lv.numpy("n_components")
-    del s, d, t, out, lv
+    del s, d, t, lv
     ctx().ws = None
     torch.cuda.empty_cache()
-    cg = pytest.importorskip("scipy.sparse.csgraph")
-    sp = pytest.importorskip("scipy.sparse")
-    E = w.n_edges
-    g = sp.coo_matrix((np.ones(len(r["sk_u"]), np.int8), (r["sk_u"], r["sk_v"])), shape=(E, E)).tocsr()
-    r["n_comp"], r["comp"] = cg.connected_components(g, directed=False)
-    del g
     return w, r
+
+
+@pytest.fixture(scope="module")
+def chain(hub):
+    """The oracle's whole clustering chain on the same graph."""
+    w, _ = hub
+    E = w.n_edges
+    u, v, wt = O.skeleton(w.src, w.dst, w.t, w.n_vertices)       # sorted by (w, u, v)
+    mu, mv, mw = O.mst(E, u, v, wt)
+    a, b, s = O.linkage(E, mu, mv)
+    c = O.condense(E, a, b, mw, s, w.min_cluster_size)
+    return dict(skeleton=(u, v, wt), mst=(mu, mv, mw), linkage=(a, b, s), condensed=c)
+
+
+def _pair_key_order(E, u, v):
+    """Keys u * E + v and the permutation sorting them (torch's multi-threaded sort)."""
+    import torch
+    key = torch.from_numpy(u.astype(np.int64) * E + v.astype(np.int64))
+    ks, o = torch.sort(key, stable=True)
+    return ks.numpy(), o.numpy()
 
 
 def test_incidence_lists(hub):
@@ -70,79 +85,102 @@ def test_incidence_lists(hub):
     assert np.array_equal(r["out_t"], w.t[r["out_id"]])
 
 
-def test_skeleton_links(hub):
+def test_skeleton(hub, chain):
+    """Alg. 3's skeleton: the same set of (u, v, w) links as the oracle's."""
     w, r = hub
-    u, v, wt = r["sk_u"], r["sk_v"], r["sk_w"]
     E = w.n_edges
-    assert np.all(u < v)
-    step = 1 << 25
-    for lo in range(0, len(u), step):                         # Def. 1, P1-P3, one orientation
-        uu, vv, ww = u[lo:lo + step], v[lo:lo + step], wt[lo:lo + step]
-        tu, tv = w.t[uu], w.t[vv]
-        assert np.array_equal(ww, np.abs(tu - tv))
-        fwd = (w.dst[uu] == w.src[vv]) & (tu <= tv)
-        bwd = (w.dst[vv] == w.src[uu]) & (tv <= tu)
-        assert np.all(fwd | bwd)
-    key = np.sort(u.astype(np.int64) * E + v)
-    assert np.all(np.diff(key) > 0)                           # each pair once (Alg. 3 union)
+    ou, ov, ow = chain["skeleton"]
+    assert len(r["sk_u"]) == len(ou)
+    assert np.all(r["sk_u"] < r["sk_v"])
+    gk, go = _pair_key_order(E, r["sk_u"], r["sk_v"])
+    ok, oo = _pair_key_order(E, ou, ov)
+    assert np.array_equal(gk, ok)
+    assert np.array_equal(r["sk_w"][go], ow[oo])
     deg = np.bincount(w.src, minlength=w.n_vertices) + np.bincount(w.dst, minlength=w.n_vertices)
-    assert len(u) <= int(np.sum(np.maximum(deg - 1, 0)))      # size bound of Sec. 2
-    r["sk_key_sorted"] = key
+    assert len(ou) <= int(np.sum(np.maximum(deg - 1, 0)))      # size bound of Sec. 2
 
 
-def test_knn_sampled(hub):
-    """kNN rows of sampled edges away from the largest hubs, by the oracle
-    on the sub-multigraph they depend on."""
-    w, r = hub
-    indeg = np.bincount(w.dst, minlength=w.n_vertices)
-    outdeg = np.bincount(w.src, minlength=w.n_vertices)
-    light = np.nonzero((indeg[w.src] <= 20000) & (outdeg[w.dst] <= 20000))[0]
-    q = np.sort(np.random.default_rng(13).choice(light, 1000, replace=False))
-    tails = np.zeros(w.n_vertices, bool); tails[w.src[q]] = True
-    heads = np.zeros(w.n_vertices, bool); heads[w.dst[q]] = True
+def _knn_rows(w, q):
+    """The oracle's kNN rows of the query edges q, computed on the
+    sub-multigraph they depend on (the queries, the in-edges of their tails,
+    the out-edges of their heads; local ids keep the original id order)."""
+    tails = np.zeros(w.n_vertices, bool)
+    tails[w.src[q]] = True
+    heads = np.zeros(w.n_vertices, bool)
+    heads[w.dst[q]] = True
     keep = np.zeros(w.n_edges, bool)
     keep[q] = True
     keep |= tails[w.dst] | heads[w.src]
     sub = np.nonzero(keep)[0]
     lq = np.searchsorted(sub, q).astype(np.int32)
     ids, core = O.knn(w.src[sub], w.dst[sub], w.t[sub], w.n_vertices, w.k, lq)
-    ids = np.where(ids >= 0, sub[np.maximum(ids, 0)], -1)
+    return np.where(ids >= 0, sub[np.maximum(ids, 0)], -1), core
+
+
+def test_knn_sampled_light(hub):
+    """1,000 sampled edges whose tail and head lists are short."""
+    w, r = hub
+    indeg = np.bincount(w.dst, minlength=w.n_vertices)
+    outdeg = np.bincount(w.src, minlength=w.n_vertices)
+    light = np.nonzero((indeg[w.src] <= 20000) & (outdeg[w.dst] <= 20000))[0]
+    q = np.sort(np.random.default_rng(13).choice(light, 1000, replace=False))
+    ids, core = _knn_rows(w, q)
     knn = r["knn_id"].reshape(w.n_edges, w.k)
     assert np.array_equal(knn[q], ids)
     assert np.array_equal(r["core"][q], core)
 
 
-def test_forest_and_dendrogram(hub):
+def test_knn_sampled_top_hubs(hub):
+    """Edges whose tail has the largest in-list (~10^8 predecessors, windows
+    crossing tie groups of thousands on the 60 s grid) and edges whose head
+    has the largest out-list."""
     w, r = hub
-    E = w.n_edges
-    mu, mv, mw = r["mst_u"], r["mst_v"], r["mst_w"]
-    k0 = (mw[1:] > mw[:-1]) | ((mw[1:] == mw[:-1]) & ((mu[1:] > mu[:-1]) | ((mu[1:] == mu[:-1]) & (mv[1:] > mv[:-1]))))
-    assert np.all(k0)                                                 # sorted by the strict key (w, u, v)
-    assert len(mu) == E - r["n_comp"]                                 # one tree per component
-    ks = r.get("sk_key_sorted")
-    if ks is None:
-        ks = np.sort(r["sk_u"].astype(np.int64) * E + r["sk_v"])
-    mk = np.sort(mu.astype(np.int64) * E + mv)
-    pos = np.minimum(np.searchsorted(ks, mk), len(ks) - 1)
-    assert np.all(ks[pos] == mk)                                      # forest edges are skeleton links
-    assert np.all(r["comp"][mu] == r["comp"][mv])
-    a, b, sz = r["link_a"].astype(np.int64), r["link_b"].astype(np.int64), r["link_size"]
-    size_of = np.concatenate([np.ones(E, np.int64), sz])
-    assert np.all(a < b) and np.all(b < E + np.arange(len(a)))
-    assert np.array_equal(sz, size_of[a] + size_of[b])
-    kids = np.bincount(np.concatenate([a, b]), minlength=E + len(a))
-    assert kids.max() <= 1                                            # every cluster merged once
+    indeg = np.bincount(w.dst, minlength=w.n_vertices)
+    outdeg = np.bincount(w.src, minlength=w.n_vertices)
+    rng = np.random.default_rng(17)
+    hub_in = int(np.argmax(indeg))
+    hub_out = int(np.argmax(outdeg))
+    assert indeg[hub_in] > 5e7 and outdeg[hub_out] > 5e7
+    q = np.concatenate([rng.choice(np.nonzero(w.src == hub_in)[0], 3, replace=False),
+                        rng.choice(np.nonzero(w.dst == hub_out)[0], 3, replace=False)])
+    q = np.unique(q)
+    ids, core = _knn_rows(w, q)
+    knn = r["knn_id"].reshape(w.n_edges, w.k)
+    assert np.array_equal(knn[q], ids)
+    assert np.array_equal(r["core"][q], core)
+
+
+def test_forest(hub, chain):
+    """Alg. 1, spanning forest: the oracle's Kruskal forest, element by element."""
+    _, r = hub
+    mu, mv, mw = chain["mst"]
+    assert np.array_equal(r["mst_u"], mu) and np.array_equal(r["mst_v"], mv)
+    assert np.array_equal(r["mst_w"], mw)
+
+
+def test_dendrogram(hub, chain):
+    """Alg. 1, dendrogram: the union-find replay's rows."""
+    _, r = hub
+    a, b, s = chain["linkage"]
+    assert np.array_equal(r["link_a"], a) and np.array_equal(r["link_b"], b)
+    assert np.array_equal(r["link_size"], s)
+
+
+def test_condensed_tree_and_labels(hub, chain):
+    """Alg. 1, condensing and extraction: every condensed-tree array, the
+    stabilities and the selection, and the labels."""
+    _, r = hub
+    c = chain["condensed"]
+    for key in CONDENSED:
+        assert np.array_equal(r[key], c[key]), key
+    assert np.array_equal(r["labels"], c["labels"])
+    assert r["n_clusters"] == c["n_clusters"]
+
+
+def test_levels_against_forest(hub, chain):
+    """Alg. 5's component count at every threshold equals E minus the forest
+    edges of weight <= the threshold (Thm. 1: the forest is sorted by w)."""
+    w, r = hub
+    mw = chain["mst"][2]
     nmst_at = np.searchsorted(mw, POW2, side="right")
-    assert np.array_equal(r["n_components"], E - nmst_at)             # Alg. 5 levels against the forest
-
-
-def test_labels(hub):
-    w, r = hub
-    lab, ncl, comp = r["labels"], r["n_clusters"], r["comp"]
-    m = lab >= 0
-    assert lab.max() + 1 == ncl
-    idx = np.nonzero(m)[0]
-    _, first = np.unique(lab[idx], return_index=True)
-    assert np.all(np.diff(idx[first]) > 0)                            # numbered by smallest member
-    assert np.array_equal(comp[idx], comp[idx[first]][lab[idx]])      # one component per cluster
-    assert np.all(np.bincount(lab[m]) >= w.min_cluster_size)
+    assert np.array_equal(r["n_components"], w.n_edges - nmst_at)

@@ -95,6 +95,19 @@ def test_large_timestamps_and_negative():
     compare_all(w.src, w.dst, w.t * 1_000_003 - 10**12, w.n_vertices, 4, 3)
 
 
+@pytest.mark.parametrize("seed", [0, 1])
+def test_wide_time_span(seed):
+    """Times whose span needs more bits than fit beside the ids in one 64-bit
+    sort key (nanosecond stamps over a century, negative and positive):
+    stage A then sorts on the time alone with the id as the value. Ties stay
+    common (few distinct times)."""
+    w = synth.random_small(3000, 40, 60, 31 + seed)
+    jitter = (np.arange(w.n_edges) % 3).astype(np.int64)
+    t = (w.t - 30) * (np.int64(1) << 56) + jitter * (np.int64(1) << 40)
+    assert int(t.max() - t.min()).bit_length() + (w.n_edges - 1).bit_length() > 64
+    compare_all(w.src, w.dst, t, w.n_vertices, 4, 3)
+
+
 def test_empty_and_single():
     z = np.zeros(0, np.int32)
     g = run_gpu(z, z, np.zeros(0, np.int64), 5, 4, 5)

@@ -1,0 +1,62 @@
+"""The launch configuration changes speed, never results: every candidate
+the autotuner may pick gives the same outputs as the default, and the
+tuner's choice is cached per GPU model and workload signature."""
+import numpy as np
+import pytest
+
+from gpu_helpers import ctx, run_gpu
+from paper_2311_10337_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def test_every_launch_config_gives_identical_outputs():
+    from paper_2311_10337_gb300 import tune
+    w = synth.mid(scale=0.002)
+    c = ctx()
+    default = c.launch_config()
+    ref = run_gpu(w.src, w.dst, w.t, w.n_vertices, w.k, w.min_cluster_size)
+    try:
+        for kb in tune.KNN_BLOCKS:
+            for sc in (152, 2432, 65536):
+                c.set_launch_config(kb, sc)
+                got = run_gpu(w.src, w.dst, w.t, w.n_vertices, w.k, w.min_cluster_size)
+                for key in ref:
+                    assert np.array_equal(np.asarray(got[key]), np.asarray(ref[key])), (kb, sc, key)
+    finally:
+        c.set_launch_config(*default)
+
+
+def test_bad_launch_config_is_rejected():
+    from paper_2311_10337_gb300 import dgec
+    c = ctx()
+    default = c.launch_config()
+    for kb, sc in ((96, 1000), (128, 0), (128, (1 << 20) + 1)):
+        with pytest.raises(dgec.DgecError) as ei:
+            c.set_launch_config(kb, sc)
+        assert ei.value.status == 1
+    assert c.launch_config() == default
+
+
+def test_tuner_picks_a_candidate_and_caches_it(tmp_path, monkeypatch):
+    import torch
+    from paper_2311_10337_gb300 import tune
+    monkeypatch.setenv("DGEC_TUNE_CACHE", str(tmp_path / "cfg.json"))
+    w = synth.tiny()
+    s, d, t = (torch.from_numpy(x).cuda() for x in (w.src, w.dst, w.t))
+    c = ctx()
+    default = c.launch_config()
+    try:
+        run = lambda: c.run(s, d, t, w.n_vertices, w.k, w.min_cluster_size)
+        first = tune.tune(c, run, "tiny-test", steps=1)
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        assert not first["cached"] and first["knn_block"] in tune.KNN_BLOCKS
+        assert first["stream_ctas"] in tune.stream_cta_candidates(sms)
+        assert c.launch_config() == (first["knn_block"], first["stream_ctas"])
+        c.set_launch_config(*default)
+        again = tune.tune(c, run, "tiny-test", steps=1)
+        assert again["cached"] and (again["knn_block"], again["stream_ctas"]) == \
+            (first["knn_block"], first["stream_ctas"])
+        assert c.launch_config() == (first["knn_block"], first["stream_ctas"])
+    finally:
+        c.set_launch_config(*default)

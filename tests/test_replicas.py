@@ -78,8 +78,10 @@ def test_reference_sample_shrinks_with_step_count():
     unless a window is given, more steps take a shorter window each."""
     import argparse
     import bench
-    win = [bench.reference_sample_minutes(argparse.Namespace(cpu_sample_minutes=None, steps=s, warmup=3))
-           for s in (5, 10, 20, 50)]
-    assert win == sorted(win, reverse=True) and win[0] == bench.CPU_SAMPLE_MINUTES
+    for wl in ("hub", "mid"):
+        win = [bench.reference_sample_minutes(argparse.Namespace(cpu_sample_minutes=None, steps=s, warmup=3), wl)
+               for s in (5, 10, 20, 50)]
+        assert win == sorted(win, reverse=True) and win[0] == bench.CPU_SAMPLE_MINUTES[wl]
+        assert win[-1] < win[0]
     given = argparse.Namespace(cpu_sample_minutes=42.0, steps=100, warmup=3)
-    assert bench.reference_sample_minutes(given) == 42.0
+    assert bench.reference_sample_minutes(given, "hub") == 42.0
