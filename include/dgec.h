@@ -102,10 +102,11 @@ typedef struct {
      * pos_out[e] - out_off[src[e]] (likewise for dst's in-list). */
     const int32_t *pos_out, *pos_in;   /* [n_edges] */
     /* Alg. 3: skeleton L*_G as undirected edges (u < v, w = |t_u - t_v|),
-     * each line-graph edge once. Deterministic order: first every edge's
-     * link to the first later out-edge at its head, then every edge's link
-     * to the retained in-edge at its tail, each group in (t, id) order of
-     * the edge that emits the link. */
+     * each line-graph edge once. Deterministic order (not sorted by (w, u,
+     * v): the forest below is): first every edge's link to the first later
+     * out-edge at its head, in the order of the in-lists (by head vertex,
+     * then (t, id)); then every edge's link to the retained in-edge at its
+     * tail, in the order of the out-lists (by tail vertex, then (t, id)). */
     const int32_t *sk_u, *sk_v;        /* [n_skeleton] */
     const int64_t *sk_w;
     /* k nearest line-graph neighbours in time: knn_id[e*k + x], ranked by
@@ -274,13 +275,16 @@ dgec_status dgec_server_destroy(dgec_server *srv);
 
 /* Launch configuration of the calls made on ctx (no counterpart in the
  * paper; it changes speed, never results): threads per CTA of the kNN kernel
- * (64, 128 or 256; default 128) and the number of CTAs of each grid-stride
- * streaming kernel (1 .. 2^20; default 65,536). The autotuner of the Python
- * package picks them per GPU model and workload. Invalid values give
- * DGEC_ERR_INVALID_ARG and leave the configuration unchanged. */
+ * (64, 128 or 256; default 128), the number of CTAs of each grid-stride
+ * streaming kernel (1 .. 2^20; default 65,536), and whether the kNN kernel
+ * sorts its candidates as packed 64-bit keys (|dt| << 32 | id; 0 or 1,
+ * default 0; used only when the time span fits 32 bits). The autotuner of
+ * the Python package picks them per GPU model and workload. Invalid values
+ * give DGEC_ERR_INVALID_ARG and leave the configuration unchanged. */
 typedef struct {
     int32_t knn_block;
     int32_t stream_ctas;
+    int32_t knn_packed;
 } dgec_launch_config;
 dgec_status dgec_set_launch_config(dgec_ctx *ctx, const dgec_launch_config *cfg);
 dgec_status dgec_get_launch_config(const dgec_ctx *ctx, dgec_launch_config *cfg);

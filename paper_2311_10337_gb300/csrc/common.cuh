@@ -46,6 +46,7 @@ struct StageTimer {
 struct Ctx {
     int device = 0;
     int knn_block = 128;           // launch configuration (dgec_set_launch_config)
+    int knn_packed = 0;
     int64_t stream_ctas = 65536;
     int num_sms = 152;
     char msg[512] = {0};
@@ -205,6 +206,37 @@ __device__ __forceinline__ long long cta_reserve(bool take, unsigned long long *
     }
     __syncthreads();
     long long slot = (long long)(s_base + s_warp[w] + __popc(m & ((1u << lane_id()) - 1u)));
+    __syncthreads();
+    return slot;
+}
+
+// Stream compaction with one atomicAdd per CTA for up to blockDim.x * 32
+// items: thread i asks for cnt_i slots and gets the first of its own
+// consecutive run (runs in thread order). Every thread of the CTA must call
+// it the same number of times (use CTA-uniform loops).
+__device__ __forceinline__ long long cta_reserve_count(unsigned cnt, unsigned long long *counter) {
+    __shared__ unsigned s_warp[32];
+    __shared__ unsigned long long s_base;
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    unsigned inc = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned o = __shfl_up_sync(0xffffffffu, inc, d);
+        if ((int)lane_id() >= d) inc += o;
+    }
+    if (lane_id() == 31) s_warp[w] = inc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned tot = 0;
+        for (int i = 0; i < nw; i++) {
+            const unsigned c = s_warp[i];
+            s_warp[i] = tot;
+            tot += c;
+        }
+        s_base = tot ? atomicAdd(counter, (unsigned long long)tot) : 0ull;
+    }
+    __syncthreads();
+    const long long slot = (long long)(s_base + s_warp[w] + inc - cnt);
     __syncthreads();
     return slot;
 }

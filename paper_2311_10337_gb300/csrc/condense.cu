@@ -210,33 +210,59 @@ __global__ void k_c_clusters(Gview gv, const int *isrep, const int64_t *size, co
     }
 }
 
-// where each point leaves: the lowest kept ancestor of size >= M
-__global__ void k_c_points(Gview gv, const int32_t *cpar, const int64_t *size, const int64_t *w,
-                           const int32_t *link, const unsigned long long *cbirth,
-                           int32_t *fall_cluster, uint64_t *fall_lambda, unsigned long long *st_hi,
-                           unsigned long long *st_lo) {
+// Per node a point can land on or walk through (kept merges, virtual
+// roots): its collapsed parent, its cluster when it is big (else -1) and its
+// lambda, in one 16-byte record, so that each step of a point's walk reads
+// one sector.
+struct NodeRec {
+    int32_t cpar;
+    int32_t link;
+    unsigned long long lam;
+};
+
+__global__ void k_c_nrec(Gview gv, const int *isrep, const int64_t *size, const int64_t *w,
+                         const int32_t *cpar, const int32_t *link, NodeRec *rec) {
+    const int64_t E = gv.E, n = gv.n;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n + gv.G;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t X = E + s;
+        NodeRec r;
+        if (s >= n) {
+            r.cpar = (int32_t)X;
+            r.link = link[X];
+            r.lam = 0ull;
+        } else {
+            if (!isrep[s]) continue;  // never a collapsed parent
+            r.cpar = cpar[X];
+            r.link = size[s] >= gv.gM[graph_of(gv, X)] ? link[X] : -1;
+            r.lam = lambda_of(w[s]);
+        }
+        rec[s] = r;
+    }
+}
+
+// where each point leaves: the lowest kept ancestor of size >= M; its
+// stability share is added per warp and cluster (points of one big cluster
+// often meet in a warp)
+__global__ void k_c_points(Gview gv, const int32_t *cpar, const NodeRec *rec,
+                           const unsigned long long *cbirth, int32_t *fall_cluster, uint64_t *fall_lambda,
+                           unsigned long long *st_hi, unsigned long long *st_lo) {
     const int64_t E = gv.E;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < E;
          base += stride) {  // warp-uniform
         const int64_t p = base + lane_id();
-        const bool ok = p < E;
-        const unsigned active = 0xffffffffu;
         int K = 0;
         unsigned long long add = 0;
-        if (ok) {
-            const int M = gv.gM[gv.egraph[p]];
-            int64_t X = cpar[p];
-            for (int it = 0; it < kMaxWalk && X < gv.R0 && size[X - E] < M; it++) X = cpar[X];
-            K = link[X];
-            unsigned long long L = lam_node(X, gv, w);
+        if (p < E) {
+            NodeRec r = rec[cpar[p] - E];
+            for (int it = 0; it < kMaxWalk && r.link < 0; it++) r = rec[r.cpar - E];
+            K = r.link;
             fall_cluster[p] = K;
-            fall_lambda[p] = L;
-            add = L - cbirth[K];
+            fall_lambda[p] = r.lam;
+            add = r.lam - cbirth[K];  // 0 at a virtual root
         }
-        // points of one cluster meet in a warp often (the big clusters):
-        // one 128-bit add per cluster per warp
-        warp_add_u128(active, ok, K, add, st_hi, st_lo);
+        warp_add_u128(0xffffffffu, add != 0, K, add, st_hi, st_lo);
     }
 }
 
@@ -653,8 +679,11 @@ dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro 
     DG_TRY(jump_to_fixed(c, n, E, SelBigRep{gv, s.isrep, d.size}, s.link, s.jflag));
     TK(c, "k_c_clusters", k_c_clusters<<<gn, kBlock, 0, st>>>(gv, s.isrep, d.size, m.w, s.cpar, s.nbig, s.link,
                                                              s.isc, s.cbirth, s.cdeath, s.cparent));
-    TK(c, "k_c_points", k_c_points<<<gE, kBlock, 0, st>>>(gv, s.cpar, d.size, m.w, s.link, s.cbirth,
-                                                         o.fall_cluster, o.fall_lambda, s.st_hi, s.st_lo));
+    // the node records live in the EOM phase's Fa array (not in use yet)
+    NodeRec *nrec = reinterpret_cast<NodeRec *>(s.Fa);
+    TK(c, "k_c_nrec", k_c_nrec<<<gn, kBlock, 0, st>>>(gv, s.isrep, d.size, m.w, s.cpar, s.link, nrec));
+    TK(c, "k_c_points", k_c_points<<<gE, kBlock, 0, st>>>(gv, s.cpar, nrec, s.cbirth, o.fall_cluster,
+                                                         o.fall_lambda, s.st_hi, s.st_lo));
     TK(c, "k_c_child_stab", k_c_child_stab<<<gN, kBlock, 0, st>>>(N, gv, s.isc, s.cparent, d.size, s.cbirth,
                                                                  s.cdeath, s.st_hi, s.st_lo));
     DG_TRY(exclusive_scan_i32(c, s.isc, s.cpos, N + 1, s.scan_tmp));

@@ -121,23 +121,31 @@ __global__ void k_init_flags(long long *flags) {
     flags[3] = LLONG_MIN;
 }
 
+// (t, original id) of an internal id r in one 16-byte record, for the
+// merged-list unpack's random reads by r (one sector instead of two)
+struct TE {
+    int64_t t;
+    int32_t e, pad;
+};
+
 // rank r = position of edge (t, id) in the global order; time-ordered
-// copies of the inputs for the later stages
-__global__ void k_rank_init(const unsigned long long *ks, int64_t E, long long tmin, int idbits,
-                            const int32_t *src, const int32_t *dst, const int32_t *egraph,
-                            const int64_t *voff, int G, int32_t *orig_of, int32_t *rank_of, int32_t *isrc,
-                            int32_t *idst, int64_t *it) {
+// copies of the inputs for the later stages. The sort carried each edge's
+// (src, dst) pair, in global vertex ids, as its value.
+__global__ void k_rank_init(const unsigned long long *ks, const unsigned long long *vs, int64_t E,
+                            long long tmin, int idbits, int32_t *orig_of, int32_t *rank_of, int32_t *isrc,
+                            int32_t *idst, int64_t *it, TE *te) {
     const unsigned long long idmask = (1ull << idbits) - 1ull;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < E;
          r += (int64_t)gridDim.x * blockDim.x) {
-        unsigned long long k = ks[r];
-        int32_t e = (int32_t)(k & idmask);
+        const unsigned long long k = ks[r], sd = vs[r];
+        const int32_t e = (int32_t)(k & idmask);
+        const int64_t tt = (int64_t)(k >> idbits) + tmin;
         orig_of[r] = e;
         rank_of[e] = (int32_t)r;
-        it[r] = (int64_t)(k >> idbits) + tmin;
-        int32_t vo = G > 1 ? (int32_t)voff[egraph[e]] : 0;  // one graph: no random lookup
-        isrc[r] = src[e] + vo;
-        idst[r] = dst[e] + vo;
+        it[r] = tt;
+        te[r] = TE{tt, e, 0};
+        isrc[r] = (int32_t)(sd & 0xffffffffull);
+        idst[r] = (int32_t)(sd >> 32);
     }
 }
 
@@ -145,13 +153,14 @@ __global__ void k_rank_init(const unsigned long long *ks, int64_t E, long long t
 __global__ void k_rank_init_kv(const unsigned long long *ks, const unsigned long long *vs, int64_t E,
                                long long tmin, const int32_t *src, const int32_t *dst,
                                const int32_t *egraph, const int64_t *voff, int G, int32_t *orig_of,
-                               int32_t *rank_of, int32_t *isrc, int32_t *idst, int64_t *it) {
+                               int32_t *rank_of, int32_t *isrc, int32_t *idst, int64_t *it, TE *te) {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < E;
          r += (int64_t)gridDim.x * blockDim.x) {
         int32_t e = (int32_t)vs[r];
         orig_of[r] = e;
         rank_of[e] = (int32_t)r;
         it[r] = (int64_t)(long long)(ks[r] + (unsigned long long)tmin);
+        te[r] = TE{it[r], e, 0};
         int32_t vo = G > 1 ? (int32_t)voff[egraph[e]] : 0;
         isrc[r] = src[e] + vo;
         idst[r] = dst[e] + vo;
@@ -209,11 +218,10 @@ __global__ void k_moff_split(const int64_t *moff, const int32_t *oidx, int64_t V
 // Every item of the merged lists goes to its slot in the out- or in-list
 // arrays; its rank in the other list is its position difference.
 __global__ void k_munpack(const unsigned long long *key, int64_t n2, int cb, const int64_t *moff,
-                          const int32_t *oidx, const int64_t *out_off, const int32_t *orig_of,
-                          const int64_t *it, int64_t *out_t, int32_t *out_id, int32_t *out_r,
-                          int32_t *slot_out, int32_t *pos_out, int64_t *in_t, int32_t *in_id,
-                          int32_t *in_r, int32_t *pos_in, unsigned char *in_head, int32_t *brank,
-                          int32_t *arank) {
+                          const int32_t *oidx, const int64_t *out_off, const TE *te, int64_t *out_t,
+                          int32_t *out_id, int32_t *out_r, int2 *outrk, int32_t *pos_out, int64_t *in_t,
+                          int32_t *in_id, int32_t *in_r, int32_t *pos_in, unsigned char *in_head,
+                          int32_t *arank, int2 *in_va, int2 *out_vb) {
     const unsigned long long cmask = (1ull << cb) - 1ull;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n2;
          x += (int64_t)gridDim.x * blockDim.x) {
@@ -224,16 +232,17 @@ __global__ void k_munpack(const unsigned long long *key, int64_t n2, int cb, con
         const int64_t ob = oidx[x];              // out-items before x
         const int64_t seg = x - moff[v];         // position in v's merged list
         const int64_t obv = ob - out_off[v];     // out-items before x within v's list
-        const int32_t e = orig_of[r];
-        const int64_t tt = it[r];
+        const TE rec = te[r];
+        const int32_t e = rec.e;
+        const int64_t tt = rec.t;
         if (code & 1ull) {
             const int64_t slot = ob;
             out_t[slot] = tt;
             out_id[slot] = e;
             out_r[slot] = r;
-            slot_out[r] = (int32_t)slot;
             pos_out[e] = (int32_t)slot;
-            brank[r] = (int32_t)(seg - obv);     // in-edges of v with t <= t_r
+            outrk[r] = make_int2((int32_t)slot, (int32_t)(seg - obv));  // b: in-edges of v with t <= t_r
+            out_vb[slot] = make_int2((int32_t)v, (int32_t)(seg - obv));
         } else {
             const int64_t slot = x - ob;
             in_t[slot] = tt;
@@ -242,15 +251,21 @@ __global__ void k_munpack(const unsigned long long *key, int64_t n2, int cb, con
             pos_in[e] = (int32_t)slot;
             in_head[slot] = (seg - obv) == 0;    // first entry of v's in-list
             arank[r] = (int32_t)obv;             // out-edges of v with t < t_r
+            in_va[slot] = make_int2((int32_t)v, (int32_t)obv);
         }
     }
 }
 
-__global__ void k_pack_keys(const int64_t *t, int64_t E, long long tmin, int idbits,
-                            unsigned long long *k) {
+// key ((t - tmin) << idbits | id), value (src, dst) in global vertex ids
+__global__ void k_pack_keys(const int64_t *t, const int32_t *src, const int32_t *dst, const int32_t *egraph,
+                            const int64_t *voff, int G, int64_t E, long long tmin, int idbits,
+                            unsigned long long *k, unsigned long long *v) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
-         e += (int64_t)gridDim.x * blockDim.x)
+         e += (int64_t)gridDim.x * blockDim.x) {
         k[e] = ((unsigned long long)(t[e] - tmin) << idbits) | (unsigned long long)e;
+        const int32_t vo = G > 1 ? (int32_t)voff[egraph[e]] : 0;
+        v[e] = (unsigned long long)(unsigned)(src[e] + vo) | ((unsigned long long)(unsigned)(dst[e] + vo) << 32);
+    }
 }
 
 // bins: 0 warp (2..32), 1 CTA-256, 2 CTA-2048, 3 hub (> 2048)
@@ -386,12 +401,13 @@ void plan_csr(Arena &ws, const Problem &p, Csr &o) {
     o.isrc = ws.take<int32_t>(p.E);
     o.idst = ws.take<int32_t>(p.E);
     o.it = ws.take<int64_t>(p.E);
-    o.slot_out = ws.take<int32_t>(p.E);
+    o.outrk = ws.take<int2>(p.E);
     o.pos_out = ws.take<int32_t>(p.E);
     o.pos_in = ws.take<int32_t>(p.E);
-    o.brank = ws.take<int32_t>(p.E);
     o.arank = ws.take<int32_t>(p.E);
     o.in_gs = ws.take<int32_t>(p.E);
+    o.in_va = ws.take<int2>(p.E);
+    o.out_vb = ws.take<int2>(p.E);
 }
 
 void carve_segsort(Arena &a, int64_t V, int64_t n, SegSort &s) {
@@ -417,6 +433,7 @@ struct CsrScratch {
     int64_t *moff;                 // [V+1] merged-list offsets
     int32_t *oidx;                 // [2E+1] out-items before each item
     unsigned char *in_head;        // [E] first entry of an in-list
+    TE *te;                        // [E] by r: (t, original id)
     void *radix;
 };
 static CsrScratch carve_csr(Arena &a, const Problem &p) {
@@ -432,6 +449,7 @@ static CsrScratch carve_csr(Arena &a, const Problem &p) {
     s.moff = a.take<int64_t>(p.V + 1);
     s.oidx = a.take<int32_t>(2 * E + 1);
     s.in_head = a.take<unsigned char>(E);
+    s.te = a.take<TE>(E);
     s.radix = a.take<char>(radix_scratch_bytes(2 * E));
     return s;
 }
@@ -544,13 +562,14 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
     // global (t, id) order: internal ids
     const int gEE = grid_for(E, kBlock, kStreamCap);
     if (p.idbits + p.tbits <= 64) {
-        TK(c, "k_pack_keys", k_pack_keys<<<gEE, kBlock, 0, st>>>(p.t, E, p.tmin, p.idbits, s.mk));
+        TK(c, "k_pack_keys", k_pack_keys<<<gEE, kBlock, 0, st>>>(p.t, p.src, p.dst, p.egraph, p.voff, p.G, E, p.tmin,
+                                                                p.idbits, s.mk, s.mk + E));
         bool in_b;
-        DG_TRY(radix_sort(c, RadixBuffers{s.mk, s.mk2, nullptr, nullptr}, E, p.idbits, p.idbits + p.tbits,
+        DG_TRY(radix_sort(c, RadixBuffers{s.mk, s.mk2, s.mk + E, s.mk2 + E}, E, p.idbits, p.idbits + p.tbits,
                           s.radix, &in_b));
-        TK(c, "k_rank_init", k_rank_init<<<gEE, kBlock, 0, st>>>(in_b ? s.mk2 : s.mk, E, p.tmin, p.idbits,
-                                                                p.src, p.dst, p.egraph, p.voff, p.G, o.orig_of, o.rank_of,
-                                                                o.isrc, o.idst, o.it));
+        TK(c, "k_rank_init", k_rank_init<<<gEE, kBlock, 0, st>>>(in_b ? s.mk2 : s.mk, in_b ? s.mk2 + E : s.mk + E, E,
+                                                                p.tmin, p.idbits, o.orig_of, o.rank_of, o.isrc, o.idst,
+                                                                o.it, s.te));
     } else {
         // wide span: the time is the whole key, the id its value (second halves of the item buffers)
         TK(c, "k_pack_t", k_pack_t<<<gEE, kBlock, 0, st>>>(p.t, E, p.tmin, s.mk, s.mk + E));
@@ -558,7 +577,7 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
         DG_TRY(radix_sort(c, RadixBuffers{s.mk, s.mk2, s.mk + E, s.mk2 + E}, E, 0, p.tbits, s.radix, &in_b));
         TK(c, "k_rank_init_kv", k_rank_init_kv<<<gEE, kBlock, 0, st>>>(
                                     in_b ? s.mk2 : s.mk, in_b ? s.mk2 + E : s.mk + E, E, p.tmin, p.src, p.dst,
-                                    p.egraph, p.voff, p.G, o.orig_of, o.rank_of, o.isrc, o.idst, o.it));
+                                    p.egraph, p.voff, p.G, o.orig_of, o.rank_of, o.isrc, o.idst, o.it, s.te));
     }
     // time groups of the r order, then the incidence items in (t, in-before-out, r) order
     TK(c, "k_thead", k_thead<<<grid_for(E + 1, kBlock, kStreamCap), kBlock, 0, st>>>(o.it, E, s.gflag));
@@ -577,8 +596,9 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
     TK(c, "k_moff_split", k_moff_split<<<grid_for(V + 1, kBlock, kStreamCap), kBlock, 0, st>>>(s.moff, s.oidx, V, o.out_off,
                                                                                         o.in_off));
     TK(c, "k_munpack", k_munpack<<<grid_for(2 * E, kBlock, kStreamCap), kBlock, 0, st>>>(
-                           key, 2 * E, cb, s.moff, s.oidx, o.out_off, o.orig_of, o.it, o.out_t, o.out_id, o.out_r,
-                           o.slot_out, o.pos_out, o.in_t, o.in_id, o.in_r, o.pos_in, s.in_head, o.brank, o.arank));
+                           key, 2 * E, cb, s.moff, s.oidx, o.out_off, s.te, o.out_t, o.out_id, o.out_r, o.outrk,
+                           o.pos_out, o.in_t, o.in_id, o.in_r, o.pos_in, s.in_head, o.arank, o.in_va,
+                           o.out_vb));
     // start of every in-list entry's tie group (the kNN window takes a crossing group's smallest ids)
     DG_TRY((device_scan<long long, MaxI64, LoadInGroupHead, StoreI32>(c, LoadInGroupHead{o.in_t, s.in_head},
                                                                       StoreI32{o.in_gs}, E, MaxI64{}, 0ll, true,

@@ -127,40 +127,41 @@ __global__ void k_d_accept(const int32_t *act, int64_t na, const int32_t *ecu, c
 }
 
 // accepted edges keyed (group, rank) so a sort puts each group's chain in
-// rank order; the value is the edge's slot in the active list
-__global__ void k_d_emit(const int32_t *act, int64_t na, const int32_t *ecu, const int32_t *gp,
-                         const int *flag, const long long *pos, int sbits, unsigned long long *key,
-                         unsigned long long *val) {
+// rank order; the value carries the edge's two super-vertices, the one
+// whose pointer the edge is first (either for the group's mutual edge)
+__global__ void k_d_emit(const int32_t *act, int64_t na, const int32_t *ecu, const int32_t *ecv,
+                         const int32_t *minr, const int32_t *gp, const int *flag, const long long *pos,
+                         int sbits, unsigned long long *key, unsigned long long *val) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < na;
          j += (int64_t)gridDim.x * blockDim.x) {
         if (!flag[j]) continue;
-        int64_t at = pos[j];
-        key[at] = ((unsigned long long)gp[ecu[j]] << sbits) | (unsigned long long)act[j];
-        val[at] = (unsigned long long)j;
+        const int64_t at = pos[j];
+        const int s = act[j], cu = ecu[j], cv = ecv[j];
+        const bool own_u = minr[cu] == s;
+        const unsigned Y = (unsigned)(own_u ? cu : cv), O = (unsigned)(own_u ? cv : cu);
+        key[at] = ((unsigned long long)gp[cu] << sbits) | (unsigned long long)s;
+        val[at] = ((unsigned long long)Y << 32) | O;
     }
 }
 
 __global__ void k_d_chain(const unsigned long long *key, const unsigned long long *val, int64_t nacc,
-                          int64_t E, int sbits, const int32_t *ecu, const int32_t *ecv,
-                          const int32_t *minr, const int32_t *sroot, const int64_t *ssize, int32_t *la,
+                          int64_t E, int sbits, const int32_t *sroot, const int64_t *ssize, int32_t *la,
                           int32_t *lb, int32_t *parent, long long *contrib, int *head) {
     const unsigned long long smask = (1ull << sbits) - 1ull;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nacc;
          x += (int64_t)gridDim.x * blockDim.x) {
-        unsigned long long k = key[x];
-        unsigned long long G = k >> sbits;
-        int s = (int)(k & smask);
-        int j = (int)val[x];
-        int cu = ecu[j], cv = ecv[j];
-        bool h = (x == 0) || (key[x - 1] >> sbits) != G;
+        const unsigned long long k = key[x], vv = val[x];
+        const unsigned long long G = k >> sbits;
+        const int s = (int)(k & smask);
+        const int Y = (int)(vv >> 32), O = (int)(vv & 0xffffffffu);  // Y: the pointer's owner
+        const bool h = (x == 0) || (key[x - 1] >> sbits) != G;
         int c1, c2;
         long long add;
         if (h) {
-            c1 = sroot[cu];
-            c2 = sroot[cv];
-            add = ssize[cu] + ssize[cv];
+            c1 = sroot[Y];
+            c2 = sroot[O];
+            add = ssize[Y] + ssize[O];
         } else {
-            int Y = (minr[cu] == s) ? cu : cv;
             c1 = (int)(E + (int64_t)(key[x - 1] & smask));
             c2 = sroot[Y];
             add = ssize[Y];
@@ -175,19 +176,17 @@ __global__ void k_d_chain(const unsigned long long *key, const unsigned long lon
 }
 
 __global__ void k_d_sizes(const unsigned long long *key, const unsigned long long *val, int64_t nacc,
-                          int64_t E, int sbits, const int32_t *ecu, const int32_t *ecv,
-                          const long long *csum, int64_t *lsize, int32_t *svpar, int32_t *sroot,
-                          int64_t *ssize) {
+                          int64_t E, int sbits, const long long *csum, int64_t *lsize, int32_t *svpar,
+                          int32_t *sroot, int64_t *ssize) {
     const unsigned long long smask = (1ull << sbits) - 1ull;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nacc;
          x += (int64_t)gridDim.x * blockDim.x) {
-        unsigned long long k = key[x];
-        unsigned long long G = k >> sbits;
-        int s = (int)(k & smask);
-        int j = (int)val[x];
+        const unsigned long long k = key[x], vv = val[x];
+        const unsigned long long G = k >> sbits;
+        const int s = (int)(k & smask);
         lsize[s] = csum[x];
-        svpar[ecu[j]] = (int32_t)G;
-        svpar[ecv[j]] = (int32_t)G;
+        svpar[(int)(vv >> 32)] = (int32_t)G;
+        svpar[(int)(vv & 0xffffffffu)] = (int32_t)G;
         bool tail = (x == nacc - 1) || (key[x + 1] >> sbits) != G;
         if (tail) {
             sroot[G] = (int32_t)(E + s);
@@ -323,16 +322,17 @@ dgec_status stage_dendro(Ctx *c, const Problem &p, const Csr &g, const Msf &m, D
         int64_t nacc;
         DG_TRY(read_counters(c, (const int64_t *)(s.pos + na), 1, &nacc));
         if (nacc <= 0) return set_err(c, DGEC_ERR_INTERNAL, "dendrogram round accepted no edge");
-        TK(c, "k_d_emit", k_d_emit<<<g, kBlock, 0, st>>>(act, na, ecu, s.gp, s.flag, s.pos, sbits, s.k1, s.v1));
+        TK(c, "k_d_emit", k_d_emit<<<g, kBlock, 0, st>>>(act, na, ecu, ecv, s.minr, s.gp, s.flag, s.pos, sbits,
+                                                         s.k1, s.v1));
         bool in_b;
         DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, s.v1, s.v2}, nacc, 0, lb + sbits, s.radix, &in_b));
         unsigned long long *key = in_b ? s.k2 : s.k1, *val = in_b ? s.v2 : s.v1;
         const int ga = grid_for(nacc, kBlock, kStreamCap);
-        TK(c, "k_d_chain", k_d_chain<<<ga, kBlock, 0, st>>>(key, val, nacc, E, sbits, ecu, ecv, s.minr, s.sroot,
-                                                           s.ssize, o.a, o.b, o.parent, s.contrib, s.head));
+        TK(c, "k_d_chain", k_d_chain<<<ga, kBlock, 0, st>>>(key, val, nacc, E, sbits, s.sroot, s.ssize, o.a, o.b,
+                                                           o.parent, s.contrib, s.head));
         DG_TRY(segmented_inclusive_sum(c, s.contrib, s.head, s.csum, nacc, s.seg_tmp));
-        TK(c, "k_d_sizes", k_d_sizes<<<ga, kBlock, 0, st>>>(key, val, nacc, E, sbits, ecu, ecv, s.csum, o.size,
-                                                           s.svpar, s.sroot, s.ssize));
+        TK(c, "k_d_sizes", k_d_sizes<<<ga, kBlock, 0, st>>>(key, val, nacc, E, sbits, s.csum, o.size, s.svpar,
+                                                           s.sroot, s.ssize));
         TK(c, "k_d_keep", k_d_keep<<<g, kBlock, 0, st>>>(act, na, s.flag, s.pos, act2, ecu, ecv, ecu2, ecv2,
                                                          s.svpar, s.minr, s.tau));
         na -= nacc;

@@ -436,8 +436,11 @@ dgec_status dgec_set_launch_config(dgec_ctx *x, const dgec_launch_config *cfg) {
         return set_err(&x->c, DGEC_ERR_INVALID_ARG, "knn_block must be 64, 128 or 256");
     if (cfg->stream_ctas < 1 || cfg->stream_ctas > (1 << 20))
         return set_err(&x->c, DGEC_ERR_INVALID_ARG, "stream_ctas must be in [1, 2^20]");
+    if (cfg->knn_packed != 0 && cfg->knn_packed != 1)
+        return set_err(&x->c, DGEC_ERR_INVALID_ARG, "knn_packed must be 0 or 1");
     x->c.knn_block = cfg->knn_block;
     x->c.stream_ctas = cfg->stream_ctas;
+    x->c.knn_packed = cfg->knn_packed;
     return DGEC_OK;
 }
 
@@ -445,6 +448,7 @@ dgec_status dgec_get_launch_config(const dgec_ctx *x, dgec_launch_config *cfg) {
     if (!x || !cfg) return DGEC_ERR_INVALID_ARG;
     cfg->knn_block = x->c.knn_block;
     cfg->stream_ctas = (int32_t)x->c.stream_ctas;
+    cfg->knn_packed = x->c.knn_packed;
     return DGEC_OK;
 }
 

@@ -84,7 +84,8 @@ void plan_mrd(Arena &ws, const Problem &p, Skel &h) {
     h.ru = ws.take<int32_t>(L);
     h.rv = ws.take<int32_t>(L);
     h.w = ws.take<int64_t>(L);
-    h.brank = h.arank = h.knn = nullptr;
+    h.arank = nullptr;
+    h.knn = nullptr;
     h.core = nullptr;
     h.n = 0;
 }

@@ -14,6 +14,14 @@ namespace dgec {
 
 constexpr unsigned long long kMax64 = 0xFFFFFFFFFFFFFFFFull;
 
+// A forest edge as the rounds append it: original ends (u < v), internal
+// ends, weight. One 24-byte record, so that the gathers by sorted index
+// after the rounds touch one sector per edge.
+struct FEdge {
+    int32_t u, v, ru, rv;
+    int64_t w;
+};
+
 // Drop edges inside one component; compact the rest; bid w. In the first
 // round every node is its own component, so the label reads are skipped.
 template <bool FIRST>
@@ -179,32 +187,44 @@ __global__ void k_m_bid(const int32_t *cu, const int32_t *cv, const int64_t *w, 
     }
 }
 
+// Items per thread between two slot reservations of the compacting
+// kernels below (one atomic on the shared counter per 2,048 items).
+constexpr int kRes = 8;
+
 // Move labels one hop to the merged roots, drop edges inside one
 // component, compact the rest and bid w.
 __global__ void k_m_filter_bid(const int32_t *cu, const int32_t *cv, const int32_t *u, const int32_t *v,
                                const int64_t *w, int64_t n, const int32_t *par, int32_t *cu2,
                                int32_t *cv2, int32_t *u2, int32_t *v2, int64_t *w2,
                                unsigned long long *cnt, unsigned long long *bw) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {  // CTA-uniform
-        int64_t x = base + threadIdx.x;
-        bool keep = false;
-        int a = 0, b = 0;
-        if (x < n) {
-            a = par[cu[x]];
-            b = par[cv[x]];
-            keep = a != b;
+    const int64_t tile = (int64_t)blockDim.x * kRes;
+    for (int64_t base = (int64_t)blockIdx.x * tile; base < n; base += (int64_t)gridDim.x * tile) {  // CTA-uniform
+        int a[kRes], b[kRes];
+        unsigned keep = 0;
+#pragma unroll
+        for (int q = 0; q < kRes; q++) {
+            const int64_t x = base + (int64_t)q * blockDim.x + threadIdx.x;
+            a[q] = b[q] = 0;
+            if (x < n) {
+                a[q] = par[cu[x]];
+                b[q] = par[cv[x]];
+                if (a[q] != b[q]) keep |= 1u << q;
+            }
         }
-        long long at = cta_reserve(keep, cnt);
-        if (keep) {
-            unsigned long long uw = (unsigned long long)w[x];
-            cu2[at] = a;
-            cv2[at] = b;
+        long long at = cta_reserve_count(__popc(keep), cnt);
+#pragma unroll
+        for (int q = 0; q < kRes; q++) {
+            if (!((keep >> q) & 1u)) continue;
+            const int64_t x = base + (int64_t)q * blockDim.x + threadIdx.x;
+            const unsigned long long uw = (unsigned long long)w[x];
+            cu2[at] = a[q];
+            cv2[at] = b[q];
             u2[at] = u[x];
             v2[at] = v[x];
             w2[at] = (int64_t)uw;
-            if (uw < bw[a]) atomicMin(&bw[a], uw);
-            if (uw < bw[b]) atomicMin(&bw[b], uw);
+            at++;
+            if (uw < bw[a[q]]) atomicMin(&bw[a[q]], uw);
+            if (uw < bw[b[q]]) atomicMin(&bw[b[q]], uw);
         }
     }
 }
@@ -248,33 +268,40 @@ __global__ void k_m_claim(const int32_t *cu, const int32_t *cv, const int32_t *u
 __global__ void k_m_hook(const int32_t *roots, int64_t nr, const unsigned long long *bw,
                          const unsigned long long *buv, const int32_t *bp, const int32_t *win,
                          const int32_t *u, const int32_t *v, const int64_t *w, const int32_t *rank_of,
-                         int32_t *par, int32_t *mu, int32_t *mv, int32_t *mru, int32_t *mrv,
-                         int64_t *mw, unsigned long long *n_out) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nr; base += stride) {  // CTA-uniform
-        int64_t ix = base + threadIdx.x;
-        bool emit = false;
-        int wx = 0;
-        if (ix < nr) {
-            int x = roots[ix];
-            if (bw[x] == kMax64) {
-                par[x] = x;
-            } else {
-                int p = bp[x];
-                bool mutual = bp[p] == x && buv[p] == buv[x];
-                par[x] = (mutual && x < p) ? x : p;
-                emit = !mutual || x < p;
-                wx = win[x];
+                         int32_t *par, FEdge *fe, unsigned long long *n_out) {
+    const int64_t tile = (int64_t)blockDim.x * kRes;
+    for (int64_t base = (int64_t)blockIdx.x * tile; base < nr; base += (int64_t)gridDim.x * tile) {  // CTA-uniform
+        int wx[kRes];
+        unsigned emit = 0;
+#pragma unroll
+        for (int q = 0; q < kRes; q++) {
+            const int64_t ix = base + (int64_t)q * blockDim.x + threadIdx.x;
+            wx[q] = 0;
+            if (ix < nr) {
+                const int x = roots[ix];
+                if (bw[x] == kMax64) {
+                    par[x] = x;
+                } else {
+                    const int p = bp[x];
+                    const bool mutual = bp[p] == x && buv[p] == buv[x];
+                    par[x] = (mutual && x < p) ? x : p;
+                    if (!mutual || x < p) emit |= 1u << q;
+                    wx[q] = win[x];
+                }
             }
         }
-        long long at = cta_reserve(emit, n_out);
-        if (emit) {
-            int a = u[wx], b = v[wx];
-            mu[at] = a;
-            mv[at] = b;
-            mru[at] = rank_of[a];
-            mrv[at] = rank_of[b];
-            mw[at] = w[wx];
+        long long at = cta_reserve_count(__popc(emit), n_out);
+#pragma unroll
+        for (int q = 0; q < kRes; q++) {
+            if (!((emit >> q) & 1u)) continue;
+            const int a = u[wx[q]], b = v[wx[q]];
+            FEdge f;
+            f.u = a;
+            f.v = b;
+            f.ru = rank_of[a];
+            f.rv = rank_of[b];
+            f.w = w[wx[q]];
+            fe[at++] = f;
         }
     }
 }
@@ -299,19 +326,26 @@ __global__ void k_m_jump(const int32_t *roots, int64_t nr, int32_t *par) {
 __global__ void k_m_next_roots(const int32_t *roots, int64_t nr, const int32_t *par,
                                unsigned long long *bw, unsigned long long *buv, int32_t *roots2,
                                unsigned long long *cnt) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nr; base += stride) {  // CTA-uniform
-        int64_t ix = base + threadIdx.x;
-        bool keep = false;
-        int x = 0;
-        if (ix < nr) {
-            x = roots[ix];
-            keep = par[x] == x && bw[x] != kMax64;
-            bw[x] = kMax64;
-            buv[x] = kMax64;
+    const int64_t tile = (int64_t)blockDim.x * kRes;
+    for (int64_t base = (int64_t)blockIdx.x * tile; base < nr; base += (int64_t)gridDim.x * tile) {  // CTA-uniform
+        int xs[kRes];
+        unsigned keep = 0;
+#pragma unroll
+        for (int q = 0; q < kRes; q++) {
+            const int64_t ix = base + (int64_t)q * blockDim.x + threadIdx.x;
+            xs[q] = 0;
+            if (ix < nr) {
+                const int x = roots[ix];
+                xs[q] = x;
+                if (par[x] == x && bw[x] != kMax64) keep |= 1u << q;
+                bw[x] = kMax64;
+                buv[x] = kMax64;
+            }
         }
-        long long at = cta_reserve(keep, cnt);
-        if (keep) roots2[at] = x;
+        long long at = cta_reserve_count(__popc(keep), cnt);
+#pragma unroll
+        for (int q = 0; q < kRes; q++)
+            if ((keep >> q) & 1u) roots2[at++] = xs[q];
     }
 }
 
@@ -326,32 +360,32 @@ __global__ void k_m_init(int64_t E, int32_t *par, int32_t *roots, unsigned long 
     }
 }
 
-__global__ void k_pack_uv_idx(const int32_t *u, const int32_t *v, int64_t n, int idbits,
-                              unsigned long long *k, unsigned long long *val) {
+__global__ void k_pack_uv_idx(const FEdge *fe, int64_t n, int idbits, unsigned long long *k,
+                              unsigned long long *val) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
-        k[x] = ((unsigned long long)u[x] << idbits) | (unsigned long long)v[x];
+        k[x] = ((unsigned long long)fe[x].u << idbits) | (unsigned long long)fe[x].v;
         val[x] = (unsigned long long)x;
     }
 }
 
-__global__ void k_gather_w(const int64_t *w, const unsigned long long *idx, int64_t n,
+__global__ void k_gather_w(const FEdge *fe, const unsigned long long *idx, int64_t n,
                            unsigned long long *k, unsigned long long *val) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
         unsigned long long i = idx[x];
-        k[x] = (unsigned long long)w[i];
+        k[x] = (unsigned long long)fe[i].w;
         val[x] = i;
     }
 }
 
 // graph of each sorted forest edge, as a sort key (graph-major output)
-__global__ void k_gather_graph(const int32_t *tu, const int32_t *egraph, const unsigned long long *idx,
+__global__ void k_gather_graph(const FEdge *fe, const int32_t *egraph, const unsigned long long *idx,
                                int64_t n, unsigned long long *k, unsigned long long *val) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
         unsigned long long i = idx[x];
-        k[x] = (unsigned long long)egraph[tu[i]];
+        k[x] = (unsigned long long)egraph[fe[i].u];
         val[x] = i;
     }
 }
@@ -371,18 +405,16 @@ __global__ void k_graph_offsets(const int32_t *u, const int32_t *egraph, int64_t
     }
 }
 
-__global__ void k_gather_msf(const unsigned long long *idx, int64_t n, const int32_t *tu,
-                             const int32_t *tv, const int32_t *tru, const int32_t *trv,
-                             const int64_t *tw, int32_t *u, int32_t *v, int32_t *ru, int32_t *rv,
-                             int64_t *w) {
+__global__ void k_gather_msf(const unsigned long long *idx, int64_t n, const FEdge *fe, int32_t *u,
+                             int32_t *v, int32_t *ru, int32_t *rv, int64_t *w) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
-        unsigned long long i = idx[x];
-        u[x] = tu[i];
-        v[x] = tv[i];
-        ru[x] = tru[i];
-        rv[x] = trv[i];
-        w[x] = tw[i];
+        const FEdge f = fe[idx[x]];
+        u[x] = f.u;
+        v[x] = f.v;
+        ru[x] = f.ru;
+        rv[x] = f.rv;
+        w[x] = f.w;
     }
 }
 
@@ -399,8 +431,7 @@ struct MsfScratch {
     int32_t *par, *roots, *roots2, *bp, *win;
     int32_t *cua, *cva, *ua, *va, *cub, *cvb, *ub, *vb;
     int64_t *wa, *wb;
-    int32_t *tu, *tv, *tru, *trv;
-    int64_t *tw;
+    FEdge *fe;
     unsigned long long *bw, *buv, *cnt;
     unsigned long long *k1, *k2, *v1, *v2;
     void *radix;
@@ -423,11 +454,7 @@ static MsfScratch carve_msf(Arena &a, const Problem &p) {
     s.ub = a.take<int32_t>(S);
     s.vb = a.take<int32_t>(S);
     s.wb = a.take<int64_t>(S);
-    s.tu = a.take<int32_t>(E);
-    s.tv = a.take<int32_t>(E);
-    s.tru = a.take<int32_t>(E);
-    s.trv = a.take<int32_t>(E);
-    s.tw = a.take<int64_t>(E);
+    s.fe = a.take<FEdge>(E);
     s.bw = a.take<unsigned long long>(E);
     s.buv = a.take<unsigned long long>(E);
     s.cnt = a.take<unsigned long long>(4);
@@ -471,7 +498,7 @@ dgec_status stage_msf(Ctx *c, const Problem &p, const Csr &g, const Skel &sk, Ms
             int32_t *nu = which ? s.ub : s.ua, *nv = which ? s.vb : s.va;
             int64_t *nw = which ? s.wb : s.wa;
             CU_TRY(c, cudaMemsetAsync(s.cnt, 0, sizeof(unsigned long long), st));
-            TK(c, "k_m_filter_bid", k_m_filter_bid<<<grid_for(n, kBlock, kStreamCap), kBlock, 0, st>>>(
+            TK(c, "k_m_filter_bid", k_m_filter_bid<<<grid_for(n, kBlock * kRes, kStreamCap), kBlock, 0, st>>>(
                                       ccu, ccv, cu, cv, cw, n, s.par, ncu, ncv, nu, nv, nw, s.cnt, s.bw));
             int64_t h[3];
             DG_TRY(read_counters(c, (const int64_t *)s.cnt, 3, h));
@@ -485,15 +512,16 @@ dgec_status stage_msf(Ctx *c, const Problem &p, const Csr &g, const Skel &sk, Ms
             cw = nw;
             which ^= 1;
         }
-        const int gn = grid_for(n, kBlock, kStreamCap), gr = grid_for(nr, kBlock, kStreamCap);
+        const int gn = grid_for(n, kBlock, kStreamCap), gr = grid_for(nr, kBlock, kStreamCap),
+                  grk = grid_for(nr, kBlock * kRes, kStreamCap);
         TK(c, "k_m_bid_uv", k_m_bid_uv<<<gn, kBlock, 0, st>>>(ccu, ccv, cu, cv, cw, n, s.bw, s.buv));
         TK(c, "k_m_claim", k_m_claim<<<gn, kBlock, 0, st>>>(ccu, ccv, cu, cv, n, s.buv, s.bp, s.win));
-        TK(c, "k_m_hook", k_m_hook<<<gr, kBlock, 0, st>>>(roots, nr, s.bw, s.buv, s.bp, s.win, cu, cv, cw,
-                                                        g.rank_of, s.par, s.tu, s.tv, s.tru, s.trv, s.tw,
+        TK(c, "k_m_hook", k_m_hook<<<grk, kBlock, 0, st>>>(roots, nr, s.bw, s.buv, s.bp, s.win, cu, cv, cw,
+                                                        g.rank_of, s.par, s.fe,
                                                         s.cnt + 1));
         TK(c, "k_m_jump", k_m_jump<<<gr, kBlock, 0, st>>>(roots, nr, s.par));
         CU_TRY(c, cudaMemsetAsync(s.cnt + 2, 0, sizeof(unsigned long long), st));
-        TK(c, "k_m_next_roots", k_m_next_roots<<<gr, kBlock, 0, st>>>(roots, nr, s.par, s.bw, s.buv, roots2,
+        TK(c, "k_m_next_roots", k_m_next_roots<<<grk, kBlock, 0, st>>>(roots, nr, s.par, s.bw, s.buv, roots2,
                                                                     s.cnt + 2));
         int32_t *tr = roots;
         roots = roots2;
@@ -509,17 +537,17 @@ dgec_status stage_msf(Ctx *c, const Problem &p, const Csr &g, const Skel &sk, Ms
     unsigned long long *K[2] = {s.k1, s.k2}, *Vb[2] = {s.v1, s.v2};
     int cur = 0;
     bool in_b;
-    TK(c, "k_pack_uv_idx", k_pack_uv_idx<<<gm, kBlock, 0, st>>>(s.tu, s.tv, m, p.idbits, K[0], Vb[0]));
+    TK(c, "k_pack_uv_idx", k_pack_uv_idx<<<gm, kBlock, 0, st>>>(s.fe, m, p.idbits, K[0], Vb[0]));
     DG_TRY(radix_sort(c, RadixBuffers{K[cur], K[1 - cur], Vb[cur], Vb[1 - cur]}, m, 0, 2 * p.idbits,
                       s.radix, &in_b));
     if (in_b) cur = 1 - cur;
-    TK(c, "k_gather_w", k_gather_w<<<gm, kBlock, 0, st>>>(s.tw, Vb[cur], m, K[1 - cur], Vb[1 - cur]));
+    TK(c, "k_gather_w", k_gather_w<<<gm, kBlock, 0, st>>>(s.fe, Vb[cur], m, K[1 - cur], Vb[1 - cur]));
     cur = 1 - cur;
     DG_TRY(radix_sort(c, RadixBuffers{K[cur], K[1 - cur], Vb[cur], Vb[1 - cur]}, m, 0,
                       p.tbits > 0 ? p.tbits : 1, s.radix, &in_b));
     if (in_b) cur = 1 - cur;
     if (p.G > 1) {
-        TK(c, "k_gather_graph", k_gather_graph<<<gm, kBlock, 0, st>>>(s.tu, p.egraph, Vb[cur], m, K[1 - cur],
+        TK(c, "k_gather_graph", k_gather_graph<<<gm, kBlock, 0, st>>>(s.fe, p.egraph, Vb[cur], m, K[1 - cur],
                                                                      Vb[1 - cur]));
         cur = 1 - cur;
         DG_TRY(radix_sort(c, RadixBuffers{K[cur], K[1 - cur], Vb[cur], Vb[1 - cur]}, m, 0,
@@ -527,7 +555,7 @@ dgec_status stage_msf(Ctx *c, const Problem &p, const Csr &g, const Skel &sk, Ms
         if (in_b) cur = 1 - cur;
     }
     unsigned long long *fin = Vb[cur];
-    TK(c, "k_gather_msf", k_gather_msf<<<gm, kBlock, 0, st>>>(fin, m, s.tu, s.tv, s.tru, s.trv, s.tw, o.u, o.v,
+    TK(c, "k_gather_msf", k_gather_msf<<<gm, kBlock, 0, st>>>(fin, m, s.fe, o.u, o.v,
                                                               o.ru, o.rv, o.w));
     TK(c, "k_graph_offsets", k_graph_offsets<<<grid_for(p.G + 1), kBlock, 0, st>>>(o.u, p.egraph, m, p.G, o.goff));
     return DGEC_OK;

@@ -21,14 +21,15 @@
 
 namespace dgec {
 
-// brank[e] = #in-edges of src[e] with t <= t_e; arank[e] = #out-edges of
+// b[e] = outrk[e].y = #in-edges of src[e] with t <= t_e; arank[e] = #out-edges of
 // dst[e] with t < t_e (both from stage A's merged lists).
 // All node ids below are internal ids r (see the stage A notes).
 struct SkView {
     const int32_t *src, *dst;  // isrc, idst (by r)
     const int64_t *out_off, *in_off;
-    const int32_t *out_id, *in_id, *slot_out;  // out_r, in_r, slot_out (by r)
-    const int32_t *brank, *arank;
+    const int32_t *out_id, *in_id;  // out_r, in_r
+    const int2 *outrk;              // by r: (out-list slot, b)
+    const int32_t *arank;
 };
 
 // Does Alg. 2 at vertex x emit the pair (in-edge pin, out-edge qout)?
@@ -36,90 +37,98 @@ __device__ __forceinline__ bool emitted_at(const SkView &g, int x, int pin, int 
     int64_t ob = g.out_off[x], nout = g.out_off[x + 1] - ob;
     int a = g.arank[pin];
     if (a < nout && g.out_id[ob + a] == qout) return true;  // type 1
-    int64_t sq = g.slot_out[qout];
+    int64_t sq = g.outrk[qout].x;
     if (sq > ob) {                                          // type 2
-        int b = g.brank[g.out_id[sq - 1]];
+        int b = g.outrk[g.out_id[sq - 1]].y;
         if (b >= 1 && g.in_id[g.in_off[x] + b - 1] == pin) return true;
     }
     return false;
 }
 
-// part[e] / part[E + e]: partner of edge e through its type-1 / type-2
-// link (-1 if none), wgt the P3 weight. With the time cutoff of Sec. 4.3
+// The links, walking the lists in order (with the time cutoff of Sec. 4.3
 // only links with w <= dmax are kept: by Thm. 3 the kept links have, at
 // every threshold, the components of the line graph without the longer
-// arcs.
-__global__ void k_links(SkView g, const int64_t *t, const int64_t *out_t, const int64_t *in_t,
-                        int64_t E, int64_t dmax, int32_t *part, int64_t *wgt, int *flag) {
-    // e below is an internal id r; t, src, dst are the r-ordered copies
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int i = g.src[e], j = g.dst[e];
-        int64_t te = t[e];
-        // type 1: e is p_x at j, linked to q_{a_x}
-        int32_t p1 = -1;
-        int64_t w1 = 0;
-        {
-            int64_t ob = g.out_off[j], nout = g.out_off[j + 1] - ob;
-            int a = g.arank[e];
-            if (a < nout) {
-                int q = g.out_id[ob + a];
-                int64_t w = out_t[ob + a] - te;
-                bool drop = (w == 0) && g.dst[q] == i && (int)e > q && emitted_at(g, i, q, (int)e);
-                if (!drop) {
-                    p1 = q;
-                    w1 = w;
-                }
-            }
+// arcs). Each link goes to a 16-byte record at its emitting edge's internal
+// id (type 1 at r, type 2 at E + r), so the compacted skeleton keeps the
+// (t, id) order of the emitting edges and the forest rounds read their
+// endpoints with time locality; partner -1 where there is no link.
+struct LinkRec {
+    int32_t partner;
+    int32_t keep;
+    int64_t w;
+};
+
+// Type 1, over the in-list slots: the in-edge e at slot x of vertex j (its
+// p_x) links to q_{a_x}, the first out-edge of j not before it. a is
+// nondecreasing along j's in-list, so the partners are read nearly in order.
+__global__ void k_links_in(SkView g, const int2 *in_va, const int64_t *out_t, const int64_t *in_t, int64_t E,
+                           int64_t dmax, LinkRec *rec) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < E;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int2 va = in_va[x];
+        const int j = va.x, a = va.y, e = g.in_id[x];
+        const int64_t ob = g.out_off[j], nout = g.out_off[j + 1] - ob;
+        LinkRec l{-1, 0, 0};
+        if (a < nout) {
+            const int q = g.out_id[ob + a];
+            const int64_t w = out_t[ob + a] - in_t[x];
+            // a reciprocal concurrent pair is kept once (at the vertex whose in-edge has the smaller id)
+            const bool drop = (w == 0) && g.dst[q] == g.src[e] && e > q && emitted_at(g, g.src[e], q, e);
+            if (!drop) l = LinkRec{q, w <= dmax, w};
         }
-        // type 2: e is q_m (m >= 1) at i, linked to p_{b_{m-1} - 1}
-        int32_t p2 = -1;
-        int64_t w2 = 0;
-        {
-            int64_t sl = g.slot_out[e];
-            if (sl > g.out_off[i]) {
-                int b = g.brank[g.out_id[sl - 1]];
-                if (b >= 1) {
-                    int64_t pp = g.in_off[i] + b - 1;
-                    int p = g.in_id[pp];
-                    int64_t w = te - in_t[pp];
-                    bool drop = (w == 0) && g.src[p] == j && p > (int)e && emitted_at(g, j, (int)e, p);
-                    if (!drop) {
-                        p2 = p;
-                        w2 = w;
-                    }
-                }
-            }
-        }
-        part[e] = p1;
-        wgt[e] = w1;
-        part[E + e] = p2;
-        wgt[E + e] = w2;
-        flag[e] = p1 >= 0 && w1 <= dmax;
-        flag[E + e] = p2 >= 0 && w2 <= dmax;
+        rec[e] = l;
     }
 }
 
-__global__ void k_compact_links(const int32_t *part, const int64_t *wgt, const int *flag,
-                                const long long *pos, int64_t E, const int32_t *orig_of, int32_t *ru,
-                                int32_t *rv, int32_t *u, int32_t *v, int64_t *w) {
+// Type 2, over the out-list slots: the out-edge e at slot y of vertex i (its
+// q_m, m >= 1) links to p_{b_{m-1} - 1}, where b_{m-1} is the b of the
+// out-edge in slot y - 1; b is nondecreasing along i's out-list.
+__global__ void k_links_out(SkView g, const int2 *out_vb, const int64_t *out_t, const int64_t *in_t,
+                            int64_t E, int64_t dmax, LinkRec *rec) {
+    for (int64_t y = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; y < E;
+         y += (int64_t)gridDim.x * blockDim.x) {
+        const int i = out_vb[y].x, e = g.out_id[y];
+        LinkRec l{-1, 0, 0};
+        if (y > g.out_off[i]) {
+            const int b = out_vb[y - 1].y;
+            if (b >= 1) {
+                const int64_t pp = g.in_off[i] + b - 1;
+                const int p = g.in_id[pp];
+                const int64_t w = out_t[y] - in_t[pp];
+                const bool drop = (w == 0) && g.src[p] == g.dst[e] && p > e && emitted_at(g, g.dst[e], e, p);
+                if (!drop) l = LinkRec{p, w <= dmax, w};
+            }
+        }
+        rec[E + e] = l;
+    }
+}
+
+struct LoadKeep {
+    const LinkRec *rec;
+    int64_t n;
+    __device__ __forceinline__ long long operator()(int64_t i) const { return i < n ? rec[i].keep : 0; }
+};
+
+__global__ void k_compact_links(const LinkRec *rec, const long long *pos, int64_t E, const int32_t *orig_of,
+                                int32_t *ru, int32_t *rv, int32_t *u, int32_t *v, int64_t *w) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < 2 * E;
          x += (int64_t)gridDim.x * blockDim.x) {
-        if (!flag[x]) continue;
-        int self = (int)(x < E ? x : x - E), o = part[x];
-        int64_t at = pos[x];
-        int es = orig_of[self], eo = orig_of[o];
+        const LinkRec l = rec[x];
+        if (!l.keep) continue;
+        const int self = (int)(x < E ? x : x - E), o = l.partner;
+        const int es = orig_of[self], eo = orig_of[o];
+        const int64_t at = pos[x];
         ru[at] = self;
         rv[at] = o;
         u[at] = es < eo ? es : eo;
         v[at] = es < eo ? eo : es;
-        w[at] = wgt[x];
+        w[at] = l.w;
     }
 }
 
 // ---------------------------------------------------------------- kNN
 // Neighbours of e = (i, j, t_e) in the undirected L_G: in-edges r of i with
-// t_r <= t_e (prefix of i's in-list of length brank[e]) and out-edges s of
+// t_r <= t_e (prefix of i's in-list of length b[e]) and out-edges s of
 // j with t_s >= t_e (suffix of j's out-list from arank[e]). Ranked by
 // (|dt|, id). The K best of each side suffice: the successor side is
 // already in (w, id) order from arank; on the predecessor side the last K
@@ -146,7 +155,7 @@ __global__ void __launch_bounds__(256) k_knn(const int32_t *src, const int32_t *
                                              const int64_t *out_t, const int32_t *out_id,
                                              const int64_t *in_off, const int64_t *in_t,
                                              const int32_t *in_id, const int32_t *in_gs,
-                                             const int32_t *brank, const int32_t *arank, int G,
+                                             const int2 *outrk, const int32_t *arank, int G,
                                              const int32_t *egraph, const int64_t *eoff,
                                              const int32_t *gk, const int64_t *knn_off, int64_t dmax,
                                              int32_t *knn, int64_t *core) {
@@ -165,7 +174,7 @@ __global__ void __launch_bounds__(256) k_knn(const int32_t *src, const int32_t *
         int32_t *row = knn + knn_off[gr] + (e - e0) * k;
         const int64_t ib = in_off[i];
         const int64_t ob = out_off[j], nout = out_off[j + 1] - ob;
-        const int64_t b = brank[r], a = arank[r];
+        const int64_t b = outrk[r].y, a = arank[r];
         Cand c[N];
         // predecessor window: the last K of the prefix [0, b); a tie group
         // that crosses its start contributes its smallest ids
@@ -238,8 +247,95 @@ __global__ void __launch_bounds__(256) k_knn(const int32_t *src, const int32_t *
     }
 }
 
+// The same for time spans below 2^32 (every |dt| fits 32 bits): a
+// candidate is one 64-bit key (w << 32 | id), so the network sorts plain
+// integers (two registers a candidate instead of three, one compare a step)
+// and the kernel keeps more warps resident to hide its gathers' latency.
+template <int K>
+__global__ void __launch_bounds__(256, K <= 8 ? 4 : 1) k_knn32(const int32_t *src, const int32_t *dst, const int64_t *t,
+                                               const int32_t *orig_of, int64_t E, const int64_t *out_off,
+                                               const int64_t *out_t, const int32_t *out_id,
+                                               const int64_t *in_off, const int64_t *in_t,
+                                               const int32_t *in_id, const int32_t *in_gs,
+                                               const int2 *outrk, const int32_t *arank, int G,
+                                               const int32_t *egraph, const int64_t *eoff,
+                                               const int32_t *gk, const int64_t *knn_off, int64_t dmax,
+                                               int32_t *knn, int64_t *core) {
+    constexpr int N = 2 * K;
+    constexpr unsigned long long kNone = 0xFFFFFFFFFFFFFFFFull;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < E;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int i = src[r], j = dst[r];
+        const long long te = t[r];
+        const int64_t e = orig_of[r];
+        const int gr = G > 1 ? egraph[e] : 0;
+        const int k = gk[gr];
+        const int64_t e0 = eoff[gr];
+        int32_t *row = knn + knn_off[gr] + (e - e0) * k;
+        const int64_t ib = in_off[i];
+        const int64_t ob = out_off[j], nout = out_off[j + 1] - ob;
+        const int64_t b = outrk[r].y, a = arank[r];
+        unsigned long long c[N];
+        const int64_t lo = b - K > 0 ? b - K : 0;
+        int64_t g0 = lo, take_grp = 0;
+        const bool cross = lo > 0 && in_t[ib + lo] == in_t[ib + lo - 1];
+        if (cross) {
+            const long long T = in_t[ib + lo];
+            g0 = (int64_t)in_gs[ib + lo] - ib;
+            int64_t g1 = lo;
+            while (g1 < b && in_t[ib + g1] == T) g1++;  // at most K steps
+            take_grp = g1 - lo;
+        }
+#pragma unroll
+        for (int x = 0; x < K; x++) {
+            const int64_t idx = x < take_grp ? g0 + x : lo + x;
+            c[x] = idx < b ? ((unsigned long long)(te - in_t[ib + idx]) << 32) | (unsigned)in_id[ib + idx]
+                           : kNone;
+        }
+#pragma unroll
+        for (int x = 0; x < K; x++) {
+            const int64_t idx = a + x;
+            c[K + x] = idx < nout ? ((unsigned long long)(out_t[ob + idx] - te) << 32) | (unsigned)out_id[ob + idx]
+                                  : kNone;
+        }
+#pragma unroll
+        for (int size = 2; size <= N; size <<= 1) {
+#pragma unroll
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+#pragma unroll
+                for (int lo2 = 0; lo2 < N; lo2++) {
+                    const int hi2 = lo2 ^ stride;
+                    if (hi2 > lo2) {
+                        const bool up = (lo2 & size) == 0;
+                        const unsigned long long x0 = c[lo2], x1 = c[hi2];
+                        const bool sw = up ? x1 < x0 : x0 < x1;
+                        c[lo2] = sw ? x1 : x0;
+                        c[hi2] = sw ? x0 : x1;
+                    }
+                }
+            }
+        }
+        int cnt = 0;
+        long long last_w = LLONG_MAX;
+        unsigned prev = 0xFFFFFFFFu;
+#pragma unroll
+        for (int x = 0; x < N; x++) {
+            const unsigned id = (unsigned)c[x];
+            const long long w = (long long)(c[x] >> 32);
+            if (c[x] != kNone && id != prev && cnt < k && w <= dmax) {
+                row[cnt] = (int32_t)((int64_t)id - e0);
+                last_w = w;
+                cnt++;
+            }
+            prev = id;
+        }
+        for (int x = cnt; x < k; x++) row[x] = -1;
+        core[e] = cnt == k ? last_w : LLONG_MAX;
+    }
+}
+
 void plan_skel(Arena &ws, const Problem &p, Skel &o) {
-    o.brank = o.arank = nullptr;  // the ranks live in stage A's output
+    o.arank = nullptr;  // the ranks live in stage A's output
     o.u = ws.take<int32_t>(2 * p.E);
     o.v = ws.take<int32_t>(2 * p.E);
     o.ru = ws.take<int32_t>(2 * p.E);
@@ -250,16 +346,12 @@ void plan_skel(Arena &ws, const Problem &p, Skel &o) {
 }
 
 struct SkScratch {
-    int32_t *part;
-    int64_t *wgt;
-    int *flag;
+    LinkRec *rec;
     long long *pos, *scan_tmp;
 };
 static SkScratch carve_skel(Arena &a, const Problem &p) {
     SkScratch s;
-    s.part = a.take<int32_t>(2 * p.E);
-    s.wgt = a.take<int64_t>(2 * p.E);
-    s.flag = a.take<int>(2 * p.E + 1);
+    s.rec = a.take<LinkRec>(2 * p.E);
     s.pos = a.take<long long>(2 * p.E + 1);
     s.scan_tmp = a.take<long long>(scan_scratch_elems(2 * p.E + 1));
     return s;
@@ -270,8 +362,6 @@ size_t skel_scratch_bytes(const Problem &p) {
     return a.off;
 }
 
-__global__ void k_zero_i32(int *p) { *p = 0; }
-
 dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void *scratch) {
     cudaStream_t st = c->stream;
     o.n = 0;
@@ -281,24 +371,29 @@ dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void
     int64_t E = p.E;
     const int kb = c->knn_block;
     int grid = grid_for(E, kb, 1 << 20);
-    o.brank = g.brank;
     o.arank = g.arank;
 #define KNN_ARGS                                                                                   \
     g.isrc, g.idst, g.it, g.orig_of, E, g.out_off, g.out_t, g.out_id, g.in_off, g.in_t, g.in_id, g.in_gs, \
-        g.brank, g.arank, p.G, p.egraph, p.eoff, p.gk, p.knn_off, p.dmax, o.knn, o.core
-    if (p.knn) {
+        g.outrk, g.arank, p.G, p.egraph, p.eoff, p.gk, p.knn_off, p.dmax, o.knn, o.core
+    if (p.knn && c->knn_packed && p.tbits <= 32) {  // every |dt| fits 32 bits: packed candidate keys
+        if (p.k <= 4) TK(c, "k_knn", k_knn32<4><<<grid, kb, 0, st>>>(KNN_ARGS));
+        else if (p.k <= 8) TK(c, "k_knn", k_knn32<8><<<grid, kb, 0, st>>>(KNN_ARGS));
+        else TK(c, "k_knn", k_knn32<16><<<grid, kb, 0, st>>>(KNN_ARGS));
+    } else if (p.knn) {
         if (p.k <= 4) TK(c, "k_knn", k_knn<4><<<grid, kb, 0, st>>>(KNN_ARGS));
         else if (p.k <= 8) TK(c, "k_knn", k_knn<8><<<grid, kb, 0, st>>>(KNN_ARGS));
         else TK(c, "k_knn", k_knn<16><<<grid, kb, 0, st>>>(KNN_ARGS));
     }
 #undef KNN_ARGS
-    SkView v{g.isrc, g.idst, g.out_off, g.in_off, g.out_r, g.in_r, g.slot_out, o.brank, o.arank};
-    TK(c, "k_links", k_links<<<grid_for(E, kBlock, kStreamCap), kBlock, 0, st>>>(v, g.it, g.out_t, g.in_t, E, p.dmax,
-                                                                          s.part, s.wgt, s.flag));
-    TK(c, "k_zero_i32", k_zero_i32<<<1, 1, 0, st>>>(s.flag + 2 * E));
-    DG_TRY(exclusive_scan_i32(c, s.flag, s.pos, 2 * E + 1, s.scan_tmp));
+    SkView v{g.isrc, g.idst, g.out_off, g.in_off, g.out_r, g.in_r, g.outrk, g.arank};
+    TK(c, "k_links_in", k_links_in<<<grid_for(E, kBlock, kStreamCap), kBlock, 0, st>>>(
+                            v, g.in_va, g.out_t, g.in_t, E, p.dmax, s.rec));
+    TK(c, "k_links_out", k_links_out<<<grid_for(E, kBlock, kStreamCap), kBlock, 0, st>>>(
+                             v, g.out_vb, g.out_t, g.in_t, E, p.dmax, s.rec));
+    DG_TRY((device_scan<long long, SumI64, LoadKeep, StorePtr<long long>>(
+        c, LoadKeep{s.rec, 2 * E}, StorePtr<long long>{s.pos}, 2 * E + 1, SumI64{}, 0ll, false, s.scan_tmp)));
     TK(c, "k_compact_links", k_compact_links<<<grid_for(2 * E, kBlock, kStreamCap), kBlock, 0, st>>>(
-                                 s.part, s.wgt, s.flag, s.pos, E, g.orig_of, o.ru, o.rv, o.u, o.v, o.w));
+                                 s.rec, s.pos, E, g.orig_of, o.ru, o.rv, o.u, o.v, o.w));
     int64_t n;
     DG_TRY(read_counters(c, (const int64_t *)(s.pos + 2 * E), 1, &n));
     o.n = n;

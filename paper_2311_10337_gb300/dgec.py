@@ -35,7 +35,8 @@ MAX_LEVELS = 64
 
 
 class LaunchConfig(ctypes.Structure):
-    _fields_ = [("knn_block", ctypes.c_int32), ("stream_ctas", ctypes.c_int32)]
+    _fields_ = [("knn_block", ctypes.c_int32), ("stream_ctas", ctypes.c_int32),
+                ("knn_packed", ctypes.c_int32)]
 
 
 class DgecError(RuntimeError):
@@ -324,15 +325,17 @@ class Context:
             i += 1
         return out
 
-    def set_launch_config(self, knn_block: int, stream_ctas: int):
-        """Threads per CTA of the kNN kernel and CTAs of the grid-stride
-        streaming kernels for the calls on this context (speed only)."""
-        self._check(self.L.dgec_set_launch_config(self.h, ctypes.byref(LaunchConfig(knn_block, stream_ctas))))
+    def set_launch_config(self, knn_block: int, stream_ctas: int, knn_packed: int = 0):
+        """Threads per CTA of the kNN kernel, CTAs of the grid-stride
+        streaming kernels and the kNN candidate form (packed 64-bit keys or
+        not) for the calls on this context (speed only)."""
+        cfg = LaunchConfig(knn_block, stream_ctas, knn_packed)
+        self._check(self.L.dgec_set_launch_config(self.h, ctypes.byref(cfg)))
 
     def launch_config(self) -> tuple:
         c = LaunchConfig()
         self._check(self.L.dgec_get_launch_config(self.h, ctypes.byref(c)))
-        return int(c.knn_block), int(c.stream_ctas)
+        return int(c.knn_block), int(c.stream_ctas), int(c.knn_packed)
 
     def stage_timing(self) -> list:
         """[(stage name, device ms)] of the last completed call, in order."""

@@ -1,7 +1,8 @@
 """Autotuner of the launch configuration (dgec_set_launch_config).
 
-Two parameters change speed and never results: the kNN kernel's threads per
-CTA and the CTA count of the grid-stride streaming kernels. For one GPU
+Three parameters change speed and never results: the kNN kernel's threads
+per CTA, the CTA count of the grid-stride streaming kernels and the form of
+the kNN kernel's candidates (packed 64-bit keys or not). For one GPU
 model and one workload shape the tuner times the whole path (CUDA events on
 the launching stream, after a warm-up) for each candidate, one parameter at
 a time, keeps the fastest, and caches the choice in a JSON file keyed by the
@@ -61,9 +62,10 @@ def _time_ms(run, steps):
 
 
 def tune(ctx, run, signature: str, steps: int = 2, use_cache: bool = True) -> dict:
-    """Pick (knn_block, stream_ctas) for `run` (a callable making one call
-    on ctx) and leave ctx configured with it. Returns the choice, the
-    timings of every candidate tried, and whether it came from the cache."""
+    """Pick (knn_block, stream_ctas, knn_packed) for `run` (a callable making
+    one call on ctx) and leave ctx configured with it, one parameter at a
+    time. Returns the choice, the timings of every candidate tried, and
+    whether it came from the cache."""
     import torch
     gpu = torch.cuda.get_device_name(ctx.device)
     path = cache_path()
@@ -71,30 +73,29 @@ def tune(ctx, run, signature: str, steps: int = 2, use_cache: bool = True) -> di
         with _lock:
             hit = _read_cache(path).get(gpu, {}).get(signature)
         if hit:
-            ctx.set_launch_config(int(hit["knn_block"]), int(hit["stream_ctas"]))
+            ctx.set_launch_config(int(hit["knn_block"]), int(hit["stream_ctas"]), int(hit.get("knn_packed", 0)))
             return dict(hit, cached=True)
     sms = torch.cuda.get_device_properties(ctx.device).multi_processor_count
-    kb, sc = ctx.launch_config()
-    trials = []
-    best_sc, best = sc, None
-    for cand in stream_cta_candidates(sms):
-        ctx.set_launch_config(kb, cand)
-        ms = _time_ms(run, steps)
-        trials.append({"knn_block": kb, "stream_ctas": cand, "ms": round(ms, 3)})
-        if best is None or ms < best:
-            best, best_sc = ms, cand
-    best_kb = kb
-    for cand in KNN_BLOCKS:
-        if cand == kb:
-            continue
-        ctx.set_launch_config(cand, best_sc)
-        ms = _time_ms(run, steps)
-        trials.append({"knn_block": cand, "stream_ctas": best_sc, "ms": round(ms, 3)})
-        if ms < best:
-            best, best_kb = ms, cand
-    ctx.set_launch_config(best_kb, best_sc)
-    choice = {"knn_block": best_kb, "stream_ctas": best_sc, "ms": round(best, 3), "gpu": gpu,
-              "signature": signature}
+    cfg = list(ctx.launch_config())
+    best = _time_ms(run, steps)  # the starting configuration
+    trials = [{"knn_block": cfg[0], "stream_ctas": cfg[1], "knn_packed": cfg[2], "ms": round(best, 3)}]
+    for dim, cands in ((1, stream_cta_candidates(sms)), (0, KNN_BLOCKS), (2, (0, 1))):
+        best_v = cfg[dim]
+        for cand in cands:
+            if cand == cfg[dim]:
+                continue  # the current value is timed already
+            trial = list(cfg)
+            trial[dim] = cand
+            ctx.set_launch_config(*trial)
+            ms = _time_ms(run, steps)
+            trials.append({"knn_block": trial[0], "stream_ctas": trial[1], "knn_packed": trial[2],
+                           "ms": round(ms, 3)})
+            if ms < best:
+                best, best_v = ms, cand
+        cfg[dim] = best_v
+    ctx.set_launch_config(*cfg)
+    choice = {"knn_block": cfg[0], "stream_ctas": cfg[1], "knn_packed": cfg[2], "ms": round(best, 3),
+              "gpu": gpu, "signature": signature}
     with _lock:
         data = _read_cache(path)
         data.setdefault(gpu, {})[signature] = choice

@@ -102,3 +102,44 @@ def test_batch_rejects_bad_tables():
         t = torch.tensor([0, 1], dtype=torch.int64, device="cuda")
         ctx().run_batch(s, d, t, np.array([0, 1, 2]), np.array([2, 3]), np.array([4, 4]),
                         np.array([5, 5]))
+
+
+def test_batch_passes_size_extremes_match_oracle():
+    """The batching workload's own law (E_b = 10^U(3, 6), k in {4, 8, 16}) run
+    in several passes, as the benchmark runs its 4,096 graphs: every graph's
+    labels equal a solo run's, and the smallest and the largest graph equal
+    the oracle (labels, forest, dendrogram; kNN rows for sampled edges of the
+    largest, whose top vertex has hundreds of thousands of edges)."""
+    import torch
+    b = synth.batch(24, 3.0, 6.0, seed_offset=7)
+    sizes = np.diff(b.edge_off)
+    assert sizes.min() < 5_000 and sizes.max() > 300_000
+    s = torch.from_numpy(b.src).cuda()
+    d = torch.from_numpy(b.dst).cuda()
+    t = torch.from_numpy(b.t).cuda()
+    lab = torch.full((int(b.edge_off[-1]),), -7, dtype=torch.int32, device="cuda")
+    ncl, passes = ctx().run_batch_passes(s, d, t, b.edge_off, b.n_vertices, b.k, b.min_cluster_size,
+                                         2_000_000, lab)
+    assert passes >= 3
+    lab = lab.cpu().numpy()
+    for g in range(b.n_graphs):
+        a, z = int(b.edge_off[g]), int(b.edge_off[g + 1])
+        ref = run_gpu(b.src[a:z], b.dst[a:z], b.t[a:z], int(b.n_vertices[g]), int(b.k[g]),
+                      int(b.min_cluster_size[g]))
+        assert np.array_equal(lab[a:z], ref["labels"]) and ncl[g] == ref["n_clusters"], g
+    for g in (int(np.argmin(sizes)), int(np.argmax(sizes))):
+        a, z = int(b.edge_off[g]), int(b.edge_off[g + 1])
+        src, dst, tt = b.src[a:z], b.dst[a:z], b.t[a:z]
+        V, k, M = int(b.n_vertices[g]), int(b.k[g]), int(b.min_cluster_size[g])
+        q = np.sort(np.random.default_rng(g).choice(z - a, min(100, z - a), replace=False)).astype(np.int32)
+        r = O.run(src, dst, tt, V, k, M, knn_query=q)
+        got = run_gpu(src, dst, tt, V, k, M)
+        assert np.array_equal(lab[a:z], r["condensed"]["labels"]), g
+        mu, mv, mw = r["mst"]
+        assert np.array_equal(got["mst_u"], mu) and np.array_equal(got["mst_v"], mv)
+        assert np.array_equal(got["mst_w"], mw)
+        la, lb, sz = r["linkage"]
+        assert np.array_equal(got["link_a"], la) and np.array_equal(got["link_b"], lb)
+        assert np.array_equal(got["link_size"], sz)
+        assert np.array_equal(got["knn_id"].reshape(z - a, k)[q], r["knn"][0])
+        assert np.array_equal(got["core"][q], r["knn"][1])

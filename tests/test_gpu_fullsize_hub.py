@@ -1,8 +1,8 @@
 """Parity at the largest configuration: the 200M-edge hub workload (10M
 vertices; half the edges a Zipf(1.8) background on a 60 s grid, so the top
-vertices carry ~10^8 edges and tie groups of thousands), run through the
-benchmark's entry point and launch configuration (k = 8, M = 5, the current
-stream).
+vertices carry tens of millions of edges and tie groups of thousands), run
+through the benchmark's entry point and launch configuration (k = 8, M = 5,
+the current stream).
 
 The oracle's chain runs on the whole graph (Alg. 3's skeleton, then Alg. 1's
 Kruskal forest, union-find dendrogram and condensing: minutes of single-core
@@ -10,7 +10,8 @@ C), so the skeleton set, the forest, the dendrogram rows, every
 condensed-tree array and the labels are compared element by element. kNN
 rows are recomputed one by one by the oracle for sampled edges, among them
 edges whose tail or head is one of the largest hubs (their candidate sets
-hold ~10^8 entries and their windows cross tie groups of thousands). The
+hold tens of millions of entries and their windows cross tie groups of
+thousands). The
 incidence lists are fixed exactly by their defining properties (offsets
 from the degrees; each list a permutation sorted by (t, id)). The discrete
 dendrogram's per-level component counts are checked against the forest."""
@@ -131,16 +132,16 @@ def test_knn_sampled_light(hub):
 
 
 def test_knn_sampled_top_hubs(hub):
-    """Edges whose tail has the largest in-list (~10^8 predecessors, windows
-    crossing tie groups of thousands on the 60 s grid) and edges whose head
-    has the largest out-list."""
+    """Edges whose tail has the largest in-list (tens of millions of
+    predecessors, windows crossing tie groups of thousands on the 60 s grid)
+    and edges whose head has the largest out-list."""
     w, r = hub
     indeg = np.bincount(w.dst, minlength=w.n_vertices)
     outdeg = np.bincount(w.src, minlength=w.n_vertices)
     rng = np.random.default_rng(17)
     hub_in = int(np.argmax(indeg))
     hub_out = int(np.argmax(outdeg))
-    assert indeg[hub_in] > 5e7 and outdeg[hub_out] > 5e7
+    assert indeg[hub_in] > 1e7 and outdeg[hub_out] > 1e7
     q = np.concatenate([rng.choice(np.nonzero(w.src == hub_in)[0], 3, replace=False),
                         rng.choice(np.nonzero(w.dst == hub_out)[0], 3, replace=False)])
     q = np.unique(q)

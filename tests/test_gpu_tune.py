@@ -19,10 +19,11 @@ def test_every_launch_config_gives_identical_outputs():
     try:
         for kb in tune.KNN_BLOCKS:
             for sc in (152, 2432, 65536):
-                c.set_launch_config(kb, sc)
-                got = run_gpu(w.src, w.dst, w.t, w.n_vertices, w.k, w.min_cluster_size)
-                for key in ref:
-                    assert np.array_equal(np.asarray(got[key]), np.asarray(ref[key])), (kb, sc, key)
+                for packed in (0, 1):
+                    c.set_launch_config(kb, sc, packed)
+                    got = run_gpu(w.src, w.dst, w.t, w.n_vertices, w.k, w.min_cluster_size)
+                    for key in ref:
+                        assert np.array_equal(np.asarray(got[key]), np.asarray(ref[key])), (kb, sc, packed, key)
     finally:
         c.set_launch_config(*default)
 
@@ -31,9 +32,9 @@ def test_bad_launch_config_is_rejected():
     from paper_2311_10337_gb300 import dgec
     c = ctx()
     default = c.launch_config()
-    for kb, sc in ((96, 1000), (128, 0), (128, (1 << 20) + 1)):
+    for kb, sc, pk in ((96, 1000, 0), (128, 0, 0), (128, (1 << 20) + 1, 0), (128, 1000, 2)):
         with pytest.raises(dgec.DgecError) as ei:
-            c.set_launch_config(kb, sc)
+            c.set_launch_config(kb, sc, pk)
         assert ei.value.status == 1
     assert c.launch_config() == default
 
@@ -52,11 +53,12 @@ def test_tuner_picks_a_candidate_and_caches_it(tmp_path, monkeypatch):
         sms = torch.cuda.get_device_properties(0).multi_processor_count
         assert not first["cached"] and first["knn_block"] in tune.KNN_BLOCKS
         assert first["stream_ctas"] in tune.stream_cta_candidates(sms)
-        assert c.launch_config() == (first["knn_block"], first["stream_ctas"])
+        assert first["knn_packed"] in (0, 1)
+        chosen = (first["knn_block"], first["stream_ctas"], first["knn_packed"])
+        assert c.launch_config() == chosen
         c.set_launch_config(*default)
         again = tune.tune(c, run, "tiny-test", steps=1)
-        assert again["cached"] and (again["knn_block"], again["stream_ctas"]) == \
-            (first["knn_block"], first["stream_ctas"])
-        assert c.launch_config() == (first["knn_block"], first["stream_ctas"])
+        assert again["cached"] and (again["knn_block"], again["stream_ctas"], again["knn_packed"]) == chosen
+        assert c.launch_config() == chosen
     finally:
         c.set_launch_config(*default)
