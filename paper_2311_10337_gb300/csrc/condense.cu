@@ -151,8 +151,9 @@ static dgec_status jump_to_fixed(Ctx *c, int64_t n, int64_t off, Sel sel, int32_
 
 
 // collapsed parent of every leaf and kept merge; nbig counts big children
-__global__ void k_c_cpar(Gview gv, const int32_t *parent, const int32_t *up, const int *isrep,
-                         const int64_t *size, int32_t *cpar, int *nbig) {
+__global__ void k_c_cpar(Gview gv, const int32_t *__restrict__ parent, const int32_t *__restrict__ up,
+                         const int *__restrict__ isrep, const int64_t *__restrict__ size,
+                         int32_t *__restrict__ cpar, int *__restrict__ nbig) {
     const int64_t E = gv.E;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < E + gv.n;
          x += (int64_t)gridDim.x * blockDim.x) {

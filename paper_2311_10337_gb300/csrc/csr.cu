@@ -219,9 +219,9 @@ __global__ void k_moff_split(const int64_t *moff, const int32_t *oidx, int64_t V
 // arrays; its rank in the other list is its position difference.
 __global__ void k_munpack(const unsigned long long *key, int64_t n2, int cb, const int64_t *moff,
                           const int32_t *oidx, const int64_t *out_off, const TE *te, int64_t *out_t,
-                          int32_t *out_id, int32_t *out_r, int2 *outrk, int32_t *pos_out, int64_t *in_t,
+                          int32_t *out_id, int32_t *out_r, int4 *outrk, int32_t *pos_out, int64_t *in_t,
                           int32_t *in_id, int32_t *in_r, int32_t *pos_in, unsigned char *in_head,
-                          int32_t *arank, int2 *in_va, int2 *out_vb) {
+                          int2 *inrk, int2 *in_va, int2 *out_vb) {
     const unsigned long long cmask = (1ull << cb) - 1ull;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n2;
          x += (int64_t)gridDim.x * blockDim.x) {
@@ -241,7 +241,8 @@ __global__ void k_munpack(const unsigned long long *key, int64_t n2, int cb, con
             out_id[slot] = e;
             out_r[slot] = r;
             pos_out[e] = (int32_t)slot;
-            outrk[r] = make_int2((int32_t)slot, (int32_t)(seg - obv));  // b: in-edges of v with t <= t_r
+            // b: in-edges of v with t <= t_r; v's in-list starts at moff[v] - out_off[v]
+            outrk[r] = make_int4((int32_t)slot, (int32_t)(seg - obv), (int32_t)(moff[v] - out_off[v]), 0);
             out_vb[slot] = make_int2((int32_t)v, (int32_t)(seg - obv));
         } else {
             const int64_t slot = x - ob;
@@ -250,7 +251,7 @@ __global__ void k_munpack(const unsigned long long *key, int64_t n2, int cb, con
             in_r[slot] = r;
             pos_in[e] = (int32_t)slot;
             in_head[slot] = (seg - obv) == 0;    // first entry of v's in-list
-            arank[r] = (int32_t)obv;             // out-edges of v with t < t_r
+            inrk[r] = make_int2((int32_t)ob, (int32_t)out_off[v + 1]);  // ob = out_off[v] + a
             in_va[slot] = make_int2((int32_t)v, (int32_t)obv);
         }
     }
@@ -401,10 +402,10 @@ void plan_csr(Arena &ws, const Problem &p, Csr &o) {
     o.isrc = ws.take<int32_t>(p.E);
     o.idst = ws.take<int32_t>(p.E);
     o.it = ws.take<int64_t>(p.E);
-    o.outrk = ws.take<int2>(p.E);
+    o.outrk = ws.take<int4>(p.E);
     o.pos_out = ws.take<int32_t>(p.E);
     o.pos_in = ws.take<int32_t>(p.E);
-    o.arank = ws.take<int32_t>(p.E);
+    o.inrk = ws.take<int2>(p.E);
     o.in_gs = ws.take<int32_t>(p.E);
     o.in_va = ws.take<int2>(p.E);
     o.out_vb = ws.take<int2>(p.E);
@@ -597,7 +598,7 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
                                                                                         o.in_off));
     TK(c, "k_munpack", k_munpack<<<grid_for(2 * E, kBlock, kStreamCap), kBlock, 0, st>>>(
                            key, 2 * E, cb, s.moff, s.oidx, o.out_off, s.te, o.out_t, o.out_id, o.out_r, o.outrk,
-                           o.pos_out, o.in_t, o.in_id, o.in_r, o.pos_in, s.in_head, o.arank, o.in_va,
+                           o.pos_out, o.in_t, o.in_id, o.in_r, o.pos_in, s.in_head, o.inrk, o.in_va,
                            o.out_vb));
     // start of every in-list entry's tie group (the kNN window takes a crossing group's smallest ids)
     DG_TRY((device_scan<long long, MaxI64, LoadInGroupHead, StoreI32>(c, LoadInGroupHead{o.in_t, s.in_head},

@@ -144,9 +144,10 @@ __global__ void k_d_emit(const int32_t *act, int64_t na, const int32_t *ecu, con
     }
 }
 
-__global__ void k_d_chain(const unsigned long long *key, const unsigned long long *val, int64_t nacc,
-                          int64_t E, int sbits, const int32_t *sroot, const int64_t *ssize, int32_t *la,
-                          int32_t *lb, int32_t *parent, long long *contrib, int *head) {
+__global__ void k_d_chain(const unsigned long long *__restrict__ key, const unsigned long long *__restrict__ val,
+                          int64_t nacc, int64_t E, int sbits, const int32_t *__restrict__ sroot,
+                          const int64_t *__restrict__ ssize, int32_t *__restrict__ la, int32_t *__restrict__ lb,
+                          int32_t *__restrict__ parent, long long *__restrict__ contrib, int *__restrict__ head) {
     const unsigned long long smask = (1ull << sbits) - 1ull;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nacc;
          x += (int64_t)gridDim.x * blockDim.x) {
@@ -175,9 +176,10 @@ __global__ void k_d_chain(const unsigned long long *key, const unsigned long lon
     }
 }
 
-__global__ void k_d_sizes(const unsigned long long *key, const unsigned long long *val, int64_t nacc,
-                          int64_t E, int sbits, const long long *csum, int64_t *lsize, int32_t *svpar,
-                          int32_t *sroot, int64_t *ssize) {
+__global__ void k_d_sizes(const unsigned long long *__restrict__ key, const unsigned long long *__restrict__ val,
+                          int64_t nacc, int64_t E, int sbits, const long long *__restrict__ csum,
+                          int64_t *__restrict__ lsize, int32_t *__restrict__ svpar, int32_t *__restrict__ sroot,
+                          int64_t *__restrict__ ssize) {
     const unsigned long long smask = (1ull << sbits) - 1ull;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nacc;
          x += (int64_t)gridDim.x * blockDim.x) {
@@ -216,9 +218,12 @@ __global__ void k_d_order_act(const unsigned long long *k, int64_t n, int sbits,
     }
 }
 
-__global__ void k_d_keep(const int32_t *act, int64_t na, const int *flag, const long long *pos,
-                         int32_t *act2, const int32_t *ecu, const int32_t *ecv, int32_t *ecu2,
-                         int32_t *ecv2, const int32_t *svpar, int32_t *minr, int32_t *tau) {
+__global__ void k_d_keep(const int32_t *__restrict__ act, int64_t na, const int *__restrict__ flag,
+                         const long long *__restrict__ pos, int32_t *__restrict__ act2,
+                         const int32_t *__restrict__ ecu, const int32_t *__restrict__ ecv,
+                         int32_t *__restrict__ ecu2, int32_t *__restrict__ ecv2,
+                         const int32_t *__restrict__ svpar, int32_t *__restrict__ minr,
+                         int32_t *__restrict__ tau) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < na;
          j += (int64_t)gridDim.x * blockDim.x) {
         int cu = ecu[j], cv = ecv[j];

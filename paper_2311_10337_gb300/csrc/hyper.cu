@@ -258,7 +258,6 @@ void plan_hyper(Arena &ws, const HyperProblem &h, Csr &g, HyperLists &S, HyperLi
     sk.ru = ws.take<int32_t>(L);
     sk.rv = ws.take<int32_t>(L);
     sk.w = ws.take<int64_t>(L);
-    sk.arank = nullptr;
     sk.knn = nullptr;
     sk.core = nullptr;
     sk.n = 0;

@@ -84,7 +84,6 @@ void plan_mrd(Arena &ws, const Problem &p, Skel &h) {
     h.ru = ws.take<int32_t>(L);
     h.rv = ws.take<int32_t>(L);
     h.w = ws.take<int64_t>(L);
-    h.arank = nullptr;
     h.knn = nullptr;
     h.core = nullptr;
     h.n = 0;

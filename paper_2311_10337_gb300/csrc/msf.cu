@@ -264,31 +264,52 @@ __global__ void k_m_claim(const int32_t *cu, const int32_t *cv, const int32_t *u
 }
 
 // Over the current roots: hook along the winner (a mutual pair keeps the
-// smaller label), append each forest edge once.
-__global__ void k_m_hook(const int32_t *roots, int64_t nr, const unsigned long long *bw,
-                         const unsigned long long *buv, const int32_t *bp, const int32_t *win,
-                         const int32_t *u, const int32_t *v, const int64_t *w, const int32_t *rank_of,
-                         int32_t *par, FEdge *fe, unsigned long long *n_out) {
+// smaller label), append each forest edge once. Each thread first issues
+// all its loads (8 roots), then writes: the loads of one tile are in flight
+// together.
+__global__ void k_m_hook(const int32_t *__restrict__ roots, int64_t nr, const unsigned long long *__restrict__ bw,
+                         const unsigned long long *__restrict__ buv, const int32_t *__restrict__ bp,
+                         const int32_t *__restrict__ win, const int32_t *__restrict__ u,
+                         const int32_t *__restrict__ v, const int64_t *__restrict__ w,
+                         const int32_t *__restrict__ rank_of, int32_t *__restrict__ par, FEdge *__restrict__ fe,
+                         unsigned long long *n_out) {
     const int64_t tile = (int64_t)blockDim.x * kRes;
     for (int64_t base = (int64_t)blockIdx.x * tile; base < nr; base += (int64_t)gridDim.x * tile) {  // CTA-uniform
-        int wx[kRes];
-        unsigned emit = 0;
+        int xs[kRes], ps[kRes], wx[kRes];
+        unsigned live = 0, mutual = 0;
 #pragma unroll
         for (int q = 0; q < kRes; q++) {
             const int64_t ix = base + (int64_t)q * blockDim.x + threadIdx.x;
-            wx[q] = 0;
-            if (ix < nr) {
-                const int x = roots[ix];
-                if (bw[x] == kMax64) {
-                    par[x] = x;
-                } else {
-                    const int p = bp[x];
-                    const bool mutual = bp[p] == x && buv[p] == buv[x];
-                    par[x] = (mutual && x < p) ? x : p;
-                    if (!mutual || x < p) emit |= 1u << q;
-                    wx[q] = win[x];
-                }
+            xs[q] = ix < nr ? roots[ix] : -1;
+        }
+#pragma unroll
+        for (int q = 0; q < kRes; q++) {
+            ps[q] = wx[q] = 0;
+            if (xs[q] < 0) continue;
+            if (bw[xs[q]] != kMax64) {
+                live |= 1u << q;
+                ps[q] = bp[xs[q]];
+                wx[q] = win[xs[q]];
             }
+        }
+#pragma unroll
+        for (int q = 0; q < kRes; q++) {
+            if (!((live >> q) & 1u)) continue;
+            const int x = xs[q], p = ps[q];
+            if (bp[p] == x && buv[p] == buv[x]) mutual |= 1u << q;
+        }
+        unsigned emit = 0;
+#pragma unroll
+        for (int q = 0; q < kRes; q++) {
+            if (xs[q] < 0) continue;
+            const int x = xs[q];
+            if (!((live >> q) & 1u)) {
+                par[x] = x;
+                continue;
+            }
+            const bool mu = (mutual >> q) & 1u;
+            par[x] = (mu && x < ps[q]) ? x : ps[q];
+            if (!mu || x < ps[q]) emit |= 1u << q;
         }
         long long at = cta_reserve_count(__popc(emit), n_out);
 #pragma unroll
@@ -322,10 +343,10 @@ __global__ void k_m_jump(const int32_t *roots, int64_t nr, int32_t *par) {
 }
 
 // Next round's roots (old roots that stayed roots); every old root's bid
-// slots are cleared.
-__global__ void k_m_next_roots(const int32_t *roots, int64_t nr, const int32_t *par,
-                               unsigned long long *bw, unsigned long long *buv, int32_t *roots2,
-                               unsigned long long *cnt) {
+// slots are cleared. Loads first, then stores (see k_m_hook).
+__global__ void k_m_next_roots(const int32_t *__restrict__ roots, int64_t nr, const int32_t *__restrict__ par,
+                               unsigned long long *__restrict__ bw, unsigned long long *__restrict__ buv,
+                               int32_t *__restrict__ roots2, unsigned long long *cnt) {
     const int64_t tile = (int64_t)blockDim.x * kRes;
     for (int64_t base = (int64_t)blockIdx.x * tile; base < nr; base += (int64_t)gridDim.x * tile) {  // CTA-uniform
         int xs[kRes];
@@ -333,14 +354,16 @@ __global__ void k_m_next_roots(const int32_t *roots, int64_t nr, const int32_t *
 #pragma unroll
         for (int q = 0; q < kRes; q++) {
             const int64_t ix = base + (int64_t)q * blockDim.x + threadIdx.x;
-            xs[q] = 0;
-            if (ix < nr) {
-                const int x = roots[ix];
-                xs[q] = x;
-                if (par[x] == x && bw[x] != kMax64) keep |= 1u << q;
-                bw[x] = kMax64;
-                buv[x] = kMax64;
-            }
+            xs[q] = ix < nr ? roots[ix] : -1;
+        }
+#pragma unroll
+        for (int q = 0; q < kRes; q++)
+            if (xs[q] >= 0 && par[xs[q]] == xs[q] && bw[xs[q]] != kMax64) keep |= 1u << q;
+#pragma unroll
+        for (int q = 0; q < kRes; q++) {
+            if (xs[q] < 0) continue;
+            bw[xs[q]] = kMax64;
+            buv[xs[q]] = kMax64;
         }
         long long at = cta_reserve_count(__popc(keep), cnt);
 #pragma unroll

@@ -116,7 +116,6 @@ void plan_nc(Arena &ws, const Problem &p, Skel &h) {
     h.w = ws.take<int64_t>(L);
     h.knn = ws.take<int32_t>(p.E * (int64_t)p.k);
     h.core = ws.take<int64_t>(p.E);
-    h.arank = nullptr;
     h.n = 0;
 }
 

@@ -21,22 +21,22 @@
 
 namespace dgec {
 
-// b[e] = outrk[e].y = #in-edges of src[e] with t <= t_e; arank[e] = #out-edges of
-// dst[e] with t < t_e (both from stage A's merged lists).
+// b[e] = outrk[e].y = #in-edges of src[e] with t <= t_e; inrk[e].x - out_off[dst[e]]
+// = #out-edges of dst[e] with t < t_e (both from stage A's merged lists).
 // All node ids below are internal ids r (see the stage A notes).
 struct SkView {
     const int32_t *src, *dst;  // isrc, idst (by r)
     const int64_t *out_off, *in_off;
     const int32_t *out_id, *in_id;  // out_r, in_r
-    const int2 *outrk;              // by r: (out-list slot, b)
-    const int32_t *arank;
+    const int4 *outrk;              // by r: (out-list slot, b, first in-list slot of src)
+    const int2 *inrk;               // by r: (first out-slot of dst not before t_r, end of dst's out-list)
 };
 
 // Does Alg. 2 at vertex x emit the pair (in-edge pin, out-edge qout)?
 __device__ __forceinline__ bool emitted_at(const SkView &g, int x, int pin, int qout) {
-    int64_t ob = g.out_off[x], nout = g.out_off[x + 1] - ob;
-    int a = g.arank[pin];
-    if (a < nout && g.out_id[ob + a] == qout) return true;  // type 1
+    const int64_t ob = g.out_off[x];
+    const int2 ia = g.inrk[pin];  // pin is an in-edge of x
+    if (ia.x < ia.y && g.out_id[ia.x] == qout) return true;  // type 1
     int64_t sq = g.outrk[qout].x;
     if (sq > ob) {                                          // type 2
         int b = g.outrk[g.out_id[sq - 1]].y;
@@ -129,9 +129,9 @@ __global__ void k_compact_links(const LinkRec *rec, const long long *pos, int64_
 // ---------------------------------------------------------------- kNN
 // Neighbours of e = (i, j, t_e) in the undirected L_G: in-edges r of i with
 // t_r <= t_e (prefix of i's in-list of length b[e]) and out-edges s of
-// j with t_s >= t_e (suffix of j's out-list from arank[e]). Ranked by
+// j with t_s >= t_e (suffix of j's out-list from its slot inrk[e].x). Ranked by
 // (|dt|, id). The K best of each side suffice: the successor side is
-// already in (w, id) order from arank; on the predecessor side the last K
+// already in (w, id) order from its first slot; on the predecessor side the last K
 // of the prefix, except that when the boundary tie group crosses the
 // window its smallest ids are taken instead of its largest (the group's
 // first slot comes from stage A's in_gs). The two ranks come from stage A,
@@ -150,12 +150,11 @@ __device__ __forceinline__ bool cand_less(const Cand &a, const Cand &b) {
 }
 
 template <int K>
-__global__ void __launch_bounds__(256) k_knn(const int32_t *src, const int32_t *dst, const int64_t *t,
-                                             const int32_t *orig_of, int64_t E, const int64_t *out_off,
+__global__ void __launch_bounds__(256) k_knn(const int64_t *t, const int32_t *orig_of, int64_t E,
                                              const int64_t *out_t, const int32_t *out_id,
-                                             const int64_t *in_off, const int64_t *in_t,
-                                             const int32_t *in_id, const int32_t *in_gs,
-                                             const int2 *outrk, const int32_t *arank, int G,
+                                             const int64_t *in_t, const int32_t *in_id,
+                                             const int32_t *in_gs, const int4 *outrk, const int2 *inrk,
+                                             int G,
                                              const int32_t *egraph, const int64_t *eoff,
                                              const int32_t *gk, const int64_t *knn_off, int64_t dmax,
                                              int32_t *knn, int64_t *core) {
@@ -164,7 +163,6 @@ __global__ void __launch_bounds__(256) k_knn(const int32_t *src, const int32_t *
     // neighbour lists are written under the original id, with original ids
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < E;
          r += (int64_t)gridDim.x * blockDim.x) {
-        const int i = src[r], j = dst[r];
         const long long te = t[r];
         const int64_t e = orig_of[r];
         // the edge's graph: its k, its kNN rows, its local id base
@@ -172,9 +170,11 @@ __global__ void __launch_bounds__(256) k_knn(const int32_t *src, const int32_t *
         const int k = gk[gr];
         const int64_t e0 = eoff[gr];
         int32_t *row = knn + knn_off[gr] + (e - e0) * k;
-        const int64_t ib = in_off[i];
-        const int64_t ob = out_off[j], nout = out_off[j + 1] - ob;
-        const int64_t b = outrk[r].y, a = arank[r];
+        // the two windows' places come with the edge: no offset lookups
+        const int4 orec = outrk[r];
+        const int2 irec = inrk[r];
+        const int64_t b = orec.y, ib = orec.z;
+        const int64_t a0 = irec.x, a1 = irec.y;  // successor window: out-list slots [a0, a1)
         Cand c[N];
         // predecessor window: the last K of the prefix [0, b); a tie group
         // that crosses its start contributes its smallest ids
@@ -201,10 +201,10 @@ __global__ void __launch_bounds__(256) k_knn(const int32_t *src, const int32_t *
         }
 #pragma unroll
         for (int x = 0; x < K; x++) {
-            const int64_t idx = a + x;
-            if (idx < nout) {
-                c[K + x].w = out_t[ob + idx] - te;
-                c[K + x].id = out_id[ob + idx];
+            const int64_t idx = a0 + x;
+            if (idx < a1) {
+                c[K + x].w = out_t[idx] - te;
+                c[K + x].id = out_id[idx];
             } else {
                 c[K + x].w = LLONG_MAX;
                 c[K + x].id = INT_MAX;
@@ -252,12 +252,11 @@ __global__ void __launch_bounds__(256) k_knn(const int32_t *src, const int32_t *
 // integers (two registers a candidate instead of three, one compare a step)
 // and the kernel keeps more warps resident to hide its gathers' latency.
 template <int K>
-__global__ void __launch_bounds__(256, K <= 8 ? 4 : 1) k_knn32(const int32_t *src, const int32_t *dst, const int64_t *t,
-                                               const int32_t *orig_of, int64_t E, const int64_t *out_off,
+__global__ void __launch_bounds__(256, K <= 8 ? 4 : 1) k_knn32(const int64_t *t, const int32_t *orig_of, int64_t E,
                                                const int64_t *out_t, const int32_t *out_id,
-                                               const int64_t *in_off, const int64_t *in_t,
-                                               const int32_t *in_id, const int32_t *in_gs,
-                                               const int2 *outrk, const int32_t *arank, int G,
+                                               const int64_t *in_t, const int32_t *in_id,
+                                               const int32_t *in_gs, const int4 *outrk, const int2 *inrk,
+                                               int G,
                                                const int32_t *egraph, const int64_t *eoff,
                                                const int32_t *gk, const int64_t *knn_off, int64_t dmax,
                                                int32_t *knn, int64_t *core) {
@@ -265,16 +264,17 @@ __global__ void __launch_bounds__(256, K <= 8 ? 4 : 1) k_knn32(const int32_t *sr
     constexpr unsigned long long kNone = 0xFFFFFFFFFFFFFFFFull;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < E;
          r += (int64_t)gridDim.x * blockDim.x) {
-        const int i = src[r], j = dst[r];
         const long long te = t[r];
         const int64_t e = orig_of[r];
         const int gr = G > 1 ? egraph[e] : 0;
         const int k = gk[gr];
         const int64_t e0 = eoff[gr];
         int32_t *row = knn + knn_off[gr] + (e - e0) * k;
-        const int64_t ib = in_off[i];
-        const int64_t ob = out_off[j], nout = out_off[j + 1] - ob;
-        const int64_t b = outrk[r].y, a = arank[r];
+        // the two windows' places come with the edge: no offset lookups
+        const int4 orec = outrk[r];
+        const int2 irec = inrk[r];
+        const int64_t b = orec.y, ib = orec.z;
+        const int64_t a0 = irec.x, a1 = irec.y;  // successor window: out-list slots [a0, a1)
         unsigned long long c[N];
         const int64_t lo = b - K > 0 ? b - K : 0;
         int64_t g0 = lo, take_grp = 0;
@@ -294,9 +294,8 @@ __global__ void __launch_bounds__(256, K <= 8 ? 4 : 1) k_knn32(const int32_t *sr
         }
 #pragma unroll
         for (int x = 0; x < K; x++) {
-            const int64_t idx = a + x;
-            c[K + x] = idx < nout ? ((unsigned long long)(out_t[ob + idx] - te) << 32) | (unsigned)out_id[ob + idx]
-                                  : kNone;
+            const int64_t idx = a0 + x;
+            c[K + x] = idx < a1 ? ((unsigned long long)(out_t[idx] - te) << 32) | (unsigned)out_id[idx] : kNone;
         }
 #pragma unroll
         for (int size = 2; size <= N; size <<= 1) {
@@ -335,7 +334,6 @@ __global__ void __launch_bounds__(256, K <= 8 ? 4 : 1) k_knn32(const int32_t *sr
 }
 
 void plan_skel(Arena &ws, const Problem &p, Skel &o) {
-    o.arank = nullptr;  // the ranks live in stage A's output
     o.u = ws.take<int32_t>(2 * p.E);
     o.v = ws.take<int32_t>(2 * p.E);
     o.ru = ws.take<int32_t>(2 * p.E);
@@ -371,10 +369,9 @@ dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void
     int64_t E = p.E;
     const int kb = c->knn_block;
     int grid = grid_for(E, kb, 1 << 20);
-    o.arank = g.arank;
 #define KNN_ARGS                                                                                   \
-    g.isrc, g.idst, g.it, g.orig_of, E, g.out_off, g.out_t, g.out_id, g.in_off, g.in_t, g.in_id, g.in_gs, \
-        g.outrk, g.arank, p.G, p.egraph, p.eoff, p.gk, p.knn_off, p.dmax, o.knn, o.core
+    g.it, g.orig_of, E, g.out_t, g.out_id, g.in_t, g.in_id, g.in_gs, g.outrk, g.inrk, p.G, p.egraph, p.eoff, \
+        p.gk, p.knn_off, p.dmax, o.knn, o.core
     if (p.knn && c->knn_packed && p.tbits <= 32) {  // every |dt| fits 32 bits: packed candidate keys
         if (p.k <= 4) TK(c, "k_knn", k_knn32<4><<<grid, kb, 0, st>>>(KNN_ARGS));
         else if (p.k <= 8) TK(c, "k_knn", k_knn32<8><<<grid, kb, 0, st>>>(KNN_ARGS));
@@ -385,7 +382,7 @@ dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void
         else TK(c, "k_knn", k_knn<16><<<grid, kb, 0, st>>>(KNN_ARGS));
     }
 #undef KNN_ARGS
-    SkView v{g.isrc, g.idst, g.out_off, g.in_off, g.out_r, g.in_r, g.outrk, g.arank};
+    SkView v{g.isrc, g.idst, g.out_off, g.in_off, g.out_r, g.in_r, g.outrk, g.inrk};
     TK(c, "k_links_in", k_links_in<<<grid_for(E, kBlock, kStreamCap), kBlock, 0, st>>>(
                             v, g.in_va, g.out_t, g.in_t, E, p.dmax, s.rec));
     TK(c, "k_links_out", k_links_out<<<grid_for(E, kBlock, kStreamCap), kBlock, 0, st>>>(

@@ -64,10 +64,12 @@ struct Csr {
     int32_t *rank_of;           // [E] original id -> r
     int32_t *isrc, *idst;       // [E] src, dst in r order
     int64_t *it;                // [E] t in r order
-    int2 *outrk;                // [E] by r: (.x) global slot in the out-lists, (.y) b = #in-edges of
-                                //   src with t <= t_r (one record: written together, read together)
+    int4 *outrk;                // [E] by r: (.x) global slot in the out-lists, (.y) b = #in-edges of
+                                //   src with t <= t_r, (.z) first slot of src's in-list (one record:
+                                //   written together, read together)
+    int2 *inrk;                 // [E] by r: (.x) first slot of dst's out-list not before t_r, (.y) end
+                                //   of dst's out-list (a = .x - out_off[dst] = #out-edges with t < t_r)
     int32_t *pos_out, *pos_in;  // [E] by original id: position in out_id / in_id (outputs)
-    int32_t *arank;             // [E] by r: #out-edges of dst with t < t_r
     int2 *in_va, *out_vb;       // [E] by list slot: (vertex, a) of each in-list entry, (vertex, b) of
                                 //   each out-list entry (the skeleton pass walks the lists in order)
     int32_t *in_gs;             // [E] by in-list slot: first slot of its tie group (same vertex, same t)
@@ -79,7 +81,6 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch);
 // Stage B: skeleton (Alg. 2 as rank arithmetic + Alg. 3 union) and the
 // k-nearest-in-time neighbours.
 struct Skel {
-    int32_t *arank;          // [E] by r: stage A's rank a (the rank b lives in Csr::outrk)
     int32_t *u, *v;          // [2E] capacity; original ids, u < v (output)
     int32_t *ru, *rv;        // [2E] the same links in internal ids
     int64_t *w;
