@@ -212,31 +212,39 @@ __global__ void k_c_clusters(Gview gv, const int *isrep, const int64_t *size, co
 }
 
 // Per node a point can land on or walk through (kept merges, virtual
-// roots): its collapsed parent, its cluster when it is big (else -1) and its
-// lambda, in one 16-byte record, so that each step of a point's walk reads
-// one sector.
-struct NodeRec {
+// roots): its collapsed parent, its cluster when it is big (else -1), its
+// lambda and, when big, the stability share of a point leaving its cluster
+// there (lambda - the cluster's birth), in one 32-byte record: each step of
+// a point's walk reads one sector, and the landing needs no other lookup.
+struct __align__(32) NodeRec {
     int32_t cpar;
     int32_t link;
     unsigned long long lam;
+    unsigned long long share;
+    unsigned long long pad;
 };
 
 __global__ void k_c_nrec(Gview gv, const int *isrep, const int64_t *size, const int64_t *w,
-                         const int32_t *cpar, const int32_t *link, NodeRec *rec) {
+                         const int32_t *cpar, const int32_t *link, const unsigned long long *cbirth,
+                         NodeRec *rec) {
     const int64_t E = gv.E, n = gv.n;
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n + gv.G;
          s += (int64_t)gridDim.x * blockDim.x) {
         const int64_t X = E + s;
         NodeRec r;
+        r.pad = 0;
         if (s >= n) {
             r.cpar = (int32_t)X;
             r.link = link[X];
             r.lam = 0ull;
+            r.share = 0ull;  // a virtual root: lambda 0, birth 0
         } else {
             if (!isrep[s]) continue;  // never a collapsed parent
+            const bool big = size[s] >= gv.gM[graph_of(gv, X)];
             r.cpar = cpar[X];
-            r.link = size[s] >= gv.gM[graph_of(gv, X)] ? link[X] : -1;
+            r.link = big ? link[X] : -1;
             r.lam = lambda_of(w[s]);
+            r.share = big ? r.lam - cbirth[r.link] : 0ull;
         }
         rec[s] = r;
     }
@@ -245,9 +253,8 @@ __global__ void k_c_nrec(Gview gv, const int *isrep, const int64_t *size, const 
 // where each point leaves: the lowest kept ancestor of size >= M; its
 // stability share is added per warp and cluster (points of one big cluster
 // often meet in a warp)
-__global__ void k_c_points(Gview gv, const int32_t *cpar, const NodeRec *rec,
-                           const unsigned long long *cbirth, int32_t *fall_cluster, uint64_t *fall_lambda,
-                           unsigned long long *st_hi, unsigned long long *st_lo) {
+__global__ void k_c_points(Gview gv, const int32_t *cpar, const NodeRec *rec, int32_t *fall_cluster,
+                           uint64_t *fall_lambda, unsigned long long *st_hi, unsigned long long *st_lo) {
     const int64_t E = gv.E;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < E;
@@ -261,7 +268,7 @@ __global__ void k_c_points(Gview gv, const int32_t *cpar, const NodeRec *rec,
             K = r.link;
             fall_cluster[p] = K;
             fall_lambda[p] = r.lam;
-            add = r.lam - cbirth[K];  // 0 at a virtual root
+            add = r.share;  // 0 at a virtual root
         }
         warp_add_u128(0xffffffffu, add != 0, K, add, st_hi, st_lo);
     }
@@ -616,8 +623,8 @@ static CScratch carve_condense(Arena &a, const Problem &p) {
     s.nxt2 = a.take<int32_t>(E + p.G + 1);
     s.stab = a.take<u128>(E + p.G + 1);
     s.S = a.take<u128>(E + p.G + 1);
-    s.Fa = a.take<u128>(E + p.G + 1);
-    s.Fc = a.take<u128>(E + p.G + 1);
+    s.Fa = a.take<u128>(2 * (E + p.G + 1));  // Fa and Fc adjacent: the node records span both
+    s.Fc = s.Fa + (E + p.G + 1);
     s.Fa2 = a.take<u128>(E + p.G + 1);
     s.Fc2 = a.take<u128>(E + p.G + 1);
     s.acc_hi = a.take<unsigned long long>(E + p.G + 1);
@@ -680,11 +687,11 @@ dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro 
     DG_TRY(jump_to_fixed(c, n, E, SelBigRep{gv, s.isrep, d.size}, s.link, s.jflag));
     TK(c, "k_c_clusters", k_c_clusters<<<gn, kBlock, 0, st>>>(gv, s.isrep, d.size, m.w, s.cpar, s.nbig, s.link,
                                                              s.isc, s.cbirth, s.cdeath, s.cparent));
-    // the node records live in the EOM phase's Fa array (not in use yet)
+    // the node records live in the EOM phase's Fa and Fc arrays (adjacent, not in use yet)
     NodeRec *nrec = reinterpret_cast<NodeRec *>(s.Fa);
-    TK(c, "k_c_nrec", k_c_nrec<<<gn, kBlock, 0, st>>>(gv, s.isrep, d.size, m.w, s.cpar, s.link, nrec));
-    TK(c, "k_c_points", k_c_points<<<gE, kBlock, 0, st>>>(gv, s.cpar, nrec, s.cbirth, o.fall_cluster,
-                                                         o.fall_lambda, s.st_hi, s.st_lo));
+    TK(c, "k_c_nrec", k_c_nrec<<<gn, kBlock, 0, st>>>(gv, s.isrep, d.size, m.w, s.cpar, s.link, s.cbirth, nrec));
+    TK(c, "k_c_points", k_c_points<<<gE, kBlock, 0, st>>>(gv, s.cpar, nrec, o.fall_cluster, o.fall_lambda,
+                                                         s.st_hi, s.st_lo));
     TK(c, "k_c_child_stab", k_c_child_stab<<<gN, kBlock, 0, st>>>(N, gv, s.isc, s.cparent, d.size, s.cbirth,
                                                                  s.cdeath, s.st_hi, s.st_lo));
     DG_TRY(exclusive_scan_i32(c, s.isc, s.cpos, N + 1, s.scan_tmp));

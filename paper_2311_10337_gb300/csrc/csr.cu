@@ -143,7 +143,7 @@ __global__ void k_rank_init(const unsigned long long *ks, const unsigned long lo
         orig_of[r] = e;
         rank_of[e] = (int32_t)r;
         it[r] = tt;
-        te[r] = TE{tt, e, 0};
+        if (te) te[r] = TE{tt, e, 0};  // only when the merged sort cannot carry (t, id)
         isrc[r] = (int32_t)(sd & 0xffffffffull);
         idst[r] = (int32_t)(sd >> 32);
     }
@@ -160,7 +160,7 @@ __global__ void k_rank_init_kv(const unsigned long long *ks, const unsigned long
         orig_of[r] = e;
         rank_of[e] = (int32_t)r;
         it[r] = (int64_t)(long long)(ks[r] + (unsigned long long)tmin);
-        te[r] = TE{it[r], e, 0};
+        if (te) te[r] = TE{it[r], e, 0};
         int32_t vo = G > 1 ? (int32_t)voff[egraph[e]] : 0;
         isrc[r] = src[e] + vo;
         idst[r] = dst[e] + vo;
@@ -193,8 +193,11 @@ __global__ void k_tgstart(const int *flag, const long long *gpos, int64_t E, int
 // Incidence items in the order (t, in-before-out, r): time group [gs, ge)
 // puts its in-items at 2 gs + (r - gs) and its out-items after them.
 // key = (vertex << cb) | (2 r + dir), dir 0 = in-item (at dst), 1 = out-item.
+// With val (time spans below 2^32): each item also carries (original id,
+// t - tmin) as its sort value, so the unpack reads nothing at random.
 __global__ void k_mkeys(const int32_t *isrc, const int32_t *idst, const int *flag, const long long *gpos,
-                        const int32_t *gstart, int64_t E, int cb, unsigned long long *key) {
+                        const int32_t *gstart, int64_t E, int cb, unsigned long long *key,
+                        const int32_t *orig_of, const int64_t *it, long long tmin, unsigned long long *val) {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < E;
          r += (int64_t)gridDim.x * blockDim.x) {
         const long long g = gpos[r] + flag[r] - 1;
@@ -202,6 +205,12 @@ __global__ void k_mkeys(const int32_t *isrc, const int32_t *idst, const int *fla
         const unsigned long long code = 2ull * (unsigned long long)r;
         key[r + gs] = ((unsigned long long)(unsigned)idst[r] << cb) | code;
         key[r + ge] = ((unsigned long long)(unsigned)isrc[r] << cb) | (code | 1ull);
+        if (val) {
+            const unsigned long long te = ((unsigned long long)(unsigned)orig_of[r] << 32) |
+                                          (unsigned long long)(it[r] - tmin);
+            val[r + gs] = te;
+            val[r + ge] = te;
+        }
     }
 }
 // out_off[v] = out-items before v's segment; in_off[v] = in-items before it
@@ -217,7 +226,8 @@ __global__ void k_moff_split(const int64_t *moff, const int32_t *oidx, int64_t V
 }
 // Every item of the merged lists goes to its slot in the out- or in-list
 // arrays; its rank in the other list is its position difference.
-__global__ void k_munpack(const unsigned long long *key, int64_t n2, int cb, const int64_t *moff,
+__global__ void k_munpack(const unsigned long long *key, const unsigned long long *val, long long tmin,
+                          int64_t n2, int cb, const int64_t *moff,
                           const int32_t *oidx, const int64_t *out_off, const TE *te, int64_t *out_t,
                           int32_t *out_id, int32_t *out_r, int4 *outrk, int32_t *pos_out, int64_t *in_t,
                           int32_t *in_id, int32_t *in_r, int32_t *pos_in, unsigned char *in_head,
@@ -232,9 +242,17 @@ __global__ void k_munpack(const unsigned long long *key, int64_t n2, int cb, con
         const int64_t ob = oidx[x];              // out-items before x
         const int64_t seg = x - moff[v];         // position in v's merged list
         const int64_t obv = ob - out_off[v];     // out-items before x within v's list
-        const TE rec = te[r];
-        const int32_t e = rec.e;
-        const int64_t tt = rec.t;
+        int32_t e;
+        int64_t tt;
+        if (val) {  // carried by the sort
+            const unsigned long long vv = val[x];
+            e = (int32_t)(vv >> 32);
+            tt = (int64_t)(vv & 0xffffffffull) + tmin;
+        } else {
+            const TE rec = te[r];
+            e = rec.e;
+            tt = rec.t;
+        }
         if (code & 1ull) {
             const int64_t slot = ob;
             out_t[slot] = tt;
@@ -428,6 +446,7 @@ void carve_segsort(Arena &a, int64_t V, int64_t n, SegSort &s) {
 struct CsrScratch {
     long long *flags;
     unsigned long long *mk, *mk2;  // [2E] incidence-item keys (the first sort uses both halves)
+    unsigned long long *mv, *mv2;  // [2E] their values (original id, t - tmin) when the span fits 32 bits
     int *gflag;                    // [E+1] time-group heads
     long long *gpos, *scan_tmp;    // [E+1] group index (exclusive)
     int32_t *gstart;               // [E+1]
@@ -443,6 +462,8 @@ static CsrScratch carve_csr(Arena &a, const Problem &p) {
     s.flags = a.take<long long>(8);
     s.mk = a.take<unsigned long long>(2 * E);
     s.mk2 = a.take<unsigned long long>(2 * E);
+    s.mv = a.take<unsigned long long>(2 * E);
+    s.mv2 = a.take<unsigned long long>(2 * E);
     s.gflag = a.take<int>(E + 1);
     s.gpos = a.take<long long>(E + 1);
     s.gstart = a.take<int32_t>(E + 1);
@@ -570,7 +591,7 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
                           s.radix, &in_b));
         TK(c, "k_rank_init", k_rank_init<<<gEE, kBlock, 0, st>>>(in_b ? s.mk2 : s.mk, in_b ? s.mk2 + E : s.mk + E, E,
                                                                 p.tmin, p.idbits, o.orig_of, o.rank_of, o.isrc, o.idst,
-                                                                o.it, s.te));
+                                                                o.it, p.tbits <= 32 ? nullptr : s.te));
     } else {
         // wide span: the time is the whole key, the id its value (second halves of the item buffers)
         TK(c, "k_pack_t", k_pack_t<<<gEE, kBlock, 0, st>>>(p.t, E, p.tmin, s.mk, s.mk + E));
@@ -586,18 +607,23 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
     TK(c, "k_tgstart", k_tgstart<<<grid_for(E + 1, kBlock, kStreamCap), kBlock, 0, st>>>(s.gflag, s.gpos, E, s.gstart));
     const int cb = p.idbits + 1;  // bits of an item code 2r + dir
     const int vbits = bits_for((uint64_t)(V > 1 ? V - 1 : 1));
-    TK(c, "k_mkeys", k_mkeys<<<gEE, kBlock, 0, st>>>(o.isrc, o.idst, s.gflag, s.gpos, s.gstart, E, cb, s.mk));
+    const bool carry = p.tbits <= 32;  // (id, t - tmin) fits the 64-bit sort value
+    TK(c, "k_mkeys", k_mkeys<<<gEE, kBlock, 0, st>>>(o.isrc, o.idst, s.gflag, s.gpos, s.gstart, E, cb, s.mk,
+                                                     o.orig_of, o.it, p.tmin, carry ? s.mv : nullptr));
     // every vertex's merged list: a stable sort over the vertex bits alone
     bool in_b;
-    DG_TRY(radix_sort(c, RadixBuffers{s.mk, s.mk2, nullptr, nullptr}, 2 * E, cb, cb + vbits, s.radix, &in_b));
+    DG_TRY(radix_sort(c, RadixBuffers{s.mk, s.mk2, carry ? s.mv : nullptr, carry ? s.mv2 : nullptr}, 2 * E, cb,
+                      cb + vbits, s.radix, &in_b));
     const unsigned long long *key = in_b ? s.mk2 : s.mk;
+    const unsigned long long *mval = carry ? (in_b ? s.mv2 : s.mv) : nullptr;
     TK(c, "k_voffsets", k_voffsets<<<grid_for(2 * E + 1, kBlock, kStreamCap), kBlock, 0, st>>>(key, 2 * E, V, cb, s.moff));
     DG_TRY((device_scan<long long, SumI64, LoadOutBit, StoreI32>(c, LoadOutBit{key, 2 * E}, StoreI32{s.oidx},
                                                                  2 * E + 1, SumI64{}, 0ll, false, s.scan_tmp)));
     TK(c, "k_moff_split", k_moff_split<<<grid_for(V + 1, kBlock, kStreamCap), kBlock, 0, st>>>(s.moff, s.oidx, V, o.out_off,
                                                                                         o.in_off));
     TK(c, "k_munpack", k_munpack<<<grid_for(2 * E, kBlock, kStreamCap), kBlock, 0, st>>>(
-                           key, 2 * E, cb, s.moff, s.oidx, o.out_off, s.te, o.out_t, o.out_id, o.out_r, o.outrk,
+                           key, mval, p.tmin, 2 * E, cb, s.moff, s.oidx, o.out_off, s.te, o.out_t, o.out_id,
+                           o.out_r, o.outrk,
                            o.pos_out, o.in_t, o.in_id, o.in_r, o.pos_in, s.in_head, o.inrk, o.in_va,
                            o.out_vb));
     // start of every in-list entry's tie group (the kNN window takes a crossing group's smallest ids)

@@ -25,9 +25,23 @@ namespace dgec {
 
 // Super-vertex labels are internal ids r (a leaf's label is its own r);
 // sroot holds dendrogram node ids, so a leaf's root is its original id.
+//
+// minr (a super-vertex's smallest live edge) and tau (a pointer tree's
+// smallest non-pointer edge) live one round each. A slot holds
+// (stamp << 32) | rank with stamp = kStampTop - round: newer rounds have
+// smaller stamps, so atomicMin over the whole key keeps this round's
+// minimum, and a slot with another stamp holds nothing this round. No pass
+// resets them between rounds.
+constexpr unsigned kStampTop = 0xFFFFFFF0u;
+__device__ __forceinline__ unsigned long long rkey(unsigned stamp, int v) {
+    return ((unsigned long long)stamp << 32) | (unsigned)v;
+}
+__device__ __forceinline__ int rval(unsigned long long k, unsigned stamp) {
+    return (unsigned)(k >> 32) == stamp ? (int)(unsigned)k : INT_MAX;
+}
 __global__ void k_d_init(int64_t E, int64_t n, const int32_t *mu, const int32_t *mv,
                          const int32_t *orig_of, int32_t *svpar, int32_t *sroot, int64_t *ssize,
-                         int32_t *minr, int32_t *tau, int32_t *parent, int32_t *act, int32_t *ecu,
+                         unsigned long long *minr, unsigned long long *tau, int32_t *parent, int32_t *act, int32_t *ecu,
                          int32_t *ecv) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < E + n;
          x += (int64_t)gridDim.x * blockDim.x) {
@@ -36,8 +50,8 @@ __global__ void k_d_init(int64_t E, int64_t n, const int32_t *mu, const int32_t 
             svpar[x] = (int32_t)x;
             sroot[x] = orig_of[x];
             ssize[x] = 1;
-            minr[x] = INT_MAX;
-            tau[x] = INT_MAX;
+            minr[x] = ~0ull;
+            tau[x] = ~0ull;
         }
         if (x < n) {
             act[x] = (int32_t)x;
@@ -52,22 +66,23 @@ __global__ void k_d_init(int64_t E, int64_t n, const int32_t *mu, const int32_t 
 // each round's merges, so no label chain is ever walked. A read before the
 // atomic skips bids that cannot win (slots only decrease).
 __global__ void k_d_bid(const int32_t *act, int64_t na, const int32_t *ecu, const int32_t *ecv,
-                        int32_t *minr) {
+                        unsigned long long *minr, unsigned stamp) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < na;
          j += (int64_t)gridDim.x * blockDim.x) {
         int s = act[j];
         int cu = ecu[j], cv = ecv[j];
-        if (s < minr[cu]) atomicMin(&minr[cu], s);
-        if (s < minr[cv]) atomicMin(&minr[cv], s);
+        const unsigned long long key = rkey(stamp, s);
+        if (key < minr[cu]) atomicMin(&minr[cu], key);
+        if (key < minr[cv]) atomicMin(&minr[cv], key);
     }
 }
 
 __global__ void k_d_ptr(const int32_t *act, int64_t na, const int32_t *ecu, const int32_t *ecv,
-                        const int32_t *minr, int32_t *gp) {
+                        const unsigned long long *minr, unsigned stamp, int32_t *gp) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < na;
          j += (int64_t)gridDim.x * blockDim.x) {
         int s = act[j], cu = ecu[j], cv = ecv[j];
-        bool pu = minr[cu] == s, pv = minr[cv] == s;
+        bool pu = rval(minr[cu], stamp) == s, pv = rval(minr[cv], stamp) == s;
         if (pu && pv) {
             int r = cu < cv ? cu : cv;
             gp[cu] = r;
@@ -80,14 +95,14 @@ __global__ void k_d_ptr(const int32_t *act, int64_t na, const int32_t *ecu, cons
 }
 
 __global__ void k_d_gjump(const int32_t *act, int64_t na, const int32_t *ecu, const int32_t *ecv,
-                          const int32_t *minr, int32_t *gp) {
+                          const unsigned long long *minr, unsigned stamp, int32_t *gp) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < na;
          j += (int64_t)gridDim.x * blockDim.x) {
         int s = act[j];
 #pragma unroll
         for (int side = 0; side < 2; side++) {
             int c = side ? ecv[j] : ecu[j];
-            if (minr[c] != s) continue;
+            if (rval(minr[c], stamp) != s) continue;
             int r = gp[c];
             for (int it = 0; it < kMaxWalk; it++) {  // bounded: pointer trees
                 int rr = gp[r];
@@ -100,20 +115,23 @@ __global__ void k_d_gjump(const int32_t *act, int64_t na, const int32_t *ecu, co
 }
 
 __global__ void k_d_tau(const int32_t *act, int64_t na, const int32_t *ecu, const int32_t *ecv,
-                        const int32_t *minr, const int32_t *gp, int32_t *tau) {
+                        const unsigned long long *minr, unsigned stamp, const int32_t *gp,
+                        unsigned long long *tau) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < na;
          j += (int64_t)gridDim.x * blockDim.x) {
         int s = act[j], cu = ecu[j], cv = ecv[j];
-        if (minr[cu] != s && minr[cv] != s) {
-            int gu = gp[cu], gv = gp[cv];
-            if (s < tau[gu]) atomicMin(&tau[gu], s);
-            if (s < tau[gv]) atomicMin(&tau[gv], s);
+        if (rval(minr[cu], stamp) != s && rval(minr[cv], stamp) != s) {
+            const int gu = gp[cu], gv = gp[cv];
+            const unsigned long long key = rkey(stamp, s);
+            if (key < tau[gu]) atomicMin(&tau[gu], key);
+            if (key < tau[gv]) atomicMin(&tau[gv], key);
         }
     }
 }
 
 __global__ void k_d_accept(const int32_t *act, int64_t na, const int32_t *ecu, const int32_t *ecv,
-                           const int32_t *minr, const int32_t *gp, const int32_t *tau, int *flag) {
+                           const unsigned long long *minr, unsigned stamp, const int32_t *gp,
+                           const unsigned long long *tau, int *flag) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j <= na;
          j += (int64_t)gridDim.x * blockDim.x) {
         if (j == na) {
@@ -121,8 +139,8 @@ __global__ void k_d_accept(const int32_t *act, int64_t na, const int32_t *ecu, c
             continue;
         }
         int s = act[j], cu = ecu[j], cv = ecv[j];
-        bool ptr = minr[cu] == s || minr[cv] == s;
-        flag[j] = ptr && s < tau[gp[cu]];
+        bool ptr = rval(minr[cu], stamp) == s || rval(minr[cv], stamp) == s;
+        flag[j] = ptr && s < rval(tau[gp[cu]], stamp);
     }
 }
 
@@ -130,14 +148,15 @@ __global__ void k_d_accept(const int32_t *act, int64_t na, const int32_t *ecu, c
 // rank order; the value carries the edge's two super-vertices, the one
 // whose pointer the edge is first (either for the group's mutual edge)
 __global__ void k_d_emit(const int32_t *act, int64_t na, const int32_t *ecu, const int32_t *ecv,
-                         const int32_t *minr, const int32_t *gp, const int *flag, const long long *pos,
+                         const unsigned long long *minr, unsigned stamp, const int32_t *gp, const int *flag,
+                         const long long *pos,
                          int sbits, unsigned long long *key, unsigned long long *val) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < na;
          j += (int64_t)gridDim.x * blockDim.x) {
         if (!flag[j]) continue;
         const int64_t at = pos[j];
         const int s = act[j], cu = ecu[j], cv = ecv[j];
-        const bool own_u = minr[cu] == s;
+        const bool own_u = rval(minr[cu], stamp) == s;
         const unsigned Y = (unsigned)(own_u ? cu : cv), O = (unsigned)(own_u ? cv : cu);
         key[at] = ((unsigned long long)gp[cu] << sbits) | (unsigned long long)s;
         val[at] = ((unsigned long long)Y << 32) | O;
@@ -222,8 +241,7 @@ __global__ void k_d_keep(const int32_t *__restrict__ act, int64_t na, const int 
                          const long long *__restrict__ pos, int32_t *__restrict__ act2,
                          const int32_t *__restrict__ ecu, const int32_t *__restrict__ ecv,
                          int32_t *__restrict__ ecu2, int32_t *__restrict__ ecv2,
-                         const int32_t *__restrict__ svpar, int32_t *__restrict__ minr,
-                         int32_t *__restrict__ tau) {
+                         const int32_t *__restrict__ svpar) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < na;
          j += (int64_t)gridDim.x * blockDim.x) {
         int cu = ecu[j], cv = ecv[j];
@@ -233,10 +251,6 @@ __global__ void k_d_keep(const int32_t *__restrict__ act, int64_t na, const int 
             ecu2[at] = svpar[cu];
             ecv2[at] = svpar[cv];
         }
-        if (minr[cu] != INT_MAX) minr[cu] = INT_MAX;
-        if (minr[cv] != INT_MAX) minr[cv] = INT_MAX;
-        if (tau[cu] != INT_MAX) tau[cu] = INT_MAX;
-        if (tau[cv] != INT_MAX) tau[cv] = INT_MAX;
     }
 }
 
@@ -248,7 +262,8 @@ void plan_dendro(Arena &ws, const Problem &p, Dendro &o) {
 }
 
 struct DScratch {
-    int32_t *svpar, *sroot, *minr, *tau, *gp, *act, *act2, *ecu, *ecv, *ecu2, *ecv2;
+    int32_t *svpar, *sroot, *gp, *act, *act2, *ecu, *ecv, *ecu2, *ecv2;
+    unsigned long long *minr, *tau;  // round-stamped slots (see rkey)
     int64_t *ssize;
     int *flag, *head;
     long long *pos, *contrib, *csum, *scan_tmp;
@@ -261,8 +276,8 @@ static DScratch carve_dendro(Arena &a, const Problem &p) {
     int64_t E = p.E;
     s.svpar = a.take<int32_t>(E);
     s.sroot = a.take<int32_t>(E);
-    s.minr = a.take<int32_t>(E);
-    s.tau = a.take<int32_t>(E);
+    s.minr = a.take<unsigned long long>(E);
+    s.tau = a.take<unsigned long long>(E);
     s.gp = a.take<int32_t>(E);
     s.ssize = a.take<int64_t>(E);
     s.act = a.take<int32_t>(E);
@@ -317,17 +332,18 @@ dgec_status stage_dendro(Ctx *c, const Problem &p, const Csr &g, const Msf &m, D
         if (round >= (1 << 16))
             return set_err(c, DGEC_ERR_TIMEOUT, "dendrogram rounds exceeded %d", 1 << 16);
         const int g = grid_for(na, kBlock, kStreamCap);
-        TK(c, "k_d_bid", k_d_bid<<<g, kBlock, 0, st>>>(act, na, ecu, ecv, s.minr));
-        TK(c, "k_d_ptr", k_d_ptr<<<g, kBlock, 0, st>>>(act, na, ecu, ecv, s.minr, s.gp));
-        TK(c, "k_d_gjump", k_d_gjump<<<g, kBlock, 0, st>>>(act, na, ecu, ecv, s.minr, s.gp));
-        TK(c, "k_d_tau", k_d_tau<<<g, kBlock, 0, st>>>(act, na, ecu, ecv, s.minr, s.gp, s.tau));
+        const unsigned stamp = kStampTop - (unsigned)round;
+        TK(c, "k_d_bid", k_d_bid<<<g, kBlock, 0, st>>>(act, na, ecu, ecv, s.minr, stamp));
+        TK(c, "k_d_ptr", k_d_ptr<<<g, kBlock, 0, st>>>(act, na, ecu, ecv, s.minr, stamp, s.gp));
+        TK(c, "k_d_gjump", k_d_gjump<<<g, kBlock, 0, st>>>(act, na, ecu, ecv, s.minr, stamp, s.gp));
+        TK(c, "k_d_tau", k_d_tau<<<g, kBlock, 0, st>>>(act, na, ecu, ecv, s.minr, stamp, s.gp, s.tau));
         TK(c, "k_d_accept", k_d_accept<<<grid_for(na + 1, kBlock, kStreamCap), kBlock, 0, st>>>(
-                                act, na, ecu, ecv, s.minr, s.gp, s.tau, s.flag));
+                                act, na, ecu, ecv, s.minr, stamp, s.gp, s.tau, s.flag));
         DG_TRY(exclusive_scan_i32(c, s.flag, s.pos, na + 1, s.scan_tmp));
         int64_t nacc;
         DG_TRY(read_counters(c, (const int64_t *)(s.pos + na), 1, &nacc));
         if (nacc <= 0) return set_err(c, DGEC_ERR_INTERNAL, "dendrogram round accepted no edge");
-        TK(c, "k_d_emit", k_d_emit<<<g, kBlock, 0, st>>>(act, na, ecu, ecv, s.minr, s.gp, s.flag, s.pos, sbits,
+        TK(c, "k_d_emit", k_d_emit<<<g, kBlock, 0, st>>>(act, na, ecu, ecv, s.minr, stamp, s.gp, s.flag, s.pos, sbits,
                                                          s.k1, s.v1));
         bool in_b;
         DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, s.v1, s.v2}, nacc, 0, lb + sbits, s.radix, &in_b));
@@ -339,7 +355,7 @@ dgec_status stage_dendro(Ctx *c, const Problem &p, const Csr &g, const Msf &m, D
         TK(c, "k_d_sizes", k_d_sizes<<<ga, kBlock, 0, st>>>(key, val, nacc, E, sbits, s.csum, o.size, s.svpar,
                                                            s.sroot, s.ssize));
         TK(c, "k_d_keep", k_d_keep<<<g, kBlock, 0, st>>>(act, na, s.flag, s.pos, act2, ecu, ecv, ecu2, ecv2,
-                                                         s.svpar, s.minr, s.tau));
+                                                         s.svpar));
         na -= nacc;
         int32_t *t = act;
         act = act2;
