@@ -225,14 +225,15 @@ __global__ void k_d_order_keys(const int32_t *ru, int64_t n, int sbits, unsigned
          x += (int64_t)gridDim.x * blockDim.x)
         k[x] = ((unsigned long long)(unsigned)ru[x] << sbits) | (unsigned long long)x;
 }
-__global__ void k_d_order_act(const unsigned long long *k, int64_t n, int sbits, const int32_t *ru,
-                              const int32_t *rv, int32_t *act, int32_t *ecu, int32_t *ecv) {
+__global__ void k_d_order_act(const unsigned long long *k, int64_t n, int sbits, const int32_t *rv,
+                              int32_t *act, int32_t *ecu, int32_t *ecv) {
     const unsigned long long smask = (1ull << sbits) - 1ull;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
          j += (int64_t)gridDim.x * blockDim.x) {
-        int s = (int)(k[j] & smask);
+        const unsigned long long kk = k[j];
+        const int s = (int)(kk & smask);
         act[j] = s;
-        ecu[j] = ru[s];
+        ecu[j] = (int32_t)(kk >> sbits);  // ru, from the key
         ecv[j] = rv[s];
     }
 }
@@ -323,7 +324,7 @@ dgec_status stage_dendro(Ctx *c, const Problem &p, const Csr &g, const Msf &m, D
         TK(c, "k_d_order_keys", k_d_order_keys<<<gn, kBlock, 0, st>>>(m.ru, n, sbits, s.k1));
         bool in_b;
         DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, nullptr, nullptr}, n, sbits, sbits + lb, s.radix, &in_b));
-        TK(c, "k_d_order_act", k_d_order_act<<<gn, kBlock, 0, st>>>(in_b ? s.k2 : s.k1, n, sbits, m.ru, m.rv, s.act,
+        TK(c, "k_d_order_act", k_d_order_act<<<gn, kBlock, 0, st>>>(in_b ? s.k2 : s.k1, n, sbits, m.rv, s.act,
                                                                s.ecu, s.ecv));
     }
     int64_t na = n;

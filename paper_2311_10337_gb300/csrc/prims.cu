@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(kBlock) k_radix_scatter(
     __shared__ unsigned long long svals[VALS ? kTile : 1];
     __shared__ int wcnt[kWarps][kRadix];
     __shared__ int dstart[kRadix];
+    __shared__ long long soff[kRadix];
     __shared__ int scan_sm[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < kWarps * kRadix; i += kBlock) (&wcnt[0][0])[i] = 0;
@@ -116,6 +117,8 @@ __global__ void __launch_bounds__(kBlock) k_radix_scatter(
     int total;
     int start = block_exclusive(run, AddI{}, 0, scan_sm, &total);
     dstart[digit] = start;
+    // this tile's global start of every digit, less its start in the tile
+    soff[digit] = offs[(int64_t)digit * tiles + blockIdx.x] - start;
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < kItems; i++) {
@@ -128,11 +131,54 @@ __global__ void __launch_bounds__(kBlock) k_radix_scatter(
     __syncthreads();
     int64_t m = n - base < kTile ? n - base : kTile;
     for (int j = threadIdx.x; j < m; j += kBlock) {
-        unsigned long long key = skeys[j];
-        int dd = (int)((key >> shift) & mask);
-        int64_t g = offs[(int64_t)dd * tiles + blockIdx.x] + (j - dstart[dd]);
+        const unsigned long long key = skeys[j];
+        const int dd = (int)((key >> shift) & mask);
+        const int64_t g = soff[dd] + j;
         kout[g] = key;
         if (VALS) vout[g] = svals[j];
+    }
+}
+
+// Small inputs (n <= kSmallSort): one CTA sorts the pairs (key bits
+// [begin, end), input position) by a bitonic network in shared memory --
+// the same stable order as the LSD passes -- and gathers keys and values
+// into the second buffers. One launch instead of five per 8-bit pass.
+constexpr int kSmallSort = 2048;
+__global__ void __launch_bounds__(1024) k_sort_small(const unsigned long long *kin, const unsigned long long *vin,
+                                                     unsigned long long *kout, unsigned long long *vout, int n,
+                                                     int begin_bit, int end_bit) {
+    __shared__ unsigned long long sf[kSmallSort];
+    __shared__ int si[kSmallSort];
+    const int nb = end_bit - begin_bit;
+    const unsigned long long fmask = nb >= 64 ? ~0ull : ((1ull << nb) - 1ull);
+    int N = 1;
+    while (N < n) N <<= 1;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        sf[i] = i < n ? (kin[i] >> begin_bit) & fmask : ~0ull;
+        si[i] = i < n ? i : kSmallSort + i;  // padding sorts last
+    }
+    __syncthreads();
+    for (int size = 2; size <= N; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < (N >> 1); i += blockDim.x) {
+                const int lo = 2 * stride * (i / stride) + (i % stride), hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const unsigned long long fa = sf[lo], fb = sf[hi];
+                const int ia = si[lo], ib = si[hi];
+                const bool greater = fa > fb || (fa == fb && ia > ib);
+                if (greater == up) {
+                    sf[lo] = fb;
+                    sf[hi] = fa;
+                    si[lo] = ib;
+                    si[hi] = ia;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        kout[i] = kin[si[i]];
+        if (vin) vout[i] = vin[si[i]];
     }
 }
 
@@ -147,6 +193,12 @@ dgec_status radix_sort(Ctx *c, RadixBuffers buf, int64_t n, int begin_bit, int e
                        void *scratch, bool *in_b) {
     *in_b = false;
     if (n <= 1 || end_bit <= begin_bit) return DGEC_OK;
+    if (n <= kSmallSort) {
+        TK(c, "k_sort_small", k_sort_small<<<1, 1024, 0, c->stream>>>(buf.ka, buf.va, buf.kb, buf.vb, (int)n,
+                                                                      begin_bit, end_bit));
+        *in_b = true;
+        return DGEC_OK;
+    }
     int64_t tiles = cdiv(n, kTile);
     size_t hist_n = (size_t)tiles * kRadix;
     char *s = (char *)scratch;

@@ -13,7 +13,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libdgec.so")
+# the in-tree build; DGEC_LIBRARY may name another build of the same library
+LIB_PATH = os.environ.get("DGEC_LIBRARY") or os.path.join(_HERE, "_lib", "libdgec.so")
 
 DGEC_OK = 0
 STATUS = {0: "DGEC_OK", 1: "DGEC_ERR_INVALID_ARG", 2: "DGEC_ERR_VERTEX_RANGE",
