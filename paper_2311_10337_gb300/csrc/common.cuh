@@ -46,7 +46,7 @@ struct StageTimer {
 struct Ctx {
     int device = 0;
     int knn_block = 128;           // launch configuration (dgec_set_launch_config)
-    int knn_packed = 0;
+    int knn_packed = 1;
     int64_t stream_ctas = 65536;
     int num_sms = 152;
     char msg[512] = {0};

@@ -274,30 +274,33 @@ __global__ void k_c_points(Gview gv, const int32_t *cpar, const NodeRec *rec, in
     }
 }
 
-// a child cluster's points leave the parent at the parent's death
-__global__ void k_c_child_stab(int64_t N, Gview gv, const int *isc, const int32_t *cparent,
-                               const int64_t *size, const unsigned long long *cbirth,
-                               const unsigned long long *cdeath, unsigned long long *st_hi,
-                               unsigned long long *st_lo) {
-    for (int64_t K = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; K < N;
-         K += (int64_t)gridDim.x * blockDim.x) {
-        if (!isc[K] || K >= gv.R0) continue;
-        int P = cparent[K];
-        unsigned long long span = cdeath[P] - cbirth[P];
-        unsigned long long sz = (unsigned long long)size[K - gv.E];
-        unsigned long long lo = sz * span, hi = __umul64hi(sz, span);
-        atomic_add_u128(&st_hi[P], &st_lo[P], hi, lo);
+// A child cluster's points leave the parent P at P's death: P gains
+// (death - birth) * (total size of its child clusters). The sizes are summed
+// here per cluster index (plain adds, no returned value, so the many
+// components under a virtual root do not wait on one hot address), over the
+// compacted cluster list; the product is taken when the stabilities are
+// gathered.
+__global__ void k_c_child_size(int64_t ncl, Gview gv, const int32_t *__restrict__ clist,
+                               const int32_t *__restrict__ cparent, const int32_t *__restrict__ cidx,
+                               const int64_t *__restrict__ size, unsigned long long *csz) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncl;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int K = clist[c];
+        if (K >= gv.R0) continue;
+        atomicAdd(&csz[cidx[cparent[K]]], (unsigned long long)size[K - gv.E]);
     }
 }
 
-// compact cluster list (ascending node id) and per-cluster arrays
-__global__ void k_c_compact(int64_t N, const int *isc, const long long *cpos, int32_t *clist,
+// compact cluster list (ascending node id) and per-cluster arrays; only
+// merges and virtual roots (node ids E + i) can be clusters, so the flags
+// and their prefix sums cover those alone
+__global__ void k_c_compact(int64_t E, int64_t m, const int *isc, const long long *cpos, int32_t *clist,
                             int32_t *cidx) {
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N;
-         x += (int64_t)gridDim.x * blockDim.x) {
-        if (!isc[x]) continue;
-        clist[cpos[x]] = (int32_t)x;
-        cidx[x] = (int32_t)cpos[x];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (!isc[i]) continue;
+        clist[cpos[i]] = (int32_t)(E + i);
+        cidx[E + i] = (int32_t)cpos[i];
     }
 }
 
@@ -315,13 +318,17 @@ struct Eom {
     unsigned long long *flag;  // [0] changed
 };
 
-__global__ void k_e_init(Eom e, const unsigned long long *st_hi, const unsigned long long *st_lo) {
+__global__ void k_e_init(Eom e, const unsigned long long *st_hi, const unsigned long long *st_lo,
+                         const unsigned long long *cbirth, const unsigned long long *cdeath,
+                         const unsigned long long *csz) {
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < e.ncl;
          c += (int64_t)gridDim.x * blockDim.x) {
         int node = e.clist[c];
         int pn = e.cparent[node];
         e.par[c] = pn < 0 ? -1 : e.cidx[pn];
-        e.stab[c] = ((u128)st_hi[node] << 64) | st_lo[node];
+        const unsigned long long kids = csz[c];
+        const u128 from_kids = kids ? (u128)(cdeath[node] - cbirth[node]) * kids : (u128)0;
+        e.stab[c] = (((u128)st_hi[node] << 64) | st_lo[node]) + from_kids;
         e.done[c] = 0;
         e.acc_hi[c] = 0;
         e.acc_lo[c] = 0;
@@ -590,7 +597,7 @@ struct CScratch {
     int32_t *up, *cpar, *link, *cparent, *clist, *cidx, *par, *ucand, *nxt, *nxt2, *H, *J, *H2, *J2,
         *rank, *al1, *al2;
     int *isrep, *nbig, *isc, *pending, *done, *state, *minmem, *flag;
-    unsigned long long *cbirth, *cdeath, *st_hi, *st_lo, *acc_hi, *acc_lo, *cnt, *k1, *k2, *v1, *v2, *jflag;
+    unsigned long long *cbirth, *cdeath, *st_hi, *st_lo, *acc_hi, *acc_lo, *csz, *cnt, *k1, *k2, *v1, *v2, *jflag;
     long long *cpos, *scan_tmp;
     int64_t *gstart;
     u128 *stab, *S, *Fa, *Fc, *Fa2, *Fc2;
@@ -629,6 +636,7 @@ static CScratch carve_condense(Arena &a, const Problem &p) {
     s.Fc2 = a.take<u128>(E + p.G + 1);
     s.acc_hi = a.take<unsigned long long>(E + p.G + 1);
     s.acc_lo = a.take<unsigned long long>(E + p.G + 1);
+    s.csz = a.take<unsigned long long>(E + p.G + 1);
     s.H = a.take<int32_t>(E + p.G + 1);
     s.J = a.take<int32_t>(E + p.G + 1);
     s.H2 = a.take<int32_t>(E + p.G + 1);
@@ -674,7 +682,7 @@ dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro 
     const int gN = grid_for(N, kBlock, kStreamCap), gE = grid_for(E, kBlock, kStreamCap),
               gn = grid_for(n + p.G, kBlock, kStreamCap);
     CU_TRY(c, cudaMemsetAsync(s.nbig, 0, sizeof(int) * N, st));
-    CU_TRY(c, cudaMemsetAsync(s.isc, 0, sizeof(int) * (N + 1), st));
+    CU_TRY(c, cudaMemsetAsync(s.isc + E, 0, sizeof(int) * (n + p.G + 1), st));
     CU_TRY(c, cudaMemsetAsync(s.cdeath, 0, sizeof(unsigned long long) * N, st));
     CU_TRY(c, cudaMemsetAsync(s.st_hi, 0, sizeof(unsigned long long) * N, st));
     CU_TRY(c, cudaMemsetAsync(s.st_lo, 0, sizeof(unsigned long long) * N, st));
@@ -692,13 +700,15 @@ dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro 
     TK(c, "k_c_nrec", k_c_nrec<<<gn, kBlock, 0, st>>>(gv, s.isrep, d.size, m.w, s.cpar, s.link, s.cbirth, nrec));
     TK(c, "k_c_points", k_c_points<<<gE, kBlock, 0, st>>>(gv, s.cpar, nrec, o.fall_cluster, o.fall_lambda,
                                                          s.st_hi, s.st_lo));
-    TK(c, "k_c_child_stab", k_c_child_stab<<<gN, kBlock, 0, st>>>(N, gv, s.isc, s.cparent, d.size, s.cbirth,
-                                                                 s.cdeath, s.st_hi, s.st_lo));
-    DG_TRY(exclusive_scan_i32(c, s.isc, s.cpos, N + 1, s.scan_tmp));
+    // cluster flags of node ids E .. N (the last one a zero sentinel)
+    DG_TRY(exclusive_scan_i32(c, s.isc + E, s.cpos, n + p.G + 1, s.scan_tmp));
     int64_t ncl;
-    DG_TRY(read_counters(c, (const int64_t *)(s.cpos + N), 1, &ncl));
-    TK(c, "k_c_compact", k_c_compact<<<gN, kBlock, 0, st>>>(N, s.isc, s.cpos, s.clist, s.cidx));
+    DG_TRY(read_counters(c, (const int64_t *)(s.cpos + n + p.G), 1, &ncl));
+    TK(c, "k_c_compact", k_c_compact<<<gn, kBlock, 0, st>>>(E, n + p.G, s.isc + E, s.cpos, s.clist, s.cidx));
     o.n_cl = ncl;
+    CU_TRY(c, cudaMemsetAsync(s.csz, 0, sizeof(unsigned long long) * (ncl + 1), st));
+    TK(c, "k_c_child_size", k_c_child_size<<<grid_for(ncl, kBlock, kStreamCap), kBlock, 0, st>>>(
+                                ncl, gv, s.clist, s.cparent, s.cidx, d.size, s.csz));
     // ---- excess of mass over the cluster tree
     Eom e;
     e.ncl = ncl;
@@ -724,7 +734,7 @@ dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro 
     const int gc = grid_for(ncl + 1, kBlock, kStreamCap);
     e.flag = s.cnt + 2;
     CU_TRY(c, cudaMemsetAsync(s.pending, 0, sizeof(int) * (ncl + 1), st));
-    TK(c, "k_e_init", k_e_init<<<gc, kBlock, 0, st>>>(e, s.st_hi, s.st_lo));
+    TK(c, "k_e_init", k_e_init<<<gc, kBlock, 0, st>>>(e, s.st_hi, s.st_lo, s.cbirth, s.cdeath, s.csz));
     TK(c, "k_e_iota", k_e_iota<<<gc, kBlock, 0, st>>>(ncl, s.al1));
     int32_t *al = s.al1, *al2 = s.al2;
     int64_t nact = ncl;

@@ -231,7 +231,8 @@ __global__ void k_munpack(const unsigned long long *key, const unsigned long lon
                           const int32_t *oidx, const int64_t *out_off, const TE *te, int64_t *out_t,
                           int32_t *out_id, int32_t *out_r, int4 *outrk, int32_t *pos_out, int64_t *in_t,
                           int32_t *in_id, int32_t *in_r, int32_t *pos_in, unsigned char *in_head,
-                          int2 *inrk, int2 *in_va, int2 *out_vb) {
+                          int2 *inrk, int2 *in_va, int2 *out_vb, unsigned long long *out_key,
+                          unsigned long long *in_key) {
     const unsigned long long cmask = (1ull << cb) - 1ull;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n2;
          x += (int64_t)gridDim.x * blockDim.x) {
@@ -244,10 +245,12 @@ __global__ void k_munpack(const unsigned long long *key, const unsigned long lon
         const int64_t obv = ob - out_off[v];     // out-items before x within v's list
         int32_t e;
         int64_t tt;
+        unsigned long long pk = 0;  // (t - tmin) << 32 | e
         if (val) {  // carried by the sort
             const unsigned long long vv = val[x];
             e = (int32_t)(vv >> 32);
             tt = (int64_t)(vv & 0xffffffffull) + tmin;
+            pk = (vv << 32) | (vv >> 32);
         } else {
             const TE rec = te[r];
             e = rec.e;
@@ -262,6 +265,7 @@ __global__ void k_munpack(const unsigned long long *key, const unsigned long lon
             // b: in-edges of v with t <= t_r; v's in-list starts at moff[v] - out_off[v]
             outrk[r] = make_int4((int32_t)slot, (int32_t)(seg - obv), (int32_t)(moff[v] - out_off[v]), 0);
             out_vb[slot] = make_int2((int32_t)v, (int32_t)(seg - obv));
+            if (val) out_key[slot] = pk;
         } else {
             const int64_t slot = x - ob;
             in_t[slot] = tt;
@@ -271,6 +275,7 @@ __global__ void k_munpack(const unsigned long long *key, const unsigned long lon
             in_head[slot] = (seg - obv) == 0;    // first entry of v's in-list
             inrk[r] = make_int2((int32_t)ob, (int32_t)out_off[v + 1]);  // ob = out_off[v] + a
             in_va[slot] = make_int2((int32_t)v, (int32_t)obv);
+            if (val) in_key[slot] = pk;
         }
     }
 }
@@ -427,6 +432,8 @@ void plan_csr(Arena &ws, const Problem &p, Csr &o) {
     o.in_gs = ws.take<int32_t>(p.E);
     o.in_va = ws.take<int2>(p.E);
     o.out_vb = ws.take<int2>(p.E);
+    o.out_key = ws.take<unsigned long long>(p.E);
+    o.in_key = ws.take<unsigned long long>(p.E);
 }
 
 void carve_segsort(Arena &a, int64_t V, int64_t n, SegSort &s) {
@@ -625,7 +632,7 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
                            key, mval, p.tmin, 2 * E, cb, s.moff, s.oidx, o.out_off, s.te, o.out_t, o.out_id,
                            o.out_r, o.outrk,
                            o.pos_out, o.in_t, o.in_id, o.in_r, o.pos_in, s.in_head, o.inrk, o.in_va,
-                           o.out_vb));
+                           o.out_vb, o.out_key, o.in_key));
     // start of every in-list entry's tie group (the kNN window takes a crossing group's smallest ids)
     DG_TRY((device_scan<long long, MaxI64, LoadInGroupHead, StoreI32>(c, LoadInGroupHead{o.in_t, s.in_head},
                                                                       StoreI32{o.in_gs}, E, MaxI64{}, 0ll, true,

@@ -23,8 +23,15 @@
 
 namespace dgec {
 
-// Super-vertex labels are internal ids r (a leaf's label is its own r);
-// sroot holds dendrogram node ids, so a leaf's root is its original id.
+// Super-vertex labels are internal ids r (a leaf's label is its own r).
+// Each super-vertex's dendrogram root (a node id, so a leaf's root is its
+// original id) and size share one 16-byte record: a chain step reads both
+// with one sector.
+struct SvRec {
+    int64_t size;
+    int32_t root;
+    int32_t pad;
+};
 //
 // minr (a super-vertex's smallest live edge) and tau (a pointer tree's
 // smallest non-pointer edge) live one round each. A slot holds
@@ -40,7 +47,7 @@ __device__ __forceinline__ int rval(unsigned long long k, unsigned stamp) {
     return (unsigned)(k >> 32) == stamp ? (int)(unsigned)k : INT_MAX;
 }
 __global__ void k_d_init(int64_t E, int64_t n, const int32_t *mu, const int32_t *mv,
-                         const int32_t *orig_of, int32_t *svpar, int32_t *sroot, int64_t *ssize,
+                         const int32_t *orig_of, int32_t *svpar, SvRec *sv,
                          unsigned long long *minr, unsigned long long *tau, int32_t *parent, int32_t *act, int32_t *ecu,
                          int32_t *ecv) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < E + n;
@@ -48,8 +55,7 @@ __global__ void k_d_init(int64_t E, int64_t n, const int32_t *mu, const int32_t 
         parent[x] = -1;
         if (x < E) {
             svpar[x] = (int32_t)x;
-            sroot[x] = orig_of[x];
-            ssize[x] = 1;
+            sv[x] = SvRec{1, orig_of[x], 0};
             minr[x] = ~0ull;
             tau[x] = ~0ull;
         }
@@ -164,8 +170,7 @@ __global__ void k_d_emit(const int32_t *act, int64_t na, const int32_t *ecu, con
 }
 
 __global__ void k_d_chain(const unsigned long long *__restrict__ key, const unsigned long long *__restrict__ val,
-                          int64_t nacc, int64_t E, int sbits, const int32_t *__restrict__ sroot,
-                          const int64_t *__restrict__ ssize, int32_t *__restrict__ la, int32_t *__restrict__ lb,
+                          int64_t nacc, int64_t E, int sbits, const SvRec *__restrict__ sv, int2 *__restrict__ lab,
                           int32_t *__restrict__ parent, long long *__restrict__ contrib, int *__restrict__ head) {
     const unsigned long long smask = (1ull << sbits) - 1ull;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nacc;
@@ -177,17 +182,18 @@ __global__ void k_d_chain(const unsigned long long *__restrict__ key, const unsi
         const bool h = (x == 0) || (key[x - 1] >> sbits) != G;
         int c1, c2;
         long long add;
+        const SvRec ry = sv[Y];
         if (h) {
-            c1 = sroot[Y];
-            c2 = sroot[O];
-            add = ssize[Y] + ssize[O];
+            const SvRec ro = sv[O];
+            c1 = ry.root;
+            c2 = ro.root;
+            add = ry.size + ro.size;
         } else {
             c1 = (int)(E + (int64_t)(key[x - 1] & smask));
-            c2 = sroot[Y];
-            add = ssize[Y];
+            c2 = ry.root;
+            add = ry.size;
         }
-        la[s] = c1 < c2 ? c1 : c2;
-        lb[s] = c1 < c2 ? c2 : c1;
+        lab[s] = c1 < c2 ? make_int2(c1, c2) : make_int2(c2, c1);  // one sector per row
         parent[c1] = (int32_t)(E + s);
         parent[c2] = (int32_t)(E + s);
         contrib[x] = add;
@@ -197,8 +203,7 @@ __global__ void k_d_chain(const unsigned long long *__restrict__ key, const unsi
 
 __global__ void k_d_sizes(const unsigned long long *__restrict__ key, const unsigned long long *__restrict__ val,
                           int64_t nacc, int64_t E, int sbits, const long long *__restrict__ csum,
-                          int64_t *__restrict__ lsize, int32_t *__restrict__ svpar, int32_t *__restrict__ sroot,
-                          int64_t *__restrict__ ssize) {
+                          int64_t *__restrict__ lsize, int32_t *__restrict__ svpar, SvRec *__restrict__ sv) {
     const unsigned long long smask = (1ull << sbits) - 1ull;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nacc;
          x += (int64_t)gridDim.x * blockDim.x) {
@@ -209,10 +214,7 @@ __global__ void k_d_sizes(const unsigned long long *__restrict__ key, const unsi
         svpar[(int)(vv >> 32)] = (int32_t)G;
         svpar[(int)(vv & 0xffffffffu)] = (int32_t)G;
         bool tail = (x == nacc - 1) || (key[x + 1] >> sbits) != G;
-        if (tail) {
-            sroot[G] = (int32_t)(E + s);
-            ssize[G] = csum[x];
-        }
+        if (tail) sv[G] = SvRec{csum[x], (int32_t)(E + s), 0};
     }
 }
 
@@ -255,6 +257,16 @@ __global__ void k_d_keep(const int32_t *__restrict__ act, int64_t na, const int 
     }
 }
 
+__global__ void k_d_split(const int2 *__restrict__ lab, int64_t n, int32_t *__restrict__ la,
+                          int32_t *__restrict__ lb) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int2 r = lab[s];
+        la[s] = r.x;
+        lb[s] = r.y;
+    }
+}
+
 void plan_dendro(Arena &ws, const Problem &p, Dendro &o) {
     o.a = ws.take<int32_t>(p.E);
     o.b = ws.take<int32_t>(p.E);
@@ -263,9 +275,10 @@ void plan_dendro(Arena &ws, const Problem &p, Dendro &o) {
 }
 
 struct DScratch {
-    int32_t *svpar, *sroot, *gp, *act, *act2, *ecu, *ecv, *ecu2, *ecv2;
+    int32_t *svpar, *gp, *act, *act2, *ecu, *ecv, *ecu2, *ecv2;
+    SvRec *sv;
+    int2 *lab;  // rows (a, b) side by side; split into the two outputs at the end
     unsigned long long *minr, *tau;  // round-stamped slots (see rkey)
-    int64_t *ssize;
     int *flag, *head;
     long long *pos, *contrib, *csum, *scan_tmp;
     SegVal *seg_tmp;
@@ -276,11 +289,11 @@ static DScratch carve_dendro(Arena &a, const Problem &p) {
     DScratch s;
     int64_t E = p.E;
     s.svpar = a.take<int32_t>(E);
-    s.sroot = a.take<int32_t>(E);
+    s.sv = a.take<SvRec>(E);
+    s.lab = a.take<int2>(E);
     s.minr = a.take<unsigned long long>(E);
     s.tau = a.take<unsigned long long>(E);
     s.gp = a.take<int32_t>(E);
-    s.ssize = a.take<int64_t>(E);
     s.act = a.take<int32_t>(E);
     s.act2 = a.take<int32_t>(E);
     s.ecu = a.take<int32_t>(E);
@@ -315,7 +328,7 @@ dgec_status stage_dendro(Ctx *c, const Problem &p, const Csr &g, const Msf &m, D
     Arena a(scratch, SIZE_MAX);
     DScratch s = carve_dendro(a, p);
     TK(c, "k_d_init", k_d_init<<<grid_for(E + n, kBlock, kStreamCap), kBlock, 0, st>>>(
-                          E, n, m.ru, m.rv, g.orig_of, s.svpar, s.sroot, s.ssize, s.minr, s.tau,
+                          E, n, m.ru, m.rv, g.orig_of, s.svpar, s.sv, s.minr, s.tau,
                           o.parent, s.act, s.ecu, s.ecv));
     const int lb = p.idbits > 0 ? p.idbits : 1;
     const int sbits = bits_for((uint64_t)(n > 1 ? n - 1 : 1));
@@ -350,11 +363,11 @@ dgec_status stage_dendro(Ctx *c, const Problem &p, const Csr &g, const Msf &m, D
         DG_TRY(radix_sort(c, RadixBuffers{s.k1, s.k2, s.v1, s.v2}, nacc, 0, lb + sbits, s.radix, &in_b));
         unsigned long long *key = in_b ? s.k2 : s.k1, *val = in_b ? s.v2 : s.v1;
         const int ga = grid_for(nacc, kBlock, kStreamCap);
-        TK(c, "k_d_chain", k_d_chain<<<ga, kBlock, 0, st>>>(key, val, nacc, E, sbits, s.sroot, s.ssize, o.a, o.b,
+        TK(c, "k_d_chain", k_d_chain<<<ga, kBlock, 0, st>>>(key, val, nacc, E, sbits, s.sv, s.lab,
                                                            o.parent, s.contrib, s.head));
         DG_TRY(segmented_inclusive_sum(c, s.contrib, s.head, s.csum, nacc, s.seg_tmp));
         TK(c, "k_d_sizes", k_d_sizes<<<ga, kBlock, 0, st>>>(key, val, nacc, E, sbits, s.csum, o.size, s.svpar,
-                                                           s.sroot, s.ssize));
+                                                           s.sv));
         TK(c, "k_d_keep", k_d_keep<<<g, kBlock, 0, st>>>(act, na, s.flag, s.pos, act2, ecu, ecv, ecu2, ecv2,
                                                          s.svpar));
         na -= nacc;
@@ -369,6 +382,8 @@ dgec_status stage_dendro(Ctx *c, const Problem &p, const Csr &g, const Msf &m, D
         ecv2 = t;
         o.rounds = round + 1;
     }
+    if (n > 0)
+        TK(c, "k_d_split", k_d_split<<<grid_for(n, kBlock, kStreamCap), kBlock, 0, st>>>(s.lab, n, o.a, o.b));
     return DGEC_OK;
 }
 

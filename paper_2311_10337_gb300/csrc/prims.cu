@@ -57,19 +57,24 @@ __global__ void __launch_bounds__(kBlock) k_radix_hist(const unsigned long long 
                                                        int64_t tiles) {
     __shared__ int cnt[kRadix];
     for (int i = threadIdx.x; i < kRadix; i += kBlock) cnt[i] = 0;
-    __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * kTile;
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    // all loads first, then the counting
+    int d[kItems];
 #pragma unroll
     for (int j = 0; j < kItems; j++) {
-        int64_t idx = base + j * kBlock + threadIdx.x;
-        if (idx < n) atomicAdd(&cnt[(keys[idx] >> shift) & mask], 1);
+        const int64_t idx = base + j * kBlock + threadIdx.x;
+        d[j] = idx < n ? (int)((keys[idx] >> shift) & mask) : kRadix;
     }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kItems; j++)
+        if (d[j] < kRadix) atomicAdd(&cnt[d[j]], 1);
     __syncthreads();
     for (int i = threadIdx.x; i < kRadix; i += kBlock) hist[(int64_t)i * tiles + blockIdx.x] = cnt[i];
 }
 
 template <bool VALS>
-__global__ void __launch_bounds__(kBlock) k_radix_scatter(
+__global__ void __launch_bounds__(kBlock, 4) k_radix_scatter(
     const unsigned long long *kin, const unsigned long long *vin, unsigned long long *kout,
     unsigned long long *vout, int64_t n, int shift, unsigned mask, const long long *offs,
     int64_t tiles) {
@@ -82,26 +87,31 @@ __global__ void __launch_bounds__(kBlock) k_radix_scatter(
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < kWarps * kRadix; i += kBlock) (&wcnt[0][0])[i] = 0;
     const int64_t base = (int64_t)blockIdx.x * kTile;
+    // this tile's global start of digit threadIdx.x (kBlock == kRadix): it
+    // does not depend on the keys, so its load overlaps theirs
+    const long long gstart = offs[(int64_t)threadIdx.x * tiles + blockIdx.x];
     unsigned long long k[kItems], v[kItems];
-    int d[kItems], r[kItems];
+    int r[kItems];  // rank among the warp's items of its digit; -1 past the end
+    const int64_t wbase = base + warp * (32 * kItems) + lane;
+    const int nv = n - wbase > 0 ? (int)((n - wbase + 31) >> 5) : 0;  // this lane's valid items
 #pragma unroll
     for (int i = 0; i < kItems; i++) {
-        int64_t idx = base + warp * (32 * kItems) + i * 32 + lane;
-        bool ok = idx < n;
-        k[i] = ok ? kin[idx] : 0ull;
-        if (VALS) v[i] = ok ? vin[idx] : 0ull;
-        d[i] = ok ? (int)((k[i] >> shift) & mask) : kRadix;
+        const bool ok = i < nv;
+        k[i] = ok ? kin[wbase + i * 32] : 0ull;
+        if (VALS) v[i] = ok ? vin[wbase + i * 32] : 0ull;
     }
     __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
     for (int i = 0; i < kItems; i++) {
-        unsigned peers = __match_any_sync(0xffffffffu, d[i]);
+        // the digit is recomputed from the key where needed (fewer live registers)
+        const int d = i < nv ? (int)((k[i] >> shift) & mask) : kRadix;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
         int leader = __ffs(peers) - 1;
-        int before = d[i] < kRadix ? wcnt[warp][d[i]] : 0;
-        r[i] = before + __popc(peers & lt);
+        int before = d < kRadix ? wcnt[warp][d] : 0;
+        r[i] = d < kRadix ? before + __popc(peers & lt) : -1;
         __syncwarp();
-        if (lane == leader && d[i] < kRadix) wcnt[warp][d[i]] = before + __popc(peers);
+        if (lane == leader && d < kRadix) wcnt[warp][d] = before + __popc(peers);
         __syncwarp();
     }
     __syncthreads();
@@ -118,12 +128,13 @@ __global__ void __launch_bounds__(kBlock) k_radix_scatter(
     int start = block_exclusive(run, AddI{}, 0, scan_sm, &total);
     dstart[digit] = start;
     // this tile's global start of every digit, less its start in the tile
-    soff[digit] = offs[(int64_t)digit * tiles + blockIdx.x] - start;
+    soff[digit] = gstart - start;
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < kItems; i++) {
-        if (d[i] < kRadix) {
-            int lpos = dstart[d[i]] + wcnt[warp][d[i]] + r[i];
+        if (r[i] >= 0) {
+            const int d = (int)((k[i] >> shift) & mask);
+            int lpos = dstart[d] + wcnt[warp][d] + r[i];
             skeys[lpos] = k[i];
             if (VALS) svals[lpos] = v[i];
         }

@@ -247,14 +247,18 @@ __global__ void __launch_bounds__(256) k_knn(const int64_t *t, const int32_t *or
     }
 }
 
-// The same for time spans below 2^32 (every |dt| fits 32 bits): a
-// candidate is one 64-bit key (w << 32 | id), so the network sorts plain
-// integers (two registers a candidate instead of three, one compare a step)
-// and the kernel keeps more warps resident to hide its gathers' latency.
+// The same for time spans below 2^32 (every |dt| fits 32 bits): each list
+// entry is one 64-bit key ((t - tmin) << 32 | id) written by stage A, so a
+// window is one run of one array (half the sectors of separate time and id
+// arrays), and a candidate is one 64-bit key (w << 32 | id): the network
+// sorts plain integers (two registers a candidate instead of three, one
+// compare a step) and the kernel keeps more warps resident to hide its
+// gathers' latency.
 template <int K>
-__global__ void __launch_bounds__(256, K <= 8 ? 4 : 1) k_knn32(const int64_t *t, const int32_t *orig_of, int64_t E,
-                                               const int64_t *out_t, const int32_t *out_id,
-                                               const int64_t *in_t, const int32_t *in_id,
+__global__ void __launch_bounds__(256, K <= 8 ? 3 : 1) k_knn32(const int64_t *t, long long tmin,
+                                               const int32_t *orig_of, int64_t E,
+                                               const unsigned long long *__restrict__ out_key,
+                                               const unsigned long long *__restrict__ in_key,
                                                const int32_t *in_gs, const int4 *outrk, const int2 *inrk,
                                                int G,
                                                const int32_t *egraph, const int64_t *eoff,
@@ -262,9 +266,10 @@ __global__ void __launch_bounds__(256, K <= 8 ? 4 : 1) k_knn32(const int64_t *t,
                                                int32_t *knn, int64_t *core) {
     constexpr int N = 2 * K;
     constexpr unsigned long long kNone = 0xFFFFFFFFFFFFFFFFull;
+    constexpr unsigned long long kLo = 0xFFFFFFFFull;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < E;
          r += (int64_t)gridDim.x * blockDim.x) {
-        const long long te = t[r];
+        const unsigned long long te = (unsigned long long)(t[r] - tmin);
         const int64_t e = orig_of[r];
         const int gr = G > 1 ? egraph[e] : 0;
         const int k = gk[gr];
@@ -278,24 +283,33 @@ __global__ void __launch_bounds__(256, K <= 8 ? 4 : 1) k_knn32(const int64_t *t,
         unsigned long long c[N];
         const int64_t lo = b - K > 0 ? b - K : 0;
         int64_t g0 = lo, take_grp = 0;
-        const bool cross = lo > 0 && in_t[ib + lo] == in_t[ib + lo - 1];
+        const unsigned long long tlo = lo < b ? in_key[ib + lo] >> 32 : 0;
+        const bool cross = lo > 0 && tlo == (in_key[ib + lo - 1] >> 32);
         if (cross) {
-            const long long T = in_t[ib + lo];
             g0 = (int64_t)in_gs[ib + lo] - ib;
             int64_t g1 = lo;
-            while (g1 < b && in_t[ib + g1] == T) g1++;  // at most K steps
+            while (g1 < b && (in_key[ib + g1] >> 32) == tlo) g1++;  // at most K steps
             take_grp = g1 - lo;
         }
 #pragma unroll
         for (int x = 0; x < K; x++) {
             const int64_t idx = x < take_grp ? g0 + x : lo + x;
-            c[x] = idx < b ? ((unsigned long long)(te - in_t[ib + idx]) << 32) | (unsigned)in_id[ib + idx]
-                           : kNone;
+            if (idx < b) {
+                const unsigned long long kk = in_key[ib + idx];
+                c[x] = ((te - (kk >> 32)) << 32) | (kk & kLo);
+            } else {
+                c[x] = kNone;
+            }
         }
 #pragma unroll
         for (int x = 0; x < K; x++) {
             const int64_t idx = a0 + x;
-            c[K + x] = idx < a1 ? ((unsigned long long)(out_t[idx] - te) << 32) | (unsigned)out_id[idx] : kNone;
+            if (idx < a1) {
+                const unsigned long long kk = out_key[idx];
+                c[K + x] = (((kk >> 32) - te) << 32) | (kk & kLo);
+            } else {
+                c[K + x] = kNone;
+            }
         }
 #pragma unroll
         for (int size = 2; size <= N; size <<= 1) {
@@ -372,16 +386,20 @@ dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void
 #define KNN_ARGS                                                                                   \
     g.it, g.orig_of, E, g.out_t, g.out_id, g.in_t, g.in_id, g.in_gs, g.outrk, g.inrk, p.G, p.egraph, p.eoff, \
         p.gk, p.knn_off, p.dmax, o.knn, o.core
-    if (p.knn && c->knn_packed && p.tbits <= 32) {  // every |dt| fits 32 bits: packed candidate keys
-        if (p.k <= 4) TK(c, "k_knn", k_knn32<4><<<grid, kb, 0, st>>>(KNN_ARGS));
-        else if (p.k <= 8) TK(c, "k_knn", k_knn32<8><<<grid, kb, 0, st>>>(KNN_ARGS));
-        else TK(c, "k_knn", k_knn32<16><<<grid, kb, 0, st>>>(KNN_ARGS));
+#define KNN32_ARGS                                                                                 \
+    g.it, p.tmin, g.orig_of, E, g.out_key, g.in_key, g.in_gs, g.outrk, g.inrk, p.G, p.egraph, p.eoff, p.gk, \
+        p.knn_off, p.dmax, o.knn, o.core
+    if (p.knn && c->knn_packed && p.tbits <= 32) {  // every |dt| fits 32 bits: packed list and candidate keys
+        if (p.k <= 4) TK(c, "k_knn", k_knn32<4><<<grid, kb, 0, st>>>(KNN32_ARGS));
+        else if (p.k <= 8) TK(c, "k_knn", k_knn32<8><<<grid, kb, 0, st>>>(KNN32_ARGS));
+        else TK(c, "k_knn", k_knn32<16><<<grid, kb, 0, st>>>(KNN32_ARGS));
     } else if (p.knn) {
         if (p.k <= 4) TK(c, "k_knn", k_knn<4><<<grid, kb, 0, st>>>(KNN_ARGS));
         else if (p.k <= 8) TK(c, "k_knn", k_knn<8><<<grid, kb, 0, st>>>(KNN_ARGS));
         else TK(c, "k_knn", k_knn<16><<<grid, kb, 0, st>>>(KNN_ARGS));
     }
 #undef KNN_ARGS
+#undef KNN32_ARGS
     SkView v{g.isrc, g.idst, g.out_off, g.in_off, g.out_r, g.in_r, g.outrk, g.inrk};
     TK(c, "k_links_in", k_links_in<<<grid_for(E, kBlock, kStreamCap), kBlock, 0, st>>>(
                             v, g.in_va, g.out_t, g.in_t, E, p.dmax, s.rec));

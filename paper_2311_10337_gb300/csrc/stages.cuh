@@ -73,6 +73,9 @@ struct Csr {
     int2 *in_va, *out_vb;       // [E] by list slot: (vertex, a) of each in-list entry, (vertex, b) of
                                 //   each out-list entry (the skeleton pass walks the lists in order)
     int32_t *in_gs;             // [E] by in-list slot: first slot of its tie group (same vertex, same t)
+    unsigned long long *out_key, *in_key;  // [E] by list slot, written when every t - tmin fits 32 bits:
+                                           //   (t - tmin) << 32 | original id, so a kNN window is one run
+                                           //   of one array
 };
 void plan_csr(Arena &ws, const Problem &p, Csr &o);
 size_t csr_scratch_bytes(const Problem &p);
