@@ -277,8 +277,9 @@ dgec_status dgec_server_destroy(dgec_server *srv);
  * paper; it changes speed, never results): threads per CTA of the kNN kernel
  * (64, 128 or 256; default 128), the number of CTAs of each grid-stride
  * streaming kernel (1 .. 2^20; default 65,536), and whether the kNN kernel
- * sorts its candidates as packed 64-bit keys (|dt| << 32 | id; 0 or 1,
- * default 0; used only when the time span fits 32 bits). The autotuner of
+ * reads its windows from packed 64-bit list keys ((t - tmin) << 32 | id) and
+ * sorts its candidates as packed keys (|dt| << 32 | id) (0 or 1, default 1;
+ * used only when the time span fits 32 bits). The autotuner of
  * the Python package picks them per GPU model and workload. Invalid values
  * give DGEC_ERR_INVALID_ARG and leave the configuration unchanged. */
 typedef struct {

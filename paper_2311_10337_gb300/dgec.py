@@ -326,10 +326,10 @@ class Context:
             i += 1
         return out
 
-    def set_launch_config(self, knn_block: int, stream_ctas: int, knn_packed: int = 0):
+    def set_launch_config(self, knn_block: int, stream_ctas: int, knn_packed: int = 1):
         """Threads per CTA of the kNN kernel, CTAs of the grid-stride
-        streaming kernels and the kNN candidate form (packed 64-bit keys or
-        not) for the calls on this context (speed only)."""
+        streaming kernels and the kNN form (packed 64-bit list and candidate
+        keys or not) for the calls on this context (speed only)."""
         cfg = LaunchConfig(knn_block, stream_ctas, knn_packed)
         self._check(self.L.dgec_set_launch_config(self.h, ctypes.byref(cfg)))
 
