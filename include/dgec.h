@@ -331,8 +331,8 @@ dgec_status dgec_kernel_timing(dgec_ctx *ctx, int i, const char **name, double *
  * Limits: n_nodes <= 262,144 and n_edges <= 524,288, else
  * DGEC_ERR_TOO_LARGE; a bad id, u >= v or w < 0 gives
  * DGEC_ERR_INVALID_ARG (nothing is written to the outputs then).
- * The first call on a device looks up the array's device address; make it
- * before any stream capture. Every call reuses the same array (each call
+ * It synchronises the stream once per Boruvka round (a counter read), so it
+ * cannot be stream-captured. Every call reuses the same array (each call
  * re-initialises what must start from a known value), so calls that
  * overlap on the GPU race with each other: serialise them.
  */

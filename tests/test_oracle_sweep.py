@@ -191,7 +191,11 @@ def test_mutual_reachability_clusters_against_the_filtration():
     R-19): H = L* together with every node's kNN pairs taken by brute force
     from the explicit L_G, each pair once, weighed max(core_a, core_b, |dt|)
     with brute-force core distances, pairs with an infinite core dropped;
-    the oracle's clusters equal the restatement's on that H, k = 1, 2, 3."""
+    the oracle's clusters equal the restatement's on that H, k = 1, 2, 3.
+    The L* part of H is the oracle's own skeleton, so a skeleton defect would
+    sit on both sides here: this pin relies on the separate Thm. 3 pin of
+    O.skeleton against the explicit line graph; the kNN pairs and core
+    distances are independent of the oracle."""
     for seed in range(0, N_GRAPHS, 7):
         g = _graph(seed)
         E, M, k = g.n_edges, 2 + seed % 3, 1 + seed % 3
