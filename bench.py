@@ -63,11 +63,11 @@ def knn_bytes_per_edge(k: int) -> int:
     return 24 + 4 * k + 8
 
 
-# DRAM bytes (read + write) per edge of k_knn (k = 8) from one ncu capture of
-# the kernel on the hub graph at scale 0.05 (10M edges), scaled to a launch by
-# the edges it processes (profiles/k_knn_hub_small.md); None until captured
-# for the kernel as it stands.
-KNN_TRAFFIC_BYTES_PER_EDGE_K8 = None
+# DRAM bytes (read + write) per edge of the kNN kernel (packed form, k = 8)
+# from one ncu capture on the hub graph at scale 0.02 (4M edges: 312.6 MB read
+# + 212.7 MB written), scaled to a launch by the edges it processes
+# (profiles/k_knn32_hub_small.md). Set back to None when the kernel changes.
+KNN_TRAFFIC_BYTES_PER_EDGE_K8 = (312_571_904 + 212_684_800) / 4_000_000
 
 CPU_SAMPLE_MINUTES = {"hub": 25.0, "mid": 150.0, "tiny": 1e9}
 
