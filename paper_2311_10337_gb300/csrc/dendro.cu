@@ -267,6 +267,254 @@ __global__ void k_d_split(const int2 *__restrict__ lab, int64_t n, int32_t *__re
     }
 }
 
+// ------------------------------------------------ one-CTA tail of the rounds
+// Once at most kTailMax forest edges are live, one CTA runs every remaining
+// round: the same steps as the kernels above (bids, pointers, jumps, tau,
+// acceptance, chains, sizes, keep), separated by barriers instead of
+// launches, the accepted edges sorted by (group, rank) in shared memory by a
+// bitonic network, and no count read on the host between rounds. The output
+// orders of acceptance and keep come from shared counters: the sort orders
+// the accepted edges, and the live list's order changes no result.
+constexpr int kTailMax = 8192;
+constexpr int kTailThreads = 1024;
+constexpr size_t kTailSmem = (size_t)kTailMax * 16 + kTailMax;
+
+__device__ __forceinline__ SegVal tail_seg(SegVal a, SegVal b) {
+    SegVal r;
+    r.v = b.f ? b.v : a.v + b.v;
+    r.f = a.f | b.f;
+    return r;
+}
+
+__global__ void __launch_bounds__(kTailThreads) k_d_tail(
+    int32_t *act, int32_t *act2, int32_t *ecu, int32_t *ecu2, int32_t *ecv, int32_t *ecv2, int64_t na0, int64_t E,
+    int sbits, unsigned round0, unsigned max_rounds, unsigned long long *minr, unsigned long long *tau, int32_t *gp,
+    SvRec *sv, int32_t *svpar, int2 *lab, int32_t *parent, int64_t *lsize, int *status) {
+    extern __shared__ unsigned long long tsm[];
+    unsigned long long *skey = tsm, *sval = tsm + kTailMax;
+    unsigned char *sflag = (unsigned char *)(tsm + 2 * kTailMax);
+    __shared__ int s_nacc, s_nkeep;
+    __shared__ SegVal s_warp[kTailThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const unsigned long long smask = (1ull << sbits) - 1ull;
+    int na = (int)na0;
+    unsigned round = round0;
+    while (na > 0) {
+        if (round - round0 >= max_rounds) {
+            if (tid == 0) status[1] = 1;
+            return;
+        }
+        const unsigned stamp = kStampTop - round;
+        // bids: every live edge offers its rank to both super-vertices
+        for (int j = tid; j < na; j += kTailThreads) {
+            const unsigned long long key = rkey(stamp, act[j]);
+            const int cu = ecu[j], cv = ecv[j];
+            if (key < minr[cu]) atomicMin(&minr[cu], key);
+            if (key < minr[cv]) atomicMin(&minr[cv], key);
+        }
+        if (tid == 0) {
+            s_nacc = 0;
+            s_nkeep = 0;
+        }
+        __syncthreads();
+        // pointers (a mutual pair points both ends at its smaller label)
+        for (int j = tid; j < na; j += kTailThreads) {
+            const int s = act[j], cu = ecu[j], cv = ecv[j];
+            const bool pu = rval(minr[cu], stamp) == s, pv = rval(minr[cv], stamp) == s;
+            if (pu && pv) {
+                const int r = cu < cv ? cu : cv;
+                gp[cu] = r;
+                gp[cv] = r;
+            } else {
+                if (pu) gp[cu] = cv;
+                if (pv) gp[cv] = cu;
+            }
+        }
+        __syncthreads();
+        // every pointer to its tree's root
+        for (int j = tid; j < na; j += kTailThreads) {
+            const int s = act[j];
+            for (int side = 0; side < 2; side++) {
+                const int c = side ? ecv[j] : ecu[j];
+                if (rval(minr[c], stamp) != s) continue;
+                int r = gp[c];
+                for (int it = 0; it < kMaxWalk; it++) {
+                    const int rr = *(volatile int32_t *)(gp + r);
+                    if (rr == r) break;
+                    r = rr;
+                    *(volatile int32_t *)(gp + c) = r;
+                }
+            }
+        }
+        __syncthreads();
+        // tau: the smallest non-pointer edge touching each tree
+        for (int j = tid; j < na; j += kTailThreads) {
+            const int s = act[j], cu = ecu[j], cv = ecv[j];
+            if (rval(minr[cu], stamp) != s && rval(minr[cv], stamp) != s) {
+                const int gu = gp[cu], gv = gp[cv];
+                const unsigned long long key = rkey(stamp, s);
+                if (key < tau[gu]) atomicMin(&tau[gu], key);
+                if (key < tau[gv]) atomicMin(&tau[gv], key);
+            }
+        }
+        __syncthreads();
+        // accept the pointer edges below their tree's tau; emit (group, rank)
+        for (int j = tid; j < na; j += kTailThreads) {
+            const int s = act[j], cu = ecu[j], cv = ecv[j];
+            const bool own_u = rval(minr[cu], stamp) == s, own_v = rval(minr[cv], stamp) == s;
+            const int G = gp[cu];
+            const bool acc = (own_u || own_v) && s < rval(tau[G], stamp);
+            sflag[j] = acc;
+            if (acc) {
+                const int at = atomicAdd(&s_nacc, 1);
+                const unsigned Y = (unsigned)(own_u ? cu : cv), O = (unsigned)(own_u ? cv : cu);
+                skey[at] = ((unsigned long long)G << sbits) | (unsigned long long)s;
+                sval[at] = ((unsigned long long)Y << 32) | O;
+            }
+        }
+        __syncthreads();
+        const int nacc = s_nacc;
+        if (nacc == 0) {  // every round accepts each tree's mutual edge
+            if (tid == 0) status[1] = 2;
+            return;
+        }
+        int N = 1;
+        while (N < nacc) N <<= 1;
+        for (int i = nacc + tid; i < N; i += kTailThreads) skey[i] = ~0ull;  // padding sorts last
+        __syncthreads();
+        for (int size = 2; size <= N; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int i = tid; i < (N >> 1); i += kTailThreads) {
+                    const int lo = 2 * stride * (i / stride) + (i % stride), hi = lo + stride;
+                    const bool up = (lo & size) == 0;
+                    const unsigned long long ka = skey[lo], kb = skey[hi];
+                    if ((ka > kb) == up) {
+                        skey[lo] = kb;
+                        skey[hi] = ka;
+                        const unsigned long long t = sval[lo];
+                        sval[lo] = sval[hi];
+                        sval[hi] = t;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        // chains: each thread a run of up to 8 consecutive sorted edges
+        const int C = (nacc + kTailThreads - 1) / kTailThreads;  // <= kTailMax / kTailThreads
+        const int x0 = tid * C;
+        long long add[kTailMax / kTailThreads];
+        int hd[kTailMax / kTailThreads];
+#pragma unroll
+        for (int q = 0; q < kTailMax / kTailThreads; q++) {
+            const int x = x0 + q;
+            add[q] = 0;
+            hd[q] = 0;
+            if (q >= C || x >= nacc) continue;
+            const unsigned long long k = skey[x], vv = sval[x];
+            const int s = (int)(k & smask), Y = (int)(vv >> 32), O = (int)(vv & 0xffffffffu);
+            const bool h = x == 0 || (skey[x - 1] >> sbits) != (k >> sbits);
+            const SvRec ry = sv[Y];
+            int c1, c2;
+            if (h) {
+                const SvRec ro = sv[O];
+                c1 = ry.root;
+                c2 = ro.root;
+                add[q] = ry.size + ro.size;
+            } else {
+                c1 = (int)(E + (int64_t)(skey[x - 1] & smask));
+                c2 = ry.root;
+                add[q] = ry.size;
+            }
+            lab[s] = c1 < c2 ? make_int2(c1, c2) : make_int2(c2, c1);
+            parent[c1] = (int32_t)(E + s);
+            parent[c2] = (int32_t)(E + s);
+            hd[q] = h;
+        }
+        // sizes along each chain: a segmented inclusive sum over the runs
+        SegVal agg;
+        agg.v = 0;
+        agg.f = 0;
+#pragma unroll
+        for (int q = 0; q < kTailMax / kTailThreads; q++) {
+            SegVal it;
+            it.v = add[q];
+            it.f = hd[q];
+            agg = tail_seg(agg, it);
+        }
+        SegVal inc = agg;
+        for (int d = 1; d < 32; d <<= 1) {
+            SegVal o;
+            o.v = ::__shfl_up_sync(0xffffffffu, inc.v, d);
+            o.f = ::__shfl_up_sync(0xffffffffu, inc.f, d);
+            if (lane >= d) inc = tail_seg(o, inc);
+        }
+        if (lane == 31) s_warp[wid] = inc;
+        __syncthreads();  // also orders the chains' reads of sv before the writes below
+        if (wid == 0) {
+            SegVal w = s_warp[lane];
+            for (int d = 1; d < 32; d <<= 1) {
+                SegVal o;
+                o.v = ::__shfl_up_sync(0xffffffffu, w.v, d);
+                o.f = ::__shfl_up_sync(0xffffffffu, w.f, d);
+                if (lane >= d) w = tail_seg(o, w);
+            }
+            s_warp[lane] = w;
+        }
+        __syncthreads();
+        SegVal run;
+        {
+            SegVal ex;
+            ex.v = ::__shfl_up_sync(0xffffffffu, inc.v, 1);
+            ex.f = ::__shfl_up_sync(0xffffffffu, inc.f, 1);
+            if (lane == 0) {
+                ex.v = 0;
+                ex.f = 0;
+            }
+            if (wid > 0) ex = lane == 0 ? s_warp[wid - 1] : tail_seg(s_warp[wid - 1], ex);
+            run = ex;
+        }
+#pragma unroll
+        for (int q = 0; q < kTailMax / kTailThreads; q++) {
+            const int x = x0 + q;
+            if (q >= C || x >= nacc) continue;
+            SegVal it;
+            it.v = add[q];
+            it.f = hd[q];
+            run = tail_seg(run, it);
+            const unsigned long long k = skey[x], vv = sval[x];
+            const unsigned long long G = k >> sbits;
+            const int s = (int)(k & smask);
+            lsize[s] = run.v;
+            svpar[(int)(vv >> 32)] = (int32_t)G;
+            svpar[(int)(vv & 0xffffffffu)] = (int32_t)G;
+            if (x == nacc - 1 || (skey[x + 1] >> sbits) != G) sv[G] = SvRec{run.v, (int32_t)(E + s), 0};
+        }
+        __syncthreads();
+        // the edges not accepted stay live, their labels moved one hop
+        for (int j = tid; j < na; j += kTailThreads) {
+            if (sflag[j]) continue;
+            const int at = atomicAdd(&s_nkeep, 1);
+            act2[at] = act[j];
+            ecu2[at] = svpar[ecu[j]];
+            ecv2[at] = svpar[ecv[j]];
+        }
+        __syncthreads();
+        na = s_nkeep;
+        int32_t *t = act;
+        act = act2;
+        act2 = t;
+        t = ecu;
+        ecu = ecu2;
+        ecu2 = t;
+        t = ecv;
+        ecv = ecv2;
+        ecv2 = t;
+        round++;
+        __syncthreads();
+    }
+    if (tid == 0) status[0] = (int)(round - round0);
+}
+
 void plan_dendro(Arena &ws, const Problem &p, Dendro &o) {
     o.a = ws.take<int32_t>(p.E);
     o.b = ws.take<int32_t>(p.E);
@@ -277,6 +525,7 @@ void plan_dendro(Arena &ws, const Problem &p, Dendro &o) {
 struct DScratch {
     int32_t *svpar, *gp, *act, *act2, *ecu, *ecv, *ecu2, *ecv2;
     SvRec *sv;
+    int *tstat;  // one-CTA tail: [0] rounds run, [1] error
     int2 *lab;  // rows (a, b) side by side; split into the two outputs at the end
     unsigned long long *minr, *tau;  // round-stamped slots (see rkey)
     int *flag, *head;
@@ -290,6 +539,7 @@ static DScratch carve_dendro(Arena &a, const Problem &p) {
     int64_t E = p.E;
     s.svpar = a.take<int32_t>(E);
     s.sv = a.take<SvRec>(E);
+    s.tstat = a.take<int>(2);
     s.lab = a.take<int2>(E);
     s.minr = a.take<unsigned long long>(E);
     s.tau = a.take<unsigned long long>(E);
@@ -345,6 +595,21 @@ dgec_status stage_dendro(Ctx *c, const Problem &p, const Csr &g, const Msf &m, D
     for (int64_t round = 0; na > 0; round++) {
         if (round >= (1 << 16))
             return set_err(c, DGEC_ERR_TIMEOUT, "dendrogram rounds exceeded %d", 1 << 16);
+        if (na <= kTailMax) {  // the rest in one CTA, one launch
+            CU_TRY(c, cudaFuncSetAttribute(k_d_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmem));
+            CU_TRY(c, cudaMemsetAsync(s.tstat, 0, 2 * sizeof(int), st));
+            TK(c, "k_d_tail", k_d_tail<<<1, kTailThreads, kTailSmem, st>>>(
+                                  act, act2, ecu, ecu2, ecv, ecv2, na, E, sbits, (unsigned)round,
+                                  (unsigned)((1 << 16) - round), s.minr, s.tau, s.gp, s.sv, s.svpar, s.lab,
+                                  o.parent, o.size, s.tstat));
+            int64_t ts;
+            DG_TRY(read_counters(c, (const int64_t *)s.tstat, 1, &ts));
+            const int done_rounds = (int)(ts & 0xffffffff), err = (int)(ts >> 32);
+            if (err == 1) return set_err(c, DGEC_ERR_TIMEOUT, "dendrogram rounds exceeded %d", 1 << 16);
+            if (err) return set_err(c, DGEC_ERR_INTERNAL, "dendrogram round accepted no edge");
+            o.rounds = round + done_rounds;
+            break;
+        }
         const int g = grid_for(na, kBlock, kStreamCap);
         const unsigned stamp = kStampTop - (unsigned)round;
         TK(c, "k_d_bid", k_d_bid<<<g, kBlock, 0, st>>>(act, na, ecu, ecv, s.minr, stamp));
