@@ -449,6 +449,50 @@ __global__ void k_e_commit(Eom e, int32_t *alist2, unsigned long long *n_open) {
     }
 }
 
+// Small cluster trees (at most kEomSmall clusters) in one CTA. Clusters are
+// numbered in ascending node id, and a parent cluster starts at a merge
+// above its children's, so every child comes before its parent: one
+// bottom-up sweep gives S = max(stab, sum of children's S) and the
+// children's sums, one top-down sweep the highest selected ancestor-or-self.
+// The sweeps are sequential (one thread, shared memory); loading and storing
+// are spread over the CTA. Same results as the contraction below.
+constexpr int kEomSmall = 4096;
+constexpr int kEomThreads = 1024;
+constexpr size_t kEomSmem = (size_t)kEomSmall * (16 + 16 + 4 + 4);
+__global__ void __launch_bounds__(kEomThreads) k_e_small(Eom e, int32_t *H) {
+    extern __shared__ __align__(16) unsigned long long esm[];
+    u128 *sst = reinterpret_cast<u128 *>(esm);       // stab
+    u128 *sacc = sst + kEomSmall;                    // children's S
+    int32_t *spar = reinterpret_cast<int32_t *>(sacc + kEomSmall);
+    int32_t *sh = spar + kEomSmall;
+    const int n = (int)e.ncl;
+    for (int c = threadIdx.x; c < n; c += kEomThreads) {
+        sst[c] = e.stab[c];
+        sacc[c] = 0;
+        spar[c] = e.par[c];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < n; c++) {  // children first
+            const u128 a = sacc[c], st = sst[c];
+            const int p = spar[c];
+            if (p >= 0) sacc[p] += st > a ? st : a;
+        }
+        for (int c = n - 1; c >= 0; c--) {  // parents first
+            const bool sel = e.clist[c] < e.R0 && sst[c] >= sacc[c];
+            const int p = spar[c];
+            const int hp = p >= 0 ? sh[p] : -1;
+            sh[c] = hp >= 0 ? hp : (sel ? c : -1);
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < n; c += kEomThreads) {
+        e.acc_hi[c] = (unsigned long long)(sacc[c] >> 64);
+        e.acc_lo[c] = (unsigned long long)sacc[c];
+        H[c] = sh[c];
+    }
+}
+
 __global__ void k_e_iota(int64_t n, int32_t *a) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x)
@@ -735,6 +779,11 @@ dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro 
     e.flag = s.cnt + 2;
     CU_TRY(c, cudaMemsetAsync(s.pending, 0, sizeof(int) * (ncl + 1), st));
     TK(c, "k_e_init", k_e_init<<<gc, kBlock, 0, st>>>(e, s.st_hi, s.st_lo, s.cbirth, s.cdeath, s.csz));
+    int32_t *Hi = s.H;  // highest selected ancestor-or-self of every cluster
+    if (ncl <= kEomSmall) {
+        CU_TRY(c, cudaFuncSetAttribute(k_e_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEomSmem));
+        TK(c, "k_e_small", k_e_small<<<1, kEomThreads, kEomSmem, st>>>(e, Hi));
+    } else {
     TK(c, "k_e_iota", k_e_iota<<<gc, kBlock, 0, st>>>(ncl, s.al1));
     int32_t *al = s.al1, *al2 = s.al2;
     int64_t nact = ncl;
@@ -783,7 +832,7 @@ dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro 
     TK(c, "k_e_childsum", k_e_childsum<<<gc, kBlock, 0, st>>>(e));
     TK(c, "k_e_childsum2", k_e_childsum2<<<gc, kBlock, 0, st>>>(e));
     TK(c, "k_e_select", k_e_select<<<gc, kBlock, 0, st>>>(e, s.H, s.J));
-    int32_t *Hi = s.H, *Ji = s.J, *Ho = s.H2, *Jo = s.J2;
+    int32_t *Ji = s.J, *Ho = s.H2, *Jo = s.J2;
     for (int it = 0; it < kMaxDouble; it++) {
         if ((it & 1) == 0) CU_TRY(c, cudaMemsetAsync(e.flag, 0, sizeof(unsigned long long), st));
         TK(c, "k_e_hdouble", k_e_hdouble<<<gc, kBlock, 0, st>>>(ncl, Hi, Ji, Ho, Jo, e.flag));
@@ -798,6 +847,7 @@ dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro 
             DG_TRY(read_counters(c, (const int64_t *)e.flag, 1, &live));
             if (!live) break;
         }
+    }
     }
     TK(c, "k_fill_i32", k_fill_i32<<<gc, kBlock, 0, st>>>(s.minmem, ncl + 1, INT_MAX));
     TK(c, "k_e_labels", k_e_labels<<<gE, kBlock, 0, st>>>(E, o.fall_cluster, s.cidx, Hi, o.labels, s.minmem));
