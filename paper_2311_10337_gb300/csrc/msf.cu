@@ -402,6 +402,26 @@ __global__ void k_gather_w(const FEdge *fe, const unsigned long long *idx, int64
     }
 }
 
+// When every w fits 32 bits the w (and graph) passes sort keys only: the
+// edge index rides in the low 32 bits, which the passes do not sort on, so
+// the order stays that of the previous sort among equal w (LSD stability)
+// and each pass moves 8 bytes an edge instead of 16.
+__global__ void k_gather_w32(const FEdge *fe, const unsigned long long *idx, int64_t n, unsigned long long *k) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long i = idx[x];
+        k[x] = ((unsigned long long)fe[i].w << 32) | i;
+    }
+}
+__global__ void k_gather_graph32(const FEdge *fe, const int32_t *egraph, const unsigned long long *kin, int64_t n,
+                                 unsigned long long *k) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long i = kin[x] & 0xffffffffull;
+        k[x] = ((unsigned long long)egraph[fe[i].u] << 32) | i;
+    }
+}
+
 // graph of each sorted forest edge, as a sort key (graph-major output)
 __global__ void k_gather_graph(const FEdge *fe, const int32_t *egraph, const unsigned long long *idx,
                                int64_t n, unsigned long long *k, unsigned long long *val) {
@@ -428,11 +448,11 @@ __global__ void k_graph_offsets(const int32_t *u, const int32_t *egraph, int64_t
     }
 }
 
-__global__ void k_gather_msf(const unsigned long long *idx, int64_t n, const FEdge *fe, int32_t *u,
-                             int32_t *v, int32_t *ru, int32_t *rv, int64_t *w) {
+__global__ void k_gather_msf(const unsigned long long *idx, unsigned long long imask, int64_t n, const FEdge *fe,
+                             int32_t *u, int32_t *v, int32_t *ru, int32_t *rv, int64_t *w) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
-        const FEdge f = fe[idx[x]];
+        const FEdge f = fe[idx[x] & imask];
         u[x] = f.u;
         v[x] = f.v;
         ru[x] = f.ru;
@@ -564,6 +584,20 @@ dgec_status stage_msf(Ctx *c, const Problem &p, const Csr &g, const Skel &sk, Ms
     DG_TRY(radix_sort(c, RadixBuffers{K[cur], K[1 - cur], Vb[cur], Vb[1 - cur]}, m, 0, 2 * p.idbits,
                       s.radix, &in_b));
     if (in_b) cur = 1 - cur;
+    if (p.tbits <= 32) {
+        TK(c, "k_gather_w", k_gather_w32<<<gm, kBlock, 0, st>>>(s.fe, Vb[cur], m, K[1 - cur]));
+        cur = 1 - cur;
+        DG_TRY(radix_sort(c, RadixBuffers{K[cur], K[1 - cur], nullptr, nullptr}, m, 32,
+                          32 + (p.tbits > 0 ? p.tbits : 1), s.radix, &in_b));
+        if (in_b) cur = 1 - cur;
+        if (p.G > 1) {
+            TK(c, "k_gather_graph", k_gather_graph32<<<gm, kBlock, 0, st>>>(s.fe, p.egraph, K[cur], m, K[1 - cur]));
+            cur = 1 - cur;
+            DG_TRY(radix_sort(c, RadixBuffers{K[cur], K[1 - cur], nullptr, nullptr}, m, 32,
+                              32 + bits_for((uint64_t)(p.G - 1)), s.radix, &in_b));
+            if (in_b) cur = 1 - cur;
+        }
+    } else {
     TK(c, "k_gather_w", k_gather_w<<<gm, kBlock, 0, st>>>(s.fe, Vb[cur], m, K[1 - cur], Vb[1 - cur]));
     cur = 1 - cur;
     DG_TRY(radix_sort(c, RadixBuffers{K[cur], K[1 - cur], Vb[cur], Vb[1 - cur]}, m, 0,
@@ -577,9 +611,11 @@ dgec_status stage_msf(Ctx *c, const Problem &p, const Csr &g, const Skel &sk, Ms
                           bits_for((uint64_t)(p.G - 1)), s.radix, &in_b));
         if (in_b) cur = 1 - cur;
     }
-    unsigned long long *fin = Vb[cur];
-    TK(c, "k_gather_msf", k_gather_msf<<<gm, kBlock, 0, st>>>(fin, m, s.fe, o.u, o.v,
-                                                              o.ru, o.rv, o.w));
+    }
+    const bool low32 = p.tbits <= 32;  // the index is the sorted key's low word
+    const unsigned long long *fin = low32 ? K[cur] : Vb[cur];
+    TK(c, "k_gather_msf", k_gather_msf<<<gm, kBlock, 0, st>>>(fin, low32 ? 0xffffffffull : ~0ull, m, s.fe, o.u,
+                                                              o.v, o.ru, o.rv, o.w));
     TK(c, "k_graph_offsets", k_graph_offsets<<<grid_for(p.G + 1), kBlock, 0, st>>>(o.u, p.egraph, m, p.G, o.goff));
     return DGEC_OK;
 }
