@@ -276,10 +276,14 @@ dgec_status dgec_server_destroy(dgec_server *srv);
 /* Launch configuration of the calls made on ctx (no counterpart in the
  * paper; it changes speed, never results): threads per CTA of the kNN kernel
  * (64, 128 or 256; default 128), the number of CTAs of each grid-stride
- * streaming kernel (1 .. 2^20; default 65,536), and whether the kNN kernel
- * reads its windows from packed 64-bit list keys ((t - tmin) << 32 | id) and
- * sorts its candidates as packed keys (|dt| << 32 | id) (0 or 1, default 1;
- * used only when the time span fits 32 bits). The autotuner of
+ * streaming kernel (1 .. 2^20; default 65,536), and the form of the kNN
+ * kernel (knn_packed): 0 reads separate time and id arrays; 1 reads its
+ * windows from packed 64-bit list keys ((t - tmin) << 32 | id) and sorts its
+ * candidates as packed keys (|dt| << 32 | id), one edge a thread; 2 (the
+ * default) does the same in list order, one pass over the out-lists for the
+ * predecessor windows and one over the in-lists for the successor windows,
+ * with K keys an edge held in the workspace in between. Forms 1 and 2 apply
+ * only when the time span fits 32 bits (else form 0 runs). The autotuner of
  * the Python package picks them per GPU model and workload. Invalid values
  * give DGEC_ERR_INVALID_ARG and leave the configuration unchanged. */
 typedef struct {

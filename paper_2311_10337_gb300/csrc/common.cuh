@@ -46,7 +46,7 @@ struct StageTimer {
 struct Ctx {
     int device = 0;
     int knn_block = 128;           // launch configuration (dgec_set_launch_config)
-    int knn_packed = 1;
+    int knn_packed = 2;
     int64_t stream_ctas = 65536;
     int num_sms = 152;
     char msg[512] = {0};
@@ -266,6 +266,22 @@ __device__ __forceinline__ void warp_add_u128(unsigned active, bool has, int key
     if ((int)lane_id() == __ffs(peers) - 1) {
         unsigned __int128 tot = (unsigned __int128)s0 + ((unsigned __int128)s1 << 16) +
                                 ((unsigned __int128)s2 << 32) + ((unsigned __int128)s3 << 48);
+        atomic_add_u128(&hi[key], &lo[key], (unsigned long long)(tot >> 64), (unsigned long long)tot);
+    }
+}
+
+// The same for a 128-bit `val` below 2^96 (six 16-bit limbs).
+__device__ __forceinline__ void warp_add_u96(unsigned active, bool has, int key, unsigned __int128 val,
+                                             unsigned long long *hi, unsigned long long *lo) {
+    const unsigned peers = __match_any_sync(active, has ? key : -1);
+    if (!has) return;
+    unsigned s[6];
+#pragma unroll
+    for (int i = 0; i < 6; i++) s[i] = __reduce_add_sync(peers, (unsigned)(val >> (16 * i)) & 0xffffu);
+    if ((int)lane_id() == __ffs(peers) - 1) {
+        unsigned __int128 tot = 0;
+#pragma unroll
+        for (int i = 0; i < 6; i++) tot += (unsigned __int128)s[i] << (16 * i);
         atomic_add_u128(&hi[key], &lo[key], (unsigned long long)(tot >> 64), (unsigned long long)tot);
     }
 }

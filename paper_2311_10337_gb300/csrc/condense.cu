@@ -150,10 +150,14 @@ static dgec_status jump_to_fixed(Ctx *c, int64_t n, int64_t off, Sel sel, int32_
 }
 
 
-// collapsed parent of every leaf and kept merge; nbig counts big children
+// Collapsed parent of every leaf and kept merge. nbs[X - E] of a kept merge
+// or virtual root X sums (1 << 32) + size over its big children: the high
+// word counts them, the low word totals their sizes (below 2^31, as every
+// child count and size is), so the points that leave a big X's cluster at X
+// number size(X) minus the low word.
 __global__ void k_c_cpar(Gview gv, const int32_t *__restrict__ parent, const int32_t *__restrict__ up,
                          const int *__restrict__ isrep, const int64_t *__restrict__ size,
-                         int32_t *__restrict__ cpar, int *__restrict__ nbig) {
+                         int32_t *__restrict__ cpar, unsigned long long *__restrict__ nbs) {
     const int64_t E = gv.E;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < E + gv.n;
          x += (int64_t)gridDim.x * blockDim.x) {
@@ -161,7 +165,10 @@ __global__ void k_c_cpar(Gview gv, const int32_t *__restrict__ parent, const int
         int P = parent[x];
         int64_t cp = P < 0 ? gv.R0 + graph_of(gv, x) : E + up[P - E];
         cpar[x] = (int32_t)cp;
-        if (x >= E && size[x - E] >= gv.gM[graph_of(gv, x)]) atomicAdd(&nbig[cp], 1);
+        if (x >= E) {
+            const int64_t sz = size[x - E];
+            if (sz >= gv.gM[graph_of(gv, x)]) atomicAdd(&nbs[cp - E], (1ull << 32) | (unsigned long long)sz);
+        }
     }
 }
 
@@ -169,7 +176,7 @@ __global__ void k_c_cpar(Gview gv, const int32_t *__restrict__ parent, const int
 // parent's only big child, else it starts a cluster (link to itself);
 // virtual roots link to themselves.
 __global__ void k_c_link(Gview gv, const int *isrep, const int64_t *size, const int32_t *cpar,
-                         const int *nbig, int32_t *link) {
+                         const unsigned long long *nbs, int32_t *link) {
     const int64_t E = gv.E, n = gv.n;
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n + gv.G;
          s += (int64_t)gridDim.x * blockDim.x) {
@@ -179,14 +186,14 @@ __global__ void k_c_link(Gview gv, const int *isrep, const int64_t *size, const 
         }
         if (!isrep[s] || size[s] < gv.gM[graph_of(gv, E + s)]) continue;
         int64_t X = cpar[E + s];
-        link[E + s] = nbig[X] >= 2 ? (int32_t)(E + s) : (int32_t)X;
+        link[E + s] = (nbs[X - E] >> 32) >= 2 ? (int32_t)(E + s) : (int32_t)X;
     }
 }
 
 
 // cluster records, indexed by node id
 __global__ void k_c_clusters(Gview gv, const int *isrep, const int64_t *size, const int64_t *w,
-                             const int32_t *cpar, const int *nbig, const int32_t *link, int *isc,
+                             const int32_t *cpar, const unsigned long long *nbs, const int32_t *link, int *isc,
                              unsigned long long *cbirth, unsigned long long *cdeath,
                              int32_t *cparent) {
     const int64_t E = gv.E, n = gv.n;
@@ -196,7 +203,7 @@ __global__ void k_c_clusters(Gview gv, const int *isrep, const int64_t *size, co
         bool big = s >= n || (isrep[s] && size[s] >= gv.gM[graph_of(gv, X)]);
         if (!big) continue;
         int K = link[X];
-        if (nbig[X] >= 2) cdeath[K] = lam_node(X, gv, w);
+        if ((nbs[s] >> 32) >= 2) cdeath[K] = lam_node(X, gv, w);
         if (K == (int)X) {
             isc[X] = 1;
             if (X >= gv.R0) {
@@ -224,53 +231,69 @@ struct __align__(32) NodeRec {
     unsigned long long pad;
 };
 
+// The records, and the stability the points leaving at each node give its
+// cluster. Every point that leaves cluster K at the big node X does so at
+// lambda(X), so together they add nf(X) * (lambda(X) - birth(K)), with nf(X)
+// = size(X) minus the sizes of X's big children (the points under its small
+// children, which walk up to X): one exact 128-bit add per node, summed per
+// warp and cluster, instead of one per point.
 __global__ void k_c_nrec(Gview gv, const int *isrep, const int64_t *size, const int64_t *w,
                          const int32_t *cpar, const int32_t *link, const unsigned long long *cbirth,
-                         NodeRec *rec) {
-    const int64_t E = gv.E, n = gv.n;
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n + gv.G;
-         s += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t X = E + s;
-        NodeRec r;
-        r.pad = 0;
-        if (s >= n) {
-            r.cpar = (int32_t)X;
-            r.link = link[X];
-            r.lam = 0ull;
-            r.share = 0ull;  // a virtual root: lambda 0, birth 0
-        } else {
-            if (!isrep[s]) continue;  // never a collapsed parent
-            const bool big = size[s] >= gv.gM[graph_of(gv, X)];
-            r.cpar = cpar[X];
-            r.link = big ? link[X] : -1;
-            r.lam = lambda_of(w[s]);
-            r.share = big ? r.lam - cbirth[r.link] : 0ull;
+                         const unsigned long long *__restrict__ nbs, NodeRec *rec, unsigned long long *st_hi,
+                         unsigned long long *st_lo) {
+    const int64_t E = gv.E, n = gv.n, total = n + gv.G;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < total;
+         base += stride) {  // warp-uniform
+        const int64_t s = base + lane_id();
+        bool has = false;
+        int K = 0;
+        unsigned __int128 val = 0;
+        if (s < total) {
+            const int64_t X = E + s;
+            NodeRec r;
+            r.pad = 0;
+            bool write = true;
+            if (s >= n) {
+                r.cpar = (int32_t)X;
+                r.link = link[X];
+                r.lam = 0ull;
+                r.share = 0ull;  // a virtual root: lambda 0, birth 0
+            } else if (!isrep[s]) {
+                write = false;  // never a collapsed parent
+            } else {
+                const int64_t sz = size[s];
+                const bool big = sz >= gv.gM[graph_of(gv, X)];
+                r.cpar = cpar[X];
+                r.link = big ? link[X] : -1;
+                r.lam = lambda_of(w[s]);
+                r.share = big ? r.lam - cbirth[r.link] : 0ull;
+                if (big && r.share != 0ull) {
+                    const int64_t nf = sz - (int64_t)(nbs[s] & 0xffffffffull);
+                    if (nf > 0) {
+                        has = true;
+                        K = r.link;
+                        val = (unsigned __int128)(unsigned long long)nf * r.share;  // below 2^95
+                    }
+                }
+            }
+            if (write) rec[s] = r;
         }
-        rec[s] = r;
+        warp_add_u96(0xffffffffu, has, K, val, st_hi, st_lo);
     }
 }
 
-// where each point leaves: the lowest kept ancestor of size >= M; its
-// stability share is added per warp and cluster (points of one big cluster
-// often meet in a warp)
-__global__ void k_c_points(Gview gv, const int32_t *cpar, const NodeRec *rec, int32_t *fall_cluster,
-                           uint64_t *fall_lambda, unsigned long long *st_hi, unsigned long long *st_lo) {
+// where each point leaves: the lowest kept ancestor of size >= M (its
+// stability share is counted per node above)
+__global__ void k_c_points(Gview gv, const int32_t *__restrict__ cpar, const NodeRec *__restrict__ rec,
+                           int32_t *__restrict__ fall_cluster, uint64_t *__restrict__ fall_lambda) {
     const int64_t E = gv.E;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < E;
-         base += stride) {  // warp-uniform
-        const int64_t p = base + lane_id();
-        int K = 0;
-        unsigned long long add = 0;
-        if (p < E) {
-            NodeRec r = rec[cpar[p] - E];
-            for (int it = 0; it < kMaxWalk && r.link < 0; it++) r = rec[r.cpar - E];
-            K = r.link;
-            fall_cluster[p] = K;
-            fall_lambda[p] = r.lam;
-            add = r.share;  // 0 at a virtual root
-        }
-        warp_add_u128(0xffffffffu, add != 0, K, add, st_hi, st_lo);
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < E;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        NodeRec r = rec[cpar[p] - E];
+        for (int it = 0; it < kMaxWalk && r.link < 0; it++) r = rec[r.cpar - E];
+        fall_cluster[p] = r.link;
+        fall_lambda[p] = r.lam;
     }
 }
 
@@ -640,7 +663,7 @@ void plan_condensed(Arena &ws, const Problem &p, Condensed &o) {
 struct CScratch {
     int32_t *up, *cpar, *link, *cparent, *clist, *cidx, *par, *ucand, *nxt, *nxt2, *H, *J, *H2, *J2,
         *rank, *al1, *al2;
-    int *isrep, *nbig, *isc, *pending, *done, *state, *minmem, *flag;
+    int *isrep, *isc, *pending, *done, *state, *minmem, *flag;
     unsigned long long *cbirth, *cdeath, *st_hi, *st_lo, *acc_hi, *acc_lo, *csz, *cnt, *k1, *k2, *v1, *v2, *jflag;
     long long *cpos, *scan_tmp;
     int64_t *gstart;
@@ -653,7 +676,6 @@ static CScratch carve_condense(Arena &a, const Problem &p) {
     s.up = a.take<int32_t>(E);
     s.isrep = a.take<int>(E);
     s.cpar = a.take<int32_t>(N);
-    s.nbig = a.take<int>(N);
     s.link = a.take<int32_t>(N);
     s.isc = a.take<int>(N + 1);
     s.cbirth = a.take<unsigned long long>(N);
@@ -725,7 +747,9 @@ dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro 
     CScratch s = carve_condense(a, p);
     const int gN = grid_for(N, kBlock, kStreamCap), gE = grid_for(E, kBlock, kStreamCap),
               gn = grid_for(n + p.G, kBlock, kStreamCap);
-    CU_TRY(c, cudaMemsetAsync(s.nbig, 0, sizeof(int) * N, st));
+    // big-child counts and sizes of node ids E .. N: in cpos, unused until the cluster scan
+    unsigned long long *nbs = reinterpret_cast<unsigned long long *>(s.cpos);
+    CU_TRY(c, cudaMemsetAsync(nbs, 0, sizeof(unsigned long long) * (n + p.G), st));
     CU_TRY(c, cudaMemsetAsync(s.isc + E, 0, sizeof(int) * (n + p.G + 1), st));
     CU_TRY(c, cudaMemsetAsync(s.cdeath, 0, sizeof(unsigned long long) * N, st));
     CU_TRY(c, cudaMemsetAsync(s.st_hi, 0, sizeof(unsigned long long) * N, st));
@@ -734,16 +758,16 @@ dgec_status stage_condense(Ctx *c, const Problem &p, const Msf &m, const Dendro 
         TK(c, "k_c_up", k_c_up<<<gn, kBlock, 0, st>>>(E, n, d.parent, m.w, s.up, s.isrep));
         DG_TRY(jump_to_fixed(c, n, 0, SelAll{}, s.up, s.jflag));
     }
-    TK(c, "k_c_cpar", k_c_cpar<<<gN, kBlock, 0, st>>>(gv, d.parent, s.up, s.isrep, d.size, s.cpar, s.nbig));
-    TK(c, "k_c_link", k_c_link<<<gn, kBlock, 0, st>>>(gv, s.isrep, d.size, s.cpar, s.nbig, s.link));
+    TK(c, "k_c_cpar", k_c_cpar<<<gN, kBlock, 0, st>>>(gv, d.parent, s.up, s.isrep, d.size, s.cpar, nbs));
+    TK(c, "k_c_link", k_c_link<<<gn, kBlock, 0, st>>>(gv, s.isrep, d.size, s.cpar, nbs, s.link));
     DG_TRY(jump_to_fixed(c, n, E, SelBigRep{gv, s.isrep, d.size}, s.link, s.jflag));
-    TK(c, "k_c_clusters", k_c_clusters<<<gn, kBlock, 0, st>>>(gv, s.isrep, d.size, m.w, s.cpar, s.nbig, s.link,
+    TK(c, "k_c_clusters", k_c_clusters<<<gn, kBlock, 0, st>>>(gv, s.isrep, d.size, m.w, s.cpar, nbs, s.link,
                                                              s.isc, s.cbirth, s.cdeath, s.cparent));
     // the node records live in the EOM phase's Fa and Fc arrays (adjacent, not in use yet)
     NodeRec *nrec = reinterpret_cast<NodeRec *>(s.Fa);
-    TK(c, "k_c_nrec", k_c_nrec<<<gn, kBlock, 0, st>>>(gv, s.isrep, d.size, m.w, s.cpar, s.link, s.cbirth, nrec));
-    TK(c, "k_c_points", k_c_points<<<gE, kBlock, 0, st>>>(gv, s.cpar, nrec, o.fall_cluster, o.fall_lambda,
-                                                         s.st_hi, s.st_lo));
+    TK(c, "k_c_nrec", k_c_nrec<<<gn, kBlock, 0, st>>>(gv, s.isrep, d.size, m.w, s.cpar, s.link, s.cbirth, nbs,
+                                                     nrec, s.st_hi, s.st_lo));
+    TK(c, "k_c_points", k_c_points<<<gE, kBlock, 0, st>>>(gv, s.cpar, nrec, o.fall_cluster, o.fall_lambda));
     // cluster flags of node ids E .. N (the last one a zero sentinel)
     DG_TRY(exclusive_scan_i32(c, s.isc + E, s.cpos, n + p.G + 1, s.scan_tmp));
     int64_t ncl;

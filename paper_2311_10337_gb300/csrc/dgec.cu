@@ -436,8 +436,8 @@ dgec_status dgec_set_launch_config(dgec_ctx *x, const dgec_launch_config *cfg) {
         return set_err(&x->c, DGEC_ERR_INVALID_ARG, "knn_block must be 64, 128 or 256");
     if (cfg->stream_ctas < 1 || cfg->stream_ctas > (1 << 20))
         return set_err(&x->c, DGEC_ERR_INVALID_ARG, "stream_ctas must be in [1, 2^20]");
-    if (cfg->knn_packed != 0 && cfg->knn_packed != 1)
-        return set_err(&x->c, DGEC_ERR_INVALID_ARG, "knn_packed must be 0 or 1");
+    if (cfg->knn_packed < 0 || cfg->knn_packed > 2)
+        return set_err(&x->c, DGEC_ERR_INVALID_ARG, "knn_packed must be 0, 1 or 2");
     x->c.knn_block = cfg->knn_block;
     x->c.stream_ctas = cfg->stream_ctas;
     x->c.knn_packed = cfg->knn_packed;

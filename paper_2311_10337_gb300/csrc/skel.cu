@@ -347,6 +347,141 @@ __global__ void __launch_bounds__(256, K <= 8 ? 3 : 1) k_knn32(const int64_t *t,
     }
 }
 
+// The same candidates and selection in list order, as two passes that read
+// their windows nearly in sequence. An edge e = (i, j, t) has its
+// predecessors in i's in-list, before e's place among i's out-items, and its
+// successors in j's out-list, after e's place among j's in-items. Walking
+// the out-lists slot by slot, consecutive slots of one vertex read
+// overlapping predecessor windows; walking the in-lists slot by slot, the
+// same holds for the successor windows. So:
+//   pass 1 (out-list slots): e's K predecessor keys, stored as one 8K-byte
+//          run at e's in-list slot (one scattered 4-byte read of that slot
+//          and whole-sector scattered writes; no load waits on another);
+//   pass 2 (in-list slots): e's K successor keys, its predecessor keys read
+//          in sequence from its own slot, the 2K-candidate sort and the row.
+// The per-edge form above reads both windows at scattered places, several
+// sectors each, and its warps wait on them.
+template <int K>
+__global__ void __launch_bounds__(256) k_knn_pred(int64_t E, const unsigned long long *__restrict__ out_key,
+                                                  const int2 *__restrict__ out_vb,
+                                                  const int64_t *__restrict__ in_off,
+                                                  const unsigned long long *__restrict__ in_key,
+                                                  const int32_t *__restrict__ in_gs,
+                                                  const int32_t *__restrict__ pos_in,
+                                                  ulonglong2 *__restrict__ half) {
+    constexpr unsigned long long kNone = 0xFFFFFFFFFFFFFFFFull;
+    constexpr unsigned long long kLo = 0xFFFFFFFFull;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < E;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long q = out_key[x];
+        const int2 vb = out_vb[x];
+        const int32_t y = pos_in[(int64_t)(q & kLo)];  // e's in-list slot: where pass 2 reads its keys
+        const unsigned long long te = q >> 32;
+        const int64_t ib = in_off[vb.x], b = vb.y;
+        unsigned long long c[K];
+        const int64_t lo = b - K > 0 ? b - K : 0;
+        int64_t g0 = lo, take_grp = 0;
+        const unsigned long long tlo = lo < b ? in_key[ib + lo] >> 32 : 0;
+        const bool cross = lo > 0 && tlo == (in_key[ib + lo - 1] >> 32);
+        if (cross) {  // a tie group crossing the window's start gives its smallest ids
+            g0 = (int64_t)in_gs[ib + lo] - ib;
+            int64_t g1 = lo;
+            while (g1 < b && (in_key[ib + g1] >> 32) == tlo) g1++;  // at most K steps
+            take_grp = g1 - lo;
+        }
+#pragma unroll
+        for (int u = 0; u < K; u++) {
+            const int64_t idx = u < take_grp ? g0 + u : lo + u;
+            if (idx < b) {
+                const unsigned long long kk = in_key[ib + idx];
+                c[u] = ((te - (kk >> 32)) << 32) | (kk & kLo);
+            } else {
+                c[u] = kNone;
+            }
+        }
+        ulonglong2 *dstp = half + (int64_t)y * (K / 2);
+#pragma unroll
+        for (int u = 0; u < K / 2; u++) dstp[u] = make_ulonglong2(c[2 * u], c[2 * u + 1]);
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(256, K <= 8 ? 3 : 1) k_knn_succ(
+    int64_t E, const unsigned long long *__restrict__ in_key, const int2 *__restrict__ in_va,
+    const int64_t *__restrict__ out_off, const unsigned long long *__restrict__ out_key,
+    const ulonglong2 *__restrict__ half, int G, const int32_t *egraph, const int64_t *eoff,
+    const int32_t *gk, const int64_t *knn_off, int64_t dmax, int32_t *knn, int64_t *core) {
+    constexpr int N = 2 * K;
+    constexpr unsigned long long kNone = 0xFFFFFFFFFFFFFFFFull;
+    constexpr unsigned long long kLo = 0xFFFFFFFFull;
+    for (int64_t y = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; y < E;
+         y += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long p = in_key[y];
+        const int2 va = in_va[y];
+        const unsigned long long te = p >> 32;
+        const int64_t e = (int64_t)(p & kLo);
+        const int64_t a0 = out_off[va.x] + va.y, a1 = out_off[va.x + 1];  // successor window [a0, a1)
+        unsigned long long c[N];
+        const ulonglong2 *srcp = half + y * (K / 2);
+#pragma unroll
+        for (int u = 0; u < K / 2; u++) {
+            const ulonglong2 h = srcp[u];
+            c[2 * u] = h.x;
+            c[2 * u + 1] = h.y;
+        }
+#pragma unroll
+        for (int u = 0; u < K; u++) {
+            const int64_t idx = a0 + u;
+            if (idx < a1) {
+                const unsigned long long kk = out_key[idx];
+                c[K + u] = (((kk >> 32) - te) << 32) | (kk & kLo);
+            } else {
+                c[K + u] = kNone;
+            }
+        }
+        const int gr = G > 1 ? egraph[e] : 0;
+        const int k = gk[gr];
+        const int64_t e0 = eoff[gr];
+        int32_t *row = knn + knn_off[gr] + (e - e0) * k;
+#pragma unroll
+        for (int size = 2; size <= N; size <<= 1) {
+#pragma unroll
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+#pragma unroll
+                for (int lo2 = 0; lo2 < N; lo2++) {
+                    const int hi2 = lo2 ^ stride;
+                    if (hi2 > lo2) {
+                        const bool up = (lo2 & size) == 0;
+                        const unsigned long long x0 = c[lo2], x1 = c[hi2];
+                        const bool sw = up ? x1 < x0 : x0 < x1;
+                        c[lo2] = sw ? x1 : x0;
+                        c[hi2] = sw ? x0 : x1;
+                    }
+                }
+            }
+        }
+        int cnt = 0;
+        long long last_w = LLONG_MAX;
+        unsigned prev = 0xFFFFFFFFu;
+#pragma unroll
+        for (int u = 0; u < N; u++) {
+            const unsigned id = (unsigned)c[u];
+            const long long w = (long long)(c[u] >> 32);
+            if (c[u] != kNone && id != prev && cnt < k && w <= dmax) {
+                row[cnt] = (int32_t)((int64_t)id - e0);
+                last_w = w;
+                cnt++;
+            }
+            prev = id;
+        }
+        for (int u = cnt; u < k; u++) row[u] = -1;
+        core[e] = cnt == k ? last_w : LLONG_MAX;
+    }
+}
+
+// K of the kNN kernels: the batch's largest k rounded up to 4, 8 or 16
+static int knn_kpad(int k) { return k <= 4 ? 4 : (k <= 8 ? 8 : 16); }
+
 void plan_skel(Arena &ws, const Problem &p, Skel &o) {
     o.u = ws.take<int32_t>(2 * p.E);
     o.v = ws.take<int32_t>(2 * p.E);
@@ -360,12 +495,14 @@ void plan_skel(Arena &ws, const Problem &p, Skel &o) {
 struct SkScratch {
     LinkRec *rec;
     long long *pos, *scan_tmp;
+    ulonglong2 *half;  // list-order kNN: K predecessor keys per in-list slot
 };
 static SkScratch carve_skel(Arena &a, const Problem &p) {
     SkScratch s;
     s.rec = a.take<LinkRec>(2 * p.E);
     s.pos = a.take<long long>(2 * p.E + 1);
     s.scan_tmp = a.take<long long>(scan_scratch_elems(2 * p.E + 1));
+    s.half = (p.knn && p.tbits <= 32) ? a.take<ulonglong2>(p.E * (int64_t)(knn_kpad(p.k) / 2)) : nullptr;
     return s;
 }
 size_t skel_scratch_bytes(const Problem &p) {
@@ -389,7 +526,28 @@ dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void
 #define KNN32_ARGS                                                                                 \
     g.it, p.tmin, g.orig_of, E, g.out_key, g.in_key, g.in_gs, g.outrk, g.inrk, p.G, p.egraph, p.eoff, p.gk, \
         p.knn_off, p.dmax, o.knn, o.core
-    if (p.knn && c->knn_packed && p.tbits <= 32) {  // every |dt| fits 32 bits: packed list and candidate keys
+    if (p.knn && c->knn_packed == 2 && p.tbits <= 32) {  // packed keys, in list order (two passes)
+        const int gl = grid_for(E, kb, 1 << 20);
+#define KNN_PRED_ARGS E, g.out_key, g.out_vb, g.in_off, g.in_key, g.in_gs, g.pos_in, s.half
+#define KNN_SUCC_ARGS \
+    E, g.in_key, g.in_va, g.out_off, g.out_key, s.half, p.G, p.egraph, p.eoff, p.gk, p.knn_off, p.dmax, o.knn, o.core
+        switch (knn_kpad(p.k)) {
+        case 4:
+            TK(c, "k_knn_pred", k_knn_pred<4><<<gl, kb, 0, st>>>(KNN_PRED_ARGS));
+            TK(c, "k_knn", k_knn_succ<4><<<gl, kb, 0, st>>>(KNN_SUCC_ARGS));
+            break;
+        case 8:
+            TK(c, "k_knn_pred", k_knn_pred<8><<<gl, kb, 0, st>>>(KNN_PRED_ARGS));
+            TK(c, "k_knn", k_knn_succ<8><<<gl, kb, 0, st>>>(KNN_SUCC_ARGS));
+            break;
+        default:
+            TK(c, "k_knn_pred", k_knn_pred<16><<<gl, kb, 0, st>>>(KNN_PRED_ARGS));
+            TK(c, "k_knn", k_knn_succ<16><<<gl, kb, 0, st>>>(KNN_SUCC_ARGS));
+            break;
+        }
+#undef KNN_PRED_ARGS
+#undef KNN_SUCC_ARGS
+    } else if (p.knn && c->knn_packed && p.tbits <= 32) {  // every |dt| fits 32 bits: packed list and candidate keys
         if (p.k <= 4) TK(c, "k_knn", k_knn32<4><<<grid, kb, 0, st>>>(KNN32_ARGS));
         else if (p.k <= 8) TK(c, "k_knn", k_knn32<8><<<grid, kb, 0, st>>>(KNN32_ARGS));
         else TK(c, "k_knn", k_knn32<16><<<grid, kb, 0, st>>>(KNN32_ARGS));

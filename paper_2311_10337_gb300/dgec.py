@@ -326,10 +326,11 @@ class Context:
             i += 1
         return out
 
-    def set_launch_config(self, knn_block: int, stream_ctas: int, knn_packed: int = 1):
+    def set_launch_config(self, knn_block: int, stream_ctas: int, knn_packed: int = 2):
         """Threads per CTA of the kNN kernel, CTAs of the grid-stride
-        streaming kernels and the kNN form (packed 64-bit list and candidate
-        keys or not) for the calls on this context (speed only)."""
+        streaming kernels and the kNN form (0 separate time and id arrays,
+        1 packed 64-bit keys one edge a thread, 2 packed keys in list order)
+        for the calls on this context (speed only)."""
         cfg = LaunchConfig(knn_block, stream_ctas, knn_packed)
         self._check(self.L.dgec_set_launch_config(self.h, ctypes.byref(cfg)))
 

@@ -79,7 +79,7 @@ def tune(ctx, run, signature: str, steps: int = 2, use_cache: bool = True) -> di
     cfg = list(ctx.launch_config())
     best = _time_ms(run, steps)  # the starting configuration
     trials = [{"knn_block": cfg[0], "stream_ctas": cfg[1], "knn_packed": cfg[2], "ms": round(best, 3)}]
-    for dim, cands in ((1, stream_cta_candidates(sms)), (0, KNN_BLOCKS), (2, (0, 1))):
+    for dim, cands in ((1, stream_cta_candidates(sms)), (0, KNN_BLOCKS), (2, (0, 1, 2))):
         best_v = cfg[dim]
         for cand in cands:
             if cand == cfg[dim]:

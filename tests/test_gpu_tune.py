@@ -19,7 +19,7 @@ def test_every_launch_config_gives_identical_outputs():
     try:
         for kb in tune.KNN_BLOCKS:
             for sc in (152, 2432, 65536):
-                for packed in (0, 1):
+                for packed in (0, 1, 2):
                     c.set_launch_config(kb, sc, packed)
                     got = run_gpu(w.src, w.dst, w.t, w.n_vertices, w.k, w.min_cluster_size)
                     for key in ref:
@@ -53,7 +53,7 @@ def test_tuner_picks_a_candidate_and_caches_it(tmp_path, monkeypatch):
         sms = torch.cuda.get_device_properties(0).multi_processor_count
         assert not first["cached"] and first["knn_block"] in tune.KNN_BLOCKS
         assert first["stream_ctas"] in tune.stream_cta_candidates(sms)
-        assert first["knn_packed"] in (0, 1)
+        assert first["knn_packed"] in (0, 1, 2)
         chosen = (first["knn_block"], first["stream_ctas"], first["knn_packed"])
         assert c.launch_config() == chosen
         c.set_launch_config(*default)
