@@ -63,11 +63,13 @@ def knn_bytes_per_edge(k: int) -> int:
     return 24 + 4 * k + 8
 
 
-# DRAM bytes (read + write) per edge of the kNN kernel (packed form, k = 8)
-# from one ncu capture on the hub graph at scale 0.02 (4M edges: 312.6 MB read
-# + 212.7 MB written), scaled to a launch by the edges it processes
-# (profiles/k_knn32_hub_small.md). Set back to None when the kernel changes.
-KNN_TRAFFIC_BYTES_PER_EDGE_K8 = (312_571_904 + 212_684_800) / 4_000_000
+# DRAM bytes (read + write) per edge of the kNN step at k = 8, by kNN form
+# (the launch configuration's knn_packed), each from one ncu capture on the
+# hub graph at scale 0.02 (4M edges), scaled to a full step by the edges it
+# processes. Form 1, the per-edge packed kernel: 312.6 MB read + 212.7 MB
+# written (profiles/k_knn32_hub_small.md). A form without a capture of its
+# current kernels, or whose kernels changed since, maps to None.
+KNN_TRAFFIC_BYTES_PER_EDGE_K8 = {1: (312_571_904 + 212_684_800) / 4_000_000, 2: None}
 
 CPU_SAMPLE_MINUTES = {"hub": 25.0, "mid": 150.0, "tiny": 1e9}
 
@@ -625,7 +627,7 @@ def run(args, rank, world, local, futs):
         ctx.run(src, dst, tt, V, k, M)
         bd = ctx.kernel_timing()
         ctx.set_kernel_timing(0)
-    ctx.set_kernel_timing(1, args.roofline_kernel)
+    ctx.set_kernel_timing(3, args.roofline_kernel)  # every kernel of the step: k_knn, or k_knn_pred + k_knn
     clocks = Clocks(local)
     clocks.start()
     if world > 1:
@@ -640,7 +642,9 @@ def run(args, rank, world, local, futs):
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / args.steps
     stages = ctx.stage_timing()           # the last timed step, from the library's stage events
-    dom = ctx.kernel_timing().get(args.roofline_kernel, (0.0, 0))
+    dom_by = ctx.kernel_timing()
+    dom = (sum(v[0] for v in dom_by.values()), sum(v[1] for v in dom_by.values()))
+    knn_form = ctx.launch_config()[2]
     ctx.set_kernel_timing(0)
     ms = max_over_ranks(ms, world, "cuda")
     if world > 1:
@@ -677,16 +681,18 @@ def run(args, rank, world, local, futs):
     if rank == 0:
         dom_ms, dom_n = dom
         kb = knn_bytes_per_edge(k)
-        avg = dom_ms / dom_n if dom_n else None
+        # one unit = the kNN step of one pass (one launch, or the two passes of the list-order form)
+        avg = dom_ms / args.steps if dom_n else None
         achieved = (kb * E) / (avg / 1000.0) / 1e9 if avg else None
-        traffic = (KNN_TRAFFIC_BYTES_PER_EDGE_K8 * E
-                   if args.roofline_kernel == "k_knn" and k == 8 and KNN_TRAFFIC_BYTES_PER_EDGE_K8 else None)
+        per_edge = KNN_TRAFFIC_BYTES_PER_EDGE_K8.get(knn_form)
+        traffic = (per_edge * E if args.roofline_kernel == "k_knn" and k == 8 and per_edge else None)
         share = None
         top = None
         if bd:
             tot = sum(v[0] for v in bd.values())
-            if args.roofline_kernel in bd and tot > 0:
-                share = bd[args.roofline_kernel][0] / tot
+            mine = sum(v[0] for n_, v in bd.items() if n_.startswith(args.roofline_kernel))
+            if mine > 0 and tot > 0:
+                share = mine / tot
             top = [[n, round(v[0], 3), v[1], round(v[0] / tot, 4)] for n, v in
                    sorted(bd.items(), key=lambda kv: -kv[1][0])[:12]]
         roof = {"bound": "hbm", "kernel": args.roofline_kernel, "achieved": achieved, "peak": peak,
@@ -696,6 +702,7 @@ def run(args, rank, world, local, futs):
                 "traffic_over_algorithmic": (traffic / (kb * E)) if traffic else None,
                 "algorithmic_bytes_per_edge": kb, "algorithmic_bytes_per_launch": kb * E,
                 "avg_launch_ms": avg, "share_of_step": share,
+                "kernels": sorted(dom_by), "launches_per_step": dom_n / args.steps, "knn_form": knn_form,
                 "stages": stage_report(stages, E, k, peak),
                 "pipeline": {"bytes_per_edge": pipeline_bytes_per_edge(k),
                              "achieved": pipeline_bytes_per_edge(k) * E / (ms / 1000.0) / 1e9,

@@ -308,7 +308,10 @@ int64_t dgec_last_launch_count(const dgec_ctx *ctx);
 
 /* Measurement aid: time kernels with CUDA events recorded on the run's
  * stream around each launch. mode 0 = off, 1 = only launches of the kernel
- * called `name` (e.g. "k_knn"), 2 = every launch. Resets the totals. */
+ * called `name` (e.g. "k_knn"), 2 = every launch, 3 = launches of every
+ * kernel whose name starts with `name` (e.g. "k_knn": the kNN step in any
+ * form, one launch or the two passes "k_knn_pred" and "k_knn"). Resets the
+ * totals. */
 dgec_status dgec_set_kernel_timing(dgec_ctx *ctx, int mode, const char *name);
 /* Totals since the last reset for the i-th kernel name seen (0-based):
  * its name (static string), summed milliseconds and launch count.

@@ -28,6 +28,7 @@ int kt_begin(Ctx *c, const char *name) {
     KernelTimer *k = c->kt;
     if (!k || k->mode == 0) return -1;
     if (k->mode == 1 && strcmp(k->only, name) != 0) return -1;
+    if (k->mode == 3 && strncmp(k->only, name, strlen(k->only)) != 0) return -1;
     if (k->used >= kMaxTimed) return -1;
     if (!k->ev) {
         k->ev = (cudaEvent_t *)calloc(2 * kMaxTimed, sizeof(cudaEvent_t));

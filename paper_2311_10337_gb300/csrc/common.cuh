@@ -22,7 +22,7 @@ constexpr int kMaxWalk = 1 << 26;
 constexpr int kMaxTimed = 1 << 14;
 constexpr int kMaxNames = 128;
 struct KernelTimer {
-    int mode = 0;              // 0 off, 1 only `only`, 2 all
+    int mode = 0;              // 0 off, 1 only `only`, 2 all, 3 names starting with `only`
     char only[64] = {0};
     cudaEvent_t *ev = nullptr;  // 2 * kMaxTimed events, created on first use
     int used = 0;

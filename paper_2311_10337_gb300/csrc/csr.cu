@@ -263,7 +263,7 @@ __global__ void k_munpack(const unsigned long long *key, const unsigned long lon
             out_r[slot] = r;
             pos_out[e] = (int32_t)slot;
             // b: in-edges of v with t <= t_r; v's in-list starts at moff[v] - out_off[v]
-            outrk[r] = make_int4((int32_t)slot, (int32_t)(seg - obv), (int32_t)(moff[v] - out_off[v]), 0);
+            if (outrk) outrk[r] = make_int4((int32_t)slot, (int32_t)(seg - obv), (int32_t)(moff[v] - out_off[v]), 0);
             out_vb[slot] = make_int2((int32_t)v, (int32_t)(seg - obv));
             if (val) out_key[slot] = pk;
         } else {
@@ -273,7 +273,7 @@ __global__ void k_munpack(const unsigned long long *key, const unsigned long lon
             in_r[slot] = r;
             pos_in[e] = (int32_t)slot;
             in_head[slot] = (seg - obv) == 0;    // first entry of v's in-list
-            inrk[r] = make_int2((int32_t)ob, (int32_t)out_off[v + 1]);  // ob = out_off[v] + a
+            if (inrk) inrk[r] = make_int2((int32_t)ob, (int32_t)out_off[v + 1]);  // ob = out_off[v] + a
             in_va[slot] = make_int2((int32_t)v, (int32_t)obv);
             if (val) in_key[slot] = pk;
         }
@@ -583,6 +583,8 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
     uint64_t span = E > 0 ? (uint64_t)f[3] - (uint64_t)f[2] : 0;
     p.idbits = bits_for((uint64_t)(E > 1 ? E - 1 : 1));
     p.tbits = bits_for(span);
+    // forms 1 and 2 read packed keys, written only when every t - tmin fits 32 bits
+    p.knn_form = p.tbits > 32 ? 0 : c->knn_packed;
     if (E == 0) {
         CU_TRY(c, cudaMemsetAsync(o.out_off, 0, sizeof(int64_t) * (V + 1), st));
         CU_TRY(c, cudaMemsetAsync(o.in_off, 0, sizeof(int64_t) * (V + 1), st));
@@ -628,10 +630,12 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
                                                                  2 * E + 1, SumI64{}, 0ll, false, s.scan_tmp)));
     TK(c, "k_moff_split", k_moff_split<<<grid_for(V + 1, kBlock, kStreamCap), kBlock, 0, st>>>(s.moff, s.oidx, V, o.out_off,
                                                                                         o.in_off));
+    // the per-edge kNN forms read the window places by r; the list-order form and the skeleton do not
+    const bool rk = p.knn && p.knn_form != 2;
     TK(c, "k_munpack", k_munpack<<<grid_for(2 * E, kBlock, kStreamCap), kBlock, 0, st>>>(
                            key, mval, p.tmin, 2 * E, cb, s.moff, s.oidx, o.out_off, s.te, o.out_t, o.out_id,
-                           o.out_r, o.outrk,
-                           o.pos_out, o.in_t, o.in_id, o.in_r, o.pos_in, s.in_head, o.inrk, o.in_va,
+                           o.out_r, rk ? o.outrk : nullptr,
+                           o.pos_out, o.in_t, o.in_id, o.in_r, o.pos_in, s.in_head, rk ? o.inrk : nullptr, o.in_va,
                            o.out_vb, o.out_key, o.in_key));
     // start of every in-list entry's tie group (the kNN window takes a crossing group's smallest ids)
     DG_TRY((device_scan<long long, MaxI64, LoadInGroupHead, StoreI32>(c, LoadInGroupHead{o.in_t, s.in_head},

@@ -408,11 +408,11 @@ const char *dgec_status_string(dgec_status s) {
 int64_t dgec_last_launch_count(const dgec_ctx *x) { return x ? x->c.launches : -1; }
 
 dgec_status dgec_set_kernel_timing(dgec_ctx *x, int mode, const char *name) {
-    if (!x || !x->c.kt || mode < 0 || mode > 2 || (mode == 1 && !name))
+    if (!x || !x->c.kt || mode < 0 || mode > 3 || ((mode == 1 || mode == 3) && !name))
         return DGEC_ERR_INVALID_ARG;
     KernelTimer *k = x->c.kt;
     k->mode = mode;
-    snprintf(k->only, sizeof(k->only), "%s", mode == 1 ? name : "");
+    snprintf(k->only, sizeof(k->only), "%s", (mode == 1 || mode == 3) ? name : "");
     k->used = 0;
     k->n_names = 0;
     return DGEC_OK;

@@ -21,25 +21,25 @@
 
 namespace dgec {
 
-// b[e] = outrk[e].y = #in-edges of src[e] with t <= t_e; inrk[e].x - out_off[dst[e]]
-// = #out-edges of dst[e] with t < t_e (both from stage A's merged lists).
 // All node ids below are internal ids r (see the stage A notes).
 struct SkView {
     const int32_t *src, *dst;  // isrc, idst (by r)
     const int64_t *out_off, *in_off;
-    const int32_t *out_id, *in_id;  // out_r, in_r
-    const int4 *outrk;              // by r: (out-list slot, b, first in-list slot of src)
-    const int2 *inrk;               // by r: (first out-slot of dst not before t_r, end of dst's out-list)
+    const int32_t *out_id, *in_id;    // out_r, in_r
+    const int32_t *orig_of;           // r -> original id
+    const int32_t *pos_out, *pos_in;  // original id -> list slot
+    const int2 *in_va, *out_vb;       // by slot: (vertex, a) of in-entries, (vertex, b) of out-entries
 };
 
-// Does Alg. 2 at vertex x emit the pair (in-edge pin, out-edge qout)?
+// Does Alg. 2 at vertex x emit the pair (in-edge pin, out-edge qout)? Only
+// asked for a reciprocal pair at equal times, so its scattered reads are rare.
 __device__ __forceinline__ bool emitted_at(const SkView &g, int x, int pin, int qout) {
     const int64_t ob = g.out_off[x];
-    const int2 ia = g.inrk[pin];  // pin is an in-edge of x
-    if (ia.x < ia.y && g.out_id[ia.x] == qout) return true;  // type 1
-    int64_t sq = g.outrk[qout].x;
-    if (sq > ob) {                                          // type 2
-        int b = g.outrk[g.out_id[sq - 1]].y;
+    const int64_t a0 = ob + g.in_va[g.pos_in[g.orig_of[pin]]].y;  // pin's first out-edge of x not before it
+    if (a0 < g.out_off[x + 1] && g.out_id[a0] == qout) return true;  // type 1
+    const int64_t sq = g.pos_out[g.orig_of[qout]];
+    if (sq > ob) {  // type 2
+        const int b = g.out_vb[sq - 1].y;
         if (b >= 1 && g.in_id[g.in_off[x] + b - 1] == pin) return true;
     }
     return false;
@@ -502,7 +502,7 @@ static SkScratch carve_skel(Arena &a, const Problem &p) {
     s.rec = a.take<LinkRec>(2 * p.E);
     s.pos = a.take<long long>(2 * p.E + 1);
     s.scan_tmp = a.take<long long>(scan_scratch_elems(2 * p.E + 1));
-    s.half = (p.knn && p.tbits <= 32) ? a.take<ulonglong2>(p.E * (int64_t)(knn_kpad(p.k) / 2)) : nullptr;
+    s.half = p.knn ? a.take<ulonglong2>(p.E * (int64_t)(knn_kpad(p.k) / 2)) : nullptr;
     return s;
 }
 size_t skel_scratch_bytes(const Problem &p) {
@@ -526,7 +526,7 @@ dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void
 #define KNN32_ARGS                                                                                 \
     g.it, p.tmin, g.orig_of, E, g.out_key, g.in_key, g.in_gs, g.outrk, g.inrk, p.G, p.egraph, p.eoff, p.gk, \
         p.knn_off, p.dmax, o.knn, o.core
-    if (p.knn && c->knn_packed == 2 && p.tbits <= 32) {  // packed keys, in list order (two passes)
+    if (p.knn && p.knn_form == 2) {  // packed keys, in list order (two passes)
         const int gl = grid_for(E, kb, 1 << 20);
 #define KNN_PRED_ARGS E, g.out_key, g.out_vb, g.in_off, g.in_key, g.in_gs, g.pos_in, s.half
 #define KNN_SUCC_ARGS \
@@ -547,7 +547,7 @@ dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void
         }
 #undef KNN_PRED_ARGS
 #undef KNN_SUCC_ARGS
-    } else if (p.knn && c->knn_packed && p.tbits <= 32) {  // every |dt| fits 32 bits: packed list and candidate keys
+    } else if (p.knn && p.knn_form == 1) {  // every |dt| fits 32 bits: packed list and candidate keys
         if (p.k <= 4) TK(c, "k_knn", k_knn32<4><<<grid, kb, 0, st>>>(KNN32_ARGS));
         else if (p.k <= 8) TK(c, "k_knn", k_knn32<8><<<grid, kb, 0, st>>>(KNN32_ARGS));
         else TK(c, "k_knn", k_knn32<16><<<grid, kb, 0, st>>>(KNN32_ARGS));
@@ -558,7 +558,7 @@ dgec_status stage_skeleton(Ctx *c, const Problem &p, const Csr &g, Skel &o, void
     }
 #undef KNN_ARGS
 #undef KNN32_ARGS
-    SkView v{g.isrc, g.idst, g.out_off, g.in_off, g.out_r, g.in_r, g.outrk, g.inrk};
+    SkView v{g.isrc, g.idst, g.out_off, g.in_off, g.out_r, g.in_r, g.orig_of, g.pos_out, g.pos_in, g.in_va, g.out_vb};
     TK(c, "k_links_in", k_links_in<<<grid_for(E, kBlock, kStreamCap), kBlock, 0, st>>>(
                             v, g.in_va, g.out_t, g.in_t, E, p.dmax, s.rec));
     TK(c, "k_links_out", k_links_out<<<grid_for(E, kBlock, kStreamCap), kBlock, 0, st>>>(

@@ -26,6 +26,7 @@ struct Problem {
     const int64_t *knn_off = nullptr; // [G+1] first kNN slot of each graph
     int32_t *egraph = nullptr;        // [E] graph of each edge (built in stage A)
     bool knn = true;                  // stage B also writes the kNN lists
+    int knn_form = 0;                 // kNN kernel form, fixed in stage A (knn_packed, when the span allows)
     int64_t dmax = INT64_MAX;         // time cutoff (Sec. 4.3): only links with w <= dmax
     int64_t links_cap = -1;           // skeleton capacity; -1 = 2E (graphs: <= 2 links per edge)
     bool mrd = false;                 // cluster the mutual-reachability graph (stage M)

@@ -307,7 +307,8 @@ class Context:
         return int(self.L.dgec_last_launch_count(self.h))
 
     def set_kernel_timing(self, mode: int, name: str | None = None):
-        """0 off, 1 only kernel `name`, 2 every launch (resets totals)."""
+        """0 off, 1 only kernel `name`, 2 every launch, 3 kernels whose name
+        starts with `name` (resets totals)."""
         self._check(self.L.dgec_set_kernel_timing(self.h, mode, name.encode() if name else None))
 
     def kernel_timing(self) -> dict:

@@ -32,7 +32,7 @@ def test_bad_launch_config_is_rejected():
     from paper_2311_10337_gb300 import dgec
     c = ctx()
     default = c.launch_config()
-    for kb, sc, pk in ((96, 1000, 0), (128, 0, 0), (128, (1 << 20) + 1, 0), (128, 1000, 2)):
+    for kb, sc, pk in ((96, 1000, 0), (128, 0, 0), (128, (1 << 20) + 1, 0), (128, 1000, 3), (128, 1000, -1)):
         with pytest.raises(dgec.DgecError) as ei:
             c.set_launch_config(kb, sc, pk)
         assert ei.value.status == 1
