@@ -67,9 +67,14 @@ def knn_bytes_per_edge(k: int) -> int:
 # (the launch configuration's knn_packed), each from one ncu capture on the
 # hub graph at scale 0.02 (4M edges), scaled to a full step by the edges it
 # processes. Form 1, the per-edge packed kernel: 312.6 MB read + 212.7 MB
-# written (profiles/k_knn32_hub_small.md). A form without a capture of its
+# written (profiles/k_knn32_hub_small.md). Form 2, the two list-order passes:
+# 139.0 + 427.7 MB read, 218.1 + 216.4 MB written
+# (profiles/k_knn_list_order_hub_small.md). A form without a capture of its
 # current kernels, or whose kernels changed since, maps to None.
-KNN_TRAFFIC_BYTES_PER_EDGE_K8 = {1: (312_571_904 + 212_684_800) / 4_000_000, 2: None}
+KNN_TRAFFIC_BYTES_PER_EDGE_K8 = {
+    1: (312_571_904 + 212_684_800) / 4_000_000,
+    2: (139_018_240 + 218_062_336 + 427_675_136 + 216_392_960) / 4_000_000,
+}
 
 CPU_SAMPLE_MINUTES = {"hub": 25.0, "mid": 150.0, "tiny": 1e9}
 
