@@ -141,7 +141,7 @@ __global__ void k_rank_init(const unsigned long long *ks, const unsigned long lo
         const int32_t e = (int32_t)(k & idmask);
         const int64_t tt = (int64_t)(k >> idbits) + tmin;
         orig_of[r] = e;
-        if (rank_of) rank_of[e] = (int32_t)r;
+        rank_of[e] = (int32_t)r;
         it[r] = tt;
         if (te) te[r] = TE{tt, e, 0};  // only when the merged sort cannot carry (t, id)
         isrc[r] = (int32_t)(sd & 0xffffffffull);
@@ -158,7 +158,7 @@ __global__ void k_rank_init_kv(const unsigned long long *ks, const unsigned long
          r += (int64_t)gridDim.x * blockDim.x) {
         int32_t e = (int32_t)vs[r];
         orig_of[r] = e;
-        if (rank_of) rank_of[e] = (int32_t)r;
+        rank_of[e] = (int32_t)r;
         it[r] = (int64_t)(long long)(ks[r] + (unsigned long long)tmin);
         if (te) te[r] = TE{it[r], e, 0};
         int32_t vo = G > 1 ? (int32_t)voff[egraph[e]] : 0;
@@ -599,7 +599,7 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
         DG_TRY(radix_sort(c, RadixBuffers{s.mk, s.mk2, s.mk + E, s.mk2 + E}, E, p.idbits, p.idbits + p.tbits,
                           s.radix, &in_b));
         TK(c, "k_rank_init", k_rank_init<<<gEE, kBlock, 0, st>>>(in_b ? s.mk2 : s.mk, in_b ? s.mk2 + E : s.mk + E, E,
-                                                                p.tmin, p.idbits, o.orig_of, p.need_rank_of ? o.rank_of : nullptr, o.isrc, o.idst,
+                                                                p.tmin, p.idbits, o.orig_of, o.rank_of, o.isrc, o.idst,
                                                                 o.it, p.tbits <= 32 ? nullptr : s.te));
     } else {
         // wide span: the time is the whole key, the id its value (second halves of the item buffers)
@@ -608,7 +608,7 @@ dgec_status stage_csr(Ctx *c, Problem &p, Csr &o, void *scratch) {
         DG_TRY(radix_sort(c, RadixBuffers{s.mk, s.mk2, s.mk + E, s.mk2 + E}, E, 0, p.tbits, s.radix, &in_b));
         TK(c, "k_rank_init_kv", k_rank_init_kv<<<gEE, kBlock, 0, st>>>(
                                     in_b ? s.mk2 : s.mk, in_b ? s.mk2 + E : s.mk + E, E, p.tmin, p.src, p.dst,
-                                    p.egraph, p.voff, p.G, o.orig_of, p.need_rank_of ? o.rank_of : nullptr, o.isrc, o.idst, o.it, s.te));
+                                    p.egraph, p.voff, p.G, o.orig_of, o.rank_of, o.isrc, o.idst, o.it, s.te));
     }
     // time groups of the r order, then the incidence items in (t, in-before-out, r) order
     TK(c, "k_thead", k_thead<<<grid_for(E + 1, kBlock, kStreamCap), kBlock, 0, st>>>(o.it, E, s.gflag));

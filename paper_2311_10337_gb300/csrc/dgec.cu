@@ -343,7 +343,6 @@ LvDesc lv_desc(int64_t E, int32_t V, const dgec_levels_params *lp) {
 Problem lv_problem(const LvDesc &d) {
     Problem p = make_problem(d.hb());
     p.knn = false;
-    p.need_rank_of = true;
     return p;
 }
 

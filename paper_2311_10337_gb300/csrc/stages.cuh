@@ -27,7 +27,6 @@ struct Problem {
     int32_t *egraph = nullptr;        // [E] graph of each edge (built in stage A)
     bool knn = true;                  // stage B also writes the kNN lists
     int knn_form = 0;                 // kNN kernel form, fixed in stage A (knn_packed, when the span allows)
-    bool need_rank_of = false;        // stage A also writes rank_of (original id -> r; the levels stage reads it)
     int64_t dmax = INT64_MAX;         // time cutoff (Sec. 4.3): only links with w <= dmax
     int64_t links_cap = -1;           // skeleton capacity; -1 = 2E (graphs: <= 2 links per edge)
     bool mrd = false;                 // cluster the mutual-reachability graph (stage M)
@@ -63,7 +62,7 @@ struct Csr {
     int32_t *out_id, *in_id;    // [E] original ids (outputs)
     int32_t *out_r, *in_r;      // [E] internal ids of the same entries
     int32_t *orig_of;           // [E] r -> original id
-    int32_t *rank_of;           // [E] original id -> r (written when Problem::need_rank_of)
+    int32_t *rank_of;           // [E] original id -> r
     int32_t *isrc, *idst;       // [E] src, dst in r order
     int64_t *it;                // [E] t in r order
     int4 *outrk;                // [E] by r: (.x) global slot in the out-lists, (.y) b = #in-edges of
