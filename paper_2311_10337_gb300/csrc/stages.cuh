@@ -62,7 +62,7 @@ struct Csr {
     int32_t *out_id, *in_id;    // [E] original ids (outputs)
     int32_t *out_r, *in_r;      // [E] internal ids of the same entries
     int32_t *orig_of;           // [E] r -> original id
-    int32_t *rank_of;           // [E] original id -> r
+    int32_t *rank_of;           // [E] original id -> r (read by the forest, levels, MRD and NC stages)
     int32_t *isrc, *idst;       // [E] src, dst in r order
     int64_t *it;                // [E] t in r order
     int4 *outrk;                // [E] by r: (.x) global slot in the out-lists, (.y) b = #in-edges of
