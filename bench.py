@@ -240,6 +240,46 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def knn_roofline(timed, steps, E, k, knn_form, peak, peak_kind, breakdown, prefix="k_knn"):
+    """Roofline object of the kNN step from the kernel timers of the timed
+    steps. `timed` maps each kernel name timed (every name starting with
+    `prefix`: one launch a pass in the per-edge forms, the two passes
+    k_knn_pred and k_knn in the list-order form) to (total ms, launches).
+    The unit of work is the kNN step of one pass over the E edges, so
+    `achieved` is its algorithmic bytes (64 B/edge at k = 8)
+    over its device time per pass. `breakdown` (name -> (ms, launches)) of
+    one pass with every launch timed gives the step's share and the top
+    kernels. Returns (roofline dict, top kernels or None)."""
+    tot_ms = sum(v[0] for v in timed.values())
+    tot_n = sum(v[1] for v in timed.values())
+    kb = knn_bytes_per_edge(k)
+    per_pass = tot_ms / steps if tot_n else None
+    achieved = (kb * E) / (per_pass / 1000.0) / 1e9 if per_pass else None
+    per_edge = KNN_TRAFFIC_BYTES_PER_EDGE_K8.get(knn_form) if prefix == "k_knn" and k == 8 else None
+    traffic = per_edge * E if per_edge else None
+    share = None
+    top = None
+    if breakdown:
+        tot = sum(v[0] for v in breakdown.values())
+        mine = sum(v[0] for n_, v in breakdown.items() if n_.startswith(prefix))
+        if mine > 0 and tot > 0:
+            share = mine / tot
+        if tot > 0:
+            top = [[n, round(v[0], 3), v[1], round(v[0] / tot, 4)] for n, v in
+                   sorted(breakdown.items(), key=lambda kv: -kv[1][0])[:12]]
+    roof = {"bound": "hbm", "kernel": prefix, "achieved": achieved, "peak": peak,
+            "peak_kind": peak_kind, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": traffic,
+            "traffic_over_algorithmic": (traffic / (kb * E)) if traffic else None,
+            "algorithmic_bytes_per_edge": kb, "algorithmic_bytes_per_launch": kb * E,
+            "ms_per_pass": per_pass,
+            "avg_launch_ms": (tot_ms / tot_n) if tot_n else None,
+            "share_of_step": share,
+            "kernels": sorted(timed), "launches_per_step": tot_n / steps, "knn_form": knn_form}
+    return roof, top
+
+
 def stage_report(stages, E, k, peak):
     """Per-stage device time of one pass (CUDA events at the stage boundaries,
     from the library) against the stage's algorithmic bytes; D = D1 + D2."""
@@ -684,34 +724,12 @@ def run(args, rank, world, local, futs):
     torch.cuda.empty_cache()
     side = {}
     if rank == 0:
-        dom_ms, dom_n = dom
-        kb = knn_bytes_per_edge(k)
-        # one unit = the kNN step of one pass (one launch, or the two passes of the list-order form)
-        avg = dom_ms / args.steps if dom_n else None
-        achieved = (kb * E) / (avg / 1000.0) / 1e9 if avg else None
-        per_edge = KNN_TRAFFIC_BYTES_PER_EDGE_K8.get(knn_form)
-        traffic = (per_edge * E if args.roofline_kernel == "k_knn" and k == 8 and per_edge else None)
-        share = None
-        top = None
-        if bd:
-            tot = sum(v[0] for v in bd.values())
-            mine = sum(v[0] for n_, v in bd.items() if n_.startswith(args.roofline_kernel))
-            if mine > 0 and tot > 0:
-                share = mine / tot
-            top = [[n, round(v[0], 3), v[1], round(v[0] / tot, 4)] for n, v in
-                   sorted(bd.items(), key=lambda kv: -kv[1][0])[:12]]
-        roof = {"bound": "hbm", "kernel": args.roofline_kernel, "achieved": achieved, "peak": peak,
-                "peak_kind": peak_kind, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None,
-                "traffic": traffic,
-                "traffic_over_algorithmic": (traffic / (kb * E)) if traffic else None,
-                "algorithmic_bytes_per_edge": kb, "algorithmic_bytes_per_launch": kb * E,
-                "avg_launch_ms": avg, "share_of_step": share,
-                "kernels": sorted(dom_by), "launches_per_step": dom_n / args.steps, "knn_form": knn_form,
+        roof, top = knn_roofline(dom_by, args.steps, E, k, knn_form, peak, peak_kind, bd, args.roofline_kernel)
+        roof.update({
                 "stages": stage_report(stages, E, k, peak),
                 "pipeline": {"bytes_per_edge": pipeline_bytes_per_edge(k),
                              "achieved": pipeline_bytes_per_edge(k) * E / (ms / 1000.0) / 1e9,
-                             "frac": pipeline_bytes_per_edge(k) * E / (ms / 1000.0) / 1e9 / peak}}
+                             "frac": pipeline_bytes_per_edge(k) * E / (ms / 1000.0) / 1e9 / peak}})
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             try:
