@@ -688,7 +688,6 @@ def run(args, rank, world, local, futs):
     ms = ev0.elapsed_time(ev1) / args.steps
     stages = ctx.stage_timing()           # the last timed step, from the library's stage events
     dom_by = ctx.kernel_timing()
-    dom = (sum(v[0] for v in dom_by.values()), sum(v[1] for v in dom_by.values()))
     knn_form = ctx.launch_config()[2]
     ctx.set_kernel_timing(0)
     ms = max_over_ranks(ms, world, "cuda")
