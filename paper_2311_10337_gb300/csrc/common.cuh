@@ -251,26 +251,11 @@ __device__ __forceinline__ void atomic_add_u128(unsigned long long *hi,
     if (add_hi | carry) atomicAdd(hi, add_hi + carry);
 }
 
-// Adds the 64-bit `val` of every lane in `active` to the 128-bit counter
-// (hi[key], lo[key]), summing lanes that share a key first (one atomic pair
-// per distinct key per warp). The sum is exact: values are split into 16-bit
-// limbs whose warp sums fit in 32 bits.
-__device__ __forceinline__ void warp_add_u128(unsigned active, bool has, int key, unsigned long long val,
-                                              unsigned long long *hi, unsigned long long *lo) {
-    const unsigned peers = __match_any_sync(active, has ? key : -1);
-    if (!has) return;
-    unsigned s0 = __reduce_add_sync(peers, (unsigned)(val & 0xffffu));
-    unsigned s1 = __reduce_add_sync(peers, (unsigned)((val >> 16) & 0xffffu));
-    unsigned s2 = __reduce_add_sync(peers, (unsigned)((val >> 32) & 0xffffu));
-    unsigned s3 = __reduce_add_sync(peers, (unsigned)(val >> 48));
-    if ((int)lane_id() == __ffs(peers) - 1) {
-        unsigned __int128 tot = (unsigned __int128)s0 + ((unsigned __int128)s1 << 16) +
-                                ((unsigned __int128)s2 << 32) + ((unsigned __int128)s3 << 48);
-        atomic_add_u128(&hi[key], &lo[key], (unsigned long long)(tot >> 64), (unsigned long long)tot);
-    }
-}
-
-// The same for a 128-bit `val` below 2^96 (six 16-bit limbs).
+// Adds the `val` (below 2^96) of every lane in `active` with `has` set to
+// the 128-bit counter (hi[key], lo[key]), summing lanes that share a key
+// first (one atomic pair per distinct key per warp). The sum is exact: values
+// are split into six 16-bit limbs whose warp sums fit in 32 bits. All lanes
+// in `active` must call it.
 __device__ __forceinline__ void warp_add_u96(unsigned active, bool has, int key, unsigned __int128 val,
                                              unsigned long long *hi, unsigned long long *lo) {
     const unsigned peers = __match_any_sync(active, has ? key : -1);
